@@ -1,0 +1,93 @@
+"""Planted mistakes in the oracle must fail the pins.
+
+Each case swaps one oracle function for a copy with a plausible mistake (a
+dropped term, a wrong sign, a wrong weight) and checks that the pin that
+guards it reports a large residual.  The mistakes live only in this file.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from tests import pins
+
+
+def _hard_threshold_s_step(M, U, V, lam):
+    R = M - U @ V.T
+    return np.where(np.abs(R) > lam, R, 0.0)
+
+
+def _flipped_s_step(M, U, V, lam):
+    return -O.s_step(M, U, V, lam)
+
+
+def _v_step_no_rho(M, S, U, rho):
+    return O.v_step(M, S, U, 0.0)
+
+
+def _v_step_half_rho(M, S, U, rho):
+    return O.v_step(M, S, U, 0.5 * rho)
+
+
+def _v_step_ignores_S(M, S, U, rho):
+    return O.v_step(M, np.zeros_like(M), U, rho)
+
+
+def _u_exact_no_rho(Ms, Ss, Vs, rho):
+    return O.u_step_exact(Ms, Ss, Vs, 1e-12)
+
+
+def _u_exact_ignores_S(Ms, Ss, Vs, rho):
+    return O.u_step_exact(Ms, [np.zeros_like(S) for S in Ss], Vs, rho)
+
+
+def _grad_no_share(M_i, U, V_i, S_i, rho, n_i, n):
+    return rho * U + (U @ V_i.T + S_i - M_i) @ V_i
+
+
+def _grad_wrong_sign(M_i, U, V_i, S_i, rho, n_i, n):
+    return rho * (n_i / n) * U + (U @ V_i.T - S_i - M_i) @ V_i
+
+
+def _huber_no_offset(x, lam):
+    a = np.abs(np.asarray(x, dtype=float))
+    return float(np.sum(np.where(a <= lam, 0.5 * a * a, lam * a)))
+
+
+def _local_no_share(M_i, U, V_i, S_i, rho, lam, n_i, n):
+    return O.local_objective(M_i, U, V_i, S_i, rho, lam, n_i, n) \
+        - 0.5 * rho * (n_i / n) * float(np.sum(U * U))
+
+
+def _weighted_fedavg_iteration(M, n_i, U, V, rho, lam, *, u_mode=0, eta=0.0, local_steps=1):
+    # averages the client U_i with weights n_i/n instead of 1/E
+    off = O.block_offsets(n_i)
+    n = int(off[-1])
+    acc = np.zeros_like(U)
+    for i in range(len(n_i)):
+        Mi = M[:, off[i]:off[i + 1]]
+        Si = O.s_step(Mi, U, V[off[i]:off[i + 1]], lam)
+        Vi = O.v_step(Mi, Si, U, rho)
+        acc += (n_i[i] / n) * (U - eta * O.grad_U_local(Mi, U, Vi, Si, rho, int(n_i[i]), n))
+    return acc, None, None
+
+
+CASES = [
+    ("s_hard", lambda: pins.check_s_step(_hard_threshold_s_step)),
+    ("s_sign", lambda: pins.check_s_step(_flipped_s_step)),
+    ("v_no_rho", lambda: pins.check_v_step(_v_step_no_rho)),
+    ("v_half_rho", lambda: pins.check_v_step(_v_step_half_rho)),
+    ("v_ignores_S", lambda: pins.check_v_step(_v_step_ignores_S)),
+    ("u_no_rho", lambda: pins.check_u_step_exact(_u_exact_no_rho, O.objective)),
+    ("u_ignores_S", lambda: pins.check_u_step_exact(_u_exact_ignores_S, O.objective)),
+    ("grad_no_share", lambda: pins.check_grad_U_local(_grad_no_share, O.local_objective)),
+    ("grad_sign", lambda: pins.check_grad_U_local(_grad_wrong_sign, O.local_objective)),
+    ("huber_offset", lambda: pins.check_huber(_huber_no_offset)),
+    ("local_share", lambda: pins.check_local_split(_local_no_share, O.objective)),
+    ("fedavg_weights", lambda: pins.check_fedavg_is_global_gd(
+        _weighted_fedavg_iteration, O.objective, O.s_step, O.v_step)),
+]
+
+
+@pytest.mark.parametrize("name,run", CASES, ids=[c[0] for c in CASES])
+def test_planted_mistake_is_caught(name, run):
+    assert run() > 1e-4
