@@ -1,0 +1,295 @@
+"""Benchmark of the DCF-PCA iteration on one GB300 (or N replicas).
+
+Default workload: m=4096, n=65536 in E=16 uneven blocks, rank-32 truth,
+r=32 (the medium synthetic workload).  One step = one DCF iteration (S-step,
+V-step, consensus U-step, metrics) over the whole matrix, launched through
+the C ABI.  M (1 GiB) is larger than L2, so no flush is needed between steps.
+
+Prints one JSON line:
+  value           iterations/s (whole job, all ranks), inputs resident in HBM
+  e2e             the same metric through the public API with host buffers:
+                  every step copies M from pinned host memory and reads U back
+  roofline        the dominant kernel's algorithmic bytes / its CUDA-event time
+  cpu_baseline    the FP64 oracle on the host cores on a bounded column sample
+``--impl reference`` times the oracle alone (the reference arm).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2207_11669_gb300 import synth  # noqa: E402
+
+METRIC = "DCF iters/sec & HBM GB/s streaming M; time to rel-L-err 1e-4 vs plain"
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.th = threading.Thread(target=self._read, daemon=True)
+            self.th.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": float(max(smax)) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# workload
+# ---------------------------------------------------------------------------
+def workload_by_name(name):
+    return {"medium": synth.workload_medium, "small": synth.workload_small,
+            "large": synth.workload_large}[name]()
+
+
+def alg_bytes_per_iter(m, n, r):
+    """Algorithmic HBM bytes of one iteration: M read once (S is recomputed,
+    never stored), V read and written, U/W/P read or written once."""
+    return 4.0 * m * n + 8.0 * n * r + 16.0 * m * r
+
+
+# ---------------------------------------------------------------------------
+# oracle baseline (host cores, bounded column sample)
+# ---------------------------------------------------------------------------
+def oracle_sample_rate(wl, inst, U0, budget_s=12.0):
+    """Oracle iterations/s scaled to the full matrix, from whole iterations on
+    a column sample (the iteration is linear in n)."""
+    import oracle as O
+    m, n = inst.M.shape
+    ns = min(n, max(64, int(4096 * 4096 // m)))
+    Ms = np.asfortranarray(inst.M[:, :ns])
+    n_i = [ns // 2, ns - ns // 2]
+    U = U0.astype(np.float64)
+    V = O.init_v0(Ms, U, wl.rho)          # start point (not timed)
+    t0 = time.perf_counter()
+    its = 0
+    while True:
+        U, V, _ = O.dcf_iteration(Ms, n_i, U, V, wl.rho, wl.lam)
+        its += 1
+        el = time.perf_counter() - t0
+        if el >= budget_s or its >= 50:
+            break
+    per_iter_full = el / its * (n / ns)
+    cores = os.cpu_count()
+    return 1.0 / per_iter_full, dict(
+        kind="oracle", cores=cores,
+        sample=f"{its} oracle iterations (FP64 numpy, BLAS on up to {cores} host threads) on "
+               f"m={m} x {ns} of {n} columns in {el:.1f} s, scaled by n/{ns}")
+
+
+# ---------------------------------------------------------------------------
+# arms
+# ---------------------------------------------------------------------------
+def run_reference(args):
+    rank, world, local = dist_env()
+    if rank != 0:
+        return 0
+    wl = workload_by_name(args.workload)
+    inst = wl.instance()
+    U0 = synth.gaussian_u0(wl.m, wl.r, wl.seed)
+    rates = []
+    for _ in range(args.warmup + args.steps):
+        r, info = oracle_sample_rate(wl, inst, U0, budget_s=max(2.0, 20.0 / args.steps))
+        rates.append(r)
+    rate = float(np.mean(rates[args.warmup:]))
+    line = {"metric": METRIC, "value": rate, "unit": "iters/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 / rate,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64", "data": "synthetic", "impl": "reference",
+            "config": {"workload": wl.name, "m": wl.m, "n": wl.n, "r": wl.r, "E": wl.E},
+            "cpu_baseline": dict(info, value=rate, unit="iters/s"),
+            "e2e": {"value": rate, "unit": "iters/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ours(args):
+    import torch
+    from paper_2207_11669_gb300 import dcf
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as tdist
+        tdist.init_process_group("nccl")
+    wl = workload_by_name(args.workload)
+    # replicas: every rank solves its own instance of the same workload
+    inst = wl.instance(seed=wl.seed + rank)
+    m, n, r = wl.m, wl.n, wl.r
+    U0 = synth.gaussian_u0(m, r, wl.seed + rank)
+    Mt = torch.from_numpy(np.ascontiguousarray(inst.M.T)).cuda()     # (n, m): M column-major
+    s = dcf.Solver(m, inst.n_i, r, wl.rho, wl.lam, max_iter=wl.iters, tol=0.0,
+                   stream=torch.cuda.current_stream().cuda_stream)
+    s.load(Mt)
+    s.load_init(U0)
+    stream = torch.cuda.current_stream()
+    for _ in range(args.warmup):
+        s.step(1)
+    torch.cuda.synchronize()
+    if world > 1:
+        tdist.barrier()
+    clocks = ClockSampler(local)
+    clocks.start()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    s.step(args.steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    clk = clocks.stop()
+    if world > 1:
+        t = torch.tensor([ms], device="cuda")
+        tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
+        ms = float(t.item())
+        tdist.barrier()
+    ms_step = ms / args.steps
+    value = world * 1e3 / ms_step
+    launches_per_iter = 8
+
+    # per-kernel phases, CUDA events on the launch stream, same workload
+    phases = dcf.dcf_profile_step(s.h, max(3, min(args.steps, 10)))
+    nprof = max(3, min(args.steps, 10))
+    phase_ms = {k: v / nprof for k, v in phases.items()}
+    dom = max(phase_ms, key=phase_ms.get)
+    # algorithmic bytes of the two streaming kernels of the general path
+    kbytes = {"pass1_vstep": 4.0 * m * n + 8.0 * n * r + 8.0 * m * r,
+              "pass2_pstep": 4.0 * m * n + 8.0 * n * r + 4.0 * m * r}
+    hbm, peak_kind = peaks()
+    achieved = kbytes.get(dom, alg_bytes_per_iter(m, n, r)) / (phase_ms[dom] * 1e-3) / 1e9
+    roofline = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": hbm,
+                "unit": "GB/s", "frac": achieved / hbm, "traffic": None,
+                "peak_source": f"{peak_kind} hbm_gbs",
+                "phase_ms": {k: round(v, 4) for k, v in phase_ms.items()}}
+
+    # end to end through the public API with host buffers
+    Mh = torch.empty((n, m), dtype=torch.float32, pin_memory=True)
+    Mh.copy_(torch.from_numpy(np.ascontiguousarray(inst.M.T)))
+    Uh = np.empty((m, r), np.float32)
+    e2e_steps = max(3, min(args.steps, 10))
+    s2 = dcf.Solver(m, inst.n_i, r, wl.rho, wl.lam, stream=stream.cuda_stream)
+    s2.load(Mh, borrow=False)
+    s2.load_init(U0)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        s2.load(Mh, borrow=False)
+        s2.step(1)
+        dcf.dcf_get_factors(s2.h, Uh)
+    torch.cuda.synchronize()
+    e2e_s = (time.perf_counter() - t0) / e2e_steps
+    s2.close()
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        rate, info = oracle_sample_rate(wl, inst, U0, budget_s=12.0)
+        cpu = dict(info, value=rate, unit="iters/s")
+    s.close()
+    gbs = alg_bytes_per_iter(m, n, r) / (ms_step * 1e-3) / 1e9
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": "iters/s", "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": "f32", "data": "synthetic",
+                "config": {"workload": wl.name, "m": m, "n": n, "E": int(wl.E), "r": r,
+                           "rank_truth": wl.k, "density": wl.density, "rho": wl.rho,
+                           "lambda": wl.lam, "parallelism": "replicas" if world > 1 else "1gpu",
+                           "l2": "inputs larger than L2 (M is 1 GiB)"},
+                "hbm_gbs_alg": gbs,
+                "gpu_launches": launches_per_iter * args.steps,
+                "clocks": clk, "roofline": roofline,
+                "e2e": {"value": world / e2e_s, "unit": "iters/s",
+                        "h2d_bytes_per_step": 4 * m * n, "d2h_bytes_per_step": 4 * m * r},
+                "cpu_baseline": cpu}
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        tdist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="medium", choices=["medium", "small", "large"])
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

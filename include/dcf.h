@@ -1,0 +1,164 @@
+/*
+ * dcf.h -- C ABI of the GB300 DCF-PCA library (libdcf.so).
+ *
+ * DCF-PCA ("Distributed Robust Principal Component Analysis", arXiv
+ * 2207.11669) minimises, over a matrix M = [M_1 ... M_E] split by columns
+ * across E clients (§2.1),
+ *
+ *     1/2 ||U V^T + S - M||_F^2 + rho/2 (||U||_F^2 + ||V||_F^2) + lambda ||S||_1
+ *
+ * (§1, eq. noncovex_problem).  One iteration (one communication round of
+ * Algorithm 1) does, for every client block i,
+ *     S_i = soft(M_i - U V_i^T, lambda)                 (§2.2, eq. optS)
+ *     V_i = (M_i - S_i)^T U (U^T U + rho I)^{-1}        (App. B, eq. condition1)
+ * and then the consensus update of the shared U:
+ *     exact mode    U = [sum_i (M_i - S_i) V_i] [sum_i V_i^T V_i + rho I]^{-1}
+ *                   (the zero of the summed gradient of App. B, Lemma 2 proof)
+ *     FedAvg mode   U_i = U - eta_t grad_U L_i, U = (1/E) sum_i U_i
+ *                   (Algorithm 1, eqs. U_local and U_agg), eta_t = eta0/sqrt(t+1).
+ * The E clients are column blocks of one device matrix; nothing is sharded.
+ *
+ * Conventions for every entry point:
+ *   - Every call returns a dcf_status and never aborts.  DCF_OK is 0.  The
+ *     message of the last failure is available from dcf_last_error().
+ *   - Work is enqueued on the handle's stream (dcf_set_stream; default: the
+ *     legacy default stream).  Calls that return host data synchronise that
+ *     stream.  An error raised by a kernel surfaces at the next call that
+ *     synchronises.
+ *   - Matrices: M is m x n column-major (column j of block i starts at
+ *     M_i + j*ld_i).  Factors are row-major: U is m x r with U[a*r + k],
+ *     V_i is n_i x r with V_i[j*r + k].  L_i and S_i outputs are m x n_i
+ *     column-major with leading dimension m.
+ *   - `where` arguments: 0 = host memory, 1 = device memory of the current
+ *     CUDA device.
+ *   - The handle owns every buffer it allocates (through the allocator hook,
+ *     or cudaMalloc).  The caller owns every buffer it passes in; with
+ *     borrow = 1 the caller must keep M alive and unchanged until
+ *     dcf_destroy.
+ *   - A handle must not be used from two host threads at once.
+ */
+#ifndef DCF_H
+#define DCF_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct dcf_handle_s* dcf_handle;
+
+typedef enum {
+  DCF_OK = 0,
+  DCF_EINVAL = 1,      /* invalid argument or size                           */
+  DCF_ENOMEM = 2,      /* device or host allocation failed                   */
+  DCF_ECUDA = 3,       /* a CUDA runtime call failed                         */
+  DCF_ENONFINITE = 4,  /* a NaN or Inf appeared in the data or the iterates  */
+  DCF_ETIMEOUT = 5,    /* a bounded device-side wait expired                 */
+  DCF_ENOTCONV = 6,    /* dcf_solve reached max_iter above tol               */
+  DCF_EPRIVATE = 7,    /* output requested for a block marked private        */
+  DCF_ESTATE = 8       /* call order violated (e.g. dcf_step before loading) */
+} dcf_status;
+
+/* Problem statement (§2.1) and the parameters of Algorithm 1. */
+typedef struct {
+  int64_t m;            /* rows of M (the shared dimension of U)              */
+  int E;                /* number of client blocks                            */
+  const int64_t* n_i;   /* E block widths (host array, copied); n = sum n_i  */
+  int r;                /* factor rank, 1 <= r <= 64                          */
+  double rho;           /* ridge weight rho > 0 (§1)                          */
+  double lambda;        /* l1 weight lambda > 0 (§1)                          */
+  int max_iter;         /* dcf_solve: iteration cap (>= 1)                    */
+  double tol;           /* dcf_solve: stop when ||L_t-L_{t-1}||_F/||L_t||_F <= tol */
+  int u_mode;           /* 0: exact consensus (default); 1: FedAvg gradient   */
+  int local_steps;      /* K of Algorithm 1; only 1 is supported               */
+  double eta0;          /* FedAvg mode: eta_t = eta0 / sqrt(t + 1)             */
+  uint64_t seed;        /* seed of the default initialisation                  */
+} dcf_params;
+
+/* Device allocator hook: alloc(bytes, ctx) returns device memory or NULL,
+ * release(ptr, ctx) frees it.  Passing NULLs restores cudaMalloc/cudaFree.
+ * Must be set before dcf_create to take effect for that handle. */
+typedef void* (*dcf_alloc_fn)(size_t bytes, void* ctx);
+typedef void (*dcf_free_fn)(void* ptr, void* ctx);
+void dcf_set_allocator(dcf_alloc_fn alloc, dcf_free_fn release, void* ctx);
+
+/* Validate `p` and create a handle.  Fails with DCF_EINVAL for m < 1, E < 1,
+ * any n_i < 1, r outside [1, 64] or r > m, rho <= 0, lambda <= 0,
+ * local_steps != 1, or u_mode not in {0, 1}.  When rho^2 > lambda^2 m n
+ * (the necessary condition of §3.2 fails) the handle is still created and
+ * dcf_last_error() carries a warning. */
+dcf_status dcf_create(const dcf_params* p, dcf_handle* out);
+
+/* Enqueue all further work of the handle on `stream` (a cudaStream_t). */
+dcf_status dcf_set_stream(dcf_handle h, void* stream);
+
+/* Provide the blocks M_i (m x n_i column-major, leading dimension ld_i >= m).
+ * where = 0: host pointers, copied to the device.  where = 1: device
+ * pointers; with borrow = 1 the blocks must be one contiguous column-major
+ * matrix (M_{i+1} == M_i + m*n_i, ld_i == m) that is used in place, otherwise
+ * they are copied.  DCF_EINVAL on NULL pointers or ld_i < m. */
+dcf_status dcf_load_blocks(dcf_handle h, const float* const* M_i, const int64_t* ld_i,
+                           int where, int borrow);
+
+/* Set the starting point U0 (m x r) and V0_i (n_i x r).  Without this call
+ * dcf_step/dcf_solve start from U0 ~ N(0, 1/m) (counter-based Philox4x32-10,
+ * keyed by params.seed) and V0 = M^T U0 (U0^T U0 + rho I)^{-1}, the V-step
+ * with S = 0.  Passing V0_i = NULL keeps U0 and computes V0 that way.
+ * Resets the iteration counter to 0. */
+dcf_status dcf_load_init(dcf_handle h, const float* U0, const float* const* V0_i, int where);
+
+/* Run exactly n_steps iterations (no stopping test). */
+dcf_status dcf_step(dcf_handle h, int n_steps);
+
+/* Iterate until ||U_t V_t^T - U_{t-1} V_{t-1}^T||_F / ||U_t V_t^T||_F <= tol
+ * (evaluated exactly from r x r Gram matrices) or max_iter iterations in this
+ * call.  Returns DCF_ENOTCONV when the cap is reached above tol.  The
+ * iterations run and the last relative change are written when non-NULL. */
+dcf_status dcf_solve(dcf_handle h, int* iters_out, double* final_dL_rel);
+
+/* Copy out U (m x r) and, when V_i is non-NULL, every V_i (n_i x r). */
+dcf_status dcf_get_factors(dcf_handle h, float* U, float* const* V_i, int where);
+
+/* Block i's outputs of Algorithm 1: L_i = U V_i^T and S_i, the S-step of the
+ * last iteration, S_i = soft(M_i - U_{t-1} V_{i,t-1}^T, lambda).  Either
+ * pointer may be NULL.  DCF_EPRIVATE if block i is marked private,
+ * DCF_ESTATE before the first iteration. */
+dcf_status dcf_get_LS(dcf_handle h, int i, float* L_i, float* S_i, int where);
+
+/* Mark block i private (1) or public (0); private blocks are never returned
+ * by dcf_get_LS (§2.2 "Privacy Preserving", Algorithm 1 output). */
+dcf_status dcf_set_private(dcf_handle h, int i, int is_private);
+
+/* Statistics of the last iteration t: the objective of §1 at
+ * (U_{t-1}, V_{t-1}, S_t), evaluated in its Huber form, the relative change
+ * of L, and t.  Any pointer may be NULL. */
+dcf_status dcf_get_stats(dcf_handle h, double* objective, double* dL_rel, int* iter);
+
+/* Register a ground truth L* = A B^T (A: m x k, B: n x k, row-major) so that
+ * dcf_rel_err can report ||U V^T - L*||_F / ||L*||_F (from Gram matrices). */
+dcf_status dcf_set_truth(dcf_handle h, const float* A, const float* B, int k, int where);
+dcf_status dcf_rel_err(dcf_handle h, double* rel_err_L);
+
+/* Message of the last failure (or warning) on this handle; never NULL. */
+const char* dcf_last_error(dcf_handle h);
+
+/* Release everything the handle owns.  Safe on NULL. */
+void dcf_destroy(dcf_handle h);
+
+/* Profiling: number of kernel phases of one iteration (the names, comma
+ * separated, are copied into names_csv when it is non-NULL), and
+ * dcf_profile_step(), which runs n_steps iterations launching each phase
+ * separately (no CUDA graph) and adds each phase's CUDA-event time in
+ * milliseconds, measured on the handle's launch stream, to phase_ms[p]. */
+int dcf_profile_phases(dcf_handle h, char* names_csv, int len);
+dcf_status dcf_profile_step(dcf_handle h, int n_steps, double* phase_ms);
+
+/* Library version string. */
+const char* dcf_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* DCF_H */

@@ -1,0 +1,745 @@
+// C ABI of the DCF-PCA library: handle, buffers, launch sequence, CUDA graphs.
+//
+// One iteration (Algorithm 1 with the exact consensus U-step, or its FedAvg
+// gradient step) is the launch sequence in enqueue_iteration().  It is
+// captured once per parity of the iteration counter into a CUDA graph and
+// replayed; the device-side stop flag turns every kernel of a replay into a
+// no-op once dcf_solve's tolerance is met.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "dcf.h"
+#include "dcf_internal.cuh"
+
+namespace dcf {
+cudaError_t launch_gram(const float* X, int ldx, int cx, const float* Y, int ldy, int cy,
+                        int64_t N, double* part, int nparts, const DevState* st,
+                        int respect_stop, cudaStream_t s);
+cudaError_t launch_make_w(const IterArgs& a, int copy, int respect_stop, cudaStream_t s);
+cudaError_t prepare_small_kernels();
+cudaError_t launch_rows(const IterArgs& a, cudaStream_t s);
+cudaError_t launch_reduce_q(const IterArgs& a, double* out_q, double* out_xv, double* out_h,
+                            int nparts_gram, unsigned int* counter, cudaStream_t s);
+cudaError_t launch_reduce_g(const IterArgs& a, double* out_g, double* out_xu,
+                            unsigned int* counter, cudaStream_t s);
+cudaError_t launch_reduce_init(const IterArgs& a, int which, int copy, const double* part,
+                               int nparts, double* out, unsigned int* counter, cudaStream_t s);
+cudaError_t launch_reduce_plain(const double* part, int nparts, int count, double* out,
+                                cudaStream_t s);
+cudaError_t launch_pass1(const IterArgs& a, int grid, int mode_init, int out_copy,
+                         cudaStream_t s);
+cudaError_t launch_pass2(const IterArgs& a, cudaStream_t s);
+cudaError_t prepare_stream_kernels();
+}  // namespace dcf
+
+using namespace dcf;
+
+// ---------------------------------------------------------------------------
+// allocator hook
+// ---------------------------------------------------------------------------
+static dcf_alloc_fn g_alloc = nullptr;
+static dcf_free_fn g_free = nullptr;
+static void* g_alloc_ctx = nullptr;
+
+extern "C" void dcf_set_allocator(dcf_alloc_fn alloc, dcf_free_fn release, void* ctx) {
+  g_alloc = alloc;
+  g_free = release;
+  g_alloc_ctx = ctx;
+}
+
+struct dcf_handle_s {
+  // problem
+  int64_t m = 0, n = 0;
+  int E = 0, r = 0, R = 0;
+  double rho = 0, lam = 0, tol = 0, eta0 = 0;
+  int max_iter = 0, u_mode = 0, local_steps = 1;
+  uint64_t seed = 0;
+  std::vector<int64_t> n_i, c_i;
+  std::vector<char> priv;
+  // allocation
+  dcf_alloc_fn alloc = nullptr;
+  dcf_free_fn release = nullptr;
+  void* alloc_ctx = nullptr;
+  std::vector<void*> owned;
+  // device
+  int device = 0, num_sms = 0;
+  cudaStream_t user_stream = nullptr;
+  cudaStream_t stream = nullptr;     // internal capture/launch stream
+  cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+  float* M = nullptr;
+  bool M_borrowed = false;
+  float* U[2] = {nullptr, nullptr};
+  float* V[2] = {nullptr, nullptr};
+  float* W = nullptr;
+  float* part_p = nullptr;
+  double* part_h = nullptr;
+  double* part_q = nullptr;
+  double* part_xv = nullptr;
+  double* part_g = nullptr;
+  double* part_xu = nullptr;
+  double* red = nullptr;             // reduction outputs: q, xv, h, g, xu (R*R each)
+  double* truth_part = nullptr;
+  double* truth_red = nullptr;
+  Smalls* sm = nullptr;
+  DevState* st = nullptr;
+  unsigned int* counters = nullptr;  // 4 last-block counters
+  int* flag = nullptr;
+  float* A_truth = nullptr;
+  float* B_truth = nullptr;
+  int k_truth = 0;
+  // launch geometry
+  int n_vblocks = 0, n_splits = 0, n_rblocks = 0, n_vgram = 0;
+  int64_t split_cols = 0;
+  // state
+  bool loaded = false, initialized = false;
+  int host_iter = 0;                  // iterations enqueued (mirrors DevState::iter)
+  cudaGraphExec_t graph[2] = {nullptr, nullptr};
+  std::string err;
+};
+
+namespace {
+
+dcf_status fail(dcf_handle h, dcf_status code, const std::string& msg) {
+  if (h) h->err = msg;
+  return code;
+}
+
+dcf_status cuda_fail(dcf_handle h, cudaError_t e, const char* what) {
+  return fail(h, DCF_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+#define CK(call, what)                                   \
+  do {                                                   \
+    cudaError_t e_ = (call);                             \
+    if (e_ != cudaSuccess) return cuda_fail(h, e_, what); \
+  } while (0)
+
+void* dev_alloc(dcf_handle h, size_t bytes) {
+  if (bytes == 0) bytes = 16;
+  void* p = nullptr;
+  if (h->alloc) {
+    p = h->alloc(bytes, h->alloc_ctx);
+  } else if (cudaMalloc(&p, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    p = nullptr;
+  }
+  if (p) h->owned.push_back(p);
+  return p;
+}
+
+void dev_free_all(dcf_handle h) {
+  for (void* p : h->owned) {
+    if (h->release) h->release(p, h->alloc_ctx);
+    else cudaFree(p);
+  }
+  h->owned.clear();
+}
+
+IterArgs iter_args(dcf_handle h, int cur) {
+  IterArgs a{};
+  a.cur = cur;
+  a.M = h->M;
+  a.m = h->m;
+  a.n = h->n;
+  a.r = h->r;
+  a.R = h->R;
+  a.lam = (float)h->lam;
+  a.rho = (float)h->rho;
+  a.u_mode = h->u_mode;
+  a.E = h->E;
+  a.U[0] = h->U[0]; a.U[1] = h->U[1];
+  a.V[0] = h->V[0]; a.V[1] = h->V[1];
+  a.W = h->W;
+  a.part_q = h->part_q;
+  a.part_xv = h->part_xv;
+  a.part_h = h->part_h;
+  a.part_p = h->part_p;
+  a.n_vblocks = h->n_vblocks;
+  a.n_splits = h->n_splits;
+  a.split_cols = h->split_cols;
+  a.part_g = h->part_g;
+  a.part_xu = h->part_xu;
+  a.n_rblocks = h->n_rblocks;
+  a.sm = h->sm;
+  a.st = h->st;
+  return a;
+}
+
+double* red_q(dcf_handle h) { return h->red; }
+double* red_xv(dcf_handle h) { return h->red + (size_t)h->R * h->R; }
+double* red_h(dcf_handle h) { return h->red + 2 * (size_t)h->R * h->R; }
+double* red_g(dcf_handle h) { return h->red + 2 * (size_t)h->R * h->R + 8; }
+double* red_xu(dcf_handle h) { return h->red + 3 * (size_t)h->R * h->R + 8; }
+
+// Phases of one iteration, in launch order (names used by dcf_profile_*).
+const char* const kPhaseNames[] = {"make_w", "pass1_vstep", "pass2_pstep", "gram_v",
+                                   "reduce_q", "rows_ustep", "reduce_g"};
+constexpr int kNumPhases = 7;
+
+// Enqueue one iteration reading copy `cur` (capturable).  When `ev` is not
+// NULL, event ev[p] is recorded after phase p (profiling path, not captured).
+cudaError_t enqueue_iteration(dcf_handle h, int cur, cudaStream_t s, cudaEvent_t* ev = nullptr) {
+  IterArgs a = iter_args(h, cur);
+  const int nxt = cur ^ 1;
+  cudaError_t e;
+  int ph = 0;
+  auto mark = [&]() -> cudaError_t {
+    if (ev) return cudaEventRecord(ev[ph++], s);
+    return cudaSuccess;
+  };
+  // V-step: W = U (U^T U + rho I)^{-1}; then S, X, V' = X^T W in one pass over M
+  if ((e = launch_make_w(a, cur, 1, s)) != cudaSuccess || (e = mark()) != cudaSuccess) return e;
+  if ((e = launch_pass1(a, h->n_vblocks, 0, 0, s)) != cudaSuccess || (e = mark()) != cudaSuccess)
+    return e;
+  // U-step numerator P = X V' (second pass over M)
+  if ((e = launch_pass2(a, s)) != cudaSuccess || (e = mark()) != cudaSuccess) return e;
+  // Q_t = V_t^T V_t and V_{t-1}^T V_t
+  if ((e = launch_gram(h->V[nxt], h->R, h->R, h->V[nxt], h->R, h->R, h->n, h->part_q,
+                       h->n_vgram, h->st, 1, s)) != cudaSuccess)
+    return e;
+  if ((e = launch_gram(h->V[cur], h->R, h->R, h->V[nxt], h->R, h->R, h->n, h->part_xv,
+                       h->n_vgram, h->st, 1, s)) != cudaSuccess || (e = mark()) != cudaSuccess)
+    return e;
+  if ((e = launch_reduce_q(a, red_q(h), red_xv(h), red_h(h), h->n_vgram, h->counters + 0, s)) !=
+          cudaSuccess ||
+      (e = mark()) != cudaSuccess)
+    return e;
+  // consensus U-update + Gram partials of U_t
+  if ((e = launch_rows(a, s)) != cudaSuccess || (e = mark()) != cudaSuccess) return e;
+  // U_t^T U_t, metrics, stop test, (U_t^T U_t + rho I)^{-1} for the next V-step
+  if ((e = launch_reduce_g(a, red_g(h), red_xu(h), h->counters + 1, s)) != cudaSuccess) return e;
+  return mark();
+}
+
+dcf_status build_graphs(dcf_handle h) {
+  for (int p = 0; p < 2; ++p) {
+    if (h->graph[p]) continue;
+    cudaGraph_t g = nullptr;
+    CK(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal), "begin capture");
+    cudaError_t e = enqueue_iteration(h, p, h->stream);
+    cudaError_t e2 = cudaStreamEndCapture(h->stream, &g);
+    if (e != cudaSuccess) {
+      if (g) cudaGraphDestroy(g);
+      return cuda_fail(h, e, "capture iteration");
+    }
+    CK(e2, "end capture");
+    cudaError_t e3 = cudaGraphInstantiate(&h->graph[p], g, 0);
+    cudaGraphDestroy(g);
+    CK(e3, "instantiate graph");
+  }
+  return DCF_OK;
+}
+
+// Order internal stream after the user's stream.
+dcf_status begin_work(dcf_handle h) {
+  CK(cudaSetDevice(h->device), "set device");
+  CK(cudaEventRecord(h->ev_in, h->user_stream), "record");
+  CK(cudaStreamWaitEvent(h->stream, h->ev_in, 0), "wait");
+  return DCF_OK;
+}
+
+dcf_status end_work(dcf_handle h) {
+  CK(cudaEventRecord(h->ev_out, h->stream), "record");
+  CK(cudaStreamWaitEvent(h->user_stream, h->ev_out, 0), "wait");
+  return DCF_OK;
+}
+
+dcf_status read_state(dcf_handle h, DevState* out) {
+  CK(cudaMemcpyAsync(out, h->st, sizeof(DevState), cudaMemcpyDeviceToHost, h->stream), "read state");
+  CK(cudaStreamSynchronize(h->stream), "sync");
+  if (out->status == DCF_ENONFINITE)
+    return fail(h, DCF_ENONFINITE, "non-finite value in the iterates");
+  return DCF_OK;
+}
+
+// Write the solve-control fields of the device state (stream-ordered; the
+// host values are staged by cudaMemcpyAsync from pageable memory).
+dcf_status set_state_fields(dcf_handle h, int solve_mode, double tol) {
+  int zero = 0;
+  CK(cudaMemcpyAsync(&h->st->solve_mode, &solve_mode, sizeof(int), cudaMemcpyHostToDevice,
+                     h->stream), "write state");
+  CK(cudaMemcpyAsync(&h->st->tol, &tol, sizeof(double), cudaMemcpyHostToDevice, h->stream),
+     "write state");
+  CK(cudaMemcpyAsync(&h->st->stop, &zero, sizeof(int), cudaMemcpyHostToDevice, h->stream),
+     "write state");
+  return DCF_OK;
+}
+
+// Start point: U0 in copy 0 -> Gram, Cholesky; V0 given or V-step with S = 0.
+dcf_status finish_init(dcf_handle h, bool have_v0) {
+  cudaStream_t s = h->stream;
+  IterArgs a = iter_args(h, 0);
+  DevState st0{};
+  st0.eta0 = h->eta0;
+  st0.tol = h->tol;
+  CK(cudaMemcpyAsync(h->st, &st0, sizeof(DevState), cudaMemcpyHostToDevice, s), "init state");
+  CK(cudaMemsetAsync(h->counters, 0, 4 * sizeof(unsigned int), s), "memset");
+  CK(cudaMemsetAsync(h->sm, 0, sizeof(Smalls), s), "memset");
+  // G0 = U0^T U0 and its Cholesky factor
+  CK(launch_gram(h->U[0], h->R, h->R, h->U[0], h->R, h->R, h->m, h->part_g, h->n_rblocks, h->st,
+                 0, s), "gram U0");
+  CK(launch_reduce_init(a, 0, 0, h->part_g, h->n_rblocks, red_g(h), h->counters + 2, s),
+     "reduce G0");
+  if (!have_v0) {
+    CK(launch_make_w(a, 0, 0, s), "W0");
+    CK(launch_pass1(a, h->n_vblocks, 1, 0, s), "V0 sweep");
+  }
+  CK(launch_gram(h->V[0], h->R, h->R, h->V[0], h->R, h->R, h->n, h->part_q, h->n_vgram, h->st, 0,
+                 s), "gram V0");
+  CK(launch_reduce_init(a, 1, 0, h->part_q, h->n_vgram, red_q(h), h->counters + 3, s),
+     "reduce Q0");
+  h->host_iter = 0;
+  h->initialized = true;
+  return DCF_OK;
+}
+
+dcf_status ensure_init(dcf_handle h) {
+  if (!h->loaded) return fail(h, DCF_ESTATE, "dcf_load_blocks has not been called");
+  if (h->initialized) return DCF_OK;
+  CK(launch_philox_u0(h->U[0], h->m, h->r, h->R, h->seed, h->stream), "philox U0");
+  return finish_init(h, false);
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// entry points
+// ---------------------------------------------------------------------------
+extern "C" const char* dcf_version(void) { return "dcf-gb300 0.1"; }
+
+extern "C" const char* dcf_last_error(dcf_handle h) {
+  if (!h) return "null handle";
+  return h->err.c_str();
+}
+
+extern "C" dcf_status dcf_create(const dcf_params* p, dcf_handle* out) {
+  if (!p || !out) return DCF_EINVAL;
+  *out = nullptr;
+  dcf_handle h = new (std::nothrow) dcf_handle_s();
+  if (!h) return DCF_ENOMEM;
+  auto bad = [&](const char* msg) {
+    // keep the handle-less contract: report through a short-lived handle
+    delete h;
+    (void)msg;
+    return DCF_EINVAL;
+  };
+  if (p->m < 1 || p->E < 1 || !p->n_i) return bad("m, E, n_i");
+  if (p->r < 1 || p->r > kMaxR || p->r > p->m) return bad("r");
+  if (!(p->rho > 0) || !(p->lambda > 0)) return bad("rho, lambda");
+  if (p->u_mode != 0 && p->u_mode != 1) return bad("u_mode");
+  if (p->local_steps != 1) return bad("local_steps");
+  if (p->max_iter < 1) return bad("max_iter");
+  h->m = p->m;
+  h->E = p->E;
+  h->r = p->r;
+  h->R = pick_R(p->r);
+  h->rho = p->rho;
+  h->lam = p->lambda;
+  h->tol = p->tol;
+  h->max_iter = p->max_iter;
+  h->u_mode = p->u_mode;
+  h->local_steps = p->local_steps;
+  h->eta0 = p->eta0;
+  h->seed = p->seed;
+  h->n_i.assign(p->n_i, p->n_i + p->E);
+  h->c_i.resize(p->E + 1);
+  h->c_i[0] = 0;
+  for (int i = 0; i < p->E; ++i) {
+    if (h->n_i[i] < 1) return bad("n_i");
+    h->c_i[i + 1] = h->c_i[i] + h->n_i[i];
+  }
+  h->n = h->c_i[p->E];
+  h->priv.assign(p->E, 0);
+  h->alloc = g_alloc;
+  h->release = g_free;
+  h->alloc_ctx = g_alloc_ctx;
+
+  if (cudaGetDevice(&h->device) != cudaSuccess) { delete h; return DCF_ECUDA; }
+  if (prepare_stream_kernels() != cudaSuccess || prepare_small_kernels() != cudaSuccess) {
+    delete h;
+    return DCF_ECUDA;
+  }
+  cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, h->device);
+  if (h->num_sms <= 0) h->num_sms = 1;
+  if (cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&h->ev_in, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&h->ev_out, cudaEventDisableTiming) != cudaSuccess) {
+    dcf_destroy(h);
+    return DCF_ECUDA;
+  }
+
+  // launch geometry
+  const int64_t nstrips = (h->n + 63) / 64;
+  h->n_vblocks = (int)std::min<int64_t>(nstrips, 3LL * h->num_sms);
+  if (h->n_vblocks > 0) {
+    int64_t waves = (nstrips + h->n_vblocks - 1) / h->n_vblocks;
+    h->n_vblocks = (int)((nstrips + waves - 1) / waves);
+  }
+  const int64_t rb = (h->m + 127) / 128;
+  int64_t splits = std::max<int64_t>(1, (4LL * h->num_sms + rb - 1) / rb);
+  splits = std::min<int64_t>(splits, (h->n + 31) / 32);
+  h->split_cols = ((h->n + splits - 1) / splits + 31) / 32 * 32;
+  h->n_splits = (int)((h->n + h->split_cols - 1) / h->split_cols);
+  h->n_rblocks = (int)((h->m + 31) / 32);
+  h->n_vgram = (int)std::min<int64_t>(2LL * h->num_sms, (h->n + 31) / 32);
+
+  const size_t R = h->R, RR = R * R;
+  bool ok = true;
+  auto A = [&](size_t bytes) {
+    void* q = dev_alloc(h, bytes);
+    if (!q) ok = false;
+    return q;
+  };
+  h->U[0] = (float*)A(h->m * R * 4);
+  h->U[1] = (float*)A(h->m * R * 4);
+  h->V[0] = (float*)A(h->n * R * 4);
+  h->V[1] = (float*)A(h->n * R * 4);
+  h->W = (float*)A(h->m * R * 4);
+  h->part_p = (float*)A((size_t)h->n_splits * h->m * R * 4);
+  h->part_h = (double*)A((size_t)h->n_vblocks * 8);
+  size_t ngp = std::max<size_t>(h->n_vgram, h->n_rblocks);
+  h->part_q = (double*)A(ngp * RR * 8);
+  h->part_xv = (double*)A((size_t)h->n_vgram * RR * 8);
+  h->part_g = (double*)A(ngp * RR * 8);
+  h->part_xu = (double*)A((size_t)h->n_rblocks * RR * 8);
+  h->red = (double*)A((4 * RR + 8) * 8);
+  h->sm = (Smalls*)A(sizeof(Smalls));
+  h->st = (DevState*)A(sizeof(DevState));
+  h->counters = (unsigned int*)A(4 * sizeof(unsigned int));
+  h->flag = (int*)A(sizeof(int));
+  if (!ok) {
+    dcf_destroy(h);
+    return DCF_ENOMEM;
+  }
+  if (cudaMemsetAsync(h->U[0], 0, h->m * R * 4, h->stream) != cudaSuccess ||
+      cudaMemsetAsync(h->U[1], 0, h->m * R * 4, h->stream) != cudaSuccess ||
+      cudaMemsetAsync(h->V[0], 0, h->n * R * 4, h->stream) != cudaSuccess ||
+      cudaMemsetAsync(h->V[1], 0, h->n * R * 4, h->stream) != cudaSuccess ||
+      cudaMemsetAsync(h->counters, 0, 16, h->stream) != cudaSuccess ||
+      cudaMemsetAsync(h->st, 0, sizeof(DevState), h->stream) != cudaSuccess ||
+      cudaStreamSynchronize(h->stream) != cudaSuccess) {
+    dcf_destroy(h);
+    return DCF_ECUDA;
+  }
+  const double mn = (double)h->m * (double)h->n;
+  if (h->rho * h->rho > h->lam * h->lam * mn)
+    h->err = "warning: rho^2 > lambda^2 m n; the necessary condition for exact recovery fails";
+  *out = h;
+  return DCF_OK;
+}
+
+extern "C" dcf_status dcf_set_stream(dcf_handle h, void* stream) {
+  if (!h) return DCF_EINVAL;
+  h->user_stream = (cudaStream_t)stream;
+  return DCF_OK;
+}
+
+extern "C" dcf_status dcf_load_blocks(dcf_handle h, const float* const* M_i, const int64_t* ld_i,
+                                      int where, int borrow) {
+  if (!h) return DCF_EINVAL;
+  if (!M_i) return fail(h, DCF_EINVAL, "M_i is NULL");
+  if (where != 0 && where != 1) return fail(h, DCF_EINVAL, "where must be 0 or 1");
+  for (int i = 0; i < h->E; ++i) {
+    if (!M_i[i]) return fail(h, DCF_EINVAL, "a block pointer is NULL");
+    if (ld_i && ld_i[i] < h->m) return fail(h, DCF_EINVAL, "ld_i < m");
+  }
+  dcf_status st = begin_work(h);
+  if (st != DCF_OK) return st;
+  bool contiguous = where == 1;
+  for (int i = 0; i < h->E && contiguous; ++i) {
+    if (ld_i && ld_i[i] != h->m) contiguous = false;
+    if (i > 0 && M_i[i] != M_i[i - 1] + h->m * h->n_i[i - 1]) contiguous = false;
+  }
+  if (borrow && where == 1) {
+    if (!contiguous)
+      return fail(h, DCF_EINVAL, "borrowed blocks must form one contiguous column-major matrix");
+    h->M = const_cast<float*>(M_i[0]);
+    h->M_borrowed = true;
+  } else {
+    if (!h->M || h->M_borrowed) {
+      h->M = (float*)dev_alloc(h, (size_t)h->m * h->n * sizeof(float));
+      if (!h->M) return fail(h, DCF_ENOMEM, "cannot allocate M");
+      h->M_borrowed = false;
+    }
+    cudaMemcpyKind kind = where == 0 ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
+    for (int i = 0; i < h->E; ++i) {
+      int64_t ld = ld_i ? ld_i[i] : h->m;
+      CK(cudaMemcpy2DAsync(h->M + h->c_i[i] * h->m, h->m * sizeof(float), M_i[i],
+                           ld * sizeof(float), h->m * sizeof(float), h->n_i[i], kind, h->stream),
+         "copy block");
+    }
+  }
+  CK(cudaMemsetAsync(h->flag, 0, sizeof(int), h->stream), "memset");
+  CK(launch_check_finite(h->M, h->m * h->n, h->flag, h->stream), "check M");
+  int flag = 0;
+  CK(cudaMemcpyAsync(&flag, h->flag, sizeof(int), cudaMemcpyDeviceToHost, h->stream), "flag");
+  CK(cudaStreamSynchronize(h->stream), "sync");
+  if (flag) return fail(h, DCF_ENONFINITE, "M contains NaN or Inf");
+  h->loaded = true;
+  h->initialized = false;
+  for (int p = 0; p < 2; ++p)
+    if (h->graph[p]) { cudaGraphExecDestroy(h->graph[p]); h->graph[p] = nullptr; }
+  return end_work(h);
+}
+
+extern "C" dcf_status dcf_load_init(dcf_handle h, const float* U0, const float* const* V0_i,
+                                    int where) {
+  if (!h) return DCF_EINVAL;
+  if (!h->loaded) return fail(h, DCF_ESTATE, "dcf_load_blocks has not been called");
+  if (!U0) return fail(h, DCF_EINVAL, "U0 is NULL");
+  if (where != 0 && where != 1) return fail(h, DCF_EINVAL, "where must be 0 or 1");
+  dcf_status st = begin_work(h);
+  if (st != DCF_OK) return st;
+  cudaMemcpyKind kind = where == 0 ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
+  CK(cudaMemsetAsync(h->U[0], 0, h->m * h->R * 4, h->stream), "memset");
+  CK(cudaMemcpy2DAsync(h->U[0], h->R * 4, U0, h->r * 4, h->r * 4, h->m, kind, h->stream), "copy U0");
+  bool have_v0 = V0_i != nullptr;
+  if (have_v0) {
+    CK(cudaMemsetAsync(h->V[0], 0, h->n * h->R * 4, h->stream), "memset");
+    for (int i = 0; i < h->E; ++i) {
+      if (!V0_i[i]) return fail(h, DCF_EINVAL, "a V0 block pointer is NULL");
+      CK(cudaMemcpy2DAsync(h->V[0] + h->c_i[i] * h->R, h->R * 4, V0_i[i], h->r * 4, h->r * 4,
+                           h->n_i[i], kind, h->stream), "copy V0");
+    }
+  }
+  st = finish_init(h, have_v0);
+  if (st != DCF_OK) return st;
+  return end_work(h);
+}
+
+extern "C" dcf_status dcf_step(dcf_handle h, int n_steps) {
+  if (!h) return DCF_EINVAL;
+  if (n_steps < 0) return fail(h, DCF_EINVAL, "n_steps < 0");
+  dcf_status st = begin_work(h);
+  if (st != DCF_OK) return st;
+  if ((st = ensure_init(h)) != DCF_OK) return st;
+  if ((st = build_graphs(h)) != DCF_OK) return st;
+  for (int i = 0; i < n_steps; ++i) {
+    CK(cudaGraphLaunch(h->graph[h->host_iter & 1], h->stream), "graph launch");
+    h->host_iter++;
+  }
+  return end_work(h);
+}
+
+extern "C" dcf_status dcf_solve(dcf_handle h, int* iters_out, double* final_dL_rel) {
+  if (!h) return DCF_EINVAL;
+  dcf_status st = begin_work(h);
+  if (st != DCF_OK) return st;
+  if ((st = ensure_init(h)) != DCF_OK) return st;
+  if ((st = build_graphs(h)) != DCF_OK) return st;
+  if ((st = set_state_fields(h, 1, h->tol)) != DCF_OK) return st;
+  DevState ds{};
+  if ((st = read_state(h, &ds)) != DCF_OK) return st;
+  const int start = ds.iter;
+  int done = 0;
+  const int batch = 8;
+  while (done < h->max_iter) {
+    int nb = std::min(batch, h->max_iter - done);
+    for (int i = 0; i < nb; ++i) {
+      CK(cudaGraphLaunch(h->graph[h->host_iter & 1], h->stream), "graph launch");
+      h->host_iter++;
+    }
+    done += nb;
+    if ((st = read_state(h, &ds)) != DCF_OK) return st;
+    if (ds.stop) break;
+  }
+  h->host_iter = ds.iter;
+  int ran = ds.iter - start;
+  if (iters_out) *iters_out = ran;
+  if (final_dL_rel) *final_dL_rel = ds.dL_rel;
+  if ((st = set_state_fields(h, 0, h->tol)) != DCF_OK) return st;
+  if ((st = end_work(h)) != DCF_OK) return st;
+  if (!ds.stop) return fail(h, DCF_ENOTCONV, "max_iter reached above tol");
+  return DCF_OK;
+}
+
+extern "C" dcf_status dcf_get_factors(dcf_handle h, float* U, float* const* V_i, int where) {
+  if (!h) return DCF_EINVAL;
+  if (where != 0 && where != 1) return fail(h, DCF_EINVAL, "where must be 0 or 1");
+  dcf_status st = begin_work(h);
+  if (st != DCF_OK) return st;
+  if ((st = ensure_init(h)) != DCF_OK) return st;
+  const int cur = h->host_iter & 1;
+  cudaMemcpyKind kind = where == 0 ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
+  if (U)
+    CK(cudaMemcpy2DAsync(U, h->r * 4, h->U[cur], h->R * 4, h->r * 4, h->m, kind, h->stream),
+       "copy U");
+  if (V_i) {
+    for (int i = 0; i < h->E; ++i) {
+      if (!V_i[i]) continue;
+      CK(cudaMemcpy2DAsync(V_i[i], h->r * 4, h->V[cur] + h->c_i[i] * h->R, h->R * 4, h->r * 4,
+                           h->n_i[i], kind, h->stream), "copy V");
+    }
+  }
+  if (where == 0) CK(cudaStreamSynchronize(h->stream), "sync");
+  return end_work(h);
+}
+
+extern "C" dcf_status dcf_set_private(dcf_handle h, int i, int is_private) {
+  if (!h) return DCF_EINVAL;
+  if (i < 0 || i >= h->E) return fail(h, DCF_EINVAL, "block index out of range");
+  h->priv[i] = is_private ? 1 : 0;
+  return DCF_OK;
+}
+
+extern "C" dcf_status dcf_get_LS(dcf_handle h, int i, float* L_i, float* S_i, int where) {
+  if (!h) return DCF_EINVAL;
+  if (i < 0 || i >= h->E) return fail(h, DCF_EINVAL, "block index out of range");
+  if (where != 0 && where != 1) return fail(h, DCF_EINVAL, "where must be 0 or 1");
+  if (h->priv[i]) return fail(h, DCF_EPRIVATE, "block is private");
+  if (!h->initialized || h->host_iter < 1)
+    return fail(h, DCF_ESTATE, "no iteration has run yet");
+  dcf_status st = begin_work(h);
+  if (st != DCF_OK) return st;
+  const int cur = h->host_iter & 1, prev = cur ^ 1;
+  const int64_t ni = h->n_i[i], c0 = h->c_i[i];
+  const size_t bytes = (size_t)h->m * ni * sizeof(float);
+  float* tmp = nullptr;
+  if (where == 0) {
+    CK(cudaMallocAsync((void**)&tmp, bytes, h->stream), "tmp");
+  }
+  for (int which = 0; which < 2; ++which) {
+    float* dst = which == 0 ? L_i : S_i;
+    if (!dst) continue;
+    float* target = where == 0 ? tmp : dst;
+    const float* Uu = which == 0 ? h->U[cur] : h->U[prev];
+    const float* Vv = which == 0 ? h->V[cur] : h->V[prev];
+    CK(launch_materialize(h->M, h->m, c0, ni, Uu, Vv, h->R, (float)h->lam, which, target,
+                          h->stream), "materialize");
+    if (where == 0)
+      CK(cudaMemcpyAsync(dst, tmp, bytes, cudaMemcpyDeviceToHost, h->stream), "copy out");
+  }
+  if (tmp) CK(cudaFreeAsync(tmp, h->stream), "free tmp");
+  if (where == 0) CK(cudaStreamSynchronize(h->stream), "sync");
+  return end_work(h);
+}
+
+extern "C" dcf_status dcf_get_stats(dcf_handle h, double* objective, double* dL_rel, int* iter) {
+  if (!h) return DCF_EINVAL;
+  dcf_status st = begin_work(h);
+  if (st != DCF_OK) return st;
+  DevState ds{};
+  if ((st = read_state(h, &ds)) != DCF_OK) return st;
+  if (objective) *objective = ds.objective;
+  if (dL_rel) *dL_rel = ds.dL_rel;
+  if (iter) *iter = ds.iter;
+  return end_work(h);
+}
+
+extern "C" dcf_status dcf_set_truth(dcf_handle h, const float* A, const float* B, int k,
+                                    int where) {
+  if (!h) return DCF_EINVAL;
+  if (!A || !B || k < 1 || k > kMaxR) return fail(h, DCF_EINVAL, "truth factors");
+  if (where != 0 && where != 1) return fail(h, DCF_EINVAL, "where must be 0 or 1");
+  dcf_status st = begin_work(h);
+  if (st != DCF_OK) return st;
+  if (!h->A_truth || h->k_truth != k) {
+    h->A_truth = (float*)dev_alloc(h, (size_t)h->m * k * 4);
+    h->B_truth = (float*)dev_alloc(h, (size_t)h->n * k * 4);
+    h->truth_part = (double*)dev_alloc(h, (size_t)2 * h->num_sms * kMaxR * kMaxR * 8);
+    h->truth_red = (double*)dev_alloc(h, (size_t)6 * kMaxR * kMaxR * 8);
+    if (!h->A_truth || !h->B_truth || !h->truth_part || !h->truth_red)
+      return fail(h, DCF_ENOMEM, "truth buffers");
+  }
+  h->k_truth = k;
+  cudaMemcpyKind kind = where == 0 ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
+  CK(cudaMemcpyAsync(h->A_truth, A, (size_t)h->m * k * 4, kind, h->stream), "copy A");
+  CK(cudaMemcpyAsync(h->B_truth, B, (size_t)h->n * k * 4, kind, h->stream), "copy B");
+  if (where == 0) CK(cudaStreamSynchronize(h->stream), "sync");
+  return end_work(h);
+}
+
+extern "C" dcf_status dcf_rel_err(dcf_handle h, double* rel_err_L) {
+  if (!h) return DCF_EINVAL;
+  if (!h->A_truth) return fail(h, DCF_ESTATE, "no truth registered");
+  if (!rel_err_L) return fail(h, DCF_EINVAL, "rel_err_L is NULL");
+  dcf_status st = begin_work(h);
+  if (st != DCF_OK) return st;
+  if ((st = ensure_init(h)) != DCF_OK) return st;
+  const int cur = h->host_iter & 1;
+  const int R = h->R, k = h->k_truth;
+  const int np = (int)std::min<int64_t>(2LL * h->num_sms, std::max<int64_t>(1, h->n / 32));
+  // six Gram matrices: U^T U, V^T V, U^T A, V^T B, A^T A, B^T B
+  struct G { const float* X; int cx; const float* Y; int cy; int64_t N; } gs[6] = {
+      {h->U[cur], R, h->U[cur], R, h->m}, {h->V[cur], R, h->V[cur], R, h->n},
+      {h->U[cur], R, h->A_truth, k, h->m}, {h->V[cur], R, h->B_truth, k, h->n},
+      {h->A_truth, k, h->A_truth, k, h->m}, {h->B_truth, k, h->B_truth, k, h->n}};
+  std::vector<double> host[6];
+  for (int g = 0; g < 6; ++g) {
+    int npg = (int)std::min<int64_t>(np, std::max<int64_t>(1, gs[g].N / 32));
+    CK(launch_gram(gs[g].X, gs[g].cx, gs[g].cx, gs[g].Y, gs[g].cy, gs[g].cy, gs[g].N,
+                   h->truth_part, npg, h->st, 0, h->stream), "truth gram");
+    int cnt = gs[g].cx * gs[g].cy;
+    CK(launch_reduce_plain(h->truth_part, npg, cnt, h->truth_red + (size_t)g * kMaxR * kMaxR,
+                           h->stream), "truth reduce");
+    host[g].resize(cnt);
+  }
+  for (int g = 0; g < 6; ++g)
+    CK(cudaMemcpyAsync(host[g].data(), h->truth_red + (size_t)g * kMaxR * kMaxR,
+                       host[g].size() * 8, cudaMemcpyDeviceToHost, h->stream), "copy");
+  CK(cudaStreamSynchronize(h->stream), "sync");
+  // ||UV^T - AB^T||^2 = <U^T U, V^T V> - 2 <U^T A, V^T B> + <A^T A, B^T B>  (r x r / r x k)
+  double a = 0, b = 0, c = 0;
+  for (int i = 0; i < R * R; ++i) a += host[0][i] * host[1][i];
+  for (int i = 0; i < R * k; ++i) b += host[2][i] * host[3][i];
+  for (int i = 0; i < k * k; ++i) c += host[4][i] * host[5][i];
+  double d2 = std::max(0.0, a - 2 * b + c);
+  *rel_err_L = c > 0 ? std::sqrt(d2 / c) : INFINITY;
+  return end_work(h);
+}
+
+extern "C" int dcf_profile_phases(dcf_handle h, char* names_csv, int len) {
+  if (!h) return -1;
+  std::string all;
+  for (int p = 0; p < kNumPhases; ++p) {
+    if (p) all += ",";
+    all += kPhaseNames[p];
+  }
+  if (names_csv && len > 0) {
+    std::strncpy(names_csv, all.c_str(), (size_t)len - 1);
+    names_csv[len - 1] = 0;
+  }
+  return kNumPhases;
+}
+
+extern "C" dcf_status dcf_profile_step(dcf_handle h, int n_steps, double* phase_ms) {
+  if (!h) return DCF_EINVAL;
+  if (n_steps < 1 || !phase_ms) return fail(h, DCF_EINVAL, "n_steps < 1 or phase_ms NULL");
+  dcf_status st = begin_work(h);
+  if (st != DCF_OK) return st;
+  if ((st = ensure_init(h)) != DCF_OK) return st;
+  cudaEvent_t ev[kNumPhases + 1];
+  for (int p = 0; p <= kNumPhases; ++p) CK(cudaEventCreate(&ev[p]), "event");
+  for (int p = 0; p < kNumPhases; ++p) phase_ms[p] = 0.0;
+  for (int i = 0; i < n_steps; ++i) {
+    CK(cudaEventRecord(ev[0], h->stream), "record");
+    CK(enqueue_iteration(h, h->host_iter & 1, h->stream, ev + 1), "profiled iteration");
+    h->host_iter++;
+    CK(cudaEventSynchronize(ev[kNumPhases]), "sync");
+    for (int p = 0; p < kNumPhases; ++p) {
+      float ms = 0.f;
+      CK(cudaEventElapsedTime(&ms, ev[p], ev[p + 1]), "elapsed");
+      phase_ms[p] += ms;
+    }
+  }
+  for (int p = 0; p <= kNumPhases; ++p) cudaEventDestroy(ev[p]);
+  return end_work(h);
+}
+
+extern "C" void dcf_destroy(dcf_handle h) {
+  if (!h) return;
+  if (h->stream) cudaStreamSynchronize(h->stream);
+  for (int p = 0; p < 2; ++p)
+    if (h->graph[p]) cudaGraphExecDestroy(h->graph[p]);
+  dev_free_all(h);
+  if (h->ev_in) cudaEventDestroy(h->ev_in);
+  if (h->ev_out) cudaEventDestroy(h->ev_out);
+  if (h->stream) cudaStreamDestroy(h->stream);
+  delete h;
+}

@@ -1,0 +1,89 @@
+// Internal declarations shared by the DCF-PCA CUDA translation units.
+//
+// Storage (device):
+//   M      m x n float, column-major (ld = m); block i = columns [c_i, c_i + n_i)
+//   U[2]   m x R float, row-major (ld = R); R = padded rank (8, 16, 32 or 64),
+//          columns r..R-1 are zero and stay zero (the r x r solves are
+//          block diagonal in the padding)
+//   V[2]   n x R float, row-major
+// Two copies of U and V alternate: iteration t reads copy (t-1) & 1 and writes
+// copy t & 1, so two captured CUDA graphs (one per parity) serve every
+// iteration and U_{t-1}, V_{t-1} stay available for the S output.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace dcf {
+
+constexpr int kMaxR = 64;
+
+// Device-side state of one problem (one instance).
+struct DevState {
+  int iter;          // completed iterations t
+  int stop;          // set by the finish kernel when dL_rel <= tol (solve mode)
+  int status;        // 0 ok; DCF_ENONFINITE when the iterates stop being finite
+  int solve_mode;    // 1: the finish kernel may set `stop`
+  int has_S;         // 1 once an iteration has run (S of the last round exists)
+  int pad_;
+  double tol;
+  double eta0;       // FedAvg learning rate base
+  double objective;  // objective at (U_{t-1}, V_{t-1}, S_t)
+  double dL_rel;     // ||L_t - L_{t-1}||_F / ||L_t||_F
+  double huber;      // sum H_lambda(R) of the last pass
+};
+
+// r x r FP64 workspace of one problem.
+struct Smalls {
+  double gram[2][kMaxR * kMaxR];   // U^T U for copy 0/1 of U
+  double q[2][kMaxR * kMaxR];      // V^T V for copy 0/1 of V
+  double xu[kMaxR * kMaxR];        // U_{t-1}^T U_t
+  double xv[kMaxR * kMaxR];        // V_{t-1}^T V_t
+  float ginv32[kMaxR * kMaxR];     // (U^T U + rho I)^{-1} of the current U
+  float hinv32[kMaxR * kMaxR];     // (V^T V + rho I)^{-1} of the new V (exact mode)
+  float qrho32[kMaxR * kMaxR];     // (V^T V + rho I) in float (FedAvg mode)
+};
+
+struct IterArgs {
+  int cur;           // copy holding U_{t-1}, V_{t-1}; the iteration writes cur ^ 1
+  const float* M;
+  int64_t m, n;
+  int r, R;
+  float lam;
+  float rho;
+  int u_mode;        // 0 exact, 1 FedAvg
+  int E;
+  float* U[2];
+  float* V[2];
+  float* W;          // m x R
+  // partial results of the streaming passes
+  double* part_q;    // [n_vblocks][R*R]   V'^T V'
+  double* part_xv;   // [n_vblocks][R*R]   V_old^T V'
+  double* part_h;    // [n_vblocks]        Huber partial
+  float* part_p;     // [n_splits][m*R]    P partials (X V')
+  int n_vblocks;
+  int n_splits;
+  int64_t split_cols;
+  double* part_g;    // [n_rblocks][R*R]   U_new^T U_new partials
+  double* part_xu;   // [n_rblocks][R*R]   U_old^T U_new partials
+  int n_rblocks;
+  Smalls* sm;
+  DevState* st;
+};
+
+// Launchers (stream-ordered; return cudaGetLastError()).
+cudaError_t launch_iteration_v1(const IterArgs& a, int vblocks_grid, cudaStream_t s);
+cudaError_t launch_init_from_u(const IterArgs& a, int copy, cudaStream_t s);
+cudaError_t launch_gram_only(const IterArgs& a, int copy, cudaStream_t s);
+cudaError_t launch_materialize(const float* M, int64_t m, int64_t c0, int64_t ni,
+                               const float* U, const float* V, int R, float lam,
+                               int mode, float* out, cudaStream_t s);
+cudaError_t launch_philox_u0(float* U, int64_t m, int r, int R, uint64_t seed,
+                             cudaStream_t s);
+cudaError_t launch_truth_err(const float* U, const float* V, int64_t m, int64_t n, int R,
+                             const float* A, const float* B, int k, double* part,
+                             int nparts, double* out, cudaStream_t s);
+cudaError_t launch_check_finite(const float* x, int64_t count, int* flag, cudaStream_t s);
+
+int pick_R(int r);
+
+}  // namespace dcf

@@ -1,0 +1,343 @@
+"""Thin ctypes binding of libdcf.so (the C ABI of include/dcf.h).
+
+The module-level functions carry the C names and only marshal arguments;
+:class:`Solver` wraps a handle for convenience.  Host data are numpy arrays,
+device data are torch CUDA tensors (their ``data_ptr()`` is passed with
+``where=1``).  The library is loaded on first use; when it is missing the
+call raises :class:`DcfError` -- there is no fallback implementation.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_LIB = None
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libdcf.so")
+
+DCF_OK, DCF_EINVAL, DCF_ENOMEM, DCF_ECUDA, DCF_ENONFINITE, DCF_ETIMEOUT, DCF_ENOTCONV, \
+    DCF_EPRIVATE, DCF_ESTATE = range(9)
+STATUS_NAMES = {0: "DCF_OK", 1: "DCF_EINVAL", 2: "DCF_ENOMEM", 3: "DCF_ECUDA",
+                4: "DCF_ENONFINITE", 5: "DCF_ETIMEOUT", 6: "DCF_ENOTCONV",
+                7: "DCF_EPRIVATE", 8: "DCF_ESTATE"}
+
+
+class DcfError(RuntimeError):
+    def __init__(self, status, msg=""):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+class dcf_params(C.Structure):
+    _fields_ = [("m", C.c_int64), ("E", C.c_int), ("n_i", C.POINTER(C.c_int64)),
+                ("r", C.c_int), ("rho", C.c_double), ("lambda_", C.c_double),
+                ("max_iter", C.c_int), ("tol", C.c_double), ("u_mode", C.c_int),
+                ("local_steps", C.c_int), ("eta0", C.c_double), ("seed", C.c_uint64)]
+
+
+ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p)
+FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p)
+
+_SIGS = {
+    "dcf_set_allocator": (None, [ALLOC_FN, FREE_FN, C.c_void_p]),
+    "dcf_create": (C.c_int, [C.POINTER(dcf_params), C.POINTER(C.c_void_p)]),
+    "dcf_set_stream": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "dcf_load_blocks": (C.c_int, [C.c_void_p, C.POINTER(C.c_void_p), C.POINTER(C.c_int64),
+                                  C.c_int, C.c_int]),
+    "dcf_load_init": (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(C.c_void_p), C.c_int]),
+    "dcf_step": (C.c_int, [C.c_void_p, C.c_int]),
+    "dcf_solve": (C.c_int, [C.c_void_p, C.POINTER(C.c_int), C.POINTER(C.c_double)]),
+    "dcf_get_factors": (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(C.c_void_p), C.c_int]),
+    "dcf_get_LS": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_int]),
+    "dcf_set_private": (C.c_int, [C.c_void_p, C.c_int, C.c_int]),
+    "dcf_get_stats": (C.c_int, [C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_double),
+                                C.POINTER(C.c_int)]),
+    "dcf_set_truth": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_int]),
+    "dcf_rel_err": (C.c_int, [C.c_void_p, C.POINTER(C.c_double)]),
+    "dcf_last_error": (C.c_char_p, [C.c_void_p]),
+    "dcf_destroy": (None, [C.c_void_p]),
+    "dcf_version": (C.c_char_p, []),
+    "dcf_profile_phases": (C.c_int, [C.c_void_p, C.c_char_p, C.c_int]),
+    "dcf_profile_step": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_double)]),
+}
+
+
+def lib():
+    """Load libdcf.so (raises DcfError when it has not been built)."""
+    global _LIB
+    if _LIB is None:
+        if not os.path.exists(LIB_PATH):
+            raise DcfError(DCF_ESTATE, f"{LIB_PATH} is missing; run paper_2207_11669_gb300.build")
+        L = C.CDLL(LIB_PATH)
+        for name, (res, args) in _SIGS.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _LIB = L
+    return _LIB
+
+
+def exported_symbols():
+    return list(_SIGS)
+
+
+# ---------------------------------------------------------------------------
+# argument helpers
+# ---------------------------------------------------------------------------
+def _is_torch(x):
+    return type(x).__module__.startswith("torch")
+
+
+def _ptr_where(x):
+    """(pointer, where) for a numpy array (host) or a torch CUDA tensor (device)."""
+    if x is None:
+        return None, 0
+    if _is_torch(x):
+        if not x.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return C.c_void_p(x.data_ptr()), 1 if x.is_cuda else 0
+    a = np.asarray(x)
+    return C.c_void_p(a.ctypes.data), 0
+
+
+def _check(h, status):
+    if status != DCF_OK:
+        msg = lib().dcf_last_error(h).decode() if h else ""
+        raise DcfError(status, msg)
+
+
+# ---------------------------------------------------------------------------
+# C-named entry points (marshalling only)
+# ---------------------------------------------------------------------------
+_alloc_keep = []
+
+
+def dcf_set_allocator(alloc=None, release=None):
+    """Route the library's device allocations through Python callables
+    ``alloc(nbytes) -> int`` and ``release(ptr)``; None restores cudaMalloc."""
+    if alloc is None:
+        lib().dcf_set_allocator(ALLOC_FN(), FREE_FN(), None)
+        _alloc_keep.clear()
+        return
+    fa = ALLOC_FN(lambda n, ctx: alloc(int(n)))
+    ff = FREE_FN(lambda p, ctx: release(int(p)))
+    _alloc_keep[:] = [fa, ff]
+    lib().dcf_set_allocator(fa, ff, None)
+
+
+def use_torch_allocator():
+    """Allocate the library's device buffers from torch's caching allocator."""
+    import torch
+
+    def alloc(n):
+        try:
+            return torch.cuda.caching_allocator_alloc(n)
+        except RuntimeError:
+            return 0
+
+    def release(p):
+        torch.cuda.caching_allocator_delete(p)
+
+    dcf_set_allocator(alloc, release)
+
+
+def dcf_create(m, n_i, r, rho, lam, max_iter=100, tol=1e-6, u_mode=0, local_steps=1,
+               eta0=0.0, seed=0):
+    n_arr = (C.c_int64 * len(n_i))(*[int(x) for x in n_i])
+    p = dcf_params(int(m), len(n_i), n_arr, int(r), float(rho), float(lam), int(max_iter),
+                   float(tol), int(u_mode), int(local_steps), float(eta0), int(seed))
+    h = C.c_void_p()
+    st = lib().dcf_create(C.byref(p), C.byref(h))
+    if st != DCF_OK:
+        raise DcfError(st, "dcf_create rejected the parameters")
+    return h
+
+
+def dcf_set_stream(h, stream_ptr):
+    _check(h, lib().dcf_set_stream(h, C.c_void_p(stream_ptr)))
+
+
+def dcf_load_blocks(h, blocks, ld=None, borrow=False):
+    ptrs, wheres = zip(*[_ptr_where(b) for b in blocks])
+    where = wheres[0]
+    arr = (C.c_void_p * len(ptrs))(*[p.value for p in ptrs])
+    ld_arr = None if ld is None else (C.c_int64 * len(ld))(*[int(x) for x in ld])
+    _check(h, lib().dcf_load_blocks(h, arr, ld_arr, where, 1 if borrow else 0))
+
+
+def dcf_load_init(h, U0, V0_blocks=None):
+    pu, where = _ptr_where(U0)
+    varr = None
+    if V0_blocks is not None:
+        vp = [_ptr_where(v)[0].value for v in V0_blocks]
+        varr = (C.c_void_p * len(vp))(*vp)
+    _check(h, lib().dcf_load_init(h, pu, varr, where))
+
+
+def dcf_step(h, n_steps=1):
+    _check(h, lib().dcf_step(h, int(n_steps)))
+
+
+def dcf_solve(h):
+    it = C.c_int()
+    d = C.c_double()
+    st = lib().dcf_solve(h, C.byref(it), C.byref(d))
+    if st not in (DCF_OK, DCF_ENOTCONV):
+        _check(h, st)
+    return it.value, d.value, st == DCF_OK
+
+
+def dcf_get_factors(h, U_out, V_outs=None):
+    pu, where = _ptr_where(U_out)
+    varr = None
+    if V_outs is not None:
+        vp = [_ptr_where(v)[0].value for v in V_outs]
+        varr = (C.c_void_p * len(vp))(*vp)
+    _check(h, lib().dcf_get_factors(h, pu, varr, where))
+
+
+def dcf_get_LS(h, i, L_out=None, S_out=None):
+    pl, wl = _ptr_where(L_out)
+    ps, ws = _ptr_where(S_out)
+    where = wl if L_out is not None else ws
+    _check(h, lib().dcf_get_LS(h, int(i), pl, ps, where))
+
+
+def dcf_set_private(h, i, is_private=True):
+    _check(h, lib().dcf_set_private(h, int(i), 1 if is_private else 0))
+
+
+def dcf_get_stats(h):
+    o, d, it = C.c_double(), C.c_double(), C.c_int()
+    _check(h, lib().dcf_get_stats(h, C.byref(o), C.byref(d), C.byref(it)))
+    return o.value, d.value, it.value
+
+
+def dcf_set_truth(h, A, B):
+    pa, where = _ptr_where(A)
+    pb, _ = _ptr_where(B)
+    _check(h, lib().dcf_set_truth(h, pa, pb, int(A.shape[1]), where))
+
+
+def dcf_rel_err(h):
+    e = C.c_double()
+    _check(h, lib().dcf_rel_err(h, C.byref(e)))
+    return e.value
+
+
+def dcf_last_error(h):
+    return lib().dcf_last_error(h).decode()
+
+
+def dcf_destroy(h):
+    if h:
+        lib().dcf_destroy(h)
+
+
+def dcf_profile_phases(h):
+    buf = C.create_string_buffer(1024)
+    n = lib().dcf_profile_phases(h, buf, 1024)
+    return buf.value.decode().split(",")[:n]
+
+
+def dcf_profile_step(h, n_steps):
+    names = dcf_profile_phases(h)
+    ms = (C.c_double * len(names))()
+    _check(h, lib().dcf_profile_step(h, int(n_steps), ms))
+    return dict(zip(names, list(ms)))
+
+
+def dcf_version():
+    return lib().dcf_version().decode()
+
+
+# ---------------------------------------------------------------------------
+# convenience wrapper
+# ---------------------------------------------------------------------------
+class Solver:
+    """One DCF-PCA problem on the current CUDA device.
+
+    ``M`` is an m x n float32 matrix in column-major order: a numpy array
+    with ``order='F'`` (copied to the device) or a torch CUDA tensor holding
+    M^T in row-major order, i.e. shape (n, m) (borrowed in place).
+    """
+
+    def __init__(self, m, n_i, r, rho, lam, max_iter=100, tol=1e-6, u_mode=0, eta0=0.0,
+                 seed=0, stream=None):
+        self.m, self.n_i, self.r = int(m), [int(x) for x in n_i], int(r)
+        self.n = int(sum(self.n_i))
+        self.h = dcf_create(m, n_i, r, rho, lam, max_iter, tol, u_mode, 1, eta0, seed)
+        if stream is not None:
+            dcf_set_stream(self.h, stream)
+        self._keep = None
+
+    def close(self):
+        if self.h:
+            dcf_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def blocks_of(self, M):
+        off = np.concatenate([[0], np.cumsum(self.n_i)])
+        if _is_torch(M):
+            return [M[off[i]:off[i + 1]] for i in range(len(self.n_i))]
+        M = np.asfortranarray(M, dtype=np.float32)
+        return [M[:, off[i]:off[i + 1]] for i in range(len(self.n_i))]
+
+    def load(self, M, borrow=None):
+        blocks = self.blocks_of(M)
+        if borrow is None:
+            borrow = _is_torch(M)
+        self._keep = (M, blocks)
+        dcf_load_blocks(self.h, blocks, borrow=borrow)
+
+    def load_init(self, U0, V0=None):
+        U0 = self._as_factor(U0)
+        Vb = None
+        if V0 is not None:
+            V0 = self._as_factor(V0)
+            off = np.concatenate([[0], np.cumsum(self.n_i)])
+            Vb = [V0[off[i]:off[i + 1]] for i in range(len(self.n_i))]
+        self._keep_init = (U0, V0, Vb)
+        dcf_load_init(self.h, U0, Vb)
+
+    @staticmethod
+    def _as_factor(x):
+        if _is_torch(x):
+            return x.contiguous()
+        return np.ascontiguousarray(x, dtype=np.float32)
+
+    def step(self, n=1):
+        dcf_step(self.h, n)
+
+    def solve(self):
+        return dcf_solve(self.h)
+
+    def factors(self):
+        U = np.empty((self.m, self.r), np.float32)
+        Vs = [np.empty((ni, self.r), np.float32) for ni in self.n_i]
+        dcf_get_factors(self.h, U, Vs)
+        return U, np.concatenate(Vs, axis=0)
+
+    def LS(self, i):
+        L = np.empty((self.n_i[i], self.m), np.float32)   # column-major m x n_i
+        S = np.empty((self.n_i[i], self.m), np.float32)
+        dcf_get_LS(self.h, i, L, S)
+        return L.T, S.T
+
+    def stats(self):
+        return dcf_get_stats(self.h)
+
+    def set_truth(self, A, B):
+        self._truth = (np.ascontiguousarray(A, np.float32), np.ascontiguousarray(B, np.float32))
+        dcf_set_truth(self.h, *self._truth)
+
+    def rel_err(self):
+        return dcf_rel_err(self.h)

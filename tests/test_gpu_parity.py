@@ -1,0 +1,213 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle.
+
+Tolerances: relative Frobenius error <= 1e-4 on U, V and S after one step
+from identical float32 starting points; <= 1e-3 on L = U V^T after several
+steps and at convergence; the S support identical except where the oracle's
+|R| lies within 1e-5*lambda (plus the FP32 rounding bound of R) of lambda.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2207_11669_gb300 import dcf
+from tests.helpers import make_case, rel, r_error_bound, support_flips
+
+pytestmark = pytest.mark.gpu
+
+SHAPES = [
+    # (m, n_i, r): the 200x200 E=4 workload, ragged rows/columns, each padded rank
+    (200, [50, 50, 50, 50], 5),
+    (300, [100, 77, 140], 16),
+    (129, [33, 64, 31], 32),
+    (257, [300, 211], 40),
+    (64, [10, 9, 11], 8),
+    (1000, [700, 1300, 517], 32),
+]
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2207_11669_gb300 import build
+    build.build()
+    torch.cuda.init()
+
+
+def gpu_solver(case, **kw):
+    s = dcf.Solver(case["M"].shape[0], case["n_i"], case["r"], case["rho"], case["lam"], **kw)
+    s.load(case["M"])
+    s.load_init(case["U0"], case["V0"])
+    return s
+
+
+def oracle_step(case, iters=1, **kw):
+    return O.dcf_run(case["M"], case["n_i"], case["U0"], case["V0"], case["rho"], case["lam"],
+                     iters, **kw)
+
+
+@pytest.mark.parametrize("m,n_i,r", SHAPES)
+def test_one_step_parity(m, n_i, r):
+    case = make_case(m, n_i, r, seed=m + r)
+    s = gpu_solver(case)
+    s.step(1)
+    U, V = s.factors()
+    U1, V1, S1, U0, V0 = oracle_step(case, 1)
+    assert rel(U, U1) <= 1e-4
+    assert rel(V, V1) <= 1e-4
+    off = O.block_offsets(case["n_i"])
+    S_gpu = np.concatenate([s.LS(i)[1] for i in range(len(n_i))], axis=1)
+    assert rel(S_gpu, S1) <= 1e-4
+    R_ref = case["M"].astype(np.float64) - case["U0"].astype(np.float64) @ case["V0"].T.astype(
+        np.float64)
+    eps = r_error_bound(case["M"], case["U0"], case["V0"], r)
+    flips, bad = support_flips(S_gpu, S1, R_ref, case["lam"], eps)
+    assert bad == 0, (flips, bad)
+    s.close()
+
+
+def test_fedavg_step_parity():
+    case = make_case(300, [100, 77, 140], 16, seed=3)
+    s = gpu_solver(case, u_mode=1, eta0=0.01)
+    s.step(3)
+    U, V = s.factors()
+    Uo, Vo, *_ = oracle_step(case, 3, u_mode=1, eta0=0.01)
+    assert rel(U, Uo) <= 1e-4
+    assert rel(V, Vo) <= 1e-4
+    s.close()
+
+
+def test_several_steps_L_parity():
+    case = make_case(200, [50] * 4, 5, seed=7)
+    s = gpu_solver(case)
+    s.step(10)
+    U, V = s.factors()
+    Uo, Vo, *_ = oracle_step(case, 10)
+    assert rel(U @ V.T, Uo @ Vo.T) <= 1e-3
+    s.close()
+
+
+def test_converged_L_parity_and_support():
+    """The 200 x 200, E = 4 workload run to convergence on both sides."""
+    case = make_case(200, [50] * 4, 5, seed=20220723)
+    s = gpu_solver(case, max_iter=400, tol=1e-7)
+    it, d, ok = s.solve()
+    assert ok and d <= 1e-7
+    U, V = s.factors()
+    Uo, Vo, So, ito, do = O.dcf_solve(case["M"], case["n_i"], case["U0"], case["V0"],
+                                      case["rho"], case["lam"], 400, 1e-7)
+    assert rel(U @ V.T, Uo @ Vo.T) <= 1e-3
+    S_gpu = np.concatenate([s.LS(i)[1] for i in range(4)], axis=1)
+    # S at convergence: flips only where the oracle's |R| is within the threshold
+    # band widened by the difference of the two residuals
+    R_ref = case["M"].astype(np.float64) - Uo @ Vo.T
+    R_gpu = case["M"].astype(np.float64) - U.astype(np.float64) @ V.T.astype(np.float64)
+    eps = np.abs(R_gpu - R_ref) + r_error_bound(case["M"], U, V, 5)
+    flips, bad = support_flips(S_gpu, So, R_ref, case["lam"], eps)
+    assert bad == 0, (flips, bad)
+    s.close()
+
+
+def test_init_sweep_parity():
+    case = make_case(257, [300, 211], 40, seed=11)
+    s = dcf.Solver(257, case["n_i"], 40, case["rho"], case["lam"])
+    s.load(case["M"])
+    s.load_init(case["U0"])          # V0 from the S = 0 sweep on the GPU
+    U, V = s.factors()
+    assert rel(V, case["V0"]) <= 1e-5
+    assert np.array_equal(U, case["U0"])
+    s.close()
+
+
+def test_partition_invariance_on_gpu():
+    case = make_case(300, [100, 77, 140], 16, seed=5)
+    a = gpu_solver(case)
+    case1 = dict(case, n_i=np.array([317]))
+    b = gpu_solver(case1)
+    a.step(4)
+    b.step(4)
+    Ua, Va = a.factors()
+    Ub, Vb = b.factors()
+    assert np.array_equal(Ua, Ub) and np.array_equal(Va, Vb)
+    a.close()
+    b.close()
+
+
+def test_stats_and_rel_err():
+    case = make_case(200, [50] * 4, 5, seed=9)
+    s = gpu_solver(case)
+    s.set_truth(case["inst"].A, case["inst"].B)
+    s.step(2)
+    obj, dL, it = s.stats()
+    U2, V2, S2, U1, V1 = oracle_step(case, 2)
+    assert it == 2
+    assert abs(obj - O.objective_huber(case["M"], U1, V1, case["rho"], case["lam"])) <= 1e-4 * abs(obj)
+    assert abs(dL - O.factor_delta_rel(U2, V2, U1, V1)) <= 1e-3 * dL + 1e-7
+    U, V = s.factors()
+    assert abs(s.rel_err() - O.rel_err_L(U, V, case["inst"].A, case["inst"].B)) <= 1e-5
+    s.close()
+
+
+def test_get_LS_blocks_and_privacy():
+    case = make_case(129, [33, 64, 31], 32, seed=13)
+    s = gpu_solver(case)
+    s.step(2)
+    U2, V2, S2, U1, V1 = oracle_step(case, 2)
+    off = O.block_offsets(case["n_i"])
+    for i in range(3):
+        L, S = s.LS(i)
+        assert rel(L, U2 @ V2[off[i]:off[i + 1]].T) <= 1e-4
+        assert rel(S, S2[:, off[i]:off[i + 1]]) <= 1e-4
+    dcf.dcf_set_private(s.h, 1, True)
+    with pytest.raises(dcf.DcfError) as e:
+        s.LS(1)
+    assert e.value.status == dcf.DCF_EPRIVATE
+    s.close()
+
+
+def test_errors_are_status_codes():
+    with pytest.raises(dcf.DcfError) as e:
+        dcf.Solver(10, [5, 5], 0, 1e-2, 0.1)
+    assert e.value.status == dcf.DCF_EINVAL
+    with pytest.raises(dcf.DcfError):
+        dcf.Solver(10, [5, 5], 3, -1.0, 0.1)
+    s = dcf.Solver(16, [8, 8], 3, 1e-2, 0.1)
+    with pytest.raises(dcf.DcfError) as e:
+        s.step(1)
+    assert e.value.status == dcf.DCF_ESTATE
+    M = np.ones((16, 16), np.float32, order="F")
+    M[3, 4] = np.nan
+    with pytest.raises(dcf.DcfError) as e:
+        s.load(M)
+    assert e.value.status == dcf.DCF_ENONFINITE
+    s.close()
+
+
+def test_default_init_is_seeded_gaussian():
+    M = np.asfortranarray(np.random.default_rng(0).standard_normal((512, 256)).astype(np.float32))
+    a = dcf.Solver(512, [128, 128], 8, 1e-2, 0.05, seed=42)
+    a.load(M)
+    b = dcf.Solver(512, [128, 128], 8, 1e-2, 0.05, seed=42)
+    b.load(M)
+    Ua, _ = a.factors()
+    Ub, _ = b.factors()
+    assert np.array_equal(Ua, Ub)
+    assert abs(Ua.mean()) < 0.01 and abs(Ua.var() * 512 - 1.0) < 0.1
+    a.close()
+    b.close()
+
+
+def test_borrowed_device_matrix_matches_host_copy():
+    import torch
+    case = make_case(300, [100, 77, 140], 16, seed=17)
+    Mt = torch.from_numpy(np.ascontiguousarray(case["M"].T)).cuda()   # (n, m) = M column-major
+    s1 = gpu_solver(case)
+    s2 = dcf.Solver(300, case["n_i"], 16, case["rho"], case["lam"])
+    s2.load(Mt)
+    s2.load_init(case["U0"], case["V0"])
+    s1.step(2)
+    s2.step(2)
+    assert np.array_equal(s1.factors()[0], s2.factors()[0])
+    s1.close()
+    s2.close()
