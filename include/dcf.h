@@ -155,6 +155,15 @@ void dcf_destroy(dcf_handle h);
 int dcf_profile_phases(dcf_handle h, char* names_csv, int len);
 dcf_status dcf_profile_step(dcf_handle h, int n_steps, double* phase_ms);
 
+/* Diagnostic: one tcgen05 MMA (fp16 operands, FP32 accumulators in tensor
+ * memory) on integer test data with caller-chosen operand layouts and
+ * descriptor strides; copies the 128 x 256 accumulator region to out_host.
+ * cfg = {M, N, K, a_kind (0 smem K-major, 1 smem MN-major, 2 TMEM),
+ *        a_lbo, a_sbo, desc_a_lbo, desc_a_sbo, b_lbo, b_sbo, desc_b_lbo,
+ *        desc_b_sbo}.  Used by the tests that pin the tensor-core layouts the
+ * fused kernel uses; no counterpart in the paper. */
+int dcf_tc_selftest(const int* cfg, float* out_host);
+
 /* Library version string. */
 const char* dcf_version(void);
 

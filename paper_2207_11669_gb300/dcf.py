@@ -61,6 +61,7 @@ _SIGS = {
     "dcf_version": (C.c_char_p, []),
     "dcf_profile_phases": (C.c_int, [C.c_void_p, C.c_char_p, C.c_int]),
     "dcf_profile_step": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_double)]),
+    "dcf_tc_selftest": (C.c_int, [C.POINTER(C.c_int), C.POINTER(C.c_float)]),
 }
 
 
@@ -247,6 +248,16 @@ def dcf_profile_step(h, n_steps):
     ms = (C.c_double * len(names))()
     _check(h, lib().dcf_profile_step(h, int(n_steps), ms))
     return dict(zip(names, list(ms)))
+
+
+def dcf_tc_selftest(cfg):
+    """Run the tensor-core layout self-test; returns the 128 x 256 accumulator dump."""
+    arr = (C.c_int * 12)(*[int(x) for x in cfg])
+    out = np.zeros((128, 256), np.float32)
+    st = lib().dcf_tc_selftest(arr, out.ctypes.data_as(C.POINTER(C.c_float)))
+    if st != DCF_OK:
+        raise DcfError(st, "dcf_tc_selftest")
+    return out
 
 
 def dcf_version():
