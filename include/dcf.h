@@ -75,6 +75,10 @@ typedef struct {
   int local_steps;      /* K of Algorithm 1; only 1 is supported               */
   double eta0;          /* FedAvg mode: eta_t = eta0 / sqrt(t + 1)             */
   uint64_t seed;        /* seed of the default initialisation                  */
+  int path;             /* 0: automatic; 1: general two-pass kernels; 2: fused
+                           single-pass tensor-core kernel (DCF_EINVAL if the
+                           shape does not qualify: r <= 32, m % 4 == 0,
+                           m <= 4096)                                          */
 } dcf_params;
 
 /* Device allocator hook: alloc(bytes, ctx) returns device memory or NULL,
@@ -90,6 +94,10 @@ void dcf_set_allocator(dcf_alloc_fn alloc, dcf_free_fn release, void* ctx);
  * (the necessary condition of §3.2 fails) the handle is still created and
  * dcf_last_error() carries a warning. */
 dcf_status dcf_create(const dcf_params* p, dcf_handle* out);
+
+/* Which kernels run an iteration: 1 general two-pass path, 2 fused
+ * single-pass tensor-core path. */
+int dcf_get_path(dcf_handle h);
 
 /* Enqueue all further work of the handle on `stream` (a cudaStream_t). */
 dcf_status dcf_set_stream(dcf_handle h, void* stream);

@@ -96,6 +96,15 @@ struct dcf_handle_s {
   // launch geometry
   int n_vblocks = 0, n_splits = 0, n_rblocks = 0, n_vgram = 0;
   int64_t split_cols = 0;
+  // fused single-pass path
+  int path = 1;                       // 1 general, 2 fused
+  int cs = 0, nclusters = 0, nslabs = 0;
+  uint8_t* img = nullptr;
+  float* scales = nullptr;
+  float* zmat = nullptr;
+  unsigned int* vmax = nullptr;       // [2]: max |V| of copy 0 / 1 (float bits)
+  int* kerr = nullptr;                // kernel-side error (DCF_ETIMEOUT)
+  alignas(64) unsigned char tmap[128];
   // state
   bool loaded = false, initialized = false;
   int host_iter = 0;                  // iterations enqueued (mirrors DevState::iter)
@@ -168,6 +177,11 @@ IterArgs iter_args(dcf_handle h, int cur) {
   a.n_rblocks = h->n_rblocks;
   a.sm = h->sm;
   a.st = h->st;
+  a.add_uxv = h->path == 2 ? 1 : 0;
+  if (h->path == 2) {
+    a.n_vblocks = h->cs * h->nclusters;   // per-CTA partials of the fused kernel
+    a.n_splits = h->nclusters;            // P partials: one per cluster
+  }
   return a;
 }
 
@@ -181,10 +195,66 @@ double* red_xu(dcf_handle h) { return h->red + 3 * (size_t)h->R * h->R + 8; }
 const char* const kPhaseNames[] = {"make_w", "pass1_vstep", "pass2_pstep", "gram_v",
                                    "reduce_q", "rows_ustep", "reduce_g"};
 constexpr int kNumPhases = 7;
+const char* const kFusedPhaseNames[] = {"fused_prep", "fused_step", "reduce_q", "rows_ustep",
+                                        "reduce_g"};
+constexpr int kNumFusedPhases = 5;
+int num_phases(dcf_handle h) { return h->path == 2 ? kNumFusedPhases : kNumPhases; }
+const char* phase_name(dcf_handle h, int p) {
+  return h->path == 2 ? kFusedPhaseNames[p] : kPhaseNames[p];
+}
+
+// One iteration of the fused path: prep (W and fp16 images), the single pass
+// over M, Q/X_v reduction with (Q + rho I)^{-1}, consensus rows, metrics.
+cudaError_t enqueue_fused_iteration(dcf_handle h, int cur, cudaStream_t s, cudaEvent_t* ev) {
+  IterArgs a = iter_args(h, cur);
+  const int nxt = cur ^ 1;
+  cudaError_t e;
+  int ph = 0;
+  auto mark = [&]() -> cudaError_t {
+    if (ev) return cudaEventRecord(ev[ph++], s);
+    return cudaSuccess;
+  };
+  if ((e = launch_fused_prep(h->R, h->U[cur], h->sm, h->st, h->m, h->nslabs, (float)h->rho,
+                             h->vmax + cur, h->vmax + nxt, h->img, h->scales, h->zmat, s)) !=
+          cudaSuccess ||
+      (e = mark()) != cudaSuccess)
+    return e;
+  FusedArgs fa{};
+  fa.cur = cur;
+  fa.cs = h->cs;
+  fa.nclusters = h->nclusters;
+  fa.nslabs = h->nslabs;
+  fa.m = h->m;
+  fa.n = h->n;
+  fa.lam = (float)h->lam;
+  fa.Vold = h->V[cur];
+  fa.Vnew = h->V[nxt];
+  fa.img = h->img;
+  fa.scales = h->scales;
+  fa.zmat = h->zmat;
+  fa.vmax_out = h->vmax + nxt;
+  fa.part_q = h->part_q;
+  fa.part_xv = h->part_xv;
+  fa.part_h = h->part_h;
+  fa.part_p = h->part_p;
+  fa.st = h->st;
+  fa.err = h->kerr;
+  if ((e = launch_fused(h->R, h->tmap, fa, s)) != cudaSuccess || (e = mark()) != cudaSuccess)
+    return e;
+  const int grid = h->cs * h->nclusters;
+  if ((e = launch_reduce_q(a, red_q(h), red_xv(h), red_h(h), grid, h->counters + 0, s)) !=
+          cudaSuccess ||
+      (e = mark()) != cudaSuccess)
+    return e;
+  if ((e = launch_rows(a, s)) != cudaSuccess || (e = mark()) != cudaSuccess) return e;
+  if ((e = launch_reduce_g(a, red_g(h), red_xu(h), h->counters + 1, s)) != cudaSuccess) return e;
+  return mark();
+}
 
 // Enqueue one iteration reading copy `cur` (capturable).  When `ev` is not
 // NULL, event ev[p] is recorded after phase p (profiling path, not captured).
 cudaError_t enqueue_iteration(dcf_handle h, int cur, cudaStream_t s, cudaEvent_t* ev = nullptr) {
+  if (h->path == 2) return enqueue_fused_iteration(h, cur, s, ev);
   IterArgs a = iter_args(h, cur);
   const int nxt = cur ^ 1;
   cudaError_t e;
@@ -251,8 +321,12 @@ dcf_status end_work(dcf_handle h) {
 }
 
 dcf_status read_state(dcf_handle h, DevState* out) {
+  int kerr = 0;
   CK(cudaMemcpyAsync(out, h->st, sizeof(DevState), cudaMemcpyDeviceToHost, h->stream), "read state");
+  CK(cudaMemcpyAsync(&kerr, h->kerr, sizeof(int), cudaMemcpyDeviceToHost, h->stream), "read err");
   CK(cudaStreamSynchronize(h->stream), "sync");
+  if (kerr == DCF_ETIMEOUT)
+    return fail(h, DCF_ETIMEOUT, "a bounded device-side wait expired in the fused kernel");
   if (out->status == DCF_ENONFINITE)
     return fail(h, DCF_ENONFINITE, "non-finite value in the iterates");
   return DCF_OK;
@@ -292,6 +366,10 @@ dcf_status finish_init(dcf_handle h, bool have_v0) {
   }
   CK(launch_gram(h->V[0], h->R, h->R, h->V[0], h->R, h->R, h->n, h->part_q, h->n_vgram, h->st, 0,
                  s), "gram V0");
+  if (h->path == 2) {
+    CK(cudaMemsetAsync(h->vmax, 0, 2 * sizeof(unsigned int), s), "memset");
+    CK(launch_absmax(h->V[0], h->n * h->R, h->vmax, s), "max |V0|");
+  }
   CK(launch_reduce_init(a, 1, 0, h->part_q, h->n_vgram, red_q(h), h->counters + 3, s),
      "reduce Q0");
   h->host_iter = 0;
@@ -335,6 +413,7 @@ extern "C" dcf_status dcf_create(const dcf_params* p, dcf_handle* out) {
   if (p->u_mode != 0 && p->u_mode != 1) return bad("u_mode");
   if (p->local_steps != 1) return bad("local_steps");
   if (p->max_iter < 1) return bad("max_iter");
+  if (p->path < 0 || p->path > 2) return bad("path");
   h->m = p->m;
   h->E = p->E;
   h->r = p->r;
@@ -374,6 +453,33 @@ extern "C" dcf_status dcf_create(const dcf_params* p, dcf_handle* out) {
     return DCF_ECUDA;
   }
 
+  // fused single-pass path: r <= 32, m a multiple of 4 (TMA row stride), at most
+  // 16 slabs of 256 rows per cluster, and the cluster shape must fit on the GPU
+  {
+    const bool shape_ok = p->r <= 32 && h->m % 4 == 0 && (h->m + 255) / 256 <= 16;
+    if (p->path == 2 && !shape_ok) {
+      dcf_destroy(h);
+      return DCF_EINVAL;
+    }
+    if (p->path != 1 && shape_ok) {
+      const int Rf = p->r <= 16 ? 16 : 32;
+      const int cs = (int)((h->m + 255) / 256);
+      int ncl = 0;
+      if (fused_prepare(Rf) == cudaSuccess) ncl = fused_max_clusters(Rf, cs);
+      cudaGetLastError();
+      if (ncl > 0) {
+        h->path = 2;
+        h->R = Rf;
+        h->cs = cs;
+        h->nslabs = cs;
+        const int64_t nstrips64 = (h->n + 63) / 64;
+        h->nclusters = (int)std::min<int64_t>(ncl, nstrips64);
+      } else if (p->path == 2) {
+        dcf_destroy(h);
+        return DCF_EINVAL;
+      }
+    }
+  }
   // launch geometry
   const int64_t nstrips = (h->n + 63) / 64;
   h->n_vblocks = (int)std::min<int64_t>(nstrips, 3LL * h->num_sms);
@@ -413,6 +519,18 @@ extern "C" dcf_status dcf_create(const dcf_params* p, dcf_handle* out) {
   h->st = (DevState*)A(sizeof(DevState));
   h->counters = (unsigned int*)A(4 * sizeof(unsigned int));
   h->flag = (int*)A(sizeof(int));
+  h->kerr = (int*)A(sizeof(int));
+  if (h->path == 2) {
+    const size_t grid = (size_t)h->cs * h->nclusters;
+    h->img = (uint8_t*)A((size_t)h->nslabs * 2048 * R);
+    h->scales = (float*)A((2 * (size_t)h->nslabs + 1) * sizeof(float));
+    h->zmat = (float*)A(RR * sizeof(float));
+    h->vmax = (unsigned int*)A(2 * sizeof(unsigned int));
+    h->part_p = (float*)A((size_t)h->nclusters * h->m * R * 4);
+    h->part_h = (double*)A(grid * 8);
+    h->part_q = (double*)A(std::max(grid, ngp) * RR * 8);
+    h->part_xv = (double*)A(std::max(grid, (size_t)h->n_vgram) * RR * 8);
+  }
   if (!ok) {
     dcf_destroy(h);
     return DCF_ENOMEM;
@@ -422,6 +540,7 @@ extern "C" dcf_status dcf_create(const dcf_params* p, dcf_handle* out) {
       cudaMemsetAsync(h->V[0], 0, h->n * R * 4, h->stream) != cudaSuccess ||
       cudaMemsetAsync(h->V[1], 0, h->n * R * 4, h->stream) != cudaSuccess ||
       cudaMemsetAsync(h->counters, 0, 16, h->stream) != cudaSuccess ||
+      cudaMemsetAsync(h->kerr, 0, sizeof(int), h->stream) != cudaSuccess ||
       cudaMemsetAsync(h->st, 0, sizeof(DevState), h->stream) != cudaSuccess ||
       cudaStreamSynchronize(h->stream) != cudaSuccess) {
     dcf_destroy(h);
@@ -433,6 +552,8 @@ extern "C" dcf_status dcf_create(const dcf_params* p, dcf_handle* out) {
   *out = h;
   return DCF_OK;
 }
+
+extern "C" int dcf_get_path(dcf_handle h) { return h ? h->path : 0; }
 
 extern "C" dcf_status dcf_set_stream(dcf_handle h, void* stream) {
   if (!h) return DCF_EINVAL;
@@ -481,6 +602,8 @@ extern "C" dcf_status dcf_load_blocks(dcf_handle h, const float* const* M_i, con
   CK(cudaMemcpyAsync(&flag, h->flag, sizeof(int), cudaMemcpyDeviceToHost, h->stream), "flag");
   CK(cudaStreamSynchronize(h->stream), "sync");
   if (flag) return fail(h, DCF_ENONFINITE, "M contains NaN or Inf");
+  if (h->path == 2 && fused_make_tmap(h->tmap, h->M, h->m, h->n) != 0)
+    return fail(h, DCF_ECUDA, "cuTensorMapEncodeTiled failed for M");
   h->loaded = true;
   h->initialized = false;
   for (int p = 0; p < 2; ++p)
@@ -697,15 +820,15 @@ extern "C" dcf_status dcf_rel_err(dcf_handle h, double* rel_err_L) {
 extern "C" int dcf_profile_phases(dcf_handle h, char* names_csv, int len) {
   if (!h) return -1;
   std::string all;
-  for (int p = 0; p < kNumPhases; ++p) {
+  for (int p = 0; p < num_phases(h); ++p) {
     if (p) all += ",";
-    all += kPhaseNames[p];
+    all += phase_name(h, p);
   }
   if (names_csv && len > 0) {
     std::strncpy(names_csv, all.c_str(), (size_t)len - 1);
     names_csv[len - 1] = 0;
   }
-  return kNumPhases;
+  return num_phases(h);
 }
 
 extern "C" dcf_status dcf_profile_step(dcf_handle h, int n_steps, double* phase_ms) {
@@ -714,21 +837,22 @@ extern "C" dcf_status dcf_profile_step(dcf_handle h, int n_steps, double* phase_
   dcf_status st = begin_work(h);
   if (st != DCF_OK) return st;
   if ((st = ensure_init(h)) != DCF_OK) return st;
+  const int np = num_phases(h);
   cudaEvent_t ev[kNumPhases + 1];
-  for (int p = 0; p <= kNumPhases; ++p) CK(cudaEventCreate(&ev[p]), "event");
-  for (int p = 0; p < kNumPhases; ++p) phase_ms[p] = 0.0;
+  for (int p = 0; p <= np; ++p) CK(cudaEventCreate(&ev[p]), "event");
+  for (int p = 0; p < np; ++p) phase_ms[p] = 0.0;
   for (int i = 0; i < n_steps; ++i) {
     CK(cudaEventRecord(ev[0], h->stream), "record");
     CK(enqueue_iteration(h, h->host_iter & 1, h->stream, ev + 1), "profiled iteration");
     h->host_iter++;
-    CK(cudaEventSynchronize(ev[kNumPhases]), "sync");
-    for (int p = 0; p < kNumPhases; ++p) {
+    CK(cudaEventSynchronize(ev[np]), "sync");
+    for (int p = 0; p < np; ++p) {
       float ms = 0.f;
       CK(cudaEventElapsedTime(&ms, ev[p], ev[p + 1]), "elapsed");
       phase_ms[p] += ms;
     }
   }
-  for (int p = 0; p <= kNumPhases; ++p) cudaEventDestroy(ev[p]);
+  for (int p = 0; p <= np; ++p) cudaEventDestroy(ev[p]);
   return end_work(h);
 }
 

@@ -68,6 +68,7 @@ struct IterArgs {
   int n_rblocks;
   Smalls* sm;
   DevState* st;
+  int add_uxv;       // 1: P[a,:] += U_{t-1}[a,:] (V_{t-1}^T V_t)  (fused path)
 };
 
 // Launchers (stream-ordered; return cudaGetLastError()).
@@ -85,5 +86,36 @@ cudaError_t launch_truth_err(const float* U, const float* V, int64_t m, int64_t 
 cudaError_t launch_check_finite(const float* x, int64_t count, int* flag, cudaStream_t s);
 
 int pick_R(int r);
+
+// Fused single-pass path (k_fused.cu)
+struct FusedArgs {
+  int cur;                  // copy holding U_{t-1}, V_{t-1}
+  int cs;                   // cluster size (CTAs per cluster)
+  int nclusters;
+  int nslabs;
+  int64_t m, n;
+  float lam;
+  const float* Vold;        // n x R
+  float* Vnew;              // n x R
+  const uint8_t* img;       // [slab][U image | W image]
+  const float* scales;      // [2*slab] = s_u, [2*slab+1] = s_w, [2*nslabs] = s_v
+  const float* zmat;        // R x R, Z = I - rho (U^T U + rho I)^{-1}
+  unsigned int* vmax_out;   // max |V'| (float bits)
+  double* part_q;           // [grid][R*R]
+  double* part_xv;          // [grid][R*R]
+  double* part_h;           // [grid]
+  float* part_p;            // [nclusters][m][R]
+  DevState* st;
+  int* err;
+};
+cudaError_t launch_fused(int R, const void* tmap, const FusedArgs& fa, cudaStream_t s);
+cudaError_t fused_prepare(int R);
+int fused_max_clusters(int R, int cs);
+int fused_make_tmap(void* tmap_out, const float* M, int64_t m, int64_t n);
+cudaError_t launch_fused_prep(int R, const float* U, const Smalls* sm, const DevState* st,
+                              int64_t m, int nslabs, float rho, const unsigned int* vmax_in,
+                              unsigned int* vmax_reset, uint8_t* img, float* scales, float* zmat,
+                              cudaStream_t s);
+cudaError_t launch_absmax(const float* x, int64_t count, unsigned int* out, cudaStream_t s);
 
 }  // namespace dcf

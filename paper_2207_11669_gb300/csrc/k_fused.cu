@@ -27,6 +27,7 @@
 // DCF_ETIMEOUT and runs to completion (all cluster barriers are still
 // executed, tensor memory is always released).
 #include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_fp16.h>
 
 #include "dcf.h"
@@ -40,26 +41,6 @@ constexpr int kFH = 256;         // rows per CTA (2 row blocks of 128)
 constexpr int kSubBytes = 128 * 32 * 4;
 constexpr uint32_t kWaitLimit = 1u << 26;
 
-struct FusedArgs {
-  int cur;                  // copy holding U_{t-1}, V_{t-1}
-  int cs;                   // cluster size (CTAs per cluster)
-  int nclusters;
-  int nslabs;
-  int64_t m, n;
-  float lam;
-  const float* Vold;        // n x R
-  float* Vnew;              // n x R
-  const uint8_t* img;       // [slab][U image | W image]
-  const float* scales;      // [2*slab] = s_u, [2*slab+1] = s_w, [2*nslabs] = s_v
-  const float* zmat;        // R x R, Z = I - rho (U^T U + rho I)^{-1}
-  unsigned int* vmax_out;   // max |V'| (float bits)
-  double* part_q;           // [grid][R*R]
-  double* part_xv;          // [grid][R*R]
-  double* part_h;           // [grid]
-  float* part_p;            // [nclusters][m][R]
-  DevState* st;
-  int* err;
-};
 
 template <int R, int NST>
 struct FL {  // shared-memory layout (bytes)
@@ -470,12 +451,19 @@ __global__ void __launch_bounds__(256) k_fused_prep(const float* __restrict__ U,
   // U image: term t, row a, k -> t*(256*R*2) + (a/8)*SB_R + (k/8)*128 + (a%8)*16 + (k%8)*2
 #pragma unroll
   for (int k8 = 0; k8 < R / 8; ++k8) {
-    __half h[8], l[8];
+    uint32_t ph[4], pl[4];
 #pragma unroll
-    for (int i = 0; i < 8; ++i) split_h(u[k8 * 8 + i], s_u, h[i], l[i]);
+    for (int i = 0; i < 4; ++i) {
+      __half h0, l0, h1, l1;
+      split_h(u[k8 * 8 + 2 * i], s_u, h0, l0);
+      split_h(u[k8 * 8 + 2 * i + 1], s_u, h1, l1);
+      __half2 hh = __halves2half2(h0, h1), ll = __halves2half2(l0, l1);
+      ph[i] = *reinterpret_cast<uint32_t*>(&hh);
+      pl[i] = *reinterpret_cast<uint32_t*>(&ll);
+    }
     const int off = (tid >> 3) * SB_R + k8 * 128 + (tid & 7) * 16;
-    *reinterpret_cast<uint4*>(dst + off) = *reinterpret_cast<uint4*>(h);
-    *reinterpret_cast<uint4*>(dst + kFH * R * 2 + off) = *reinterpret_cast<uint4*>(l);
+    *reinterpret_cast<uint4*>(dst + off) = make_uint4(ph[0], ph[1], ph[2], ph[3]);
+    *reinterpret_cast<uint4*>(dst + kFH * R * 2 + off) = make_uint4(pl[0], pl[1], pl[2], pl[3]);
   }
   // W image: entry (n, a), n < R -> W_hi[a, n], n >= R -> W_lo[a, n-R]:
   //   (n/8)*(256*16) + (a/8)*128 + (n%8)*16 + (a%8)*2
@@ -589,12 +577,6 @@ int fused_make_tmap(void* tmap_out, const float* M, int64_t m, int64_t n) {
                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS ? 0 : (int)r;
 }
-
-struct FusedLaunch {
-  const void* tmap;
-  FusedArgs args;
-  int R;
-};
 
 cudaError_t launch_fused_prep(int R, const float* U, const Smalls* sm, const DevState* st,
                               int64_t m, int nslabs, float rho, const unsigned int* vmax_in,

@@ -379,7 +379,8 @@ __global__ void __launch_bounds__(256) k_rows(IterArgs a) {
   float* Unew = a.U[nxt];
   const int64_t row0 = (int64_t)blockIdx.x * kRowsPerCta;
   const int rows = (int)dmin64((int64_t)kRowsPerCta, a.m - row0);
-  for (int i = tid; i < R * R; i += 256) Mat[i] = a.u_mode == 0 ? a.sm->hinv32[i] : a.sm->qrho32[i];
+  if (a.add_uxv)
+    for (int i = tid; i < R * R; i += 256) Mat[i] = (float)a.sm->xv[i];
   for (int i = tid; i < kRowsPerCta * R; i += 256) {
     const int rr = i / R;
     float hi = 0.f, lo = 0.f, uo = 0.f;
@@ -393,6 +394,22 @@ __global__ void __launch_bounds__(256) k_rows(IterArgs a) {
   }
   __syncthreads();
   const int ar = tid >> 3, g = tid & 7;
+  if (a.add_uxv) {
+    // P = U_{t-1} (V_{t-1}^T V_t) + C V'   (the fused pass returns only C V')
+    float add[CG];
+#pragma unroll
+    for (int l = 0; l < CG; ++l) add[l] = 0.f;
+    for (int k = 0; k < R; ++k) {
+      const float u = Uo[ar * R + k];
+#pragma unroll
+      for (int l = 0; l < CG; ++l) add[l] = fmaf(u, Mat[k * R + g * CG + l], add[l]);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int l = 0; l < CG; ++l) Ps[ar * R + g * CG + l] += add[l];
+  }
+  for (int i = tid; i < R * R; i += 256) Mat[i] = a.u_mode == 0 ? a.sm->hinv32[i] : a.sm->qrho32[i];
+  __syncthreads();
   float acc[CG];
 #pragma unroll
   for (int l = 0; l < CG; ++l) acc[l] = 0.f;

@@ -34,7 +34,8 @@ class dcf_params(C.Structure):
     _fields_ = [("m", C.c_int64), ("E", C.c_int), ("n_i", C.POINTER(C.c_int64)),
                 ("r", C.c_int), ("rho", C.c_double), ("lambda_", C.c_double),
                 ("max_iter", C.c_int), ("tol", C.c_double), ("u_mode", C.c_int),
-                ("local_steps", C.c_int), ("eta0", C.c_double), ("seed", C.c_uint64)]
+                ("local_steps", C.c_int), ("eta0", C.c_double), ("seed", C.c_uint64),
+                ("path", C.c_int)]
 
 
 ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p)
@@ -44,6 +45,7 @@ _SIGS = {
     "dcf_set_allocator": (None, [ALLOC_FN, FREE_FN, C.c_void_p]),
     "dcf_create": (C.c_int, [C.POINTER(dcf_params), C.POINTER(C.c_void_p)]),
     "dcf_set_stream": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "dcf_get_path": (C.c_int, [C.c_void_p]),
     "dcf_load_blocks": (C.c_int, [C.c_void_p, C.POINTER(C.c_void_p), C.POINTER(C.c_int64),
                                   C.c_int, C.c_int]),
     "dcf_load_init": (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(C.c_void_p), C.c_int]),
@@ -144,16 +146,23 @@ def use_torch_allocator():
     dcf_set_allocator(alloc, release)
 
 
+PATH_AUTO, PATH_GENERAL, PATH_FUSED = 0, 1, 2
+
+
 def dcf_create(m, n_i, r, rho, lam, max_iter=100, tol=1e-6, u_mode=0, local_steps=1,
-               eta0=0.0, seed=0):
+               eta0=0.0, seed=0, path=PATH_AUTO):
     n_arr = (C.c_int64 * len(n_i))(*[int(x) for x in n_i])
     p = dcf_params(int(m), len(n_i), n_arr, int(r), float(rho), float(lam), int(max_iter),
-                   float(tol), int(u_mode), int(local_steps), float(eta0), int(seed))
+                   float(tol), int(u_mode), int(local_steps), float(eta0), int(seed), int(path))
     h = C.c_void_p()
     st = lib().dcf_create(C.byref(p), C.byref(h))
     if st != DCF_OK:
         raise DcfError(st, "dcf_create rejected the parameters")
     return h
+
+
+def dcf_get_path(h):
+    return lib().dcf_get_path(h)
 
 
 def dcf_set_stream(h, stream_ptr):
@@ -276,10 +285,10 @@ class Solver:
     """
 
     def __init__(self, m, n_i, r, rho, lam, max_iter=100, tol=1e-6, u_mode=0, eta0=0.0,
-                 seed=0, stream=None):
+                 seed=0, stream=None, path=PATH_AUTO):
         self.m, self.n_i, self.r = int(m), [int(x) for x in n_i], int(r)
         self.n = int(sum(self.n_i))
-        self.h = dcf_create(m, n_i, r, rho, lam, max_iter, tol, u_mode, 1, eta0, seed)
+        self.h = dcf_create(m, n_i, r, rho, lam, max_iter, tol, u_mode, 1, eta0, seed, path)
         if stream is not None:
             dcf_set_stream(self.h, stream)
         self._keep = None
@@ -324,6 +333,10 @@ class Solver:
         if _is_torch(x):
             return x.contiguous()
         return np.ascontiguousarray(x, dtype=np.float32)
+
+    @property
+    def path(self):
+        return dcf_get_path(self.h)
 
     def step(self, n=1):
         dcf_step(self.h, n)

@@ -35,6 +35,13 @@ def built():
     torch.cuda.init()
 
 
+def fused_ok(m, r):
+    return r <= 32 and m % 4 == 0 and (m + 255) // 256 <= 16
+
+
+PATHS = [dcf.PATH_GENERAL, dcf.PATH_FUSED]
+
+
 def gpu_solver(case, **kw):
     s = dcf.Solver(case["M"].shape[0], case["n_i"], case["r"], case["rho"], case["lam"], **kw)
     s.load(case["M"])
@@ -47,10 +54,14 @@ def oracle_step(case, iters=1, **kw):
                      iters, **kw)
 
 
+@pytest.mark.parametrize("path", PATHS)
 @pytest.mark.parametrize("m,n_i,r", SHAPES)
-def test_one_step_parity(m, n_i, r):
+def test_one_step_parity(m, n_i, r, path):
+    if path == dcf.PATH_FUSED and not fused_ok(m, r):
+        pytest.skip("shape outside the fused path")
     case = make_case(m, n_i, r, seed=m + r)
-    s = gpu_solver(case)
+    s = gpu_solver(case, path=path)
+    assert s.path == path
     s.step(1)
     U, V = s.factors()
     U1, V1, S1, U0, V0 = oracle_step(case, 1)
@@ -67,9 +78,10 @@ def test_one_step_parity(m, n_i, r):
     s.close()
 
 
-def test_fedavg_step_parity():
+@pytest.mark.parametrize("path", PATHS)
+def test_fedavg_step_parity(path):
     case = make_case(300, [100, 77, 140], 16, seed=3)
-    s = gpu_solver(case, u_mode=1, eta0=0.01)
+    s = gpu_solver(case, u_mode=1, eta0=0.01, path=path)
     s.step(3)
     U, V = s.factors()
     Uo, Vo, *_ = oracle_step(case, 3, u_mode=1, eta0=0.01)
@@ -78,9 +90,10 @@ def test_fedavg_step_parity():
     s.close()
 
 
-def test_several_steps_L_parity():
+@pytest.mark.parametrize("path", PATHS)
+def test_several_steps_L_parity(path):
     case = make_case(200, [50] * 4, 5, seed=7)
-    s = gpu_solver(case)
+    s = gpu_solver(case, path=path)
     s.step(10)
     U, V = s.factors()
     Uo, Vo, *_ = oracle_step(case, 10)
@@ -88,10 +101,11 @@ def test_several_steps_L_parity():
     s.close()
 
 
-def test_converged_L_parity_and_support():
+@pytest.mark.parametrize("path", PATHS)
+def test_converged_L_parity_and_support(path):
     """The 200 x 200, E = 4 workload run to convergence on both sides."""
     case = make_case(200, [50] * 4, 5, seed=20220723)
-    s = gpu_solver(case, max_iter=400, tol=1e-7)
+    s = gpu_solver(case, max_iter=400, tol=1e-7, path=path)
     it, d, ok = s.solve()
     assert ok and d <= 1e-7
     U, V = s.factors()
@@ -109,6 +123,19 @@ def test_converged_L_parity_and_support():
     s.close()
 
 
+def test_fused_path_is_chosen_automatically():
+    case = make_case(300, [100, 77, 140], 16, seed=21)
+    s = gpu_solver(case)
+    assert s.path == dcf.PATH_FUSED
+    s.close()
+    case = make_case(257, [300, 211], 40, seed=21)
+    s = gpu_solver(case)
+    assert s.path == dcf.PATH_GENERAL
+    s.close()
+    with pytest.raises(dcf.DcfError):
+        dcf.Solver(257, [300, 211], 40, 1e-2, 0.1, path=dcf.PATH_FUSED)
+
+
 def test_init_sweep_parity():
     case = make_case(257, [300, 211], 40, seed=11)
     s = dcf.Solver(257, case["n_i"], 40, case["rho"], case["lam"])
@@ -120,11 +147,12 @@ def test_init_sweep_parity():
     s.close()
 
 
-def test_partition_invariance_on_gpu():
+@pytest.mark.parametrize("path", PATHS)
+def test_partition_invariance_on_gpu(path):
     case = make_case(300, [100, 77, 140], 16, seed=5)
-    a = gpu_solver(case)
+    a = gpu_solver(case, path=path)
     case1 = dict(case, n_i=np.array([317]))
-    b = gpu_solver(case1)
+    b = gpu_solver(case1, path=path)
     a.step(4)
     b.step(4)
     Ua, Va = a.factors()
@@ -134,9 +162,10 @@ def test_partition_invariance_on_gpu():
     b.close()
 
 
-def test_stats_and_rel_err():
+@pytest.mark.parametrize("path", PATHS)
+def test_stats_and_rel_err(path):
     case = make_case(200, [50] * 4, 5, seed=9)
-    s = gpu_solver(case)
+    s = gpu_solver(case, path=path)
     s.set_truth(case["inst"].A, case["inst"].B)
     s.step(2)
     obj, dL, it = s.stats()
@@ -149,9 +178,10 @@ def test_stats_and_rel_err():
     s.close()
 
 
-def test_get_LS_blocks_and_privacy():
-    case = make_case(129, [33, 64, 31], 32, seed=13)
-    s = gpu_solver(case)
+@pytest.mark.parametrize("path", PATHS)
+def test_get_LS_blocks_and_privacy(path):
+    case = make_case(132, [33, 64, 31], 32, seed=13)
+    s = gpu_solver(case, path=path)
     s.step(2)
     U2, V2, S2, U1, V1 = oracle_step(case, 2)
     off = O.block_offsets(case["n_i"])
@@ -198,12 +228,13 @@ def test_default_init_is_seeded_gaussian():
     b.close()
 
 
-def test_borrowed_device_matrix_matches_host_copy():
+@pytest.mark.parametrize("path", PATHS)
+def test_borrowed_device_matrix_matches_host_copy(path):
     import torch
     case = make_case(300, [100, 77, 140], 16, seed=17)
     Mt = torch.from_numpy(np.ascontiguousarray(case["M"].T)).cuda()   # (n, m) = M column-major
-    s1 = gpu_solver(case)
-    s2 = dcf.Solver(300, case["n_i"], 16, case["rho"], case["lam"])
+    s1 = gpu_solver(case, path=path)
+    s2 = dcf.Solver(300, case["n_i"], 16, case["rho"], case["lam"], path=path)
     s2.load(Mt)
     s2.load_init(case["U0"], case["V0"])
     s1.step(2)
