@@ -172,6 +172,40 @@ dcf_status dcf_profile_step(dcf_handle h, int n_steps, double* phase_ms);
  * fused kernel uses; no counterpart in the paper. */
 int dcf_tc_selftest(const int* cfg, float* out_host);
 
+/* ---- Allocation-free iteration ----------------------------------------------
+ * One exact-consensus DCF-PCA iteration on buffers the caller owns, for
+ * callers that cannot let a library allocate device memory: work being
+ * recorded into a CUDA graph by stream capture, latency-critical loops where
+ * cudaMalloc/cudaFree would synchronise the device, and frameworks that hand
+ * out all device memory from their own pools.  The paper has no counterpart;
+ * it is a deployment variant of the general two-pass path of dcf_step.
+ *
+ * Inputs (device memory of the current device): M, m x n column-major
+ * (one block; exact consensus does not depend on the client split); U_in,
+ * m x r row-major; V_in, n x r row-major.  Outputs: U_out (m x r) and V_out
+ * (n x r), row-major, device memory, not aliasing the inputs.  The work is
+ * enqueued on `stream` (a cudaStream_t, NULL = legacy default stream) and is
+ * asynchronous; results are valid once the stream has completed it.
+ *
+ * Scratch: a fixed device array of DCF_NOALLOC_SCRATCH_BYTES inside the
+ * library, held by every GPU that loads the library until the process
+ * exits.  Returns DCF_EINVAL, touching nothing, when the problem needs more
+ * scratch than that (about 4(3m + 2n)R + 4mR*splits bytes plus r x r
+ * workspace, R = r rounded up to 8, 16, 32 or 64), and for invalid sizes,
+ * rho <= 0, lambda <= 0 or NULL pointers.  Never calls cudaMalloc, cudaFree
+ * or any allocating routine.
+ *
+ * The first call on a device resolves the scratch array's address on that
+ * device and raises kernel attributes; make that first call before any stream
+ * capture.  Every call shares the array and leaves its contents behind (each
+ * call clears what must start at zero), so calls whose work overlaps on the
+ * GPU -- on different streams or from different host threads -- race and
+ * must be serialised by the caller. */
+#define DCF_NOALLOC_SCRATCH_BYTES ((size_t)16 << 20)
+dcf_status dcf_iterate_noalloc(const float* M, int64_t m, int64_t n, int r, double rho,
+                               double lambda, const float* U_in, const float* V_in,
+                               float* U_out, float* V_out, void* stream);
+
 /* Library version string. */
 const char* dcf_version(void);
 

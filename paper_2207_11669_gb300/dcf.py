@@ -64,6 +64,9 @@ _SIGS = {
     "dcf_profile_phases": (C.c_int, [C.c_void_p, C.c_char_p, C.c_int]),
     "dcf_profile_step": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_double)]),
     "dcf_tc_selftest": (C.c_int, [C.POINTER(C.c_int), C.POINTER(C.c_float)]),
+    "dcf_iterate_noalloc": (C.c_int, [C.c_void_p, C.c_int64, C.c_int64, C.c_int, C.c_double,
+                                      C.c_double, C.c_void_p, C.c_void_p, C.c_void_p,
+                                      C.c_void_p, C.c_void_p]),
 }
 
 
@@ -267,6 +270,18 @@ def dcf_tc_selftest(cfg):
     if st != DCF_OK:
         raise DcfError(st, "dcf_tc_selftest")
     return out
+
+
+def dcf_iterate_noalloc(M, m, n, r, rho, lam, U_in, V_in, U_out, V_out, stream=0):
+    """One allocation-free iteration on device tensors (see include/dcf.h);
+    returns the status code (0 on success) without raising."""
+    def ptr(t):
+        if not (t.is_cuda and t.is_contiguous()):
+            raise ValueError("dcf_iterate_noalloc takes contiguous CUDA tensors")
+        return C.c_void_p(t.data_ptr())
+    return lib().dcf_iterate_noalloc(ptr(M), int(m), int(n), int(r), float(rho), float(lam),
+                                     ptr(U_in), ptr(V_in), ptr(U_out), ptr(V_out),
+                                     C.c_void_p(stream))
 
 
 def dcf_version():
