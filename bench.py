@@ -183,7 +183,9 @@ def run_ours(args):
         tdist.init_process_group("nccl")
     wl = workload_by_name(args.workload)
     # replicas: every rank solves its own instance of the same workload
-    inst = wl.instance(seed=wl.seed + rank)
+    inst = wl.instance(seed=wl.seed + rank, n=args.n_cols or None)
+    if args.n_cols:
+        wl.n, wl.name = args.n_cols, f"{wl.name}_cols{args.n_cols}"
     m, n, r = wl.m, wl.n, wl.r
     U0 = synth.gaussian_u0(m, r, wl.seed + rank)
     Mt = torch.from_numpy(np.ascontiguousarray(inst.M.T)).cuda()     # (n, m): M column-major
@@ -236,6 +238,38 @@ def run_ours(args):
                 "phase_ms": {k: round(v, 4) for k, v in phase_ms.items()}}
 
     # end to end through the public API with host buffers
+    e2e = None
+    if not args.no_e2e:
+        e2e = run_e2e(dcf, torch, inst, wl, U0, stream, args, world)
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        rate, info = oracle_sample_rate(wl, inst, U0, budget_s=12.0)
+        cpu = dict(info, value=rate, unit="iters/s")
+    s.close()
+    gbs = alg_bytes_per_iter(m, n, r) / (ms_step * 1e-3) / 1e9
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": "iters/s", "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": "f32", "data": "synthetic",
+                "config": {"workload": wl.name, "m": m, "n": n, "E": int(wl.E), "r": r,
+                           "kernel_path": {1: "general two-pass", 2: "fused single-pass tcgen05"}.get(path_id),
+                           "rank_truth": wl.k, "density": wl.density, "rho": wl.rho,
+                           "lambda": wl.lam, "parallelism": "replicas" if world > 1 else "1gpu",
+                           "l2": "inputs larger than L2 (M is %.0f MiB)" % (4.0 * m * n / 2**20)},
+                "hbm_gbs_alg": gbs,
+                "gpu_launches": launches_per_iter * args.steps,
+                "clocks": clk, "roofline": roofline, "e2e": e2e, "cpu_baseline": cpu}
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        tdist.destroy_process_group()
+    return 0
+
+
+def run_e2e(dcf, torch, inst, wl, U0, stream, args, world):
+    """The same metric through the public API with host buffers: every step
+    copies M from pinned host memory, iterates and reads U back."""
+    m, n, r = wl.m, wl.n, wl.r
     Mh = torch.empty((n, m), dtype=torch.float32, pin_memory=True)
     Mh.copy_(torch.from_numpy(np.ascontiguousarray(inst.M.T)))
     Uh = np.empty((m, r), np.float32)
@@ -252,33 +286,8 @@ def run_ours(args):
     torch.cuda.synchronize()
     e2e_s = (time.perf_counter() - t0) / e2e_steps
     s2.close()
-
-    cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu:
-        rate, info = oracle_sample_rate(wl, inst, U0, budget_s=12.0)
-        cpu = dict(info, value=rate, unit="iters/s")
-    s.close()
-    gbs = alg_bytes_per_iter(m, n, r) / (ms_step * 1e-3) / 1e9
-    if rank == 0:
-        line = {"metric": METRIC, "value": value, "unit": "iters/s", "n_gpus": world,
-                "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
-                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-                "dtype": "f32", "data": "synthetic",
-                "config": {"workload": wl.name, "m": m, "n": n, "E": int(wl.E), "r": r,
-                           "kernel_path": {1: "general two-pass", 2: "fused single-pass tcgen05"}.get(path_id),
-                           "rank_truth": wl.k, "density": wl.density, "rho": wl.rho,
-                           "lambda": wl.lam, "parallelism": "replicas" if world > 1 else "1gpu",
-                           "l2": "inputs larger than L2 (M is 1 GiB)"},
-                "hbm_gbs_alg": gbs,
-                "gpu_launches": launches_per_iter * args.steps,
-                "clocks": clk, "roofline": roofline,
-                "e2e": {"value": world / e2e_s, "unit": "iters/s",
-                        "h2d_bytes_per_step": 4 * m * n, "d2h_bytes_per_step": 4 * m * r},
-                "cpu_baseline": cpu}
-        print(json.dumps(line), flush=True)
-    if world > 1:
-        tdist.destroy_process_group()
-    return 0
+    return {"value": world / e2e_s, "unit": "iters/s", "h2d_bytes_per_step": 4 * m * n,
+            "d2h_bytes_per_step": 4 * m * r}
 
 
 def main():
@@ -288,7 +297,10 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="medium", choices=["medium", "small", "large"])
-    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the oracle baseline leg")
+    ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end leg")
+    ap.add_argument("--n-cols", type=int, default=0,
+                    help="shrink n (same value laws), e.g. for profiler captures")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

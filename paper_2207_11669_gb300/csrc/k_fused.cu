@@ -42,24 +42,34 @@ constexpr int kSubBytes = 128 * 32 * 4;
 constexpr uint32_t kWaitLimit = 1u << 26;
 
 
+constexpr int kFThreads = 512;   // 16 warps, see the role map below
+constexpr int kChunk = 4;        // columns per reduce-scatter chunk (16 chunks per strip)
+
 template <int R, int NST>
 struct FL {  // shared-memory layout (bytes)
-  static constexpr int RING = 0;
-  static constexpr int UIMG = RING + NST * kSubBytes;            // 2 terms x 256 x R fp16
-  static constexpr int WIMG = UIMG + 2 * kFH * R * 2;            // 2R x 256 fp16
-  static constexpr int CBUF = WIMG + 2 * R * kFH * 2;            // 256 x 64 fp16
-  static constexpr int VIMG = CBUF + kFH * kFW * 2;              // 2 terms x 64 x R fp16
-  static constexpr int PIMG = VIMG + 2 * kFW * R * 2;            // 2R x 64 fp16
+  static constexpr int RING = 0;                                 // NST x (128 x 32 fp32)
+  static constexpr int WIMG = RING + NST * kSubBytes;            // 2R x 256 fp16
+  static constexpr int CBYTES = kFH * kFW * 2;                   // one C tile (256 x 64 fp16)
+  static constexpr int CBUF = WIMG + 2 * R * kFH * 2;            // 2 C tiles
+  static constexpr int VBYTES = 2 * kFW * R * 2;                 // one V image (2 terms)
+  static constexpr int VIMG = CBUF + 2 * CBYTES;                 // 2 V images
+  static constexpr int PIMG = VIMG + 2 * VBYTES;                 // 2R x 64 fp16
   static constexpr int YPART = PIMG + 2 * R * kFW * 2;           // 64 x R fp32
   static constexpr int ZM = YPART + kFW * R * 4;                 // R x R fp32
-  static constexpr int VSL = ZM + R * R * 4;                     // 8 x R fp32 (V_s rows)
-  static constexpr int VNL = VSL + 8 * R * 4;                    // 8 x R fp32 (V' rows)
-  static constexpr int STG = VNL + 8 * R * 4;                    // 2R x 8 fp16 image chunk
-  static constexpr int BAR = STG + 2 * R * 8 * 2;                // mbarriers
-  static constexpr int NBAR = NST + 4;                           // full[NST], g1, g2, g3, img
+  static constexpr int VSLX = ZM + R * R * 4;                    // <= 64 x R fp32 (V_s rows)
+  static constexpr int VNL = VSLX + kFW * R * 4;                 // 4 x R fp32 (V' rows)
+  static constexpr int STG = VNL + kChunk * R * 4;               // 2R x 4 fp16 image chunk
+  static constexpr int BAR = STG + 2 * R * kChunk * 2;           // mbarriers
+  static constexpr int NBAR = 2 * NST + 20;
   static constexpr int TSLOT = BAR + NBAR * 8;
-  static constexpr int RED = TSLOT + 16;                         // 8 doubles
-  static constexpr int TOTAL = RED + 8 * 8;
+  static constexpr int RED = TSLOT + 16;                         // 16 doubles
+  static constexpr int TOTAL = RED + 16 * 8;
+  // tensor-memory columns (512 allocated)
+  static constexpr int T_D2 = 256;                               // M=64 result, 2R columns
+  static constexpr int T_D3 = T_D2 + 2 * R;                      // 2 blocks x 2R (P_C)
+  static constexpr int T_U = T_D3 + 4 * R;                       // U hi/lo, 2 blocks x 2 x R/2
+  static_assert(T_U + 2 * R <= 512, "tensor memory");
+  static_assert(TOTAL <= 232448, "shared memory");
 };
 
 __device__ __forceinline__ float pow2_scale_dev(float mx, float target) {
@@ -82,152 +92,280 @@ __device__ __forceinline__ void tsum(float& hi, float& lo, float x) {
   hi = t;
 }
 
+// Warp-specialised pipeline over the strips of the cluster (16 warps):
+//   warp 0       TMA producer: M sub-tiles into a ring of NST slots
+//   warp 1       MMA issuer (GEMM1 of strip i, GEMM2 of i-1, GEMM3 of i-2) and
+//                tensor-memory owner
+//   warps 2-3    fp16 images of V_s (B operand of GEMM1), two strips ahead
+//   warps 4-11   S-step epilogue: R, C/lambda into the C tile, Huber
+//   warps 12-15  exchange: column sums out of tensor memory, reduce-scatter
+//                over the cluster (DSMEM), V', all-gather of the V' image
+// Local mbarriers link the roles inside a CTA; four mbarriers per CTA,
+// arrived on remotely, link the CTAs of the cluster:
+//   yfull  (count CS)  every CTA has published its column sums of the strip
+//   yfree  (count CS)  every reducer has read this CTA's column sums
+//   pfull  (count CS)  every reducer has written its chunk of the V' image here
+//   pfree  (count CS)  every CTA's GEMM3 of the previous strip has completed
+// Each of them completes once per strip; an arrival for strip s+1 can only
+// happen after the phase of strip s has completed (see the waits below).
 template <int R, int NST>
-__global__ void __launch_bounds__(256, 1)
+__global__ void __launch_bounds__(kFThreads, 1)
     k_fused(const __grid_constant__ CUtensorMap tmap, const FusedArgs a) {
   using L = FL<R, NST>;
   if (a.st->stop) return;  // uniform over the grid
   extern __shared__ __align__(1024) uint8_t smem[];
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const uint32_t crank = tc::cluster_rank();
-  const int cid = blockIdx.x / a.cs;
-  const int slab = (int)(blockIdx.x % a.cs);   // == crank
+  const int cs = a.cs;
+  const int cid = blockIdx.x / cs;
+  const int slab = (int)(blockIdx.x % cs);   // == crank
   const int64_t row0 = (int64_t)slab * kFH;
   const uint32_t sbase = tc::smem_u32(smem);
-  const uint32_t bar = sbase + L::BAR;
-  auto full_bar = [&](int i) { return bar + 8u * i; };
-  const uint32_t g1_bar = bar + 8u * NST, g2_bar = g1_bar + 8, g3_bar = g2_bar + 8,
-                 img_bar = g3_bar + 8;
+  const uint32_t bar0 = sbase + L::BAR;
+  auto B = [&](int i) { return bar0 + 8u * (uint32_t)i; };
+  // barrier indices
+  const int b_full = 0, b_empty = NST, b_vfull = 2 * NST, b_vempty = b_vfull + 2,
+            b_d1full = b_vempty + 2, b_d1empty = b_d1full + 2, b_cfull = b_d1empty + 2,
+            b_cempty = b_cfull + 2, b_d2full = b_cempty + 2, b_d2empty = b_d2full + 1,
+            b_g3done = b_d2empty + 1, b_yfull = b_g3done + 1, b_yfree = b_yfull + 1,
+            b_pfull = b_yfree + 1, b_pfree = b_pfull + 1, b_img = b_pfree + 1,
+            b_last = b_img + 1;
   float* ypart = reinterpret_cast<float*>(smem + L::YPART);
   float* zm = reinterpret_cast<float*>(smem + L::ZM);
-  float* vsl = reinterpret_cast<float*>(smem + L::VSL);
+  float* vslx = reinterpret_cast<float*>(smem + L::VSLX);
   float* vnl = reinterpret_cast<float*>(smem + L::VNL);
+  double* red = reinterpret_cast<double*>(smem + L::RED);
   int err = 0;
 
   // ---- set-up -------------------------------------------------------------
-  if (warp == 0) {
+  if (warp == 1) {
     tc::tmem_alloc(sbase + L::TSLOT, 512);
     tc::tmem_relinquish();
   }
   if (tid == 0) {
-    for (int i = 0; i < L::NBAR; ++i) tc::mbar_init(bar + 8u * i, 1);
+    for (int i = 0; i < NST; ++i) {
+      tc::mbar_init(B(b_full + i), 1);
+      tc::mbar_init(B(b_empty + i), 4);     // the 4 epilogue warps of a row block
+    }
+    for (int p = 0; p < 2; ++p) {
+      tc::mbar_init(B(b_vfull + p), 2);     // the 2 V-image warps
+      tc::mbar_init(B(b_vempty + p), 1);    // GEMM1 commit
+      tc::mbar_init(B(b_d1full + p), 1);    // GEMM1 commit
+      tc::mbar_init(B(b_d1empty + p), 8);   // the 8 epilogue warps
+      tc::mbar_init(B(b_cfull + p), 8);     // the 8 epilogue warps
+      tc::mbar_init(B(b_cempty + p), 1);    // GEMM3 commit
+    }
+    tc::mbar_init(B(b_d2full), 1);
+    tc::mbar_init(B(b_d2empty), 4);         // the 4 exchange warps
+    tc::mbar_init(B(b_g3done), 1);
+    tc::mbar_init(B(b_yfull), cs);
+    tc::mbar_init(B(b_yfree), cs);
+    tc::mbar_init(B(b_pfull), cs);
+    tc::mbar_init(B(b_pfree), cs);
+    tc::mbar_init(B(b_img), 1);
+    tc::mbar_init(B(b_last), 1);            // every MMA of the kernel has completed
     tc::fence_mbar_init();
     tc::prefetch_tmap(&tmap);
   }
-  for (int i = tid; i < R * R; i += 256) zm[i] = a.zmat[i];
+  for (int i = tid; i < R * R; i += kFThreads) zm[i] = a.zmat[i];
   tc::fence_before_sync();
   __syncthreads();
   tc::fence_after_sync();
   const uint32_t tbase = *reinterpret_cast<volatile uint32_t*>(smem + L::TSLOT);
-  const uint32_t d1 = tbase, d2 = tbase + 128, d3 = tbase + 256;
+  auto d1 = [&](int s) { return tbase + 128u * (uint32_t)s; };
+  const uint32_t d2 = tbase + L::T_D2, d3 = tbase + L::T_D3, tu = tbase + L::T_U;
   const float s_u = a.scales[2 * slab], s_w = a.scales[2 * slab + 1];
   const float s_v = a.scales[2 * a.nslabs];
-  const float inv_uv = 1.f / (s_u * s_v);
-  const float inv_lam = 1.f / a.lam;
-  const float y_scale = a.lam / s_w;
   const int64_t nstrips = (a.n + kFW - 1) / kFW;
-  const int my_strips = cid < nstrips ? (int)((nstrips - 1 - cid) / a.nclusters + 1) : 0;
-  const int total_sub = my_strips * 4;
+  const int S = cid < nstrips ? (int)((nstrips - 1 - cid) / a.nclusters + 1) : 0;
+  const int nch = (int)((kFW / kChunk - 1 - (int)crank) / cs + 1);   // chunks this CTA reduces
+  const uint8_t* slab_img = a.img + (size_t)slab * (4 * kFH * R * 2);
+  auto strip_col0 = [&](int ls) { return (cid + (int64_t)ls * a.nclusters) * kFW; };
 
-  auto issue_tma = [&](int g) {
-    const int ls = g >> 2, sub = g & 3, b = sub >> 1, q = sub & 1;
-    const int64_t s = cid + (int64_t)ls * a.nclusters;
-    const int slot = g % NST;
-    tc::mbar_arrive_expect_tx(full_bar(slot), kSubBytes);
-    tc::tma_load_2d(sbase + L::RING + slot * kSubBytes, &tmap, (int)(row0 + 128 * b),
-                    (int)(s * kFW + 32 * q), full_bar(slot));
-  };
   if (tid == 0) {
-    // U and W images of this row slab (prepared by k_fused_prep)
-    const uint8_t* src = a.img + (size_t)slab * (4 * kFH * R * 2);
-    tc::mbar_arrive_expect_tx(img_bar, 4 * kFH * R * 2);
-    tc::bulk_load(sbase + L::UIMG, src, 2 * kFH * R * 2, img_bar);
-    tc::bulk_load(sbase + L::WIMG, src + 2 * kFH * R * 2, 2 * kFH * R * 2, img_bar);
-    for (int g = 0; g < NST && g < total_sub; ++g) issue_tma(g);
+    tc::mbar_arrive_expect_tx(B(b_img), 2 * R * kFH * 2);
+    tc::bulk_load(sbase + L::WIMG, slab_img + 2 * kFH * R * 2, 2 * R * kFH * 2, B(b_img));
   }
-  tc::cluster_sync();  // peers' barriers initialised before any remote access
-  if (!tc::mbar_wait(img_bar, 0, kWaitLimit)) err = 1;
-
-  constexpr int NE = (R * R + 255) / 256;   // Q/X_v entries per thread
-  float q_hi[NE], q_lo[NE], x_hi[NE], x_lo[NE];
+  // U rows (fp16 hi/lo pairs) into tensor memory, by the epilogue warps (thread = row)
+  if (warp >= 4 && warp < 12) {
+    const int quarter = warp & 3, rb = (warp - 4) >> 2;
+    const int arow = rb * 128 + quarter * 32 + lane;
+    const uint4* src = reinterpret_cast<const uint4*>(slab_img + (size_t)arow * R * 4);
+    uint32_t w[R];
 #pragma unroll
-  for (int i = 0; i < NE; ++i) { q_hi[i] = q_lo[i] = x_hi[i] = x_lo[i] = 0.f; }
-  float hub_hi = 0.f, hub_lo = 0.f, vmax = 0.f;
-  const uint32_t idesc1 = tc::idesc_f16(128, kFW, 0, 0);
-  const uint32_t idesc2 = tc::idesc_f16(64, 2 * R, 1, 0);
-  const uint32_t idesc3 = tc::idesc_f16(128, 2 * R, 0, 0);
-  constexpr uint32_t SB_R = (R / 8) * 128;    // M/N-direction core stride of K=R images
-
-  for (int ls = 0; ls < my_strips; ++ls) {
-    const int64_t col0 = (cid + (int64_t)ls * a.nclusters) * kFW;
-    const uint32_t par = ls & 1;
-    // (1) fp16 hi/lo image of V_s (B operand of GEMM1; GEMM1 of the previous
-    //     strip completed before its epilogue, so the buffer is free)
-    for (int idx = tid; idx < kFW * R; idx += 256) {
-      const int j = idx / R, k = idx % R;
-      const float v = col0 + j < a.n ? a.Vold[(col0 + j) * R + k] : 0.f;
-      __half hi, lo;
-      split_h(v, s_v, hi, lo);
-      const int off = (j >> 3) * SB_R + (k >> 3) * 128 + (j & 7) * 16 + (k & 7) * 2;
-      *reinterpret_cast<__half*>(smem + L::VIMG + off) = hi;
-      *reinterpret_cast<__half*>(smem + L::VIMG + kFW * R * 2 + off) = lo;
+    for (int i = 0; i < R / 4; ++i) {
+      const uint4 v = src[i];
+      w[4 * i] = v.x; w[4 * i + 1] = v.y; w[4 * i + 2] = v.z; w[4 * i + 3] = v.w;
     }
-    tc::fence_proxy_async_smem();
-    tc::fence_before_sync();
-    __syncthreads();
-    tc::fence_after_sync();
-    // (2) GEMM1: D1_b = U_b V_s^T with terms (hi,hi), (hi,lo), (lo,hi)
-    if (tid == 0) {
+    const uint32_t ta = tu + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(rb * R);
+    if (R == 32) {
+      tc::tmem_st16(ta, w);
+      tc::tmem_st16(ta + 16, w + 16);
+    } else {
+      tc::tmem_st8(ta, w);
+      tc::tmem_st8(ta + 8, w + 8);
+    }
+    tc::tmem_st_wait();
+  }
+  tc::fence_before_sync();
+  tc::cluster_sync();  // peers' barriers initialised; U in tensor memory
+  tc::fence_after_sync();
+
+  constexpr uint32_t SB_R = (R / 8) * 128;    // N-direction core stride of the K=R V image
+  if (warp == 0) {
+    // ================= TMA producer ==========================================
+    if (lane == 0) {
+      const int total = S * 4;
+      for (int g = 0; g < total; ++g) {
+        const int slot = g % NST;
+        if (g >= NST && !tc::mbar_wait(B(b_empty + slot), (uint32_t)((g / NST - 1) & 1), kWaitLimit))
+          err = 1;
+        const int ls = g >> 2, sub = g & 3, b = sub >> 1, q = sub & 1;
+        tc::mbar_arrive_expect_tx(B(b_full + slot), kSubBytes);
+        tc::tma_load_2d(sbase + L::RING + slot * kSubBytes, &tmap, (int)(row0 + 128 * b),
+                        (int)(strip_col0(ls) + 32 * q), B(b_full + slot));
+      }
+    }
+  } else if (warp == 1) {
+    // ================= MMA issuer ============================================
+    if (lane == 0) {
+      if (!tc::mbar_wait(B(b_img), 0, kWaitLimit)) err = 1;
+      const uint32_t idesc1 = tc::idesc_f16(128, kFW, 0, 0);
+      const uint32_t idesc2 = tc::idesc_f16(64, 2 * R, 1, 0);
+      const uint32_t idesc3 = tc::idesc_f16(128, 2 * R, 0, 0);
+      for (int i = 0; i < S + 2; ++i) {
+        if (i < S) {   // GEMM1(i): D1 = U_b V_s^T, terms (hi,hi), (hi,lo), (lo,hi)
+          const int p = i & 1;
+          if (!tc::mbar_wait(B(b_vfull + p), (uint32_t)((i >> 1) & 1), kWaitLimit)) err = 1;
+          if (i >= 2 && !tc::mbar_wait(B(b_d1empty + p), (uint32_t)(((i >> 1) - 1) & 1), kWaitLimit))
+            err = 1;
+          tc::fence_after_sync();
+          const uint32_t vimg = sbase + L::VIMG + p * L::VBYTES;
 #pragma unroll
-      for (int b = 0; b < 2; ++b) {
-        int first = 1;
+          for (int b = 0; b < 2; ++b) {
+            int first = 1;
 #pragma unroll
-        for (int t = 0; t < 3; ++t) {
-          const int tu = t == 2 ? 1 : 0, tv = t == 1 ? 1 : 0;
+            for (int t = 0; t < 3; ++t) {
+              const int tuu = t == 2 ? 1 : 0, tvv = t == 1 ? 1 : 0;
 #pragma unroll
-          for (int kk = 0; kk < R / 16; ++kk) {
-            const uint64_t ad = tc::smem_desc(
-                sbase + L::UIMG + tu * (kFH * R * 2) + b * 16 * SB_R + kk * 256, 128, SB_R);
-            const uint64_t bd =
-                tc::smem_desc(sbase + L::VIMG + tv * (kFW * R * 2) + kk * 256, 128, SB_R);
-            tc::mma_ss(d1 + b * kFW, ad, bd, idesc1, first ? 0u : 1u);
-            first = 0;
+              for (int kk = 0; kk < R / 16; ++kk) {
+                const uint64_t bd = tc::smem_desc(vimg + tvv * (kFW * R * 2) + kk * 256, 128, SB_R);
+                tc::mma_ts(d1(p) + b * kFW, tu + (uint32_t)((2 * b + tuu) * (R / 2) + kk * 8), bd,
+                           idesc1, first ? 0u : 1u);
+                first = 0;
+              }
+            }
           }
+          tc::mma_commit(B(b_d1full + p));
+          tc::mma_commit(B(b_vempty + p));
+        }
+        if (i >= 1 && i <= S) {   // GEMM2(i-1): Y = C^T [W_hi | W_lo]
+          const int s2 = i - 1, p = s2 & 1;
+          if (!tc::mbar_wait(B(b_cfull + p), (uint32_t)((s2 >> 1) & 1), kWaitLimit)) err = 1;
+          if (s2 >= 1 && !tc::mbar_wait(B(b_d2empty), (uint32_t)((s2 - 1) & 1), kWaitLimit)) err = 1;
+          tc::fence_after_sync();
+          const uint32_t cbuf = sbase + L::CBUF + p * L::CBYTES;
+#pragma unroll
+          for (int kk = 0; kk < kFH / 16; ++kk) {
+            const uint64_t ad = tc::smem_desc(cbuf + kk * 256, 128, kFH * 16);
+            const uint64_t bd = tc::smem_desc(sbase + L::WIMG + kk * 256, 128, kFH * 16);
+            tc::mma_ss(d2, ad, bd, idesc2, kk > 0 ? 1u : 0u);
+          }
+          tc::mma_commit(B(b_d2full));
+        }
+        if (i >= 2) {   // GEMM3(i-2): P_C += C [V'_hi | V'_lo]^T
+          const int s3 = i - 2, p = s3 & 1;
+          if (!tc::mbar_wait_cluster(B(b_pfull), (uint32_t)(s3 & 1), kWaitLimit)) err = 1;
+          tc::fence_proxy_async_smem();
+          tc::fence_after_sync();
+          const uint32_t cbuf = sbase + L::CBUF + p * L::CBYTES;
+#pragma unroll
+          for (int b = 0; b < 2; ++b) {
+#pragma unroll
+            for (int kk = 0; kk < kFW / 16; ++kk) {
+              const uint64_t ad = tc::smem_desc(cbuf + b * 2048 + kk * 2 * (kFH * 16), kFH * 16, 128);
+              const uint64_t bd = tc::smem_desc(sbase + L::PIMG + kk * 256, 128, (kFW / 8) * 128);
+              tc::mma_ss(d3 + b * 2 * R, ad, bd, idesc3, (s3 > 0 || kk > 0) ? 1u : 0u);
+            }
+          }
+          tc::mma_commit(B(b_cempty + p));
+          tc::mma_commit(B(b_g3done));
         }
       }
-      tc::mma_commit(g1_bar);
+      // A parity wait only tells the current phase from the previous one, so the
+      // final read-out waits on a barrier of its own rather than on g3done.
+      tc::mma_commit(B(b_last));
     }
-    __syncwarp();
-    if (!tc::mbar_wait(g1_bar, par, kWaitLimit)) err = 1;
-    if (ls > 0 && !tc::mbar_wait(g3_bar, par ^ 1, kWaitLimit)) err = 1;  // C buffer free
-    tc::fence_after_sync();
-    // (3) epilogue: R, C/lambda (fp16), Huber; warp -> (row block, lane quarter)
-    {
-      const int b = warp >> 2, quarter = warp & 3;
-      const int al = quarter * 32 + lane;      // row inside the block
-      const int arow = b * 128 + al;           // row inside the slab
+  } else if (warp < 4) {
+    // ================= V images (64 threads), two strips ahead ================
+    const int vt = tid - 64;
+    constexpr int VPT = kFW * R / 64;
+    for (int ls = 0; ls < S; ++ls) {
+      const int p = ls & 1;
+      const int64_t col0 = strip_col0(ls);
+      float vr[VPT];
+#pragma unroll
+      for (int i = 0; i < VPT; ++i) {
+        const int idx = vt + 64 * i, j = idx / R, k = idx % R;
+        vr[i] = col0 + j < a.n ? a.Vold[(col0 + j) * R + k] : 0.f;
+      }
+      if (ls >= 2 && !tc::mbar_wait(B(b_vempty + p), (uint32_t)(((ls >> 1) - 1) & 1), kWaitLimit))
+        err = 1;
+      uint8_t* img = smem + L::VIMG + p * L::VBYTES;
+#pragma unroll
+      for (int i = 0; i < VPT; ++i) {
+        const int idx = vt + 64 * i, j = idx / R, k = idx % R;
+        __half hi, lo;
+        split_h(vr[i], s_v, hi, lo);
+        const int off = (j >> 3) * SB_R + (k >> 3) * 128 + (j & 7) * 16 + (k & 7) * 2;
+        *reinterpret_cast<__half*>(img + off) = hi;
+        *reinterpret_cast<__half*>(img + kFW * R * 2 + off) = lo;
+      }
+      tc::fence_proxy_async_smem();
+      __syncwarp();
+      if (lane == 0) tc::mbar_arrive(B(b_vfull + p));
+    }
+  } else if (warp < 12) {
+    // ================= S-step epilogue (256 threads) ==========================
+    const int quarter = warp & 3, rb = (warp - 4) >> 2;
+    const int al = quarter * 32 + lane;
+    const int arow = rb * 128 + al;
+    const float inv_uv = 1.f / (s_u * s_v);
+    const float inv_lam = 1.f / a.lam;
+    float hub_hi = 0.f, hub_lo = 0.f;
+    for (int ls = 0; ls < S; ++ls) {
+      const int p = ls & 1;
+      if (!tc::mbar_wait(B(b_d1full + p), (uint32_t)((ls >> 1) & 1), kWaitLimit)) err = 1;
+      if (ls >= 2 && !tc::mbar_wait(B(b_cempty + p), (uint32_t)(((ls >> 1) - 1) & 1), kWaitLimit))
+        err = 1;
+      tc::fence_after_sync();
+      uint8_t* cbuf = smem + L::CBUF + p * L::CBYTES;
       float hub = 0.f;
 #pragma unroll
       for (int q = 0; q < 2; ++q) {
-        const int g = ls * 4 + b * 2 + q;
-        const int slot = g % NST;
-        if (!tc::mbar_wait(full_bar(slot), (uint32_t)((g / NST) & 1), kWaitLimit)) err = 1;
+        const int g = ls * 4 + rb * 2 + q;
+        const int rs = g % NST;
         float dv[32];
-        const uint32_t ta = d1 + ((uint32_t)(quarter * 32) << 16) + b * kFW + q * 32;
+        const uint32_t ta = d1(p) + ((uint32_t)(quarter * 32) << 16) + rb * kFW + q * 32;
         tc::tmem_ld16(ta, dv);
         tc::tmem_ld16(ta + 16, dv + 16);
+        if (!tc::mbar_wait(B(b_full + rs), (uint32_t)((g / NST) & 1), kWaitLimit)) err = 1;
+        const float* msub = reinterpret_cast<const float*>(smem + L::RING + rs * kSubBytes);
+        float mv[32];
+#pragma unroll
+        for (int jj = 0; jj < 32; ++jj) mv[jj] = msub[jj * 128 + al];
         tc::tmem_ld_wait();
-        const float* msub = reinterpret_cast<const float*>(smem + L::RING + slot * kSubBytes);
+        __syncwarp();
+        if (lane == 0) tc::mbar_arrive(B(b_empty + rs));
         uint32_t packed[16];
 #pragma unroll
         for (int jj = 0; jj < 32; jj += 2) {
           float c2[2];
 #pragma unroll
           for (int u = 0; u < 2; ++u) {
-            const float mv = msub[(jj + u) * 128 + al];
-            const float rn = (mv - dv[jj + u] * inv_uv) * inv_lam;   // R / lambda
-            const float c = fminf(fmaxf(rn, -1.f), 1.f);             // C / lambda
-            hub = fmaf(c, rn - 0.5f * c, hub);                       // H(R) / lambda^2
+            const float rn = (mv[jj + u] - dv[jj + u] * inv_uv) * inv_lam;   // R / lambda
+            const float c = fminf(fmaxf(rn, -1.f), 1.f);                     // C / lambda
+            hub = fmaf(c, rn - 0.5f * c, hub);                               // H(R) / lambda^2
             c2[u] = c;
           }
           __half2 h2 = __floats2half2_rn(c2[0], c2[1]);
@@ -237,161 +375,179 @@ __global__ void __launch_bounds__(256, 1)
         for (int ch = 0; ch < 4; ++ch) {
           const int j8 = (q * 32 + ch * 8) >> 3;
           const int off = j8 * (kFH * 16) + (arow >> 3) * 128 + (arow & 7) * 16;
-          *reinterpret_cast<uint4*>(smem + L::CBUF + off) =
+          *reinterpret_cast<uint4*>(cbuf + off) =
               make_uint4(packed[4 * ch], packed[4 * ch + 1], packed[4 * ch + 2], packed[4 * ch + 3]);
         }
       }
       tsum(hub_hi, hub_lo, hub);
-    }
-    tc::fence_proxy_async_smem();
-    tc::fence_before_sync();
-    __syncthreads();
-    tc::fence_after_sync();
-    // (4) refill the ring; GEMM2: Y = C_s^T [W_hi | W_lo] over the 256 rows
-    if (tid == 0) {
-      for (int g = ls * 4 + NST; g < ls * 4 + NST + 4 && g < total_sub; ++g) issue_tma(g);
-#pragma unroll
-      for (int kk = 0; kk < kFH / 16; ++kk) {
-        const uint64_t ad = tc::smem_desc(sbase + L::CBUF + kk * 256, 128, kFH * 16);
-        const uint64_t bd = tc::smem_desc(sbase + L::WIMG + kk * 256, 128, kFH * 16);
-        tc::mma_ss(d2, ad, bd, idesc2, kk > 0 ? 1u : 0u);
+      tc::fence_before_sync();
+      tc::fence_proxy_async_smem();
+      __syncwarp();
+      if (lane == 0) {
+        tc::mbar_arrive(B(b_d1empty + p));
+        tc::mbar_arrive(B(b_cfull + p));
       }
-      tc::mma_commit(g2_bar);
     }
-    __syncwarp();
-    if (!tc::mbar_wait(g2_bar, par, kWaitLimit)) err = 1;
+    // P partial of this cluster's columns (after the last GEMM3)
+    if (!tc::mbar_wait(B(b_last), 0, kWaitLimit)) err = 1;
     tc::fence_after_sync();
-    // (5) partial column sums: rows j = 16*quarter + lane (lane < 16) of the M=64 result
-    if (warp < 4) {
+    {
+      const int64_t grow = row0 + arow;
+      float pv[2 * R];
+#pragma unroll
+      for (int c = 0; c < 2 * R; c += 16)
+        tc::tmem_ld16(d3 + ((uint32_t)(quarter * 32) << 16) + rb * 2 * R + c, pv + c);
+      tc::tmem_ld_wait();
+      if (grow < a.m) {
+        const float ps = a.lam / s_v;
+        float* out = a.part_p + ((int64_t)cid * a.m + grow) * R;
+#pragma unroll
+        for (int k = 0; k < R; ++k) out[k] = S > 0 ? (pv[k] + pv[R + k]) * ps : 0.f;
+      }
+    }
+    double hsum = ((double)hub_hi + (double)hub_lo) * (double)a.lam * (double)a.lam;
+    for (int o = 16; o > 0; o >>= 1) hsum += __shfl_xor_sync(0xffffffffu, hsum, o);
+    if (lane == 0) red[warp - 4] = hsum;
+  } else {
+    // ================= exchange (128 threads) =================================
+    const int xt = tid - 384;            // 0..127
+    const int xw = warp - 12;            // == TMEM lane quarter
+    const float y_scale = a.lam / s_w;
+    constexpr int NE = R * R / 128;      // Q / X_v entries per thread
+    float q_hi[NE], q_lo[NE], x_hi[NE], x_lo[NE];
+#pragma unroll
+    for (int i = 0; i < NE; ++i) { q_hi[i] = q_lo[i] = x_hi[i] = x_lo[i] = 0.f; }
+    float vmax = 0.f;
+    constexpr int XPT = kFW * R / 128;   // V_s rows of all chunks, entries per thread (max)
+    for (int ls = 0; ls < S; ++ls) {
+      const int64_t col0 = strip_col0(ls);
+      // V_s rows of this CTA's chunks (global loads overlap the waits below)
+      float sr[XPT];
+#pragma unroll
+      for (int i = 0; i < XPT; ++i) {
+        const int e = xt + 128 * i;
+        float v = 0.f;
+        if (e < nch * kChunk * R) {
+          const int ci = e / (kChunk * R), jl = (e / R) % kChunk, k = e % R;
+          const int64_t col = col0 + ((int)crank + ci * cs) * kChunk + jl;
+          if (col < a.n) v = a.Vold[col * R + k];
+        }
+        sr[i] = v;
+      }
+      // ---- column sums of this CTA's rows out of tensor memory ----
+      if (!tc::mbar_wait(B(b_d2full), (uint32_t)(ls & 1), kWaitLimit)) err = 1;
+      tc::fence_after_sync();
       float yv[2 * R];
 #pragma unroll
       for (int c = 0; c < 2 * R; c += 16)
-        tc::tmem_ld16(d2 + ((uint32_t)(warp * 32) << 16) + c, yv + c);
+        tc::tmem_ld16(d2 + ((uint32_t)(xw * 32) << 16) + c, yv + c);
       tc::tmem_ld_wait();
+      tc::fence_before_sync();
+      __syncwarp();
+      if (lane == 0) tc::mbar_arrive(B(b_d2empty));
+      if (ls >= 1 && !tc::mbar_wait_cluster(B(b_yfree), (uint32_t)((ls - 1) & 1), kWaitLimit))
+        err = 1;
       if (lane < 16) {
-        const int j = warp * 16 + lane;
+        const int j = xw * 16 + lane;
 #pragma unroll
         for (int k = 0; k < R; ++k) ypart[j * R + k] = (yv[k] + yv[R + k]) * y_scale;
       }
-    }
-    tc::fence_before_sync();
-    tc::cluster_sync();  // #1: every CTA's partial column sums are visible
-    tc::fence_after_sync();
-    // (6) reduce-scatter over 8-column chunks, V' = V_s Z + Y, all-gather of the fp16 image
-    for (int cc = (int)crank; cc < kFW / 8; cc += a.cs) {
-      const int jl = tid / R, k = tid % R;  // active for tid < 8R
-      if (tid < 8 * R) {
-        const int64_t col = col0 + cc * 8 + jl;
-        vsl[jl * R + k] = col < a.n ? a.Vold[col * R + k] : 0.f;
-      }
-      __syncthreads();
-      if (tid < 8 * R) {
-        const int j = cc * 8 + jl;
-        const int64_t col = col0 + j;
-        float y = 0.f;
-        const uint32_t yaddr = sbase + L::YPART + (uint32_t)(j * R + k) * 4;
-        for (int p = 0; p < a.cs; ++p) y += tc::ld_cluster_f32(tc::map_cluster(yaddr, p));
-#pragma unroll 8
-        for (int l = 0; l < R; ++l) y = fmaf(vsl[jl * R + l], zm[l * R + k], y);
-        const float v = col < a.n ? y : 0.f;
-        if (col < a.n) a.Vnew[col * R + k] = v;
-        vnl[jl * R + k] = v;
-        vmax = fmaxf(vmax, fabsf(v));
-        __half hi, lo;
-        split_h(v, s_v, hi, lo);
-        // chunk image: entry (n, jl) at (n/8)*128 + (n%8)*16 + jl*2, n = k (hi) or R + k (lo)
-        *reinterpret_cast<__half*>(smem + L::STG + (k >> 3) * 128 + (k & 7) * 16 + jl * 2) = hi;
-        *reinterpret_cast<__half*>(smem + L::STG + ((R + k) >> 3) * 128 + (k & 7) * 16 + jl * 2) =
-            lo;
-      }
-      __syncthreads();
-      // Q_t and V_{t-1}^T V_t contributions of the 8 columns
 #pragma unroll
-      for (int i = 0; i < NE; ++i) {
-        const int e = tid + 256 * i;
-        if (e < R * R) {
+      for (int i = 0; i < XPT; ++i) {
+        const int e = xt + 128 * i;
+        if (e < nch * kChunk * R) vslx[e] = sr[i];
+      }
+      tc::fence_acq_rel_cluster();
+      tc::named_bar(1, 128);
+      if (xt < cs) tc::mbar_arrive_cluster(B(b_yfull), (uint32_t)xt);
+      // ---- GEMM3 of the previous strip done here: tell every reducer ----
+      if (ls >= 1) {
+        if (xw == 0) {
+          if (!tc::mbar_wait(B(b_g3done), (uint32_t)((ls - 1) & 1), kWaitLimit)) err = 1;
+          if (lane < cs) tc::mbar_arrive_cluster(B(b_pfree), (uint32_t)lane);
+        }
+      }
+      // ---- reduce-scatter: sums of this CTA's chunks over the cluster ----
+      if (!tc::mbar_wait_cluster(B(b_yfull), (uint32_t)(ls & 1), kWaitLimit)) err = 1;
+      for (int ci = 0; ci < nch; ++ci) {
+        const int cc = (int)crank + ci * cs;
+        const bool act = xt < kChunk * R;
+        const int jl = xt / R, k = xt % R;
+        float y = 0.f;
+        if (act) {
+          const int j = cc * kChunk + jl;
+          const uint32_t yaddr = sbase + L::YPART + (uint32_t)(j * R + k) * 4;
+          float yp[16];
+#pragma unroll
+          for (int p2 = 0; p2 < 16; ++p2)
+            yp[p2] = p2 < cs ? tc::ld_cluster_f32_relaxed(tc::map_cluster(yaddr, p2)) : 0.f;
+#pragma unroll
+          for (int p2 = 0; p2 < 16; ++p2) y += yp[p2];
+        }
+        if (ci == nch - 1) {
+          // every remote read of this strip is done: release the column-sum buffers
+          tc::fence_acq_rel_cluster();
+          tc::named_bar(1, 128);
+          if (xt < cs) tc::mbar_arrive_cluster(B(b_yfree), (uint32_t)xt);
+        }
+        if (act) {
+          const int64_t col = col0 + cc * kChunk + jl;
+          const float* vs = vslx + (ci * kChunk + jl) * R;
+#pragma unroll 8
+          for (int l = 0; l < R; ++l) y = fmaf(vs[l], zm[l * R + k], y);
+          const float v = col < a.n ? y : 0.f;
+          if (col < a.n) a.Vnew[col * R + k] = v;
+          vnl[jl * R + k] = v;
+          vmax = fmaxf(vmax, fabsf(v));
+          __half hi, lo;
+          split_h(v, s_v, hi, lo);
+          // chunk image: entry (n, jl) at n*8 + jl*2, n = k (hi) or R + k (lo)
+          *reinterpret_cast<__half*>(smem + L::STG + k * 8 + jl * 2) = hi;
+          *reinterpret_cast<__half*>(smem + L::STG + (R + k) * 8 + jl * 2) = lo;
+        }
+        tc::named_bar(1, 128);
+        // Q_t and V_{t-1}^T V_t contributions of the chunk's columns
+#pragma unroll
+        for (int i = 0; i < NE; ++i) {
+          const int e = xt + 128 * i;
           const int k1 = e / R, k2 = e % R;
           float qa = 0.f, xa = 0.f;
 #pragma unroll
-          for (int jj = 0; jj < 8; ++jj) {
+          for (int jj = 0; jj < kChunk; ++jj) {
             qa = fmaf(vnl[jj * R + k1], vnl[jj * R + k2], qa);
-            xa = fmaf(vsl[jj * R + k1], vnl[jj * R + k2], xa);
+            xa = fmaf(vslx[(ci * kChunk + jj) * R + k1], vnl[jj * R + k2], xa);
           }
           tsum(q_hi[i], q_lo[i], qa);
           tsum(x_hi[i], x_lo[i], xa);
         }
-      }
-      // all-gather: 2R/8 groups of 128 contiguous bytes into every CTA's V' image
-      constexpr int NPIECE = (2 * R / 8) * 8;   // 16-byte pieces per destination
-      for (int idx = tid; idx < a.cs * NPIECE; idx += 256) {
-        const int p = idx / NPIECE, pc = idx % NPIECE;
-        const int g8 = pc >> 3, w16 = pc & 7;
-        const uint4 v = *reinterpret_cast<const uint4*>(smem + L::STG + g8 * 128 + w16 * 16);
-        const uint32_t dst = sbase + L::PIMG + g8 * (kFW / 8) * 128 + cc * 128 + w16 * 16;
-        tc::st_cluster_u32x4(tc::map_cluster(dst, p), v);
-      }
-      __syncthreads();
-    }
-    asm volatile("fence.proxy.async;" ::: "memory");
-    tc::fence_before_sync();
-    tc::cluster_sync();  // #2: the V' image of the strip is complete in every CTA
-    tc::fence_after_sync();
-    // (7) GEMM3: P_C += C_s [V'_hi | V'_lo]^T for both row blocks
-    if (tid == 0) {
-      asm volatile("fence.proxy.async;" ::: "memory");
-#pragma unroll
-      for (int b = 0; b < 2; ++b) {
-#pragma unroll
-        for (int kk = 0; kk < kFW / 16; ++kk) {
-          const uint64_t ad =
-              tc::smem_desc(sbase + L::CBUF + b * 2048 + kk * 2 * (kFH * 16), kFH * 16, 128);
-          const uint64_t bd =
-              tc::smem_desc(sbase + L::PIMG + kk * 256, 128, (kFW / 8) * 128);
-          tc::mma_ss(d3 + b * 2 * R, ad, bd, idesc3, (ls > 0 || kk > 0) ? 1u : 0u);
+        // all-gather of the chunk's V' image into every CTA (after their GEMM3 of ls-1)
+        if (ci == 0 && ls >= 1 &&
+            !tc::mbar_wait_cluster(B(b_pfree), (uint32_t)((ls - 1) & 1), kWaitLimit))
+          err = 1;
+        for (int idx = xt; idx < cs * 2 * R; idx += 128) {
+          const int p2 = idx / (2 * R), nn = idx % (2 * R);
+          const uint2 v = *reinterpret_cast<const uint2*>(smem + L::STG + nn * 8);
+          const uint32_t dst = sbase + L::PIMG + (nn >> 3) * (kFW / 8) * 128 + (cc >> 1) * 128 +
+                               (nn & 7) * 16 + (cc & 1) * 8;
+          tc::st_cluster_u32x2(tc::map_cluster(dst, p2), v.x, v.y);
         }
+        tc::fence_proxy_async_cluster();
+        tc::fence_acq_rel_cluster();
+        tc::named_bar(1, 128);   // STG and VNL reused by the next chunk
       }
-      tc::mma_commit(g3_bar);
+      if (xt < cs) tc::mbar_arrive_cluster(B(b_pfull), (uint32_t)xt);
     }
-    __syncwarp();
-  }
-
-  // ---- P partial of this cluster's columns ---------------------------------
-  if (my_strips > 0 && !tc::mbar_wait(g3_bar, (uint32_t)((my_strips - 1) & 1), kWaitLimit))
-    err = 1;
-  tc::fence_after_sync();
-  {
-    const int b = warp >> 2, quarter = warp & 3;
-    const int al = quarter * 32 + lane;
-    const int64_t arow = row0 + b * 128 + al;
-    float pv[2 * R];
+    // per-CTA partials
 #pragma unroll
-    for (int c = 0; c < 2 * R; c += 16)
-      tc::tmem_ld16(d3 + ((uint32_t)(quarter * 32) << 16) + b * 2 * R + c, pv + c);
-    tc::tmem_ld_wait();
-    if (arow < a.m) {
-      const float ps = a.lam / s_v;
-      float* out = a.part_p + ((int64_t)cid * a.m + arow) * R;
-#pragma unroll
-      for (int k = 0; k < R; ++k) out[k] = my_strips > 0 ? (pv[k] + pv[R + k]) * ps : 0.f;
-    }
-  }
-  // ---- per-CTA partials ----------------------------------------------------------
-#pragma unroll
-  for (int i = 0; i < NE; ++i) {
-    const int e = tid + 256 * i;
-    if (e < R * R) {
+    for (int i = 0; i < NE; ++i) {
+      const int e = xt + 128 * i;
       a.part_q[(int64_t)blockIdx.x * R * R + e] = (double)q_hi[i] + (double)q_lo[i];
       a.part_xv[(int64_t)blockIdx.x * R * R + e] = (double)x_hi[i] + (double)x_lo[i];
     }
-  }
-  double* red = reinterpret_cast<double*>(smem + L::RED);
-  {
-    double hsum = ((double)hub_hi + (double)hub_lo) * (double)a.lam * (double)a.lam;
-    for (int o = 16; o > 0; o >>= 1) hsum += __shfl_xor_sync(0xffffffffu, hsum, o);
     for (int o = 16; o > 0; o >>= 1) vmax = fmaxf(vmax, __shfl_xor_sync(0xffffffffu, vmax, o));
-    if (lane == 0) red[warp] = hsum;
     if (lane == 0 && vmax > 0.f) atomicMax(a.vmax_out, __float_as_uint(vmax));
   }
+
   if (err) atomicExch(a.err, DCF_ETIMEOUT);
   tc::fence_before_sync();
   __syncthreads();
@@ -400,7 +556,7 @@ __global__ void __launch_bounds__(256, 1)
     for (int w = 0; w < 8; ++w) t += red[w];
     a.part_h[blockIdx.x] = t;
   }
-  if (warp == 0) tc::tmem_dealloc(tbase, 512);
+  if (warp == 1) tc::tmem_dealloc(tbase, 512);
   tc::cluster_sync();  // no CTA leaves while a peer may still address its shared memory
 }
 
@@ -447,23 +603,24 @@ __global__ void __launch_bounds__(256) k_fused_prep(const float* __restrict__ U,
   for (int i = 0; i < 8; ++i) { umax = fmaxf(umax, red[0][i]); wmax = fmaxf(wmax, red[1][i]); }
   const float s_u = pow2_scale_dev(umax, 16384.f), s_w = pow2_scale_dev(wmax, 16384.f);
   uint8_t* dst = img + (size_t)slab * (4 * kFH * R * 2);
-  constexpr uint32_t SB_R = (R / 8) * 128;
-  // U image: term t, row a, k -> t*(256*R*2) + (a/8)*SB_R + (k/8)*128 + (a%8)*16 + (k%8)*2
+  // U image for tensor memory: row a -> R/2 words of fp16 hi pairs, then R/2 of lo pairs
+  {
+    uint32_t wh[R / 2], wl[R / 2];
 #pragma unroll
-  for (int k8 = 0; k8 < R / 8; ++k8) {
-    uint32_t ph[4], pl[4];
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
+    for (int i = 0; i < R / 2; ++i) {
       __half h0, l0, h1, l1;
-      split_h(u[k8 * 8 + 2 * i], s_u, h0, l0);
-      split_h(u[k8 * 8 + 2 * i + 1], s_u, h1, l1);
+      split_h(u[2 * i], s_u, h0, l0);
+      split_h(u[2 * i + 1], s_u, h1, l1);
       __half2 hh = __halves2half2(h0, h1), ll = __halves2half2(l0, l1);
-      ph[i] = *reinterpret_cast<uint32_t*>(&hh);
-      pl[i] = *reinterpret_cast<uint32_t*>(&ll);
+      wh[i] = *reinterpret_cast<uint32_t*>(&hh);
+      wl[i] = *reinterpret_cast<uint32_t*>(&ll);
     }
-    const int off = (tid >> 3) * SB_R + k8 * 128 + (tid & 7) * 16;
-    *reinterpret_cast<uint4*>(dst + off) = make_uint4(ph[0], ph[1], ph[2], ph[3]);
-    *reinterpret_cast<uint4*>(dst + kFH * R * 2 + off) = make_uint4(pl[0], pl[1], pl[2], pl[3]);
+    uint4* row = reinterpret_cast<uint4*>(dst + (size_t)tid * R * 4);
+#pragma unroll
+    for (int i = 0; i < R / 8; ++i) {
+      row[i] = make_uint4(wh[4 * i], wh[4 * i + 1], wh[4 * i + 2], wh[4 * i + 3]);
+      row[R / 8 + i] = make_uint4(wl[4 * i], wl[4 * i + 1], wl[4 * i + 2], wl[4 * i + 3]);
+    }
   }
   // W image: entry (n, a), n < R -> W_hi[a, n], n >= R -> W_lo[a, n-R]:
   //   (n/8)*(256*16) + (a/8)*128 + (n%8)*16 + (a%8)*2
@@ -505,8 +662,8 @@ __global__ void k_absmax(const float* x, int64_t count, unsigned int* out) {
 // ---------------------------------------------------------------------------
 // host side
 // ---------------------------------------------------------------------------
-constexpr int kNST32 = 6;
-constexpr int kNST16 = 8;
+constexpr int kNST32 = 5;
+constexpr int kNST16 = 7;
 
 template <int R, int NST>
 static size_t fused_smem() {
@@ -529,7 +686,7 @@ template <int R, int NST>
 static int max_clusters_T(int cs) {
   cudaLaunchConfig_t cfg{};
   cfg.gridDim = dim3(cs, 1, 1);
-  cfg.blockDim = dim3(256, 1, 1);
+  cfg.blockDim = dim3(kFThreads, 1, 1);
   cfg.dynamicSmemBytes = fused_smem<R, NST>();
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeClusterDimension;
@@ -595,7 +752,7 @@ template <int R, int NST>
 static cudaError_t launch_fused_T(const void* tmap, const FusedArgs& fa, cudaStream_t s) {
   cudaLaunchConfig_t cfg{};
   cfg.gridDim = dim3(fa.cs * fa.nclusters, 1, 1);
-  cfg.blockDim = dim3(256, 1, 1);
+  cfg.blockDim = dim3(kFThreads, 1, 1);
   cfg.dynamicSmemBytes = fused_smem<R, NST>();
   cfg.stream = s;
   cudaLaunchAttribute attr[1];
