@@ -206,6 +206,43 @@ dcf_status dcf_iterate_noalloc(const float* M, int64_t m, int64_t n, int r, doub
                                double lambda, const float* U_in, const float* V_in,
                                float* U_out, float* V_out, void* stream);
 
+/* ------------------------------------------------------------------------
+ * Learned unrolled network (K iterations with per-step parameters) and its
+ * adjoint.
+ *
+ * Step k runs one exact-consensus iteration (S-step of Sec. 2.2, V-step and
+ * U-step of App. B) with lambda_k = lambda * exp(a[k]), rho_k = rho * exp(b[k])
+ * and the relaxed update U <- U + c[k] (U* - U), where U* is the consensus
+ * U-step.  a = b = 0, c = 1 gives K plain iterations.  The loss is
+ *   sum_k w_k ||U_k V_k^T - A B^T||_F^2 / ||A B^T||_F^2   (k = 1..K),
+ * A, B from dcf_set_truth, w_k = weights[k-1] or 2k / (K (K + 1)) when
+ * weights is NULL; it is evaluated through rank-sized Gram matrices.
+ * ------------------------------------------------------------------------ */
+
+/* Forward pass from the handle's current factors (the seeded start point if
+ * nothing ran yet).  a, b, c: K host doubles each; weights: K host doubles or
+ * NULL.  loss_terms (K host doubles, the unweighted per-step losses) and
+ * total_loss may be NULL; when either is given, dcf_set_truth must have been
+ * called (DCF_ESTATE otherwise).  Afterwards the handle holds U_K, V_K, so
+ * dcf_step / dcf_solve continue with plain iterations (lambda, rho of the
+ * params).  Checkpoints (U_k, V_k, U*_k): (K+1)(m+n)r + K m r floats on the
+ * device, owned by the handle.  Requires u_mode = 0 and r <= 32
+ * (DCF_EINVAL).  Synchronous. */
+dcf_status dcf_unrolled_forward(dcf_handle h, int K, const double* a, const double* b,
+                                const double* c, const double* weights, double* loss_terms,
+                                double* total_loss);
+
+/* Reverse mode of the last dcf_unrolled_forward (which must have had a truth
+ * registered; DCF_ESTATE otherwise): d loss / d a[k], d b[k], d c[k] into
+ * grad_a, grad_b, grad_c (K host doubles each, any may be NULL), and the
+ * gradient with respect to the start point: grad_U0 (m x r row-major) and
+ * grad_V0_i[i] (n_i x r row-major), each NULL to skip, on the host
+ * (where = 0) or the device (where = 1).  Every m x n quantity is recomputed
+ * from M and the checkpoints.  M must be the one the forward pass used.
+ * Synchronous. */
+dcf_status dcf_unrolled_backward(dcf_handle h, double* grad_a, double* grad_b, double* grad_c,
+                                 float* grad_U0, float* const* grad_V0_i, int where);
+
 /* Library version string. */
 const char* dcf_version(void);
 

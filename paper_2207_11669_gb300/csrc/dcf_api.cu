@@ -15,6 +15,7 @@
 #include <vector>
 
 #include "dcf.h"
+#include "dcf_handle.h"
 #include "dcf_internal.cuh"
 
 namespace dcf {
@@ -39,6 +40,7 @@ cudaError_t prepare_stream_kernels();
 }  // namespace dcf
 
 using namespace dcf;
+using namespace dcf::api;
 
 // ---------------------------------------------------------------------------
 // allocator hook
@@ -53,66 +55,9 @@ extern "C" void dcf_set_allocator(dcf_alloc_fn alloc, dcf_free_fn release, void*
   g_alloc_ctx = ctx;
 }
 
-struct dcf_handle_s {
-  // problem
-  int64_t m = 0, n = 0;
-  int E = 0, r = 0, R = 0;
-  double rho = 0, lam = 0, tol = 0, eta0 = 0;
-  int max_iter = 0, u_mode = 0, local_steps = 1;
-  uint64_t seed = 0;
-  std::vector<int64_t> n_i, c_i;
-  std::vector<char> priv;
-  // allocation
-  dcf_alloc_fn alloc = nullptr;
-  dcf_free_fn release = nullptr;
-  void* alloc_ctx = nullptr;
-  std::vector<void*> owned;
-  // device
-  int device = 0, num_sms = 0;
-  cudaStream_t user_stream = nullptr;
-  cudaStream_t stream = nullptr;     // internal capture/launch stream
-  cudaEvent_t ev_in = nullptr, ev_out = nullptr;
-  float* M = nullptr;
-  bool M_borrowed = false;
-  float* U[2] = {nullptr, nullptr};
-  float* V[2] = {nullptr, nullptr};
-  float* W = nullptr;
-  float* part_p = nullptr;
-  double* part_h = nullptr;
-  double* part_q = nullptr;
-  double* part_xv = nullptr;
-  double* part_g = nullptr;
-  double* part_xu = nullptr;
-  double* red = nullptr;             // reduction outputs: q, xv, h, g, xu (R*R each)
-  double* truth_part = nullptr;
-  double* truth_red = nullptr;
-  Smalls* sm = nullptr;
-  DevState* st = nullptr;
-  unsigned int* counters = nullptr;  // 4 last-block counters
-  int* flag = nullptr;
-  float* A_truth = nullptr;
-  float* B_truth = nullptr;
-  int k_truth = 0;
-  // launch geometry
-  int n_vblocks = 0, n_splits = 0, n_rblocks = 0, n_vgram = 0;
-  int64_t split_cols = 0;
-  // fused single-pass path
-  int path = 1;                       // 1 general, 2 fused
-  int cs = 0, nclusters = 0, nslabs = 0;
-  uint8_t* img = nullptr;
-  float* scales = nullptr;
-  float* zmat = nullptr;
-  unsigned int* vmax = nullptr;       // [2]: max |V| of copy 0 / 1 (float bits)
-  int* kerr = nullptr;                // kernel-side error (DCF_ETIMEOUT)
-  alignas(64) unsigned char tmap[128];
-  // state
-  bool loaded = false, initialized = false;
-  int host_iter = 0;                  // iterations enqueued (mirrors DevState::iter)
-  cudaGraphExec_t graph[2] = {nullptr, nullptr};
-  std::string err;
-};
 
-namespace {
+namespace dcf {
+namespace api {
 
 dcf_status fail(dcf_handle h, dcf_status code, const std::string& msg) {
   if (h) h->err = msg;
@@ -178,6 +123,8 @@ IterArgs iter_args(dcf_handle h, int cur) {
   a.sm = h->sm;
   a.st = h->st;
   a.add_uxv = h->path == 2 ? 1 : 0;
+  a.alpha = h->alpha;
+  a.ustar_out = h->ustar_out;
   if (h->path == 2) {
     a.n_vblocks = h->cs * h->nclusters;   // per-CTA partials of the fused kernel
     a.n_splits = h->nclusters;            // P partials: one per cluster
@@ -195,9 +142,9 @@ double* red_xu(dcf_handle h) { return h->red + 3 * (size_t)h->R * h->R + 8; }
 const char* const kPhaseNames[] = {"make_w", "pass1_vstep", "pass2_pstep", "gram_v",
                                    "reduce_q", "rows_ustep", "reduce_g"};
 constexpr int kNumPhases = 7;
-const char* const kFusedPhaseNames[] = {"fused_prep", "fused_step", "reduce_q", "rows_ustep",
-                                        "reduce_g"};
-constexpr int kNumFusedPhases = 5;
+const char* const kFusedPhaseNames[] = {"fused_prep", "fused_step", "gram_v", "reduce_q",
+                                        "rows_ustep", "reduce_g"};
+constexpr int kNumFusedPhases = 6;
 int num_phases(dcf_handle h) { return h->path == 2 ? kNumFusedPhases : kNumPhases; }
 const char* phase_name(dcf_handle h, int p) {
   return h->path == 2 ? kFusedPhaseNames[p] : kPhaseNames[p];
@@ -217,6 +164,7 @@ cudaError_t enqueue_fused_iteration(dcf_handle h, int cur, cudaStream_t s, cudaE
   if ((e = launch_fused_prep(h->R, h->U[cur], h->sm, h->st, h->m, h->nslabs, (float)h->rho,
                              h->vmax + cur, h->vmax + nxt, h->img, h->scales, h->zmat, s)) !=
           cudaSuccess ||
+      (e = launch_rowmat(h->R, h->V[cur], h->zmat, h->n, h->W_vz, h->st, s)) != cudaSuccess ||
       (e = mark()) != cudaSuccess)
     return e;
   FusedArgs fa{};
@@ -232,17 +180,22 @@ cudaError_t enqueue_fused_iteration(dcf_handle h, int cur, cudaStream_t s, cudaE
   fa.img = h->img;
   fa.scales = h->scales;
   fa.zmat = h->zmat;
+  fa.VZ = h->W_vz;
   fa.vmax_out = h->vmax + nxt;
-  fa.part_q = h->part_q;
-  fa.part_xv = h->part_xv;
   fa.part_h = h->part_h;
   fa.part_p = h->part_p;
   fa.st = h->st;
   fa.err = h->kerr;
   if ((e = launch_fused(h->R, h->tmap, fa, s)) != cudaSuccess || (e = mark()) != cudaSuccess)
     return e;
-  const int grid = h->cs * h->nclusters;
-  if ((e = launch_reduce_q(a, red_q(h), red_xv(h), red_h(h), grid, h->counters + 0, s)) !=
+  // Q_t = V_t^T V_t and V_{t-1}^T V_t from the new V (Gram partials)
+  if ((e = launch_gram(h->V[nxt], h->R, h->R, h->V[nxt], h->R, h->R, h->n, h->part_q,
+                       h->n_vgram, h->st, 1, s)) != cudaSuccess)
+    return e;
+  if ((e = launch_gram(h->V[cur], h->R, h->R, h->V[nxt], h->R, h->R, h->n, h->part_xv,
+                       h->n_vgram, h->st, 1, s)) != cudaSuccess || (e = mark()) != cudaSuccess)
+    return e;
+  if ((e = launch_reduce_q(a, red_q(h), red_xv(h), red_h(h), h->n_vgram, h->counters + 0, s)) !=
           cudaSuccess ||
       (e = mark()) != cudaSuccess)
     return e;
@@ -253,7 +206,7 @@ cudaError_t enqueue_fused_iteration(dcf_handle h, int cur, cudaStream_t s, cudaE
 
 // Enqueue one iteration reading copy `cur` (capturable).  When `ev` is not
 // NULL, event ev[p] is recorded after phase p (profiling path, not captured).
-cudaError_t enqueue_iteration(dcf_handle h, int cur, cudaStream_t s, cudaEvent_t* ev = nullptr) {
+cudaError_t enqueue_iteration(dcf_handle h, int cur, cudaStream_t s, cudaEvent_t* ev) {
   if (h->path == 2) return enqueue_fused_iteration(h, cur, s, ev);
   IterArgs a = iter_args(h, cur);
   const int nxt = cur ^ 1;
@@ -292,7 +245,7 @@ dcf_status build_graphs(dcf_handle h) {
     if (h->graph[p]) continue;
     cudaGraph_t g = nullptr;
     CK(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal), "begin capture");
-    cudaError_t e = enqueue_iteration(h, p, h->stream);
+    cudaError_t e = enqueue_iteration(h, p, h->stream, nullptr);
     cudaError_t e2 = cudaStreamEndCapture(h->stream, &g);
     if (e != cudaSuccess) {
       if (g) cudaGraphDestroy(g);
@@ -384,7 +337,8 @@ dcf_status ensure_init(dcf_handle h) {
   return finish_init(h, false);
 }
 
-}  // namespace
+}  // namespace api
+}  // namespace dcf
 
 // ---------------------------------------------------------------------------
 // entry points
@@ -525,11 +479,11 @@ extern "C" dcf_status dcf_create(const dcf_params* p, dcf_handle* out) {
     h->img = (uint8_t*)A((size_t)h->nslabs * 2048 * R);
     h->scales = (float*)A((2 * (size_t)h->nslabs + 1) * sizeof(float));
     h->zmat = (float*)A(RR * sizeof(float));
+    h->W_vz = (float*)A((size_t)h->n * R * sizeof(float));
     h->vmax = (unsigned int*)A(2 * sizeof(unsigned int));
     h->part_p = (float*)A((size_t)h->nclusters * h->m * R * 4);
     h->part_h = (double*)A(grid * 8);
-    h->part_q = (double*)A(std::max(grid, ngp) * RR * 8);
-    h->part_xv = (double*)A(std::max(grid, (size_t)h->n_vgram) * RR * 8);
+
   }
   if (!ok) {
     dcf_destroy(h);
@@ -859,6 +813,7 @@ extern "C" dcf_status dcf_profile_step(dcf_handle h, int n_steps, double* phase_
 extern "C" void dcf_destroy(dcf_handle h) {
   if (!h) return;
   if (h->stream) cudaStreamSynchronize(h->stream);
+  free_unrolled(h);
   for (int p = 0; p < 2; ++p)
     if (h->graph[p]) cudaGraphExecDestroy(h->graph[p]);
   dev_free_all(h);

@@ -1,0 +1,92 @@
+// Internal: the handle behind dcf_handle and the host helpers shared by the
+// C-ABI translation units (dcf_api.cu, dcf_unrolled.cu).
+#pragma once
+#include <cuda_runtime.h>
+
+#include <string>
+#include <vector>
+
+#include "dcf.h"
+#include "dcf_internal.cuh"
+
+struct UnrolledState;
+
+struct dcf_handle_s {
+  // problem
+  int64_t m = 0, n = 0;
+  int E = 0, r = 0, R = 0;
+  double rho = 0, lam = 0, tol = 0, eta0 = 0;
+  int max_iter = 0, u_mode = 0, local_steps = 1;
+  uint64_t seed = 0;
+  std::vector<int64_t> n_i, c_i;
+  std::vector<char> priv;
+  // allocation
+  dcf_alloc_fn alloc = nullptr;
+  dcf_free_fn release = nullptr;
+  void* alloc_ctx = nullptr;
+  std::vector<void*> owned;
+  // device
+  int device = 0, num_sms = 0;
+  cudaStream_t user_stream = nullptr;
+  cudaStream_t stream = nullptr;     // internal capture/launch stream
+  cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+  float* M = nullptr;
+  bool M_borrowed = false;
+  float* U[2] = {nullptr, nullptr};
+  float* V[2] = {nullptr, nullptr};
+  float* W = nullptr;
+  float* part_p = nullptr;
+  double* part_h = nullptr;
+  double* part_q = nullptr;
+  double* part_xv = nullptr;
+  double* part_g = nullptr;
+  double* part_xu = nullptr;
+  double* red = nullptr;             // reduction outputs: q, xv, h, g, xu (R*R each)
+  double* truth_part = nullptr;
+  double* truth_red = nullptr;
+  dcf::Smalls* sm = nullptr;
+  dcf::DevState* st = nullptr;
+  unsigned int* counters = nullptr;  // 4 last-block counters
+  int* flag = nullptr;
+  float* A_truth = nullptr;
+  float* B_truth = nullptr;
+  int k_truth = 0;
+  // launch geometry
+  int n_vblocks = 0, n_splits = 0, n_rblocks = 0, n_vgram = 0;
+  int64_t split_cols = 0;
+  // fused single-pass path
+  int path = 1;                       // 1 general, 2 fused
+  int cs = 0, nclusters = 0, nslabs = 0;
+  uint8_t* img = nullptr;
+  float* scales = nullptr;
+  float* zmat = nullptr;
+  float* W_vz = nullptr;              // n x R, V_old Z (fused path)
+  unsigned int* vmax = nullptr;       // [2]: max |V| of copy 0 / 1 (float bits)
+  int* kerr = nullptr;                // kernel-side error (DCF_ETIMEOUT)
+  alignas(64) unsigned char tmap[128];
+  // state
+  bool loaded = false, initialized = false;
+  int host_iter = 0;                  // iterations enqueued (mirrors DevState::iter)
+  cudaGraphExec_t graph[2] = {nullptr, nullptr};
+  float alpha = 1.0f;                 // relaxation of the U-step (learned network)
+  float* ustar_out = nullptr;         // when set, the U-step also stores U* here
+  UnrolledState* unrolled = nullptr;  // checkpoints and buffers of the learned network
+  std::string err;
+};
+
+
+namespace dcf {
+namespace api {
+dcf_status fail(dcf_handle h, dcf_status code, const std::string& msg);
+dcf_status cuda_fail(dcf_handle h, cudaError_t e, const char* what);
+void* dev_alloc(dcf_handle h, size_t bytes);
+IterArgs iter_args(dcf_handle h, int cur);
+cudaError_t enqueue_iteration(dcf_handle h, int cur, cudaStream_t s, cudaEvent_t* ev);
+dcf_status begin_work(dcf_handle h);
+dcf_status end_work(dcf_handle h);
+dcf_status read_state(dcf_handle h, DevState* out);
+dcf_status ensure_init(dcf_handle h);
+dcf_status set_state_fields(dcf_handle h, int solve_mode, double tol);
+void free_unrolled(dcf_handle h);
+}  // namespace api
+}  // namespace dcf

@@ -69,6 +69,8 @@ struct IterArgs {
   Smalls* sm;
   DevState* st;
   int add_uxv;       // 1: P[a,:] += U_{t-1}[a,:] (V_{t-1}^T V_t)  (fused path)
+  float alpha;       // U_t = U_{t-1} + alpha (U* - U_{t-1}) in exact mode (1: plain step)
+  float* ustar_out;  // optional m x R copy of U* (learned network checkpoints)
 };
 
 // Launchers (stream-ordered; return cudaGetLastError()).
@@ -100,9 +102,8 @@ struct FusedArgs {
   const uint8_t* img;       // [slab][U image | W image]
   const float* scales;      // [2*slab] = s_u, [2*slab+1] = s_w, [2*nslabs] = s_v
   const float* zmat;        // R x R, Z = I - rho (U^T U + rho I)^{-1}
+  const float* VZ;          // n x R, V_old Z
   unsigned int* vmax_out;   // max |V'| (float bits)
-  double* part_q;           // [grid][R*R]
-  double* part_xv;          // [grid][R*R]
   double* part_h;           // [grid]
   float* part_p;            // [nclusters][m][R]
   DevState* st;
@@ -117,5 +118,7 @@ cudaError_t launch_fused_prep(int R, const float* U, const Smalls* sm, const Dev
                               unsigned int* vmax_reset, uint8_t* img, float* scales, float* zmat,
                               cudaStream_t s);
 cudaError_t launch_absmax(const float* x, int64_t count, unsigned int* out, cudaStream_t s);
+cudaError_t launch_rowmat(int R, const float* in, const float* zmat, int64_t n, float* out,
+                          const DevState* st, cudaStream_t s);
 
 }  // namespace dcf

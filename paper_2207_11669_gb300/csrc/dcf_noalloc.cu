@@ -169,6 +169,8 @@ extern "C" dcf_status dcf_iterate_noalloc(const float* M, int64_t m, int64_t n, 
   a.split_cols = split_cols;
   a.n_rblocks = n_rblocks;
   a.add_uxv = 0;
+  a.alpha = 1.0f;
+  a.ustar_out = nullptr;
   double* red_q = red;
   double* red_xv = red + RR;
   double* red_h = red + 2 * RR;

@@ -11,9 +11,11 @@
 // so the dense work is three tensor-core products per strip of 64 columns:
 //   GEMM1  D1 = U V_s^T            (3-term fp16 split of U and V: ~FP32 accuracy;
 //                                   R feeds the soft-threshold support)
-//   GEMM2  Y  = C_s^T [W_hi|W_lo]  (C/lambda in [-1,1] stored once in fp16)
-//   GEMM3  P_C += C_s [V'_hi|V'_lo]^T
-// and V^T V' (= V_{t-1}^T V_t, also a metric) closes P in the r x r algebra.
+//   GEMM2  Y  = C_s^T W_hi + C_s^T W_lo   (C/lambda in [-1,1] stored once in fp16)
+//   GEMM3  P_C += C_s V'_hi^T + C_s V'_lo^T
+// V Z is precomputed (k_rowmat) and added by the reducers; V^T V' (= V_{t-1}^T V_t,
+// also a metric) closes P in the r x r algebra and, with Q = V'^T V', comes
+// from the Gram kernels after the pass.
 //
 // Parallel layout: a thread-block cluster of CS CTAs owns whole columns; CTA c
 // of a cluster holds rows [256c, 256c+256) of U, W and of every M strip, so
@@ -42,7 +44,7 @@ constexpr int kSubBytes = 128 * 32 * 4;
 constexpr uint32_t kWaitLimit = 1u << 26;
 
 
-constexpr int kFThreads = 512;   // 16 warps, see the role map below
+constexpr int kFThreads = 640;   // 20 warps, see the role map below
 constexpr int kChunk = 4;        // columns per reduce-scatter chunk (16 chunks per strip)
 
 template <int R, int NST>
@@ -53,21 +55,21 @@ struct FL {  // shared-memory layout (bytes)
   static constexpr int CBUF = WIMG + 2 * R * kFH * 2;            // 2 C tiles
   static constexpr int VBYTES = 2 * kFW * R * 2;                 // one V image (2 terms)
   static constexpr int VIMG = CBUF + 2 * CBYTES;                 // 2 V images
-  static constexpr int PIMG = VIMG + 2 * VBYTES;                 // 2R x 64 fp16
-  static constexpr int YPART = PIMG + 2 * R * kFW * 2;           // 64 x R fp32
-  static constexpr int ZM = YPART + kFW * R * 4;                 // R x R fp32
-  static constexpr int VSLX = ZM + R * R * 4;                    // <= 64 x R fp32 (V_s rows)
-  static constexpr int VNL = VSLX + kFW * R * 4;                 // 4 x R fp32 (V' rows)
-  static constexpr int STG = VNL + kChunk * R * 4;               // 2R x 4 fp16 image chunk
-  static constexpr int BAR = STG + 2 * R * kChunk * 2;           // mbarriers
-  static constexpr int NBAR = 2 * NST + 20;
+  static constexpr int PBYTES = 2 * R * kFW * 2;                 // one V' image (2R x 64 fp16)
+  static constexpr int PIMG = VIMG + 2 * VBYTES;                 // 2 V' images
+  static constexpr int YBYTES = kFW * R * 4;                     // one column-sum block
+  static constexpr int YPART = PIMG + 2 * PBYTES;                // 2 x (64 x R fp32)
+  static constexpr int ZM = YPART + 2 * YBYTES;                  // R x R fp32
+  static constexpr int STG = ZM + R * R * 4;                     // 2R x 4 fp16 image chunk
+  static constexpr int BAR = STG + 2 * (2 * R * kChunk * 2);     // mbarriers (2 staging chunks)
+  static constexpr int NBAR = 2 * NST + 27;
   static constexpr int TSLOT = BAR + NBAR * 8;
   static constexpr int RED = TSLOT + 16;                         // 16 doubles
   static constexpr int TOTAL = RED + 16 * 8;
   // tensor-memory columns (512 allocated)
-  static constexpr int T_D2 = 256;                               // M=64 result, 2R columns
-  static constexpr int T_D3 = T_D2 + 2 * R;                      // 2 blocks x 2R (P_C)
-  static constexpr int T_U = T_D3 + 4 * R;                       // U hi/lo, 2 blocks x 2 x R/2
+  static constexpr int T_D2 = 256;                               // 2 x (M=64 result, R columns)
+  static constexpr int T_D3 = T_D2 + 2 * R;                      // 2 blocks x R (P_C)
+  static constexpr int T_U = T_D3 + 2 * R;                       // U hi/lo, 2 blocks x 2 x R/2
   static_assert(T_U + 2 * R <= 512, "tensor memory");
   static_assert(TOTAL <= 232448, "shared memory");
 };
@@ -92,22 +94,27 @@ __device__ __forceinline__ void tsum(float& hi, float& lo, float x) {
   hi = t;
 }
 
-// Warp-specialised pipeline over the strips of the cluster (16 warps):
+// Warp-specialised pipeline over the strips of the cluster (20 warps):
 //   warp 0       TMA producer: M sub-tiles into a ring of NST slots
-//   warp 1       MMA issuer (GEMM1 of strip i, GEMM2 of i-1, GEMM3 of i-2) and
-//                tensor-memory owner
-//   warps 2-3    fp16 images of V_s (B operand of GEMM1), two strips ahead
+//   warp 1       MMA issuer for GEMM1 (strip i) and GEMM2 (strip i-1); owns TMEM
+//   warp 2       MMA issuer for GEMM3, which waits on the cluster exchange and
+//                therefore must not hold up GEMM1/GEMM2 (tcgen05 ops complete in
+//                the issuing thread's order)
+//   warp 3       fp16 images of V_s (B operand of GEMM1), two strips ahead
 //   warps 4-11   S-step epilogue: R, C/lambda into the C tile, Huber
-//   warps 12-15  exchange: column sums out of tensor memory, reduce-scatter
-//                over the cluster (DSMEM), V', all-gather of the V' image
+//   warps 12-19  exchange, two groups of 4 warps for even and odd strips:
+//                column sums out of tensor memory, reduce-scatter over the
+//                cluster (DSMEM), V', all-gather of the V' image
 // Local mbarriers link the roles inside a CTA; four mbarriers per CTA,
 // arrived on remotely, link the CTAs of the cluster:
 //   yfull  (count CS)  every CTA has published its column sums of the strip
 //   yfree  (count CS)  every reducer has read this CTA's column sums
 //   pfull  (count CS)  every reducer has written its chunk of the V' image here
-//   pfree  (count CS)  every CTA's GEMM3 of the previous strip has completed
-// Each of them completes once per strip; an arrival for strip s+1 can only
-// happen after the phase of strip s has completed (see the waits below).
+//   pfree  (count CS)  every CTA's GEMM3 that read this V' image buffer is done
+// Column sums and V' images are double-buffered, so each of these exists
+// once per buffer and completes every other strip; an arrival for strip s+2
+// can only happen after the phase of strip s has completed.  The exchange
+// groups work on alternate strips with the buffers of their parity.
 template <int R, int NST>
 __global__ void __launch_bounds__(kFThreads, 1)
     k_fused(const __grid_constant__ CUtensorMap tmap, const FusedArgs a) {
@@ -126,14 +133,12 @@ __global__ void __launch_bounds__(kFThreads, 1)
   // barrier indices
   const int b_full = 0, b_empty = NST, b_vfull = 2 * NST, b_vempty = b_vfull + 2,
             b_d1full = b_vempty + 2, b_d1empty = b_d1full + 2, b_cfull = b_d1empty + 2,
-            b_cempty = b_cfull + 2, b_d2full = b_cempty + 2, b_d2empty = b_d2full + 1,
-            b_g3done = b_d2empty + 1, b_yfull = b_g3done + 1, b_yfree = b_yfull + 1,
-            b_pfull = b_yfree + 1, b_pfree = b_pfull + 1, b_img = b_pfree + 1,
+            b_cempty = b_cfull + 2, b_d2full = b_cempty + 2, b_d2empty = b_d2full + 2,
+            b_g3done = b_d2empty + 2, b_yfull = b_g3done + 2, b_yfree = b_yfull + 2,
+            b_pfull = b_yfree + 2, b_pfree = b_pfull + 2, b_img = b_pfree + 2,
             b_last = b_img + 1;
   float* ypart = reinterpret_cast<float*>(smem + L::YPART);
   float* zm = reinterpret_cast<float*>(smem + L::ZM);
-  float* vslx = reinterpret_cast<float*>(smem + L::VSLX);
-  float* vnl = reinterpret_cast<float*>(smem + L::VNL);
   double* red = reinterpret_cast<double*>(smem + L::RED);
   int err = 0;
 
@@ -148,20 +153,25 @@ __global__ void __launch_bounds__(kFThreads, 1)
       tc::mbar_init(B(b_empty + i), 4);     // the 4 epilogue warps of a row block
     }
     for (int p = 0; p < 2; ++p) {
-      tc::mbar_init(B(b_vfull + p), 2);     // the 2 V-image warps
+      tc::mbar_init(B(b_vfull + p), 1);     // the V-image warp
       tc::mbar_init(B(b_vempty + p), 1);    // GEMM1 commit
       tc::mbar_init(B(b_d1full + p), 1);    // GEMM1 commit
       tc::mbar_init(B(b_d1empty + p), 8);   // the 8 epilogue warps
       tc::mbar_init(B(b_cfull + p), 8);     // the 8 epilogue warps
       tc::mbar_init(B(b_cempty + p), 1);    // GEMM3 commit
     }
-    tc::mbar_init(B(b_d2full), 1);
-    tc::mbar_init(B(b_d2empty), 4);         // the 4 exchange warps
+    for (int p = 0; p < 2; ++p) {
+      tc::mbar_init(B(b_d2full + p), 1);
+      tc::mbar_init(B(b_d2empty + p), 4);   // the 4 exchange warps
+    }
     tc::mbar_init(B(b_g3done), 1);
-    tc::mbar_init(B(b_yfull), cs);
-    tc::mbar_init(B(b_yfree), cs);
-    tc::mbar_init(B(b_pfull), cs);
-    tc::mbar_init(B(b_pfree), cs);
+    tc::mbar_init(B(b_g3done + 1), 1);
+    for (int p = 0; p < 2; ++p) {           // cross-CTA, one per buffer of the pair
+      tc::mbar_init(B(b_yfull + p), cs);
+      tc::mbar_init(B(b_yfree + p), cs);
+      tc::mbar_init(B(b_pfull + p), cs);
+      tc::mbar_init(B(b_pfree + p), cs);
+    }
     tc::mbar_init(B(b_img), 1);
     tc::mbar_init(B(b_last), 1);            // every MMA of the kernel has completed
     tc::fence_mbar_init();
@@ -173,7 +183,8 @@ __global__ void __launch_bounds__(kFThreads, 1)
   tc::fence_after_sync();
   const uint32_t tbase = *reinterpret_cast<volatile uint32_t*>(smem + L::TSLOT);
   auto d1 = [&](int s) { return tbase + 128u * (uint32_t)s; };
-  const uint32_t d2 = tbase + L::T_D2, d3 = tbase + L::T_D3, tu = tbase + L::T_U;
+  auto d2 = [&](int s) { return tbase + (uint32_t)(L::T_D2 + s * R); };
+  const uint32_t d3 = tbase + L::T_D3, tu = tbase + L::T_U;
   const float s_u = a.scales[2 * slab], s_w = a.scales[2 * slab + 1];
   const float s_v = a.scales[2 * a.nslabs];
   const int64_t nstrips = (a.n + kFW - 1) / kFW;
@@ -227,99 +238,115 @@ __global__ void __launch_bounds__(kFThreads, 1)
       }
     }
   } else if (warp == 1) {
-    // ================= MMA issuer ============================================
+    // ================= MMA issuer: GEMM1 and GEMM2 ============================
     if (lane == 0) {
       if (!tc::mbar_wait(B(b_img), 0, kWaitLimit)) err = 1;
       const uint32_t idesc1 = tc::idesc_f16(128, kFW, 0, 0);
-      const uint32_t idesc2 = tc::idesc_f16(64, 2 * R, 1, 0);
-      const uint32_t idesc3 = tc::idesc_f16(128, 2 * R, 0, 0);
-      for (int i = 0; i < S + 2; ++i) {
+      const uint32_t idesc2 = tc::idesc_f16(64, R, 1, 0);
+      // descriptors are built once; moving along K adds (bytes >> 4) to the address field
+      const uint64_t vdesc0 = tc::smem_desc(sbase + L::VIMG, 128, SB_R);
+      const uint64_t cdesc0 = tc::smem_desc(sbase + L::CBUF, 128, kFH * 16);
+      const uint64_t wdesc0 = tc::smem_desc(sbase + L::WIMG, 128, kFH * 16);
+      for (int i = 0; i < S + 1; ++i) {
         if (i < S) {   // GEMM1(i): D1 = U_b V_s^T, terms (hi,hi), (hi,lo), (lo,hi)
           const int p = i & 1;
           if (!tc::mbar_wait(B(b_vfull + p), (uint32_t)((i >> 1) & 1), kWaitLimit)) err = 1;
           if (i >= 2 && !tc::mbar_wait(B(b_d1empty + p), (uint32_t)(((i >> 1) - 1) & 1), kWaitLimit))
             err = 1;
           tc::fence_after_sync();
-          const uint32_t vimg = sbase + L::VIMG + p * L::VBYTES;
+          const uint64_t vd = vdesc0 + (uint64_t)((p * L::VBYTES) >> 4);
 #pragma unroll
           for (int b = 0; b < 2; ++b) {
-            int first = 1;
 #pragma unroll
             for (int t = 0; t < 3; ++t) {
               const int tuu = t == 2 ? 1 : 0, tvv = t == 1 ? 1 : 0;
 #pragma unroll
-              for (int kk = 0; kk < R / 16; ++kk) {
-                const uint64_t bd = tc::smem_desc(vimg + tvv * (kFW * R * 2) + kk * 256, 128, SB_R);
-                tc::mma_ts(d1(p) + b * kFW, tu + (uint32_t)((2 * b + tuu) * (R / 2) + kk * 8), bd,
-                           idesc1, first ? 0u : 1u);
-                first = 0;
-              }
+              for (int kk = 0; kk < R / 16; ++kk)
+                tc::mma_ts(d1(p) + b * kFW, tu + (uint32_t)((2 * b + tuu) * (R / 2) + kk * 8),
+                           vd + (uint64_t)((tvv * (kFW * R * 2) + kk * 256) >> 4), idesc1,
+                           (t > 0 || kk > 0) ? 1u : 0u);
             }
           }
           tc::mma_commit(B(b_d1full + p));
           tc::mma_commit(B(b_vempty + p));
         }
-        if (i >= 1 && i <= S) {   // GEMM2(i-1): Y = C^T [W_hi | W_lo]
+        if (i >= 1) {   // GEMM2(i-1): Y = C^T W_hi + C^T W_lo (same columns)
           const int s2 = i - 1, p = s2 & 1;
           if (!tc::mbar_wait(B(b_cfull + p), (uint32_t)((s2 >> 1) & 1), kWaitLimit)) err = 1;
-          if (s2 >= 1 && !tc::mbar_wait(B(b_d2empty), (uint32_t)((s2 - 1) & 1), kWaitLimit)) err = 1;
+          if (s2 >= 2 &&
+              !tc::mbar_wait(B(b_d2empty + p), (uint32_t)(((s2 >> 1) - 1) & 1), kWaitLimit))
+            err = 1;
           tc::fence_after_sync();
-          const uint32_t cbuf = sbase + L::CBUF + p * L::CBYTES;
+          const uint64_t cd = cdesc0 + (uint64_t)((p * L::CBYTES) >> 4);
 #pragma unroll
-          for (int kk = 0; kk < kFH / 16; ++kk) {
-            const uint64_t ad = tc::smem_desc(cbuf + kk * 256, 128, kFH * 16);
-            const uint64_t bd = tc::smem_desc(sbase + L::WIMG + kk * 256, 128, kFH * 16);
-            tc::mma_ss(d2, ad, bd, idesc2, kk > 0 ? 1u : 0u);
+          for (int t = 0; t < 2; ++t) {
+#pragma unroll
+            for (int kk = 0; kk < kFH / 16; ++kk)
+              tc::mma_ss(d2(p), cd + (uint64_t)((kk * 256) >> 4),
+                         wdesc0 + (uint64_t)((t * (R / 8) * (kFH * 16) + kk * 256) >> 4), idesc2,
+                         (t > 0 || kk > 0) ? 1u : 0u);
           }
-          tc::mma_commit(B(b_d2full));
+          tc::mma_commit(B(b_d2full + p));
         }
-        if (i >= 2) {   // GEMM3(i-2): P_C += C [V'_hi | V'_lo]^T
-          const int s3 = i - 2, p = s3 & 1;
-          if (!tc::mbar_wait_cluster(B(b_pfull), (uint32_t)(s3 & 1), kWaitLimit)) err = 1;
-          tc::fence_proxy_async_smem();
-          tc::fence_after_sync();
-          const uint32_t cbuf = sbase + L::CBUF + p * L::CBYTES;
+      }
+    }
+  } else if (warp == 2) {
+    // ================= MMA issuer: GEMM3 =======================================
+    if (lane == 0) {
+      const uint32_t idesc3 = tc::idesc_f16(128, R, 0, 0);
+      const uint64_t cdesc0 = tc::smem_desc(sbase + L::CBUF, kFH * 16, 128);
+      const uint64_t pdesc0 = tc::smem_desc(sbase + L::PIMG, 128, (kFW / 8) * 128);
+      for (int s3 = 0; s3 < S; ++s3) {   // P_C += C V'_hi^T + C V'_lo^T
+        const int p = s3 & 1;
+        if (!tc::mbar_wait_cluster(B(b_pfull + p), (uint32_t)((s3 >> 1) & 1), kWaitLimit)) err = 1;
+        tc::fence_proxy_async_smem();
+        tc::fence_after_sync();
+        const uint64_t cd = cdesc0 + (uint64_t)((p * L::CBYTES) >> 4);
+        const uint64_t pd = pdesc0 + (uint64_t)((p * L::PBYTES) >> 4);
 #pragma unroll
-          for (int b = 0; b < 2; ++b) {
+        for (int b = 0; b < 2; ++b) {
 #pragma unroll
-            for (int kk = 0; kk < kFW / 16; ++kk) {
-              const uint64_t ad = tc::smem_desc(cbuf + b * 2048 + kk * 2 * (kFH * 16), kFH * 16, 128);
-              const uint64_t bd = tc::smem_desc(sbase + L::PIMG + kk * 256, 128, (kFW / 8) * 128);
-              tc::mma_ss(d3 + b * 2 * R, ad, bd, idesc3, (s3 > 0 || kk > 0) ? 1u : 0u);
-            }
+          for (int t = 0; t < 2; ++t) {   // V'_hi then V'_lo into the same columns
+#pragma unroll
+            for (int kk = 0; kk < kFW / 16; ++kk)
+              tc::mma_ss(d3 + b * R, cd + (uint64_t)((b * 2048 + kk * 2 * (kFH * 16)) >> 4),
+                         pd + (uint64_t)((t * (R / 8) * (kFW / 8) * 128 + kk * 256) >> 4), idesc3,
+                         (s3 > 0 || t > 0 || kk > 0) ? 1u : 0u);
           }
-          tc::mma_commit(B(b_cempty + p));
-          tc::mma_commit(B(b_g3done));
         }
+        tc::mma_commit(B(b_cempty + p));
+        tc::mma_commit(B(b_g3done + p));
       }
       // A parity wait only tells the current phase from the previous one, so the
       // final read-out waits on a barrier of its own rather than on g3done.
       tc::mma_commit(B(b_last));
     }
-  } else if (warp < 4) {
-    // ================= V images (64 threads), two strips ahead ================
-    const int vt = tid - 64;
-    constexpr int VPT = kFW * R / 64;
+  } else if (warp == 3) {
+    // ================= V images (one warp), two strips ahead ===================
+    constexpr int VPT = kFW * R / 32;
     for (int ls = 0; ls < S; ++ls) {
       const int p = ls & 1;
       const int64_t col0 = strip_col0(ls);
-      float vr[VPT];
-#pragma unroll
-      for (int i = 0; i < VPT; ++i) {
-        const int idx = vt + 64 * i, j = idx / R, k = idx % R;
-        vr[i] = col0 + j < a.n ? a.Vold[(col0 + j) * R + k] : 0.f;
-      }
       if (ls >= 2 && !tc::mbar_wait(B(b_vempty + p), (uint32_t)(((ls >> 1) - 1) & 1), kWaitLimit))
         err = 1;
       uint8_t* img = smem + L::VIMG + p * L::VBYTES;
 #pragma unroll
-      for (int i = 0; i < VPT; ++i) {
-        const int idx = vt + 64 * i, j = idx / R, k = idx % R;
-        __half hi, lo;
-        split_h(vr[i], s_v, hi, lo);
-        const int off = (j >> 3) * SB_R + (k >> 3) * 128 + (j & 7) * 16 + (k & 7) * 2;
-        *reinterpret_cast<__half*>(img + off) = hi;
-        *reinterpret_cast<__half*>(img + kFW * R * 2 + off) = lo;
+      for (int c0 = 0; c0 < VPT; c0 += 16) {
+        float vr[16];
+#pragma unroll
+        for (int i = 0; i < 16; ++i) {
+          const int idx = lane + 32 * (c0 + i), j = idx / R, k = idx % R;
+          vr[i] = col0 + j < a.n ? a.Vold[(col0 + j) * R + k] : 0.f;
+        }
+#pragma unroll
+        for (int i = 0; i < 16; ++i) {
+          const int idx = lane + 32 * (c0 + i), j = idx / R, k = idx % R;
+          __half hi, lo;
+          split_h(vr[i], s_v, hi, lo);
+          const int off = (j >> 3) * SB_R + (k >> 3) * 128 + (j & 7) * 16 + (k & 7) * 2;
+          *reinterpret_cast<__half*>(img + off) = hi;
+          *reinterpret_cast<__half*>(img + kFW * R * 2 + off) = lo;
+        }
       }
       tc::fence_proxy_async_smem();
       __syncwarp();
@@ -341,42 +368,44 @@ __global__ void __launch_bounds__(kFThreads, 1)
       tc::fence_after_sync();
       uint8_t* cbuf = smem + L::CBUF + p * L::CBYTES;
       float hub = 0.f;
-#pragma unroll
+#pragma unroll 1
       for (int q = 0; q < 2; ++q) {
         const int g = ls * 4 + rb * 2 + q;
         const int rs = g % NST;
-        float dv[32];
-        const uint32_t ta = d1(p) + ((uint32_t)(quarter * 32) << 16) + rb * kFW + q * 32;
-        tc::tmem_ld16(ta, dv);
-        tc::tmem_ld16(ta + 16, dv + 16);
         if (!tc::mbar_wait(B(b_full + rs), (uint32_t)((g / NST) & 1), kWaitLimit)) err = 1;
         const float* msub = reinterpret_cast<const float*>(smem + L::RING + rs * kSubBytes);
-        float mv[32];
 #pragma unroll
-        for (int jj = 0; jj < 32; ++jj) mv[jj] = msub[jj * 128 + al];
-        tc::tmem_ld_wait();
-        __syncwarp();
-        if (lane == 0) tc::mbar_arrive(B(b_empty + rs));
-        uint32_t packed[16];
+        for (int h = 0; h < 2; ++h) {   // 16 columns at a time
+          float dv[16], mv[16];
+          tc::tmem_ld16(d1(p) + ((uint32_t)(quarter * 32) << 16) + rb * kFW + q * 32 + h * 16, dv);
 #pragma unroll
-        for (int jj = 0; jj < 32; jj += 2) {
-          float c2[2];
-#pragma unroll
-          for (int u = 0; u < 2; ++u) {
-            const float rn = (mv[jj + u] - dv[jj + u] * inv_uv) * inv_lam;   // R / lambda
-            const float c = fminf(fmaxf(rn, -1.f), 1.f);                     // C / lambda
-            hub = fmaf(c, rn - 0.5f * c, hub);                               // H(R) / lambda^2
-            c2[u] = c;
+          for (int jj = 0; jj < 16; ++jj) mv[jj] = msub[(h * 16 + jj) * 128 + al];
+          tc::tmem_ld_wait();
+          if (h == 1) {
+            __syncwarp();
+            if (lane == 0) tc::mbar_arrive(B(b_empty + rs));
           }
-          __half2 h2 = __floats2half2_rn(c2[0], c2[1]);
-          packed[jj / 2] = *reinterpret_cast<uint32_t*>(&h2);
-        }
+          uint32_t packed[8];
 #pragma unroll
-        for (int ch = 0; ch < 4; ++ch) {
-          const int j8 = (q * 32 + ch * 8) >> 3;
-          const int off = j8 * (kFH * 16) + (arow >> 3) * 128 + (arow & 7) * 16;
-          *reinterpret_cast<uint4*>(cbuf + off) =
-              make_uint4(packed[4 * ch], packed[4 * ch + 1], packed[4 * ch + 2], packed[4 * ch + 3]);
+          for (int jj = 0; jj < 16; jj += 2) {
+            float c2[2];
+#pragma unroll
+            for (int u = 0; u < 2; ++u) {
+              const float rn = (mv[jj + u] - dv[jj + u] * inv_uv) * inv_lam;   // R / lambda
+              const float c = fminf(fmaxf(rn, -1.f), 1.f);                     // C / lambda
+              hub = fmaf(c, rn - 0.5f * c, hub);                               // H(R) / lambda^2
+              c2[u] = c;
+            }
+            __half2 h2 = __floats2half2_rn(c2[0], c2[1]);
+            packed[jj / 2] = *reinterpret_cast<uint32_t*>(&h2);
+          }
+#pragma unroll
+          for (int ch = 0; ch < 2; ++ch) {
+            const int j8 = (q * 32 + h * 16 + ch * 8) >> 3;
+            const int off = j8 * (kFH * 16) + (arow >> 3) * 128 + (arow & 7) * 16;
+            *reinterpret_cast<uint4*>(cbuf + off) =
+                make_uint4(packed[4 * ch], packed[4 * ch + 1], packed[4 * ch + 2], packed[4 * ch + 3]);
+          }
         }
       }
       tsum(hub_hi, hub_lo, hub);
@@ -393,156 +422,119 @@ __global__ void __launch_bounds__(kFThreads, 1)
     tc::fence_after_sync();
     {
       const int64_t grow = row0 + arow;
-      float pv[2 * R];
+      float pv[R];
 #pragma unroll
-      for (int c = 0; c < 2 * R; c += 16)
-        tc::tmem_ld16(d3 + ((uint32_t)(quarter * 32) << 16) + rb * 2 * R + c, pv + c);
+      for (int c = 0; c < R; c += 16)
+        tc::tmem_ld16(d3 + ((uint32_t)(quarter * 32) << 16) + rb * R + c, pv + c);
       tc::tmem_ld_wait();
       if (grow < a.m) {
         const float ps = a.lam / s_v;
         float* out = a.part_p + ((int64_t)cid * a.m + grow) * R;
 #pragma unroll
-        for (int k = 0; k < R; ++k) out[k] = S > 0 ? (pv[k] + pv[R + k]) * ps : 0.f;
+        for (int k = 0; k < R; ++k) out[k] = S > 0 ? pv[k] * ps : 0.f;
       }
     }
     double hsum = ((double)hub_hi + (double)hub_lo) * (double)a.lam * (double)a.lam;
     for (int o = 16; o > 0; o >>= 1) hsum += __shfl_xor_sync(0xffffffffu, hsum, o);
     if (lane == 0) red[warp - 4] = hsum;
   } else {
-    // ================= exchange (128 threads) =================================
-    const int xt = tid - 384;            // 0..127
-    const int xw = warp - 12;            // == TMEM lane quarter
+    // ================= exchange: two groups of 128 threads =====================
+    const int grp = (warp - 12) >> 2;    // 0: even strips, 1: odd strips
+    const int xt = tid - 384 - 128 * grp;
+    const int xw = warp & 3;             // == TMEM lane quarter
+    const int nb = 1 + grp;              // named barrier of the group
+    const int p = grp;                   // every strip of the group uses buffers [p]
     const float y_scale = a.lam / s_w;
-    constexpr int NE = R * R / 128;      // Q / X_v entries per thread
-    float q_hi[NE], q_lo[NE], x_hi[NE], x_lo[NE];
-#pragma unroll
-    for (int i = 0; i < NE; ++i) { q_hi[i] = q_lo[i] = x_hi[i] = x_lo[i] = 0.f; }
     float vmax = 0.f;
-    constexpr int XPT = kFW * R / 128;   // V_s rows of all chunks, entries per thread (max)
-    for (int ls = 0; ls < S; ++ls) {
-      const int64_t col0 = strip_col0(ls);
-      // V_s rows of this CTA's chunks (global loads overlap the waits below)
-      float sr[XPT];
-#pragma unroll
-      for (int i = 0; i < XPT; ++i) {
-        const int e = xt + 128 * i;
-        float v = 0.f;
-        if (e < nch * kChunk * R) {
-          const int ci = e / (kChunk * R), jl = (e / R) % kChunk, k = e % R;
-          const int64_t col = col0 + ((int)crank + ci * cs) * kChunk + jl;
-          if (col < a.n) v = a.Vold[col * R + k];
-        }
-        sr[i] = v;
-      }
+    const bool act = xt < kChunk * R;
+    const int jl = xt / R, kx = xt % R;
+    auto vz_of = [&](int ls, int ci) {
+      const int64_t col = strip_col0(ls) + ((int)crank + ci * cs) * kChunk + jl;
+      return (act && col < a.n) ? a.VZ[col * R + kx] : 0.f;
+    };
+    const uint32_t ybase = sbase + L::YPART + p * L::YBYTES;
+    const uint32_t pbase = sbase + L::PIMG + p * L::PBYTES;
+    float vz_next = grp < S ? vz_of(grp, 0) : 0.f;
+    for (int ls = grp; ls < S; ls += 2) {
+      const uint32_t par = (uint32_t)((ls >> 1) & 1);
+      const float vz_first = vz_next;
+      if (ls + 2 < S) vz_next = vz_of(ls + 2, 0);   // in flight for a whole strip pair
       // ---- column sums of this CTA's rows out of tensor memory ----
-      if (!tc::mbar_wait(B(b_d2full), (uint32_t)(ls & 1), kWaitLimit)) err = 1;
+      if (!tc::mbar_wait(B(b_d2full + p), par, kWaitLimit)) err = 1;
       tc::fence_after_sync();
-      float yv[2 * R];
+      float yv[R];
 #pragma unroll
-      for (int c = 0; c < 2 * R; c += 16)
-        tc::tmem_ld16(d2 + ((uint32_t)(xw * 32) << 16) + c, yv + c);
+      for (int c = 0; c < R; c += 16)
+        tc::tmem_ld16(d2(p) + ((uint32_t)(xw * 32) << 16) + c, yv + c);
       tc::tmem_ld_wait();
       tc::fence_before_sync();
       __syncwarp();
-      if (lane == 0) tc::mbar_arrive(B(b_d2empty));
-      if (ls >= 1 && !tc::mbar_wait_cluster(B(b_yfree), (uint32_t)((ls - 1) & 1), kWaitLimit))
-        err = 1;
+      if (lane == 0) tc::mbar_arrive(B(b_d2empty + p));
+      if (ls >= 2 && !tc::mbar_wait_cluster(B(b_yfree + p), par ^ 1u, kWaitLimit)) err = 1;
       if (lane < 16) {
+        float* yp = ypart + p * (kFW * R);
         const int j = xw * 16 + lane;
 #pragma unroll
-        for (int k = 0; k < R; ++k) ypart[j * R + k] = (yv[k] + yv[R + k]) * y_scale;
+        for (int k = 0; k < R; ++k) yp[j * R + k] = yv[k] * y_scale;
       }
-#pragma unroll
-      for (int i = 0; i < XPT; ++i) {
-        const int e = xt + 128 * i;
-        if (e < nch * kChunk * R) vslx[e] = sr[i];
+      // bar.sync orders the writes of the group before the arriving threads,
+      // whose arrive.release.cluster publishes them to the cluster
+      tc::named_bar(nb, 128);
+      if (xt < cs) tc::mbar_arrive_cluster(B(b_yfull + p), (uint32_t)xt);
+      // ---- GEMM3 of strip ls-2 done here: its V' image buffer may be refilled ----
+      if (ls >= 2 && xw == 0) {
+        if (!tc::mbar_wait(B(b_g3done + p), par ^ 1u, kWaitLimit)) err = 1;
+        if (lane < cs) tc::mbar_arrive_cluster_relaxed(B(b_pfree + p), (uint32_t)lane);
       }
-      tc::fence_acq_rel_cluster();
-      tc::named_bar(1, 128);
-      if (xt < cs) tc::mbar_arrive_cluster(B(b_yfull), (uint32_t)xt);
-      // ---- GEMM3 of the previous strip done here: tell every reducer ----
-      if (ls >= 1) {
-        if (xw == 0) {
-          if (!tc::mbar_wait(B(b_g3done), (uint32_t)((ls - 1) & 1), kWaitLimit)) err = 1;
-          if (lane < cs) tc::mbar_arrive_cluster(B(b_pfree), (uint32_t)lane);
-        }
-      }
-      // ---- reduce-scatter: sums of this CTA's chunks over the cluster ----
-      if (!tc::mbar_wait_cluster(B(b_yfull), (uint32_t)(ls & 1), kWaitLimit)) err = 1;
+      // ---- reduce-scatter of strip ls ----
+      const int64_t col0 = strip_col0(ls);
+      if (!tc::mbar_wait_cluster(B(b_yfull + p), par, kWaitLimit)) err = 1;
       for (int ci = 0; ci < nch; ++ci) {
         const int cc = (int)crank + ci * cs;
-        const bool act = xt < kChunk * R;
-        const int jl = xt / R, k = xt % R;
-        float y = 0.f;
+        float y = ci == 0 ? vz_first : vz_of(ls, ci);
         if (act) {
           const int j = cc * kChunk + jl;
-          const uint32_t yaddr = sbase + L::YPART + (uint32_t)(j * R + k) * 4;
-          float yp[16];
+          const uint32_t yaddr = ybase + (uint32_t)(j * R + kx) * 4;
+          float ypv[16];
 #pragma unroll
           for (int p2 = 0; p2 < 16; ++p2)
-            yp[p2] = p2 < cs ? tc::ld_cluster_f32_relaxed(tc::map_cluster(yaddr, p2)) : 0.f;
+            ypv[p2] = p2 < cs ? tc::ld_cluster_f32_relaxed(tc::map_cluster(yaddr, p2)) : 0.f;
 #pragma unroll
-          for (int p2 = 0; p2 < 16; ++p2) y += yp[p2];
+          for (int p2 = 0; p2 < 16; ++p2) y += ypv[p2];
         }
         if (ci == nch - 1) {
-          // every remote read of this strip is done: release the column-sum buffers
-          tc::fence_acq_rel_cluster();
-          tc::named_bar(1, 128);
-          if (xt < cs) tc::mbar_arrive_cluster(B(b_yfree), (uint32_t)xt);
+          // every remote read of this strip is done (the values are in registers)
+          tc::named_bar(nb, 128);
+          if (xt < cs) tc::mbar_arrive_cluster_relaxed(B(b_yfree + p), (uint32_t)xt);
         }
         if (act) {
           const int64_t col = col0 + cc * kChunk + jl;
-          const float* vs = vslx + (ci * kChunk + jl) * R;
-#pragma unroll 8
-          for (int l = 0; l < R; ++l) y = fmaf(vs[l], zm[l * R + k], y);
           const float v = col < a.n ? y : 0.f;
-          if (col < a.n) a.Vnew[col * R + k] = v;
-          vnl[jl * R + k] = v;
+          if (col < a.n) a.Vnew[col * R + kx] = v;
           vmax = fmaxf(vmax, fabsf(v));
           __half hi, lo;
           split_h(v, s_v, hi, lo);
           // chunk image: entry (n, jl) at n*8 + jl*2, n = k (hi) or R + k (lo)
-          *reinterpret_cast<__half*>(smem + L::STG + k * 8 + jl * 2) = hi;
-          *reinterpret_cast<__half*>(smem + L::STG + (R + k) * 8 + jl * 2) = lo;
+          uint8_t* stg = smem + L::STG + grp * (2 * R * kChunk * 2);
+          *reinterpret_cast<__half*>(stg + kx * 8 + jl * 2) = hi;
+          *reinterpret_cast<__half*>(stg + (R + kx) * 8 + jl * 2) = lo;
         }
-        tc::named_bar(1, 128);
-        // Q_t and V_{t-1}^T V_t contributions of the chunk's columns
-#pragma unroll
-        for (int i = 0; i < NE; ++i) {
-          const int e = xt + 128 * i;
-          const int k1 = e / R, k2 = e % R;
-          float qa = 0.f, xa = 0.f;
-#pragma unroll
-          for (int jj = 0; jj < kChunk; ++jj) {
-            qa = fmaf(vnl[jj * R + k1], vnl[jj * R + k2], qa);
-            xa = fmaf(vslx[(ci * kChunk + jj) * R + k1], vnl[jj * R + k2], xa);
-          }
-          tsum(q_hi[i], q_lo[i], qa);
-          tsum(x_hi[i], x_lo[i], xa);
-        }
-        // all-gather of the chunk's V' image into every CTA (after their GEMM3 of ls-1)
-        if (ci == 0 && ls >= 1 &&
-            !tc::mbar_wait_cluster(B(b_pfree), (uint32_t)((ls - 1) & 1), kWaitLimit))
+        // all-gather of the chunk's V' image into every CTA (after their GEMM3 of ls-2)
+        if (ci == 0 && ls >= 2 && !tc::mbar_wait_cluster(B(b_pfree + p), par ^ 1u, kWaitLimit))
           err = 1;
+        tc::named_bar(nb, 128);
+        const uint8_t* stg = smem + L::STG + grp * (2 * R * kChunk * 2);
         for (int idx = xt; idx < cs * 2 * R; idx += 128) {
           const int p2 = idx / (2 * R), nn = idx % (2 * R);
-          const uint2 v = *reinterpret_cast<const uint2*>(smem + L::STG + nn * 8);
-          const uint32_t dst = sbase + L::PIMG + (nn >> 3) * (kFW / 8) * 128 + (cc >> 1) * 128 +
+          const uint2 v = *reinterpret_cast<const uint2*>(stg + nn * 8);
+          const uint32_t dst = pbase + (nn >> 3) * (kFW / 8) * 128 + (cc >> 1) * 128 +
                                (nn & 7) * 16 + (cc & 1) * 8;
           tc::st_cluster_u32x2(tc::map_cluster(dst, p2), v.x, v.y);
         }
         tc::fence_proxy_async_cluster();
-        tc::fence_acq_rel_cluster();
-        tc::named_bar(1, 128);   // STG and VNL reused by the next chunk
+        tc::named_bar(nb, 128);   // the staging chunk is reused by the next chunk
       }
-      if (xt < cs) tc::mbar_arrive_cluster(B(b_pfull), (uint32_t)xt);
-    }
-    // per-CTA partials
-#pragma unroll
-    for (int i = 0; i < NE; ++i) {
-      const int e = xt + 128 * i;
-      a.part_q[(int64_t)blockIdx.x * R * R + e] = (double)q_hi[i] + (double)q_lo[i];
-      a.part_xv[(int64_t)blockIdx.x * R * R + e] = (double)x_hi[i] + (double)x_lo[i];
+      if (xt < cs) tc::mbar_arrive_cluster(B(b_pfull + p), (uint32_t)xt);
     }
     for (int o = 16; o > 0; o >>= 1) vmax = fmaxf(vmax, __shfl_xor_sync(0xffffffffu, vmax, o));
     if (lane == 0 && vmax > 0.f) atomicMax(a.vmax_out, __float_as_uint(vmax));
@@ -650,6 +642,41 @@ __global__ void __launch_bounds__(256) k_fused_prep(const float* __restrict__ U,
   }
 }
 
+// out = in Z for n rows of R (V_old Z, added to the cluster's column sums)
+template <int R>
+__global__ void __launch_bounds__(256) k_rowmat(const float* __restrict__ in,
+                                                const float* __restrict__ zmat, int64_t n,
+                                                float* __restrict__ out, const DevState* st) {
+  if (st->stop) return;
+  __shared__ float Z[R * R];
+  for (int i = threadIdx.x; i < R * R; i += 256) Z[i] = zmat[i];
+  __syncthreads();
+  const int64_t idx = (int64_t)blockIdx.x * 256 + threadIdx.x;   // (row, column group of 8)
+  const int64_t row = idx / (R / 8);
+  const int cg = (int)(idx % (R / 8));
+  if (row >= n) return;
+  const float* v = in + row * R;
+  float acc[8];
+#pragma unroll
+  for (int l = 0; l < 8; ++l) acc[l] = 0.f;
+  for (int k = 0; k < R; ++k) {
+    const float x = v[k];
+#pragma unroll
+    for (int l = 0; l < 8; ++l) acc[l] = fmaf(x, Z[k * R + cg * 8 + l], acc[l]);
+  }
+#pragma unroll
+  for (int l = 0; l < 8; ++l) out[row * R + cg * 8 + l] = acc[l];
+}
+
+cudaError_t launch_rowmat(int R, const float* in, const float* zmat, int64_t n, float* out,
+                          const DevState* st, cudaStream_t s) {
+  const int64_t items = n * (R / 8);
+  const unsigned grid = (unsigned)((items + 255) / 256);
+  if (R == 16) k_rowmat<16><<<grid, 256, 0, s>>>(in, zmat, n, out, st);
+  else k_rowmat<32><<<grid, 256, 0, s>>>(in, zmat, n, out, st);
+  return cudaGetLastError();
+}
+
 __global__ void k_absmax(const float* x, int64_t count, unsigned int* out) {
   float mx = 0.f;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count;
@@ -662,7 +689,7 @@ __global__ void k_absmax(const float* x, int64_t count, unsigned int* out) {
 // ---------------------------------------------------------------------------
 // host side
 // ---------------------------------------------------------------------------
-constexpr int kNST32 = 5;
+constexpr int kNST32 = 4;
 constexpr int kNST16 = 7;
 
 template <int R, int NST>

@@ -147,6 +147,14 @@ __device__ __forceinline__ void mbar_arrive_cluster(uint32_t mbar, uint32_t rank
       "r"(rank)
       : "memory");
 }
+// Arrival that publishes no data (only "done with your buffer"): no release fence.
+__device__ __forceinline__ void mbar_arrive_cluster_relaxed(uint32_t mbar, uint32_t rank) {
+  asm volatile(
+      "{\n\t.reg .b32 ra;\n\tmapa.shared::cluster.u32 ra, %0, %1;\n\t"
+      "mbarrier.arrive.relaxed.cluster.shared::cluster.b64 _, [ra];\n\t}" ::"r"(mbar),
+      "r"(rank)
+      : "memory");
+}
 __device__ __forceinline__ uint32_t mbar_try_wait(uint32_t mbar, uint32_t parity) {
   uint32_t ok;
   asm volatile(

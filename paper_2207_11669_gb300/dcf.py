@@ -64,6 +64,13 @@ _SIGS = {
     "dcf_profile_phases": (C.c_int, [C.c_void_p, C.c_char_p, C.c_int]),
     "dcf_profile_step": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_double)]),
     "dcf_tc_selftest": (C.c_int, [C.POINTER(C.c_int), C.POINTER(C.c_float)]),
+    "dcf_unrolled_forward": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_double),
+                                       C.POINTER(C.c_double), C.POINTER(C.c_double),
+                                       C.POINTER(C.c_double), C.POINTER(C.c_double),
+                                       C.POINTER(C.c_double)]),
+    "dcf_unrolled_backward": (C.c_int, [C.c_void_p, C.POINTER(C.c_double),
+                                        C.POINTER(C.c_double), C.POINTER(C.c_double),
+                                        C.c_void_p, C.POINTER(C.c_void_p), C.c_int]),
     "dcf_iterate_noalloc": (C.c_int, [C.c_void_p, C.c_int64, C.c_int64, C.c_int, C.c_double,
                                       C.c_double, C.c_void_p, C.c_void_p, C.c_void_p,
                                       C.c_void_p, C.c_void_p]),
@@ -284,6 +291,44 @@ def dcf_iterate_noalloc(M, m, n, r, rho, lam, U_in, V_in, U_out, V_out, stream=0
                                      C.c_void_p(stream))
 
 
+def _dvec(x, K):
+    if x is None:
+        return None
+    a = np.ascontiguousarray(np.asarray(x, dtype=np.float64).reshape(-1))
+    if a.size != K:
+        raise ValueError(f"expected {K} values, got {a.size}")
+    return a
+
+
+def dcf_unrolled_forward(h, a, b, c, weights=None, want_loss=True):
+    """Forward pass of the learned network; returns (total_loss, per-step losses)
+    or (None, None) when want_loss is False."""
+    K = len(a)
+    av, bv, cv = _dvec(a, K), _dvec(b, K), _dvec(c, K)
+    wv = _dvec(weights, K)
+    dp = lambda v: None if v is None else v.ctypes.data_as(C.POINTER(C.c_double))
+    terms = np.zeros(K) if want_loss else None
+    tot = C.c_double()
+    _check(h, lib().dcf_unrolled_forward(h, int(K), dp(av), dp(bv), dp(cv), dp(wv), dp(terms),
+                                         C.byref(tot) if want_loss else None))
+    return (tot.value, terms) if want_loss else (None, None)
+
+
+def dcf_unrolled_backward(h, K, grad_U0=None, grad_V0_blocks=None):
+    """Reverse pass of the last forward: returns (grad_a, grad_b, grad_c); the
+    start-point gradients go into grad_U0 / grad_V0_blocks when given."""
+    ga, gb, gc = np.zeros(K), np.zeros(K), np.zeros(K)
+    dp = lambda v: v.ctypes.data_as(C.POINTER(C.c_double))
+    pu, where = _ptr_where(grad_U0)
+    varr = None
+    if grad_V0_blocks is not None:
+        vp = [_ptr_where(v)[0].value for v in grad_V0_blocks]
+        where = _ptr_where(grad_V0_blocks[0])[1]
+        varr = (C.c_void_p * len(vp))(*vp)
+    _check(h, lib().dcf_unrolled_backward(h, dp(ga), dp(gb), dp(gc), pu, varr, where))
+    return ga, gb, gc
+
+
 def dcf_version():
     return lib().dcf_version().decode()
 
@@ -380,3 +425,15 @@ class Solver:
 
     def rel_err(self):
         return dcf_rel_err(self.h)
+
+    def unrolled_forward(self, a, b, c, weights=None, want_loss=True):
+        return dcf_unrolled_forward(self.h, a, b, c, weights, want_loss)
+
+    def unrolled_backward(self, K, start_grads=False):
+        """(grad_a, grad_b, grad_c), plus (grad_U0, grad_V0) when start_grads."""
+        if not start_grads:
+            return dcf_unrolled_backward(self.h, K)
+        gU = np.empty((self.m, self.r), np.float32)
+        gVs = [np.empty((ni, self.r), np.float32) for ni in self.n_i]
+        g = dcf_unrolled_backward(self.h, K, gU, gVs)
+        return g + (gU, np.concatenate(gVs, axis=0))
