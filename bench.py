@@ -123,7 +123,7 @@ def alg_bytes_per_iter(m, n, r):
 # from an ncu capture of the kernel as it is now (profiles/k_fused_r32_m4096_n16384.md).
 # The capture ran a smaller n; traffic grows in proportion to n (M is streamed
 # once, V read and written), so it is scaled by n.  None for other shapes.
-NCU_TRAFFIC = {"fused_step": {"m": 4096, "r": 32, "n": 16384, "bytes": 273.886720e6 + 4.625664e6}}
+NCU_TRAFFIC = {}   # no capture of the current kernels yet
 
 
 def ncu_traffic(kernel, m, n, r):

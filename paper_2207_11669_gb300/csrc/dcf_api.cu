@@ -18,26 +18,6 @@
 #include "dcf_handle.h"
 #include "dcf_internal.cuh"
 
-namespace dcf {
-cudaError_t launch_gram(const float* X, int ldx, int cx, const float* Y, int ldy, int cy,
-                        int64_t N, double* part, int nparts, const DevState* st,
-                        int respect_stop, cudaStream_t s);
-cudaError_t launch_make_w(const IterArgs& a, int copy, int respect_stop, cudaStream_t s);
-cudaError_t prepare_small_kernels();
-cudaError_t launch_rows(const IterArgs& a, cudaStream_t s);
-cudaError_t launch_reduce_q(const IterArgs& a, double* out_q, double* out_xv, double* out_h,
-                            int nparts_gram, unsigned int* counter, cudaStream_t s);
-cudaError_t launch_reduce_g(const IterArgs& a, double* out_g, double* out_xu,
-                            unsigned int* counter, cudaStream_t s);
-cudaError_t launch_reduce_init(const IterArgs& a, int which, int copy, const double* part,
-                               int nparts, double* out, unsigned int* counter, cudaStream_t s);
-cudaError_t launch_reduce_plain(const double* part, int nparts, int count, double* out,
-                                cudaStream_t s);
-cudaError_t launch_pass1(const IterArgs& a, int grid, int mode_init, int out_copy,
-                         cudaStream_t s);
-cudaError_t launch_pass2(const IterArgs& a, cudaStream_t s);
-cudaError_t prepare_stream_kernels();
-}  // namespace dcf
 
 using namespace dcf;
 using namespace dcf::api;
@@ -189,11 +169,9 @@ cudaError_t enqueue_fused_iteration(dcf_handle h, int cur, cudaStream_t s, cudaE
   if ((e = launch_fused(h->R, h->tmap, fa, s)) != cudaSuccess || (e = mark()) != cudaSuccess)
     return e;
   // Q_t = V_t^T V_t and V_{t-1}^T V_t from the new V (Gram partials)
-  if ((e = launch_gram(h->V[nxt], h->R, h->R, h->V[nxt], h->R, h->R, h->n, h->part_q,
-                       h->n_vgram, h->st, 1, s)) != cudaSuccess)
-    return e;
-  if ((e = launch_gram(h->V[cur], h->R, h->R, h->V[nxt], h->R, h->R, h->n, h->part_xv,
-                       h->n_vgram, h->st, 1, s)) != cudaSuccess || (e = mark()) != cudaSuccess)
+  if ((e = launch_gram_vv(h->R, h->V[cur], h->V[nxt], h->n, h->part_q, h->part_xv, h->n_vgram,
+                          h->st, s)) != cudaSuccess ||
+      (e = mark()) != cudaSuccess)
     return e;
   if ((e = launch_reduce_q(a, red_q(h), red_xv(h), red_h(h), h->n_vgram, h->counters + 0, s)) !=
           cudaSuccess ||
@@ -223,11 +201,9 @@ cudaError_t enqueue_iteration(dcf_handle h, int cur, cudaStream_t s, cudaEvent_t
   // U-step numerator P = X V' (second pass over M)
   if ((e = launch_pass2(a, s)) != cudaSuccess || (e = mark()) != cudaSuccess) return e;
   // Q_t = V_t^T V_t and V_{t-1}^T V_t
-  if ((e = launch_gram(h->V[nxt], h->R, h->R, h->V[nxt], h->R, h->R, h->n, h->part_q,
-                       h->n_vgram, h->st, 1, s)) != cudaSuccess)
-    return e;
-  if ((e = launch_gram(h->V[cur], h->R, h->R, h->V[nxt], h->R, h->R, h->n, h->part_xv,
-                       h->n_vgram, h->st, 1, s)) != cudaSuccess || (e = mark()) != cudaSuccess)
+  if ((e = launch_gram_vv(h->R, h->V[cur], h->V[nxt], h->n, h->part_q, h->part_xv, h->n_vgram,
+                          h->st, s)) != cudaSuccess ||
+      (e = mark()) != cudaSuccess)
     return e;
   if ((e = launch_reduce_q(a, red_q(h), red_xv(h), red_h(h), h->n_vgram, h->counters + 0, s)) !=
           cudaSuccess ||
@@ -464,10 +440,10 @@ extern "C" dcf_status dcf_create(const dcf_params* p, dcf_handle* out) {
   h->part_p = (float*)A((size_t)h->n_splits * h->m * R * 4);
   h->part_h = (double*)A((size_t)h->n_vblocks * 8);
   size_t ngp = std::max<size_t>(h->n_vgram, h->n_rblocks);
-  h->part_q = (double*)A(ngp * RR * 8);
-  h->part_xv = (double*)A((size_t)h->n_vgram * RR * 8);
-  h->part_g = (double*)A(ngp * RR * 8);
-  h->part_xu = (double*)A((size_t)h->n_rblocks * RR * 8);
+  h->part_q = (float2*)A(ngp * RR * 8);
+  h->part_xv = (float2*)A((size_t)h->n_vgram * RR * 8);
+  h->part_g = (float2*)A(ngp * RR * 8);
+  h->part_xu = (float2*)A((size_t)h->n_rblocks * RR * 8);
   h->red = (double*)A((4 * RR + 8) * 8);
   h->sm = (Smalls*)A(sizeof(Smalls));
   h->st = (DevState*)A(sizeof(DevState));
@@ -719,7 +695,7 @@ extern "C" dcf_status dcf_set_truth(dcf_handle h, const float* A, const float* B
   if (!h->A_truth || h->k_truth != k) {
     h->A_truth = (float*)dev_alloc(h, (size_t)h->m * k * 4);
     h->B_truth = (float*)dev_alloc(h, (size_t)h->n * k * 4);
-    h->truth_part = (double*)dev_alloc(h, (size_t)2 * h->num_sms * kMaxR * kMaxR * 8);
+    h->truth_part = (float2*)dev_alloc(h, (size_t)2 * h->num_sms * kMaxR * kMaxR * 8);
     h->truth_red = (double*)dev_alloc(h, (size_t)6 * kMaxR * kMaxR * 8);
     if (!h->A_truth || !h->B_truth || !h->truth_part || !h->truth_red)
       return fail(h, DCF_ENOMEM, "truth buffers");

@@ -37,12 +37,12 @@ struct dcf_handle_s {
   float* W = nullptr;
   float* part_p = nullptr;
   double* part_h = nullptr;
-  double* part_q = nullptr;
-  double* part_xv = nullptr;
-  double* part_g = nullptr;
-  double* part_xu = nullptr;
+  float2* part_q = nullptr;
+  float2* part_xv = nullptr;
+  float2* part_g = nullptr;
+  float2* part_xu = nullptr;
   double* red = nullptr;             // reduction outputs: q, xv, h, g, xu (R*R each)
-  double* truth_part = nullptr;
+  float2* truth_part = nullptr;
   double* truth_red = nullptr;
   dcf::Smalls* sm = nullptr;
   dcf::DevState* st = nullptr;

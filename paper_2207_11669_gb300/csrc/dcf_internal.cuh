@@ -56,15 +56,15 @@ struct IterArgs {
   float* V[2];
   float* W;          // m x R
   // partial results of the streaming passes
-  double* part_q;    // [n_vblocks][R*R]   V'^T V'
-  double* part_xv;   // [n_vblocks][R*R]   V_old^T V'
+  float2* part_q;    // [n_vblocks][R*R]   V'^T V'      (compensated pairs hi, lo)
+  float2* part_xv;   // [n_vblocks][R*R]   V_old^T V'
   double* part_h;    // [n_vblocks]        Huber partial
   float* part_p;     // [n_splits][m*R]    P partials (X V')
   int n_vblocks;
   int n_splits;
   int64_t split_cols;
-  double* part_g;    // [n_rblocks][R*R]   U_new^T U_new partials
-  double* part_xu;   // [n_rblocks][R*R]   U_old^T U_new partials
+  float2* part_g;    // [n_rblocks][R*R]   U_new^T U_new partials (hi, lo)
+  float2* part_xu;   // [n_rblocks][R*R]   U_old^T U_new partials (hi, lo)
   int n_rblocks;
   Smalls* sm;
   DevState* st;
@@ -74,17 +74,34 @@ struct IterArgs {
 };
 
 // Launchers (stream-ordered; return cudaGetLastError()).
-cudaError_t launch_iteration_v1(const IterArgs& a, int vblocks_grid, cudaStream_t s);
-cudaError_t launch_init_from_u(const IterArgs& a, int copy, cudaStream_t s);
-cudaError_t launch_gram_only(const IterArgs& a, int copy, cudaStream_t s);
+// Gram partials part[b][k*cy + l] = sum over the rows of CTA b of X[a,k] Y[a,l],
+// as compensated pairs (hi, lo).
+cudaError_t launch_gram(const float* X, int ldx, int cx, const float* Y, int ldy, int cy,
+                        int64_t N, float2* part, int nparts, const DevState* st,
+                        int respect_stop, cudaStream_t s);
+// Q = V'^T V' and X_v = V_old^T V' partials in one pass (square R x R, stop-aware).
+cudaError_t launch_gram_vv(int R, const float* Vo, const float* Vn, int64_t N, float2* part_q,
+                           float2* part_xv, int nparts, const DevState* st, cudaStream_t s);
+cudaError_t launch_make_w(const IterArgs& a, int copy, int respect_stop, cudaStream_t s);
+cudaError_t launch_rows(const IterArgs& a, cudaStream_t s);
+cudaError_t launch_reduce_q(const IterArgs& a, double* out_q, double* out_xv, double* out_h,
+                            int nparts_gram, unsigned int* counter, cudaStream_t s);
+cudaError_t launch_reduce_g(const IterArgs& a, double* out_g, double* out_xu,
+                            unsigned int* counter, cudaStream_t s);
+cudaError_t launch_reduce_init(const IterArgs& a, int which, int copy, const float2* part,
+                               int nparts, double* out, unsigned int* counter, cudaStream_t s);
+cudaError_t launch_reduce_plain(const float2* part, int nparts, int count, double* out,
+                                cudaStream_t s);
+cudaError_t launch_pass1(const IterArgs& a, int grid, int mode_init, int out_copy,
+                         cudaStream_t s);
+cudaError_t launch_pass2(const IterArgs& a, cudaStream_t s);
+cudaError_t prepare_stream_kernels();
+cudaError_t prepare_small_kernels();
 cudaError_t launch_materialize(const float* M, int64_t m, int64_t c0, int64_t ni,
                                const float* U, const float* V, int R, float lam,
                                int mode, float* out, cudaStream_t s);
 cudaError_t launch_philox_u0(float* U, int64_t m, int r, int R, uint64_t seed,
                              cudaStream_t s);
-cudaError_t launch_truth_err(const float* U, const float* V, int64_t m, int64_t n, int R,
-                             const float* A, const float* B, int k, double* part,
-                             int nparts, double* out, cudaStream_t s);
 cudaError_t launch_check_finite(const float* x, int64_t count, int* flag, cudaStream_t s);
 
 int pick_R(int r);

@@ -23,24 +23,6 @@
 #include "dcf.h"
 #include "dcf_internal.cuh"
 
-namespace dcf {
-cudaError_t launch_gram(const float* X, int ldx, int cx, const float* Y, int ldy, int cy,
-                        int64_t N, double* part, int nparts, const DevState* st,
-                        int respect_stop, cudaStream_t s);
-cudaError_t launch_make_w(const IterArgs& a, int copy, int respect_stop, cudaStream_t s);
-cudaError_t launch_rows(const IterArgs& a, cudaStream_t s);
-cudaError_t launch_reduce_q(const IterArgs& a, double* out_q, double* out_xv, double* out_h,
-                            int nparts_gram, unsigned int* counter, cudaStream_t s);
-cudaError_t launch_reduce_g(const IterArgs& a, double* out_g, double* out_xu,
-                            unsigned int* counter, cudaStream_t s);
-cudaError_t launch_reduce_init(const IterArgs& a, int which, int copy, const double* part,
-                               int nparts, double* out, unsigned int* counter, cudaStream_t s);
-cudaError_t launch_pass1(const IterArgs& a, int grid, int mode_init, int out_copy,
-                         cudaStream_t s);
-cudaError_t launch_pass2(const IterArgs& a, cudaStream_t s);
-cudaError_t prepare_stream_kernels();
-cudaError_t prepare_small_kernels();
-}  // namespace dcf
 
 using namespace dcf;
 
@@ -131,10 +113,10 @@ extern "C" dcf_status dcf_iterate_noalloc(const float* M, int64_t m, int64_t n, 
     a.W = (float*)c.take((size_t)m * R * 4);
     a.part_p = (float*)c.take((size_t)n_splits * m * R * 4);
     a.part_h = (double*)c.take((size_t)n_vblocks * 8);
-    a.part_q = (double*)c.take(ngp * RR * 8);
-    a.part_xv = (double*)c.take((size_t)n_vgram * RR * 8);
-    a.part_g = (double*)c.take(ngp * RR * 8);
-    a.part_xu = (double*)c.take((size_t)n_rblocks * RR * 8);
+    a.part_q = (float2*)c.take(ngp * RR * 8);
+    a.part_xv = (float2*)c.take((size_t)n_vgram * RR * 8);
+    a.part_g = (float2*)c.take(ngp * RR * 8);
+    a.part_xu = (float2*)c.take((size_t)n_rblocks * RR * 8);
     *red = (double*)c.take((4 * RR + 8) * 8);
     a.sm = (Smalls*)c.take(sizeof(Smalls));
     a.st = (DevState*)c.take(sizeof(DevState));
@@ -203,8 +185,7 @@ extern "C" dcf_status dcf_iterate_noalloc(const float* M, int64_t m, int64_t n, 
   NA_CK(launch_make_w(a, 0, 1, s));
   NA_CK(launch_pass1(a, n_vblocks, 0, 0, s));
   NA_CK(launch_pass2(a, s));
-  NA_CK(launch_gram(a.V[1], R, R, a.V[1], R, R, n, a.part_q, n_vgram, a.st, 1, s));
-  NA_CK(launch_gram(a.V[0], R, R, a.V[1], R, R, n, a.part_xv, n_vgram, a.st, 1, s));
+  NA_CK(launch_gram_vv(R, a.V[0], a.V[1], n, a.part_q, a.part_xv, n_vgram, a.st, s));
   NA_CK(launch_reduce_q(a, red_q, red_xv, red_h, n_vgram, counters + 0, s));
   NA_CK(launch_rows(a, s));
   NA_CK(launch_reduce_g(a, red_g, red_xu, counters + 1, s));

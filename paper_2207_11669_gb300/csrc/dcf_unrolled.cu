@@ -40,14 +40,6 @@
 #include "dcf_small.cuh"
 
 namespace dcf {
-cudaError_t launch_gram(const float* X, int ldx, int cx, const float* Y, int ldy, int cy,
-                        int64_t N, double* part, int nparts, const DevState* st,
-                        int respect_stop, cudaStream_t s);
-cudaError_t launch_reduce_plain(const double* part, int nparts, int count, double* out,
-                                cudaStream_t s);
-cudaError_t launch_pass1(const IterArgs& a, int grid, int mode_init, int out_copy,
-                         cudaStream_t s);
-
 namespace {
 
 constexpr int kUnrolledMaxR = 32;
@@ -645,7 +637,7 @@ struct UnrolledState {
   float* part_wb = nullptr;
   float* mats = nullptr;
   double* red = nullptr;
-  double* part = nullptr;
+  float2* part = nullptr;
   double* sc = nullptr;
   double* loss = nullptr;  // [K]
   double* grads = nullptr; // [3K]
@@ -722,7 +714,7 @@ dcf_status ensure_unrolled(dcf_handle h, int K) {
     u->part_wb = (float*)dev_alloc(h, mR * u->n_splits);
     u->mats = (float*)dev_alloc(h, (size_t)kNumMat * kSlot * 4);
     u->red = (double*)dev_alloc(h, (size_t)kNumRed * kSlot * 8);
-    u->part = (double*)dev_alloc(h, (size_t)u->n_gram * kSlot * 8);
+    u->part = (float2*)dev_alloc(h, (size_t)u->n_gram * kSlot * 8);
     u->sc = (double*)dev_alloc(h, (size_t)kNumSc * 8);
     u->lam_part = (double*)dev_alloc(h, (size_t)grid * 8);
     u->hub_part = (double*)dev_alloc(h, (size_t)std::max(grid, h->n_vblocks) * 8);

@@ -46,23 +46,26 @@ constexpr uint32_t kWaitLimit = 1u << 26;
 
 constexpr int kFThreads = 640;   // 20 warps, see the role map below
 constexpr int kChunk = 4;        // columns per reduce-scatter chunk (16 chunks per strip)
+constexpr int kNC = 3;           // C tiles in flight: a tile lives from the S-step epilogue
+                                 // of its strip until that strip's GEMM3, i.e. across the
+                                 // cluster exchange, so this sets the pipeline depth
 
 template <int R, int NST>
 struct FL {  // shared-memory layout (bytes)
   static constexpr int RING = 0;                                 // NST x (128 x 32 fp32)
   static constexpr int WIMG = RING + NST * kSubBytes;            // 2R x 256 fp16
   static constexpr int CBYTES = kFH * kFW * 2;                   // one C tile (256 x 64 fp16)
-  static constexpr int CBUF = WIMG + 2 * R * kFH * 2;            // 2 C tiles
+  static constexpr int CBUF = WIMG + 2 * R * kFH * 2;            // kNC C tiles
   static constexpr int VBYTES = 2 * kFW * R * 2;                 // one V image (2 terms)
-  static constexpr int VIMG = CBUF + 2 * CBYTES;                 // 2 V images
+  static constexpr int VIMG = CBUF + kNC * CBYTES;               // one V image
   static constexpr int PBYTES = 2 * R * kFW * 2;                 // one V' image (2R x 64 fp16)
-  static constexpr int PIMG = VIMG + 2 * VBYTES;                 // 2 V' images
+  static constexpr int PIMG = VIMG + VBYTES;                     // 2 V' images
   static constexpr int YBYTES = kFW * R * 4;                     // one column-sum block
   static constexpr int YPART = PIMG + 2 * PBYTES;                // 2 x (64 x R fp32)
   static constexpr int ZM = YPART + 2 * YBYTES;                  // R x R fp32
   static constexpr int STG = ZM + R * R * 4;                     // 2R x 4 fp16 image chunk
   static constexpr int BAR = STG + 2 * (2 * R * kChunk * 2);     // mbarriers (2 staging chunks)
-  static constexpr int NBAR = 2 * NST + 27;
+  static constexpr int NBAR = 2 * NST + 29;
   static constexpr int TSLOT = BAR + NBAR * 8;
   static constexpr int RED = TSLOT + 16;                         // 16 doubles
   static constexpr int TOTAL = RED + 16 * 8;
@@ -133,7 +136,7 @@ __global__ void __launch_bounds__(kFThreads, 1)
   // barrier indices
   const int b_full = 0, b_empty = NST, b_vfull = 2 * NST, b_vempty = b_vfull + 2,
             b_d1full = b_vempty + 2, b_d1empty = b_d1full + 2, b_cfull = b_d1empty + 2,
-            b_cempty = b_cfull + 2, b_d2full = b_cempty + 2, b_d2empty = b_d2full + 2,
+            b_cempty = b_cfull + kNC, b_d2full = b_cempty + kNC, b_d2empty = b_d2full + 2,
             b_g3done = b_d2empty + 2, b_yfull = b_g3done + 2, b_yfree = b_yfull + 2,
             b_pfull = b_yfree + 2, b_pfree = b_pfull + 2, b_img = b_pfree + 2,
             b_last = b_img + 1;
@@ -153,10 +156,12 @@ __global__ void __launch_bounds__(kFThreads, 1)
       tc::mbar_init(B(b_empty + i), 4);     // the 4 epilogue warps of a row block
     }
     for (int p = 0; p < 2; ++p) {
-      tc::mbar_init(B(b_vfull + p), 1);     // the V-image warp
-      tc::mbar_init(B(b_vempty + p), 1);    // GEMM1 commit
+      tc::mbar_init(B(b_vfull + p), 1);     // the V-image warp (only [0] is used)
+      tc::mbar_init(B(b_vempty + p), 1);    // GEMM1 commit (only [0] is used)
       tc::mbar_init(B(b_d1full + p), 1);    // GEMM1 commit
       tc::mbar_init(B(b_d1empty + p), 8);   // the 8 epilogue warps
+    }
+    for (int p = 0; p < kNC; ++p) {
       tc::mbar_init(B(b_cfull + p), 8);     // the 8 epilogue warps
       tc::mbar_init(B(b_cempty + p), 1);    // GEMM3 commit
     }
@@ -250,11 +255,11 @@ __global__ void __launch_bounds__(kFThreads, 1)
       for (int i = 0; i < S + 1; ++i) {
         if (i < S) {   // GEMM1(i): D1 = U_b V_s^T, terms (hi,hi), (hi,lo), (lo,hi)
           const int p = i & 1;
-          if (!tc::mbar_wait(B(b_vfull + p), (uint32_t)((i >> 1) & 1), kWaitLimit)) err = 1;
+          if (!tc::mbar_wait(B(b_vfull), (uint32_t)(i & 1), kWaitLimit)) err = 1;
           if (i >= 2 && !tc::mbar_wait(B(b_d1empty + p), (uint32_t)(((i >> 1) - 1) & 1), kWaitLimit))
             err = 1;
           tc::fence_after_sync();
-          const uint64_t vd = vdesc0 + (uint64_t)((p * L::VBYTES) >> 4);
+          const uint64_t vd = vdesc0;
 #pragma unroll
           for (int b = 0; b < 2; ++b) {
 #pragma unroll
@@ -268,16 +273,17 @@ __global__ void __launch_bounds__(kFThreads, 1)
             }
           }
           tc::mma_commit(B(b_d1full + p));
-          tc::mma_commit(B(b_vempty + p));
+          tc::mma_commit(B(b_vempty));
         }
         if (i >= 1) {   // GEMM2(i-1): Y = C^T W_hi + C^T W_lo (same columns)
           const int s2 = i - 1, p = s2 & 1;
-          if (!tc::mbar_wait(B(b_cfull + p), (uint32_t)((s2 >> 1) & 1), kWaitLimit)) err = 1;
+          const int pc = s2 % kNC;
+          if (!tc::mbar_wait(B(b_cfull + pc), (uint32_t)((s2 / kNC) & 1), kWaitLimit)) err = 1;
           if (s2 >= 2 &&
               !tc::mbar_wait(B(b_d2empty + p), (uint32_t)(((s2 >> 1) - 1) & 1), kWaitLimit))
             err = 1;
           tc::fence_after_sync();
-          const uint64_t cd = cdesc0 + (uint64_t)((p * L::CBYTES) >> 4);
+          const uint64_t cd = cdesc0 + (uint64_t)((pc * L::CBYTES) >> 4);
 #pragma unroll
           for (int t = 0; t < 2; ++t) {
 #pragma unroll
@@ -301,7 +307,8 @@ __global__ void __launch_bounds__(kFThreads, 1)
         if (!tc::mbar_wait_cluster(B(b_pfull + p), (uint32_t)((s3 >> 1) & 1), kWaitLimit)) err = 1;
         tc::fence_proxy_async_smem();
         tc::fence_after_sync();
-        const uint64_t cd = cdesc0 + (uint64_t)((p * L::CBYTES) >> 4);
+        const int pc = s3 % kNC;
+        const uint64_t cd = cdesc0 + (uint64_t)((pc * L::CBYTES) >> 4);
         const uint64_t pd = pdesc0 + (uint64_t)((p * L::PBYTES) >> 4);
 #pragma unroll
         for (int b = 0; b < 2; ++b) {
@@ -314,7 +321,7 @@ __global__ void __launch_bounds__(kFThreads, 1)
                          (s3 > 0 || t > 0 || kk > 0) ? 1u : 0u);
           }
         }
-        tc::mma_commit(B(b_cempty + p));
+        tc::mma_commit(B(b_cempty + pc));
         tc::mma_commit(B(b_g3done + p));
       }
       // A parity wait only tells the current phase from the previous one, so the
@@ -322,14 +329,13 @@ __global__ void __launch_bounds__(kFThreads, 1)
       tc::mma_commit(B(b_last));
     }
   } else if (warp == 3) {
-    // ================= V images (one warp), two strips ahead ===================
+    // ================= V image (one warp), one strip ahead =====================
     constexpr int VPT = kFW * R / 32;
     for (int ls = 0; ls < S; ++ls) {
-      const int p = ls & 1;
       const int64_t col0 = strip_col0(ls);
-      if (ls >= 2 && !tc::mbar_wait(B(b_vempty + p), (uint32_t)(((ls >> 1) - 1) & 1), kWaitLimit))
+      if (ls >= 1 && !tc::mbar_wait(B(b_vempty), (uint32_t)((ls - 1) & 1), kWaitLimit))
         err = 1;
-      uint8_t* img = smem + L::VIMG + p * L::VBYTES;
+      uint8_t* img = smem + L::VIMG;
 #pragma unroll
       for (int c0 = 0; c0 < VPT; c0 += 16) {
         float vr[16];
@@ -350,7 +356,7 @@ __global__ void __launch_bounds__(kFThreads, 1)
       }
       tc::fence_proxy_async_smem();
       __syncwarp();
-      if (lane == 0) tc::mbar_arrive(B(b_vfull + p));
+      if (lane == 0) tc::mbar_arrive(B(b_vfull));
     }
   } else if (warp < 12) {
     // ================= S-step epilogue (256 threads) ==========================
@@ -363,10 +369,11 @@ __global__ void __launch_bounds__(kFThreads, 1)
     for (int ls = 0; ls < S; ++ls) {
       const int p = ls & 1;
       if (!tc::mbar_wait(B(b_d1full + p), (uint32_t)((ls >> 1) & 1), kWaitLimit)) err = 1;
-      if (ls >= 2 && !tc::mbar_wait(B(b_cempty + p), (uint32_t)(((ls >> 1) - 1) & 1), kWaitLimit))
+      const int pc = ls % kNC;
+      if (ls >= kNC && !tc::mbar_wait(B(b_cempty + pc), (uint32_t)(((ls / kNC) - 1) & 1), kWaitLimit))
         err = 1;
       tc::fence_after_sync();
-      uint8_t* cbuf = smem + L::CBUF + p * L::CBYTES;
+      uint8_t* cbuf = smem + L::CBUF + pc * L::CBYTES;
       float hub = 0.f;
 #pragma unroll 1
       for (int q = 0; q < 2; ++q) {
@@ -414,7 +421,7 @@ __global__ void __launch_bounds__(kFThreads, 1)
       __syncwarp();
       if (lane == 0) {
         tc::mbar_arrive(B(b_d1empty + p));
-        tc::mbar_arrive(B(b_cfull + p));
+        tc::mbar_arrive(B(b_cfull + pc));
       }
     }
     // P partial of this cluster's columns (after the last GEMM3)
@@ -689,8 +696,8 @@ __global__ void k_absmax(const float* x, int64_t count, unsigned int* out) {
 // ---------------------------------------------------------------------------
 // host side
 // ---------------------------------------------------------------------------
-constexpr int kNST32 = 4;
-constexpr int kNST16 = 7;
+constexpr int kNST32 = 3;
+constexpr int kNST16 = 5;
 
 template <int R, int NST>
 static size_t fused_smem() {

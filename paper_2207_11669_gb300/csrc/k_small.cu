@@ -36,6 +36,9 @@ __device__ __forceinline__ void two_sum_add(float& hi, float& lo, float x) {
 
 // ---------------------------------------------------------------------------
 // Gram partials:  part[b][k*cy + l] = sum_{rows a of CTA b} X[a,k] * Y[a,l]
+// as compensated pairs (hi, lo): FP32 sums per 32-row chunk, TwoSum across
+// chunks.  Generic shapes (cx, cy <= 64); the per-iteration V Grams use the
+// register-blocked k_gram_vv below.
 // ---------------------------------------------------------------------------
 constexpr int kGramChunk = 32;
 constexpr int kGramMaxEntriesPerThread = 16;   // (64*64)/256
@@ -43,7 +46,7 @@ constexpr int kGramMaxEntriesPerThread = 16;   // (64*64)/256
 __global__ void __launch_bounds__(256)
 k_gram_part(const float* __restrict__ X, int ldx, int cx,
             const float* __restrict__ Y, int ldy, int cy,
-            int64_t N, int64_t rows_per_cta, double* __restrict__ part,
+            int64_t N, int64_t rows_per_cta, float2* __restrict__ part,
             const DevState* st, int respect_stop) {
   if (respect_stop && st->stop) return;
   extern __shared__ float sh[];
@@ -52,8 +55,15 @@ k_gram_part(const float* __restrict__ X, int ldx, int cx,
   const int tid = threadIdx.x;
   const int ne = cx * cy;
   float hi[kGramMaxEntriesPerThread], lo[kGramMaxEntriesPerThread];
+  int xo[kGramMaxEntriesPerThread], yo[kGramMaxEntriesPerThread];
 #pragma unroll
-  for (int i = 0; i < kGramMaxEntriesPerThread; ++i) { hi[i] = 0.f; lo[i] = 0.f; }
+  for (int s = 0; s < kGramMaxEntriesPerThread; ++s) {
+    hi[s] = 0.f;
+    lo[s] = 0.f;
+    const int e = tid + s * 256;
+    xo[s] = e < ne ? e / cy : 0;
+    yo[s] = e < ne ? e % cy : 0;
+  }
   const int64_t a0 = (int64_t)blockIdx.x * rows_per_cta;
   const int64_t a1 = min(N, a0 + rows_per_cta);
   for (int64_t c = a0; c < a1; c += kGramChunk) {
@@ -68,21 +78,126 @@ k_gram_part(const float* __restrict__ X, int ldx, int cx,
       Ys[i] = rr < rows ? Y[(c + rr) * ldy + k] : 0.f;
     }
     __syncthreads();
+    float acc[kGramMaxEntriesPerThread];
 #pragma unroll
-    for (int s = 0; s < kGramMaxEntriesPerThread; ++s) {
-      int e = tid + s * 256;
-      if (e < ne) {
-        int k = e / cy, l = e % cy;
-        float acc = 0.f;
-        for (int rr = 0; rr < rows; ++rr) acc = fmaf(Xs[rr * cx + k], Ys[rr * cy + l], acc);
-        two_sum_add(hi[s], lo[s], acc);
-      }
+    for (int s = 0; s < kGramMaxEntriesPerThread; ++s) acc[s] = 0.f;
+    for (int rr = 0; rr < kGramChunk; ++rr) {   // rows past the end are zero
+#pragma unroll
+      for (int s = 0; s < kGramMaxEntriesPerThread; ++s)
+        if (tid + s * 256 < ne) acc[s] = fmaf(Xs[rr * cx + xo[s]], Ys[rr * cy + yo[s]], acc[s]);
     }
+#pragma unroll
+    for (int s = 0; s < kGramMaxEntriesPerThread; ++s) two_sum_add(hi[s], lo[s], acc[s]);
   }
 #pragma unroll
   for (int s = 0; s < kGramMaxEntriesPerThread; ++s) {
     int e = tid + s * 256;
-    if (e < ne) part[(int64_t)blockIdx.x * ne + e] = (double)hi[s] + (double)lo[s];
+    if (e < ne) part[(int64_t)blockIdx.x * ne + e] = make_float2(hi[s], lo[s]);
+  }
+}
+
+// Both Grams of the new V in one pass:  Q = V'^T V'  and  X_v = V_old^T V'.
+// Thread tile TB x TB of each output (R = 32: 2 x 2, R = 64: 4 x 4, R <= 16:
+// 1 x 1 with 256 / (R/TB)^2 row groups); 64-row chunks in shared memory.
+template <int R>
+struct GvvCfg {
+  static constexpr int TB = R >= 64 ? 4 : R >= 32 ? 2 : 1;
+  static constexpr int NT = R / TB;                 // tiles per dimension
+  static constexpr int GROUPS = 256 / (NT * NT);    // row groups
+  static constexpr int CH = 64;                     // rows per chunk
+  static constexpr size_t smem_bytes = 2 * (size_t)CH * R * 4;
+};
+
+template <int R>
+__global__ void __launch_bounds__(256)
+k_gram_vv(const float* __restrict__ Vo, const float* __restrict__ Vn, int64_t N,
+          int64_t rows_per_cta, float2* __restrict__ part_q, float2* __restrict__ part_xv,
+          const DevState* st) {
+  using C = GvvCfg<R>;
+  constexpr int TB = C::TB, NT = C::NT, G = C::GROUPS, CH = C::CH;
+  if (st->stop) return;
+  extern __shared__ __align__(16) float gsh[];
+  float* So = gsh;              // [CH][R]  V_old rows
+  float* Sn = gsh + CH * R;     // [CH][R]  V' rows
+  const int tid = threadIdx.x;
+  const int tile = tid % (NT * NT), grp = tid / (NT * NT);
+  const int k0 = (tile / NT) * TB, l0 = (tile % NT) * TB;
+  float qh[TB][TB], ql[TB][TB], xh[TB][TB], xl[TB][TB];
+#pragma unroll
+  for (int i = 0; i < TB; ++i)
+#pragma unroll
+    for (int j = 0; j < TB; ++j) { qh[i][j] = ql[i][j] = xh[i][j] = xl[i][j] = 0.f; }
+  const int64_t a0 = (int64_t)blockIdx.x * rows_per_cta;
+  const int64_t a1 = min(N, a0 + rows_per_cta);
+  for (int64_t c = a0; c < a1; c += CH) {
+    const int rows = (int)dmin64((int64_t)CH, a1 - c);
+    __syncthreads();
+    for (int i = tid; i < CH * R / 4; i += 256) {
+      const int rr = (4 * i) / R;
+      const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
+      const bool ok = rr < rows;
+      reinterpret_cast<float4*>(So)[i] = ok ? reinterpret_cast<const float4*>(Vo + c * R)[i] : z;
+      reinterpret_cast<float4*>(Sn)[i] = ok ? reinterpret_cast<const float4*>(Vn + c * R)[i] : z;
+    }
+    __syncthreads();
+    float qa[TB][TB], xa[TB][TB];
+#pragma unroll
+    for (int i = 0; i < TB; ++i)
+#pragma unroll
+      for (int j = 0; j < TB; ++j) { qa[i][j] = 0.f; xa[i][j] = 0.f; }
+    for (int rr = grp; rr < CH; rr += G) {
+      float nk[TB], nl[TB], ok[TB];
+#pragma unroll
+      for (int i = 0; i < TB; ++i) {
+        nk[i] = Sn[rr * R + k0 + i];
+        ok[i] = So[rr * R + k0 + i];
+        nl[i] = Sn[rr * R + l0 + i];
+      }
+#pragma unroll
+      for (int i = 0; i < TB; ++i)
+#pragma unroll
+        for (int j = 0; j < TB; ++j) {
+          qa[i][j] = fmaf(nk[i], nl[j], qa[i][j]);
+          xa[i][j] = fmaf(ok[i], nl[j], xa[i][j]);
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < TB; ++i)
+#pragma unroll
+      for (int j = 0; j < TB; ++j) {
+        two_sum_add(qh[i][j], ql[i][j], qa[i][j]);
+        two_sum_add(xh[i][j], xl[i][j], xa[i][j]);
+      }
+  }
+  // combine the row groups (G > 1 only for R <= 8) through shared memory
+  if (G > 1) {
+    __syncthreads();
+    float* cmb = gsh;   // [G][NT*NT][4] (hi, lo of Q and X_v); fits in the chunk buffers
+    if (grp > 0) {
+      float* d = cmb + ((size_t)grp * NT * NT + tile) * 4;
+      d[0] = qh[0][0]; d[1] = ql[0][0]; d[2] = xh[0][0]; d[3] = xl[0][0];
+    }
+    __syncthreads();
+    if (grp == 0) {
+      for (int g2 = 1; g2 < G; ++g2) {
+        const float* d = cmb + ((size_t)g2 * NT * NT + tile) * 4;
+        two_sum_add(qh[0][0], ql[0][0], d[0]);
+        ql[0][0] += d[1];
+        two_sum_add(xh[0][0], xl[0][0], d[2]);
+        xl[0][0] += d[3];
+      }
+    }
+  }
+  if (grp == 0) {
+    const int64_t base = (int64_t)blockIdx.x * R * R;
+#pragma unroll
+    for (int i = 0; i < TB; ++i)
+#pragma unroll
+      for (int j = 0; j < TB; ++j) {
+        const int e = (k0 + i) * R + l0 + j;
+        part_q[base + e] = make_float2(qh[i][j], ql[i][j]);
+        part_xv[base + e] = make_float2(xh[i][j], xl[i][j]);
+      }
   }
 }
 
@@ -92,8 +207,9 @@ k_gram_part(const float* __restrict__ X, int ldx, int cx,
 enum TailKind { TAIL_NONE = 0, TAIL_Q = 1, TAIL_G = 2, TAIL_INIT_G = 3, TAIL_INIT_Q = 4 };
 
 struct ReduceArgs {
-  const double* part[3];   // partial arrays ([nparts][count_s])
-  int count[3];            // entries per matrix (0 = unused)
+  const float2* part[2];   // compensated partial arrays ([nparts][count_s]) of inputs 0, 1
+  const double* hpart;     // input 2: FP64 partials (the Huber sum), count[2] <= 1
+  int count[3];            // entries per input (0 = unused)
   double* out[3];          // destinations (FP64)
   int nparts[3];
   int total;               // count[0] + count[1] + count[2]
@@ -121,22 +237,43 @@ __global__ void __launch_bounds__(256) k_reduce_parts(ReduceArgs a) {
   const int lane_p = tid / kRedEntriesPerCta;          // 0..15
   const int nsplit = 256 / kRedEntriesPerCta;
   const int e = blockIdx.x * kRedEntriesPerCta + e_local;
-  double s = 0.0;
+  __shared__ float2 red2[256];
+  float hi = 0.f, lo = 0.f;
+  double hs = 0.0;
   int which = -1, idx = 0;
   if (e < a.total) {
     idx = e;
     which = 0;
     while (idx >= a.count[which]) { idx -= a.count[which]; ++which; }
-    const double* p = a.part[which];
-    const int cnt = a.count[which];
-    for (int q = lane_p; q < a.nparts[which]; q += nsplit) s += p[(int64_t)q * cnt + idx];
+    if (which < 2) {
+      const float2* p = a.part[which];
+      const int cnt = a.count[which];
+      for (int q = lane_p; q < a.nparts[which]; q += nsplit) {
+        const float2 v = p[(int64_t)q * cnt + idx];
+        two_sum_add(hi, lo, v.x);
+        lo += v.y;
+      }
+    } else {
+      for (int q = lane_p; q < a.nparts[2]; q += nsplit) hs += a.hpart[q];
+    }
   }
-  red[tid] = s;
+  red2[tid] = make_float2(hi, lo);
+  red[tid] = hs;
   __syncthreads();
   if (lane_p == 0 && which >= 0) {
-    double t = 0.0;
-    for (int q = 0; q < nsplit; ++q) t += red[q * kRedEntriesPerCta + e_local];
-    a.out[which][idx] = t;
+    if (which < 2) {
+      float th = 0.f, tl = 0.f;
+      for (int q = 0; q < nsplit; ++q) {
+        const float2 v = red2[q * kRedEntriesPerCta + e_local];
+        two_sum_add(th, tl, v.x);
+        tl += v.y;
+      }
+      a.out[which][idx] = (double)th + (double)tl;
+    } else {
+      double t = 0.0;
+      for (int q = 0; q < nsplit; ++q) t += red[q * kRedEntriesPerCta + e_local];
+      a.out[which][idx] = t;
+    }
   }
   if (a.tail == TAIL_NONE) return;
   // last-block-done: the CTA that finishes last runs the serial tail
@@ -203,27 +340,38 @@ __device__ void tail_g(const ReduceArgs& a, double* A, float* F) {
     }
     __syncthreads();
     // metrics: dL^2 = <G_t,Q_t> - 2 <X_u, X_v> + <G_{t-1}, Q_{t-1}>   (all r x r)
-    __shared__ double red5[5][256];
-    double s0 = 0, s1 = 0, s2 = 0, s3 = 0, s4 = 0;
+    // five FP64 sums in one reduction: per-thread partials, a shuffle tree
+    // per warp, then the per-warp values across lanes of warp 0
+    __shared__ double wsum[5][32];
+    double v[5] = {0, 0, 0, 0, 0};
     for (int i = threadIdx.x; i < R * R; i += blockDim.x) {
-      s0 += sm->gram[tgt][i] * sm->q[tgt][i];
-      s1 += sm->xu[i] * sm->xv[i];
-      s2 += sm->gram[cur][i] * sm->q[cur][i];
-      int r = i / R, c = i % R;
-      if (r == c) { s3 += sm->gram[cur][i]; s4 += sm->q[cur][i]; }
+      v[0] = fma(sm->gram[tgt][i], sm->q[tgt][i], v[0]);
+      v[1] = fma(sm->xu[i], sm->xv[i], v[1]);
+      v[2] = fma(sm->gram[cur][i], sm->q[cur][i], v[2]);
     }
-    red5[0][threadIdx.x] = s0;
-    red5[1][threadIdx.x] = s1;
-    red5[2][threadIdx.x] = s2;
-    red5[3][threadIdx.x] = s3;
-    red5[4][threadIdx.x] = s4;
+    for (int i = threadIdx.x; i < R; i += blockDim.x) {
+      v[3] += sm->gram[cur][i * R + i];
+      v[4] += sm->q[cur][i * R + i];
+    }
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+      for (int q = 0; q < 5; ++q) v[q] += __shfl_xor_sync(0xffffffffu, v[q], o);
+    if (lane == 0)
+#pragma unroll
+      for (int q = 0; q < 5; ++q) wsum[q][wid] = v[q];
     __syncthreads();
+    if (wid == 0) {
+#pragma unroll
+      for (int q = 0; q < 5; ++q) v[q] = lane < nw ? wsum[q][lane] : 0.0;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+        for (int q = 0; q < 5; ++q) v[q] += __shfl_xor_sync(0xffffffffu, v[q], o);
+    }
+    const double a0 = v[0], a1 = v[1], a2 = v[2], t0 = v[3], t1 = v[4];   // valid in warp 0
     if (threadIdx.x == 0) {
-      double a0 = 0, a1 = 0, a2 = 0, t0 = 0, t1 = 0;
-      for (int i = 0; i < blockDim.x; ++i) {
-        a0 += red5[0][i]; a1 += red5[1][i]; a2 += red5[2][i];
-        t0 += red5[3][i]; t1 += red5[4][i];
-      }
       double d2 = a0 - 2.0 * a1 + a2;
       if (d2 < 0) d2 = 0;
       st->dL_rel = a0 > 0 ? sqrt(d2 / a0) : INFINITY;
@@ -385,8 +533,8 @@ __global__ void __launch_bounds__(256) k_rows(IterArgs a) {
       gg = fmaf(Un[rr * R + k], Un[rr * R + l], gg);
       xu = fmaf(Uo[rr * R + k], Un[rr * R + l], xu);
     }
-    a.part_g[(int64_t)blockIdx.x * R * R + e] = (double)gg;
-    a.part_xu[(int64_t)blockIdx.x * R * R + e] = (double)xu;
+    a.part_g[(int64_t)blockIdx.x * R * R + e] = make_float2(gg, 0.f);
+    a.part_xu[(int64_t)blockIdx.x * R * R + e] = make_float2(xu, 0.f);
   }
 }
 
@@ -444,12 +592,30 @@ int pick_R(int r) { return r <= 8 ? 8 : r <= 16 ? 16 : r <= 32 ? 32 : 64; }
 static size_t gram_smem(int cx, int cy) { return (size_t)kGramChunk * (cx + cy) * sizeof(float); }
 
 cudaError_t launch_gram(const float* X, int ldx, int cx, const float* Y, int ldy, int cy,
-                        int64_t N, double* part, int nparts, const DevState* st,
+                        int64_t N, float2* part, int nparts, const DevState* st,
                         int respect_stop, cudaStream_t s) {
   int64_t rows_per = (N + nparts - 1) / nparts;
   k_gram_part<<<nparts, 256, gram_smem(cx, cy), s>>>(X, ldx, cx, Y, ldy, cy, N, rows_per, part,
                                                      st, respect_stop);
   return cudaGetLastError();
+}
+
+template <int R>
+static cudaError_t gram_vv_T(const float* Vo, const float* Vn, int64_t N, float2* pq,
+                             float2* pxv, int nparts, const DevState* st, cudaStream_t s) {
+  const int64_t rows_per = (N + nparts - 1) / nparts;
+  k_gram_vv<R><<<nparts, 256, GvvCfg<R>::smem_bytes, s>>>(Vo, Vn, N, rows_per, pq, pxv, st);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gram_vv(int R, const float* Vo, const float* Vn, int64_t N, float2* part_q,
+                           float2* part_xv, int nparts, const DevState* st, cudaStream_t s) {
+  switch (R) {
+    case 8: return gram_vv_T<8>(Vo, Vn, N, part_q, part_xv, nparts, st, s);
+    case 16: return gram_vv_T<16>(Vo, Vn, N, part_q, part_xv, nparts, st, s);
+    case 32: return gram_vv_T<32>(Vo, Vn, N, part_q, part_xv, nparts, st, s);
+    default: return gram_vv_T<64>(Vo, Vn, N, part_q, part_xv, nparts, st, s);
+  }
 }
 
 static cudaError_t launch_reduce(const ReduceArgs& ra, cudaStream_t s) {
@@ -503,7 +669,7 @@ cudaError_t launch_reduce_q(const IterArgs& a, double* out_q, double* out_xv, do
   const int RR = a.R * a.R;
   ra.part[0] = a.part_q; ra.count[0] = RR; ra.out[0] = out_q; ra.nparts[0] = nparts_gram;
   ra.part[1] = a.part_xv; ra.count[1] = RR; ra.out[1] = out_xv; ra.nparts[1] = nparts_gram;
-  ra.part[2] = a.part_h; ra.count[2] = 1; ra.out[2] = out_h; ra.nparts[2] = a.n_vblocks;
+  ra.hpart = a.part_h; ra.count[2] = 1; ra.out[2] = out_h; ra.nparts[2] = a.n_vblocks;
   ra.total = 2 * RR + 1;
   ra.tail = TAIL_Q;
   ra.copy = a.cur;
@@ -527,7 +693,7 @@ cudaError_t launch_reduce_g(const IterArgs& a, double* out_g, double* out_xu,
 }
 
 cudaError_t launch_reduce_init(const IterArgs& a, int which /*0: G, 1: Q*/, int copy,
-                               const double* part, int nparts, double* out,
+                               const float2* part, int nparts, double* out,
                                unsigned int* counter, cudaStream_t s) {
   ReduceArgs ra{};
   const int RR = a.R * a.R;
@@ -539,7 +705,7 @@ cudaError_t launch_reduce_init(const IterArgs& a, int which /*0: G, 1: Q*/, int 
   return launch_reduce(ra, s);
 }
 
-cudaError_t launch_reduce_plain(const double* part, int nparts, int count, double* out,
+cudaError_t launch_reduce_plain(const float2* part, int nparts, int count, double* out,
                                 cudaStream_t s) {
   ReduceArgs ra{};
   ra.part[0] = part; ra.count[0] = count; ra.out[0] = out; ra.nparts[0] = nparts;
