@@ -393,7 +393,11 @@ extern "C" dcf_status dcf_create(const dcf_params* p, dcf_handle* out) {
     }
     if (p->path != 1 && shape_ok) {
       const int Rf = p->r <= 16 ? 16 : 32;
-      const int cs = (int)((h->m + 255) / 256);
+      // slabs of 256 rows, rounded up to a power of two: the cluster exchange
+      // splits each 64-column strip into 16 chunks, so the cluster size divides 16
+      // (slabs past the last row read zeros)
+      int cs = 1;
+      while (cs * 256 < h->m) cs *= 2;
       int ncl = 0;
       if (fused_prepare(Rf) == cudaSuccess) ncl = fused_max_clusters(Rf, cs);
       cudaGetLastError();

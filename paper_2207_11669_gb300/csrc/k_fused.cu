@@ -41,7 +41,9 @@ namespace dcf {
 constexpr int kFW = 64;          // strip width (columns)
 constexpr int kFH = 256;         // rows per CTA (2 row blocks of 128)
 constexpr int kSubBytes = 128 * 32 * 4;
-constexpr uint32_t kWaitLimit = 1u << 26;
+// Every wait of a launch together gives up after this long (a launch takes
+// milliseconds); on expiry the kernel records DCF_ETIMEOUT and runs out.
+constexpr uint64_t kDeadlineNs = 2000000000ull;
 
 
 constexpr int kFThreads = 640;   // 20 warps, see the role map below
@@ -103,17 +105,19 @@ __device__ __forceinline__ void tsum(float& hi, float& lo, float x) {
 //   warp 2       MMA issuer for GEMM3, which waits on the cluster exchange and
 //                therefore must not hold up GEMM1/GEMM2 (tcgen05 ops complete in
 //                the issuing thread's order)
-//   warp 3       fp16 images of V_s (B operand of GEMM1), two strips ahead
+//   warp 3       fp16 image of V_s (B operand of GEMM1), one strip ahead
 //   warps 4-11   S-step epilogue: R, C/lambda into the C tile, Huber
 //   warps 12-19  exchange, two groups of 4 warps for even and odd strips:
-//                column sums out of tensor memory, reduce-scatter over the
-//                cluster (DSMEM), V', all-gather of the V' image
-// Local mbarriers link the roles inside a CTA; four mbarriers per CTA,
-// arrived on remotely, link the CTAs of the cluster:
-//   yfull  (count CS)  every CTA has published its column sums of the strip
-//   yfree  (count CS)  every reducer has read this CTA's column sums
-//   pfull  (count CS)  every reducer has written its chunk of the V' image here
-//   pfree  (count CS)  every CTA's GEMM3 that read this V' image buffer is done
+//                column sums out of tensor memory, pushed to the reducer of
+//                their chunk (DSMEM), V' of this CTA's chunks, the V' image
+//                pushed to every CTA
+// Local mbarriers link the roles inside a CTA; four mbarriers per CTA link the
+// CTAs of the cluster.  Data crosses the cluster only by st.async, whose bytes
+// complete on the receiver's mbarrier (no fences, no release/acquire pairs):
+//   yfull  (1 + bytes)  the column sums of this CTA's chunks from every CTA
+//   yfree  (count CS)   every reducer has consumed this CTA's column sums
+//   pfull  (1 + bytes)  every reducer's chunk of the V' image has landed here
+//   pfree  (count CS)   every CTA's GEMM3 that read this V' image buffer is done
 // Column sums and V' images are double-buffered, so each of these exists
 // once per buffer and completes every other strip; an arrival for strip s+2
 // can only happen after the phase of strip s has completed.  The exchange
@@ -140,10 +144,13 @@ __global__ void __launch_bounds__(kFThreads, 1)
             b_g3done = b_d2empty + 2, b_yfull = b_g3done + 2, b_yfree = b_yfull + 2,
             b_pfull = b_yfree + 2, b_pfree = b_pfull + 2, b_img = b_pfree + 2,
             b_last = b_img + 1;
-  float* ypart = reinterpret_cast<float*>(smem + L::YPART);
   float* zm = reinterpret_cast<float*>(smem + L::ZM);
   double* red = reinterpret_cast<double*>(smem + L::RED);
   int err = 0;
+  const uint64_t deadline = tc::globaltimer_ns() + kDeadlineNs;
+  auto wait_ = [&](uint32_t bar, uint32_t parity) {
+    return tc::mbar_wait_deadline(bar, parity, deadline);
+  };
 
   // ---- set-up -------------------------------------------------------------
   if (warp == 1) {
@@ -172,10 +179,10 @@ __global__ void __launch_bounds__(kFThreads, 1)
     tc::mbar_init(B(b_g3done), 1);
     tc::mbar_init(B(b_g3done + 1), 1);
     for (int p = 0; p < 2; ++p) {           // cross-CTA, one per buffer of the pair
-      tc::mbar_init(B(b_yfull + p), cs);
-      tc::mbar_init(B(b_yfree + p), cs);
-      tc::mbar_init(B(b_pfull + p), cs);
-      tc::mbar_init(B(b_pfree + p), cs);
+      tc::mbar_init(B(b_yfull + p), 1);     // armed by the local reducer; st.async bytes
+      tc::mbar_init(B(b_yfree + p), cs);    // every reducer, remote arrivals
+      tc::mbar_init(B(b_pfull + p), 1);     // armed by the GEMM3 issuer; st.async bytes
+      tc::mbar_init(B(b_pfree + p), cs);    // every CTA's GEMM3, remote arrivals
     }
     tc::mbar_init(B(b_img), 1);
     tc::mbar_init(B(b_last), 1);            // every MMA of the kernel has completed
@@ -234,7 +241,7 @@ __global__ void __launch_bounds__(kFThreads, 1)
       const int total = S * 4;
       for (int g = 0; g < total; ++g) {
         const int slot = g % NST;
-        if (g >= NST && !tc::mbar_wait(B(b_empty + slot), (uint32_t)((g / NST - 1) & 1), kWaitLimit))
+        if (g >= NST && !wait_(B(b_empty + slot), (uint32_t)((g / NST - 1) & 1)))
           err = 1;
         const int ls = g >> 2, sub = g & 3, b = sub >> 1, q = sub & 1;
         tc::mbar_arrive_expect_tx(B(b_full + slot), kSubBytes);
@@ -245,7 +252,7 @@ __global__ void __launch_bounds__(kFThreads, 1)
   } else if (warp == 1) {
     // ================= MMA issuer: GEMM1 and GEMM2 ============================
     if (lane == 0) {
-      if (!tc::mbar_wait(B(b_img), 0, kWaitLimit)) err = 1;
+      if (!wait_(B(b_img), 0)) err = 1;
       const uint32_t idesc1 = tc::idesc_f16(128, kFW, 0, 0);
       const uint32_t idesc2 = tc::idesc_f16(64, R, 1, 0);
       // descriptors are built once; moving along K adds (bytes >> 4) to the address field
@@ -255,8 +262,8 @@ __global__ void __launch_bounds__(kFThreads, 1)
       for (int i = 0; i < S + 1; ++i) {
         if (i < S) {   // GEMM1(i): D1 = U_b V_s^T, terms (hi,hi), (hi,lo), (lo,hi)
           const int p = i & 1;
-          if (!tc::mbar_wait(B(b_vfull), (uint32_t)(i & 1), kWaitLimit)) err = 1;
-          if (i >= 2 && !tc::mbar_wait(B(b_d1empty + p), (uint32_t)(((i >> 1) - 1) & 1), kWaitLimit))
+          if (!wait_(B(b_vfull), (uint32_t)(i & 1))) err = 1;
+          if (i >= 2 && !wait_(B(b_d1empty + p), (uint32_t)(((i >> 1) - 1) & 1)))
             err = 1;
           tc::fence_after_sync();
           const uint64_t vd = vdesc0;
@@ -278,9 +285,9 @@ __global__ void __launch_bounds__(kFThreads, 1)
         if (i >= 1) {   // GEMM2(i-1): Y = C^T W_hi + C^T W_lo (same columns)
           const int s2 = i - 1, p = s2 & 1;
           const int pc = s2 % kNC;
-          if (!tc::mbar_wait(B(b_cfull + pc), (uint32_t)((s2 / kNC) & 1), kWaitLimit)) err = 1;
+          if (!wait_(B(b_cfull + pc), (uint32_t)((s2 / kNC) & 1))) err = 1;
           if (s2 >= 2 &&
-              !tc::mbar_wait(B(b_d2empty + p), (uint32_t)(((s2 >> 1) - 1) & 1), kWaitLimit))
+              !wait_(B(b_d2empty + p), (uint32_t)(((s2 >> 1) - 1) & 1)))
             err = 1;
           tc::fence_after_sync();
           const uint64_t cd = cdesc0 + (uint64_t)((pc * L::CBYTES) >> 4);
@@ -304,7 +311,8 @@ __global__ void __launch_bounds__(kFThreads, 1)
       const uint64_t pdesc0 = tc::smem_desc(sbase + L::PIMG, 128, (kFW / 8) * 128);
       for (int s3 = 0; s3 < S; ++s3) {   // P_C += C V'_hi^T + C V'_lo^T
         const int p = s3 & 1;
-        if (!tc::mbar_wait_cluster(B(b_pfull + p), (uint32_t)((s3 >> 1) & 1), kWaitLimit)) err = 1;
+        tc::mbar_arrive_expect_tx(B(b_pfull + p), (uint32_t)L::PBYTES);
+        if (!wait_(B(b_pfull + p), (uint32_t)((s3 >> 1) & 1))) err = 1;
         tc::fence_proxy_async_smem();
         tc::fence_after_sync();
         const int pc = s3 % kNC;
@@ -330,33 +338,43 @@ __global__ void __launch_bounds__(kFThreads, 1)
     }
   } else if (warp == 3) {
     // ================= V image (one warp), one strip ahead =====================
-    constexpr int VPT = kFW * R / 32;
-    for (int ls = 0; ls < S; ++ls) {
+    // The next strip's V rows (contiguous, 64 x R floats) are loaded into
+    // registers while GEMM1 of the current strip runs.
+    constexpr int V4 = kFW * R / 128;           // float4 per lane
+    float4 vr[V4];
+    auto load_v = [&](int ls) {
       const int64_t col0 = strip_col0(ls);
-      if (ls >= 1 && !tc::mbar_wait(B(b_vempty), (uint32_t)((ls - 1) & 1), kWaitLimit))
+#pragma unroll
+      for (int t = 0; t < V4; ++t) {
+        const int e = 4 * (lane + 32 * t), j = e / R, k = e % R;
+        vr[t] = col0 + j < a.n ? *reinterpret_cast<const float4*>(a.Vold + (col0 + j) * R + k)
+                               : make_float4(0.f, 0.f, 0.f, 0.f);
+      }
+    };
+    if (S > 0) load_v(0);
+    for (int ls = 0; ls < S; ++ls) {
+      if (ls >= 1 && !wait_(B(b_vempty), (uint32_t)((ls - 1) & 1)))
         err = 1;
       uint8_t* img = smem + L::VIMG;
 #pragma unroll
-      for (int c0 = 0; c0 < VPT; c0 += 16) {
-        float vr[16];
+      for (int t = 0; t < V4; ++t) {
+        const int e = 4 * (lane + 32 * t), j = e / R, k = e % R;
+        const float x[4] = {vr[t].x, vr[t].y, vr[t].z, vr[t].w};
+        __half hi[4], lo[4];
 #pragma unroll
-        for (int i = 0; i < 16; ++i) {
-          const int idx = lane + 32 * (c0 + i), j = idx / R, k = idx % R;
-          vr[i] = col0 + j < a.n ? a.Vold[(col0 + j) * R + k] : 0.f;
-        }
-#pragma unroll
-        for (int i = 0; i < 16; ++i) {
-          const int idx = lane + 32 * (c0 + i), j = idx / R, k = idx % R;
-          __half hi, lo;
-          split_h(vr[i], s_v, hi, lo);
-          const int off = (j >> 3) * SB_R + (k >> 3) * 128 + (j & 7) * 16 + (k & 7) * 2;
-          *reinterpret_cast<__half*>(img + off) = hi;
-          *reinterpret_cast<__half*>(img + kFW * R * 2 + off) = lo;
-        }
+        for (int u = 0; u < 4; ++u) split_h(x[u], s_v, hi[u], lo[u]);
+        const int off = (j >> 3) * SB_R + (k >> 3) * 128 + (j & 7) * 16 + (k & 7) * 2;
+        __half2 h01 = __halves2half2(hi[0], hi[1]), h23 = __halves2half2(hi[2], hi[3]);
+        __half2 l01 = __halves2half2(lo[0], lo[1]), l23 = __halves2half2(lo[2], lo[3]);
+        *reinterpret_cast<uint2*>(img + off) =
+            make_uint2(*reinterpret_cast<uint32_t*>(&h01), *reinterpret_cast<uint32_t*>(&h23));
+        *reinterpret_cast<uint2*>(img + kFW * R * 2 + off) =
+            make_uint2(*reinterpret_cast<uint32_t*>(&l01), *reinterpret_cast<uint32_t*>(&l23));
       }
       tc::fence_proxy_async_smem();
       __syncwarp();
       if (lane == 0) tc::mbar_arrive(B(b_vfull));
+      if (ls + 1 < S) load_v(ls + 1);
     }
   } else if (warp < 12) {
     // ================= S-step epilogue (256 threads) ==========================
@@ -368,9 +386,9 @@ __global__ void __launch_bounds__(kFThreads, 1)
     float hub_hi = 0.f, hub_lo = 0.f;
     for (int ls = 0; ls < S; ++ls) {
       const int p = ls & 1;
-      if (!tc::mbar_wait(B(b_d1full + p), (uint32_t)((ls >> 1) & 1), kWaitLimit)) err = 1;
+      if (!wait_(B(b_d1full + p), (uint32_t)((ls >> 1) & 1))) err = 1;
       const int pc = ls % kNC;
-      if (ls >= kNC && !tc::mbar_wait(B(b_cempty + pc), (uint32_t)(((ls / kNC) - 1) & 1), kWaitLimit))
+      if (ls >= kNC && !wait_(B(b_cempty + pc), (uint32_t)(((ls / kNC) - 1) & 1)))
         err = 1;
       tc::fence_after_sync();
       uint8_t* cbuf = smem + L::CBUF + pc * L::CBYTES;
@@ -379,7 +397,7 @@ __global__ void __launch_bounds__(kFThreads, 1)
       for (int q = 0; q < 2; ++q) {
         const int g = ls * 4 + rb * 2 + q;
         const int rs = g % NST;
-        if (!tc::mbar_wait(B(b_full + rs), (uint32_t)((g / NST) & 1), kWaitLimit)) err = 1;
+        if (!wait_(B(b_full + rs), (uint32_t)((g / NST) & 1))) err = 1;
         const float* msub = reinterpret_cast<const float*>(smem + L::RING + rs * kSubBytes);
 #pragma unroll
         for (int h = 0; h < 2; ++h) {   // 16 columns at a time
@@ -425,7 +443,7 @@ __global__ void __launch_bounds__(kFThreads, 1)
       }
     }
     // P partial of this cluster's columns (after the last GEMM3)
-    if (!tc::mbar_wait(B(b_last), 0, kWaitLimit)) err = 1;
+    if (!wait_(B(b_last), 0)) err = 1;
     tc::fence_after_sync();
     {
       const int64_t grow = row0 + arow;
@@ -459,7 +477,9 @@ __global__ void __launch_bounds__(kFThreads, 1)
       const int64_t col = strip_col0(ls) + ((int)crank + ci * cs) * kChunk + jl;
       return (act && col < a.n) ? a.VZ[col * R + kx] : 0.f;
     };
-    const uint32_t ybase = sbase + L::YPART + p * L::YBYTES;
+    // RECV[p]: the column sums this CTA reduces, [chunk ci][source][column jl][k]
+    const uint32_t rbase = sbase + L::YPART + p * L::YBYTES;
+    const float* recv = reinterpret_cast<const float*>(smem + L::YPART + p * L::YBYTES);
     const uint32_t pbase = sbase + L::PIMG + p * L::PBYTES;
     float vz_next = grp < S ? vz_of(grp, 0) : 0.f;
     for (int ls = grp; ls < S; ls += 2) {
@@ -467,7 +487,7 @@ __global__ void __launch_bounds__(kFThreads, 1)
       const float vz_first = vz_next;
       if (ls + 2 < S) vz_next = vz_of(ls + 2, 0);   // in flight for a whole strip pair
       // ---- column sums of this CTA's rows out of tensor memory ----
-      if (!tc::mbar_wait(B(b_d2full + p), par, kWaitLimit)) err = 1;
+      if (!wait_(B(b_d2full + p), par)) err = 1;
       tc::fence_after_sync();
       float yv[R];
 #pragma unroll
@@ -477,40 +497,42 @@ __global__ void __launch_bounds__(kFThreads, 1)
       tc::fence_before_sync();
       __syncwarp();
       if (lane == 0) tc::mbar_arrive(B(b_d2empty + p));
-      if (ls >= 2 && !tc::mbar_wait_cluster(B(b_yfree + p), par ^ 1u, kWaitLimit)) err = 1;
+      // ---- send them to their reducers (every reducer has consumed strip ls-2) ----
+      if (ls >= 2 && !wait_(B(b_yfree + p), par ^ 1u)) err = 1;
       if (lane < 16) {
-        float* yp = ypart + p * (kFW * R);
-        const int j = xw * 16 + lane;
+        const int j = xw * 16 + lane;               // strip column of this thread
+        const int cc = j / kChunk, owner = cc % cs, ci = cc / cs, jj = j % kChunk;
+        const uint32_t off = (uint32_t)(((ci * cs + (int)crank) * kChunk + jj) * R) * 4;
+        const uint32_t dst = tc::map_cluster(rbase + off, (uint32_t)owner);
+        const uint32_t bar = tc::map_cluster(B(b_yfull + p), (uint32_t)owner);
 #pragma unroll
-        for (int k = 0; k < R; ++k) yp[j * R + k] = yv[k] * y_scale;
+        for (int k = 0; k < R; k += 4) {
+          uint4 v;
+          v.x = __float_as_uint(yv[k] * y_scale);
+          v.y = __float_as_uint(yv[k + 1] * y_scale);
+          v.z = __float_as_uint(yv[k + 2] * y_scale);
+          v.w = __float_as_uint(yv[k + 3] * y_scale);
+          tc::st_async_u32x4(dst + (uint32_t)k * 4, v, bar);
+        }
       }
-      // bar.sync orders the writes of the group before the arriving threads,
-      // whose arrive.release.cluster publishes them to the cluster
-      tc::named_bar(nb, 128);
-      if (xt < cs) tc::mbar_arrive_cluster(B(b_yfull + p), (uint32_t)xt);
       // ---- GEMM3 of strip ls-2 done here: its V' image buffer may be refilled ----
       if (ls >= 2 && xw == 0) {
-        if (!tc::mbar_wait(B(b_g3done + p), par ^ 1u, kWaitLimit)) err = 1;
+        if (!wait_(B(b_g3done + p), par ^ 1u)) err = 1;
         if (lane < cs) tc::mbar_arrive_cluster_relaxed(B(b_pfree + p), (uint32_t)lane);
       }
-      // ---- reduce-scatter of strip ls ----
+      // ---- reduce this CTA's chunks of strip ls ----
+      if (xt == 0) tc::mbar_arrive_expect_tx(B(b_yfull + p), (uint32_t)L::YBYTES);
       const int64_t col0 = strip_col0(ls);
-      if (!tc::mbar_wait_cluster(B(b_yfull + p), par, kWaitLimit)) err = 1;
+      if (!wait_(B(b_yfull + p), par)) err = 1;
       for (int ci = 0; ci < nch; ++ci) {
         const int cc = (int)crank + ci * cs;
         float y = ci == 0 ? vz_first : vz_of(ls, ci);
         if (act) {
-          const int j = cc * kChunk + jl;
-          const uint32_t yaddr = ybase + (uint32_t)(j * R + kx) * 4;
-          float ypv[16];
-#pragma unroll
-          for (int p2 = 0; p2 < 16; ++p2)
-            ypv[p2] = p2 < cs ? tc::ld_cluster_f32_relaxed(tc::map_cluster(yaddr, p2)) : 0.f;
-#pragma unroll
-          for (int p2 = 0; p2 < 16; ++p2) y += ypv[p2];
+          const float* src = recv + (size_t)ci * cs * kChunk * R + jl * R + kx;
+          for (int s2 = 0; s2 < cs; ++s2) y += src[(size_t)s2 * kChunk * R];
         }
         if (ci == nch - 1) {
-          // every remote read of this strip is done (the values are in registers)
+          // every read of this strip's sums is done (the values are in registers)
           tc::named_bar(nb, 128);
           if (xt < cs) tc::mbar_arrive_cluster_relaxed(B(b_yfree + p), (uint32_t)xt);
         }
@@ -527,8 +549,7 @@ __global__ void __launch_bounds__(kFThreads, 1)
           *reinterpret_cast<__half*>(stg + (R + kx) * 8 + jl * 2) = lo;
         }
         // all-gather of the chunk's V' image into every CTA (after their GEMM3 of ls-2)
-        if (ci == 0 && ls >= 2 && !tc::mbar_wait_cluster(B(b_pfree + p), par ^ 1u, kWaitLimit))
-          err = 1;
+        if (ci == 0 && ls >= 2 && !wait_(B(b_pfree + p), par ^ 1u)) err = 1;
         tc::named_bar(nb, 128);
         const uint8_t* stg = smem + L::STG + grp * (2 * R * kChunk * 2);
         for (int idx = xt; idx < cs * 2 * R; idx += 128) {
@@ -536,12 +557,11 @@ __global__ void __launch_bounds__(kFThreads, 1)
           const uint2 v = *reinterpret_cast<const uint2*>(stg + nn * 8);
           const uint32_t dst = pbase + (nn >> 3) * (kFW / 8) * 128 + (cc >> 1) * 128 +
                                (nn & 7) * 16 + (cc & 1) * 8;
-          tc::st_cluster_u32x2(tc::map_cluster(dst, p2), v.x, v.y);
+          tc::st_async_u32x2(tc::map_cluster(dst, p2), v.x, v.y,
+                             tc::map_cluster(B(b_pfull + p), (uint32_t)p2));
         }
-        tc::fence_proxy_async_cluster();
         tc::named_bar(nb, 128);   // the staging chunk is reused by the next chunk
       }
-      if (xt < cs) tc::mbar_arrive_cluster(B(b_pfull + p), (uint32_t)xt);
     }
     for (int o = 16; o > 0; o >>= 1) vmax = fmaxf(vmax, __shfl_xor_sync(0xffffffffu, vmax, o));
     if (lane == 0 && vmax > 0.f) atomicMax(a.vmax_out, __float_as_uint(vmax));

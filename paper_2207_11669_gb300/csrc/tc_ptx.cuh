@@ -187,6 +187,22 @@ __device__ __forceinline__ bool mbar_wait_cluster(uint32_t mbar, uint32_t parity
   return false;
 }
 
+// Wall-clock bounded wait: gives up once %globaltimer (ns) passes `deadline`.
+// A kernel that takes one deadline at its start therefore spends at most that
+// long in all of its waits together, whatever fails.
+__device__ __forceinline__ uint64_t globaltimer_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+__device__ __forceinline__ bool mbar_wait_deadline(uint32_t mbar, uint32_t parity,
+                                                   uint64_t deadline) {
+  for (uint32_t i = 0;; ++i) {
+    if (mbar_try_wait(mbar, parity)) return true;
+    if (globaltimer_ns() > deadline) return false;
+  }
+}
+
 // --- TMA ------------------------------------------------------------------------
 __device__ __forceinline__ void tma_load_2d(uint32_t dst, const void* tmap, int x, int y,
                                             uint32_t mbar) {
@@ -254,6 +270,21 @@ __device__ __forceinline__ void st_cluster_u32x2(uint32_t addr, uint32_t x, uint
   asm volatile("st.shared::cluster.v2.u32 [%0], {%1,%2};" ::"r"(addr), "r"(x), "r"(y) : "memory");
 }
 // Writer-side fences for data that other threads / CTAs / the async proxy consume.
+// Asynchronous store into another CTA's shared memory (addresses from mapa):
+// completion is counted in bytes on the receiving CTA's mbarrier (complete_tx),
+// so the receiver needs no fence and the sender no release.
+__device__ __forceinline__ void st_async_u32x4(uint32_t addr, uint4 v, uint32_t remote_mbar) {
+  asm volatile(
+      "st.async.shared::cluster.mbarrier::complete_tx::bytes.v4.b32 [%0], {%1,%2,%3,%4}, [%5];" ::
+          "r"(addr), "r"(v.x), "r"(v.y), "r"(v.z), "r"(v.w), "r"(remote_mbar)
+      : "memory");
+}
+__device__ __forceinline__ void st_async_u32x2(uint32_t addr, uint32_t x, uint32_t y,
+                                               uint32_t remote_mbar) {
+  asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.v2.b32 [%0], {%1,%2}, [%3];" ::
+                   "r"(addr), "r"(x), "r"(y), "r"(remote_mbar)
+               : "memory");
+}
 __device__ __forceinline__ void fence_proxy_async_cluster() {
   asm volatile("fence.proxy.async.shared::cluster;" ::: "memory");
 }
