@@ -243,6 +243,62 @@ dcf_status dcf_unrolled_forward(dcf_handle h, int K, const double* a, const doub
 dcf_status dcf_unrolled_backward(dcf_handle h, double* grad_a, double* grad_b, double* grad_c,
                                  float* grad_U0, float* const* grad_V0_i, int where);
 
+/* ------------------------------------------------------------------------
+ * Batches of independent problems.
+ *
+ * Many independent DCF-PCA problems (each its own M = [M_1 ... M_E], m, n_i,
+ * r <= 32, rho, lambda: the problem of Sec. 2.1 / Algorithm 1 per instance)
+ * advance together: one iteration of the whole batch is one CUDA graph of
+ * persistent kernels over work-item lists, with the exact consensus U-step of
+ * each instance.  An instance whose stop test fired (solve mode) is skipped
+ * from then on.  Per-instance results equal those of a single handle on the
+ * general path.  All device memory is owned by the batch; M is copied in.
+ * ------------------------------------------------------------------------ */
+typedef struct dcf_batch_s* dcf_batch;
+
+typedef struct {
+  int64_t m;              /* rows */
+  int E;                  /* column blocks */
+  const int64_t* n_i;     /* E block widths (read during dcf_batch_create only) */
+  int r;                  /* rank, 1 <= r <= min(32, m) */
+  double rho, lambda;     /* > 0 */
+} dcf_problem;
+
+/* count problems; max_iter and tol drive dcf_batch_solve (stop when
+ * ||L_t - L_{t-1}||_F / ||L_t||_F <= tol); seed gives each instance's
+ * default U0.  DCF_EINVAL on a bad problem, DCF_ENOMEM, DCF_ECUDA. */
+dcf_status dcf_batch_create(const dcf_problem* problems, int count, int max_iter, double tol,
+                            uint64_t seed, dcf_batch* out);
+dcf_status dcf_batch_set_stream(dcf_batch b, void* stream);
+/* Copy instance i's blocks (column-major, leading dimension ld_i[k] >= m, or m
+ * when ld_i is NULL) from the host (where = 0, synchronous) or the device (1). */
+dcf_status dcf_batch_load(dcf_batch b, int i, const float* const* M_i, const int64_t* ld_i,
+                          int where);
+/* Optional start point of instance i (U0 m x r row-major; V0_i[k] n_k x r or
+ * V0_i = NULL for the S = 0 sweep); before the first step only. */
+dcf_status dcf_batch_load_init(dcf_batch b, int i, const float* U0, const float* const* V0_i,
+                               int where);
+/* Autotuner: times the candidate tile shapes of the two streaming passes on
+ * this batch (reps launches each) and keeps the fastest; runs by itself
+ * before the first step when not called.  The report (one line per
+ * candidate and the choice) is copied to report[0 .. report_len). */
+dcf_status dcf_batch_tune(dcf_batch b, int reps, char* report, int report_len);
+/* n_steps iterations of every running instance (asynchronous). */
+dcf_status dcf_batch_step(dcf_batch b, int n_steps);
+/* Iterate until every instance met tol or max_iter iterations passed
+ * (DCF_ENOTCONV then).  iters_out: count ints (iterations each instance ran),
+ * n_converged: instances that met tol; either may be NULL. */
+dcf_status dcf_batch_solve(dcf_batch b, int* iters_out, int* n_converged);
+/* Instance i's current U (m x r) and V_i (n_k x r), row-major. */
+dcf_status dcf_batch_get_factors(dcf_batch b, int i, float* U, float* const* V_i, int where);
+dcf_status dcf_batch_get_stats(dcf_batch b, int i, double* objective, double* dL_rel, int* iter);
+/* Diagnostics: n_steps iterations launched phase by phase with CUDA events;
+ * phase_ms[p] (n_phases >= 7) receives the summed milliseconds of phase p:
+ * make_w, pass1_vstep, pass2_pstep, gram_v, reduce_q, rows_ustep, reduce_g. */
+dcf_status dcf_batch_profile_step(dcf_batch b, int n_steps, double* phase_ms, int n_phases);
+const char* dcf_batch_last_error(dcf_batch b);
+void dcf_batch_destroy(dcf_batch b);
+
 /* Library version string. */
 const char* dcf_version(void);
 

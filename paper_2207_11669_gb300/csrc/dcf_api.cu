@@ -54,6 +54,12 @@ dcf_status cuda_fail(dcf_handle h, cudaError_t e, const char* what) {
     if (e_ != cudaSuccess) return cuda_fail(h, e_, what); \
   } while (0)
 
+void current_allocator(dcf_alloc_fn* alloc, dcf_free_fn* release, void** ctx) {
+  *alloc = g_alloc;
+  *release = g_free;
+  *ctx = g_alloc_ctx;
+}
+
 void* dev_alloc(dcf_handle h, size_t bytes) {
   if (bytes == 0) bytes = 16;
   void* p = nullptr;

@@ -1,0 +1,792 @@
+// Batches of independent DCF-PCA problems (dcf_batch_*): every instance has
+// its own M (any m, column blocks n_i) and rank r <= 32, and one iteration of
+// the whole batch is one CUDA graph whose kernels are persistent grids walking
+// work-item lists (descriptor table BInst + items BItem).  Instances are
+// grouped by padded rank R (8, 16, 32); each group has its own lists and
+// launches.  An instance whose stop test has fired is skipped by every kernel
+// (its items return at once), so the batch runs until every member converged.
+//
+// The per-item arithmetic is the general path's (pass1_strip, pass2_block,
+// gram_vv_block, rows_block, make_w_block and the r x r tails), so a batched
+// instance computes exactly what a single handle on the general path computes.
+//
+// Autotuner: the tile decisions with a real choice -- the column-split width
+// of pass 2 and the persistent grid sizes of both passes -- are timed on the
+// batch itself (the passes only write outputs that the next iteration
+// rewrites) and the fastest is kept before the graphs are captured.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <string>
+#include <vector>
+
+#include "dcf.h"
+#include "dcf_handle.h"
+#include "dcf_internal.cuh"
+
+using namespace dcf;
+
+namespace dcf {
+cudaError_t launch_philox_u0(float* U, int64_t m, int r, int R, uint64_t seed, cudaStream_t s);
+}
+
+namespace {
+
+constexpr int kClasses = 3;               // padded rank 8, 16, 32
+constexpr int kClassR[kClasses] = {8, 16, 32};
+constexpr int kSplitCandidates[] = {256, 512, 1024, 2048};
+constexpr int kMinSplit = 256;
+
+int class_of(int r) { return r <= 8 ? 0 : r <= 16 ? 1 : 2; }
+
+struct BatchClass {
+  std::vector<int> insts;                 // instance indices of this class
+  // device lists
+  BItem* mw = nullptr;  int n_mw = 0;     // (inst, 32-row block): make_w and rows
+  BItem* p1 = nullptr;  int n_p1 = 0;     // (inst, strip)
+  BItem* p2 = nullptr;  int n_p2 = 0;     // (inst, 128-row block, split)
+  BItem* gv = nullptr;  int n_gv = 0;     // (inst, Gram chunk of V)
+  BItem* gu = nullptr;  int n_gu = 0;     // (inst, Gram chunk of U)
+  int* which = nullptr;                   // instance list for the reductions
+  int grid_p1 = 0, grid_p2 = 0, split_cols = 1024;
+};
+
+}  // namespace
+
+struct dcf_batch_s {
+  int count = 0;
+  int max_iter = 0;
+  double tol = 0;
+  uint64_t seed = 0;
+  std::vector<BInst> host;                // descriptors (device pointers)
+  std::vector<std::vector<int64_t>> n_i;  // column blocks per instance
+  std::vector<std::vector<int64_t>> c_i;
+  std::vector<char> loaded, have_init;
+  BInst* dev = nullptr;                   // descriptor table on the device
+  BatchClass cls[kClasses];
+  // allocation
+  dcf_alloc_fn alloc = nullptr;
+  dcf_free_fn release = nullptr;
+  void* alloc_ctx = nullptr;
+  std::vector<void*> owned;
+  int device = 0, num_sms = 0;
+  cudaStream_t user_stream = nullptr, stream = nullptr;
+  cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+  bool initialized = false, tuned = false;
+  int host_iter = 0;
+  cudaGraphExec_t graph[2] = {nullptr, nullptr};
+  std::string tune_report;
+  std::string err;
+};
+
+namespace {
+
+dcf_status bfail(dcf_batch b, dcf_status code, const std::string& msg) {
+  if (b) b->err = msg;
+  return code;
+}
+
+#define BCK(call, what)                                                                  \
+  do {                                                                                   \
+    cudaError_t e_ = (call);                                                             \
+    if (e_ != cudaSuccess) return bfail(b, DCF_ECUDA, std::string(what) + ": " + cudaGetErrorString(e_)); \
+  } while (0)
+
+void* balloc(dcf_batch b, size_t bytes) {
+  if (bytes == 0) bytes = 16;
+  void* p = nullptr;
+  if (b->alloc) {
+    p = b->alloc(bytes, b->alloc_ctx);
+  } else if (cudaMalloc(&p, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    p = nullptr;
+  }
+  if (p) b->owned.push_back(p);
+  return p;
+}
+
+void bfree_all(dcf_batch b) {
+  for (void* p : b->owned) {
+    if (b->release) b->release(p, b->alloc_ctx);
+    else cudaFree(p);
+  }
+  b->owned.clear();
+}
+
+// Carve a region into 256-byte aligned pieces (a dry run with base = 0 sizes it).
+struct Arena {
+  char* base = nullptr;
+  size_t used = 0;
+  template <class T>
+  T* take(size_t count) {
+    T* p = base ? reinterpret_cast<T*>(base + used) : nullptr;
+    used += (count * sizeof(T) + 255) / 256 * 256;
+    return p;
+  }
+};
+
+// Per-instance buffers; the same call sizes (base = 0) and places them.
+void layout_instance(Arena& ar, BInst& I) {
+  const int64_t m = I.m, n = I.n;
+  const int R = I.R;
+  const int nsplit_max = (int)((n + kMinSplit - 1) / kMinSplit);
+  const int ng = std::max(I.n_gitems, I.n_uitems);
+  I.U[0] = ar.take<float>((size_t)m * R);
+  I.U[1] = ar.take<float>((size_t)m * R);
+  I.V[0] = ar.take<float>((size_t)n * R);
+  I.V[1] = ar.take<float>((size_t)n * R);
+  I.W = ar.take<float>((size_t)m * R);
+  I.part_p = ar.take<float>((size_t)nsplit_max * m * R);
+  I.part_h = ar.take<double>((size_t)I.n_strips);
+  I.part_q = ar.take<float2>((size_t)ng * R * R);
+  I.part_xv = ar.take<float2>((size_t)ng * R * R);
+  I.part_g = ar.take<float2>((size_t)I.n_rblocks * R * R);
+  I.part_xu = ar.take<float2>((size_t)I.n_rblocks * R * R);
+  I.red = ar.take<double>((size_t)4 * R * R + 8);
+  I.sm = ar.take<Smalls>(1);
+  I.st = ar.take<DevState>(1);
+}
+
+template <class T>
+T* upload(dcf_batch b, const std::vector<T>& v) {
+  T* d = (T*)balloc(b, v.size() * sizeof(T));
+  if (d && !v.empty() &&
+      cudaMemcpyAsync(d, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice, b->stream) !=
+          cudaSuccess)
+    return nullptr;
+  return d;
+}
+
+// Pass-2 items of a class for one split width (row blocks of 128, splits of split_cols).
+std::vector<BItem> p2_items(dcf_batch b, const BatchClass& c, int split_cols) {
+  std::vector<BItem> v;
+  for (int q : c.insts) {
+    const BInst& I = b->host[q];
+    const int rb = (int)((I.m + 127) / 128);
+    const int ns = (int)((I.n + split_cols - 1) / split_cols);
+    for (int sp = 0; sp < ns; ++sp)
+      for (int r = 0; r < rb; ++r) v.push_back(BItem{q, r, sp, 0});
+  }
+  return v;
+}
+
+void set_split(dcf_batch b, BatchClass& c, int split_cols) {
+  c.split_cols = split_cols;
+  for (int q : c.insts) {
+    BInst& I = b->host[q];
+    I.split_cols = split_cols;
+    I.nsplit = (int)((I.n + split_cols - 1) / split_cols);
+  }
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// launch sequences
+// ---------------------------------------------------------------------------
+namespace {
+
+int grid_for(int items, int cap) { return std::max(1, std::min(items, cap)); }
+
+// Phases of one batch iteration (names for dcf_batch_profile_step).
+const char* const kBatchPhases[] = {"make_w", "pass1_vstep", "pass2_pstep", "gram_v",
+                                    "reduce_q", "rows_ustep", "reduce_g"};
+constexpr int kNumBatchPhases = 7;
+
+// One iteration of every running instance, reading copy `cur`: each phase for
+// every rank class, then the next phase.  With ev, ev[p] is recorded after
+// phase p (profiling; not captured).
+cudaError_t enqueue_batch_iteration(dcf_batch b, int cur, cudaStream_t s,
+                                    cudaEvent_t* ev = nullptr) {
+  cudaError_t e = cudaSuccess;
+  const int S = b->num_sms;
+  for (int ph = 0; ph < kNumBatchPhases; ++ph) {
+    for (int k = 0; k < kClasses && e == cudaSuccess; ++k) {
+      BatchClass& c = b->cls[k];
+      if (c.insts.empty()) continue;
+      const int R = kClassR[k];
+      const int ni = (int)c.insts.size();
+      switch (ph) {
+        case 0:   // W = U G^{-1}
+          e = launch_bsmall(R, 0, b->dev, c.mw, c.n_mw, nullptr, grid_for(c.n_mw, 4 * S), cur, 1, s);
+          break;
+        case 1:   // X, V' = X^T W
+          e = launch_bpass(R, 1, b->dev, c.p1, c.n_p1, c.grid_p1, nullptr, 0, 0, cur, 0, s);
+          break;
+        case 2:   // P = X V' partials
+          e = launch_bpass(R, 2, b->dev, nullptr, 0, 0, c.p2, c.n_p2, c.grid_p2, cur, 0, s);
+          break;
+        case 3:   // Q = V'^T V', X_v partials
+          e = launch_bsmall(R, 2, b->dev, c.gv, c.n_gv, nullptr, grid_for(c.n_gv, 2 * S), cur, 0, s);
+          break;
+        case 4:   // (Q + rho I)^{-1}
+          e = launch_bsmall(R, 3, b->dev, nullptr, ni, c.which, 0, cur, 1, s);
+          break;
+        case 5:   // consensus U-step, Gram partials of U_t
+          e = launch_bsmall(R, 1, b->dev, c.mw, c.n_mw, nullptr, grid_for(c.n_mw, 4 * S), cur, 0, s);
+          break;
+        default:  // metrics, stop test, (G + rho I)^{-1}
+          e = launch_bsmall(R, 3, b->dev, nullptr, ni, c.which, 0, cur, 2, s);
+          break;
+      }
+    }
+    if (e != cudaSuccess) return e;
+    if (ev && (e = cudaEventRecord(ev[ph], s)) != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+dcf_status batch_begin(dcf_batch b) {
+  BCK(cudaSetDevice(b->device), "set device");
+  BCK(cudaEventRecord(b->ev_in, b->user_stream), "record");
+  BCK(cudaStreamWaitEvent(b->stream, b->ev_in, 0), "wait");
+  return DCF_OK;
+}
+
+dcf_status batch_end(dcf_batch b) {
+  BCK(cudaEventRecord(b->ev_out, b->stream), "record");
+  BCK(cudaStreamWaitEvent(b->user_stream, b->ev_out, 0), "wait");
+  return DCF_OK;
+}
+
+// Start point of every instance: seeded U0 (unless loaded), G0, the S = 0
+// sweep that forms V0 (unless loaded), Q0.
+dcf_status batch_init(dcf_batch b) {
+  if (b->initialized) return DCF_OK;
+  for (int q = 0; q < b->count; ++q)
+    if (!b->loaded[q]) return bfail(b, DCF_ESTATE, "instance " + std::to_string(q) + " has no M");
+  cudaStream_t s = b->stream;
+  for (int q = 0; q < b->count; ++q) {
+    BInst& I = b->host[q];
+    DevState st0{};
+    st0.tol = b->tol;
+    BCK(cudaMemcpyAsync(I.st, &st0, sizeof(DevState), cudaMemcpyHostToDevice, s), "init state");
+    BCK(cudaMemsetAsync(I.sm, 0, sizeof(Smalls), s), "memset");
+    if (!b->have_init[q]) {
+      const uint64_t seed = b->seed + 0x9E3779B97F4A7C15ull * (uint64_t)(q + 1);
+      BCK(launch_philox_u0(I.U[0], I.m, I.r, I.R, seed, s), "philox U0");
+    }
+  }
+  const int S = b->num_sms;
+  for (int k = 0; k < kClasses; ++k) {
+    BatchClass& c = b->cls[k];
+    if (c.insts.empty()) continue;
+    const int R = kClassR[k];
+    BCK(launch_bsmall(R, 2, b->dev, c.gu, c.n_gu, nullptr, grid_for(c.n_gu, 2 * S), 0, 1, s),
+        "gram U0");
+    BCK(launch_bsmall(R, 3, b->dev, nullptr, (int)c.insts.size(), c.which, 0, 0, 3, s), "G0");
+  }
+  // V0 = M^T W0 (S = 0) for the instances without a given V0; a loaded V0 is
+  // kept: the sweep below writes copy 0 only for instances that need it, so
+  // run it on a class list restricted to them.
+  for (int k = 0; k < kClasses; ++k) {
+    BatchClass& c = b->cls[k];
+    if (c.insts.empty()) continue;
+    const int R = kClassR[k];
+    std::vector<BItem> mw0, p10;
+    for (int q : c.insts) {
+      if (b->have_init[q] == 2) continue;   // V0 given
+      const BInst& I = b->host[q];
+      for (int rb = 0; rb < I.n_rblocks; ++rb) mw0.push_back(BItem{q, rb, 0, 0});
+      for (int st = 0; st < I.n_strips; ++st) p10.push_back(BItem{q, st, 0, 0});
+    }
+    if (!mw0.empty()) {
+      BItem* dmw = upload(b, mw0);
+      BItem* dp1 = upload(b, p10);
+      if (!dmw || !dp1) return bfail(b, DCF_ENOMEM, "init lists");
+      BCK(launch_bsmall(R, 0, b->dev, dmw, (int)mw0.size(), nullptr,
+                        grid_for((int)mw0.size(), 4 * S), 0, 0, s), "W0");
+      BCK(launch_bpass(R, 1, b->dev, dp1, (int)p10.size(), grid_for((int)p10.size(), 2 * S),
+                       nullptr, 0, 0, 0, 1, s), "V0 sweep");
+    }
+    BCK(launch_bsmall(R, 2, b->dev, c.gv, c.n_gv, nullptr, grid_for(c.n_gv, 2 * S), 0, 2, s),
+        "gram V0");
+    BCK(launch_bsmall(R, 3, b->dev, nullptr, (int)c.insts.size(), c.which, 0, 0, 4, s), "Q0");
+  }
+  b->host_iter = 0;
+  b->initialized = true;
+  return DCF_OK;
+}
+
+// Time `reps` launches of one pass of one class (median, ms).
+float time_pass(dcf_batch b, int k, int which, int reps) {
+  BatchClass& c = b->cls[k];
+  const int R = kClassR[k];
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  std::vector<float> t;
+  for (int i = 0; i < reps; ++i) {
+    cudaEventRecord(e0, b->stream);
+    launch_bpass(R, which, b->dev, c.p1, c.n_p1, c.grid_p1, c.p2, c.n_p2, c.grid_p2, 0, 0,
+                 b->stream);
+    cudaEventRecord(e1, b->stream);
+    cudaEventSynchronize(e1);
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    t.push_back(ms);
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  std::sort(t.begin(), t.end());
+  return t[t.size() / 2];
+}
+
+// Autotuner: per rank class, the pass-1 grid and the pass-2 (split width, grid)
+// with the smallest median time; the state is at copy 0 with W valid.
+dcf_status batch_tune(dcf_batch b, int reps) {
+  const int S = b->num_sms;
+  char line[256];
+  b->tune_report.clear();
+  BCK(cudaStreamSynchronize(b->stream), "sync");
+  for (int k = 0; k < kClasses; ++k) {
+    BatchClass& c = b->cls[k];
+    if (c.insts.empty()) continue;
+    // W for copy 0 (the passes read it)
+    BCK(launch_bsmall(kClassR[k], 0, b->dev, c.mw, c.n_mw, nullptr, grid_for(c.n_mw, 4 * S), 0,
+                      0, b->stream), "tune W");
+    float best1 = 1e30f;
+    int g1best = c.grid_p1;
+    for (int mult : {1, 2, 3, 4}) {
+      c.grid_p1 = grid_for(c.n_p1, mult * S);
+      time_pass(b, k, 1, 1);
+      const float t = time_pass(b, k, 1, reps);
+      snprintf(line, sizeof(line), "R=%d pass1 grid=%d: %.4f ms\n", kClassR[k], c.grid_p1, t);
+      b->tune_report += line;
+      if (t < best1) { best1 = t; g1best = c.grid_p1; }
+    }
+    c.grid_p1 = g1best;
+    float best2 = 1e30f;
+    int sbest = c.split_cols, g2best = c.grid_p2;
+    for (int split : kSplitCandidates) {
+      set_split(b, c, split);
+      std::vector<BItem> v = p2_items(b, c, split);
+      BItem* d = upload(b, v);
+      if (!d) return bfail(b, DCF_ENOMEM, "tune lists");
+      c.p2 = d;
+      c.n_p2 = (int)v.size();
+      BCK(cudaMemcpyAsync(b->dev, b->host.data(), b->host.size() * sizeof(BInst),
+                          cudaMemcpyHostToDevice, b->stream), "descriptors");
+      for (int mult : {2, 4, 8}) {
+        c.grid_p2 = grid_for(c.n_p2, mult * S);
+        time_pass(b, k, 2, 1);
+        const float t = time_pass(b, k, 2, reps);
+        snprintf(line, sizeof(line), "R=%d pass2 split=%d grid=%d: %.4f ms\n", kClassR[k], split,
+                 c.grid_p2, t);
+        b->tune_report += line;
+        if (t < best2) { best2 = t; sbest = split; g2best = c.grid_p2; }
+      }
+    }
+    set_split(b, c, sbest);
+    std::vector<BItem> v = p2_items(b, c, sbest);
+    c.p2 = upload(b, v);
+    c.n_p2 = (int)v.size();
+    c.grid_p2 = g2best;
+    if (!c.p2) return bfail(b, DCF_ENOMEM, "tune lists");
+    snprintf(line, sizeof(line), "R=%d chosen: pass1 grid=%d, pass2 split=%d grid=%d\n",
+             kClassR[k], c.grid_p1, sbest, g2best);
+    b->tune_report += line;
+  }
+  BCK(cudaMemcpyAsync(b->dev, b->host.data(), b->host.size() * sizeof(BInst),
+                      cudaMemcpyHostToDevice, b->stream), "descriptors");
+  BCK(cudaStreamSynchronize(b->stream), "sync");
+  b->tuned = true;
+  return DCF_OK;
+}
+
+dcf_status build_batch_graphs(dcf_batch b) {
+  for (int p = 0; p < 2; ++p) {
+    if (b->graph[p]) continue;
+    cudaGraph_t g = nullptr;
+    BCK(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal), "begin capture");
+    cudaError_t e = enqueue_batch_iteration(b, p, b->stream);
+    cudaError_t e2 = cudaStreamEndCapture(b->stream, &g);
+    if (e != cudaSuccess) {
+      if (g) cudaGraphDestroy(g);
+      return bfail(b, DCF_ECUDA, std::string("capture: ") + cudaGetErrorString(e));
+    }
+    BCK(e2, "end capture");
+    cudaError_t e3 = cudaGraphInstantiate(&b->graph[p], g, 0);
+    cudaGraphDestroy(g);
+    BCK(e3, "instantiate");
+  }
+  return DCF_OK;
+}
+
+dcf_status batch_ready(dcf_batch b) {
+  dcf_status st = batch_init(b);
+  if (st != DCF_OK) return st;
+  if (!b->tuned) {
+    if ((st = batch_tune(b, 3)) != DCF_OK) return st;
+  }
+  return build_batch_graphs(b);
+}
+
+dcf_status read_states(dcf_batch b, std::vector<DevState>& out) {
+  out.resize(b->count);
+  for (int q = 0; q < b->count; ++q)
+    BCK(cudaMemcpyAsync(&out[q], b->host[q].st, sizeof(DevState), cudaMemcpyDeviceToHost,
+                        b->stream), "read state");
+  BCK(cudaStreamSynchronize(b->stream), "sync");
+  for (int q = 0; q < b->count; ++q)
+    if (out[q].status == DCF_ENONFINITE)
+      return bfail(b, DCF_ENONFINITE, "non-finite iterates in instance " + std::to_string(q));
+  return DCF_OK;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// entry points
+// ---------------------------------------------------------------------------
+extern "C" dcf_status dcf_batch_create(const dcf_problem* problems, int count, int max_iter,
+                                       double tol, uint64_t seed, dcf_batch* out) {
+  if (!out) return DCF_EINVAL;
+  *out = nullptr;
+  if (!problems || count < 1 || max_iter < 0 || !(tol >= 0)) return DCF_EINVAL;
+  for (int q = 0; q < count; ++q) {
+    const dcf_problem& p = problems[q];
+    if (p.m < 1 || p.E < 1 || !p.n_i || p.r < 1 || p.r > 32 || p.r > p.m) return DCF_EINVAL;
+    if (!(p.rho > 0) || !(p.lambda > 0)) return DCF_EINVAL;
+    int64_t n = 0;
+    for (int i = 0; i < p.E; ++i) {
+      if (p.n_i[i] < 1) return DCF_EINVAL;
+      n += p.n_i[i];
+    }
+    if (n < 1) return DCF_EINVAL;
+  }
+  dcf_batch b = new dcf_batch_s();
+  b->count = count;
+  b->max_iter = max_iter;
+  b->tol = tol;
+  b->seed = seed;
+  dcf::api::current_allocator(&b->alloc, &b->release, &b->alloc_ctx);
+  if (cudaGetDevice(&b->device) != cudaSuccess ||
+      cudaDeviceGetAttribute(&b->num_sms, cudaDevAttrMultiProcessorCount, b->device) !=
+          cudaSuccess ||
+      cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&b->ev_in, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&b->ev_out, cudaEventDisableTiming) != cudaSuccess ||
+      prepare_stream_kernels() != cudaSuccess || prepare_small_kernels() != cudaSuccess ||
+      prepare_batch_stream_kernels() != cudaSuccess) {
+    cudaGetLastError();
+    dcf_batch_destroy(b);
+    return DCF_ECUDA;
+  }
+  b->host.resize(count);
+  b->n_i.resize(count);
+  b->c_i.resize(count);
+  b->loaded.assign(count, 0);
+  b->have_init.assign(count, 0);
+  // descriptors (sizes first), then one arena for all per-instance buffers
+  for (int q = 0; q < count; ++q) {
+    const dcf_problem& p = problems[q];
+    BInst& I = b->host[q];
+    I = BInst{};
+    I.m = p.m;
+    I.E = p.E;
+    I.r = p.r;
+    I.R = pick_R(p.r);
+    I.lam = (float)p.lambda;
+    I.rho = (float)p.rho;
+    I.u_mode = 0;
+    b->n_i[q].assign(p.n_i, p.n_i + p.E);
+    b->c_i[q].resize(p.E);
+    int64_t n = 0;
+    for (int i = 0; i < p.E; ++i) {
+      b->c_i[q][i] = n;
+      n += p.n_i[i];
+    }
+    I.n = n;
+    I.n_strips = (int)((n + 63) / 64);
+    I.n_rblocks = (int)((I.m + 31) / 32);
+    I.n_gitems = (int)((n + kBGramRows - 1) / kBGramRows);
+    I.n_uitems = (int)((I.m + kBGramRows - 1) / kBGramRows);
+    I.split_cols = 1024;
+    I.nsplit = (int)((n + 1023) / 1024);
+  }
+  size_t mbytes = 0, wbytes = 0;
+  for (int q = 0; q < count; ++q) {
+    mbytes += ((size_t)b->host[q].m * b->host[q].n * 4 + 255) / 256 * 256;
+    Arena dry;
+    layout_instance(dry, b->host[q]);
+    wbytes += dry.used;
+  }
+  char* mbase = (char*)balloc(b, mbytes);
+  char* wbase = (char*)balloc(b, wbytes);
+  if (!mbase || !wbase) {
+    dcf_batch_destroy(b);
+    return DCF_ENOMEM;
+  }
+  {
+    Arena am{mbase, 0}, aw{wbase, 0};
+    for (int q = 0; q < count; ++q) {
+      BInst& I = b->host[q];
+      I.M = am.take<float>((size_t)I.m * I.n);
+      layout_instance(aw, I);
+    }
+  }
+  if (cudaMemsetAsync(wbase, 0, wbytes, b->stream) != cudaSuccess) {
+    cudaGetLastError();
+    dcf_batch_destroy(b);
+    return DCF_ECUDA;
+  }
+  // classes and their work lists
+  for (int q = 0; q < count; ++q) b->cls[class_of(b->host[q].r)].insts.push_back(q);
+  for (int k = 0; k < kClasses; ++k) {
+    BatchClass& c = b->cls[k];
+    if (c.insts.empty()) continue;
+    std::vector<BItem> mw, p1, gv, gu;
+    for (int q : c.insts) {
+      const BInst& I = b->host[q];
+      for (int rb = 0; rb < I.n_rblocks; ++rb) mw.push_back(BItem{q, rb, 0, 0});
+      for (int s = 0; s < I.n_strips; ++s) p1.push_back(BItem{q, s, 0, 0});
+      for (int g = 0; g < I.n_gitems; ++g) gv.push_back(BItem{q, g, 0, 0});
+      for (int g = 0; g < I.n_uitems; ++g) gu.push_back(BItem{q, g, 0, 0});
+    }
+    set_split(b, c, 1024);
+    std::vector<BItem> p2 = p2_items(b, c, 1024);
+    c.mw = upload(b, mw);  c.n_mw = (int)mw.size();
+    c.p1 = upload(b, p1);  c.n_p1 = (int)p1.size();
+    c.p2 = upload(b, p2);  c.n_p2 = (int)p2.size();
+    c.gv = upload(b, gv);  c.n_gv = (int)gv.size();
+    c.gu = upload(b, gu);  c.n_gu = (int)gu.size();
+    c.which = upload(b, c.insts);
+    c.grid_p1 = grid_for(c.n_p1, 2 * b->num_sms);
+    c.grid_p2 = grid_for(c.n_p2, 4 * b->num_sms);
+    if (!c.mw || !c.p1 || !c.p2 || !c.gv || !c.gu || !c.which) {
+      dcf_batch_destroy(b);
+      return DCF_ENOMEM;
+    }
+  }
+  b->dev = upload(b, b->host);
+  if (!b->dev || cudaStreamSynchronize(b->stream) != cudaSuccess) {
+    cudaGetLastError();
+    dcf_batch_destroy(b);
+    return DCF_ENOMEM;
+  }
+  *out = b;
+  return DCF_OK;
+}
+
+extern "C" dcf_status dcf_batch_set_stream(dcf_batch b, void* stream) {
+  if (!b) return DCF_EINVAL;
+  b->user_stream = (cudaStream_t)stream;
+  return DCF_OK;
+}
+
+extern "C" dcf_status dcf_batch_load(dcf_batch b, int i, const float* const* M_i,
+                                     const int64_t* ld_i, int where) {
+  if (!b) return DCF_EINVAL;
+  if (i < 0 || i >= b->count) return bfail(b, DCF_EINVAL, "instance index out of range");
+  if (!M_i || (where != 0 && where != 1)) return bfail(b, DCF_EINVAL, "blocks or where");
+  const BInst& I = b->host[i];
+  for (int k = 0; k < I.E; ++k) {
+    if (!M_i[k]) return bfail(b, DCF_EINVAL, "NULL block");
+    if (ld_i && ld_i[k] < I.m) return bfail(b, DCF_EINVAL, "leading dimension < m");
+  }
+  dcf_status st = batch_begin(b);
+  if (st != DCF_OK) return st;
+  const cudaMemcpyKind kind = where == 0 ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
+  for (int k = 0; k < I.E; ++k) {
+    const int64_t ld = ld_i ? ld_i[k] : I.m;
+    float* dst = const_cast<float*>(I.M) + b->c_i[i][k] * I.m;
+    BCK(cudaMemcpy2DAsync(dst, (size_t)I.m * 4, M_i[k], (size_t)ld * 4, (size_t)I.m * 4,
+                          (size_t)b->n_i[i][k], kind, b->stream), "copy M");
+  }
+  if (where == 0) BCK(cudaStreamSynchronize(b->stream), "sync");
+  b->loaded[i] = 1;
+  return batch_end(b);
+}
+
+extern "C" dcf_status dcf_batch_load_init(dcf_batch b, int i, const float* U0,
+                                          const float* const* V0_i, int where) {
+  if (!b) return DCF_EINVAL;
+  if (i < 0 || i >= b->count) return bfail(b, DCF_EINVAL, "instance index out of range");
+  if (!U0 || (where != 0 && where != 1)) return bfail(b, DCF_EINVAL, "U0 or where");
+  if (b->initialized) return bfail(b, DCF_ESTATE, "the batch has started");
+  const BInst& I = b->host[i];
+  dcf_status st = batch_begin(b);
+  if (st != DCF_OK) return st;
+  const cudaMemcpyKind kind = where == 0 ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
+  BCK(cudaMemcpy2DAsync(I.U[0], (size_t)I.R * 4, U0, (size_t)I.r * 4, (size_t)I.r * 4,
+                        (size_t)I.m, kind, b->stream), "copy U0");
+  b->have_init[i] = 1;
+  if (V0_i) {
+    for (int k = 0; k < I.E; ++k) {
+      if (!V0_i[k]) return bfail(b, DCF_EINVAL, "NULL V0 block");
+      BCK(cudaMemcpy2DAsync(I.V[0] + b->c_i[i][k] * I.R, (size_t)I.R * 4, V0_i[k],
+                            (size_t)I.r * 4, (size_t)I.r * 4, (size_t)b->n_i[i][k], kind,
+                            b->stream), "copy V0");
+    }
+    b->have_init[i] = 2;
+  }
+  if (where == 0) BCK(cudaStreamSynchronize(b->stream), "sync");
+  return batch_end(b);
+}
+
+extern "C" dcf_status dcf_batch_tune(dcf_batch b, int reps, char* report, int report_len) {
+  if (!b) return DCF_EINVAL;
+  if (reps < 1) return bfail(b, DCF_EINVAL, "reps < 1");
+  dcf_status st = batch_begin(b);
+  if (st != DCF_OK) return st;
+  if ((st = batch_init(b)) != DCF_OK) return st;
+  if (b->host_iter != 0) return bfail(b, DCF_ESTATE, "tune before the first step");
+  if ((st = batch_tune(b, reps)) != DCF_OK) return st;
+  for (int p = 0; p < 2; ++p) {
+    if (b->graph[p]) cudaGraphExecDestroy(b->graph[p]);
+    b->graph[p] = nullptr;
+  }
+  if (report && report_len > 0) {
+    snprintf(report, (size_t)report_len, "%s", b->tune_report.c_str());
+  }
+  return batch_end(b);
+}
+
+extern "C" dcf_status dcf_batch_step(dcf_batch b, int n_steps) {
+  if (!b) return DCF_EINVAL;
+  if (n_steps < 0) return bfail(b, DCF_EINVAL, "n_steps < 0");
+  dcf_status st = batch_begin(b);
+  if (st != DCF_OK) return st;
+  if ((st = batch_ready(b)) != DCF_OK) return st;
+  for (int i = 0; i < n_steps; ++i) {
+    BCK(cudaGraphLaunch(b->graph[b->host_iter & 1], b->stream), "graph launch");
+    b->host_iter++;
+  }
+  return batch_end(b);
+}
+
+extern "C" dcf_status dcf_batch_solve(dcf_batch b, int* iters_out, int* n_converged) {
+  if (!b) return DCF_EINVAL;
+  dcf_status st = batch_begin(b);
+  if (st != DCF_OK) return st;
+  if ((st = batch_ready(b)) != DCF_OK) return st;
+  // solve mode on, stop flags cleared
+  for (int q = 0; q < b->count; ++q) {
+    const int one = 1, zero = 0;
+    DevState* d = b->host[q].st;
+    BCK(cudaMemcpyAsync(&d->solve_mode, &one, sizeof(int), cudaMemcpyHostToDevice, b->stream), "w");
+    BCK(cudaMemcpyAsync(&d->tol, &b->tol, sizeof(double), cudaMemcpyHostToDevice, b->stream), "w");
+    BCK(cudaMemcpyAsync(&d->stop, &zero, sizeof(int), cudaMemcpyHostToDevice, b->stream), "w");
+  }
+  std::vector<DevState> ds;
+  if ((st = read_states(b, ds)) != DCF_OK) return st;
+  std::vector<int> start(b->count);
+  for (int q = 0; q < b->count; ++q) start[q] = ds[q].iter;
+  int done = 0, conv = 0;
+  while (done < b->max_iter) {
+    const int nb = std::min(8, b->max_iter - done);
+    for (int i = 0; i < nb; ++i) {
+      BCK(cudaGraphLaunch(b->graph[b->host_iter & 1], b->stream), "graph launch");
+      b->host_iter++;
+    }
+    done += nb;
+    if ((st = read_states(b, ds)) != DCF_OK) return st;
+    conv = 0;
+    for (int q = 0; q < b->count; ++q) conv += ds[q].stop ? 1 : 0;
+    if (conv == b->count) break;
+  }
+  if (iters_out)
+    for (int q = 0; q < b->count; ++q) iters_out[q] = ds[q].iter - start[q];
+  if (n_converged) *n_converged = conv;
+  for (int q = 0; q < b->count; ++q) {
+    const int zero = 0;
+    BCK(cudaMemcpyAsync(&b->host[q].st->solve_mode, &zero, sizeof(int), cudaMemcpyHostToDevice,
+                        b->stream), "w");
+  }
+  if ((st = batch_end(b)) != DCF_OK) return st;
+  return conv == b->count ? DCF_OK : DCF_ENOTCONV;
+}
+
+extern "C" dcf_status dcf_batch_get_factors(dcf_batch b, int i, float* U, float* const* V_i,
+                                            int where) {
+  if (!b) return DCF_EINVAL;
+  if (i < 0 || i >= b->count) return bfail(b, DCF_EINVAL, "instance index out of range");
+  if (where != 0 && where != 1) return bfail(b, DCF_EINVAL, "where must be 0 or 1");
+  dcf_status st = batch_begin(b);
+  if (st != DCF_OK) return st;
+  if ((st = batch_init(b)) != DCF_OK) return st;
+  const BInst& I = b->host[i];
+  DevState ds{};
+  BCK(cudaMemcpyAsync(&ds, I.st, sizeof(DevState), cudaMemcpyDeviceToHost, b->stream), "state");
+  BCK(cudaStreamSynchronize(b->stream), "sync");
+  const int cur = ds.iter & 1;   // a stopped instance keeps the copy it stopped in
+  const cudaMemcpyKind kind = where == 0 ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
+  if (U)
+    BCK(cudaMemcpy2DAsync(U, (size_t)I.r * 4, I.U[cur], (size_t)I.R * 4, (size_t)I.r * 4,
+                          (size_t)I.m, kind, b->stream), "copy U");
+  if (V_i) {
+    for (int k = 0; k < I.E; ++k) {
+      if (!V_i[k]) continue;
+      BCK(cudaMemcpy2DAsync(V_i[k], (size_t)I.r * 4, I.V[cur] + b->c_i[i][k] * I.R,
+                            (size_t)I.R * 4, (size_t)I.r * 4, (size_t)b->n_i[i][k], kind,
+                            b->stream), "copy V");
+    }
+  }
+  if (where == 0) BCK(cudaStreamSynchronize(b->stream), "sync");
+  return batch_end(b);
+}
+
+extern "C" dcf_status dcf_batch_get_stats(dcf_batch b, int i, double* objective, double* dL_rel,
+                                          int* iter) {
+  if (!b) return DCF_EINVAL;
+  if (i < 0 || i >= b->count) return bfail(b, DCF_EINVAL, "instance index out of range");
+  dcf_status st = batch_begin(b);
+  if (st != DCF_OK) return st;
+  if ((st = batch_init(b)) != DCF_OK) return st;
+  DevState ds{};
+  BCK(cudaMemcpyAsync(&ds, b->host[i].st, sizeof(DevState), cudaMemcpyDeviceToHost, b->stream),
+      "state");
+  BCK(cudaStreamSynchronize(b->stream), "sync");
+  if (ds.status == DCF_ENONFINITE) return bfail(b, DCF_ENONFINITE, "non-finite iterates");
+  if (objective) *objective = ds.objective;
+  if (dL_rel) *dL_rel = ds.dL_rel;
+  if (iter) *iter = ds.iter;
+  return batch_end(b);
+}
+
+extern "C" const char* dcf_batch_last_error(dcf_batch b) {
+  return b ? b->err.c_str() : "NULL batch";
+}
+
+extern "C" void dcf_batch_destroy(dcf_batch b) {
+  if (!b) return;
+  if (b->stream) cudaStreamSynchronize(b->stream);
+  for (int p = 0; p < 2; ++p)
+    if (b->graph[p]) cudaGraphExecDestroy(b->graph[p]);
+  bfree_all(b);
+  if (b->ev_in) cudaEventDestroy(b->ev_in);
+  if (b->ev_out) cudaEventDestroy(b->ev_out);
+  if (b->stream) cudaStreamDestroy(b->stream);
+  delete b;
+}
+
+extern "C" dcf_status dcf_batch_profile_step(dcf_batch b, int n_steps, double* phase_ms,
+                                             int n_phases) {
+  if (!b) return DCF_EINVAL;
+  if (n_steps < 1 || !phase_ms || n_phases < kNumBatchPhases)
+    return bfail(b, DCF_EINVAL, "n_steps < 1 or phase_ms too short");
+  dcf_status st = batch_begin(b);
+  if (st != DCF_OK) return st;
+  if ((st = batch_ready(b)) != DCF_OK) return st;
+  cudaEvent_t ev[kNumBatchPhases + 1];
+  for (auto& x : ev) BCK(cudaEventCreate(&x), "event");
+  for (int p = 0; p < kNumBatchPhases; ++p) phase_ms[p] = 0.0;
+  for (int i = 0; i < n_steps; ++i) {
+    BCK(cudaEventRecord(ev[kNumBatchPhases], b->stream), "record");
+    BCK(enqueue_batch_iteration(b, b->host_iter & 1, b->stream, ev), "profiled iteration");
+    b->host_iter++;
+    BCK(cudaEventSynchronize(ev[kNumBatchPhases - 1]), "sync");
+    float prev = 0.f;
+    for (int p = 0; p < kNumBatchPhases; ++p) {
+      float ms = 0.f;
+      BCK(cudaEventElapsedTime(&ms, ev[kNumBatchPhases], ev[p]), "elapsed");
+      phase_ms[p] += ms - prev;
+      prev = ms;
+    }
+  }
+  for (auto& x : ev) cudaEventDestroy(x);
+  return batch_end(b);
+}

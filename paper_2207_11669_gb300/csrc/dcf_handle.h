@@ -80,6 +80,8 @@ namespace api {
 dcf_status fail(dcf_handle h, dcf_status code, const std::string& msg);
 dcf_status cuda_fail(dcf_handle h, cudaError_t e, const char* what);
 void* dev_alloc(dcf_handle h, size_t bytes);
+// The allocator hook set by dcf_set_allocator (NULL: cudaMalloc / cudaFree).
+void current_allocator(dcf_alloc_fn* alloc, dcf_free_fn* release, void** ctx);
 IterArgs iter_args(dcf_handle h, int cur);
 cudaError_t enqueue_iteration(dcf_handle h, int cur, cudaStream_t s, cudaEvent_t* ev);
 dcf_status begin_work(dcf_handle h);

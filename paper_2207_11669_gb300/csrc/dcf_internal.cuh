@@ -73,6 +73,78 @@ struct IterArgs {
   float* ustar_out;  // optional m x R copy of U* (learned network checkpoints)
 };
 
+// ---------------------------------------------------------------------------
+// Batches of independent problems (dcf_batch_*): one descriptor per instance
+// and, per kernel, a list of work items; a persistent grid walks the list.
+// ---------------------------------------------------------------------------
+struct BInst {
+  const float* M;    // m x n, column-major
+  int64_t m, n;
+  int r, R, E, u_mode;
+  float lam, rho;
+  float* U[2];
+  float* V[2];
+  float* W;
+  float* part_p;     // [nsplit][m][R]
+  int nsplit;
+  int64_t split_cols;
+  double* part_h;    // [n_strips]       Huber partial per 64-column strip
+  float2* part_q;    // [n_gitems][R*R]  Gram partials (V'^T V', or U^T U at the start)
+  float2* part_xv;   // [n_gitems][R*R]
+  int n_gitems;      // Gram items over the n rows of V
+  int n_uitems;      // Gram items over the m rows of U (start point)
+  float2* part_g;    // [n_rblocks][R*R]
+  float2* part_xu;   // [n_rblocks][R*R]
+  int n_rblocks;     // 32-row blocks of U
+  int n_strips;      // 64-column strips of M
+  double* red;       // 4 R*R + 8 doubles: reduced Q, X_v, Huber, G, X_u
+  Smalls* sm;
+  DevState* st;
+};
+// Work item: instance and two indices whose meaning depends on the kernel
+// (strip; row block and column split; Gram chunk; 32-row block).
+struct BItem {
+  int inst;
+  int a;
+  int b;
+  int pad_;
+};
+constexpr int kBGramRows = 512;   // rows of V (or U) per Gram item
+
+// The single-problem argument block of instance I (for the shared per-item code).
+__device__ __forceinline__ IterArgs batch_iter_args(const BInst& I, int cur) {
+  IterArgs a{};
+  a.cur = cur;
+  a.M = I.M;
+  a.m = I.m;
+  a.n = I.n;
+  a.r = I.r;
+  a.R = I.R;
+  a.lam = I.lam;
+  a.rho = I.rho;
+  a.u_mode = I.u_mode;
+  a.E = I.E;
+  a.U[0] = I.U[0]; a.U[1] = I.U[1];
+  a.V[0] = I.V[0]; a.V[1] = I.V[1];
+  a.W = I.W;
+  a.part_q = I.part_q;
+  a.part_xv = I.part_xv;
+  a.part_h = I.part_h;
+  a.part_p = I.part_p;
+  a.n_vblocks = I.n_strips;
+  a.n_splits = I.nsplit;
+  a.split_cols = I.split_cols;
+  a.part_g = I.part_g;
+  a.part_xu = I.part_xu;
+  a.n_rblocks = I.n_rblocks;
+  a.sm = I.sm;
+  a.st = I.st;
+  a.add_uxv = 0;
+  a.alpha = 1.0f;
+  a.ustar_out = nullptr;
+  return a;
+}
+
 // Launchers (stream-ordered; return cudaGetLastError()).
 // Gram partials part[b][k*cy + l] = sum over the rows of CTA b of X[a,k] Y[a,l],
 // as compensated pairs (hi, lo).
@@ -96,6 +168,18 @@ cudaError_t launch_pass1(const IterArgs& a, int grid, int mode_init, int out_cop
                          cudaStream_t s);
 cudaError_t launch_pass2(const IterArgs& a, cudaStream_t s);
 cudaError_t prepare_stream_kernels();
+// Batched kernels over work-item lists (R = 8, 16 or 32).
+//   launch_bpass: which = 1 pass 1 over it1 (mode_init: the S = 0 sweep into copy 0),
+//                 which = 2 pass 2 over it2
+//   launch_bsmall: kind 0 make_w (arg: respect stop), 1 U-step rows, 2 Gram
+//                  (arg: BG_* mode), 3 reduction + tail, one CTA per entry of
+//                  `which` (nitems = its length, arg: tail kind)
+cudaError_t launch_bpass(int R, int which, const BInst* insts, const BItem* it1, int n1, int grid1,
+                         const BItem* it2, int n2, int grid2, int cur, int mode_init,
+                         cudaStream_t s);
+cudaError_t launch_bsmall(int R, int kind, const BInst* insts, const BItem* items, int nitems,
+                          const int* which, int grid, int cur, int arg, cudaStream_t s);
+cudaError_t prepare_batch_stream_kernels();
 cudaError_t prepare_small_kernels();
 cudaError_t launch_materialize(const float* M, int64_t m, int64_t c0, int64_t ni,
                                const float* U, const float* V, int R, float lam,

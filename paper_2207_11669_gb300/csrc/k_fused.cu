@@ -64,8 +64,7 @@ struct FL {  // shared-memory layout (bytes)
   static constexpr int PIMG = VIMG + VBYTES;                     // 2 V' images
   static constexpr int YBYTES = kFW * R * 4;                     // one column-sum block
   static constexpr int YPART = PIMG + 2 * PBYTES;                // 2 x (64 x R fp32)
-  static constexpr int ZM = YPART + 2 * YBYTES;                  // R x R fp32
-  static constexpr int STG = ZM + R * R * 4;                     // 2R x 4 fp16 image chunk
+  static constexpr int STG = YPART + 2 * YBYTES;                 // 2R x 4 fp16 image chunk
   static constexpr int BAR = STG + 2 * (2 * R * kChunk * 2);     // mbarriers (2 staging chunks)
   static constexpr int NBAR = 2 * NST + 29;
   static constexpr int TSLOT = BAR + NBAR * 8;
@@ -144,7 +143,6 @@ __global__ void __launch_bounds__(kFThreads, 1)
             b_g3done = b_d2empty + 2, b_yfull = b_g3done + 2, b_yfree = b_yfull + 2,
             b_pfull = b_yfree + 2, b_pfree = b_pfull + 2, b_img = b_pfree + 2,
             b_last = b_img + 1;
-  float* zm = reinterpret_cast<float*>(smem + L::ZM);
   double* red = reinterpret_cast<double*>(smem + L::RED);
   int err = 0;
   const uint64_t deadline = tc::globaltimer_ns() + kDeadlineNs;
@@ -189,7 +187,6 @@ __global__ void __launch_bounds__(kFThreads, 1)
     tc::fence_mbar_init();
     tc::prefetch_tmap(&tmap);
   }
-  for (int i = tid; i < R * R; i += kFThreads) zm[i] = a.zmat[i];
   tc::fence_before_sync();
   __syncthreads();
   tc::fence_after_sync();

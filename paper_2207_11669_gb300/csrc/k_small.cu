@@ -108,15 +108,15 @@ struct GvvCfg {
   static constexpr size_t smem_bytes = 2 * (size_t)CH * R * 4;
 };
 
+// Rows [a0, a1) of one problem; writes the R*R partials at out_q, out_xv.
+// Block-wide (256 threads); gsh: GvvCfg smem.
 template <int R>
-__global__ void __launch_bounds__(256)
-k_gram_vv(const float* __restrict__ Vo, const float* __restrict__ Vn, int64_t N,
-          int64_t rows_per_cta, float2* __restrict__ part_q, float2* __restrict__ part_xv,
-          const DevState* st) {
+__device__ __forceinline__ void gram_vv_block(const float* __restrict__ Vo,
+                                              const float* __restrict__ Vn, int64_t a0,
+                                              int64_t a1, float2* __restrict__ out_q,
+                                              float2* __restrict__ out_xv, float* gsh) {
   using C = GvvCfg<R>;
   constexpr int TB = C::TB, NT = C::NT, G = C::GROUPS, CH = C::CH;
-  if (st->stop) return;
-  extern __shared__ __align__(16) float gsh[];
   float* So = gsh;              // [CH][R]  V_old rows
   float* Sn = gsh + CH * R;     // [CH][R]  V' rows
   const int tid = threadIdx.x;
@@ -127,8 +127,6 @@ k_gram_vv(const float* __restrict__ Vo, const float* __restrict__ Vn, int64_t N,
   for (int i = 0; i < TB; ++i)
 #pragma unroll
     for (int j = 0; j < TB; ++j) { qh[i][j] = ql[i][j] = xh[i][j] = xl[i][j] = 0.f; }
-  const int64_t a0 = (int64_t)blockIdx.x * rows_per_cta;
-  const int64_t a1 = min(N, a0 + rows_per_cta);
   for (int64_t c = a0; c < a1; c += CH) {
     const int rows = (int)dmin64((int64_t)CH, a1 - c);
     __syncthreads();
@@ -189,16 +187,28 @@ k_gram_vv(const float* __restrict__ Vo, const float* __restrict__ Vn, int64_t N,
     }
   }
   if (grp == 0) {
-    const int64_t base = (int64_t)blockIdx.x * R * R;
 #pragma unroll
     for (int i = 0; i < TB; ++i)
 #pragma unroll
       for (int j = 0; j < TB; ++j) {
         const int e = (k0 + i) * R + l0 + j;
-        part_q[base + e] = make_float2(qh[i][j], ql[i][j]);
-        part_xv[base + e] = make_float2(xh[i][j], xl[i][j]);
+        out_q[e] = make_float2(qh[i][j], ql[i][j]);
+        out_xv[e] = make_float2(xh[i][j], xl[i][j]);
       }
   }
+}
+
+template <int R>
+__global__ void __launch_bounds__(256)
+k_gram_vv(const float* __restrict__ Vo, const float* __restrict__ Vn, int64_t N,
+          int64_t rows_per_cta, float2* __restrict__ part_q, float2* __restrict__ part_xv,
+          const DevState* st) {
+  if (st->stop) return;
+  extern __shared__ __align__(16) float gsh[];
+  const int64_t a0 = (int64_t)blockIdx.x * rows_per_cta;
+  const int64_t a1 = min(N, a0 + rows_per_cta);
+  const int64_t base = (int64_t)blockIdx.x * R * R;
+  gram_vv_block<R>(Vo, Vn, a0, a1, part_q + base, part_xv + base, gsh);
 }
 
 // ---------------------------------------------------------------------------
@@ -403,17 +413,15 @@ __device__ void tail_g(const ReduceArgs& a, double* A, float* F) {
 constexpr int kRowsPerCta = 32;
 
 // W = U (U^T U + rho I)^{-1}
+// Rows [32 rb, 32 rb + 32) of W = U G^{-1}; block-wide (256 threads).
 template <int R>
-__global__ void __launch_bounds__(256) k_make_w(const float* __restrict__ U,
-                                                const DevState* st, const Smalls* sm,
-                                                float* __restrict__ W, int64_t m,
-                                                int respect_stop) {
-  if (respect_stop && st->stop) return;
+__device__ __forceinline__ void make_w_block(const float* __restrict__ U, const Smalls* sm,
+                                             float* __restrict__ W, int64_t m, int64_t rb) {
   constexpr int CG = R / 8;
   __shared__ __align__(16) float Gi[R * R];
   __shared__ __align__(16) float Us[kRowsPerCta * R];
   const int tid = threadIdx.x;
-  const int64_t row0 = (int64_t)blockIdx.x * kRowsPerCta;
+  const int64_t row0 = rb * kRowsPerCta;
   for (int i = tid; i < R * R; i += 256) Gi[i] = sm->ginv32[i];
   for (int i = tid; i < kRowsPerCta * R; i += 256) {
     int64_t a = row0 + i / R;
@@ -435,13 +443,22 @@ __global__ void __launch_bounds__(256) k_make_w(const float* __restrict__ U,
   for (int l = 0; l < CG; ++l) W[a * R + g * CG + l] = acc[l];
 }
 
+template <int R>
+__global__ void __launch_bounds__(256) k_make_w(const float* __restrict__ U,
+                                                const DevState* st, const Smalls* sm,
+                                                float* __restrict__ W, int64_t m,
+                                                int respect_stop) {
+  if (respect_stop && st->stop) return;
+  make_w_block<R>(U, sm, W, m, blockIdx.x);
+}
+
 // Consensus U-update plus Gram partials of the new U:
 //   exact:  U_t[a,:] = P[a,:] (Q_t + rho I)^{-1},  P[a,:] = sum_s part_p[s][a,:]
 //   FedAvg: U_t[a,:] = U[a,:] - (eta_t/E) (U[a,:] (Q_t + rho I) - P[a,:])
+// 32-row block rb of the U-step and its Gram partials; block-wide (256 threads).
 template <int R>
-__global__ void __launch_bounds__(256) k_rows(IterArgs a) {
+__device__ __forceinline__ void rows_block(const IterArgs& a, int64_t rb) {
   DevState* st = a.st;
-  if (st->stop) return;
   constexpr int CG = R / 8;
   __shared__ __align__(16) float Mat[R * R];
   __shared__ __align__(16) float Ps[kRowsPerCta * R];
@@ -451,7 +468,7 @@ __global__ void __launch_bounds__(256) k_rows(IterArgs a) {
   const int cur = a.cur, nxt = cur ^ 1;
   const float* U = a.U[cur];
   float* Unew = a.U[nxt];
-  const int64_t row0 = (int64_t)blockIdx.x * kRowsPerCta;
+  const int64_t row0 = rb * kRowsPerCta;
   const int rows = (int)dmin64((int64_t)kRowsPerCta, a.m - row0);
   if (a.add_uxv)
     for (int i = tid; i < R * R; i += 256) Mat[i] = (float)a.sm->xv[i];
@@ -533,9 +550,130 @@ __global__ void __launch_bounds__(256) k_rows(IterArgs a) {
       gg = fmaf(Un[rr * R + k], Un[rr * R + l], gg);
       xu = fmaf(Uo[rr * R + k], Un[rr * R + l], xu);
     }
-    a.part_g[(int64_t)blockIdx.x * R * R + e] = make_float2(gg, 0.f);
-    a.part_xu[(int64_t)blockIdx.x * R * R + e] = make_float2(xu, 0.f);
+    a.part_g[rb * R * R + e] = make_float2(gg, 0.f);
+    a.part_xu[rb * R * R + e] = make_float2(xu, 0.f);
   }
+}
+
+template <int R>
+__global__ void __launch_bounds__(256) k_rows(IterArgs a) {
+  if (a.st->stop) return;
+  rows_block<R>(a, blockIdx.x);
+}
+
+// ---------------------------------------------------------------------------
+// Batches of independent problems: the per-item functions above, driven by
+// work-item lists, and one reduction CTA per instance.
+// ---------------------------------------------------------------------------
+enum BGramMode { BG_ITER = 0, BG_INIT_U = 1, BG_INIT_V = 2 };
+
+template <int R>
+__global__ void __launch_bounds__(256) k_bmake_w(const BInst* __restrict__ insts,
+                                                 const BItem* __restrict__ items, int nitems,
+                                                 int cur, int respect_stop) {
+  for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
+    const BItem w = items[it];
+    const BInst& I = insts[w.inst];
+    if (respect_stop && I.st->stop) continue;
+    __syncthreads();
+    make_w_block<R>(I.U[cur], I.sm, I.W, I.m, w.a);
+  }
+}
+
+template <int R>
+__global__ void __launch_bounds__(256) k_brows(const BInst* __restrict__ insts,
+                                               const BItem* __restrict__ items, int nitems,
+                                               int cur) {
+  for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
+    const BItem w = items[it];
+    const BInst& I = insts[w.inst];
+    if (I.st->stop) continue;
+    const IterArgs a = batch_iter_args(I, cur);
+    __syncthreads();
+    rows_block<R>(a, w.a);
+  }
+}
+
+// Gram items: BG_ITER  Q = V'^T V', X_v = V^T V'   (item a: chunk of kBGramRows rows of V)
+//             BG_INIT_U  U0^T U0 into part_q          (chunks of the m rows of U)
+//             BG_INIT_V  V0^T V0 into part_q
+template <int R>
+__global__ void __launch_bounds__(256) k_bgram(const BInst* __restrict__ insts,
+                                               const BItem* __restrict__ items, int nitems,
+                                               int cur, int mode) {
+  extern __shared__ __align__(16) float gsh[];
+  for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
+    const BItem w = items[it];
+    const BInst& I = insts[w.inst];
+    if (mode == BG_ITER && I.st->stop) continue;
+    const float* X = mode == BG_ITER ? I.V[cur] : mode == BG_INIT_U ? I.U[0] : I.V[0];
+    const float* Y = mode == BG_ITER ? I.V[cur ^ 1] : X;
+    const int64_t N = mode == BG_INIT_U ? I.m : I.n;
+    const int64_t a0 = (int64_t)w.a * kBGramRows;
+    const int64_t a1 = min(N, a0 + (int64_t)kBGramRows);
+    __syncthreads();
+    gram_vv_block<R>(X, Y, a0, a1, I.part_q + (int64_t)w.a * R * R,
+                     I.part_xv + (int64_t)w.a * R * R, gsh);
+  }
+}
+
+// One CTA per instance (list `which`): reduce the instance's partials in
+// compensated FP32 pairs, store them in FP64, then run the r x r tail.
+//   tail TAIL_Q      Q, X_v (Gram items), Huber (strips)  -> (Q + rho I)^{-1}
+//   tail TAIL_G      G, X_u (32-row blocks)               -> metrics, stop, (G + rho I)^{-1}
+//   tail TAIL_INIT_G U0^T U0 (Gram items over m rows);  TAIL_INIT_Q  V0^T V0
+template <int R>
+__global__ void __launch_bounds__(256) k_breduce(const BInst* __restrict__ insts,
+                                                 const int* __restrict__ which, int cur,
+                                                 int tail) {
+  const BInst& I = insts[which[blockIdx.x]];
+  if ((tail == TAIL_Q || tail == TAIL_G) && I.st->stop) return;
+  constexpr int RR = R * R;
+  double* red = I.red;
+  double* out0 = tail == TAIL_G ? red + 2 * RR + 8 : red;
+  double* out1 = tail == TAIL_G ? red + 3 * RR + 8 : red + RR;
+  const float2* p0 = tail == TAIL_G ? I.part_g : I.part_q;
+  const float2* p1 = tail == TAIL_G ? I.part_xu : I.part_xv;
+  const int np = tail == TAIL_G ? I.n_rblocks : tail == TAIL_INIT_G ? I.n_uitems : I.n_gitems;
+  const bool two = tail == TAIL_Q || tail == TAIL_G;
+  for (int e = threadIdx.x; e < RR; e += blockDim.x) {
+    float h0 = 0.f, l0 = 0.f, h1 = 0.f, l1 = 0.f;
+    for (int q = 0; q < np; ++q) {
+      const float2 v0 = p0[(int64_t)q * RR + e];
+      two_sum_add(h0, l0, v0.x);
+      l0 += v0.y;
+      if (two) {
+        const float2 v1 = p1[(int64_t)q * RR + e];
+        two_sum_add(h1, l1, v1.x);
+        l1 += v1.y;
+      }
+    }
+    out0[e] = (double)h0 + (double)l0;
+    if (two) out1[e] = (double)h1 + (double)l1;
+  }
+  if (tail == TAIL_Q && threadIdx.x < 32) {
+    double hs = 0.0;
+    for (int q = threadIdx.x; q < I.n_strips; q += 32) hs += I.part_h[q];
+    for (int o = 16; o > 0; o >>= 1) hs += __shfl_xor_sync(0xffffffffu, hs, o);
+    if (threadIdx.x == 0) red[2 * RR] = hs;
+  }
+  __threadfence();
+  __syncthreads();
+  ReduceArgs ra{};
+  ra.out[0] = out0;
+  ra.out[1] = out1;
+  ra.out[2] = red + 2 * RR;
+  ra.tail = tail;
+  ra.R = R;
+  ra.rho = I.rho;
+  ra.u_mode = I.u_mode;
+  ra.copy = (tail == TAIL_INIT_G || tail == TAIL_INIT_Q) ? 0 : cur;
+  ra.sm = I.sm;
+  ra.st = I.st;
+  extern __shared__ double dsh[];   // R*R doubles, then R*R floats
+  float* F = reinterpret_cast<float*>(dsh + RR);
+  if (tail == TAIL_Q || tail == TAIL_INIT_Q) tail_q(ra, dsh, F);
+  else tail_g(ra, dsh, F);
 }
 
 // ---------------------------------------------------------------------------
@@ -615,6 +753,31 @@ cudaError_t launch_gram_vv(int R, const float* Vo, const float* Vn, int64_t N, f
     case 16: return gram_vv_T<16>(Vo, Vn, N, part_q, part_xv, nparts, st, s);
     case 32: return gram_vv_T<32>(Vo, Vn, N, part_q, part_xv, nparts, st, s);
     default: return gram_vv_T<64>(Vo, Vn, N, part_q, part_xv, nparts, st, s);
+  }
+}
+
+// Batched launchers.  kind: 0 make_w, 1 rows, 2 gram (mode), 3 reduce (tail)
+template <int R>
+static cudaError_t bsmall_T(int kind, const BInst* insts, const BItem* items, int nitems,
+                            const int* which, int grid, int cur, int arg, cudaStream_t s) {
+  if (nitems == 0) return cudaSuccess;
+  switch (kind) {
+    case 0: k_bmake_w<R><<<grid, 256, 0, s>>>(insts, items, nitems, cur, arg); break;
+    case 1: k_brows<R><<<grid, 256, 0, s>>>(insts, items, nitems, cur); break;
+    case 2: k_bgram<R><<<grid, 256, GvvCfg<R>::smem_bytes, s>>>(insts, items, nitems, cur, arg); break;
+    default:
+      k_breduce<R><<<nitems, 256, (size_t)R * R * 12, s>>>(insts, which, cur, arg);
+      break;
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_bsmall(int R, int kind, const BInst* insts, const BItem* items, int nitems,
+                          const int* which, int grid, int cur, int arg, cudaStream_t s) {
+  switch (R) {
+    case 8: return bsmall_T<8>(kind, insts, items, nitems, which, grid, cur, arg, s);
+    case 16: return bsmall_T<16>(kind, insts, items, nitems, which, grid, cur, arg, s);
+    default: return bsmall_T<32>(kind, insts, items, nitems, which, grid, cur, arg, s);
   }
 }
 

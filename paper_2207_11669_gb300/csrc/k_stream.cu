@@ -43,13 +43,13 @@ struct P1Cfg {
   static constexpr size_t smem_floats = (size_t)kP1Cols * (RC + 1) + 2 * (size_t)RC * R;
 };
 
+// One 64-column strip s of one problem: X and V'[strip] = X^T W, Huber sum
+// added to (hub_hi, hub_lo).  Block-wide (256 threads); sh: P1Cfg smem.
 template <int R>
-__global__ void __launch_bounds__(256) k_pass1(IterArgs a, int mode_init, int out_copy) {
-  DevState* st = a.st;
-  if (!mode_init && st->stop) return;
+__device__ __forceinline__ void pass1_strip(const IterArgs& a, int mode_init, int out_copy,
+                                            int64_t s, float* sh, float& hub_hi, float& hub_lo) {
   using C = P1Cfg<R>;
   constexpr int RC = C::RC, KQ = C::KQ, LDM = RC + 1;
-  extern __shared__ __align__(16) float sh[];
   float* Mt = sh;                              // [64][RC+1]   M, then X
   float* Us = Mt + kP1Cols * LDM;              // [RC][R]
   float* Ws = Us + RC * R;                     // [RC][R]
@@ -61,9 +61,7 @@ __global__ void __launch_bounds__(256) k_pass1(IterArgs a, int mode_init, int ou
   float* Vout = a.V[mode_init ? out_copy : (cur ^ 1)];
   const float lam = a.lam;
   const int64_t m = a.m, n = a.n;
-  const int64_t nstrips = (n + kP1Cols - 1) / kP1Cols;
-  float hub_hi = 0.f, hub_lo = 0.f;
-  for (int64_t s = blockIdx.x; s < nstrips; s += gridDim.x) {
+  {
     const int64_t col = s * kP1Cols + j;
     const bool valid = col < n;
     float v[R];
@@ -132,15 +130,51 @@ __global__ void __launch_bounds__(256) k_pass1(IterArgs a, int mode_init, int ou
       for (int kk = 0; kk < KQ; ++kk) Vout[col * R + q * KQ + kk] = yhi[kk] + ylo[kk];
     }
   }
-  // Huber partial of this CTA
+}
+
+// Sum of (hi + lo) over the CTA into *out (thread 0); block-wide.
+__device__ __forceinline__ void block_huber(float hub_hi, float hub_lo, double* out) {
   __shared__ double red[256];
+  const int tid = threadIdx.x;
+  __syncthreads();
   red[tid] = (double)hub_hi + (double)hub_lo;
   __syncthreads();
   for (int w = 128; w > 0; w >>= 1) {
     if (tid < w) red[tid] += red[tid + w];
     __syncthreads();
   }
-  if (tid == 0 && !mode_init) a.part_h[blockIdx.x] = red[0];
+  if (tid == 0) *out = red[0];
+}
+
+template <int R>
+__global__ void __launch_bounds__(256) k_pass1(IterArgs a, int mode_init, int out_copy) {
+  DevState* st = a.st;
+  if (!mode_init && st->stop) return;
+  extern __shared__ __align__(16) float sh[];
+  const int64_t nstrips = (a.n + kP1Cols - 1) / kP1Cols;
+  float hub_hi = 0.f, hub_lo = 0.f;
+  for (int64_t s = blockIdx.x; s < nstrips; s += gridDim.x)
+    pass1_strip<R>(a, mode_init, out_copy, s, sh, hub_hi, hub_lo);
+  // Huber partial of this CTA
+  if (!mode_init) block_huber(hub_hi, hub_lo, a.part_h + blockIdx.x);
+}
+
+// Batched pass 1: item (instance, strip); the Huber partial goes to the strip.
+template <int R>
+__global__ void __launch_bounds__(256) k_bpass1(const BInst* __restrict__ insts,
+                                                const BItem* __restrict__ items, int nitems,
+                                                int cur, int mode_init) {
+  extern __shared__ __align__(16) float sh[];
+  for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
+    const BItem w = items[it];
+    const BInst& I = insts[w.inst];
+    if (!mode_init && I.st->stop) continue;   // uniform over the CTA
+    const IterArgs a = batch_iter_args(I, cur);
+    float hub_hi = 0.f, hub_lo = 0.f;
+    __syncthreads();                           // shared memory of the previous item
+    pass1_strip<R>(a, mode_init, cur, w.a, sh, hub_hi, hub_lo);
+    if (!mode_init) block_huber(hub_hi, hub_lo, I.part_h + w.a);
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -149,10 +183,10 @@ __global__ void __launch_bounds__(256) k_pass1(IterArgs a, int mode_init, int ou
 constexpr int kP2Rows = 128;
 constexpr int kP2Cols = 32;
 
+// One (128-row block rb) x (column split sp) item of one problem: P partial.
+// Block-wide (256 threads).
 template <int R>
-__global__ void __launch_bounds__(256) k_pass2(IterArgs a) {
-  DevState* st = a.st;
-  if (st->stop) return;
+__device__ __forceinline__ void pass2_block(const IterArgs& a, int64_t rb, int64_t sp) {
   constexpr int KH = R / 2;
   __shared__ __align__(16) float Mt[kP2Cols * kP2Rows];
   __shared__ __align__(16) float Vo[kP2Cols * R];
@@ -165,10 +199,10 @@ __global__ void __launch_bounds__(256) k_pass2(IterArgs a) {
   const float* Vnew = a.V[cur ^ 1];
   const float lam = a.lam;
   const int64_t m = a.m, n = a.n;
-  const int64_t a0 = (int64_t)blockIdx.x * kP2Rows;
+  const int64_t a0 = rb * kP2Rows;
   const int64_t arow = a0 + ar;
   const bool rvalid = arow < m;
-  const int64_t c_begin = (int64_t)blockIdx.y * a.split_cols;
+  const int64_t c_begin = sp * a.split_cols;
   const int64_t c_end = min(n, c_begin + a.split_cols);
   float u[R];
 #pragma unroll
@@ -220,9 +254,30 @@ __global__ void __launch_bounds__(256) k_pass2(IterArgs a) {
     for (int kk = 0; kk < KH; ++kk) two_sum_add2(phi[kk], plo[kk], pc[kk]);
   }
   if (rvalid) {
-    float* out = a.part_p + ((int64_t)blockIdx.y * m + arow) * R + h * KH;
+    float* out = a.part_p + (sp * m + arow) * R + h * KH;
 #pragma unroll
     for (int kk = 0; kk < KH; ++kk) out[kk] = phi[kk] + plo[kk];
+  }
+}
+
+template <int R>
+__global__ void __launch_bounds__(256) k_pass2(IterArgs a) {
+  if (a.st->stop) return;
+  pass2_block<R>(a, blockIdx.x, blockIdx.y);
+}
+
+// Batched pass 2: item (instance, row block, column split).
+template <int R>
+__global__ void __launch_bounds__(256) k_bpass2(const BInst* __restrict__ insts,
+                                                const BItem* __restrict__ items, int nitems,
+                                                int cur) {
+  for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
+    const BItem w = items[it];
+    const BInst& I = insts[w.inst];
+    if (I.st->stop) continue;
+    const IterArgs a = batch_iter_args(I, cur);
+    __syncthreads();                           // shared memory of the previous item
+    pass2_block<R>(a, w.a, w.b);
   }
 }
 
@@ -300,6 +355,45 @@ cudaError_t launch_pass2(const IterArgs& a, cudaStream_t s) {
     case 32: return pass2_T<32>(a, s);
     default: return pass2_T<64>(a, s);
   }
+}
+
+template <int R>
+static cudaError_t bpass_T(const BInst* insts, const BItem* it1, int n1, int grid1,
+                           const BItem* it2, int n2, int grid2, int cur, int which,
+                           int mode_init, cudaStream_t s) {
+  if (which == 1) {
+    if (n1 == 0) return cudaSuccess;
+    size_t smem = P1Cfg<R>::smem_floats * sizeof(float);
+    k_bpass1<R><<<grid1, 256, smem, s>>>(insts, it1, n1, cur, mode_init);
+  } else {
+    if (n2 == 0) return cudaSuccess;
+    k_bpass2<R><<<grid2, 256, 0, s>>>(insts, it2, n2, cur);
+  }
+  return cudaGetLastError();
+}
+
+// which = 1: batched pass 1 over items it1; which = 2: batched pass 2 over it2.
+cudaError_t launch_bpass(int R, int which, const BInst* insts, const BItem* it1, int n1, int grid1,
+                         const BItem* it2, int n2, int grid2, int cur, int mode_init,
+                         cudaStream_t s) {
+  switch (R) {
+    case 8: return bpass_T<8>(insts, it1, n1, grid1, it2, n2, grid2, cur, which, mode_init, s);
+    case 16: return bpass_T<16>(insts, it1, n1, grid1, it2, n2, grid2, cur, which, mode_init, s);
+    default: return bpass_T<32>(insts, it1, n1, grid1, it2, n2, grid2, cur, which, mode_init, s);
+  }
+}
+
+template <int R>
+static cudaError_t prep_bpass1_T() {
+  size_t smem = P1Cfg<R>::smem_floats * sizeof(float);
+  return cudaFuncSetAttribute(k_bpass1<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+}
+
+cudaError_t prepare_batch_stream_kernels() {
+  cudaError_t e;
+  if ((e = prep_bpass1_T<8>()) != cudaSuccess) return e;
+  if ((e = prep_bpass1_T<16>()) != cudaSuccess) return e;
+  return prep_bpass1_T<32>();
 }
 
 cudaError_t launch_materialize(const float* M, int64_t m, int64_t c0, int64_t ni,

@@ -38,6 +38,11 @@ class dcf_params(C.Structure):
                 ("path", C.c_int)]
 
 
+class dcf_problem(C.Structure):
+    _fields_ = [("m", C.c_int64), ("E", C.c_int), ("n_i", C.POINTER(C.c_int64)),
+                ("r", C.c_int), ("rho", C.c_double), ("lambda_", C.c_double)]
+
+
 ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p)
 FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p)
 
@@ -71,6 +76,23 @@ _SIGS = {
     "dcf_unrolled_backward": (C.c_int, [C.c_void_p, C.POINTER(C.c_double),
                                         C.POINTER(C.c_double), C.POINTER(C.c_double),
                                         C.c_void_p, C.POINTER(C.c_void_p), C.c_int]),
+    "dcf_batch_create": (C.c_int, [C.POINTER(dcf_problem), C.c_int, C.c_int, C.c_double,
+                                   C.c_uint64, C.POINTER(C.c_void_p)]),
+    "dcf_batch_set_stream": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "dcf_batch_load": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_void_p),
+                                 C.POINTER(C.c_int64), C.c_int]),
+    "dcf_batch_load_init": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.POINTER(C.c_void_p),
+                                      C.c_int]),
+    "dcf_batch_tune": (C.c_int, [C.c_void_p, C.c_int, C.c_char_p, C.c_int]),
+    "dcf_batch_step": (C.c_int, [C.c_void_p, C.c_int]),
+    "dcf_batch_solve": (C.c_int, [C.c_void_p, C.POINTER(C.c_int), C.POINTER(C.c_int)]),
+    "dcf_batch_get_factors": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.POINTER(C.c_void_p),
+                                        C.c_int]),
+    "dcf_batch_get_stats": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_double),
+                                      C.POINTER(C.c_double), C.POINTER(C.c_int)]),
+    "dcf_batch_profile_step": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_double), C.c_int]),
+    "dcf_batch_last_error": (C.c_char_p, [C.c_void_p]),
+    "dcf_batch_destroy": (None, [C.c_void_p]),
     "dcf_iterate_noalloc": (C.c_int, [C.c_void_p, C.c_int64, C.c_int64, C.c_int, C.c_double,
                                       C.c_double, C.c_void_p, C.c_void_p, C.c_void_p,
                                       C.c_void_p, C.c_void_p]),
@@ -437,3 +459,118 @@ class Solver:
         gVs = [np.empty((ni, self.r), np.float32) for ni in self.n_i]
         g = dcf_unrolled_backward(self.h, K, gU, gVs)
         return g + (gU, np.concatenate(gVs, axis=0))
+
+
+# ---------------------------------------------------------------------------
+# batches of independent problems
+# ---------------------------------------------------------------------------
+def _bcheck(b, status):
+    if status != DCF_OK:
+        msg = lib().dcf_batch_last_error(b).decode() if b else ""
+        raise DcfError(status, msg)
+
+
+class Batch:
+    """Independent problems advanced together (dcf_batch_* of include/dcf.h).
+
+    ``problems`` is a list of dicts with keys m, n_i, r, rho, lam.
+    """
+
+    def __init__(self, problems, max_iter=100, tol=1e-6, seed=0, stream=None):
+        self.problems = [dict(m=int(p["m"]), n_i=[int(x) for x in p["n_i"]], r=int(p["r"]),
+                              rho=float(p["rho"]), lam=float(p["lam"])) for p in problems]
+        keep = []
+        arr = (dcf_problem * len(problems))()
+        for q, p in enumerate(self.problems):
+            ni = (C.c_int64 * len(p["n_i"]))(*p["n_i"])
+            keep.append(ni)
+            arr[q] = dcf_problem(p["m"], len(p["n_i"]), ni, p["r"], p["rho"], p["lam"])
+        h = C.c_void_p()
+        st = lib().dcf_batch_create(arr, len(problems), int(max_iter), float(tol), int(seed),
+                                    C.byref(h))
+        if st != DCF_OK:
+            raise DcfError(st, "dcf_batch_create rejected the problems")
+        self.h = h
+        self._keep = []
+        if stream is not None:
+            _bcheck(self.h, lib().dcf_batch_set_stream(self.h, C.c_void_p(stream)))
+
+    def close(self):
+        if self.h:
+            lib().dcf_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def load(self, i, M):
+        """M: m x n float32, numpy (column-major copy) or torch CUDA tensor of shape (n, m)."""
+        if not 0 <= i < len(self.problems):
+            _bcheck(self.h, lib().dcf_batch_load(self.h, int(i), None, None, 0))
+        p = self.problems[i]
+        off = np.concatenate([[0], np.cumsum(p["n_i"])])
+        if _is_torch(M):
+            blocks = [M[off[k]:off[k + 1]] for k in range(len(p["n_i"]))]
+        else:
+            M = np.asfortranarray(M, dtype=np.float32)
+            blocks = [M[:, off[k]:off[k + 1]] for k in range(len(p["n_i"]))]
+        ptrs, wheres = zip(*[_ptr_where(b) for b in blocks])
+        arr = (C.c_void_p * len(ptrs))(*[q.value for q in ptrs])
+        _bcheck(self.h, lib().dcf_batch_load(self.h, int(i), arr, None, wheres[0]))
+        self._keep.append((M, blocks))
+
+    def load_init(self, i, U0, V0=None):
+        p = self.problems[i]
+        U0 = np.ascontiguousarray(U0, np.float32)
+        varr = None
+        if V0 is not None:
+            V0 = np.ascontiguousarray(V0, np.float32)
+            off = np.concatenate([[0], np.cumsum(p["n_i"])])
+            vb = [np.ascontiguousarray(V0[off[k]:off[k + 1]]) for k in range(len(p["n_i"]))]
+            self._keep.append(vb)
+            varr = (C.c_void_p * len(vb))(*[v.ctypes.data for v in vb])
+        self._keep.append(U0)
+        _bcheck(self.h, lib().dcf_batch_load_init(self.h, int(i), C.c_void_p(U0.ctypes.data),
+                                                  varr, 0))
+
+    def tune(self, reps=3):
+        buf = C.create_string_buffer(8192)
+        _bcheck(self.h, lib().dcf_batch_tune(self.h, int(reps), buf, 8192))
+        return buf.value.decode()
+
+    def step(self, n=1):
+        _bcheck(self.h, lib().dcf_batch_step(self.h, int(n)))
+
+    def solve(self):
+        its = (C.c_int * len(self.problems))()
+        nc = C.c_int()
+        st = lib().dcf_batch_solve(self.h, its, C.byref(nc))
+        if st not in (DCF_OK, DCF_ENOTCONV):
+            _bcheck(self.h, st)
+        return list(its), nc.value
+
+    def factors(self, i):
+        p = self.problems[i]
+        U = np.empty((p["m"], p["r"]), np.float32)
+        Vs = [np.empty((ni, p["r"]), np.float32) for ni in p["n_i"]]
+        varr = (C.c_void_p * len(Vs))(*[v.ctypes.data for v in Vs])
+        _bcheck(self.h, lib().dcf_batch_get_factors(self.h, int(i), C.c_void_p(U.ctypes.data),
+                                                    varr, 0))
+        return U, np.concatenate(Vs, axis=0)
+
+    BATCH_PHASES = ["make_w", "pass1_vstep", "pass2_pstep", "gram_v", "reduce_q", "rows_ustep",
+                    "reduce_g"]
+
+    def profile_step(self, n):
+        ms = (C.c_double * 7)()
+        _bcheck(self.h, lib().dcf_batch_profile_step(self.h, int(n), ms, 7))
+        return dict(zip(self.BATCH_PHASES, list(ms)))
+
+    def stats(self, i):
+        o, d, it = C.c_double(), C.c_double(), C.c_int()
+        _bcheck(self.h, lib().dcf_batch_get_stats(self.h, int(i), C.byref(o), C.byref(d),
+                                                  C.byref(it)))
+        return o.value, d.value, it.value

@@ -1,0 +1,143 @@
+"""Parity of batched problems (dcf_batch_*) with the FP64 oracle.
+
+Each instance of a batch must compute what the oracle computes for it alone:
+relative Frobenius error <= 1e-4 on U and V after one step from identical
+float32 starting points, <= 1e-3 after several steps, and every instance of a
+solved batch at or below its tolerance.  Shapes mix the three padded ranks
+(8, 16, 32), ragged m and uneven column blocks.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2207_11669_gb300 import dcf
+from tests.helpers import make_case, rel
+
+pytestmark = pytest.mark.gpu
+
+SHAPES = [
+    # (m, n_i, r)
+    (64, [40, 33, 50], 3),
+    (200, [50, 50, 50, 50], 5),
+    (257, [300, 211], 12),
+    (130, [70, 90, 65, 81, 30], 16),
+    (300, [100, 77, 140], 20),
+    (96, [64, 64], 32),
+    (513, [129, 700], 8),
+]
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2207_11669_gb300 import build
+    build.build()
+    torch.cuda.init()
+
+
+def cases(seed0=0):
+    return [make_case(m, n_i, r, seed=seed0 + 17 * q + m, density=0.05, amp=5.0)
+            for q, (m, n_i, r) in enumerate(SHAPES)]
+
+
+def batch_of(cs, load_init=True, **kw):
+    probs = [dict(m=c["M"].shape[0], n_i=c["n_i"], r=c["r"], rho=c["rho"], lam=c["lam"])
+             for c in cs]
+    b = dcf.Batch(probs, **kw)
+    for q, c in enumerate(cs):
+        b.load(q, c["M"])
+        if load_init:
+            b.load_init(q, c["U0"], c["V0"])
+    return b
+
+
+def test_one_step_matches_oracle():
+    cs = cases()
+    b = batch_of(cs)
+    b.step(1)
+    for q, c in enumerate(cs):
+        U, V = b.factors(q)
+        U1, V1, S1, _, _ = O.dcf_run(c["M"], c["n_i"], c["U0"], c["V0"], c["rho"], c["lam"], 1)
+        assert rel(U, U1) <= 1e-4, (q, rel(U, U1))
+        assert rel(V, V1) <= 1e-4, (q, rel(V, V1))
+    b.close()
+
+
+def test_several_steps_match_oracle_and_single_handles():
+    cs = cases(seed0=5)
+    b = batch_of(cs)
+    b.step(6)
+    for q, c in enumerate(cs):
+        U, V = b.factors(q)
+        U6, V6, _, _, _ = O.dcf_run(c["M"], c["n_i"], c["U0"], c["V0"], c["rho"], c["lam"], 6)
+        L = U.astype(np.float64) @ V.T.astype(np.float64)
+        L6 = U6 @ V6.T
+        assert rel(L, L6) <= 1e-3, (q, rel(L, L6))
+        s = dcf.Solver(c["M"].shape[0], c["n_i"], c["r"], c["rho"], c["lam"],
+                       path=dcf.PATH_GENERAL)
+        s.load(c["M"])
+        s.load_init(c["U0"], c["V0"])
+        s.step(6)
+        Us, Vs = s.factors()
+        # same per-item arithmetic; only the column-split grouping of the P
+        # partials may differ (the tuner's choice), so agreement is to rounding
+        Ls = Us.astype(np.float64) @ Vs.T.astype(np.float64)
+        assert rel(L, Ls) <= 1e-4, (q, rel(L, Ls))
+        _, _, it = b.stats(q)
+        assert it == 6
+        s.close()
+    b.close()
+
+
+def test_solve_stops_each_instance_at_its_tolerance():
+    cs = cases(seed0=9)
+    b = batch_of(cs, max_iter=400, tol=1e-5)
+    its, nconv = b.solve()
+    assert nconv == len(cs)
+    for q in range(len(cs)):
+        _, dL, it = b.stats(q)
+        assert dL <= 1e-5
+        assert it == its[q] and it >= 1
+    # stopped instances stay where they stopped
+    U_before = [b.factors(q)[0] for q in range(len(cs))]
+    b.step(2)
+    for q in range(len(cs)):
+        assert np.array_equal(b.factors(q)[0], U_before[q])
+    # the converged point agrees with the oracle's solve to the 1e-3 bar on L
+    c = cs[1]
+    U, V = b.factors(1)
+    Uo, Vo, _, _ = O.dcf_solve(c["M"], c["n_i"], c["U0"], c["V0"], c["rho"], c["lam"], 400,
+                               1e-5)[:4]
+    L = U.astype(np.float64) @ V.T.astype(np.float64)
+    assert rel(L, Uo @ Vo.T) <= 1e-3
+    b.close()
+
+
+def test_default_start_point_and_tuner():
+    cs = cases(seed0=3)
+    b = batch_of(cs, load_init=False, seed=11)
+    report = b.tune(reps=2)
+    assert "chosen" in report
+    b.step(3)
+    for q in range(len(cs)):
+        o, dL, it = b.stats(q)
+        assert it == 3 and np.isfinite(o) and np.isfinite(dL)
+    b.close()
+
+
+def test_errors():
+    c = make_case(64, [30, 30], 4, seed=1)
+    with pytest.raises(dcf.DcfError) as e:
+        dcf.Batch([dict(m=64, n_i=[30, 30], r=40, rho=1e-2, lam=0.1)])
+    assert e.value.status == dcf.DCF_EINVAL
+    b = dcf.Batch([dict(m=64, n_i=[30, 30], r=4, rho=1e-2, lam=0.1)] * 2)
+    b.load(0, c["M"])
+    with pytest.raises(dcf.DcfError) as e:
+        b.step(1)                      # instance 1 has no M
+    assert e.value.status == dcf.DCF_ESTATE
+    with pytest.raises(dcf.DcfError) as e:
+        b.load(5, c["M"])
+    assert e.value.status == dcf.DCF_EINVAL
+    b.close()
