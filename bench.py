@@ -392,6 +392,81 @@ def run_batched(args):
     return 0
 
 
+def run_learned(args):
+    """Time to relative L error 1e-4 on held-out problems of the learned workload
+    (m=1024, n=16384, E=8, rank 16, density 0.10): the plain GPU iteration
+    against the trained K-step network followed by plain refinement.  The
+    error is measured against the plain method's own fixed point (the plain
+    iteration's bias toward lambda keeps it away from the planted L*)."""
+    import torch
+    from paper_2207_11669_gb300 import dcf
+    from paper_2207_11669_gb300.unrolled import fixed_point, steps_to_tolerance
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    here = os.path.dirname(os.path.abspath(__file__))
+    with open(os.path.join(here, "paper_2207_11669_gb300", "learned_theta.json")) as f:
+        th = json.load(f)
+    theta = (np.array(th["a"]), np.array(th["b"]), np.array(th["c"]))
+    stream = torch.cuda.current_stream()
+    tol = 1e-4
+    rows = []
+    for q in range(args.learned_count):
+        inst = synth.learned_instance(q + 1000 * rank, "test")
+        m, n = inst.M.shape
+        U0 = synth.gaussian_u0(m, 16, 7000 + q + 100000)
+        Mt = torch.from_numpy(np.ascontiguousarray(inst.M.T)).cuda()
+        s = dcf.Solver(m, inst.n_i, 16, synth.LEARNED_RHO, synth.LEARNED_LAMBDA,
+                       stream=stream.cuda_stream)
+        s.load(Mt)
+        Uf, Vf = fixed_point(s, U0, 1500)
+        s.set_truth(Uf, Vf)
+        n_plain = steps_to_tolerance(s, U0, tol, 3000)
+        n_ref = steps_to_tolerance(s, U0, tol, 3000, theta)
+        times = {}
+        for arm in ("plain", "learned"):
+            best = None
+            for _ in range(max(1, args.warmup) + 2):
+                s.load_init(U0)
+                torch.cuda.synchronize()
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                w0 = time.perf_counter()
+                e0.record(stream)
+                if arm == "plain":
+                    s.step(n_plain)
+                else:
+                    s.unrolled_forward(*theta, want_loss=False)
+                    s.step(n_ref)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                wall = (time.perf_counter() - w0) * 1e3
+                dev = e0.elapsed_time(e1)
+                best = (dev, wall) if best is None or dev < best[0] else best
+            times[arm] = best
+        rows.append(dict(n_plain=n_plain, n_refine=n_ref, plain_ms=times["plain"][0],
+                         learned_ms=times["learned"][0], plain_wall_ms=times["plain"][1],
+                         learned_wall_ms=times["learned"][1]))
+        s.close()
+        del Mt
+    plain = float(np.mean([r["plain_ms"] for r in rows]))
+    learned = float(np.mean([r["learned_ms"] for r in rows]))
+    if rank == 0:
+        line = {"metric": METRIC, "value": learned, "unit": "ms to rel-L-err 1e-4",
+                "n_gpus": world, "steps": len(rows), "warmup": args.warmup,
+                "ms_per_step": learned, "higher_is_better": False, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": {"workload": "learned_m1024_n16384_r16_E8_dens0.10",
+                           "K": th["K"], "held_out_problems": len(rows),
+                           "target": "plain fixed point (1500 plain steps)", "tol": tol,
+                           "theta": {"a": th["a"], "b": th["b"], "c": th["c"]}},
+                "plain_ms": plain, "speedup_vs_plain": plain / learned,
+                "per_problem": rows, "e2e": None, "cpu_baseline": None,
+                "gpu_launches": None}
+        print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -399,7 +474,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="medium",
-                    choices=["medium", "small", "large", "batched"])
+                    choices=["medium", "small", "large", "batched", "learned"])
+    ap.add_argument("--learned-count", type=int, default=8,
+                    help="held-out problems of the learned workload")
     ap.add_argument("--batch-count", type=int, default=512,
                     help="instances of the batched workload")
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle baseline leg")
@@ -411,6 +488,8 @@ def main():
         return run_reference(args)
     if args.workload == "batched":
         return run_batched(args)
+    if args.workload == "learned":
+        return run_learned(args)
     return run_ours(args)
 
 

@@ -227,7 +227,9 @@ dcf_status dcf_iterate_noalloc(const float* M, int64_t m, int64_t n, int r, doub
  * dcf_step / dcf_solve continue with plain iterations (lambda, rho of the
  * params).  Checkpoints (U_k, V_k, U*_k): (K+1)(m+n)r + K m r floats on the
  * device, owned by the handle.  Requires u_mode = 0 and r <= 32
- * (DCF_EINVAL).  Synchronous. */
+ * (DCF_EINVAL).  With loss_terms and total_loss both NULL the loss is not
+ * evaluated (inference) and dcf_unrolled_backward is not available for this
+ * pass.  Synchronous. */
 dcf_status dcf_unrolled_forward(dcf_handle h, int K, const double* a, const double* b,
                                 const double* c, const double* weights, double* loss_terms,
                                 double* total_loss);

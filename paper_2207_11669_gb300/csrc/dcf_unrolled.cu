@@ -819,9 +819,9 @@ extern "C" dcf_status dcf_unrolled_forward(dcf_handle h, int K, const double* a,
   if (K < 1 || !a || !b || !c) return fail(h, DCF_EINVAL, "K < 1 or a parameter array is NULL");
   if (h->u_mode != 0) return fail(h, DCF_EINVAL, "the unrolled network uses the exact U-step");
   if (h->R > kUnrolledMaxR) return fail(h, DCF_EINVAL, "the unrolled network supports r <= 32");
-  const bool with_loss = h->A_truth != nullptr;
-  if ((loss_terms || total_loss) && !with_loss)
-    return fail(h, DCF_ESTATE, "the loss needs dcf_set_truth first");
+  // the loss (and with it the reverse pass) only when asked for
+  const bool with_loss = loss_terms || total_loss;
+  if (with_loss && !h->A_truth) return fail(h, DCF_ESTATE, "the loss needs dcf_set_truth first");
   std::vector<double> lam_k(K), rho_k(K), alpha_k(K), w_k(K);
   for (int k = 0; k < K; ++k) {
     lam_k[k] = h->lam * std::exp(a[k]);

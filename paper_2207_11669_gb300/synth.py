@@ -201,3 +201,17 @@ def batched_instance_shapes(count: int, seed: int = SEED_BASE + 2):
                         factor_std=1.0 / np.sqrt(k), rho=1e-2,
                         lam=1.0 / np.sqrt(m), n_i=n_i, seed=seed * 1000 + q))
     return out
+
+
+def learned_instance(q: int, split: str = "train") -> Instance:
+    """Problem q of the learned-network workload: m = 1024, n = 16384 in E = 8
+    equal blocks, L* of rank 16 from N(0, 1/16) factors, S* density 0.10 with
+    values U[-10, 10].  Training and held-out problems use disjoint seeds."""
+    base = SEED_BASE + 3000 + (0 if split == "train" else 100000)
+    return make_instance(1024, 16384, 16, seed=base + q, density=0.10, amp=10.0,
+                         factor_std=0.25, E=8)
+
+
+LEARNED_RHO = 1e-2
+LEARNED_LAMBDA = 1.0 / 32.0     # 1 / sqrt(m)
+LEARNED_K = 10

@@ -80,3 +80,31 @@ def train(net, problems, steps, lr=0.05, log=None):
             log(it, total)
         opt.step()
     return hist
+
+
+# ---------------------------------------------------------------------------
+# Helpers of the learned workload: the plain method's fixed point is the
+# target the network is trained toward and the judge of its output.
+# ---------------------------------------------------------------------------
+def fixed_point(solver, U0, iters):
+    """Plain iterations from (U0, V0 = S = 0 sweep); returns the factors
+    reached after ``iters`` steps (the method's fixed point to rounding)."""
+    solver.load_init(U0)
+    solver.step(iters)
+    return solver.factors()
+
+
+def steps_to_tolerance(solver, U0, tol, max_steps, theta=None):
+    """Plain steps needed (after the network ``theta``, if given) until
+    ||U V^T - L_target|| / ||L_target|| <= tol, where L_target is the solver's
+    registered truth.  Returns max_steps + 1 when the tolerance is not met."""
+    solver.load_init(U0)
+    if theta is not None:
+        solver.unrolled_forward(*theta, want_loss=False)
+        if solver.rel_err() <= tol:
+            return 0
+    for t in range(1, max_steps + 1):
+        solver.step(1)
+        if solver.rel_err() <= tol:
+            return t
+    return max_steps + 1

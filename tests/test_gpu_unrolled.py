@@ -193,3 +193,35 @@ def test_training_lowers_the_loss():
     assert hist[-1] < 0.9 * hist[0], hist
     for s, _ in probs:
         s.close()
+
+
+def test_trained_network_reaches_the_fixed_point_in_fewer_steps():
+    """The committed parameters (trained on the GPU by train_unrolled) on a
+    held-out problem of their workload: K network steps plus plain refinement
+    reach 1e-4 of the plain method's fixed point in fewer total iterations than
+    the plain iteration alone, and the untrained network gains nothing."""
+    import json
+    import os
+    import torch
+    from paper_2207_11669_gb300 import synth
+    from paper_2207_11669_gb300.unrolled import fixed_point, steps_to_tolerance
+    path = os.path.join(os.path.dirname(dcf.__file__), "learned_theta.json")
+    th = json.load(open(path))
+    theta = (np.array(th["a"]), np.array(th["b"]), np.array(th["c"]))
+    Kn = th["K"]
+    inst = synth.learned_instance(7, "test")
+    m, n = inst.M.shape
+    U0 = synth.gaussian_u0(m, 16, 123456)
+    Mt = torch.from_numpy(np.ascontiguousarray(inst.M.T)).cuda()
+    s = dcf.Solver(m, inst.n_i, 16, synth.LEARNED_RHO, synth.LEARNED_LAMBDA)
+    s.load(Mt)
+    Uf, Vf = fixed_point(s, U0, 1500)
+    s.set_truth(Uf, Vf)
+    n_plain = steps_to_tolerance(s, U0, 1e-4, 1000)
+    n_ref = steps_to_tolerance(s, U0, 1e-4, 1000, theta)
+    n_untrained = steps_to_tolerance(s, U0, 1e-4, 1000,
+                                     (np.zeros(Kn), np.zeros(Kn), np.ones(Kn)))
+    assert n_plain <= 1000
+    assert Kn + n_ref < n_plain, (Kn, n_ref, n_plain)
+    assert Kn + n_untrained >= n_plain - 1        # K plain steps are just plain steps
+    s.close()
