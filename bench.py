@@ -123,7 +123,10 @@ def alg_bytes_per_iter(m, n, r):
 # from an ncu capture of the kernel as it is now (profiles/k_fused_r32_m4096_n16384.md).
 # The capture ran a smaller n; traffic grows in proportion to n (M is streamed
 # once, V read and written), so it is scaled by n.  None for other shapes.
-NCU_TRAFFIC = {}   # no capture of the current kernels yet
+NCU_TRAFFIC = {
+    # k_fused<32, 3>, m=4096, n=16384, r=32: 273.74 MB read + 4.84 MB written
+    "fused_step": {"m": 4096, "r": 32, "n": 16384, "bytes": 278.58e6},
+}
 
 
 def ncu_traffic(kernel, m, n, r):
@@ -165,18 +168,41 @@ def oracle_sample_rate(wl, inst, U0, budget_s=12.0):
 # ---------------------------------------------------------------------------
 # arms
 # ---------------------------------------------------------------------------
-def run_reference(args):
+def run_reference(args, total_s=60.0):
+    """The oracle as the reference arm: each step is one oracle iteration on a
+    column sample of the workload (the iteration is linear in n), its width
+    chosen from one calibration iteration so that warm-up plus timed steps take
+    about `total_s`; the per-step rate is scaled by n / sample width."""
+    import oracle as O
     rank, world, local = dist_env()
     if rank != 0:
         return 0
     wl = workload_by_name(args.workload)
     inst = wl.instance()
-    U0 = synth.gaussian_u0(wl.m, wl.r, wl.seed)
+    m, n = inst.M.shape
+    U0 = synth.gaussian_u0(wl.m, wl.r, wl.seed).astype(np.float64)
+    ns_max = min(n, max(64, int(4096 * 4096 // m)))
+    M_full = np.asfortranarray(inst.M[:, :ns_max])
+    V0 = O.init_v0(M_full, U0, wl.rho)                 # start point (not timed)
+    t0 = time.perf_counter()
+    O.dcf_iteration(M_full, [ns_max // 2, ns_max - ns_max // 2], U0, V0, wl.rho, wl.lam)
+    t_cal = time.perf_counter() - t0
+    per_step = total_s / (args.warmup + args.steps)
+    ns = int(min(ns_max, max(64, ns_max * per_step / max(t_cal, 1e-9)))) // 2 * 2
+    Ms = np.asfortranarray(M_full[:, :ns])
+    n_i = [ns // 2, ns - ns // 2]
+    U, V = U0, V0[:ns]
     rates = []
     for _ in range(args.warmup + args.steps):
-        r, info = oracle_sample_rate(wl, inst, U0, budget_s=max(2.0, 20.0 / args.steps))
-        rates.append(r)
+        t0 = time.perf_counter()
+        U, V, _ = O.dcf_iteration(Ms, n_i, U, V, wl.rho, wl.lam)
+        rates.append(1.0 / ((time.perf_counter() - t0) * n / ns))
     rate = float(np.mean(rates[args.warmup:]))
+    cores = os.cpu_count()
+    info = dict(kind="oracle", cores=cores,
+                sample=f"{args.warmup + args.steps} oracle iterations (FP64 numpy, BLAS on up to "
+                       f"{cores} host threads), each on m={m} x {ns} of {n} columns, "
+                       f"scaled by n/{ns}")
     line = {"metric": METRIC, "value": rate, "unit": "iters/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 / rate,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -470,7 +496,7 @@ def run_learned(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=300)
+    ap.add_argument("--steps", type=int, default=2000)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="medium",
