@@ -100,14 +100,11 @@ __device__ __forceinline__ void tsum(float& hi, float& lo, float x) {
 
 // Warp-specialised pipeline over the strips of the cluster (20 warps):
 //   warp 0       TMA producer: M sub-tiles into a ring of NST slots
-//   warp 1       MMA issuer for GEMM1 (strip i); owns TMEM
+//   warp 1       MMA issuer for GEMM1 (strip i) and GEMM2 (strip i-1); owns TMEM
 //   warp 2       MMA issuer for GEMM3, which waits on the cluster exchange and
 //                therefore must not hold up GEMM1/GEMM2 (tcgen05 ops complete in
 //                the issuing thread's order)
-//   warp 3       fp16 image of V_s (B operand of GEMM1) for strip i, then the
-//                MMA issue of GEMM2 for strip i-1 as soon as its C tile is
-//                written (issued behind GEMM1 of the next strip, it waited for
-//                that strip's V image and the completion of GEMM1)
+//   warp 3       fp16 image of V_s (B operand of GEMM1), one strip ahead
 //   warps 4-11   S-step epilogue: R, C/lambda into the C tile, Huber
 //   warps 12-19  exchange, two groups of 4 warps for even and odd strips:
 //                column sums out of tensor memory, pushed to the reducer of
@@ -250,31 +247,57 @@ __global__ void __launch_bounds__(kFThreads, 1)
       }
     }
   } else if (warp == 1) {
-    // ================= MMA issuer: GEMM1 ======================================
+    // ================= MMA issuer: GEMM1 and GEMM2 ============================
     if (lane == 0) {
+      if (!wait_(B(b_img), 0)) err = 1;
       const uint32_t idesc1 = tc::idesc_f16(128, kFW, 0, 0);
+      const uint32_t idesc2 = tc::idesc_f16(64, R, 1, 0);
       // descriptors are built once; moving along K adds (bytes >> 4) to the address field
       const uint64_t vdesc0 = tc::smem_desc(sbase + L::VIMG, 128, SB_R);
-      for (int i = 0; i < S; ++i) {   // GEMM1(i): D1 = U_b V_s^T, terms (hi,hi), (hi,lo), (lo,hi)
-        const int p = i & 1;
-        if (!wait_(B(b_vfull), (uint32_t)(i & 1))) err = 1;
-        if (i >= 2 && !wait_(B(b_d1empty + p), (uint32_t)(((i >> 1) - 1) & 1)))
-          err = 1;
-        tc::fence_after_sync();
+      const uint64_t cdesc0 = tc::smem_desc(sbase + L::CBUF, 128, kFH * 16);
+      const uint64_t wdesc0 = tc::smem_desc(sbase + L::WIMG, 128, kFH * 16);
+      for (int i = 0; i < S + 1; ++i) {
+        if (i < S) {   // GEMM1(i): D1 = U_b V_s^T, terms (hi,hi), (hi,lo), (lo,hi)
+          const int p = i & 1;
+          if (!wait_(B(b_vfull), (uint32_t)(i & 1))) err = 1;
+          if (i >= 2 && !wait_(B(b_d1empty + p), (uint32_t)(((i >> 1) - 1) & 1)))
+            err = 1;
+          tc::fence_after_sync();
+          const uint64_t vd = vdesc0;
 #pragma unroll
-        for (int b = 0; b < 2; ++b) {
+          for (int b = 0; b < 2; ++b) {
 #pragma unroll
-          for (int t = 0; t < 3; ++t) {
-            const int tuu = t == 2 ? 1 : 0, tvv = t == 1 ? 1 : 0;
+            for (int t = 0; t < 3; ++t) {
+              const int tuu = t == 2 ? 1 : 0, tvv = t == 1 ? 1 : 0;
 #pragma unroll
-            for (int kk = 0; kk < R / 16; ++kk)
-              tc::mma_ts(d1(p) + b * kFW, tu + (uint32_t)((2 * b + tuu) * (R / 2) + kk * 8),
-                         vdesc0 + (uint64_t)((tvv * (kFW * R * 2) + kk * 256) >> 4), idesc1,
+              for (int kk = 0; kk < R / 16; ++kk)
+                tc::mma_ts(d1(p) + b * kFW, tu + (uint32_t)((2 * b + tuu) * (R / 2) + kk * 8),
+                           vd + (uint64_t)((tvv * (kFW * R * 2) + kk * 256) >> 4), idesc1,
+                           (t > 0 || kk > 0) ? 1u : 0u);
+            }
+          }
+          tc::mma_commit(B(b_d1full + p));
+          tc::mma_commit(B(b_vempty));
+        }
+        if (i >= 1) {   // GEMM2(i-1): Y = C^T W_hi + C^T W_lo (same columns)
+          const int s2 = i - 1, p = s2 & 1;
+          const int pc = s2 % kNC;
+          if (!wait_(B(b_cfull + pc), (uint32_t)((s2 / kNC) & 1))) err = 1;
+          if (s2 >= 2 &&
+              !wait_(B(b_d2empty + p), (uint32_t)(((s2 >> 1) - 1) & 1)))
+            err = 1;
+          tc::fence_after_sync();
+          const uint64_t cd = cdesc0 + (uint64_t)((pc * L::CBYTES) >> 4);
+#pragma unroll
+          for (int t = 0; t < 2; ++t) {
+#pragma unroll
+            for (int kk = 0; kk < kFH / 16; ++kk)
+              tc::mma_ss(d2(p), cd + (uint64_t)((kk * 256) >> 4),
+                         wdesc0 + (uint64_t)((t * (R / 8) * (kFH * 16) + kk * 256) >> 4), idesc2,
                          (t > 0 || kk > 0) ? 1u : 0u);
           }
+          tc::mma_commit(B(b_d2full + p));
         }
-        tc::mma_commit(B(b_d1full + p));
-        tc::mma_commit(B(b_vempty));
       }
     }
   } else if (warp == 2) {
@@ -311,11 +334,9 @@ __global__ void __launch_bounds__(kFThreads, 1)
       tc::mma_commit(B(b_last));
     }
   } else if (warp == 3) {
-    // ================= V image of strip ls, then GEMM2 of strip ls-1 ==========
+    // ================= V image (one warp), one strip ahead =====================
     // The next strip's V rows (contiguous, 64 x R floats) are loaded into
-    // registers while GEMM1 of the current strip runs.  GEMM2 of a strip is
-    // issued here as soon as its C tile is written: the V image of the next
-    // strip needs only GEMM1 of this strip to have completed, which comes first.
+    // registers while GEMM1 of the current strip runs.
     constexpr int V4 = kFW * R / 128;           // float4 per lane
     float4 vr[V4];
     auto load_v = [&](int ls) {
@@ -327,55 +348,30 @@ __global__ void __launch_bounds__(kFThreads, 1)
                                : make_float4(0.f, 0.f, 0.f, 0.f);
       }
     };
-    const uint32_t idesc2 = tc::idesc_f16(64, R, 1, 0);
-    const uint64_t cdesc0 = tc::smem_desc(sbase + L::CBUF, 128, kFH * 16);
-    const uint64_t wdesc0 = tc::smem_desc(sbase + L::WIMG, 128, kFH * 16);
     if (S > 0) load_v(0);
-    for (int ls = 0; ls <= S; ++ls) {
-      if (ls < S) {
-        if (ls >= 1 && !wait_(B(b_vempty), (uint32_t)((ls - 1) & 1)))
-          err = 1;
-        uint8_t* img = smem + L::VIMG;
+    for (int ls = 0; ls < S; ++ls) {
+      if (ls >= 1 && !wait_(B(b_vempty), (uint32_t)((ls - 1) & 1)))
+        err = 1;
+      uint8_t* img = smem + L::VIMG;
 #pragma unroll
-        for (int t = 0; t < V4; ++t) {
-          const int e = 4 * (lane + 32 * t), j = e / R, k = e % R;
-          const float x[4] = {vr[t].x, vr[t].y, vr[t].z, vr[t].w};
-          __half hi[4], lo[4];
+      for (int t = 0; t < V4; ++t) {
+        const int e = 4 * (lane + 32 * t), j = e / R, k = e % R;
+        const float x[4] = {vr[t].x, vr[t].y, vr[t].z, vr[t].w};
+        __half hi[4], lo[4];
 #pragma unroll
-          for (int u = 0; u < 4; ++u) split_h(x[u], s_v, hi[u], lo[u]);
-          const int off = (j >> 3) * SB_R + (k >> 3) * 128 + (j & 7) * 16 + (k & 7) * 2;
-          __half2 h01 = __halves2half2(hi[0], hi[1]), h23 = __halves2half2(hi[2], hi[3]);
-          __half2 l01 = __halves2half2(lo[0], lo[1]), l23 = __halves2half2(lo[2], lo[3]);
-          *reinterpret_cast<uint2*>(img + off) =
-              make_uint2(*reinterpret_cast<uint32_t*>(&h01), *reinterpret_cast<uint32_t*>(&h23));
-          *reinterpret_cast<uint2*>(img + kFW * R * 2 + off) =
-              make_uint2(*reinterpret_cast<uint32_t*>(&l01), *reinterpret_cast<uint32_t*>(&l23));
-        }
-        tc::fence_proxy_async_smem();
-        __syncwarp();
-        if (lane == 0) tc::mbar_arrive(B(b_vfull));
-        if (ls + 1 < S) load_v(ls + 1);
+        for (int u = 0; u < 4; ++u) split_h(x[u], s_v, hi[u], lo[u]);
+        const int off = (j >> 3) * SB_R + (k >> 3) * 128 + (j & 7) * 16 + (k & 7) * 2;
+        __half2 h01 = __halves2half2(hi[0], hi[1]), h23 = __halves2half2(hi[2], hi[3]);
+        __half2 l01 = __halves2half2(lo[0], lo[1]), l23 = __halves2half2(lo[2], lo[3]);
+        *reinterpret_cast<uint2*>(img + off) =
+            make_uint2(*reinterpret_cast<uint32_t*>(&h01), *reinterpret_cast<uint32_t*>(&h23));
+        *reinterpret_cast<uint2*>(img + kFW * R * 2 + off) =
+            make_uint2(*reinterpret_cast<uint32_t*>(&l01), *reinterpret_cast<uint32_t*>(&l23));
       }
-      if (ls >= 1 && lane == 0) {   // GEMM2(ls-1): Y = C^T W_hi + C^T W_lo (same columns)
-        const int s2 = ls - 1, p = s2 & 1;
-        const int pc = s2 % kNC;
-        if (s2 == 0 && !wait_(B(b_img), 0)) err = 1;
-        if (!wait_(B(b_cfull + pc), (uint32_t)((s2 / kNC) & 1))) err = 1;
-        if (s2 >= 2 && !wait_(B(b_d2empty + p), (uint32_t)(((s2 >> 1) - 1) & 1)))
-          err = 1;
-        tc::fence_after_sync();
-        const uint64_t cd = cdesc0 + (uint64_t)((pc * L::CBYTES) >> 4);
-#pragma unroll
-        for (int t = 0; t < 2; ++t) {
-#pragma unroll
-          for (int kk = 0; kk < kFH / 16; ++kk)
-            tc::mma_ss(d2(p), cd + (uint64_t)((kk * 256) >> 4),
-                       wdesc0 + (uint64_t)((t * (R / 8) * (kFH * 16) + kk * 256) >> 4), idesc2,
-                       (t > 0 || kk > 0) ? 1u : 0u);
-        }
-        tc::mma_commit(B(b_d2full + p));
-      }
+      tc::fence_proxy_async_smem();
       __syncwarp();
+      if (lane == 0) tc::mbar_arrive(B(b_vfull));
+      if (ls + 1 < S) load_v(ls + 1);
     }
   } else if (warp < 12) {
     // ================= S-step epilogue (256 threads) ==========================
