@@ -66,13 +66,16 @@ struct FL {  // shared-memory layout (bytes)
   static constexpr int YPART = PIMG + 2 * PBYTES;                // 2 x (64 x R fp32)
   static constexpr int STG = YPART + 2 * YBYTES;                 // 2R x 4 fp16 image chunk
   static constexpr int BAR = STG + 2 * (2 * R * kChunk * 2);     // mbarriers (2 staging chunks)
-  static constexpr int NBAR = 2 * NST + 29;
+  // full/empty NST each; vfull, vempty, d1full, d1empty 2 each; cfull, cempty
+  // kNC each; d2full, d2empty 4 each; g3done, yfull, yfree, pfull, pfree 2
+  // each; img, last
+  static constexpr int NBAR = 2 * NST + 8 + 2 * kNC + 8 + 10 + 2;
   static constexpr int TSLOT = BAR + NBAR * 8;
   static constexpr int RED = TSLOT + 16;                         // 16 doubles
   static constexpr int TOTAL = RED + 16 * 8;
   // tensor-memory columns (512 allocated)
-  static constexpr int T_D2 = 256;                               // 2 x (M=64 result, R columns)
-  static constexpr int T_D3 = T_D2 + 2 * R;                      // 2 blocks x R (P_C)
+  static constexpr int T_D2 = 256;                               // 4 x (M=64 result, R columns)
+  static constexpr int T_D3 = T_D2 + 4 * R;                      // 2 blocks x R (P_C)
   static constexpr int T_U = T_D3 + 2 * R;                       // U hi/lo, 2 blocks x 2 x R/2
   static_assert(T_U + 2 * R <= 512, "tensor memory");
   static_assert(TOTAL <= 232448, "shared memory");
@@ -139,8 +142,8 @@ __global__ void __launch_bounds__(kFThreads, 1)
   // barrier indices
   const int b_full = 0, b_empty = NST, b_vfull = 2 * NST, b_vempty = b_vfull + 2,
             b_d1full = b_vempty + 2, b_d1empty = b_d1full + 2, b_cfull = b_d1empty + 2,
-            b_cempty = b_cfull + kNC, b_d2full = b_cempty + kNC, b_d2empty = b_d2full + 2,
-            b_g3done = b_d2empty + 2, b_yfull = b_g3done + 2, b_yfree = b_yfull + 2,
+            b_cempty = b_cfull + kNC, b_d2full = b_cempty + kNC, b_d2empty = b_d2full + 4,
+            b_g3done = b_d2empty + 4, b_yfull = b_g3done + 2, b_yfree = b_yfull + 2,
             b_pfull = b_yfree + 2, b_pfree = b_pfull + 2, b_img = b_pfree + 2,
             b_last = b_img + 1;
   double* red = reinterpret_cast<double*>(smem + L::RED);
@@ -170,7 +173,7 @@ __global__ void __launch_bounds__(kFThreads, 1)
       tc::mbar_init(B(b_cfull + p), 8);     // the 8 epilogue warps
       tc::mbar_init(B(b_cempty + p), 1);    // GEMM3 commit
     }
-    for (int p = 0; p < 2; ++p) {
+    for (int p = 0; p < 4; ++p) {           // D2 buffers: GEMM2 of strip s uses s % 4
       tc::mbar_init(B(b_d2full + p), 1);
       tc::mbar_init(B(b_d2empty + p), 4);   // the 4 exchange warps
     }
@@ -280,11 +283,12 @@ __global__ void __launch_bounds__(kFThreads, 1)
           tc::mma_commit(B(b_vempty));
         }
         if (i >= 1) {   // GEMM2(i-1): Y = C^T W_hi + C^T W_lo (same columns)
-          const int s2 = i - 1, p = s2 & 1;
+          const int s2 = i - 1, q2 = s2 & 3;
           const int pc = s2 % kNC;
           if (!wait_(B(b_cfull + pc), (uint32_t)((s2 / kNC) & 1))) err = 1;
-          if (s2 >= 2 &&
-              !wait_(B(b_d2empty + p), (uint32_t)(((s2 >> 1) - 1) & 1)))
+          // four D2 buffers: the exchange has read the result of strip s2-4
+          if (s2 >= 4 &&
+              !wait_(B(b_d2empty + q2), (uint32_t)(((s2 >> 2) - 1) & 1)))
             err = 1;
           tc::fence_after_sync();
           const uint64_t cd = cdesc0 + (uint64_t)((pc * L::CBYTES) >> 4);
@@ -292,11 +296,11 @@ __global__ void __launch_bounds__(kFThreads, 1)
           for (int t = 0; t < 2; ++t) {
 #pragma unroll
             for (int kk = 0; kk < kFH / 16; ++kk)
-              tc::mma_ss(d2(p), cd + (uint64_t)((kk * 256) >> 4),
+              tc::mma_ss(d2(q2), cd + (uint64_t)((kk * 256) >> 4),
                          wdesc0 + (uint64_t)((t * (R / 8) * (kFH * 16) + kk * 256) >> 4), idesc2,
                          (t > 0 || kk > 0) ? 1u : 0u);
           }
-          tc::mma_commit(B(b_d2full + p));
+          tc::mma_commit(B(b_d2full + q2));
         }
       }
     }
@@ -484,16 +488,17 @@ __global__ void __launch_bounds__(kFThreads, 1)
       const float vz_first = vz_next;
       if (ls + 2 < S) vz_next = vz_of(ls + 2, 0);   // in flight for a whole strip pair
       // ---- column sums of this CTA's rows out of tensor memory ----
-      if (!wait_(B(b_d2full + p), par)) err = 1;
+      const int q2 = ls & 3;                      // D2 buffer of the strip
+      if (!wait_(B(b_d2full + q2), (uint32_t)((ls >> 2) & 1))) err = 1;
       tc::fence_after_sync();
       float yv[R];
 #pragma unroll
       for (int c = 0; c < R; c += 16)
-        tc::tmem_ld16(d2(p) + ((uint32_t)(xw * 32) << 16) + c, yv + c);
+        tc::tmem_ld16(d2(q2) + ((uint32_t)(xw * 32) << 16) + c, yv + c);
       tc::tmem_ld_wait();
       tc::fence_before_sync();
       __syncwarp();
-      if (lane == 0) tc::mbar_arrive(B(b_d2empty + p));
+      if (lane == 0) tc::mbar_arrive(B(b_d2empty + q2));
       // ---- send them to their reducers (every reducer has consumed strip ls-2) ----
       if (ls >= 2 && !wait_(B(b_yfree + p), par ^ 1u)) err = 1;
       if (lane < 16) {
