@@ -19,7 +19,7 @@
 //
 // Parallel layout: a thread-block cluster of CS CTAs owns whole columns; CTA c
 // of a cluster holds rows [256c, 256c+256) of U, W and of every M strip, so
-// M is read from HBM once per iteration (TMA, 128x32 fp32 boxes).  The
+// M is read from HBM once per iteration (TMA, 256x16 fp32 boxes).  The
 // column sums of GEMM2 are reduced across the cluster through distributed
 // shared memory (reduce-scatter on 8-column chunks, all-gather of the fp16
 // V' image), which is the only cross-CTA exchange.  Each cluster walks the
@@ -40,7 +40,10 @@ namespace dcf {
 
 constexpr int kFW = 64;          // strip width (columns)
 constexpr int kFH = 256;         // rows per CTA (2 row blocks of 128)
-constexpr int kSubBytes = 128 * 32 * 4;
+// One M sub-tile: all 256 rows of the CTA x 16 columns, so that both row blocks
+// of the epilogue consume the ring in the same order (a strip is 4 sub-tiles).
+constexpr int kSubRows = kFH, kSubCols = 16;
+constexpr int kSubBytes = kSubRows * kSubCols * 4;
 // Every wait of a launch together gives up after this long (a launch takes
 // milliseconds); on expiry the kernel records DCF_ETIMEOUT and runs out.
 constexpr uint64_t kDeadlineNs = 2000000000ull;
@@ -54,7 +57,7 @@ constexpr int kNC = 3;           // C tiles in flight: a tile lives from the S-s
 
 template <int R, int NST>
 struct FL {  // shared-memory layout (bytes)
-  static constexpr int RING = 0;                                 // NST x (128 x 32 fp32)
+  static constexpr int RING = 0;                                 // NST x (256 x 16 fp32)
   static constexpr int WIMG = RING + NST * kSubBytes;            // 2R x 256 fp16
   static constexpr int CBYTES = kFH * kFW * 2;                   // one C tile (256 x 64 fp16)
   static constexpr int CBUF = WIMG + 2 * R * kFH * 2;            // kNC C tiles
@@ -161,7 +164,7 @@ __global__ void __launch_bounds__(kFThreads, 1)
   if (tid == 0) {
     for (int i = 0; i < NST; ++i) {
       tc::mbar_init(B(b_full + i), 1);
-      tc::mbar_init(B(b_empty + i), 4);     // the 4 epilogue warps of a row block
+      tc::mbar_init(B(b_empty + i), 8);     // the 8 epilogue warps
     }
     for (int p = 0; p < 2; ++p) {
       tc::mbar_init(B(b_vfull + p), 1);     // the V-image warp (only [0] is used)
@@ -243,10 +246,10 @@ __global__ void __launch_bounds__(kFThreads, 1)
         const int slot = g % NST;
         if (g >= NST && !wait_(B(b_empty + slot), (uint32_t)((g / NST - 1) & 1)))
           err = 1;
-        const int ls = g >> 2, sub = g & 3, b = sub >> 1, q = sub & 1;
+        const int ls = g >> 2, q = g & 3;
         tc::mbar_arrive_expect_tx(B(b_full + slot), kSubBytes);
-        tc::tma_load_2d(sbase + L::RING + slot * kSubBytes, &tmap, (int)(row0 + 128 * b),
-                        (int)(strip_col0(ls) + 32 * q), B(b_full + slot));
+        tc::tma_load_2d(sbase + L::RING + slot * kSubBytes, &tmap, (int)row0,
+                        (int)(strip_col0(ls) + kSubCols * q), B(b_full + slot));
       }
     }
   } else if (warp == 1) {
@@ -395,43 +398,38 @@ __global__ void __launch_bounds__(kFThreads, 1)
       uint8_t* cbuf = smem + L::CBUF + pc * L::CBYTES;
       float hub = 0.f;
 #pragma unroll 1
-      for (int q = 0; q < 2; ++q) {
-        const int g = ls * 4 + rb * 2 + q;
+      for (int q = 0; q < 4; ++q) {   // sub-tile q: columns 16q .. 16q+15 of the strip
+        const int g = ls * 4 + q;
         const int rs = g % NST;
         if (!wait_(B(b_full + rs), (uint32_t)((g / NST) & 1))) err = 1;
         const float* msub = reinterpret_cast<const float*>(smem + L::RING + rs * kSubBytes);
+        float dv[16], mv[16];
+        tc::tmem_ld16(d1(p) + ((uint32_t)(quarter * 32) << 16) + rb * kFW + q * kSubCols, dv);
 #pragma unroll
-        for (int h = 0; h < 2; ++h) {   // 16 columns at a time
-          float dv[16], mv[16];
-          tc::tmem_ld16(d1(p) + ((uint32_t)(quarter * 32) << 16) + rb * kFW + q * 32 + h * 16, dv);
+        for (int jj = 0; jj < 16; ++jj) mv[jj] = msub[jj * kSubRows + arow];
+        tc::tmem_ld_wait();
+        __syncwarp();
+        if (lane == 0) tc::mbar_arrive(B(b_empty + rs));
+        uint32_t packed[8];
 #pragma unroll
-          for (int jj = 0; jj < 16; ++jj) mv[jj] = msub[(h * 16 + jj) * 128 + al];
-          tc::tmem_ld_wait();
-          if (h == 1) {
-            __syncwarp();
-            if (lane == 0) tc::mbar_arrive(B(b_empty + rs));
+        for (int jj = 0; jj < 16; jj += 2) {
+          float c2[2];
+#pragma unroll
+          for (int u = 0; u < 2; ++u) {
+            const float rn = (mv[jj + u] - dv[jj + u] * inv_uv) * inv_lam;   // R / lambda
+            const float c = fminf(fmaxf(rn, -1.f), 1.f);                     // C / lambda
+            hub = fmaf(c, rn - 0.5f * c, hub);                               // H(R) / lambda^2
+            c2[u] = c;
           }
-          uint32_t packed[8];
+          __half2 h2 = __floats2half2_rn(c2[0], c2[1]);
+          packed[jj / 2] = *reinterpret_cast<uint32_t*>(&h2);
+        }
 #pragma unroll
-          for (int jj = 0; jj < 16; jj += 2) {
-            float c2[2];
-#pragma unroll
-            for (int u = 0; u < 2; ++u) {
-              const float rn = (mv[jj + u] - dv[jj + u] * inv_uv) * inv_lam;   // R / lambda
-              const float c = fminf(fmaxf(rn, -1.f), 1.f);                     // C / lambda
-              hub = fmaf(c, rn - 0.5f * c, hub);                               // H(R) / lambda^2
-              c2[u] = c;
-            }
-            __half2 h2 = __floats2half2_rn(c2[0], c2[1]);
-            packed[jj / 2] = *reinterpret_cast<uint32_t*>(&h2);
-          }
-#pragma unroll
-          for (int ch = 0; ch < 2; ++ch) {
-            const int j8 = (q * 32 + h * 16 + ch * 8) >> 3;
-            const int off = j8 * (kFH * 16) + (arow >> 3) * 128 + (arow & 7) * 16;
-            *reinterpret_cast<uint4*>(cbuf + off) =
-                make_uint4(packed[4 * ch], packed[4 * ch + 1], packed[4 * ch + 2], packed[4 * ch + 3]);
-          }
+        for (int ch = 0; ch < 2; ++ch) {
+          const int j8 = (q * kSubCols + ch * 8) >> 3;
+          const int off = j8 * (kFH * 16) + (arow >> 3) * 128 + (arow & 7) * 16;
+          *reinterpret_cast<uint4*>(cbuf + off) =
+              make_uint4(packed[4 * ch], packed[4 * ch + 1], packed[4 * ch + 2], packed[4 * ch + 3]);
         }
       }
       tsum(hub_hi, hub_lo, hub);
@@ -776,13 +774,13 @@ static PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
   return fn;
 }
 
-// 2-D tensor map over column-major M (dim 0 = rows, contiguous), 128 x 32 boxes.
+// 2-D tensor map over column-major M (dim 0 = rows, contiguous), 256 x 16 boxes.
 int fused_make_tmap(void* tmap_out, const float* M, int64_t m, int64_t n) {
   auto fn = encode_fn();
   if (!fn) return -1;
   cuuint64_t dims[2] = {(cuuint64_t)m, (cuuint64_t)n};
   cuuint64_t strides[1] = {(cuuint64_t)m * sizeof(float)};
-  cuuint32_t box[2] = {128, 32};
+  cuuint32_t box[2] = {(cuuint32_t)kSubRows, (cuuint32_t)kSubCols};
   cuuint32_t estr[2] = {1, 1};
   CUresult r = fn(reinterpret_cast<CUtensorMap*>(tmap_out), CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2,
                   const_cast<float*>(M), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
