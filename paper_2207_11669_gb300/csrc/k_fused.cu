@@ -44,7 +44,6 @@ constexpr int kFH = 256;         // rows per CTA (2 row blocks of 128)
 // of the epilogue consume the ring in the same order (a strip is 4 sub-tiles).
 constexpr int kSubRows = kFH, kSubCols = 16;
 constexpr int kSubBytes = kSubRows * kSubCols * 4;
-constexpr int kPrefetch = 12;    // sub-tiles prefetched into L2 ahead of the ring (3 strips)
 // Every wait of a launch together gives up after this long (a launch takes
 // milliseconds); on expiry the kernel records DCF_ETIMEOUT and runs out.
 constexpr uint64_t kDeadlineNs = 2000000000ull;
@@ -242,17 +241,8 @@ __global__ void __launch_bounds__(kFThreads, 1)
   if (warp == 0) {
     // ================= TMA producer ==========================================
     if (lane == 0) {
-      // The ring holds less than one strip, fewer bytes in flight than HBM
-      // latency needs at this rate; sub-tiles are therefore first prefetched
-      // into L2 kPrefetch sub-tiles ahead, and the ring loads hit L2.
       const int total = S * 4;
-      auto prefetch = [&](int g) {
-        if (g < total)
-          tc::tma_prefetch_l2_2d(&tmap, (int)row0, (int)(strip_col0(g >> 2) + kSubCols * (g & 3)));
-      };
-      for (int g = 0; g < kPrefetch; ++g) prefetch(g);
       for (int g = 0; g < total; ++g) {
-        prefetch(g + kPrefetch);
         const int slot = g % NST;
         if (g >= NST && !wait_(B(b_empty + slot), (uint32_t)((g / NST - 1) & 1)))
           err = 1;
