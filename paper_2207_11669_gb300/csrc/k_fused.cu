@@ -70,15 +70,15 @@ struct FL {  // shared-memory layout (bytes)
   static constexpr int STG = YPART + 2 * YBYTES;                 // 2R x 4 fp16 image chunk
   static constexpr int BAR = STG + 2 * (2 * R * kChunk * 2);     // mbarriers (2 staging chunks)
   // full/empty NST each; vfull, vempty, d1full, d1empty 2 each; cfull, cempty
-  // kNC each; d2full, d2empty 4 each; g3done, yfull, yfree, pfull, pfree 2
-  // each; img, last
-  static constexpr int NBAR = 2 * NST + 8 + 2 * kNC + 8 + 10 + 2;
+  // kNC each; d2full, d2empty, g3done, yfull, yfree, pfull, pfree 2 each;
+  // img, last
+  static constexpr int NBAR = 2 * NST + 8 + 2 * kNC + 14 + 2;
   static constexpr int TSLOT = BAR + NBAR * 8;
   static constexpr int RED = TSLOT + 16;                         // 16 doubles
   static constexpr int TOTAL = RED + 16 * 8;
   // tensor-memory columns (512 allocated)
-  static constexpr int T_D2 = 256;                               // 4 x (M=64 result, R columns)
-  static constexpr int T_D3 = T_D2 + 4 * R;                      // 2 blocks x R (P_C)
+  static constexpr int T_D2 = 256;                               // 2 x (M=64 result, R columns)
+  static constexpr int T_D3 = T_D2 + 2 * R;                      // 2 blocks x R (P_C)
   static constexpr int T_U = T_D3 + 2 * R;                       // U hi/lo, 2 blocks x 2 x R/2
   static_assert(T_U + 2 * R <= 512, "tensor memory");
   static_assert(TOTAL <= 232448, "shared memory");
@@ -145,8 +145,8 @@ __global__ void __launch_bounds__(kFThreads, 1)
   // barrier indices
   const int b_full = 0, b_empty = NST, b_vfull = 2 * NST, b_vempty = b_vfull + 2,
             b_d1full = b_vempty + 2, b_d1empty = b_d1full + 2, b_cfull = b_d1empty + 2,
-            b_cempty = b_cfull + kNC, b_d2full = b_cempty + kNC, b_d2empty = b_d2full + 4,
-            b_g3done = b_d2empty + 4, b_yfull = b_g3done + 2, b_yfree = b_yfull + 2,
+            b_cempty = b_cfull + kNC, b_d2full = b_cempty + kNC, b_d2empty = b_d2full + 2,
+            b_g3done = b_d2empty + 2, b_yfull = b_g3done + 2, b_yfree = b_yfull + 2,
             b_pfull = b_yfree + 2, b_pfree = b_pfull + 2, b_img = b_pfree + 2,
             b_last = b_img + 1;
   double* red = reinterpret_cast<double*>(smem + L::RED);
@@ -176,7 +176,7 @@ __global__ void __launch_bounds__(kFThreads, 1)
       tc::mbar_init(B(b_cfull + p), 8);     // the 8 epilogue warps
       tc::mbar_init(B(b_cempty + p), 1);    // GEMM3 commit
     }
-    for (int p = 0; p < 4; ++p) {           // D2 buffers: GEMM2 of strip s uses s % 4
+    for (int p = 0; p < 2; ++p) {           // D2 buffers: GEMM2 of strip s uses s % 2
       tc::mbar_init(B(b_d2full + p), 1);
       tc::mbar_init(B(b_d2empty + p), 4);   // the 4 exchange warps
     }
@@ -286,12 +286,12 @@ __global__ void __launch_bounds__(kFThreads, 1)
           tc::mma_commit(B(b_vempty));
         }
         if (i >= 1) {   // GEMM2(i-1): Y = C^T W_hi + C^T W_lo (same columns)
-          const int s2 = i - 1, q2 = s2 & 3;
+          const int s2 = i - 1, q2 = s2 & 1;
           const int pc = s2 % kNC;
           if (!wait_(B(b_cfull + pc), (uint32_t)((s2 / kNC) & 1))) err = 1;
-          // four D2 buffers: the exchange has read the result of strip s2-4
-          if (s2 >= 4 &&
-              !wait_(B(b_d2empty + q2), (uint32_t)(((s2 >> 2) - 1) & 1)))
+          // two D2 buffers: the exchange has read the result of strip s2-2
+          if (s2 >= 2 &&
+              !wait_(B(b_d2empty + q2), (uint32_t)(((s2 >> 1) - 1) & 1)))
             err = 1;
           tc::fence_after_sync();
           const uint64_t cd = cdesc0 + (uint64_t)((pc * L::CBYTES) >> 4);
@@ -486,8 +486,8 @@ __global__ void __launch_bounds__(kFThreads, 1)
       const float vz_first = vz_next;
       if (ls + 2 < S) vz_next = vz_of(ls + 2, 0);   // in flight for a whole strip pair
       // ---- column sums of this CTA's rows out of tensor memory ----
-      const int q2 = ls & 3;                      // D2 buffer of the strip
-      if (!wait_(B(b_d2full + q2), (uint32_t)((ls >> 2) & 1))) err = 1;
+      const int q2 = ls & 1;                      // D2 buffer of the strip (== grp)
+      if (!wait_(B(b_d2full + q2), (uint32_t)((ls >> 1) & 1))) err = 1;
       tc::fence_after_sync();
       float yv[R];
 #pragma unroll
