@@ -17,6 +17,11 @@
 // also a metric) closes P in the r x r algebra and, with Q = V'^T V', comes
 // from the Gram kernels after the pass.
 //
+// The epilogue writes each C tile twice: into shared memory for GEMM2 (freed
+// as soon as GEMM2 completes) and into tensor memory as GEMM3's A operand
+// (held across the cluster exchange, kNC tiles deep).  Keeping the long-lived
+// copies out of shared memory leaves room for a deeper M ring.
+//
 // Parallel layout: a thread-block cluster of CS CTAs owns whole columns; CTA c
 // of a cluster holds rows [256c, 256c+256) of U, W and of every M strip, so
 // M is read from HBM once per iteration (TMA, 256x16 fp32 boxes).  The
@@ -51,36 +56,41 @@ constexpr uint64_t kDeadlineNs = 2000000000ull;
 
 constexpr int kFThreads = 640;   // 20 warps, see the role map below
 constexpr int kChunk = 4;        // columns per reduce-scatter chunk (16 chunks per strip)
-constexpr int kNC = 3;           // C tiles in flight: a tile lives from the S-step epilogue
-                                 // of its strip until that strip's GEMM3, i.e. across the
-                                 // cluster exchange, so this sets the pipeline depth
+constexpr int kNC = 3;           // C tiles in flight in tensor memory (GEMM3's A operand): a
+                                 // tile lives from the S-step epilogue of its strip until that
+                                 // strip's GEMM3, i.e. across the cluster exchange, so this
+                                 // sets the pipeline depth
+constexpr int kNCS = 2;          // C tiles in shared memory (GEMM2's A operand), each freed as
+                                 // soon as its GEMM2 has completed
 
 template <int R, int NST>
 struct FL {  // shared-memory layout (bytes)
   static constexpr int RING = 0;                                 // NST x (256 x 16 fp32)
   static constexpr int WIMG = RING + NST * kSubBytes;            // 2R x 256 fp16
   static constexpr int CBYTES = kFH * kFW * 2;                   // one C tile (256 x 64 fp16)
-  static constexpr int CBUF = WIMG + 2 * R * kFH * 2;            // kNC C tiles
+  static constexpr int CBUF = WIMG + 2 * R * kFH * 2;            // kNCS C tiles
   static constexpr int VBYTES = 2 * kFW * R * 2;                 // one V image (2 terms)
-  static constexpr int VIMG = CBUF + kNC * CBYTES;               // one V image
+  static constexpr int VIMG = CBUF + kNCS * CBYTES;              // one V image
   static constexpr int PBYTES = 2 * R * kFW * 2;                 // one V' image (2R x 64 fp16)
   static constexpr int PIMG = VIMG + VBYTES;                     // 2 V' images
   static constexpr int YBYTES = kFW * R * 4;                     // one column-sum block
   static constexpr int YPART = PIMG + 2 * PBYTES;                // 2 x (64 x R fp32)
   static constexpr int STG = YPART + 2 * YBYTES;                 // 2R x 4 fp16 image chunk
   static constexpr int BAR = STG + 2 * (2 * R * kChunk * 2);     // mbarriers (2 staging chunks)
-  // full/empty NST each; vfull, vempty, d1full, d1empty 2 each; cfull, cempty
-  // kNC each; d2full, d2empty, g3done, yfull, yfree, pfull, pfree 2 each;
-  // img, last
-  static constexpr int NBAR = 2 * NST + 8 + 2 * kNC + 14 + 2;
+  // full/empty NST each; vfull, vempty, d1full, d1empty 2 each (only [0] of
+  // each is used); cfull, cempty kNC each; c2free kNCS; d2full, d2empty,
+  // g3done, yfull, yfree, pfull, pfree 2 each; img, last
+  static constexpr int NBAR = 2 * NST + 8 + 2 * kNC + kNCS + 14 + 2;
   static constexpr int TSLOT = BAR + NBAR * 8;
   static constexpr int RED = TSLOT + 16;                         // 16 doubles
   static constexpr int TOTAL = RED + 16 * 8;
   // tensor-memory columns (512 allocated)
-  static constexpr int T_D2 = 256;                               // 2 x (M=64 result, R columns)
+  static constexpr int T_D1 = 0;                                 // 2 blocks x 64 (U V_s^T)
+  static constexpr int T_D2 = 128;                               // 2 x (M=64 result, R columns)
   static constexpr int T_D3 = T_D2 + 2 * R;                      // 2 blocks x R (P_C)
   static constexpr int T_U = T_D3 + 2 * R;                       // U hi/lo, 2 blocks x 2 x R/2
-  static_assert(T_U + 2 * R <= 512, "tensor memory");
+  static constexpr int T_C = T_U + 2 * R;                        // kNC x (2 blocks x 32): C fp16 pairs
+  static_assert(T_C + kNC * 64 <= 512, "tensor memory");
   static_assert(TOTAL <= 232448, "shared memory");
 };
 
@@ -145,7 +155,8 @@ __global__ void __launch_bounds__(kFThreads, 1)
   // barrier indices
   const int b_full = 0, b_empty = NST, b_vfull = 2 * NST, b_vempty = b_vfull + 2,
             b_d1full = b_vempty + 2, b_d1empty = b_d1full + 2, b_cfull = b_d1empty + 2,
-            b_cempty = b_cfull + kNC, b_d2full = b_cempty + kNC, b_d2empty = b_d2full + 2,
+            b_cempty = b_cfull + kNC, b_c2free = b_cempty + kNC, b_d2full = b_c2free + kNCS,
+            b_d2empty = b_d2full + 2,
             b_g3done = b_d2empty + 2, b_yfull = b_g3done + 2, b_yfree = b_yfull + 2,
             b_pfull = b_yfree + 2, b_pfree = b_pfull + 2, b_img = b_pfree + 2,
             b_last = b_img + 1;
@@ -173,9 +184,10 @@ __global__ void __launch_bounds__(kFThreads, 1)
       tc::mbar_init(B(b_d1empty + p), 8);   // the 8 epilogue warps
     }
     for (int p = 0; p < kNC; ++p) {
-      tc::mbar_init(B(b_cfull + p), 8);     // the 8 epilogue warps
-      tc::mbar_init(B(b_cempty + p), 1);    // GEMM3 commit
+      tc::mbar_init(B(b_cfull + p), 8);     // the 8 epilogue warps: both C copies written
+      tc::mbar_init(B(b_cempty + p), 1);    // GEMM3 commit: tensor-memory C slot free
     }
+    for (int p = 0; p < kNCS; ++p) tc::mbar_init(B(b_c2free + p), 1);   // GEMM2 commit
     for (int p = 0; p < 2; ++p) {           // D2 buffers: GEMM2 of strip s uses s % 2
       tc::mbar_init(B(b_d2full + p), 1);
       tc::mbar_init(B(b_d2empty + p), 4);   // the 4 exchange warps
@@ -197,7 +209,8 @@ __global__ void __launch_bounds__(kFThreads, 1)
   __syncthreads();
   tc::fence_after_sync();
   const uint32_t tbase = *reinterpret_cast<volatile uint32_t*>(smem + L::TSLOT);
-  auto d1 = [&](int s) { return tbase + 128u * (uint32_t)s; };
+  const uint32_t d1 = tbase + L::T_D1;                   // one D1: GEMM1 waits for the epilogue
+  auto tcs = [&](int pc) { return tbase + (uint32_t)(L::T_C + pc * 64); };   // C slot
   auto d2 = [&](int s) { return tbase + (uint32_t)(L::T_D2 + s * R); };
   const uint32_t d3 = tbase + L::T_D3, tu = tbase + L::T_U;
   const float s_u = a.scales[2 * slab], s_w = a.scales[2 * slab + 1];
@@ -264,10 +277,9 @@ __global__ void __launch_bounds__(kFThreads, 1)
       const uint64_t wdesc0 = tc::smem_desc(sbase + L::WIMG, 128, kFH * 16);
       for (int i = 0; i < S + 1; ++i) {
         if (i < S) {   // GEMM1(i): D1 = U_b V_s^T, terms (hi,hi), (hi,lo), (lo,hi)
-          const int p = i & 1;
           if (!wait_(B(b_vfull), (uint32_t)(i & 1))) err = 1;
-          if (i >= 2 && !wait_(B(b_d1empty + p), (uint32_t)(((i >> 1) - 1) & 1)))
-            err = 1;
+          // one D1: the epilogue of strip i-1 has read it
+          if (i >= 1 && !wait_(B(b_d1empty), (uint32_t)((i - 1) & 1))) err = 1;
           tc::fence_after_sync();
           const uint64_t vd = vdesc0;
 #pragma unroll
@@ -277,12 +289,12 @@ __global__ void __launch_bounds__(kFThreads, 1)
               const int tuu = t == 2 ? 1 : 0, tvv = t == 1 ? 1 : 0;
 #pragma unroll
               for (int kk = 0; kk < R / 16; ++kk)
-                tc::mma_ts(d1(p) + b * kFW, tu + (uint32_t)((2 * b + tuu) * (R / 2) + kk * 8),
+                tc::mma_ts(d1 + b * kFW, tu + (uint32_t)((2 * b + tuu) * (R / 2) + kk * 8),
                            vd + (uint64_t)((tvv * (kFW * R * 2) + kk * 256) >> 4), idesc1,
                            (t > 0 || kk > 0) ? 1u : 0u);
             }
           }
-          tc::mma_commit(B(b_d1full + p));
+          tc::mma_commit(B(b_d1full));
           tc::mma_commit(B(b_vempty));
         }
         if (i >= 1) {   // GEMM2(i-1): Y = C^T W_hi + C^T W_lo (same columns)
@@ -294,7 +306,8 @@ __global__ void __launch_bounds__(kFThreads, 1)
               !wait_(B(b_d2empty + q2), (uint32_t)(((s2 >> 1) - 1) & 1)))
             err = 1;
           tc::fence_after_sync();
-          const uint64_t cd = cdesc0 + (uint64_t)((pc * L::CBYTES) >> 4);
+          const int ps = s2 % kNCS;                       // shared-memory C slot
+          const uint64_t cd = cdesc0 + (uint64_t)((ps * L::CBYTES) >> 4);
 #pragma unroll
           for (int t = 0; t < 2; ++t) {
 #pragma unroll
@@ -304,6 +317,7 @@ __global__ void __launch_bounds__(kFThreads, 1)
                          (t > 0 || kk > 0) ? 1u : 0u);
           }
           tc::mma_commit(B(b_d2full + q2));
+          tc::mma_commit(B(b_c2free + ps));
         }
       }
     }
@@ -311,16 +325,17 @@ __global__ void __launch_bounds__(kFThreads, 1)
     // ================= MMA issuer: GEMM3 =======================================
     if (lane == 0) {
       const uint32_t idesc3 = tc::idesc_f16(128, R, 0, 0);
-      const uint64_t cdesc0 = tc::smem_desc(sbase + L::CBUF, kFH * 16, 128);
       const uint64_t pdesc0 = tc::smem_desc(sbase + L::PIMG, 128, (kFW / 8) * 128);
       for (int s3 = 0; s3 < S; ++s3) {   // P_C += C V'_hi^T + C V'_lo^T
         const int p = s3 & 1;
         tc::mbar_arrive_expect_tx(B(b_pfull + p), (uint32_t)L::PBYTES);
         if (!wait_(B(b_pfull + p), (uint32_t)((s3 >> 1) & 1))) err = 1;
+        const int pc = s3 % kNC;
+        // the tensor-memory C tile of the strip was written before its cfull
+        // phase (already complete: GEMM2 waited for it before the exchange)
+        if (!wait_(B(b_cfull + pc), (uint32_t)((s3 / kNC) & 1))) err = 1;
         tc::fence_proxy_async_smem();
         tc::fence_after_sync();
-        const int pc = s3 % kNC;
-        const uint64_t cd = cdesc0 + (uint64_t)((pc * L::CBYTES) >> 4);
         const uint64_t pd = pdesc0 + (uint64_t)((p * L::PBYTES) >> 4);
 #pragma unroll
         for (int b = 0; b < 2; ++b) {
@@ -328,7 +343,7 @@ __global__ void __launch_bounds__(kFThreads, 1)
           for (int t = 0; t < 2; ++t) {   // V'_hi then V'_lo into the same columns
 #pragma unroll
             for (int kk = 0; kk < kFW / 16; ++kk)
-              tc::mma_ss(d3 + b * R, cd + (uint64_t)((b * 2048 + kk * 2 * (kFH * 16)) >> 4),
+              tc::mma_ts(d3 + b * R, tcs(pc) + (uint32_t)(b * 32 + kk * 8),
                          pd + (uint64_t)((t * (R / 8) * (kFW / 8) * 128 + kk * 256) >> 4), idesc3,
                          (s3 > 0 || t > 0 || kk > 0) ? 1u : 0u);
           }
@@ -389,13 +404,17 @@ __global__ void __launch_bounds__(kFThreads, 1)
     const float inv_lam = 1.f / a.lam;
     float hub_hi = 0.f, hub_lo = 0.f;
     for (int ls = 0; ls < S; ++ls) {
-      const int p = ls & 1;
-      if (!wait_(B(b_d1full + p), (uint32_t)((ls >> 1) & 1))) err = 1;
-      const int pc = ls % kNC;
+      if (!wait_(B(b_d1full), (uint32_t)(ls & 1))) err = 1;
+      const int pc = ls % kNC, ps = ls % kNCS;
+      // tensor-memory C slot: GEMM3 of strip ls-kNC has completed
       if (ls >= kNC && !wait_(B(b_cempty + pc), (uint32_t)(((ls / kNC) - 1) & 1)))
         err = 1;
+      // shared-memory C slot: GEMM2 of strip ls-kNCS has completed
+      if (ls >= kNCS && !wait_(B(b_c2free + ps), (uint32_t)(((ls / kNCS) - 1) & 1)))
+        err = 1;
       tc::fence_after_sync();
-      uint8_t* cbuf = smem + L::CBUF + pc * L::CBYTES;
+      uint8_t* cbuf = smem + L::CBUF + ps * L::CBYTES;
+      const uint32_t tcrow = tcs(pc) + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(rb * 32);
       float hub = 0.f;
 #pragma unroll 1
       for (int q = 0; q < 4; ++q) {   // sub-tile q: columns 16q .. 16q+15 of the strip
@@ -404,10 +423,15 @@ __global__ void __launch_bounds__(kFThreads, 1)
         if (!wait_(B(b_full + rs), (uint32_t)((g / NST) & 1))) err = 1;
         const float* msub = reinterpret_cast<const float*>(smem + L::RING + rs * kSubBytes);
         float dv[16], mv[16];
-        tc::tmem_ld16(d1(p) + ((uint32_t)(quarter * 32) << 16) + rb * kFW + q * kSubCols, dv);
+        tc::tmem_ld16(d1 + ((uint32_t)(quarter * 32) << 16) + rb * kFW + q * kSubCols, dv);
 #pragma unroll
         for (int jj = 0; jj < 16; ++jj) mv[jj] = msub[jj * kSubRows + arow];
         tc::tmem_ld_wait();
+        if (q == 3) {   // this warp's last read of D1: GEMM1 of the next strip may start
+          tc::fence_before_sync();
+          __syncwarp();
+          if (lane == 0) tc::mbar_arrive(B(b_d1empty));
+        }
         __syncwarp();
         if (lane == 0) tc::mbar_arrive(B(b_empty + rs));
         uint32_t packed[8];
@@ -431,15 +455,15 @@ __global__ void __launch_bounds__(kFThreads, 1)
           *reinterpret_cast<uint4*>(cbuf + off) =
               make_uint4(packed[4 * ch], packed[4 * ch + 1], packed[4 * ch + 2], packed[4 * ch + 3]);
         }
+        // GEMM3's copy: row arow, K pairs (16q + 2w, 16q + 2w + 1) in column 8q + w
+        tc::tmem_st8(tcrow + (uint32_t)(q * 8), packed);
       }
+      tc::tmem_st_wait();
       tsum(hub_hi, hub_lo, hub);
       tc::fence_before_sync();
       tc::fence_proxy_async_smem();
       __syncwarp();
-      if (lane == 0) {
-        tc::mbar_arrive(B(b_d1empty + p));
-        tc::mbar_arrive(B(b_cfull + pc));
-      }
+      if (lane == 0) tc::mbar_arrive(B(b_cfull + pc));
     }
     // P partial of this cluster's columns (after the last GEMM3)
     if (!wait_(B(b_last), 0)) err = 1;
@@ -716,8 +740,8 @@ __global__ void k_absmax(const float* x, int64_t count, unsigned int* out) {
 // ---------------------------------------------------------------------------
 // host side
 // ---------------------------------------------------------------------------
-constexpr int kNST32 = 3;
-constexpr int kNST16 = 5;
+constexpr int kNST32 = 5;
+constexpr int kNST16 = 7;
 
 template <int R, int NST>
 static size_t fused_smem() {
