@@ -416,33 +416,44 @@ __global__ void __launch_bounds__(kFThreads, 1)
       uint8_t* cbuf = smem + L::CBUF + ps * L::CBYTES;
       const uint32_t tcrow = tcs(pc) + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(rb * 32);
       float hub = 0.f;
-#pragma unroll 1
-      for (int q = 0; q < 4; ++q) {   // sub-tile q: columns 16q .. 16q+15 of the strip
+      // Software-pipelined over the 4 sub-tiles: the loads of sub-tile q+1 (D1
+      // from tensor memory, M from the ring) are in flight while sub-tile q is
+      // computed and stored.
+      float dv[2][16], mv[2][16];
+      auto load_sub = [&](int q, float* d, float* mm) {
         const int g = ls * 4 + q;
         const int rs = g % NST;
         if (!wait_(B(b_full + rs), (uint32_t)((g / NST) & 1))) err = 1;
         const float* msub = reinterpret_cast<const float*>(smem + L::RING + rs * kSubBytes);
-        float dv[16], mv[16];
-        tc::tmem_ld16(d1 + ((uint32_t)(quarter * 32) << 16) + rb * kFW + q * kSubCols, dv);
+        tc::tmem_ld16(d1 + ((uint32_t)(quarter * 32) << 16) + rb * kFW + q * kSubCols, d);
 #pragma unroll
-        for (int jj = 0; jj < 16; ++jj) mv[jj] = msub[jj * kSubRows + arow];
-        tc::tmem_ld_wait();
+        for (int jj = 0; jj < 16; ++jj) mm[jj] = msub[jj * kSubRows + arow];
+      };
+      auto release_sub = [&](int q) {   // after tcgen05.wait::ld: D1 and M of sub-tile q read
         if (q == 3) {   // this warp's last read of D1: GEMM1 of the next strip may start
           tc::fence_before_sync();
           __syncwarp();
           if (lane == 0) tc::mbar_arrive(B(b_d1empty));
         }
         __syncwarp();
-        if (lane == 0) tc::mbar_arrive(B(b_empty + rs));
+        if (lane == 0) tc::mbar_arrive(B(b_empty + (ls * 4 + q) % NST));
+      };
+      load_sub(0, dv[0], mv[0]);
+      tc::tmem_ld_wait();
+      release_sub(0);
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {   // sub-tile q: columns 16q .. 16q+15 of the strip
+        const int cb = q & 1;
+        if (q < 3) load_sub(q + 1, dv[cb ^ 1], mv[cb ^ 1]);
         uint32_t packed[8];
 #pragma unroll
         for (int jj = 0; jj < 16; jj += 2) {
           float c2[2];
 #pragma unroll
           for (int u = 0; u < 2; ++u) {
-            const float rn = (mv[jj + u] - dv[jj + u] * inv_uv) * inv_lam;   // R / lambda
-            const float c = fminf(fmaxf(rn, -1.f), 1.f);                     // C / lambda
-            hub = fmaf(c, rn - 0.5f * c, hub);                               // H(R) / lambda^2
+            const float rn = (mv[cb][jj + u] - dv[cb][jj + u] * inv_uv) * inv_lam;   // R / lambda
+            const float c = fminf(fmaxf(rn, -1.f), 1.f);                             // C / lambda
+            hub = fmaf(c, rn - 0.5f * c, hub);                                       // H(R) / lambda^2
             c2[u] = c;
           }
           __half2 h2 = __floats2half2_rn(c2[0], c2[1]);
@@ -457,6 +468,10 @@ __global__ void __launch_bounds__(kFThreads, 1)
         }
         // GEMM3's copy: row arow, K pairs (16q + 2w, 16q + 2w + 1) in column 8q + w
         tc::tmem_st8(tcrow + (uint32_t)(q * 8), packed);
+        if (q < 3) {
+          tc::tmem_ld_wait();
+          release_sub(q + 1);
+        }
       }
       tc::tmem_st_wait();
       tsum(hub_hi, hub_lo, hub);
