@@ -133,7 +133,6 @@ __device__ __forceinline__ void tsum(float& hi, float& lo, float x) {
 //   yfree  (count CS)   every reducer has consumed this CTA's column sums
 //   pfull  (1 + bytes)  every reducer's chunk of the V' image has landed here
 //   pfree  (count CS)   every CTA's GEMM3 that read this V' image buffer is done
-//                       (each GEMM3 issuer arrives once its own GEMM3 completes)
 // Column sums and V' images are double-buffered, so each of these exists
 // once per buffer and completes every other strip; an arrival for strip s+2
 // can only happen after the phase of strip s has completed.  The exchange
@@ -351,10 +350,6 @@ __global__ void __launch_bounds__(kFThreads, 1)
         }
         tc::mma_commit(B(b_cempty + pc));
         tc::mma_commit(B(b_g3done + p));
-        // once this GEMM3 has completed, V' image buffer p may be refilled: tell
-        // every CTA (their all-gathers of strip s3 + 2 wait for all of these)
-        if (!wait_(B(b_g3done + p), (uint32_t)((s3 >> 1) & 1))) err = 1;
-        for (int rk = 0; rk < cs; ++rk) tc::mbar_arrive_cluster_relaxed(B(b_pfree + p), (uint32_t)rk);
       }
       // A parity wait only tells the current phase from the previous one, so the
       // final read-out waits on a barrier of its own rather than on g3done.
@@ -558,6 +553,11 @@ __global__ void __launch_bounds__(kFThreads, 1)
           v.w = __float_as_uint(yv[k + 3] * y_scale);
           tc::st_async_u32x4(dst + (uint32_t)k * 4, v, bar);
         }
+      }
+      // ---- GEMM3 of strip ls-2 done here: its V' image buffer may be refilled ----
+      if (ls >= 2 && xw == 0) {
+        if (!wait_(B(b_g3done + p), par ^ 1u)) err = 1;
+        if (lane < cs) tc::mbar_arrive_cluster_relaxed(B(b_pfree + p), (uint32_t)lane);
       }
       // ---- reduce this CTA's chunks of strip ls ----
       if (xt == 0) tc::mbar_arrive_expect_tx(B(b_yfull + p), (uint32_t)L::YBYTES);
