@@ -124,8 +124,8 @@ def alg_bytes_per_iter(m, n, r):
 # The capture ran a smaller n; traffic grows in proportion to n (M is streamed
 # once, V read and written), so it is scaled by n.  None for other shapes.
 NCU_TRAFFIC = {
-    # k_fused<32, 3>, m=4096, n=16384, r=32: 273.74 MB read + 4.84 MB written
-    "fused_step": {"m": 4096, "r": 32, "n": 16384, "bytes": 278.58e6},
+    # k_fused<32, 5>, m=4096, n=16384, r=32: 273.77 MB read + 4.80 MB written
+    "fused_step": {"m": 4096, "r": 32, "n": 16384, "bytes": 278.57e6},
 }
 
 
