@@ -10,6 +10,15 @@
 // gram_vv_block, rows_block, make_w_block and the r x r tails), so a batched
 // instance computes exactly what a single handle on the general path computes.
 //
+// Instances with at most 16 slabs of 256 rows run their pass over M on the
+// tensor-core kernel instead (k_fused in table mode): one cluster of CS CTAs
+// per instance, CS = slabs rounded up to a power of two, instances of one
+// (R, CS) launched in waves of as many clusters as fit on the GPU, largest
+// first.  The tensor map needs a row stride that is a multiple of 16 bytes, so
+// such an instance is stored with m rounded up to a multiple of 4: the added
+// rows of M and of U are zero and stay zero (their R, C and P rows vanish), so
+// the iterates of the real rows are unchanged.
+//
 // Autotuner: the tile decisions with a real choice -- the column-split width
 // of pass 2 and the persistent grid sizes of both passes -- are timed on the
 // batch itself (the passes only write outputs that the next iteration
@@ -44,7 +53,10 @@ int class_of(int r) { return r <= 8 ? 0 : r <= 16 ? 1 : 2; }
 struct BatchClass {
   std::vector<int> insts;                 // instance indices of this class
   // device lists
-  BItem* mw = nullptr;  int n_mw = 0;     // (inst, 32-row block): make_w and rows
+  BItem* mw = nullptr;  int n_mw = 0;     // (inst, 32-row block): rows (every instance)
+  BItem* mwg = nullptr; int n_mwg = 0;    // (inst, 32-row block): make_w (general path)
+  BItem* fp = nullptr;  int n_fp = 0;     // (inst, slab): U / W images (fused path)
+  BItem* fr = nullptr;  int n_fr = 0;     // (inst, block of 256): V_old Z (fused path)
   BItem* p1 = nullptr;  int n_p1 = 0;     // (inst, strip)
   BItem* p2 = nullptr;  int n_p2 = 0;     // (inst, 128-row block, split)
   BItem* gv = nullptr;  int n_gv = 0;     // (inst, Gram chunk of V)
@@ -52,6 +64,20 @@ struct BatchClass {
   int* which = nullptr;                   // instance list for the reductions
   int grid_p1 = 0, grid_p2 = 0, split_cols = 1024;
 };
+
+// One launch of the fused kernel: a cluster per instance; an argument table
+// per copy parity (the tables differ in cur, V_old, V_new and the V max slot).
+struct FusedWave {
+  int nclusters = 0;
+  FusedArgs* table[2] = {nullptr, nullptr};
+};
+struct FusedGroup {
+  int R = 0, cs = 0;
+  std::vector<int> insts;                 // largest first
+  std::vector<FusedWave> waves;
+};
+
+constexpr int64_t kFusedMaxM = 4096;      // 16 slabs of 256 rows
 
 }  // namespace
 
@@ -66,6 +92,10 @@ struct dcf_batch_s {
   std::vector<char> loaded, have_init;
   BInst* dev = nullptr;                   // descriptor table on the device
   BatchClass cls[kClasses];
+  std::vector<int64_t> m_user;            // rows as given (host[q].m may be padded)
+  std::vector<FusedGroup> fgroups;
+  std::vector<uint8_t*> tmaps;            // device tensor map of each fused instance
+  int* kerr = nullptr;                    // fused kernel: a bounded wait expired
   // allocation
   dcf_alloc_fn alloc = nullptr;
   dcf_free_fn release = nullptr;
@@ -139,7 +169,7 @@ void layout_instance(Arena& ar, BInst& I) {
   I.V[1] = ar.take<float>((size_t)n * R);
   I.W = ar.take<float>((size_t)m * R);
   I.part_p = ar.take<float>((size_t)nsplit_max * m * R);
-  I.part_h = ar.take<double>((size_t)I.n_strips);
+  I.part_h = ar.take<double>((size_t)std::max(I.n_strips, I.nslabs));
   I.part_q = ar.take<float2>((size_t)ng * R * R);
   I.part_xv = ar.take<float2>((size_t)ng * R * R);
   I.part_g = ar.take<float2>((size_t)I.n_rblocks * R * R);
@@ -147,6 +177,13 @@ void layout_instance(Arena& ar, BInst& I) {
   I.red = ar.take<double>((size_t)4 * R * R + 8);
   I.sm = ar.take<Smalls>(1);
   I.st = ar.take<DevState>(1);
+  if (I.fused) {
+    I.img = ar.take<uint8_t>((size_t)I.nslabs * 2048 * R);
+    I.scales = ar.take<float>((size_t)2 * I.nslabs + 1);
+    I.zmat = ar.take<float>((size_t)R * R);
+    I.VZ = ar.take<float>((size_t)n * R);
+    I.vmax = ar.take<unsigned int>(2);
+  }
 }
 
 template <class T>
@@ -164,6 +201,7 @@ std::vector<BItem> p2_items(dcf_batch b, const BatchClass& c, int split_cols) {
   std::vector<BItem> v;
   for (int q : c.insts) {
     const BInst& I = b->host[q];
+    if (I.fused) continue;                 // the fused kernel forms its own P partial
     const int rb = (int)((I.m + 127) / 128);
     const int ns = (int)((I.n + split_cols - 1) / split_cols);
     for (int sp = 0; sp < ns; ++sp)
@@ -176,6 +214,7 @@ void set_split(dcf_batch b, BatchClass& c, int split_cols) {
   c.split_cols = split_cols;
   for (int q : c.insts) {
     BInst& I = b->host[q];
+    if (I.fused) continue;                 // one P partial, written by the fused kernel
     I.split_cols = split_cols;
     I.nsplit = (int)((I.n + split_cols - 1) / split_cols);
   }
@@ -209,14 +248,22 @@ cudaError_t enqueue_batch_iteration(dcf_batch b, int cur, cudaStream_t s,
       const int R = kClassR[k];
       const int ni = (int)c.insts.size();
       switch (ph) {
-        case 0:   // W = U G^{-1}
-          e = launch_bsmall(R, 0, b->dev, c.mw, c.n_mw, nullptr, grid_for(c.n_mw, 4 * S), cur, 1, s);
+        case 0:   // W = U G^{-1} (general); U / W images and V_old Z (fused)
+          if (c.n_mwg > 0)
+            e = launch_bsmall(R, 0, b->dev, c.mwg, c.n_mwg, nullptr, grid_for(c.n_mwg, 4 * S), cur,
+                              1, s);
+          if (e == cudaSuccess)
+            e = launch_bfused_small(R, 0, b->dev, c.fp, c.n_fp, grid_for(c.n_fp, 4 * S), cur, s);
+          if (e == cudaSuccess)
+            e = launch_bfused_small(R, 1, b->dev, c.fr, c.n_fr, grid_for(c.n_fr, 8 * S), cur, s);
           break;
-        case 1:   // X, V' = X^T W
-          e = launch_bpass(R, 1, b->dev, c.p1, c.n_p1, c.grid_p1, nullptr, 0, 0, cur, 0, s);
+        case 1:   // X, V' = X^T W (general; the fused waves follow)
+          if (c.n_p1 > 0)
+            e = launch_bpass(R, 1, b->dev, c.p1, c.n_p1, c.grid_p1, nullptr, 0, 0, cur, 0, s);
           break;
-        case 2:   // P = X V' partials
-          e = launch_bpass(R, 2, b->dev, nullptr, 0, 0, c.p2, c.n_p2, c.grid_p2, cur, 0, s);
+        case 2:   // P = X V' partials (general)
+          if (c.n_p2 > 0)
+            e = launch_bpass(R, 2, b->dev, nullptr, 0, 0, c.p2, c.n_p2, c.grid_p2, cur, 0, s);
           break;
         case 3:   // Q = V'^T V', X_v partials
           e = launch_bsmall(R, 2, b->dev, c.gv, c.n_gv, nullptr, grid_for(c.n_gv, 2 * S), cur, 0, s);
@@ -232,6 +279,10 @@ cudaError_t enqueue_batch_iteration(dcf_batch b, int cur, cudaStream_t s,
           break;
       }
     }
+    if (ph == 1)   // the single pass over M of every fused instance, wave by wave
+      for (const FusedGroup& g : b->fgroups)
+        for (const FusedWave& wv : g.waves)
+          if (e == cudaSuccess) e = launch_fused_table(g.R, g.cs, wv.nclusters, wv.table[cur], s);
     if (e != cudaSuccess) return e;
     if (ev && (e = cudaEventRecord(ev[ph], s)) != cudaSuccess) return e;
   }
@@ -266,7 +317,8 @@ dcf_status batch_init(dcf_batch b) {
     BCK(cudaMemsetAsync(I.sm, 0, sizeof(Smalls), s), "memset");
     if (!b->have_init[q]) {
       const uint64_t seed = b->seed + 0x9E3779B97F4A7C15ull * (uint64_t)(q + 1);
-      BCK(launch_philox_u0(I.U[0], I.m, I.r, I.R, seed, s), "philox U0");
+      // real rows only: padded rows of U stay zero
+      BCK(launch_philox_u0(I.U[0], b->m_user[q], I.r, I.R, seed, s), "philox U0");
     }
   }
   const int S = b->num_sms;
@@ -304,6 +356,13 @@ dcf_status batch_init(dcf_batch b) {
     BCK(launch_bsmall(R, 2, b->dev, c.gv, c.n_gv, nullptr, grid_for(c.n_gv, 2 * S), 0, 2, s),
         "gram V0");
     BCK(launch_bsmall(R, 3, b->dev, nullptr, (int)c.insts.size(), c.which, 0, 0, 4, s), "Q0");
+  }
+  // fused instances: max |V0| sets the first V image scale
+  for (int q = 0; q < b->count; ++q) {
+    const BInst& I = b->host[q];
+    if (!I.fused) continue;
+    BCK(cudaMemsetAsync(I.vmax, 0, 2 * sizeof(unsigned int), s), "memset");
+    BCK(launch_absmax(I.V[0], I.n * I.R, I.vmax, s), "max |V0|");
   }
   b->host_iter = 0;
   b->initialized = true;
@@ -343,10 +402,10 @@ dcf_status batch_tune(dcf_batch b, int reps) {
   BCK(cudaStreamSynchronize(b->stream), "sync");
   for (int k = 0; k < kClasses; ++k) {
     BatchClass& c = b->cls[k];
-    if (c.insts.empty()) continue;
+    if (c.insts.empty() || c.n_p1 == 0) continue;   // only general instances have passes
     // W for copy 0 (the passes read it)
-    BCK(launch_bsmall(kClassR[k], 0, b->dev, c.mw, c.n_mw, nullptr, grid_for(c.n_mw, 4 * S), 0,
-                      0, b->stream), "tune W");
+    BCK(launch_bsmall(kClassR[k], 0, b->dev, c.mwg, c.n_mwg, nullptr, grid_for(c.n_mwg, 4 * S),
+                      0, 0, b->stream), "tune W");
     float best1 = 1e30f;
     int g1best = c.grid_p1;
     for (int mult : {1, 2, 3, 4}) {
@@ -389,6 +448,14 @@ dcf_status batch_tune(dcf_batch b, int reps) {
              kClassR[k], c.grid_p1, sbest, g2best);
     b->tune_report += line;
   }
+  for (const FusedGroup& g : b->fgroups) {
+    snprintf(line, sizeof(line),
+             "R=%d cs=%d chosen: tensor-core kernel, %d instances in %d waves of up to %d "
+             "clusters\n",
+             g.R, g.cs, (int)g.insts.size(), (int)g.waves.size(),
+             g.waves.empty() ? 0 : g.waves[0].nclusters);
+    b->tune_report += line;
+  }
   BCK(cudaMemcpyAsync(b->dev, b->host.data(), b->host.size() * sizeof(BInst),
                       cudaMemcpyHostToDevice, b->stream), "descriptors");
   BCK(cudaStreamSynchronize(b->stream), "sync");
@@ -426,10 +493,14 @@ dcf_status batch_ready(dcf_batch b) {
 
 dcf_status read_states(dcf_batch b, std::vector<DevState>& out) {
   out.resize(b->count);
+  int kerr = 0;
   for (int q = 0; q < b->count; ++q)
     BCK(cudaMemcpyAsync(&out[q], b->host[q].st, sizeof(DevState), cudaMemcpyDeviceToHost,
                         b->stream), "read state");
+  BCK(cudaMemcpyAsync(&kerr, b->kerr, sizeof(int), cudaMemcpyDeviceToHost, b->stream), "err");
   BCK(cudaStreamSynchronize(b->stream), "sync");
+  if (kerr == DCF_ETIMEOUT)
+    return bfail(b, DCF_ETIMEOUT, "a bounded device-side wait expired in the fused kernel");
   for (int q = 0; q < b->count; ++q)
     if (out[q].status == DCF_ENONFINITE)
       return bfail(b, DCF_ENONFINITE, "non-finite iterates in instance " + std::to_string(q));
@@ -470,11 +541,13 @@ extern "C" dcf_status dcf_batch_create(const dcf_problem* problems, int count, i
       cudaEventCreateWithFlags(&b->ev_in, cudaEventDisableTiming) != cudaSuccess ||
       cudaEventCreateWithFlags(&b->ev_out, cudaEventDisableTiming) != cudaSuccess ||
       prepare_stream_kernels() != cudaSuccess || prepare_small_kernels() != cudaSuccess ||
-      prepare_batch_stream_kernels() != cudaSuccess) {
+      prepare_batch_stream_kernels() != cudaSuccess || fused_prepare(16) != cudaSuccess ||
+      fused_prepare(32) != cudaSuccess) {
     cudaGetLastError();
     dcf_batch_destroy(b);
     return DCF_ECUDA;
   }
+  b->m_user.resize(count);
   b->host.resize(count);
   b->n_i.resize(count);
   b->c_i.resize(count);
@@ -485,10 +558,20 @@ extern "C" dcf_status dcf_batch_create(const dcf_problem* problems, int count, i
     const dcf_problem& p = problems[q];
     BInst& I = b->host[q];
     I = BInst{};
-    I.m = p.m;
+    b->m_user[q] = p.m;
+    // the tensor-core path: at most 16 slabs of 256 rows, padded rank 16 or 32,
+    // a cluster shape that fits on this GPU; M stored with m rounded up to 4
+    const int64_t m_pad = (p.m + 3) / 4 * 4;
+    const int Rf = p.r <= 16 ? 16 : 32;
+    int cs = 1;
+    while ((int64_t)cs * 256 < m_pad) cs *= 2;
+    I.fused = (m_pad <= kFusedMaxM && fused_max_clusters(Rf, cs) > 0) ? 1 : 0;
+    cudaGetLastError();
+    I.m = I.fused ? m_pad : p.m;
+    I.nslabs = I.fused ? cs : 1;
     I.E = p.E;
     I.r = p.r;
-    I.R = pick_R(p.r);
+    I.R = I.fused ? Rf : pick_R(p.r);
     I.lam = (float)p.lambda;
     I.rho = (float)p.rho;
     I.u_mode = 0;
@@ -505,13 +588,15 @@ extern "C" dcf_status dcf_batch_create(const dcf_problem* problems, int count, i
     I.n_gitems = (int)((n + kBGramRows - 1) / kBGramRows);
     I.n_uitems = (int)((I.m + kBGramRows - 1) / kBGramRows);
     I.split_cols = 1024;
-    I.nsplit = (int)((n + 1023) / 1024);
+    I.nsplit = I.fused ? 1 : (int)((n + 1023) / 1024);
+    I.n_hparts = I.fused ? I.nslabs : I.n_strips;
   }
   size_t mbytes = 0, wbytes = 0;
   for (int q = 0; q < count; ++q) {
-    mbytes += ((size_t)b->host[q].m * b->host[q].n * 4 + 255) / 256 * 256;
+    mbytes += ((size_t)b->host[q].m * b->host[q].n * 4 + 255) / 256 * 256;   // padded m
     Arena dry;
     layout_instance(dry, b->host[q]);
+    if (b->host[q].fused) dry.take<uint8_t>(128);   // its tensor map
     wbytes += dry.used;
   }
   char* mbase = (char*)balloc(b, mbytes);
@@ -522,33 +607,49 @@ extern "C" dcf_status dcf_batch_create(const dcf_problem* problems, int count, i
   }
   {
     Arena am{mbase, 0}, aw{wbase, 0};
+    b->tmaps.assign(count, nullptr);
     for (int q = 0; q < count; ++q) {
       BInst& I = b->host[q];
       I.M = am.take<float>((size_t)I.m * I.n);
       layout_instance(aw, I);
+      if (I.fused) b->tmaps[q] = aw.take<uint8_t>(128);   // 256-byte aligned
     }
   }
-  if (cudaMemsetAsync(wbase, 0, wbytes, b->stream) != cudaSuccess) {
+  // zero everything: padded rows of M and U stay zero
+  if (cudaMemsetAsync(wbase, 0, wbytes, b->stream) != cudaSuccess ||
+      cudaMemsetAsync(mbase, 0, mbytes, b->stream) != cudaSuccess) {
     cudaGetLastError();
     dcf_batch_destroy(b);
     return DCF_ECUDA;
   }
   // classes and their work lists
-  for (int q = 0; q < count; ++q) b->cls[class_of(b->host[q].r)].insts.push_back(q);
+  // rank classes by the padded rank an instance runs with (R = 8 only on the
+  // general path)
+  for (int q = 0; q < count; ++q) b->cls[class_of(b->host[q].R)].insts.push_back(q);
   for (int k = 0; k < kClasses; ++k) {
     BatchClass& c = b->cls[k];
     if (c.insts.empty()) continue;
-    std::vector<BItem> mw, p1, gv, gu;
+    std::vector<BItem> mw, mwg, p1, gv, gu, fp, fr;
     for (int q : c.insts) {
       const BInst& I = b->host[q];
       for (int rb = 0; rb < I.n_rblocks; ++rb) mw.push_back(BItem{q, rb, 0, 0});
-      for (int s = 0; s < I.n_strips; ++s) p1.push_back(BItem{q, s, 0, 0});
       for (int g = 0; g < I.n_gitems; ++g) gv.push_back(BItem{q, g, 0, 0});
       for (int g = 0; g < I.n_uitems; ++g) gu.push_back(BItem{q, g, 0, 0});
+      if (I.fused) {
+        for (int sl = 0; sl < I.nslabs; ++sl) fp.push_back(BItem{q, sl, 0, 0});
+        const int64_t blocks = (I.n * (I.R / 8) + 255) / 256;
+        for (int64_t bk = 0; bk < blocks; ++bk) fr.push_back(BItem{q, (int)bk, 0, 0});
+      } else {
+        for (int rb = 0; rb < I.n_rblocks; ++rb) mwg.push_back(BItem{q, rb, 0, 0});
+        for (int s = 0; s < I.n_strips; ++s) p1.push_back(BItem{q, s, 0, 0});
+      }
     }
     set_split(b, c, 1024);
     std::vector<BItem> p2 = p2_items(b, c, 1024);
     c.mw = upload(b, mw);  c.n_mw = (int)mw.size();
+    c.mwg = upload(b, mwg);  c.n_mwg = (int)mwg.size();
+    c.fp = upload(b, fp);  c.n_fp = (int)fp.size();
+    c.fr = upload(b, fr);  c.n_fr = (int)fr.size();
     c.p1 = upload(b, p1);  c.n_p1 = (int)p1.size();
     c.p2 = upload(b, p2);  c.n_p2 = (int)p2.size();
     c.gv = upload(b, gv);  c.n_gv = (int)gv.size();
@@ -556,9 +657,82 @@ extern "C" dcf_status dcf_batch_create(const dcf_problem* problems, int count, i
     c.which = upload(b, c.insts);
     c.grid_p1 = grid_for(c.n_p1, 2 * b->num_sms);
     c.grid_p2 = grid_for(c.n_p2, 4 * b->num_sms);
-    if (!c.mw || !c.p1 || !c.p2 || !c.gv || !c.gu || !c.which) {
+    if (!c.mw || !c.mwg || !c.fp || !c.fr || !c.p1 || !c.p2 || !c.gv || !c.gu || !c.which) {
       dcf_batch_destroy(b);
       return DCF_ENOMEM;
+    }
+  }
+  b->kerr = (int*)balloc(b, sizeof(int));
+  if (!b->kerr || cudaMemsetAsync(b->kerr, 0, sizeof(int), b->stream) != cudaSuccess) {
+    cudaGetLastError();
+    dcf_batch_destroy(b);
+    return DCF_ENOMEM;
+  }
+  // fused groups by (R, cluster size): tensor maps, waves, argument tables
+  for (int q = 0; q < count; ++q) {
+    const BInst& I = b->host[q];
+    if (!I.fused) continue;
+    alignas(64) unsigned char tm[128];
+    if (fused_make_tmap(tm, I.M, I.m, I.n) != 0 ||
+        cudaMemcpyAsync(b->tmaps[q], tm, 128, cudaMemcpyHostToDevice, b->stream) != cudaSuccess ||
+        cudaStreamSynchronize(b->stream) != cudaSuccess) {   // the host copy goes out of scope
+      cudaGetLastError();
+      dcf_batch_destroy(b);
+      return DCF_ECUDA;
+    }
+    size_t gi = 0;
+    while (gi < b->fgroups.size() && !(b->fgroups[gi].R == I.R && b->fgroups[gi].cs == I.nslabs))
+      ++gi;
+    if (gi == b->fgroups.size()) {
+      FusedGroup g;
+      g.R = I.R;
+      g.cs = I.nslabs;
+      b->fgroups.push_back(g);
+    }
+    b->fgroups[gi].insts.push_back(q);
+  }
+  for (FusedGroup& g : b->fgroups) {
+    std::stable_sort(g.insts.begin(), g.insts.end(), [&](int x, int y) {
+      return b->host[x].n_strips > b->host[y].n_strips;
+    });
+    const int ncl = fused_max_clusters(g.R, g.cs);
+    for (size_t w0 = 0; w0 < g.insts.size(); w0 += (size_t)ncl) {
+      FusedWave wv;
+      wv.nclusters = (int)std::min<size_t>((size_t)ncl, g.insts.size() - w0);
+      for (int cur = 0; cur < 2; ++cur) {
+        std::vector<FusedArgs> tab(wv.nclusters);
+        for (int c = 0; c < wv.nclusters; ++c) {
+          const int q = g.insts[w0 + c];
+          const BInst& I = b->host[q];
+          FusedArgs& f = tab[c];
+          f = FusedArgs{};
+          f.cur = cur;
+          f.cs = g.cs;
+          f.nclusters = 1;
+          f.nslabs = I.nslabs;
+          f.m = I.m;
+          f.n = I.n;
+          f.lam = I.lam;
+          f.Vold = I.V[cur];
+          f.Vnew = I.V[cur ^ 1];
+          f.img = I.img;
+          f.scales = I.scales;
+          f.zmat = I.zmat;
+          f.VZ = I.VZ;
+          f.vmax_out = I.vmax + (cur ^ 1);
+          f.part_h = I.part_h;
+          f.part_p = I.part_p;
+          f.st = I.st;
+          f.err = b->kerr;
+          f.tmap_g = b->tmaps[q];
+        }
+        wv.table[cur] = upload(b, tab);
+        if (!wv.table[cur]) {
+          dcf_batch_destroy(b);
+          return DCF_ENOMEM;
+        }
+      }
+      g.waves.push_back(wv);
     }
   }
   b->dev = upload(b, b->host);
@@ -583,17 +757,18 @@ extern "C" dcf_status dcf_batch_load(dcf_batch b, int i, const float* const* M_i
   if (i < 0 || i >= b->count) return bfail(b, DCF_EINVAL, "instance index out of range");
   if (!M_i || (where != 0 && where != 1)) return bfail(b, DCF_EINVAL, "blocks or where");
   const BInst& I = b->host[i];
+  const int64_t mu = b->m_user[i];
   for (int k = 0; k < I.E; ++k) {
     if (!M_i[k]) return bfail(b, DCF_EINVAL, "NULL block");
-    if (ld_i && ld_i[k] < I.m) return bfail(b, DCF_EINVAL, "leading dimension < m");
+    if (ld_i && ld_i[k] < mu) return bfail(b, DCF_EINVAL, "leading dimension < m");
   }
   dcf_status st = batch_begin(b);
   if (st != DCF_OK) return st;
   const cudaMemcpyKind kind = where == 0 ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
   for (int k = 0; k < I.E; ++k) {
-    const int64_t ld = ld_i ? ld_i[k] : I.m;
-    float* dst = const_cast<float*>(I.M) + b->c_i[i][k] * I.m;
-    BCK(cudaMemcpy2DAsync(dst, (size_t)I.m * 4, M_i[k], (size_t)ld * 4, (size_t)I.m * 4,
+    const int64_t ld = ld_i ? ld_i[k] : mu;
+    float* dst = const_cast<float*>(I.M) + b->c_i[i][k] * I.m;   // padded pitch I.m >= mu
+    BCK(cudaMemcpy2DAsync(dst, (size_t)I.m * 4, M_i[k], (size_t)ld * 4, (size_t)mu * 4,
                           (size_t)b->n_i[i][k], kind, b->stream), "copy M");
   }
   if (where == 0) BCK(cudaStreamSynchronize(b->stream), "sync");
@@ -612,7 +787,7 @@ extern "C" dcf_status dcf_batch_load_init(dcf_batch b, int i, const float* U0,
   if (st != DCF_OK) return st;
   const cudaMemcpyKind kind = where == 0 ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
   BCK(cudaMemcpy2DAsync(I.U[0], (size_t)I.R * 4, U0, (size_t)I.r * 4, (size_t)I.r * 4,
-                        (size_t)I.m, kind, b->stream), "copy U0");
+                        (size_t)b->m_user[i], kind, b->stream), "copy U0");
   b->have_init[i] = 1;
   if (V0_i) {
     for (int k = 0; k < I.E; ++k) {
@@ -716,7 +891,7 @@ extern "C" dcf_status dcf_batch_get_factors(dcf_batch b, int i, float* U, float*
   const cudaMemcpyKind kind = where == 0 ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
   if (U)
     BCK(cudaMemcpy2DAsync(U, (size_t)I.r * 4, I.U[cur], (size_t)I.R * 4, (size_t)I.r * 4,
-                          (size_t)I.m, kind, b->stream), "copy U");
+                          (size_t)b->m_user[i], kind, b->stream), "copy U");
   if (V_i) {
     for (int k = 0; k < I.E; ++k) {
       if (!V_i[k]) continue;
@@ -737,9 +912,13 @@ extern "C" dcf_status dcf_batch_get_stats(dcf_batch b, int i, double* objective,
   if (st != DCF_OK) return st;
   if ((st = batch_init(b)) != DCF_OK) return st;
   DevState ds{};
+  int kerr = 0;
   BCK(cudaMemcpyAsync(&ds, b->host[i].st, sizeof(DevState), cudaMemcpyDeviceToHost, b->stream),
       "state");
+  BCK(cudaMemcpyAsync(&kerr, b->kerr, sizeof(int), cudaMemcpyDeviceToHost, b->stream), "err");
   BCK(cudaStreamSynchronize(b->stream), "sync");
+  if (kerr == DCF_ETIMEOUT)
+    return bfail(b, DCF_ETIMEOUT, "a bounded device-side wait expired in the fused kernel");
   if (ds.status == DCF_ENONFINITE) return bfail(b, DCF_ENONFINITE, "non-finite iterates");
   if (objective) *objective = ds.objective;
   if (dL_rel) *dL_rel = ds.dL_rel;

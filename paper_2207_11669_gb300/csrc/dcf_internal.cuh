@@ -100,6 +100,15 @@ struct BInst {
   double* red;       // 4 R*R + 8 doubles: reduced Q, X_v, Huber, G, X_u
   Smalls* sm;
   DevState* st;
+  // the tensor-core single-pass path (k_fused in table mode); 0 = general passes
+  int fused;
+  int nslabs;        // 256-row slabs = the cluster size
+  int n_hparts;      // Huber partials written per iteration (n_strips, or nslabs)
+  uint8_t* img;      // [nslabs][U image | W image]
+  float* scales;     // 2 nslabs + 1
+  float* zmat;       // R x R
+  float* VZ;         // n x R, V_old Z
+  unsigned int* vmax;  // [2] max |V| of copy 0 / 1 (float bits)
 };
 // Work item: instance and two indices whose meaning depends on the kernel
 // (strip; row block and column split; Gram chunk; 32-row block).
@@ -139,9 +148,10 @@ __device__ __forceinline__ IterArgs batch_iter_args(const BInst& I, int cur) {
   a.n_rblocks = I.n_rblocks;
   a.sm = I.sm;
   a.st = I.st;
-  a.add_uxv = 0;
+  a.add_uxv = I.fused;   // the fused kernel leaves U_{t-1} (V_{t-1}^T V_t) to the rows
   a.alpha = 1.0f;
   a.ustar_out = nullptr;
+  if (I.fused) a.n_vblocks = I.n_hparts;
   return a;
 }
 
@@ -180,6 +190,10 @@ cudaError_t launch_bpass(int R, int which, const BInst* insts, const BItem* it1,
 cudaError_t launch_bsmall(int R, int kind, const BInst* insts, const BItem* items, int nitems,
                           const int* which, int grid, int cur, int arg, cudaStream_t s);
 cudaError_t prepare_batch_stream_kernels();
+// Batched fused-path preparation: kind 0 U/W images per (instance, slab), kind 1
+// V_old Z per (instance, block of 256 entries).
+cudaError_t launch_bfused_small(int R, int kind, const BInst* insts, const BItem* items,
+                                int nitems, int grid, int cur, cudaStream_t s);
 cudaError_t prepare_small_kernels();
 cudaError_t launch_materialize(const float* M, int64_t m, int64_t c0, int64_t ni,
                                const float* U, const float* V, int R, float lam,
@@ -209,8 +223,14 @@ struct FusedArgs {
   float* part_p;            // [nclusters][m][R]
   DevState* st;
   int* err;
+  const void* tmap_g;       // tensor map of M in global memory (table launches)
 };
 cudaError_t launch_fused(int R, const void* tmap, const FusedArgs& fa, cudaStream_t s);
+// Many problems in one launch: cluster c runs every strip of problem table[c]
+// (cs CTAs each; table in device memory, nclusters entries, each with its own
+// tensor map in tmap_g, nclusters = 1 and cs equal to the launch's).
+cudaError_t launch_fused_table(int R, int cs, int nclusters, const FusedArgs* table,
+                               cudaStream_t s);
 cudaError_t fused_prepare(int R);
 int fused_max_clusters(int R, int cs);
 int fused_make_tmap(void* tmap_out, const float* M, int64_t m, int64_t n);

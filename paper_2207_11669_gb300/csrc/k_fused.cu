@@ -137,16 +137,30 @@ __device__ __forceinline__ void tsum(float& hi, float& lo, float x) {
 // once per buffer and completes every other strip; an arrival for strip s+2
 // can only happen after the phase of strip s has completed.  The exchange
 // groups work on alternate strips with the buffers of their parity.
-template <int R, int NST>
+template <bool kTable>
+__device__ __forceinline__ const FusedArgs& fused_args(const FusedArgs& ap,
+                                                       const FusedArgs* table, int c) {
+  if constexpr (kTable) return table[c];
+  else return ap;
+}
+
+// kTable = false: one problem, its strips dealt to the clusters of the launch
+// (cluster c takes strips c, c + #clusters, ...; P partial slot c).
+// kTable = true: cluster c runs every strip of problem table[c] (P slot 0).
+template <int R, int NST, bool kTable>
 __global__ void __launch_bounds__(kFThreads, 1)
-    k_fused(const __grid_constant__ CUtensorMap tmap, const FusedArgs a) {
+    k_fused(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ FusedArgs ap,
+            const FusedArgs* __restrict__ table) {
   using L = FL<R, NST>;
-  if (a.st->stop) return;  // uniform over the grid
+  const int cs = ap.cs;
+  const FusedArgs& a = fused_args<kTable>(ap, table, (int)(blockIdx.x / cs));
+  const void* tmp = kTable ? a.tmap_g : static_cast<const void*>(&tmap);
+  if (a.st->stop) return;  // uniform over the cluster (over the grid for one problem)
   extern __shared__ __align__(1024) uint8_t smem[];
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const uint32_t crank = tc::cluster_rank();
-  const int cs = a.cs;
-  const int cid = blockIdx.x / cs;
+  const int cid = kTable ? 0 : (int)(blockIdx.x / cs);   // cluster index within the problem
+  const int ncl = kTable ? 1 : ap.nclusters;             // clusters sharing the problem
   const int slab = (int)(blockIdx.x % cs);   // == crank
   const int64_t row0 = (int64_t)slab * kFH;
   const uint32_t sbase = tc::smem_u32(smem);
@@ -203,7 +217,7 @@ __global__ void __launch_bounds__(kFThreads, 1)
     tc::mbar_init(B(b_img), 1);
     tc::mbar_init(B(b_last), 1);            // every MMA of the kernel has completed
     tc::fence_mbar_init();
-    tc::prefetch_tmap(&tmap);
+    tc::prefetch_tmap(tmp);
   }
   tc::fence_before_sync();
   __syncthreads();
@@ -216,10 +230,10 @@ __global__ void __launch_bounds__(kFThreads, 1)
   const float s_u = a.scales[2 * slab], s_w = a.scales[2 * slab + 1];
   const float s_v = a.scales[2 * a.nslabs];
   const int64_t nstrips = (a.n + kFW - 1) / kFW;
-  const int S = cid < nstrips ? (int)((nstrips - 1 - cid) / a.nclusters + 1) : 0;
+  const int S = cid < nstrips ? (int)((nstrips - 1 - cid) / ncl + 1) : 0;
   const int nch = (int)((kFW / kChunk - 1 - (int)crank) / cs + 1);   // chunks this CTA reduces
   const uint8_t* slab_img = a.img + (size_t)slab * (4 * kFH * R * 2);
-  auto strip_col0 = [&](int ls) { return (cid + (int64_t)ls * a.nclusters) * kFW; };
+  auto strip_col0 = [&](int ls) { return (cid + (int64_t)ls * ncl) * kFW; };
 
   if (tid == 0) {
     tc::mbar_arrive_expect_tx(B(b_img), 2 * R * kFH * 2);
@@ -261,7 +275,7 @@ __global__ void __launch_bounds__(kFThreads, 1)
           err = 1;
         const int ls = g >> 2, q = g & 3;
         tc::mbar_arrive_expect_tx(B(b_full + slot), kSubBytes);
-        tc::tma_load_2d(sbase + L::RING + slot * kSubBytes, &tmap, (int)row0,
+        tc::tma_load_2d(sbase + L::RING + slot * kSubBytes, tmp, (int)row0,
                         (int)(strip_col0(ls) + kSubCols * q), B(b_full + slot));
       }
     }
@@ -612,7 +626,7 @@ __global__ void __launch_bounds__(kFThreads, 1)
   if (tid == 0) {
     double t = 0.0;
     for (int w = 0; w < 8; ++w) t += red[w];
-    a.part_h[blockIdx.x] = t;
+    a.part_h[cid * cs + (int)crank] = t;
   }
   if (warp == 1) tc::tmem_dealloc(tbase, 512);
   tc::cluster_sync();  // no CTA leaves while a peer may still address its shared memory
@@ -622,18 +636,17 @@ __global__ void __launch_bounds__(kFThreads, 1)
 // Per-iteration preparation: W rows, fp16 hi/lo images of U and W per 256-row
 // slab with power-of-two scales, Z = I - rho G^{-1}, and the V scale.
 // ---------------------------------------------------------------------------
+// One 256-row slab (block-wide, 256 threads).
 template <int R>
-__global__ void __launch_bounds__(256) k_fused_prep(const float* __restrict__ U,
-                                                    const Smalls* sm, const DevState* st,
-                                                    int64_t m, int nslabs, float rho,
-                                                    const unsigned int* vmax_in,
-                                                    unsigned int* vmax_reset, uint8_t* img,
-                                                    float* scales, float* zmat) {
-  if (st->stop) return;
+__device__ __forceinline__ void fused_prep_slab(const float* __restrict__ U, const Smalls* sm,
+                                                int64_t m, int nslabs, float rho,
+                                                const unsigned int* vmax_in,
+                                                unsigned int* vmax_reset, uint8_t* img,
+                                                float* scales, float* zmat, int slab) {
   __shared__ float gi[R * R];
   __shared__ __align__(16) uint8_t wst[2 * R * kFH * 2];
   __shared__ float red[2][8];
-  const int tid = threadIdx.x, slab = blockIdx.x;
+  const int tid = threadIdx.x;
   for (int i = tid; i < R * R; i += 256) gi[i] = sm->ginv32[i];
   __syncthreads();
   const int64_t arow = (int64_t)slab * kFH + tid;
@@ -708,16 +721,43 @@ __global__ void __launch_bounds__(256) k_fused_prep(const float* __restrict__ U,
   }
 }
 
-// out = in Z for n rows of R (V_old Z, added to the cluster's column sums)
 template <int R>
-__global__ void __launch_bounds__(256) k_rowmat(const float* __restrict__ in,
-                                                const float* __restrict__ zmat, int64_t n,
-                                                float* __restrict__ out, const DevState* st) {
+__global__ void __launch_bounds__(256) k_fused_prep(const float* __restrict__ U,
+                                                    const Smalls* sm, const DevState* st,
+                                                    int64_t m, int nslabs, float rho,
+                                                    const unsigned int* vmax_in,
+                                                    unsigned int* vmax_reset, uint8_t* img,
+                                                    float* scales, float* zmat) {
   if (st->stop) return;
+  fused_prep_slab<R>(U, sm, m, nslabs, rho, vmax_in, vmax_reset, img, scales, zmat,
+                     (int)blockIdx.x);
+}
+
+// Batches: item (instance, slab), a persistent grid walks the list.
+template <int R>
+__global__ void __launch_bounds__(256) k_bfused_prep(const BInst* __restrict__ insts,
+                                                     const BItem* __restrict__ items, int nitems,
+                                                     int cur) {
+  for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
+    const BItem w = items[it];
+    const BInst& I = insts[w.inst];
+    if (I.st->stop) continue;            // uniform over the block
+    __syncthreads();                     // the previous item's shared memory is free
+    fused_prep_slab<R>(I.U[cur], I.sm, I.m, I.nslabs, I.rho, I.vmax + cur, I.vmax + (cur ^ 1),
+                       I.img, I.scales, I.zmat, w.a);
+  }
+}
+
+// out = in Z for n rows of R (V_old Z, added to the cluster's column sums):
+// block blk of 256 (row, column group of 8) entries (block-wide).
+template <int R>
+__device__ __forceinline__ void rowmat_block(const float* __restrict__ in,
+                                             const float* __restrict__ zmat, int64_t n,
+                                             float* __restrict__ out, int64_t blk) {
   __shared__ float Z[R * R];
   for (int i = threadIdx.x; i < R * R; i += 256) Z[i] = zmat[i];
   __syncthreads();
-  const int64_t idx = (int64_t)blockIdx.x * 256 + threadIdx.x;   // (row, column group of 8)
+  const int64_t idx = blk * 256 + threadIdx.x;   // (row, column group of 8)
   const int64_t row = idx / (R / 8);
   const int cg = (int)(idx % (R / 8));
   if (row >= n) return;
@@ -732,6 +772,41 @@ __global__ void __launch_bounds__(256) k_rowmat(const float* __restrict__ in,
   }
 #pragma unroll
   for (int l = 0; l < 8; ++l) out[row * R + cg * 8 + l] = acc[l];
+}
+
+template <int R>
+__global__ void __launch_bounds__(256) k_rowmat(const float* __restrict__ in,
+                                                const float* __restrict__ zmat, int64_t n,
+                                                float* __restrict__ out, const DevState* st) {
+  if (st->stop) return;
+  rowmat_block<R>(in, zmat, n, out, blockIdx.x);
+}
+
+// Batches: item (instance, block of 256 entries of V_old Z).
+template <int R>
+__global__ void __launch_bounds__(256) k_browmat(const BInst* __restrict__ insts,
+                                                 const BItem* __restrict__ items, int nitems,
+                                                 int cur) {
+  for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
+    const BItem w = items[it];
+    const BInst& I = insts[w.inst];
+    if (I.st->stop) continue;            // uniform over the block
+    __syncthreads();                     // the previous item's shared Z is free
+    rowmat_block<R>(I.V[cur], I.zmat, I.n, I.VZ, w.a);
+  }
+}
+
+cudaError_t launch_bfused_small(int R, int kind, const BInst* insts, const BItem* items,
+                                int nitems, int grid, int cur, cudaStream_t s) {
+  if (nitems == 0) return cudaSuccess;
+  if (kind == 0) {
+    if (R == 16) k_bfused_prep<16><<<grid, 256, 0, s>>>(insts, items, nitems, cur);
+    else k_bfused_prep<32><<<grid, 256, 0, s>>>(insts, items, nitems, cur);
+  } else {
+    if (R == 16) k_browmat<16><<<grid, 256, 0, s>>>(insts, items, nitems, cur);
+    else k_browmat<32><<<grid, 256, 0, s>>>(insts, items, nitems, cur);
+  }
+  return cudaGetLastError();
 }
 
 cudaError_t launch_rowmat(int R, const float* in, const float* zmat, int64_t n, float* out,
@@ -763,12 +838,19 @@ static size_t fused_smem() {
   return FL<R, NST>::TOTAL;
 }
 
-template <int R, int NST>
-static cudaError_t prep_attr() {
-  cudaError_t e = cudaFuncSetAttribute(k_fused<R, NST>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+template <int R, int NST, bool kTable>
+static cudaError_t prep_attr1() {
+  cudaError_t e = cudaFuncSetAttribute(k_fused<R, NST, kTable>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)fused_smem<R, NST>());
   if (e != cudaSuccess) return e;
-  return cudaFuncSetAttribute(k_fused<R, NST>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+  return cudaFuncSetAttribute(k_fused<R, NST, kTable>,
+                              cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+}
+template <int R, int NST>
+static cudaError_t prep_attr() {
+  cudaError_t e = prep_attr1<R, NST, false>();
+  return e != cudaSuccess ? e : prep_attr1<R, NST, true>();
 }
 
 cudaError_t fused_prepare(int R) {
@@ -789,7 +871,7 @@ static int max_clusters_T(int cs) {
   cfg.attrs = attr;
   cfg.numAttrs = 1;
   int n = 0;
-  if (cudaOccupancyMaxActiveClusters(&n, (void*)k_fused<R, NST>, &cfg) != cudaSuccess) {
+  if (cudaOccupancyMaxActiveClusters(&n, (void*)k_fused<R, NST, false>, &cfg) != cudaSuccess) {
     cudaGetLastError();
     return 0;
   }
@@ -856,11 +938,43 @@ static cudaError_t launch_fused_T(const void* tmap, const FusedArgs& fa, cudaStr
   cfg.attrs = attr;
   cfg.numAttrs = 1;
   const CUtensorMap* tm = reinterpret_cast<const CUtensorMap*>(tmap);
-  return cudaLaunchKernelEx(&cfg, k_fused<R, NST>, *tm, fa);
+  return cudaLaunchKernelEx(&cfg, k_fused<R, NST, false>, *tm, fa,
+                            static_cast<const FusedArgs*>(nullptr));
 }
 
 cudaError_t launch_fused(int R, const void* tmap, const FusedArgs& fa, cudaStream_t s) {
   return R == 16 ? launch_fused_T<16, kNST16>(tmap, fa, s) : launch_fused_T<32, kNST32>(tmap, fa, s);
+}
+
+template <int R, int NST>
+static cudaError_t launch_fused_table_T(int cs, int nclusters, const FusedArgs* table,
+                                        cudaStream_t s) {
+  cudaLaunchConfig_t cfg{};
+  cfg.gridDim = dim3(cs * nclusters, 1, 1);
+  cfg.blockDim = dim3(kFThreads, 1, 1);
+  cfg.dynamicSmemBytes = fused_smem<R, NST>();
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = cs;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  // the parameter-space tensor map is unused in table launches (each entry
+  // carries its own); only cs is read from the parameter block
+  CUtensorMap unused{};
+  FusedArgs ap{};
+  ap.cs = cs;
+  ap.nclusters = nclusters;
+  return cudaLaunchKernelEx(&cfg, k_fused<R, NST, true>, unused, ap, table);
+}
+
+cudaError_t launch_fused_table(int R, int cs, int nclusters, const FusedArgs* table,
+                               cudaStream_t s) {
+  if (nclusters < 1) return cudaSuccess;
+  return R == 16 ? launch_fused_table_T<16, kNST16>(cs, nclusters, table, s)
+                 : launch_fused_table_T<32, kNST32>(cs, nclusters, table, s);
 }
 
 cudaError_t launch_absmax(const float* x, int64_t count, unsigned int* out, cudaStream_t s) {

@@ -653,7 +653,7 @@ __global__ void __launch_bounds__(256) k_breduce(const BInst* __restrict__ insts
   }
   if (tail == TAIL_Q && threadIdx.x < 32) {
     double hs = 0.0;
-    for (int q = threadIdx.x; q < I.n_strips; q += 32) hs += I.part_h[q];
+    for (int q = threadIdx.x; q < I.n_hparts; q += 32) hs += I.part_h[q];
     for (int o = 16; o > 0; o >>= 1) hs += __shfl_xor_sync(0xffffffffu, hs, o);
     if (threadIdx.x == 0) red[2 * RR] = hs;
   }

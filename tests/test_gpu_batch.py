@@ -1,5 +1,9 @@
 """Parity of batched problems (dcf_batch_*) with the FP64 oracle.
 
+Instances of up to 4096 rows run their pass over M on the tensor-core kernel
+(one cluster per instance, m padded to a multiple of 4 with zero rows), the
+others on the general passes; both kinds share a batch below.
+
 Each instance of a batch must compute what the oracle computes for it alone:
 relative Frobenius error <= 1e-4 on U and V after one step from identical
 float32 starting points, <= 1e-3 after several steps, and every instance of a
@@ -24,6 +28,7 @@ SHAPES = [
     (300, [100, 77, 140], 20),
     (96, [64, 64], 32),
     (513, [129, 700], 8),
+    (4100, [150, 170], 6),      # past the tensor-core kernel's 4096 rows: general passes
 ]
 
 
