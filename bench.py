@@ -333,6 +333,38 @@ def run_e2e(dcf, torch, inst, wl, U0, stream, args, world):
             "d2h_bytes_per_step": 4 * m * r}
 
 
+def batch_fused(sh):
+    """Whether a batched instance runs on the tensor-core kernel (as dcf_batch_create
+    decides: at most 16 slabs of 256 rows after padding m to a multiple of 4)."""
+    return (sh["m"] + 3) // 4 * 4 <= 4096
+
+
+def batch_R(sh):
+    """Padded rank a batched instance runs with."""
+    if batch_fused(sh):
+        return 16 if sh["r"] <= 16 else 32
+    return 8 if sh["r"] <= 8 else 16 if sh["r"] <= 16 else 32
+
+
+def batch_launches_per_iter(shapes, report):
+    """Kernel launches of one batch iteration: per rank class, make_w / pass 1 /
+    pass 2 when it has general instances, the image and V_old Z kernels when it
+    has fused ones, the Gram, two reductions and the rows; plus one launch per
+    wave of the tensor-core kernel (from the tuner's report)."""
+    import re
+    n = 0
+    for R in (8, 16, 32):
+        members = [sh for sh in shapes if batch_R(sh) == R]
+        if not members:
+            continue
+        gen = any(not batch_fused(sh) for sh in members)
+        fus = any(batch_fused(sh) for sh in members)
+        n += 4 + (3 if gen else 0) + (2 if fus else 0)
+    for mt in re.finditer(r"in (\d+) waves", report):
+        n += int(mt.group(1))
+    return n
+
+
 def run_batched(args):
     """Batched workload: independent problems with m ~ U[256,1024], n ~ U[512,8192],
     E ~ U{4..16} uneven blocks, r = true rank ~ U{4..32} (synth.batched_instance_shapes),
@@ -359,8 +391,7 @@ def run_batched(args):
         b.load(q, Mt)
         torch.cuda.synchronize()
         del Mt
-        R = 8 if sh["r"] <= 8 else 16 if sh["r"] <= 16 else 32
-        alg += 4.0 * sh["m"] * sh["n"] + 8.0 * sh["n"] * R + 16.0 * sh["m"] * R
+        alg += 4.0 * sh["m"] * sh["n"] + 8.0 * sh["n"] * batch_R(sh) + 16.0 * sh["m"] * batch_R(sh)
     report = b.tune(reps=3)
     for _ in range(args.warmup):
         b.step(1)
@@ -391,26 +422,28 @@ def run_batched(args):
     b.close()
     if rank == 0:
         chosen = [ln for ln in report.splitlines() if "chosen" in ln]
+        launches = batch_launches_per_iter(shapes, report)
         line = {"metric": METRIC, "value": world * 1e3 / ms_step, "unit": "batch iters/s",
                 "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
                 "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "f32", "data": "synthetic",
                 "config": {"workload": f"batched_{len(shapes)}_instances",
                            "instances": len(shapes), "M_bytes": bytes_m,
-                           "kernel_path": "batched general two-pass (persistent item lists, "
-                                          "one CUDA graph per iteration)",
+                           "kernel_path": "tensor-core single pass (one cluster per instance, "
+                                          "waves per rank and cluster size) for m <= 4096, "
+                                          "general two-pass item lists otherwise; one CUDA "
+                                          "graph per iteration",
                            "tuned": chosen,
                            "l2": "inputs larger than L2 (%.1f GB of M)" % (bytes_m / 1e9)},
                 "clocks": clk,
                 "roofline": {"bound": "hbm", "kernel": "whole batched iteration",
                              "achieved": achieved, "peak": hbm, "unit": "GB/s",
                              "frac": achieved / hbm, "traffic": None,
-                             "note": "algorithmic bytes 4mn+8nR+16mR per instance; the "
-                                     "two-pass kernels read M twice",
+                             "note": "algorithmic bytes 4mn+8nR+16mR per instance (R the "
+                                     "padded rank the instance runs with)",
                              "phase_ms": phase_ms,
                              "peak_source": f"{peak_kind} hbm_gbs"},
-                "gpu_launches": 7 * len({8 if sh["r"] <= 8 else 16 if sh["r"] <= 16 else 32
-                                         for sh in shapes}) * args.steps,
+                "gpu_launches": launches * args.steps,
                 "e2e": None, "cpu_baseline": None}
         print(json.dumps(line), flush=True)
     if world > 1:

@@ -146,3 +146,18 @@ def test_errors():
         b.load(5, c["M"])
     assert e.value.status == dcf.DCF_EINVAL
     b.close()
+
+
+def test_more_problems_than_clusters():
+    """400 problems of 64 rows need three waves of the tensor-core kernel (one
+    cluster each, 152 clusters per launch on this GPU)."""
+    cs = [make_case(64, [40, 30], 4, seed=500 + q, density=0.05, amp=5.0) for q in range(400)]
+    b = batch_of(cs)
+    b.step(2)
+    for q in (0, 151, 152, 303, 399):
+        c = cs[q]
+        U, V = b.factors(q)
+        U2, V2, _, _, _ = O.dcf_run(c["M"], c["n_i"], c["U0"], c["V0"], c["rho"], c["lam"], 2)
+        L = U.astype(np.float64) @ V.T.astype(np.float64)
+        assert rel(L, U2 @ V2.T) <= 1e-4, (q, rel(L, U2 @ V2.T))
+    b.close()
