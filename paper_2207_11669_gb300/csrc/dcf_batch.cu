@@ -75,6 +75,11 @@ struct FusedGroup {
   int R = 0, cs = 0;
   std::vector<int> insts;                 // largest first
   std::vector<FusedWave> waves;
+  // the group's waves run on a stream of their own, forked from and joined
+  // back to the batch stream, so that the last (partial) wave of one group
+  // overlaps the waves of the others
+  cudaStream_t side = nullptr;
+  cudaEvent_t joined = nullptr;
 };
 
 constexpr int64_t kFusedMaxM = 4096;      // 16 slabs of 256 rows
@@ -96,6 +101,7 @@ struct dcf_batch_s {
   std::vector<FusedGroup> fgroups;
   std::vector<uint8_t*> tmaps;            // device tensor map of each fused instance
   int* kerr = nullptr;                    // fused kernel: a bounded wait expired
+  cudaEvent_t forked = nullptr;           // the fused phase may start on the side streams
   // allocation
   dcf_alloc_fn alloc = nullptr;
   dcf_free_fn release = nullptr;
@@ -279,10 +285,20 @@ cudaError_t enqueue_batch_iteration(dcf_batch b, int cur, cudaStream_t s,
           break;
       }
     }
-    if (ph == 1)   // the single pass over M of every fused instance, wave by wave
-      for (const FusedGroup& g : b->fgroups)
+    if (ph == 1 && !b->fgroups.empty()) {
+      // the single pass over M of every fused instance: each group's waves on
+      // its own stream (forked here, joined before the next phase)
+      if (e == cudaSuccess) e = cudaEventRecord(b->forked, s);
+      for (const FusedGroup& g : b->fgroups) {
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(g.side, b->forked, 0);
         for (const FusedWave& wv : g.waves)
-          if (e == cudaSuccess) e = launch_fused_table(g.R, g.cs, wv.nclusters, wv.table[cur], s);
+          if (e == cudaSuccess)
+            e = launch_fused_table(g.R, g.cs, wv.nclusters, wv.table[cur], g.side);
+        if (e == cudaSuccess) e = cudaEventRecord(g.joined, g.side);
+      }
+      for (const FusedGroup& g : b->fgroups)
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(s, g.joined, 0);
+    }
     if (e != cudaSuccess) return e;
     if (ev && (e = cudaEventRecord(ev[ph], s)) != cudaSuccess) return e;
   }
@@ -691,7 +707,19 @@ extern "C" dcf_status dcf_batch_create(const dcf_problem* problems, int count, i
     }
     b->fgroups[gi].insts.push_back(q);
   }
+  if (!b->fgroups.empty() &&
+      cudaEventCreateWithFlags(&b->forked, cudaEventDisableTiming) != cudaSuccess) {
+    cudaGetLastError();
+    dcf_batch_destroy(b);
+    return DCF_ECUDA;
+  }
   for (FusedGroup& g : b->fgroups) {
+    if (cudaStreamCreateWithFlags(&g.side, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&g.joined, cudaEventDisableTiming) != cudaSuccess) {
+      cudaGetLastError();
+      dcf_batch_destroy(b);
+      return DCF_ECUDA;
+    }
     std::stable_sort(g.insts.begin(), g.insts.end(), [&](int x, int y) {
       return b->host[x].n_strips > b->host[y].n_strips;
     });
@@ -935,6 +963,14 @@ extern "C" void dcf_batch_destroy(dcf_batch b) {
   if (b->stream) cudaStreamSynchronize(b->stream);
   for (int p = 0; p < 2; ++p)
     if (b->graph[p]) cudaGraphExecDestroy(b->graph[p]);
+  for (FusedGroup& g : b->fgroups) {
+    if (g.side) {
+      cudaStreamSynchronize(g.side);
+      cudaStreamDestroy(g.side);
+    }
+    if (g.joined) cudaEventDestroy(g.joined);
+  }
+  if (b->forked) cudaEventDestroy(b->forked);
   bfree_all(b);
   if (b->ev_in) cudaEventDestroy(b->ev_in);
   if (b->ev_out) cudaEventDestroy(b->ev_out);
