@@ -70,17 +70,15 @@ struct BatchClass {
 struct FusedWave {
   int nclusters = 0;
   FusedArgs* table[2] = {nullptr, nullptr};
+  int64_t cost = 0;                       // largest instance: strips x cluster size
+  int lane = 0;                           // side stream it is launched on
 };
 struct FusedGroup {
   int R = 0, cs = 0;
   std::vector<int> insts;                 // largest first
   std::vector<FusedWave> waves;
-  // the group's waves run on a stream of their own, forked from and joined
-  // back to the batch stream, so that the last (partial) wave of one group
-  // overlaps the waves of the others
-  cudaStream_t side = nullptr;
-  cudaEvent_t joined = nullptr;
 };
+constexpr int kFusedLanes = 8;            // side streams of the fused phase
 
 constexpr int64_t kFusedMaxM = 4096;      // 16 slabs of 256 rows
 
@@ -101,7 +99,12 @@ struct dcf_batch_s {
   std::vector<FusedGroup> fgroups;
   std::vector<uint8_t*> tmaps;            // device tensor map of each fused instance
   int* kerr = nullptr;                    // fused kernel: a bounded wait expired
-  cudaEvent_t forked = nullptr;           // the fused phase may start on the side streams
+  // the waves of the fused phase run on side streams (forked from and joined
+  // back to the batch stream): the block scheduler packs their clusters onto
+  // the SMs as earlier ones finish, across waves and groups
+  cudaEvent_t forked = nullptr;
+  std::vector<cudaStream_t> lanes;
+  std::vector<cudaEvent_t> joined;
   // allocation
   dcf_alloc_fn alloc = nullptr;
   dcf_free_fn release = nullptr;
@@ -286,18 +289,19 @@ cudaError_t enqueue_batch_iteration(dcf_batch b, int cur, cudaStream_t s,
       }
     }
     if (ph == 1 && !b->fgroups.empty()) {
-      // the single pass over M of every fused instance: each group's waves on
-      // its own stream (forked here, joined before the next phase)
+      // the single pass over M of every fused instance: waves on the side
+      // streams (forked here, joined before the next phase)
       if (e == cudaSuccess) e = cudaEventRecord(b->forked, s);
-      for (const FusedGroup& g : b->fgroups) {
-        if (e == cudaSuccess) e = cudaStreamWaitEvent(g.side, b->forked, 0);
+      for (cudaStream_t ln : b->lanes)
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(ln, b->forked, 0);
+      for (const FusedGroup& g : b->fgroups)
         for (const FusedWave& wv : g.waves)
           if (e == cudaSuccess)
-            e = launch_fused_table(g.R, g.cs, wv.nclusters, wv.table[cur], g.side);
-        if (e == cudaSuccess) e = cudaEventRecord(g.joined, g.side);
+            e = launch_fused_table(g.R, g.cs, wv.nclusters, wv.table[cur], b->lanes[wv.lane]);
+      for (size_t l = 0; l < b->lanes.size(); ++l) {
+        if (e == cudaSuccess) e = cudaEventRecord(b->joined[l], b->lanes[l]);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(s, b->joined[l], 0);
       }
-      for (const FusedGroup& g : b->fgroups)
-        if (e == cudaSuccess) e = cudaStreamWaitEvent(s, g.joined, 0);
     }
     if (e != cudaSuccess) return e;
     if (ev && (e = cudaEventRecord(ev[ph], s)) != cudaSuccess) return e;
@@ -707,19 +711,7 @@ extern "C" dcf_status dcf_batch_create(const dcf_problem* problems, int count, i
     }
     b->fgroups[gi].insts.push_back(q);
   }
-  if (!b->fgroups.empty() &&
-      cudaEventCreateWithFlags(&b->forked, cudaEventDisableTiming) != cudaSuccess) {
-    cudaGetLastError();
-    dcf_batch_destroy(b);
-    return DCF_ECUDA;
-  }
   for (FusedGroup& g : b->fgroups) {
-    if (cudaStreamCreateWithFlags(&g.side, cudaStreamNonBlocking) != cudaSuccess ||
-        cudaEventCreateWithFlags(&g.joined, cudaEventDisableTiming) != cudaSuccess) {
-      cudaGetLastError();
-      dcf_batch_destroy(b);
-      return DCF_ECUDA;
-    }
     std::stable_sort(g.insts.begin(), g.insts.end(), [&](int x, int y) {
       return b->host[x].n_strips > b->host[y].n_strips;
     });
@@ -727,6 +719,7 @@ extern "C" dcf_status dcf_batch_create(const dcf_problem* problems, int count, i
     for (size_t w0 = 0; w0 < g.insts.size(); w0 += (size_t)ncl) {
       FusedWave wv;
       wv.nclusters = (int)std::min<size_t>((size_t)ncl, g.insts.size() - w0);
+      wv.cost = (int64_t)b->host[g.insts[w0]].n_strips * g.cs;
       for (int cur = 0; cur < 2; ++cur) {
         std::vector<FusedArgs> tab(wv.nclusters);
         for (int c = 0; c < wv.nclusters; ++c) {
@@ -761,6 +754,34 @@ extern "C" dcf_status dcf_batch_create(const dcf_problem* problems, int count, i
         }
       }
       g.waves.push_back(wv);
+    }
+  }
+  // side streams: waves dealt longest first to the least loaded stream
+  {
+    std::vector<FusedWave*> all;
+    for (FusedGroup& g : b->fgroups)
+      for (FusedWave& wv : g.waves) all.push_back(&wv);
+    std::stable_sort(all.begin(), all.end(),
+                     [](const FusedWave* x, const FusedWave* y) { return x->cost > y->cost; });
+    const int nl = (int)std::min<size_t>(all.size(), (size_t)kFusedLanes);
+    std::vector<int64_t> load(nl, 0);
+    for (FusedWave* wv : all) {
+      const int l = (int)(std::min_element(load.begin(), load.end()) - load.begin());
+      wv->lane = l;
+      load[l] += wv->cost;
+    }
+    bool ok = !all.empty() ? cudaEventCreateWithFlags(&b->forked, cudaEventDisableTiming) ==
+                                 cudaSuccess
+                           : true;
+    b->lanes.assign(nl, nullptr);
+    b->joined.assign(nl, nullptr);
+    for (int l = 0; l < nl && ok; ++l)
+      ok = cudaStreamCreateWithFlags(&b->lanes[l], cudaStreamNonBlocking) == cudaSuccess &&
+           cudaEventCreateWithFlags(&b->joined[l], cudaEventDisableTiming) == cudaSuccess;
+    if (!ok) {
+      cudaGetLastError();
+      dcf_batch_destroy(b);
+      return DCF_ECUDA;
     }
   }
   b->dev = upload(b, b->host);
@@ -963,12 +984,12 @@ extern "C" void dcf_batch_destroy(dcf_batch b) {
   if (b->stream) cudaStreamSynchronize(b->stream);
   for (int p = 0; p < 2; ++p)
     if (b->graph[p]) cudaGraphExecDestroy(b->graph[p]);
-  for (FusedGroup& g : b->fgroups) {
-    if (g.side) {
-      cudaStreamSynchronize(g.side);
-      cudaStreamDestroy(g.side);
+  for (size_t l = 0; l < b->lanes.size(); ++l) {
+    if (b->lanes[l]) {
+      cudaStreamSynchronize(b->lanes[l]);
+      cudaStreamDestroy(b->lanes[l]);
     }
-    if (g.joined) cudaEventDestroy(g.joined);
+    if (b->joined[l]) cudaEventDestroy(b->joined[l]);
   }
   if (b->forked) cudaEventDestroy(b->forked);
   bfree_all(b);
