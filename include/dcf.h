@@ -78,7 +78,11 @@ typedef struct {
   int path;             /* 0: automatic; 1: general two-pass kernels; 2: fused
                            single-pass tensor-core kernel (DCF_EINVAL if the
                            shape does not qualify: r <= 32, m % 4 == 0,
-                           m <= 4096)                                          */
+                           m <= 4096); 3: two-pass tensor-core kernels (M
+                           read twice, no cross-CTA exchange; DCF_EINVAL
+                           unless m % 4 == 0).  Automatic: 2 where it
+                           qualifies, else 3 for m % 4 == 0 with m > 4096 or
+                           r > 32, else 1                                      */
 } dcf_params;
 
 /* Device allocator hook: alloc(bytes, ctx) returns device memory or NULL,
@@ -96,7 +100,7 @@ void dcf_set_allocator(dcf_alloc_fn alloc, dcf_free_fn release, void* ctx);
 dcf_status dcf_create(const dcf_params* p, dcf_handle* out);
 
 /* Which kernels run an iteration: 1 general two-pass path, 2 fused
- * single-pass tensor-core path. */
+ * single-pass tensor-core path, 3 two-pass tensor-core path. */
 int dcf_get_path(dcf_handle h);
 
 /* Enqueue all further work of the handle on `stream` (a cudaStream_t). */

@@ -115,6 +115,11 @@ IterArgs iter_args(dcf_handle h, int cur) {
     a.n_vblocks = h->cs * h->nclusters;   // per-CTA partials of the fused kernel
     a.n_splits = h->nclusters;            // P partials: one per cluster
   }
+  if (h->path == 3) {
+    a.add_uxv = 1;
+    a.n_vblocks = h->nslabs * h->G;       // Huber partials: one per CTA of pass A
+    a.n_splits = h->G;                    // P partials: one per strip group
+  }
   return a;
 }
 
@@ -131,9 +136,14 @@ constexpr int kNumPhases = 7;
 const char* const kFusedPhaseNames[] = {"fused_prep", "fused_step", "gram_v", "reduce_q",
                                         "rows_ustep", "reduce_g"};
 constexpr int kNumFusedPhases = 6;
-int num_phases(dcf_handle h) { return h->path == 2 ? kNumFusedPhases : kNumPhases; }
+const char* const kTc2PhaseNames[] = {"tc_prep", "pass_a", "v_reduce", "gram_v",
+                                      "reduce_q", "pass_b", "rows_ustep", "reduce_g"};
+constexpr int kNumTc2Phases = 8;
+int num_phases(dcf_handle h) {
+  return h->path == 2 ? kNumFusedPhases : h->path == 3 ? kNumTc2Phases : kNumPhases;
+}
 const char* phase_name(dcf_handle h, int p) {
-  return h->path == 2 ? kFusedPhaseNames[p] : kPhaseNames[p];
+  return h->path == 2 ? kFusedPhaseNames[p] : h->path == 3 ? kTc2PhaseNames[p] : kPhaseNames[p];
 }
 
 // One iteration of the fused path: prep (W and fp16 images), the single pass
@@ -188,10 +198,67 @@ cudaError_t enqueue_fused_iteration(dcf_handle h, int cur, cudaStream_t s, cudaE
   return mark();
 }
 
+// One iteration of the two-pass tensor-core path: prep, pass A (column sums
+// per slab), V' = V_old Z + their sum, Q/X_v and (Q + rho I)^{-1}, pass B (P
+// partials per strip group), consensus rows, metrics.
+cudaError_t enqueue_tc2_iteration(dcf_handle h, int cur, cudaStream_t s, cudaEvent_t* ev) {
+  IterArgs a = iter_args(h, cur);
+  const int nxt = cur ^ 1;
+  cudaError_t e;
+  int ph = 0;
+  auto mark = [&]() -> cudaError_t {
+    if (ev) return cudaEventRecord(ev[ph++], s);
+    return cudaSuccess;
+  };
+  if ((e = launch_fused_prep(h->R, h->U[cur], h->sm, h->st, h->m, h->nslabs, (float)h->rho,
+                             h->vmax + cur, h->vmax + nxt, h->img, h->scales, h->zmat, s)) !=
+          cudaSuccess ||
+      (e = launch_rowmat(h->R, h->V[cur], h->zmat, h->n, h->W_vz, h->st, s)) != cudaSuccess ||
+      (e = mark()) != cudaSuccess)
+    return e;
+  Tc2Args ta{};
+  ta.cur = cur;
+  ta.nslabs = h->nslabs;
+  ta.G = h->G;
+  ta.m = h->m;
+  ta.n = h->n;
+  ta.lam = (float)h->lam;
+  ta.Vold = h->V[cur];
+  ta.Vp = h->V[nxt];
+  ta.img = h->img;
+  ta.scales = h->scales;
+  ta.vp_max = h->vmax + nxt;
+  ta.ypart = h->ypart;
+  ta.part_h = h->part_h;
+  ta.part_p = h->part_p;
+  ta.st = h->st;
+  ta.err = h->kerr;
+  if ((e = launch_tc2(h->R, 0, h->tmap, ta, s)) != cudaSuccess || (e = mark()) != cudaSuccess)
+    return e;
+  if ((e = launch_tc2_vreduce(h->R, h->ypart, h->nslabs, h->W_vz, h->n, h->V[nxt],
+                              h->vmax + nxt, h->st, h->num_sms, s)) != cudaSuccess ||
+      (e = mark()) != cudaSuccess)
+    return e;
+  if ((e = launch_gram_vv(h->R, h->V[cur], h->V[nxt], h->n, h->part_q, h->part_xv, h->n_vgram,
+                          h->st, s)) != cudaSuccess ||
+      (e = mark()) != cudaSuccess)
+    return e;
+  if ((e = launch_reduce_q(a, red_q(h), red_xv(h), red_h(h), h->n_vgram, h->counters + 0, s)) !=
+          cudaSuccess ||
+      (e = mark()) != cudaSuccess)
+    return e;
+  if ((e = launch_tc2(h->R, 1, h->tmap, ta, s)) != cudaSuccess || (e = mark()) != cudaSuccess)
+    return e;
+  if ((e = launch_rows(a, s)) != cudaSuccess || (e = mark()) != cudaSuccess) return e;
+  if ((e = launch_reduce_g(a, red_g(h), red_xu(h), h->counters + 1, s)) != cudaSuccess) return e;
+  return mark();
+}
+
 // Enqueue one iteration reading copy `cur` (capturable).  When `ev` is not
 // NULL, event ev[p] is recorded after phase p (profiling path, not captured).
 cudaError_t enqueue_iteration(dcf_handle h, int cur, cudaStream_t s, cudaEvent_t* ev) {
   if (h->path == 2) return enqueue_fused_iteration(h, cur, s, ev);
+  if (h->path == 3) return enqueue_tc2_iteration(h, cur, s, ev);
   IterArgs a = iter_args(h, cur);
   const int nxt = cur ^ 1;
   cudaError_t e;
@@ -301,7 +368,7 @@ dcf_status finish_init(dcf_handle h, bool have_v0) {
   }
   CK(launch_gram(h->V[0], h->R, h->R, h->V[0], h->R, h->R, h->n, h->part_q, h->n_vgram, h->st, 0,
                  s), "gram V0");
-  if (h->path == 2) {
+  if (h->path == 2 || h->path == 3) {
     CK(cudaMemsetAsync(h->vmax, 0, 2 * sizeof(unsigned int), s), "memset");
     CK(launch_absmax(h->V[0], h->n * h->R, h->vmax, s), "max |V0|");
   }
@@ -420,6 +487,33 @@ extern "C" dcf_status dcf_create(const dcf_params* p, dcf_handle* out) {
       }
     }
   }
+  // two-pass tensor-core path: any m that is a multiple of 4 (TMA row stride),
+  // r <= 64; chosen automatically where the fused path does not apply because
+  // of the size (m > 4096 or r > 32)
+  {
+    const bool tc2_ok = h->m % 4 == 0;
+    if (p->path == 3 && !tc2_ok) {
+      dcf_destroy(h);
+      return DCF_EINVAL;
+    }
+    const bool want = p->path == 3 ||
+                      (p->path == 0 && h->path == 1 && tc2_ok && (h->m > 4096 || p->r > 32));
+    if (want) {
+      const int Rt = p->r <= 16 ? 16 : p->r <= 32 ? 32 : 64;
+      if (tc2_prepare(Rt) != cudaSuccess || (Rt == 64 && fused_prep_prepare() != cudaSuccess)) {
+        cudaGetLastError();
+        dcf_destroy(h);
+        return DCF_ECUDA;
+      }
+      h->path = 3;
+      h->R = Rt;
+      h->nslabs = (int)((h->m + 255) / 256);
+      const int64_t nstrips64 = (h->n + 63) / 64;
+      // one CTA per SM (the kernels hold 200+ KB of shared memory): slabs x strip
+      // groups at most one wave, every CTA with at least one strip
+      h->G = (int)std::max<int64_t>(1, std::min<int64_t>(h->num_sms / h->nslabs, nstrips64));
+    }
+  }
   // launch geometry
   const int64_t nstrips = (h->n + 63) / 64;
   h->n_vblocks = (int)std::min<int64_t>(nstrips, 3LL * h->num_sms);
@@ -469,7 +563,16 @@ extern "C" dcf_status dcf_create(const dcf_params* p, dcf_handle* out) {
     h->vmax = (unsigned int*)A(2 * sizeof(unsigned int));
     h->part_p = (float*)A((size_t)h->nclusters * h->m * R * 4);
     h->part_h = (double*)A(grid * 8);
-
+  }
+  if (h->path == 3) {
+    h->img = (uint8_t*)A((size_t)h->nslabs * 2048 * R);
+    h->scales = (float*)A((2 * (size_t)h->nslabs + 1) * sizeof(float));
+    h->zmat = (float*)A(RR * sizeof(float));
+    h->W_vz = (float*)A((size_t)h->n * R * sizeof(float));
+    h->vmax = (unsigned int*)A(2 * sizeof(unsigned int));
+    h->ypart = (float*)A((size_t)h->nslabs * h->n * R * sizeof(float));
+    h->part_p = (float*)A((size_t)h->G * h->m * R * 4);
+    h->part_h = (double*)A(std::max<size_t>((size_t)h->nslabs * h->G, h->n_vblocks) * 8);
   }
   if (!ok) {
     dcf_destroy(h);
@@ -542,7 +645,7 @@ extern "C" dcf_status dcf_load_blocks(dcf_handle h, const float* const* M_i, con
   CK(cudaMemcpyAsync(&flag, h->flag, sizeof(int), cudaMemcpyDeviceToHost, h->stream), "flag");
   CK(cudaStreamSynchronize(h->stream), "sync");
   if (flag) return fail(h, DCF_ENONFINITE, "M contains NaN or Inf");
-  if (h->path == 2 && fused_make_tmap(h->tmap, h->M, h->m, h->n) != 0)
+  if ((h->path == 2 || h->path == 3) && fused_make_tmap(h->tmap, h->M, h->m, h->n) != 0)
     return fail(h, DCF_ECUDA, "cuTensorMapEncodeTiled failed for M");
   h->loaded = true;
   h->initialized = false;

@@ -55,13 +55,15 @@ struct dcf_handle_s {
   int n_vblocks = 0, n_splits = 0, n_rblocks = 0, n_vgram = 0;
   int64_t split_cols = 0;
   // fused single-pass path
-  int path = 1;                       // 1 general, 2 fused
+  int path = 1;                       // 1 general, 2 fused, 3 two-pass tensor core
   int cs = 0, nclusters = 0, nslabs = 0;
   uint8_t* img = nullptr;
   float* scales = nullptr;
   float* zmat = nullptr;
   float* W_vz = nullptr;              // n x R, V_old Z (fused path)
   unsigned int* vmax = nullptr;       // [2]: max |V| of copy 0 / 1 (float bits)
+  float* ypart = nullptr;             // two-pass tensor core: [nslabs][n][R] column sums
+  int G = 0;                          // two-pass tensor core: strip groups (CTAs per slab)
   int* kerr = nullptr;                // kernel-side error (DCF_ETIMEOUT)
   alignas(64) unsigned char tmap[128];
   // state

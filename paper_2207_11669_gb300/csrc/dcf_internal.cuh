@@ -239,6 +239,33 @@ cudaError_t launch_fused_prep(int R, const float* U, const Smalls* sm, const Dev
                               unsigned int* vmax_reset, uint8_t* img, float* scales, float* zmat,
                               cudaStream_t s);
 cudaError_t launch_absmax(const float* x, int64_t count, unsigned int* out, cudaStream_t s);
+
+// Two-pass tensor-core path (k_tc2.cu), R = 16, 32 or 64.
+struct Tc2Args {
+  int cur;
+  int nslabs;
+  int G;                     // strip groups (CTAs per slab)
+  int64_t m, n;
+  float lam;
+  const float* Vold;         // n x R
+  const float* Vp;           // pass B: V' (n x R)
+  const uint8_t* img;        // [slab][U image | W image]
+  const float* scales;       // [2 slab] = s_u, [2 slab + 1] = s_w, [2 nslabs] = s_v
+  const unsigned int* vp_max;  // pass B: max |V'| (float bits)
+  float* ypart;              // pass A: [nslabs][n][R] column sums of C^T W
+  double* part_h;            // pass A: [nslabs * G] Huber partials
+  float* part_p;             // pass B: [G][m][R] P partials
+  const DevState* st;
+  int* err;
+};
+cudaError_t tc2_prepare(int R);
+cudaError_t launch_tc2(int R, int pass_b, const void* tmap, const Tc2Args& a, cudaStream_t s);
+cudaError_t launch_tc2_vreduce(int R, const float* ypart, int nslabs, const float* VZ, int64_t n,
+                               float* Vnew, unsigned int* vmax, const DevState* st,
+                               int num_sms, cudaStream_t s);
+// The image preparation of the tensor-core paths also takes R = 64 (dynamic
+// shared memory above 48 KB): call once per process before the first launch.
+cudaError_t fused_prep_prepare();
 cudaError_t launch_rowmat(int R, const float* in, const float* zmat, int64_t n, float* out,
                           const DevState* st, cudaStream_t s);
 

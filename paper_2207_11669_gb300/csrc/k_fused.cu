@@ -636,6 +636,13 @@ __global__ void __launch_bounds__(kFThreads, 1)
 // Per-iteration preparation: W rows, fp16 hi/lo images of U and W per 256-row
 // slab with power-of-two scales, Z = I - rho G^{-1}, and the V scale.
 // ---------------------------------------------------------------------------
+// Dynamic shared memory of the preparation kernels: G^{-1} (R x R floats),
+// the W image staging (2R x 256 fp16), 16 floats of reductions.
+template <int R>
+constexpr int prep_smem() {
+  return R * R * 4 + 2 * R * kFH * 2 + 16 * 4;
+}
+
 // One 256-row slab (block-wide, 256 threads).
 template <int R>
 __device__ __forceinline__ void fused_prep_slab(const float* __restrict__ U, const Smalls* sm,
@@ -643,9 +650,10 @@ __device__ __forceinline__ void fused_prep_slab(const float* __restrict__ U, con
                                                 const unsigned int* vmax_in,
                                                 unsigned int* vmax_reset, uint8_t* img,
                                                 float* scales, float* zmat, int slab) {
-  __shared__ float gi[R * R];
-  __shared__ __align__(16) uint8_t wst[2 * R * kFH * 2];
-  __shared__ float red[2][8];
+  extern __shared__ __align__(16) uint8_t psm[];
+  float* gi = reinterpret_cast<float*>(psm);
+  uint8_t* wst = psm + R * R * 4;
+  float(*red)[8] = reinterpret_cast<float(*)[8]>(wst + 2 * R * kFH * 2);
   const int tid = threadIdx.x;
   for (int i = tid; i < R * R; i += 256) gi[i] = sm->ginv32[i];
   __syncthreads();
@@ -800,8 +808,8 @@ cudaError_t launch_bfused_small(int R, int kind, const BInst* insts, const BItem
                                 int nitems, int grid, int cur, cudaStream_t s) {
   if (nitems == 0) return cudaSuccess;
   if (kind == 0) {
-    if (R == 16) k_bfused_prep<16><<<grid, 256, 0, s>>>(insts, items, nitems, cur);
-    else k_bfused_prep<32><<<grid, 256, 0, s>>>(insts, items, nitems, cur);
+    if (R == 16) k_bfused_prep<16><<<grid, 256, prep_smem<16>(), s>>>(insts, items, nitems, cur);
+    else k_bfused_prep<32><<<grid, 256, prep_smem<32>(), s>>>(insts, items, nitems, cur);
   } else {
     if (R == 16) k_browmat<16><<<grid, 256, 0, s>>>(insts, items, nitems, cur);
     else k_browmat<32><<<grid, 256, 0, s>>>(insts, items, nitems, cur);
@@ -814,7 +822,8 @@ cudaError_t launch_rowmat(int R, const float* in, const float* zmat, int64_t n, 
   const int64_t items = n * (R / 8);
   const unsigned grid = (unsigned)((items + 255) / 256);
   if (R == 16) k_rowmat<16><<<grid, 256, 0, s>>>(in, zmat, n, out, st);
-  else k_rowmat<32><<<grid, 256, 0, s>>>(in, zmat, n, out, st);
+  else if (R == 32) k_rowmat<32><<<grid, 256, 0, s>>>(in, zmat, n, out, st);
+  else k_rowmat<64><<<grid, 256, 0, s>>>(in, zmat, n, out, st);
   return cudaGetLastError();
 }
 
@@ -915,12 +924,20 @@ cudaError_t launch_fused_prep(int R, const float* U, const Smalls* sm, const Dev
                               unsigned int* vmax_reset, uint8_t* img, float* scales, float* zmat,
                               cudaStream_t s) {
   if (R == 16)
-    k_fused_prep<16><<<nslabs, 256, 0, s>>>(U, sm, st, m, nslabs, rho, vmax_in, vmax_reset, img,
-                                            scales, zmat);
+    k_fused_prep<16><<<nslabs, 256, prep_smem<16>(), s>>>(U, sm, st, m, nslabs, rho, vmax_in,
+                                                          vmax_reset, img, scales, zmat);
+  else if (R == 32)
+    k_fused_prep<32><<<nslabs, 256, prep_smem<32>(), s>>>(U, sm, st, m, nslabs, rho, vmax_in,
+                                                          vmax_reset, img, scales, zmat);
   else
-    k_fused_prep<32><<<nslabs, 256, 0, s>>>(U, sm, st, m, nslabs, rho, vmax_in, vmax_reset, img,
-                                            scales, zmat);
+    k_fused_prep<64><<<nslabs, 256, prep_smem<64>(), s>>>(U, sm, st, m, nslabs, rho, vmax_in,
+                                                          vmax_reset, img, scales, zmat);
   return cudaGetLastError();
+}
+
+cudaError_t fused_prep_prepare() {
+  return cudaFuncSetAttribute(k_fused_prep<64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              prep_smem<64>());
 }
 
 template <int R, int NST>

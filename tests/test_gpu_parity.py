@@ -22,6 +22,8 @@ SHAPES = [
     (257, [300, 211], 40),
     (64, [10, 9, 11], 8),
     (1000, [700, 1300, 517], 32),
+    (260, [300, 211], 40),          # R = 64 on the two-pass tensor-core path
+    (4100, [150, 170], 6),          # 17 slabs: past the fused kernel's cluster
 ]
 
 
@@ -39,7 +41,15 @@ def fused_ok(m, r):
     return r <= 32 and m % 4 == 0 and (m + 255) // 256 <= 16
 
 
-PATHS = [dcf.PATH_GENERAL, dcf.PATH_FUSED]
+def path_ok(path, m, r):
+    if path == dcf.PATH_FUSED:
+        return fused_ok(m, r)
+    if path == dcf.PATH_TC2:
+        return m % 4 == 0
+    return True
+
+
+PATHS = [dcf.PATH_GENERAL, dcf.PATH_FUSED, dcf.PATH_TC2]
 
 
 def gpu_solver(case, **kw):
@@ -57,8 +67,8 @@ def oracle_step(case, iters=1, **kw):
 @pytest.mark.parametrize("path", PATHS)
 @pytest.mark.parametrize("m,n_i,r", SHAPES)
 def test_one_step_parity(m, n_i, r, path):
-    if path == dcf.PATH_FUSED and not fused_ok(m, r):
-        pytest.skip("shape outside the fused path")
+    if not path_ok(path, m, r):
+        pytest.skip("shape outside this path")
     case = make_case(m, n_i, r, seed=m + r)
     s = gpu_solver(case, path=path)
     assert s.path == path
@@ -130,8 +140,18 @@ def test_fused_path_is_chosen_automatically():
     s.close()
     case = make_case(257, [300, 211], 40, seed=21)
     s = gpu_solver(case)
-    assert s.path == dcf.PATH_GENERAL
+    assert s.path == dcf.PATH_GENERAL          # m % 4 != 0: no tensor map
     s.close()
+    case = make_case(260, [300, 211], 40, seed=21)
+    s = gpu_solver(case)
+    assert s.path == dcf.PATH_TC2              # r > 32
+    s.close()
+    case = make_case(4100, [150, 170], 6, seed=21)
+    s = gpu_solver(case)
+    assert s.path == dcf.PATH_TC2              # more than 16 slabs
+    s.close()
+    with pytest.raises(dcf.DcfError):
+        dcf.Solver(257, [300, 211], 40, 1e-2, 0.1, path=dcf.PATH_TC2)
     with pytest.raises(dcf.DcfError):
         dcf.Solver(257, [300, 211], 40, 1e-2, 0.1, path=dcf.PATH_FUSED)
 
