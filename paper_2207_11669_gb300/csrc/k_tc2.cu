@@ -284,8 +284,11 @@ __global__ void __launch_bounds__(kTThreads, 1)
           }
         }
       }
-      // every MMA of this thread (GEMM3 of the last strip included) has completed
+      // every MMA of this thread has completed (and its commits have landed)
+      // before the CTA releases tensor memory and shared memory; pass B's
+      // epilogue also reads the P partial after this
       tc::mma_commit(B(b_last));
+      if (!wait_(B(b_last), 0)) err = 1;
     }
   } else if (warp == 2) {
     // ================= V_old image (GEMM1 operand), one chunk ahead ============
