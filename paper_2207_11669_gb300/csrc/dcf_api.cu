@@ -416,7 +416,7 @@ extern "C" dcf_status dcf_create(const dcf_params* p, dcf_handle* out) {
   if (p->u_mode != 0 && p->u_mode != 1) return bad("u_mode");
   if (p->local_steps != 1) return bad("local_steps");
   if (p->max_iter < 1) return bad("max_iter");
-  if (p->path < 0 || p->path > 2) return bad("path");
+  if (p->path < 0 || p->path > 3) return bad("path");
   h->m = p->m;
   h->E = p->E;
   h->r = p->r;
