@@ -261,7 +261,7 @@ def run_ours(args):
         tdist.barrier()
     ms_step = ms / args.steps
     value = world * 1e3 / ms_step
-    launches_per_iter = 8   # kernels per iteration on either path (graph nodes)
+    launches_per_iter = 9 if path_id == 3 else 8   # kernels per iteration (graph nodes)
 
     # per-kernel phases, CUDA events on the launch stream, same workload
     phases = dcf.dcf_profile_step(s.h, max(3, min(args.steps, 10)))
@@ -273,6 +273,15 @@ def run_ours(args):
     kbytes = {"pass1_vstep": 4.0 * m * n + 8.0 * n * r + 8.0 * m * r,
               "pass2_pstep": 4.0 * m * n + 8.0 * n * r + 4.0 * m * r,
               "fused_step": 4.0 * m * n + 8.0 * n * r + 8.0 * m * r}
+    if path_id == 3:
+        # two-pass tensor-core kernels: each reads M once; pass A also writes the
+        # per-slab column sums, pass B the per-strip-group P partials
+        Rp = 16 if r <= 16 else 32 if r <= 32 else 64
+        nslabs = (m + 255) // 256
+        G = max(1, min(torch.cuda.get_device_properties(local).multi_processor_count // nslabs,
+                       (n + 63) // 64))
+        kbytes["pass_a"] = 4.0 * m * n + 4.0 * n * Rp + 4.0 * nslabs * n * Rp + 8.0 * m * Rp
+        kbytes["pass_b"] = 4.0 * m * n + 8.0 * n * Rp + 4.0 * G * m * Rp + 4.0 * m * Rp
     hbm, peak_kind = peaks()
     achieved = kbytes.get(dom, alg_bytes_per_iter(m, n, r)) / (phase_ms[dom] * 1e-3) / 1e9
     roofline = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": hbm,
@@ -296,7 +305,8 @@ def run_ours(args):
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
                 "dtype": "f32", "data": "synthetic",
                 "config": {"workload": wl.name, "m": m, "n": n, "E": int(wl.E), "r": r,
-                           "kernel_path": {1: "general two-pass", 2: "fused single-pass tcgen05"}.get(path_id),
+                           "kernel_path": {1: "general two-pass", 2: "fused single-pass tcgen05",
+                                           3: "two-pass tcgen05"}.get(path_id),
                            "rank_truth": wl.k, "density": wl.density, "rho": wl.rho,
                            "lambda": wl.lam, "parallelism": "replicas" if world > 1 else "1gpu",
                            "l2": "inputs larger than L2 (M is %.0f MiB)" % (4.0 * m * n / 2**20)},
