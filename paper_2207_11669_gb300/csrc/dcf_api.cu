@@ -881,7 +881,9 @@ extern "C" dcf_status dcf_profile_step(dcf_handle h, int n_steps, double* phase_
   if (st != DCF_OK) return st;
   if ((st = ensure_init(h)) != DCF_OK) return st;
   const int np = num_phases(h);
-  cudaEvent_t ev[kNumPhases + 1];
+  constexpr int kMaxPhases = kNumTc2Phases;   // the largest phase count of the three paths
+  static_assert(kNumTc2Phases >= kNumPhases && kNumTc2Phases >= kNumFusedPhases, "phases");
+  cudaEvent_t ev[kMaxPhases + 1];
   for (int p = 0; p <= np; ++p) CK(cudaEventCreate(&ev[p]), "event");
   for (int p = 0; p < np; ++p) phase_ms[p] = 0.0;
   for (int i = 0; i < n_steps; ++i) {
