@@ -97,10 +97,10 @@ struct TL {
 // Warp roles (16 warps):
 //   warp 0       TMA producer: M sub-tiles into a ring of NST slots
 //   warp 1       MMA issuer: GEMM1 (strip i), then GEMM2 (A) or GEMM3 (B) of strip i-1
-//   warp 2       fp16 image of V_old (B operand of GEMM1), one strip ahead
-//   warp 3       pass B: fp16 image of V' (B operand of GEMM3), double-buffered
+//   warps 2-3    fp16 image of V_old (B operand of GEMM1), one strip ahead
 //   warps 4-11   S-step epilogue: C/lambda into a C tile (and the Huber sum in A)
-//   warps 12-15  pass A: column sums out of tensor memory into the slab's partials
+//   warps 12-15  pass A: column sums out of tensor memory into the slab's partials;
+//                pass B: fp16 image of V' (B operand of GEMM3), double-buffered
 template <int R, int NST, bool kB>
 __global__ void __launch_bounds__(kTThreads, 1)
     k_tc2(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ Tc2Args a) {
@@ -135,7 +135,7 @@ __global__ void __launch_bounds__(kTThreads, 1)
       tc::mbar_init(B(b_full + i), 1);
       tc::mbar_init(B(b_empty + i), 8);     // the 8 epilogue warps
     }
-    tc::mbar_init(B(b_vfull), 1);           // the V image warp
+    tc::mbar_init(B(b_vfull), 2);           // the 2 V image warps
     tc::mbar_init(B(b_vempty), 1);          // GEMM1 commit
     for (int p = 0; p < 2; ++p) {
       tc::mbar_init(B(b_d1full + p), 1);    // GEMM1 commit
@@ -147,8 +147,8 @@ __global__ void __launch_bounds__(kTThreads, 1)
     }
     for (int p = 0; p < 2; ++p) {
       // pass A: D2 result (GEMM2 commit) / read by the 4 writer warps
-      // pass B: V' image written (the V' warp) / read by GEMM3 (commit)
-      tc::mbar_init(B(b_xfull + p), 1);
+      // pass B: V' image written (the 4 V' warps) / read by GEMM3 (commit)
+      tc::mbar_init(B(b_xfull + p), kB ? 4 : 1);
       tc::mbar_init(B(b_xempty + p), kB ? 1 : 4);
     }
     tc::mbar_init(B(b_img), 1);
@@ -290,86 +290,45 @@ __global__ void __launch_bounds__(kTThreads, 1)
       tc::mma_commit(B(b_last));
       if (!wait_(B(b_last), 0)) err = 1;
     }
-  } else if (warp == 2) {
-    // ================= V_old image (GEMM1 operand), one chunk ahead ============
-    // chunks of at most 16 float4 per lane (a strip of 64 x R floats is
-    // kTW * R / 128 float4 per lane); the next chunk (of this strip or the next)
-    // is loaded while the current one is written
-    constexpr int V4 = kTW * R / 128;
-    constexpr int CH = V4 > 16 ? 16 : V4;
-    constexpr int NCH = V4 / CH;
-    float4 vr[CH];
-    auto load_v = [&](int ls, int ch) {
+  } else if (warp == 2 || warp == 3) {
+    // ================= V_old image (GEMM1 operand), one strip ahead ============
+    // two warps, each a half of the strip's 64 x R floats (kTW * R / 256 float4
+    // per lane), the next strip's half loaded while this one is written
+    constexpr int V4 = kTW * R / 256;
+    const int half = warp - 2;
+    float4 vr[V4];
+    auto load_v = [&](int ls) {
       const int64_t col0 = strip_col0(ls);
 #pragma unroll
-      for (int t = 0; t < CH; ++t) {
-        const int e = 4 * (lane + 32 * (ch * CH + t)), j = e / R, k = e % R;
+      for (int t = 0; t < V4; ++t) {
+        const int e = 4 * (lane + 32 * (half * V4 + t)), j = e / R, k = e % R;
         vr[t] = col0 + j < a.n ? *reinterpret_cast<const float4*>(a.Vold + (col0 + j) * R + k)
                                : make_float4(0.f, 0.f, 0.f, 0.f);
       }
     };
-    if (S > 0) load_v(0, 0);
+    if (S > 0) load_v(0);
     for (int ls = 0; ls < S; ++ls) {
       if (ls >= 1 && !wait_(B(b_vempty), (uint32_t)((ls - 1) & 1))) err = 1;
       uint8_t* img = smem + L::VIMG;
-      for (int ch = 0; ch < NCH; ++ch) {
 #pragma unroll
-        for (int t = 0; t < CH; ++t) {
-          const int e = 4 * (lane + 32 * (ch * CH + t)), j = e / R, k = e % R;
-          const float x[4] = {vr[t].x, vr[t].y, vr[t].z, vr[t].w};
-          __half hi[4], lo[4];
+      for (int t = 0; t < V4; ++t) {
+        const int e = 4 * (lane + 32 * (half * V4 + t)), j = e / R, k = e % R;
+        const float x[4] = {vr[t].x, vr[t].y, vr[t].z, vr[t].w};
+        __half hi[4], lo[4];
 #pragma unroll
-          for (int u = 0; u < 4; ++u) tsplit(x[u], s_v, hi[u], lo[u]);
-          const int off = (j >> 3) * SB_R + (k >> 3) * 128 + (j & 7) * 16 + (k & 7) * 2;
-          __half2 h01 = __halves2half2(hi[0], hi[1]), h23 = __halves2half2(hi[2], hi[3]);
-          __half2 l01 = __halves2half2(lo[0], lo[1]), l23 = __halves2half2(lo[2], lo[3]);
-          *reinterpret_cast<uint2*>(img + off) =
-              make_uint2(*reinterpret_cast<uint32_t*>(&h01), *reinterpret_cast<uint32_t*>(&h23));
-          *reinterpret_cast<uint2*>(img + kTW * R * 2 + off) =
-              make_uint2(*reinterpret_cast<uint32_t*>(&l01), *reinterpret_cast<uint32_t*>(&l23));
-        }
-        if (ch + 1 < NCH) load_v(ls, ch + 1);
+        for (int u = 0; u < 4; ++u) tsplit(x[u], s_v, hi[u], lo[u]);
+        const int off = (j >> 3) * SB_R + (k >> 3) * 128 + (j & 7) * 16 + (k & 7) * 2;
+        __half2 h01 = __halves2half2(hi[0], hi[1]), h23 = __halves2half2(hi[2], hi[3]);
+        __half2 l01 = __halves2half2(lo[0], lo[1]), l23 = __halves2half2(lo[2], lo[3]);
+        *reinterpret_cast<uint2*>(img + off) =
+            make_uint2(*reinterpret_cast<uint32_t*>(&h01), *reinterpret_cast<uint32_t*>(&h23));
+        *reinterpret_cast<uint2*>(img + kTW * R * 2 + off) =
+            make_uint2(*reinterpret_cast<uint32_t*>(&l01), *reinterpret_cast<uint32_t*>(&l23));
       }
       tc::fence_proxy_async_smem();
       __syncwarp();
       if (lane == 0) tc::mbar_arrive(B(b_vfull));
-      if (ls + 1 < S) load_v(ls + 1, 0);
-    }
-  } else if (warp == 3) {
-    // ================= pass B: V' image (GEMM3 operand), double-buffered ========
-    // entry (n, j), n = k (hi) or R + k (lo), j the strip column:
-    //   (n / 8) * 1024 + (j / 8) * 128 + (n % 8) * 16 + (j % 8) * 2
-    // a lane fills 8 consecutive columns of one k (16 bytes of hi, 16 of lo)
-    if (kB) {
-      for (int ls = 0; ls < S; ++ls) {
-        const int p = ls & 1;
-        if (ls >= 2 && !wait_(B(b_xempty + p), (uint32_t)(((ls >> 1) - 1) & 1))) err = 1;
-        const int64_t col0 = strip_col0(ls);
-        uint8_t* img = smem + L::PIMG + p * L::PBYTES;
-        for (int task = lane; task < 8 * R; task += 32) {
-          const int jb = task / R, k = task % R;
-          uint32_t hw[4], lw[4];
-#pragma unroll
-          for (int jj = 0; jj < 8; jj += 2) {
-            const int64_t c0 = col0 + jb * 8 + jj;
-            const float x0 = c0 < a.n ? a.Vp[c0 * R + k] : 0.f;
-            const float x1 = c0 + 1 < a.n ? a.Vp[(c0 + 1) * R + k] : 0.f;
-            __half h0, l0, h1, l1;
-            tsplit(x0, s_p, h0, l0);
-            tsplit(x1, s_p, h1, l1);
-            __half2 hh = __halves2half2(h0, h1), ll = __halves2half2(l0, l1);
-            hw[jj / 2] = *reinterpret_cast<uint32_t*>(&hh);
-            lw[jj / 2] = *reinterpret_cast<uint32_t*>(&ll);
-          }
-          const int off = (k >> 3) * 1024 + jb * 128 + (k & 7) * 16;
-          *reinterpret_cast<uint4*>(img + off) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
-          *reinterpret_cast<uint4*>(img + (R / 8) * 1024 + off) =
-              make_uint4(lw[0], lw[1], lw[2], lw[3]);
-        }
-        tc::fence_proxy_async_smem();
-        __syncwarp();
-        if (lane == 0) tc::mbar_arrive(B(b_xfull + p));
-      }
+      if (ls + 1 < S) load_v(ls + 1);
     }
   } else if (warp < 12) {
     // ================= S-step epilogue (256 threads, thread = row) ===============
@@ -494,6 +453,68 @@ __global__ void __launch_bounds__(kTThreads, 1)
               make_float4(yv[k] * y_scale, yv[k + 1] * y_scale, yv[k + 2] * y_scale,
                           yv[k + 3] * y_scale);
       }
+    }
+  } else {
+    // ================= pass B: V' image (GEMM3 operand), double-buffered ========
+    // entry (n, j), n = k (hi) or R + k (lo), j the strip column:
+    //   (n / 8) * 1024 + (j / 8) * 128 + (n % 8) * 16 + (j % 8) * 2
+    // task (column group jb of 8, quad of k): 8 float4 loads, 4 x (16 bytes hi,
+    // 16 bytes lo); 8 R / 4 tasks over the 128 threads, the next strip's values
+    // loaded while this one is written
+    constexpr int NT = 8 * R / 4;                 // tasks per strip
+    constexpr int TPT = (NT + 127) / 128;         // tasks per thread
+    const int xt = tid - 384;
+    float4 pv[TPT][8];
+    auto load_p = [&](int ls) {
+      const int64_t col0 = strip_col0(ls);
+#pragma unroll
+      for (int u = 0; u < TPT; ++u) {
+        const int task = xt + 128 * u;
+        const int jb = task / (R / 4), k4 = (task % (R / 4)) * 4;
+#pragma unroll
+        for (int jj = 0; jj < 8; ++jj) {
+          const int64_t c = col0 + jb * 8 + jj;
+          pv[u][jj] = (task < NT && c < a.n) ? *reinterpret_cast<const float4*>(a.Vp + c * R + k4)
+                                             : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+      }
+    };
+    if (S > 0) load_p(0);
+    for (int ls = 0; ls < S; ++ls) {
+      const int p = ls & 1;
+      if (ls >= 2 && !wait_(B(b_xempty + p), (uint32_t)(((ls >> 1) - 1) & 1))) err = 1;
+      uint8_t* img = smem + L::PIMG + p * L::PBYTES;
+#pragma unroll
+      for (int u = 0; u < TPT; ++u) {
+        const int task = xt + 128 * u;
+        if (task >= NT) continue;
+        const int jb = task / (R / 4), k4 = (task % (R / 4)) * 4;
+#pragma unroll
+        for (int kq = 0; kq < 4; ++kq) {
+          uint32_t hw[4], lw[4];
+#pragma unroll
+          for (int jj = 0; jj < 8; jj += 2) {
+            const float x0 = kq == 0 ? pv[u][jj].x : kq == 1 ? pv[u][jj].y : kq == 2 ? pv[u][jj].z : pv[u][jj].w;
+            const float x1 = kq == 0 ? pv[u][jj + 1].x : kq == 1 ? pv[u][jj + 1].y
+                           : kq == 2 ? pv[u][jj + 1].z : pv[u][jj + 1].w;
+            __half h0, l0, h1, l1;
+            tsplit(x0, s_p, h0, l0);
+            tsplit(x1, s_p, h1, l1);
+            __half2 hh = __halves2half2(h0, h1), ll = __halves2half2(l0, l1);
+            hw[jj / 2] = *reinterpret_cast<uint32_t*>(&hh);
+            lw[jj / 2] = *reinterpret_cast<uint32_t*>(&ll);
+          }
+          const int k = k4 + kq;
+          const int off = (k >> 3) * 1024 + jb * 128 + (k & 7) * 16;
+          *reinterpret_cast<uint4*>(img + off) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
+          *reinterpret_cast<uint4*>(img + (R / 8) * 1024 + off) =
+              make_uint4(lw[0], lw[1], lw[2], lw[3]);
+        }
+      }
+      tc::fence_proxy_async_smem();
+      __syncwarp();
+      if (lane == 0) tc::mbar_arrive(B(b_xfull + p));
+      if (ls + 1 < S) load_p(ls + 1);
     }
   }
 
