@@ -80,9 +80,13 @@ typedef struct {
                            shape does not qualify: r <= 32, m % 4 == 0,
                            m <= 4096); 3: two-pass tensor-core kernels (M
                            read twice, no cross-CTA exchange; DCF_EINVAL
-                           unless m % 4 == 0).  Automatic: 2 where it
-                           qualifies, else 3 for m % 4 == 0 with m > 4096 or
-                           r > 32, else 1                                      */
+                           unless m % 4 == 0); 4: whole solve in one CTA,
+                           every iteration of a dcf_step / dcf_solve call in
+                           one launch (DCF_EINVAL unless u_mode = 0, r <= 16
+                           and M with the factors fits in one SM's shared
+                           memory, about 200 x 200).  Automatic: 4 where it
+                           fits, else 2 where it qualifies, else 3 for
+                           m % 4 == 0 with m > 4096 or r > 32, else 1         */
 } dcf_params;
 
 /* Device allocator hook: alloc(bytes, ctx) returns device memory or NULL,
@@ -100,7 +104,8 @@ void dcf_set_allocator(dcf_alloc_fn alloc, dcf_free_fn release, void* ctx);
 dcf_status dcf_create(const dcf_params* p, dcf_handle* out);
 
 /* Which kernels run an iteration: 1 general two-pass path, 2 fused
- * single-pass tensor-core path, 3 two-pass tensor-core path. */
+ * single-pass tensor-core path, 3 two-pass tensor-core path, 4 whole solve in
+ * one CTA. */
 int dcf_get_path(dcf_handle h);
 
 /* Enqueue all further work of the handle on `stream` (a cudaStream_t). */

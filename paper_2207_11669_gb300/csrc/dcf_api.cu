@@ -139,11 +139,34 @@ constexpr int kNumFusedPhases = 6;
 const char* const kTc2PhaseNames[] = {"tc_prep", "pass_a", "v_reduce", "gram_v",
                                       "reduce_q", "pass_b", "rows_ustep", "reduce_g"};
 constexpr int kNumTc2Phases = 8;
+const char* const kSmallPhaseNames[] = {"solve_small"};
 int num_phases(dcf_handle h) {
-  return h->path == 2 ? kNumFusedPhases : h->path == 3 ? kNumTc2Phases : kNumPhases;
+  return h->path == 2 ? kNumFusedPhases
+         : h->path == 3 ? kNumTc2Phases
+         : h->path == 4 ? 1
+                        : kNumPhases;
 }
 const char* phase_name(dcf_handle h, int p) {
-  return h->path == 2 ? kFusedPhaseNames[p] : h->path == 3 ? kTc2PhaseNames[p] : kPhaseNames[p];
+  return h->path == 2 ? kFusedPhaseNames[p]
+         : h->path == 3 ? kTc2PhaseNames[p]
+         : h->path == 4 ? kSmallPhaseNames[p]
+                        : kPhaseNames[p];
+}
+
+// Path 4: `n_iter` iterations of the whole-solve kernel from copy `cur`.
+cudaError_t enqueue_small(dcf_handle h, int cur, int n_iter, cudaStream_t s) {
+  SmallSolveArgs sa{};
+  sa.M = h->M;
+  sa.m = h->m;
+  sa.n = h->n;
+  sa.U[0] = h->U[0]; sa.U[1] = h->U[1];
+  sa.V[0] = h->V[0]; sa.V[1] = h->V[1];
+  sa.cur = cur;
+  sa.n_iter = n_iter;
+  sa.lam = (float)h->lam;
+  sa.rho = (float)h->rho;
+  sa.st = h->st;
+  return launch_solve_small(h->R, sa, s);
 }
 
 // One iteration of the fused path: prep (W and fp16 images), the single pass
@@ -259,6 +282,11 @@ cudaError_t enqueue_tc2_iteration(dcf_handle h, int cur, cudaStream_t s, cudaEve
 cudaError_t enqueue_iteration(dcf_handle h, int cur, cudaStream_t s, cudaEvent_t* ev) {
   if (h->path == 2) return enqueue_fused_iteration(h, cur, s, ev);
   if (h->path == 3) return enqueue_tc2_iteration(h, cur, s, ev);
+  if (h->path == 4) {
+    cudaError_t e = enqueue_small(h, cur, 1, s);
+    if (e == cudaSuccess && ev) e = cudaEventRecord(ev[0], s);
+    return e;
+  }
   IterArgs a = iter_args(h, cur);
   const int nxt = cur ^ 1;
   cudaError_t e;
@@ -416,7 +444,7 @@ extern "C" dcf_status dcf_create(const dcf_params* p, dcf_handle* out) {
   if (p->u_mode != 0 && p->u_mode != 1) return bad("u_mode");
   if (p->local_steps != 1) return bad("local_steps");
   if (p->max_iter < 1) return bad("max_iter");
-  if (p->path < 0 || p->path > 3) return bad("path");
+  if (p->path < 0 || p->path > 4) return bad("path");
   h->m = p->m;
   h->E = p->E;
   h->r = p->r;
@@ -456,6 +484,26 @@ extern "C" dcf_status dcf_create(const dcf_params* p, dcf_handle* out) {
     return DCF_ECUDA;
   }
 
+  // whole solve in one CTA: exact U-step, r <= 16, M and the factors in one
+  // SM's shared memory; chosen automatically wherever it fits
+  {
+    const int Rs = pick_R(p->r);
+    const bool small_ok = p->u_mode == 0 && p->r <= 16 &&
+                          solve_small_smem(Rs, h->m, h->n) + 2048 <= 232448;
+    if (p->path == 4 && !small_ok) {
+      dcf_destroy(h);
+      return DCF_EINVAL;
+    }
+    if (p->path == 4 || (p->path == 0 && small_ok)) {
+      if (solve_small_prepare(Rs, solve_small_smem(Rs, h->m, h->n)) != cudaSuccess) {
+        cudaGetLastError();
+        dcf_destroy(h);
+        return DCF_ECUDA;
+      }
+      h->path = 4;
+      h->R = Rs;
+    }
+  }
   // fused single-pass path: r <= 32, m a multiple of 4 (TMA row stride), at most
   // 16 slabs of 256 rows per cluster, and the cluster shape must fit on the GPU
   {
@@ -464,7 +512,7 @@ extern "C" dcf_status dcf_create(const dcf_params* p, dcf_handle* out) {
       dcf_destroy(h);
       return DCF_EINVAL;
     }
-    if (p->path != 1 && shape_ok) {
+    if ((p->path == 2 || (p->path == 0 && h->path == 1)) && shape_ok) {
       const int Rf = p->r <= 16 ? 16 : 32;
       // slabs of 256 rows, rounded up to a power of two: the cluster exchange
       // splits each 64-column strip into 16 chunks, so the cluster size divides 16
@@ -496,8 +544,8 @@ extern "C" dcf_status dcf_create(const dcf_params* p, dcf_handle* out) {
       dcf_destroy(h);
       return DCF_EINVAL;
     }
-    const bool want = p->path == 3 ||
-                      (p->path == 0 && h->path == 1 && tc2_ok && (h->m > 4096 || p->r > 32));
+    const bool want = p->path == 3 || (p->path == 0 && h->path == 1 && tc2_ok &&
+                                        (h->m > 4096 || p->r > 32));
     if (want) {
       const int Rt = p->r <= 16 ? 16 : p->r <= 32 ? 32 : 64;
       if (tc2_prepare(Rt) != cudaSuccess || (Rt == 64 && fused_prep_prepare() != cudaSuccess)) {
@@ -685,6 +733,13 @@ extern "C" dcf_status dcf_step(dcf_handle h, int n_steps) {
   dcf_status st = begin_work(h);
   if (st != DCF_OK) return st;
   if ((st = ensure_init(h)) != DCF_OK) return st;
+  if (h->path == 4) {   // every iteration in one launch of the whole-solve kernel
+    if (n_steps > 0) {
+      CK(enqueue_small(h, h->host_iter & 1, n_steps, h->stream), "whole solve");
+      h->host_iter += n_steps;
+    }
+    return end_work(h);
+  }
   if ((st = build_graphs(h)) != DCF_OK) return st;
   for (int i = 0; i < n_steps; ++i) {
     CK(cudaGraphLaunch(h->graph[h->host_iter & 1], h->stream), "graph launch");
@@ -698,13 +753,18 @@ extern "C" dcf_status dcf_solve(dcf_handle h, int* iters_out, double* final_dL_r
   dcf_status st = begin_work(h);
   if (st != DCF_OK) return st;
   if ((st = ensure_init(h)) != DCF_OK) return st;
-  if ((st = build_graphs(h)) != DCF_OK) return st;
+  if (h->path != 4 && (st = build_graphs(h)) != DCF_OK) return st;
   if ((st = set_state_fields(h, 1, h->tol)) != DCF_OK) return st;
   DevState ds{};
   if ((st = read_state(h, &ds)) != DCF_OK) return st;
   const int start = ds.iter;
   int done = 0;
   const int batch = 8;
+  if (h->path == 4) {   // one launch runs until the stop test or max_iter
+    CK(enqueue_small(h, h->host_iter & 1, h->max_iter, h->stream), "whole solve");
+    if ((st = read_state(h, &ds)) != DCF_OK) return st;
+    done = h->max_iter;
+  }
   while (done < h->max_iter) {
     int nb = std::min(batch, h->max_iter - done);
     for (int i = 0; i < nb; ++i) {

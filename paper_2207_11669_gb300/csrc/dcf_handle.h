@@ -55,7 +55,8 @@ struct dcf_handle_s {
   int n_vblocks = 0, n_splits = 0, n_rblocks = 0, n_vgram = 0;
   int64_t split_cols = 0;
   // fused single-pass path
-  int path = 1;                       // 1 general, 2 fused, 3 two-pass tensor core
+  int path = 1;                       // 1 general, 2 fused, 3 two-pass tensor core,
+                                      // 4 whole solve in one CTA
   int cs = 0, nclusters = 0, nslabs = 0;
   uint8_t* img = nullptr;
   float* scales = nullptr;

@@ -240,6 +240,23 @@ cudaError_t launch_fused_prep(int R, const float* U, const Smalls* sm, const Dev
                               cudaStream_t s);
 cudaError_t launch_absmax(const float* x, int64_t count, unsigned int* out, cudaStream_t s);
 
+// Whole solve of a small problem in one CTA (k_solve_small.cu), R = 8 or 16,
+// exact U-step: n_iter iterations (solve mode: until the stop test) from copy
+// `cur`; both copies of U and V are written back, and the state updated.
+struct SmallSolveArgs {
+  const float* M;     // m x n, column-major
+  int64_t m, n;
+  float* U[2];
+  float* V[2];
+  int cur;
+  int n_iter;
+  float lam, rho;
+  DevState* st;
+};
+size_t solve_small_smem(int R, int64_t m, int64_t n);
+cudaError_t solve_small_prepare(int R, size_t smem);
+cudaError_t launch_solve_small(int R, const SmallSolveArgs& a, cudaStream_t s);
+
 // Two-pass tensor-core path (k_tc2.cu), R = 16, 32 or 64.
 struct Tc2Args {
   int cur;

@@ -819,7 +819,7 @@ extern "C" dcf_status dcf_unrolled_forward(dcf_handle h, int K, const double* a,
   if (K < 1 || !a || !b || !c) return fail(h, DCF_EINVAL, "K < 1 or a parameter array is NULL");
   if (h->u_mode != 0) return fail(h, DCF_EINVAL, "the unrolled network uses the exact U-step");
   if (h->R > kUnrolledMaxR) return fail(h, DCF_EINVAL, "the unrolled network supports r <= 32");
-  if (h->path == 3)
+  if (h->path == 3 || h->path == 4)
     return fail(h, DCF_EINVAL, "the unrolled network runs on the general and fused paths");
   // the loss (and with it the reverse pass) only when asked for
   const bool with_loss = loss_terms || total_loss;

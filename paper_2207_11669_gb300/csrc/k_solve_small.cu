@@ -1,0 +1,325 @@
+// Whole solve of a small problem in one CTA (exact consensus U-step).
+//
+// A problem whose M and factors fit in one SM's shared memory (the 200 x 200,
+// E = 4 workload of §4.1 holds 160 KB of M) is latency-bound on the
+// multi-kernel path: each iteration is seven or eight launches of a few
+// microseconds of work.  Here one CTA keeps M, U, V and W in shared memory and
+// runs every iteration of a dcf_step / dcf_solve call in one launch.
+//
+// One iteration, from (U, V) to (U', V'), the same arithmetic as the other
+// paths (§2.2 S-step, App. B V-step, the consensus U-step, the factor-space
+// metrics of the stop test):
+//   G = U^T U (compensated FP32 sums, FP64 result), W = U (G + rho I)^{-1}
+//   column j:  r_ij = M_ij - u_i.v_j,  x_ij = u_i.v_j + clamp(r_ij, -lambda, lambda)
+//              (= M_ij - S_ij),  v'_j = sum_i x_ij w_i,  Huber sum of r_ij
+//   Q' = V'^T V', X_v = V^T V',  H = (Q' + rho I)^{-1}
+//   row i:     p_i = sum_j x_ij v'_j  (x recomputed),  u'_i = p_i H
+//   G' = U'^T U', X_u = U^T U'
+//   dL^2 = <G', Q'> - 2 <X_u, X_v> + <G, Q>,  objective = Huber + rho/2 (tr G + tr Q)
+// The r x r factorisations are FP64 (spd_inverse_f32), the long sums FP32.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "dcf.h"
+#include "dcf_internal.cuh"
+#include "dcf_small.cuh"
+
+namespace dcf {
+
+namespace {
+
+constexpr int kSSThreads = 512;
+
+// Shared-memory layout (bytes) for R and the problem size.
+struct SSLayout {
+  int RR;
+  int64_t ldm;        // M is stored with leading dimension m + 1 (odd: no bank
+                      // conflicts when threads walk different columns)
+  size_t A, G, Q, Gn, Qn, XU, XV, WS;   // doubles
+  size_t F, GI, HI, GP;                 // floats (GP: float2 Gram partials)
+  size_t Ms, U0, U1, V0, V1, W;         // floats
+  size_t total;
+  __host__ __device__ SSLayout(int R, int64_t m, int64_t n) {
+    RR = R * R;
+    ldm = m + 1;
+    size_t o = 0;
+    A = o;  o += (size_t)RR * 8;
+    G = o;  o += (size_t)RR * 8;
+    Q = o;  o += (size_t)RR * 8;
+    Gn = o; o += (size_t)RR * 8;
+    Qn = o; o += (size_t)RR * 8;
+    XU = o; o += (size_t)RR * 8;
+    XV = o; o += (size_t)RR * 8;
+    WS = o; o += 8 * 32 * 8;
+    F = o;  o += (size_t)RR * 4;
+    GI = o; o += (size_t)RR * 4;
+    HI = o; o += (size_t)RR * 4;
+    GP = o; o += (size_t)kSSThreads * 8;
+    Ms = o; o += (size_t)ldm * n * 4;
+    U0 = o; o += (size_t)m * R * 4;
+    U1 = o; o += (size_t)m * R * 4;
+    V0 = o; o += (size_t)n * R * 4;
+    V1 = o; o += (size_t)n * R * 4;
+    W = o;  o += (size_t)m * R * 4;
+    total = o;
+  }
+};
+
+__device__ __forceinline__ void ss_two_sum(float& hi, float& lo, float x) {
+  const float t = hi + x;
+  const float bp = t - hi;
+  lo += (hi - (t - bp)) + (x - bp);
+  hi = t;
+}
+
+// out[k*R + l] = sum_i X[i*R + k] Y[i*R + l] over N rows (compensated FP32
+// partials over row groups, FP64 result).  Block-wide.
+template <int R>
+__device__ void ss_gram(const float* X, const float* Y, int64_t N, double* out, float2* gp) {
+  constexpr int RR = R * R;
+  constexpr int NG = kSSThreads / RR >= 1 ? kSSThreads / RR : 1;   // row groups
+  const int tid = threadIdx.x;
+  for (int e0 = 0; e0 < RR; e0 += kSSThreads / NG) {
+    const int e = e0 + tid % (kSSThreads / NG), g = tid / (kSSThreads / NG);
+    float hi = 0.f, lo = 0.f;
+    if (e < RR && g < NG) {
+      const int k = e / R, l = e % R;
+      for (int64_t i = g; i < N; i += NG) ss_two_sum(hi, lo, X[i * R + k] * Y[i * R + l]);
+    }
+    __syncthreads();
+    gp[tid] = make_float2(hi, lo);
+    __syncthreads();
+    if (tid < kSSThreads / NG && e0 + tid < RR) {
+      float h = 0.f, l2 = 0.f;
+      for (int q = 0; q < NG; ++q) {
+        const float2 v = gp[q * (kSSThreads / NG) + tid];
+        ss_two_sum(h, l2, v.x);
+        l2 += v.y;
+      }
+      out[e0 + tid] = (double)h + (double)l2;
+    }
+  }
+  __syncthreads();
+}
+
+// out (floats, R x R) = (S + rho I)^{-1} for a symmetric S (FP64).  Block-wide.
+// Returns 0 when the factorisation produced a non-finite value.
+template <int R>
+__device__ int ss_ridge_inverse(const double* S, float rho, double* A, float* F, float* out) {
+  for (int i = threadIdx.x; i < R * R; i += kSSThreads)
+    A[i] = S[i] + ((i / R) == (i % R) ? (double)rho : 0.0);
+  __syncthreads();
+  if (!all_finite(A, R * R)) return 0;
+  spd_inverse_f32(A, F, R, out);
+  return 1;
+}
+
+// Sum of v over the CTA (FP64).  Block-wide; `ws` holds 32 doubles.
+__device__ double ss_block_sum(double v, double* ws) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  __syncthreads();
+  if (lane == 0) ws[wid] = v;
+  __syncthreads();
+  double t = 0.0;
+  for (int w = 0; w < kSSThreads / 32; ++w) t += ws[w];
+  __syncthreads();
+  return t;
+}
+
+}  // namespace
+
+template <int R>
+__global__ void __launch_bounds__(kSSThreads, 1) k_solve_small(SmallSolveArgs a) {
+  extern __shared__ __align__(16) uint8_t smem[];
+  const SSLayout L(R, a.m, a.n);
+  double* A = reinterpret_cast<double*>(smem + L.A);
+  double* G = reinterpret_cast<double*>(smem + L.G);
+  double* Q = reinterpret_cast<double*>(smem + L.Q);
+  double* Gn = reinterpret_cast<double*>(smem + L.Gn);
+  double* Qn = reinterpret_cast<double*>(smem + L.Qn);
+  double* XU = reinterpret_cast<double*>(smem + L.XU);
+  double* XV = reinterpret_cast<double*>(smem + L.XV);
+  double* ws = reinterpret_cast<double*>(smem + L.WS);
+  float* F = reinterpret_cast<float*>(smem + L.F);
+  float* GI = reinterpret_cast<float*>(smem + L.GI);
+  float* HI = reinterpret_cast<float*>(smem + L.HI);
+  float2* gp = reinterpret_cast<float2*>(smem + L.GP);
+  float* Ms = reinterpret_cast<float*>(smem + L.Ms);
+  // the two copies of U (and of V) are adjacent: copy c at base + c * rows * R
+  float* Ub = reinterpret_cast<float*>(smem + L.U0);
+  float* Vb = reinterpret_cast<float*>(smem + L.V0);
+  float* Ws = reinterpret_cast<float*>(smem + L.W);
+  __shared__ int s_flags[2];   // [0] stop the loop, [1] status
+  const int tid = threadIdx.x;
+  const int64_t m = a.m, n = a.n, ldm = L.ldm;
+  DevState* st = a.st;
+  if (st->status != 0 || a.n_iter < 1) return;
+  const int solve_mode = st->solve_mode;
+  const double tol = st->tol;
+  const float lam = a.lam, rho = a.rho;
+
+  // ---- load M, U, V (copy cur) and the previous copies -------------------------
+  for (int64_t e = tid; e < m * n; e += kSSThreads) {
+    const int64_t j = e / m, i = e % m;
+    Ms[j * ldm + i] = a.M[e];
+  }
+  int cur = a.cur;
+  {
+    const float* Ug = cur ? a.U[1] : a.U[0];
+    const float* Vg = cur ? a.V[1] : a.V[0];
+    for (int64_t e = tid; e < m * R; e += kSSThreads) Ub[cur * m * R + e] = Ug[e];
+    for (int64_t e = tid; e < n * R; e += kSSThreads) Vb[cur * n * R + e] = Vg[e];
+  }
+  if (tid == 0) { s_flags[0] = 0; s_flags[1] = 0; }
+  __syncthreads();
+  ss_gram<R>(Ub + cur * m * R, Ub + cur * m * R, m, G, gp);
+  ss_gram<R>(Vb + cur * n * R, Vb + cur * n * R, n, Q, gp);
+
+  int done = 0;
+  double last_dl = 0.0, last_obj = 0.0, last_hub = 0.0;
+  for (int it = 0; it < a.n_iter; ++it) {
+    const int nxt = cur ^ 1;
+    const float* U = Ub + cur * m * R;
+    const float* V = Vb + cur * n * R;
+    float* Un = Ub + nxt * m * R;
+    float* Vn = Vb + nxt * n * R;
+    // ---- W = U (G + rho I)^{-1} -------------------------------------------------
+    if (!ss_ridge_inverse<R>(G, rho, A, F, GI)) {
+      if (tid == 0) s_flags[1] = DCF_ENONFINITE;
+      __syncthreads();
+      break;
+    }
+    for (int64_t e = tid; e < m * R; e += kSSThreads) {
+      const int64_t i = e / R;
+      const int l = (int)(e % R);
+      float s = 0.f;
+#pragma unroll
+      for (int k = 0; k < R; ++k) s = fmaf(U[i * R + k], GI[k * R + l], s);
+      Ws[e] = s;
+    }
+    __syncthreads();
+    // ---- S-step and V-step, one thread per column -----------------------------
+    float hub_hi = 0.f, hub_lo = 0.f;
+    for (int64_t j = tid; j < n; j += kSSThreads) {
+      float v[R], acc[R];
+#pragma unroll
+      for (int k = 0; k < R; ++k) { v[k] = V[j * R + k]; acc[k] = 0.f; }
+      float hub = 0.f;
+      const float* Mc = Ms + j * ldm;
+      for (int64_t i = 0; i < m; ++i) {
+        float uv = 0.f;
+#pragma unroll
+        for (int k = 0; k < R; ++k) uv = fmaf(U[i * R + k], v[k], uv);
+        const float r = Mc[i] - uv;
+        const float c = fminf(fmaxf(r, -lam), lam);
+        hub = fmaf(c, r - 0.5f * c, hub);             // Huber H_lambda(r)
+        const float x = uv + c;                       // M - S
+#pragma unroll
+        for (int k = 0; k < R; ++k) acc[k] = fmaf(x, Ws[i * R + k], acc[k]);
+      }
+#pragma unroll
+      for (int k = 0; k < R; ++k) Vn[j * R + k] = acc[k];
+      ss_two_sum(hub_hi, hub_lo, hub);
+    }
+    const double huber = ss_block_sum((double)hub_hi + (double)hub_lo, ws);
+    ss_gram<R>(Vn, Vn, n, Qn, gp);
+    ss_gram<R>(V, Vn, n, XV, gp);
+    // ---- U-step: P = X V', U' = P (Q' + rho I)^{-1}, one thread per row ---------
+    if (!ss_ridge_inverse<R>(Qn, rho, A, F, HI)) {
+      if (tid == 0) s_flags[1] = DCF_ENONFINITE;
+      __syncthreads();
+      break;
+    }
+    for (int64_t i = tid; i < m; i += kSSThreads) {
+      float u[R], p[R];
+#pragma unroll
+      for (int k = 0; k < R; ++k) { u[k] = U[i * R + k]; p[k] = 0.f; }
+      for (int64_t j = 0; j < n; ++j) {
+        float uv = 0.f;
+#pragma unroll
+        for (int k = 0; k < R; ++k) uv = fmaf(u[k], V[j * R + k], uv);
+        const float r = Ms[j * ldm + i] - uv;
+        const float x = uv + fminf(fmaxf(r, -lam), lam);
+#pragma unroll
+        for (int k = 0; k < R; ++k) p[k] = fmaf(x, Vn[j * R + k], p[k]);
+      }
+#pragma unroll
+      for (int l = 0; l < R; ++l) {
+        float s = 0.f;
+#pragma unroll
+        for (int k = 0; k < R; ++k) s = fmaf(p[k], HI[k * R + l], s);
+        Un[i * R + l] = s;
+      }
+    }
+    __syncthreads();
+    ss_gram<R>(Un, Un, m, Gn, gp);
+    ss_gram<R>(U, Un, m, XU, gp);
+    // ---- metrics and the stop test -------------------------------------------------
+    double v0 = 0.0, v1 = 0.0, v2 = 0.0, t0 = 0.0, t1 = 0.0;
+    for (int e = tid; e < R * R; e += kSSThreads) {
+      v0 = fma(Gn[e], Qn[e], v0);
+      v1 = fma(XU[e], XV[e], v1);
+      v2 = fma(G[e], Q[e], v2);
+      if (e / R == e % R) { t0 += G[e]; t1 += Q[e]; }
+    }
+    const double a0 = ss_block_sum(v0, ws), a1 = ss_block_sum(v1, ws), a2 = ss_block_sum(v2, ws);
+    const double tr0 = ss_block_sum(t0, ws), tr1 = ss_block_sum(t1, ws);
+    double d2 = a0 - 2.0 * a1 + a2;
+    if (d2 < 0) d2 = 0;
+    last_dl = a0 > 0 ? sqrt(d2 / a0) : INFINITY;
+    last_hub = huber;
+    last_obj = huber + 0.5 * (double)rho * (tr0 + tr1);
+    ++done;
+    if (tid == 0) {
+      if (!isfinite(a0) || !isfinite(last_obj)) s_flags[1] = DCF_ENONFINITE;
+      if (solve_mode && last_dl <= tol) s_flags[0] = 1;
+    }
+    for (int e = tid; e < R * R; e += kSSThreads) { G[e] = Gn[e]; Q[e] = Qn[e]; }
+    cur = nxt;
+    __syncthreads();
+    if (s_flags[0] || s_flags[1]) break;
+  }
+
+  // ---- write back: current and previous copies, state ---------------------------
+  for (int64_t e = tid; e < m * R; e += kSSThreads) {
+    a.U[0][e] = Ub[e];
+    a.U[1][e] = Ub[m * R + e];
+  }
+  for (int64_t e = tid; e < n * R; e += kSSThreads) {
+    a.V[0][e] = Vb[e];
+    a.V[1][e] = Vb[n * R + e];
+  }
+  if (tid == 0) {
+    st->iter += done;
+    if (done > 0) {
+      st->has_S = 1;
+      st->dL_rel = last_dl;
+      st->objective = last_obj;
+      st->huber = last_hub;
+    }
+    if (s_flags[1]) st->status = s_flags[1];
+    if (s_flags[0]) st->stop = 1;
+  }
+}
+
+size_t solve_small_smem(int R, int64_t m, int64_t n) {
+  return SSLayout(R, m, n).total;
+}
+
+cudaError_t solve_small_prepare(int R, size_t smem) {
+  if (R == 8)
+    return cudaFuncSetAttribute(k_solve_small<8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)smem);
+  return cudaFuncSetAttribute(k_solve_small<16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)smem);
+}
+
+cudaError_t launch_solve_small(int R, const SmallSolveArgs& a, cudaStream_t s) {
+  const size_t smem = solve_small_smem(R, a.m, a.n);
+  if (R == 8) k_solve_small<8><<<1, kSSThreads, smem, s>>>(a);
+  else k_solve_small<16><<<1, kSSThreads, smem, s>>>(a);
+  return cudaGetLastError();
+}
+
+}  // namespace dcf

@@ -178,7 +178,7 @@ def use_torch_allocator():
     dcf_set_allocator(alloc, release)
 
 
-PATH_AUTO, PATH_GENERAL, PATH_FUSED, PATH_TC2 = 0, 1, 2, 3
+PATH_AUTO, PATH_GENERAL, PATH_FUSED, PATH_TC2, PATH_SMALL = 0, 1, 2, 3, 4
 
 
 def dcf_create(m, n_i, r, rho, lam, max_iter=100, tol=1e-6, u_mode=0, local_steps=1,

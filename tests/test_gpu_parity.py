@@ -41,15 +41,25 @@ def fused_ok(m, r):
     return r <= 32 and m % 4 == 0 and (m + 255) // 256 <= 16
 
 
-def path_ok(path, m, r):
+def small_ok(m, n, r):
+    # the whole-solve kernel's shared memory (M with leading dimension m + 1,
+    # two copies of U and V, W, the r x r workspace) within one SM
+    R = 8 if r <= 8 else 16
+    smem = 7 * R * R * 8 + 2048 + 3 * R * R * 4 + 512 * 8 + 4 * ((m + 1) * n + 3 * m * R + 2 * n * R)
+    return r <= 16 and smem + 2048 <= 232448
+
+
+def path_ok(path, m, r, n=None):
     if path == dcf.PATH_FUSED:
         return fused_ok(m, r)
     if path == dcf.PATH_TC2:
         return m % 4 == 0
+    if path == dcf.PATH_SMALL:
+        return small_ok(m, n, r)
     return True
 
 
-PATHS = [dcf.PATH_GENERAL, dcf.PATH_FUSED, dcf.PATH_TC2]
+PATHS = [dcf.PATH_GENERAL, dcf.PATH_FUSED, dcf.PATH_TC2, dcf.PATH_SMALL]
 
 
 def gpu_solver(case, **kw):
@@ -67,7 +77,7 @@ def oracle_step(case, iters=1, **kw):
 @pytest.mark.parametrize("path", PATHS)
 @pytest.mark.parametrize("m,n_i,r", SHAPES)
 def test_one_step_parity(m, n_i, r, path):
-    if not path_ok(path, m, r):
+    if not path_ok(path, m, r, sum(n_i)):
         pytest.skip("shape outside this path")
     case = make_case(m, n_i, r, seed=m + r)
     s = gpu_solver(case, path=path)
@@ -90,6 +100,8 @@ def test_one_step_parity(m, n_i, r, path):
 
 @pytest.mark.parametrize("path", PATHS)
 def test_fedavg_step_parity(path):
+    if path == dcf.PATH_SMALL:
+        pytest.skip("the whole-solve kernel runs the exact U-step")
     case = make_case(300, [100, 77, 140], 16, seed=3)
     s = gpu_solver(case, u_mode=1, eta0=0.01, path=path)
     s.step(3)
@@ -152,6 +164,30 @@ def test_fused_path_is_chosen_automatically():
     s.close()
     with pytest.raises(dcf.DcfError):
         dcf.Solver(257, [300, 211], 40, 1e-2, 0.1, path=dcf.PATH_TC2)
+    case = make_case(200, [50] * 4, 5, seed=21)
+    s = gpu_solver(case)
+    assert s.path == dcf.PATH_SMALL             # fits one SM: whole solve in one CTA
+    s.close()
+    with pytest.raises(dcf.DcfError):
+        dcf.Solver(300, [100, 77, 140], 16, 1e-2, 0.1, path=dcf.PATH_SMALL)
+
+
+def test_whole_solve_one_launch_equals_single_steps():
+    """dcf_step(n) on the whole-solve path is one launch of n iterations; it
+    must give the bits of n launches of one iteration each (the r x r state
+    is rebuilt from U and V, which are written back exactly)."""
+    case = make_case(200, [50] * 4, 5, seed=31)
+    a = gpu_solver(case, path=dcf.PATH_SMALL)
+    b = gpu_solver(case, path=dcf.PATH_SMALL)
+    a.step(7)
+    for _ in range(7):
+        b.step(1)
+    Ua, Va = a.factors()
+    Ub, Vb = b.factors()
+    assert np.array_equal(Ua, Ub) and np.array_equal(Va, Vb)
+    assert a.stats() == b.stats()
+    a.close()
+    b.close()
     with pytest.raises(dcf.DcfError):
         dcf.Solver(257, [300, 211], 40, 1e-2, 0.1, path=dcf.PATH_FUSED)
 
@@ -169,6 +205,8 @@ def test_init_sweep_parity():
 
 @pytest.mark.parametrize("path", PATHS)
 def test_partition_invariance_on_gpu(path):
+    if not path_ok(path, 300, 16, 317):
+        pytest.skip("shape outside this path")
     case = make_case(300, [100, 77, 140], 16, seed=5)
     a = gpu_solver(case, path=path)
     case1 = dict(case, n_i=np.array([317]))
@@ -200,6 +238,8 @@ def test_stats_and_rel_err(path):
 
 @pytest.mark.parametrize("path", PATHS)
 def test_get_LS_blocks_and_privacy(path):
+    if not path_ok(path, 132, 32, 128):
+        pytest.skip("shape outside this path")
     case = make_case(132, [33, 64, 31], 32, seed=13)
     s = gpu_solver(case, path=path)
     s.step(2)
