@@ -291,6 +291,8 @@ def test_default_init_is_seeded_gaussian():
 @pytest.mark.parametrize("path", PATHS)
 def test_borrowed_device_matrix_matches_host_copy(path):
     import torch
+    if not path_ok(path, 300, 16, 317):
+        pytest.skip("shape outside this path")
     case = make_case(300, [100, 77, 140], 16, seed=17)
     Mt = torch.from_numpy(np.ascontiguousarray(case["M"].T)).cuda()   # (n, m) = M column-major
     s1 = gpu_solver(case, path=path)
