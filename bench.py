@@ -236,8 +236,11 @@ def run_ours(args):
     m, n, r = wl.m, wl.n, wl.r
     U0 = synth.gaussian_u0(m, r, wl.seed + rank)
     Mt = torch.from_numpy(np.ascontiguousarray(inst.M.T)).cuda()     # (n, m): M column-major
+    # the small workload (200 x 200) runs whole in one CTA (path 4, on request);
+    # the others take the library's automatic choice
+    path = dcf.PATH_SMALL if args.workload == "small" else dcf.PATH_AUTO
     s = dcf.Solver(m, inst.n_i, r, wl.rho, wl.lam, max_iter=wl.iters, tol=0.0,
-                   stream=torch.cuda.current_stream().cuda_stream)
+                   stream=torch.cuda.current_stream().cuda_stream, path=path)
     s.load(Mt)
     s.load_init(U0)
     path_id = s.path
@@ -265,7 +268,7 @@ def run_ours(args):
         tdist.barrier()
     ms_step = ms / args.steps
     value = world * 1e3 / ms_step
-    launches_per_iter = 9 if path_id == 3 else 8   # kernels per iteration (graph nodes)
+    launches_per_iter = {3: 9, 4: 1}.get(path_id, 8)   # kernels per iteration (graph nodes)
 
     # per-kernel phases, CUDA events on the launch stream, same workload
     phases = dcf.dcf_profile_step(s.h, max(3, min(args.steps, 10)))
@@ -310,12 +313,13 @@ def run_ours(args):
                 "dtype": "f32", "data": "synthetic",
                 "config": {"workload": wl.name, "m": m, "n": n, "E": int(wl.E), "r": r,
                            "kernel_path": {1: "general two-pass", 2: "fused single-pass tcgen05",
-                                           3: "two-pass tcgen05"}.get(path_id),
+                                           3: "two-pass tcgen05",
+                                           4: "whole solve in one CTA"}.get(path_id),
                            "rank_truth": wl.k, "density": wl.density, "rho": wl.rho,
                            "lambda": wl.lam, "parallelism": "replicas" if world > 1 else "1gpu",
                            "l2": "inputs larger than L2 (M is %.0f MiB)" % (4.0 * m * n / 2**20)},
                 "hbm_gbs_alg": gbs,
-                "gpu_launches": launches_per_iter * args.steps,
+                "gpu_launches": 1 if path_id == 4 else launches_per_iter * args.steps,
                 "clocks": clk, "roofline": roofline, "e2e": e2e, "cpu_baseline": cpu}
         print(json.dumps(line), flush=True)
     if world > 1:

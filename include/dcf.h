@@ -84,8 +84,8 @@ typedef struct {
                            every iteration of a dcf_step / dcf_solve call in
                            one launch (DCF_EINVAL unless u_mode = 0, r <= 16
                            and M with the factors fits in one SM's shared
-                           memory, about 200 x 200).  Automatic: 4 where it
-                           fits, else 2 where it qualifies, else 3 for
+                           memory, about 200 x 200; on request only).
+                           Automatic: 2 where it qualifies, else 3 for
                            m % 4 == 0 with m > 4096 or r > 32, else 1         */
 } dcf_params;
 

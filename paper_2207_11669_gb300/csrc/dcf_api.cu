@@ -485,7 +485,8 @@ extern "C" dcf_status dcf_create(const dcf_params* p, dcf_handle* out) {
   }
 
   // whole solve in one CTA: exact U-step, r <= 16, M and the factors in one
-  // SM's shared memory; chosen automatically wherever it fits
+  // SM's shared memory; on request only (the learned network and the FedAvg
+  // step run on the multi-kernel paths)
   {
     const int Rs = pick_R(p->r);
     const bool small_ok = p->u_mode == 0 && p->r <= 16 &&
@@ -494,7 +495,7 @@ extern "C" dcf_status dcf_create(const dcf_params* p, dcf_handle* out) {
       dcf_destroy(h);
       return DCF_EINVAL;
     }
-    if (p->path == 4 || (p->path == 0 && small_ok)) {
+    if (p->path == 4) {
       if (solve_small_prepare(Rs, solve_small_smem(Rs, h->m, h->n)) != cudaSuccess) {
         cudaGetLastError();
         dcf_destroy(h);

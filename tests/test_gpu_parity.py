@@ -166,7 +166,7 @@ def test_fused_path_is_chosen_automatically():
         dcf.Solver(257, [300, 211], 40, 1e-2, 0.1, path=dcf.PATH_TC2)
     case = make_case(200, [50] * 4, 5, seed=21)
     s = gpu_solver(case)
-    assert s.path == dcf.PATH_SMALL             # fits one SM: whole solve in one CTA
+    assert s.path == dcf.PATH_FUSED             # the whole-solve path is on request only
     s.close()
     with pytest.raises(dcf.DcfError):
         dcf.Solver(300, [100, 77, 140], 16, 1e-2, 0.1, path=dcf.PATH_SMALL)
