@@ -55,7 +55,7 @@ struct SSLayout {
     GI = o; o += (size_t)RR * 4;
     HI = o; o += (size_t)RR * 4;
     GP = o; o += (size_t)kSSThreads * 8;
-    Ms = o; o += (size_t)ldm * n * 4;
+    Ms = o; o += ((size_t)ldm * n * 4 + 15) / 16 * 16;   // U, V, W rows are read as float4
     U0 = o; o += (size_t)m * R * 4;
     U1 = o; o += (size_t)m * R * 4;
     V0 = o; o += (size_t)n * R * 4;
@@ -207,16 +207,32 @@ __global__ void __launch_bounds__(kSSThreads, 1) k_solve_small(SmallSolveArgs a)
       for (int k = 0; k < R; ++k) { v[k] = V[j * R + k]; acc[k] = 0.f; }
       float hub = 0.f;
       const float* Mc = Ms + j * ldm;
+#pragma unroll 2
       for (int64_t i = 0; i < m; ++i) {
+        // rows of U and W as float4 (broadcast: every thread reads row i)
+        const float4* u4 = reinterpret_cast<const float4*>(U + i * R);
+        const float4* w4 = reinterpret_cast<const float4*>(Ws + i * R);
         float uv = 0.f;
 #pragma unroll
-        for (int k = 0; k < R; ++k) uv = fmaf(U[i * R + k], v[k], uv);
+        for (int k4 = 0; k4 < R / 4; ++k4) {
+          const float4 u = u4[k4];
+          uv = fmaf(u.x, v[4 * k4], uv);
+          uv = fmaf(u.y, v[4 * k4 + 1], uv);
+          uv = fmaf(u.z, v[4 * k4 + 2], uv);
+          uv = fmaf(u.w, v[4 * k4 + 3], uv);
+        }
         const float r = Mc[i] - uv;
         const float c = fminf(fmaxf(r, -lam), lam);
         hub = fmaf(c, r - 0.5f * c, hub);             // Huber H_lambda(r)
         const float x = uv + c;                       // M - S
 #pragma unroll
-        for (int k = 0; k < R; ++k) acc[k] = fmaf(x, Ws[i * R + k], acc[k]);
+        for (int k4 = 0; k4 < R / 4; ++k4) {
+          const float4 w = w4[k4];
+          acc[4 * k4] = fmaf(x, w.x, acc[4 * k4]);
+          acc[4 * k4 + 1] = fmaf(x, w.y, acc[4 * k4 + 1]);
+          acc[4 * k4 + 2] = fmaf(x, w.z, acc[4 * k4 + 2]);
+          acc[4 * k4 + 3] = fmaf(x, w.w, acc[4 * k4 + 3]);
+        }
       }
 #pragma unroll
       for (int k = 0; k < R; ++k) Vn[j * R + k] = acc[k];
@@ -235,14 +251,29 @@ __global__ void __launch_bounds__(kSSThreads, 1) k_solve_small(SmallSolveArgs a)
       float u[R], p[R];
 #pragma unroll
       for (int k = 0; k < R; ++k) { u[k] = U[i * R + k]; p[k] = 0.f; }
+#pragma unroll 2
       for (int64_t j = 0; j < n; ++j) {
+        const float4* v4 = reinterpret_cast<const float4*>(V + j * R);
+        const float4* vn4 = reinterpret_cast<const float4*>(Vn + j * R);
         float uv = 0.f;
 #pragma unroll
-        for (int k = 0; k < R; ++k) uv = fmaf(u[k], V[j * R + k], uv);
+        for (int k4 = 0; k4 < R / 4; ++k4) {
+          const float4 v = v4[k4];
+          uv = fmaf(u[4 * k4], v.x, uv);
+          uv = fmaf(u[4 * k4 + 1], v.y, uv);
+          uv = fmaf(u[4 * k4 + 2], v.z, uv);
+          uv = fmaf(u[4 * k4 + 3], v.w, uv);
+        }
         const float r = Ms[j * ldm + i] - uv;
         const float x = uv + fminf(fmaxf(r, -lam), lam);
 #pragma unroll
-        for (int k = 0; k < R; ++k) p[k] = fmaf(x, Vn[j * R + k], p[k]);
+        for (int k4 = 0; k4 < R / 4; ++k4) {
+          const float4 w = vn4[k4];
+          p[4 * k4] = fmaf(x, w.x, p[4 * k4]);
+          p[4 * k4 + 1] = fmaf(x, w.y, p[4 * k4 + 1]);
+          p[4 * k4 + 2] = fmaf(x, w.z, p[4 * k4 + 2]);
+          p[4 * k4 + 3] = fmaf(x, w.w, p[4 * k4 + 3]);
+        }
       }
 #pragma unroll
       for (int l = 0; l < R; ++l) {
