@@ -16,7 +16,7 @@
 //   row i:     p_i = sum_j x_ij v'_j  (x recomputed),  u'_i = p_i H
 //   G' = U'^T U', X_u = U^T U'
 //   dL^2 = <G', Q'> - 2 <X_u, X_v> + <G, Q>,  objective = Huber + rho/2 (tr G + tr Q)
-// The r x r factorisations are FP64 (spd_inverse_f32), the long sums FP32.
+// The r x r inverses are FP64 (Gauss-Jordan in one warp), the long sums FP32.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -36,14 +36,14 @@ struct SSLayout {
   int64_t ldm;        // M is stored with leading dimension m + 1 (odd: no bank
                       // conflicts when threads walk different columns)
   size_t A, G, Q, Gn, Qn, XU, XV, WS;   // doubles
-  size_t F, GI, HI, GP;                 // floats (GP: float2 Gram partials)
+  size_t GI, HI, GP;                    // floats (GP: float2 Gram partials)
   size_t Ms, U0, U1, V0, V1, W;         // floats
   size_t total;
   __host__ __device__ SSLayout(int R, int64_t m, int64_t n) {
     RR = R * R;
     ldm = m + 1;
     size_t o = 0;
-    A = o;  o += (size_t)RR * 8;
+    A = o;  o += (size_t)RR * 2 * 8;    // [S + rho I | I] for the Gauss-Jordan inverse
     G = o;  o += (size_t)RR * 8;
     Q = o;  o += (size_t)RR * 8;
     Gn = o; o += (size_t)RR * 8;
@@ -51,7 +51,6 @@ struct SSLayout {
     XU = o; o += (size_t)RR * 8;
     XV = o; o += (size_t)RR * 8;
     WS = o; o += 8 * 32 * 8;
-    F = o;  o += (size_t)RR * 4;
     GI = o; o += (size_t)RR * 4;
     HI = o; o += (size_t)RR * 4;
     GP = o; o += (size_t)kSSThreads * 8;
@@ -102,29 +101,54 @@ __device__ void ss_gram(const float* X, const float* Y, int64_t N, double* out, 
   __syncthreads();
 }
 
-// out (floats, R x R) = (S + rho I)^{-1} for a symmetric S (FP64).  Block-wide.
-// Returns 0 when the factorisation produced a non-finite value.
+// out (floats, R x R) = (S + rho I)^{-1} for a symmetric positive definite
+// S + rho I, by FP64 Gauss-Jordan elimination on [S + rho I | I] in warp 0
+// (no pivoting: the matrix is SPD; R <= 16, at most 16 entries per lane and
+// step, one __syncwarp between the read and the write of a step).  Called by
+// every thread; returns 0 when a pivot is not positive or a value not finite.
 template <int R>
-__device__ int ss_ridge_inverse(const double* S, float rho, double* A, float* F, float* out) {
-  for (int i = threadIdx.x; i < R * R; i += kSSThreads)
-    A[i] = S[i] + ((i / R) == (i % R) ? (double)rho : 0.0);
+__device__ int ss_ridge_inverse(const double* S, float rho, double* A, float* out, int* okp) {
+  constexpr int C = 2 * R, NE = R * C, PER = (NE + 31) / 32;
+  if (threadIdx.x < 32) {
+    const int lane = threadIdx.x;
+    for (int e = lane; e < NE; e += 32) {
+      const int i = e / C, j = e % C;
+      A[e] = j < R ? S[i * R + j] + (i == j ? (double)rho : 0.0) : (j - R == i ? 1.0 : 0.0);
+    }
+    __syncwarp();
+    int ok = 1;
+    for (int k = 0; k < R; ++k) {
+      const double piv = A[k * C + k];
+      if (!(piv > 0.0) || !isfinite(piv)) ok = 0;
+      const double ip = recip_f64(piv);
+      double nv[PER];
+#pragma unroll
+      for (int q = 0; q < PER; ++q) {
+        const int e = lane + 32 * q;
+        if (e < NE) {
+          const int i = e / C, j = e % C;
+          const double akj = A[k * C + j] * ip;
+          nv[q] = i == k ? akj : fma(-A[i * C + k], akj, A[e]);
+        }
+      }
+      __syncwarp();
+#pragma unroll
+      for (int q = 0; q < PER; ++q) {
+        const int e = lane + 32 * q;
+        if (e < NE) A[e] = nv[q];
+      }
+      __syncwarp();
+    }
+    for (int e = lane; e < R * R; e += 32) {
+      const double v = A[(e / R) * C + R + e % R];
+      if (!isfinite(v)) ok = 0;
+      out[e] = (float)v;
+    }
+    ok = __all_sync(0xffffffffu, ok);
+    if (lane == 0) *okp = ok;
+  }
   __syncthreads();
-  if (!all_finite(A, R * R)) return 0;
-  spd_inverse_f32(A, F, R, out);
-  return 1;
-}
-
-// Sum of v over the CTA (FP64).  Block-wide; `ws` holds 32 doubles.
-__device__ double ss_block_sum(double v, double* ws) {
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  __syncthreads();
-  if (lane == 0) ws[wid] = v;
-  __syncthreads();
-  double t = 0.0;
-  for (int w = 0; w < kSSThreads / 32; ++w) t += ws[w];
-  __syncthreads();
-  return t;
+  return *okp;
 }
 
 }  // namespace
@@ -141,7 +165,6 @@ __global__ void __launch_bounds__(kSSThreads, 1) k_solve_small(SmallSolveArgs a)
   double* XU = reinterpret_cast<double*>(smem + L.XU);
   double* XV = reinterpret_cast<double*>(smem + L.XV);
   double* ws = reinterpret_cast<double*>(smem + L.WS);
-  float* F = reinterpret_cast<float*>(smem + L.F);
   float* GI = reinterpret_cast<float*>(smem + L.GI);
   float* HI = reinterpret_cast<float*>(smem + L.HI);
   float2* gp = reinterpret_cast<float2*>(smem + L.GP);
@@ -150,7 +173,8 @@ __global__ void __launch_bounds__(kSSThreads, 1) k_solve_small(SmallSolveArgs a)
   float* Ub = reinterpret_cast<float*>(smem + L.U0);
   float* Vb = reinterpret_cast<float*>(smem + L.V0);
   float* Ws = reinterpret_cast<float*>(smem + L.W);
-  __shared__ int s_flags[2];   // [0] stop the loop, [1] status
+  __shared__ int s_flags[3];   // [0] stop the loop, [1] status, [2] inverse ok
+  __shared__ double s_met[4];  // dL_rel, objective, Huber of the last iteration
   const int tid = threadIdx.x;
   const int64_t m = a.m, n = a.n, ldm = L.ldm;
   DevState* st = a.st;
@@ -158,6 +182,14 @@ __global__ void __launch_bounds__(kSSThreads, 1) k_solve_small(SmallSolveArgs a)
   const int solve_mode = st->solve_mode;
   const double tol = st->tol;
   const float lam = a.lam, rho = a.rho;
+  // adjacent threads per column (V-step) and per row (U-step): the largest power
+  // of two up to 8 that keeps every column (row) within one pass of the CTA
+  auto tpc_of = [](int64_t cnt) {
+    int t = 1;
+    while (t < 8 && (int64_t)(2 * t) * cnt <= kSSThreads) t *= 2;
+    return t;
+  };
+  const int TPC = tpc_of(n), TPR = tpc_of(m);
 
   // ---- load M, U, V (copy cur) and the previous copies -------------------------
   for (int64_t e = tid; e < m * n; e += kSSThreads) {
@@ -185,7 +217,7 @@ __global__ void __launch_bounds__(kSSThreads, 1) k_solve_small(SmallSolveArgs a)
     float* Un = Ub + nxt * m * R;
     float* Vn = Vb + nxt * n * R;
     // ---- W = U (G + rho I)^{-1} -------------------------------------------------
-    if (!ss_ridge_inverse<R>(G, rho, A, F, GI)) {
+    if (!ss_ridge_inverse<R>(G, rho, A, GI, &s_flags[2])) {
       if (tid == 0) s_flags[1] = DCF_ENONFINITE;
       __syncthreads();
       break;
@@ -199,60 +231,76 @@ __global__ void __launch_bounds__(kSSThreads, 1) k_solve_small(SmallSolveArgs a)
       Ws[e] = s;
     }
     __syncthreads();
-    // ---- S-step and V-step, one thread per column -----------------------------
-    float hub_hi = 0.f, hub_lo = 0.f;
-    for (int64_t j = tid; j < n; j += kSSThreads) {
-      float v[R], acc[R];
+    // ---- S-step and V-step: TPC adjacent threads per column, shuffle-combined ----
+    {
+      double hub_w = 0.0;
+      for (int64_t jb = 0; jb < n; jb += kSSThreads / TPC) {
+        const int64_t j = jb + tid / TPC;
+        const int part = tid % TPC;
+        const bool act = j < n;
+        float v[R], acc[R];
 #pragma unroll
-      for (int k = 0; k < R; ++k) { v[k] = V[j * R + k]; acc[k] = 0.f; }
-      float hub = 0.f;
-      const float* Mc = Ms + j * ldm;
+        for (int k = 0; k < R; ++k) { v[k] = act ? V[j * R + k] : 0.f; acc[k] = 0.f; }
+        float hub = 0.f;
+        const float* Mc = Ms + (act ? j : 0) * ldm;
 #pragma unroll 2
-      for (int64_t i = 0; i < m; ++i) {
-        // rows of U and W as float4 (broadcast: every thread reads row i)
-        const float4* u4 = reinterpret_cast<const float4*>(U + i * R);
-        const float4* w4 = reinterpret_cast<const float4*>(Ws + i * R);
-        float uv = 0.f;
+        for (int64_t i = part; act && i < m; i += TPC) {
+          // rows of U and W as float4 (broadcast: the threads of a step read row i)
+          const float4* u4 = reinterpret_cast<const float4*>(U + i * R);
+          const float4* w4 = reinterpret_cast<const float4*>(Ws + i * R);
+          float uv = 0.f;
 #pragma unroll
-        for (int k4 = 0; k4 < R / 4; ++k4) {
-          const float4 u = u4[k4];
-          uv = fmaf(u.x, v[4 * k4], uv);
-          uv = fmaf(u.y, v[4 * k4 + 1], uv);
-          uv = fmaf(u.z, v[4 * k4 + 2], uv);
-          uv = fmaf(u.w, v[4 * k4 + 3], uv);
-        }
-        const float r = Mc[i] - uv;
-        const float c = fminf(fmaxf(r, -lam), lam);
-        hub = fmaf(c, r - 0.5f * c, hub);             // Huber H_lambda(r)
-        const float x = uv + c;                       // M - S
+          for (int k4 = 0; k4 < R / 4; ++k4) {
+            const float4 u = u4[k4];
+            uv = fmaf(u.x, v[4 * k4], uv);
+            uv = fmaf(u.y, v[4 * k4 + 1], uv);
+            uv = fmaf(u.z, v[4 * k4 + 2], uv);
+            uv = fmaf(u.w, v[4 * k4 + 3], uv);
+          }
+          const float r = Mc[i] - uv;
+          const float c = fminf(fmaxf(r, -lam), lam);
+          hub = fmaf(c, r - 0.5f * c, hub);             // Huber H_lambda(r)
+          const float x = uv + c;                       // M - S
 #pragma unroll
-        for (int k4 = 0; k4 < R / 4; ++k4) {
-          const float4 w = w4[k4];
-          acc[4 * k4] = fmaf(x, w.x, acc[4 * k4]);
-          acc[4 * k4 + 1] = fmaf(x, w.y, acc[4 * k4 + 1]);
-          acc[4 * k4 + 2] = fmaf(x, w.z, acc[4 * k4 + 2]);
-          acc[4 * k4 + 3] = fmaf(x, w.w, acc[4 * k4 + 3]);
+          for (int k4 = 0; k4 < R / 4; ++k4) {
+            const float4 w = w4[k4];
+            acc[4 * k4] = fmaf(x, w.x, acc[4 * k4]);
+            acc[4 * k4 + 1] = fmaf(x, w.y, acc[4 * k4 + 1]);
+            acc[4 * k4 + 2] = fmaf(x, w.z, acc[4 * k4 + 2]);
+            acc[4 * k4 + 3] = fmaf(x, w.w, acc[4 * k4 + 3]);
+          }
         }
+#pragma unroll
+        for (int o = TPC / 2; o > 0; o >>= 1)
+#pragma unroll
+          for (int k = 0; k < R; ++k) acc[k] += __shfl_xor_sync(0xffffffffu, acc[k], o);
+        if (act && part == 0)
+#pragma unroll
+          for (int k = 0; k < R; ++k) Vn[j * R + k] = acc[k];
+        hub_w += (double)hub;
       }
-#pragma unroll
-      for (int k = 0; k < R; ++k) Vn[j * R + k] = acc[k];
-      ss_two_sum(hub_hi, hub_lo, hub);
+      // per-warp Huber partial (summed by warp 0 with the metrics)
+      for (int o = 16; o > 0; o >>= 1) hub_w += __shfl_xor_sync(0xffffffffu, hub_w, o);
+      if ((tid & 31) == 0) ws[tid >> 5] = hub_w;
     }
-    const double huber = ss_block_sum((double)hub_hi + (double)hub_lo, ws);
+    __syncthreads();
     ss_gram<R>(Vn, Vn, n, Qn, gp);
     ss_gram<R>(V, Vn, n, XV, gp);
     // ---- U-step: P = X V', U' = P (Q' + rho I)^{-1}, one thread per row ---------
-    if (!ss_ridge_inverse<R>(Qn, rho, A, F, HI)) {
+    if (!ss_ridge_inverse<R>(Qn, rho, A, HI, &s_flags[2])) {
       if (tid == 0) s_flags[1] = DCF_ENONFINITE;
       __syncthreads();
       break;
     }
-    for (int64_t i = tid; i < m; i += kSSThreads) {
+    for (int64_t ib = 0; ib < m; ib += kSSThreads / TPR) {
+      const int64_t i = ib + tid / TPR;
+      const int part = tid % TPR;
+      const bool act = i < m;
       float u[R], p[R];
 #pragma unroll
-      for (int k = 0; k < R; ++k) { u[k] = U[i * R + k]; p[k] = 0.f; }
+      for (int k = 0; k < R; ++k) { u[k] = act ? U[i * R + k] : 0.f; p[k] = 0.f; }
 #pragma unroll 2
-      for (int64_t j = 0; j < n; ++j) {
+      for (int64_t j = part; act && j < n; j += TPR) {
         const float4* v4 = reinterpret_cast<const float4*>(V + j * R);
         const float4* vn4 = reinterpret_cast<const float4*>(Vn + j * R);
         float uv = 0.f;
@@ -276,36 +324,53 @@ __global__ void __launch_bounds__(kSSThreads, 1) k_solve_small(SmallSolveArgs a)
         }
       }
 #pragma unroll
-      for (int l = 0; l < R; ++l) {
-        float s = 0.f;
+      for (int o = TPR / 2; o > 0; o >>= 1)
 #pragma unroll
-        for (int k = 0; k < R; ++k) s = fmaf(p[k], HI[k * R + l], s);
-        Un[i * R + l] = s;
+        for (int k = 0; k < R; ++k) p[k] += __shfl_xor_sync(0xffffffffu, p[k], o);
+      if (act && part == 0) {
+#pragma unroll
+        for (int l = 0; l < R; ++l) {
+          float s2 = 0.f;
+#pragma unroll
+          for (int k = 0; k < R; ++k) s2 = fmaf(p[k], HI[k * R + l], s2);
+          Un[i * R + l] = s2;
+        }
       }
     }
     __syncthreads();
     ss_gram<R>(Un, Un, m, Gn, gp);
     ss_gram<R>(U, Un, m, XU, gp);
-    // ---- metrics and the stop test -------------------------------------------------
-    double v0 = 0.0, v1 = 0.0, v2 = 0.0, t0 = 0.0, t1 = 0.0;
-    for (int e = tid; e < R * R; e += kSSThreads) {
-      v0 = fma(Gn[e], Qn[e], v0);
-      v1 = fma(XU[e], XV[e], v1);
-      v2 = fma(G[e], Q[e], v2);
-      if (e / R == e % R) { t0 += G[e]; t1 += Q[e]; }
+    // ---- metrics and the stop test (warp 0) -----------------------------------------
+    if (tid < 32) {
+      double v[6] = {0, 0, 0, 0, 0, 0};
+      for (int e = tid; e < R * R; e += 32) {
+        v[0] = fma(Gn[e], Qn[e], v[0]);
+        v[1] = fma(XU[e], XV[e], v[1]);
+        v[2] = fma(G[e], Q[e], v[2]);
+        if (e / R == e % R) { v[3] += G[e]; v[4] += Q[e]; }
+      }
+      if (tid < kSSThreads / 32) v[5] = ws[tid];      // per-warp Huber partials
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+        for (int q = 0; q < 6; ++q) v[q] += __shfl_xor_sync(0xffffffffu, v[q], o);
+      if (tid == 0) {
+        double d2 = v[0] - 2.0 * v[1] + v[2];
+        if (d2 < 0) d2 = 0;
+        const double dl = v[0] > 0 ? sqrt(d2 / v[0]) : INFINITY;
+        const double obj = v[5] + 0.5 * (double)rho * (v[3] + v[4]);
+        s_met[0] = dl;
+        s_met[1] = obj;
+        s_met[2] = v[5];
+        if (!isfinite(v[0]) || !isfinite(obj)) s_flags[1] = DCF_ENONFINITE;
+        if (solve_mode && dl <= tol) s_flags[0] = 1;
+      }
     }
-    const double a0 = ss_block_sum(v0, ws), a1 = ss_block_sum(v1, ws), a2 = ss_block_sum(v2, ws);
-    const double tr0 = ss_block_sum(t0, ws), tr1 = ss_block_sum(t1, ws);
-    double d2 = a0 - 2.0 * a1 + a2;
-    if (d2 < 0) d2 = 0;
-    last_dl = a0 > 0 ? sqrt(d2 / a0) : INFINITY;
-    last_hub = huber;
-    last_obj = huber + 0.5 * (double)rho * (tr0 + tr1);
+    __syncthreads();
+    last_dl = s_met[0];
+    last_obj = s_met[1];
+    last_hub = s_met[2];
     ++done;
-    if (tid == 0) {
-      if (!isfinite(a0) || !isfinite(last_obj)) s_flags[1] = DCF_ENONFINITE;
-      if (solve_mode && last_dl <= tol) s_flags[0] = 1;
-    }
     for (int e = tid; e < R * R; e += kSSThreads) { G[e] = Gn[e]; Q[e] = Qn[e]; }
     cur = nxt;
     __syncthreads();
