@@ -125,8 +125,8 @@ def alg_bytes_per_iter(m, n, r):
 # The capture ran a smaller n; traffic grows in proportion to n (M is streamed
 # once, V read and written), so it is scaled by n.  None for other shapes.
 NCU_TRAFFIC = {
-    # k_fused<32, 5>, m=4096, n=16384, r=32: 273.77 MB read + 4.80 MB written
-    "fused_step": {"m": 4096, "r": 32, "n": 16384, "bytes": 278.57e6},
+    # k_fused<32, 5, false>, m=4096, n=16384, r=32: 273.81 MB read + 4.65 MB written
+    "fused_step": {"m": 4096, "r": 32, "n": 16384, "bytes": 278.46e6},
     # k_tc2<64, 5, false> / k_tc2<64, 7, true>, m=16384, n=16384, r=64
     "pass_a": {"m": 16384, "r": 64, "n": 16384, "bytes": 1335.38e6},
     "pass_b": {"m": 16384, "r": 64, "n": 16384, "bytes": 1090.35e6},
