@@ -119,6 +119,21 @@ dcf_status dcf_set_stream(dcf_handle h, void* stream);
 dcf_status dcf_load_blocks(dcf_handle h, const float* const* M_i, const int64_t* ld_i,
                            int where, int borrow);
 
+/* Replace the values of M by new blocks of the same shape and keep the rest
+ * of the state: U, V, the iteration count, the r x r workspace and the
+ * captured iteration graphs.  The next dcf_step continues from the current
+ * factors on the new data: a warm start, as when the clients' local data
+ * change between the communication rounds of Algorithm 1.  M_i, ld_i and
+ * where as for dcf_load_blocks; the values are copied into the buffer that
+ * dcf_load_blocks allocated (its device address does not change).  Returns
+ * once the copy and its NaN/Inf check have completed.  DCF_ESTATE before a
+ * dcf_load_blocks or when M is borrowed (write the new values into the
+ * borrowed matrix instead); DCF_EINVAL as for dcf_load_blocks;
+ * DCF_ENONFINITE when a value is NaN or Inf, after which the handle needs a
+ * dcf_load_blocks before the next step. */
+dcf_status dcf_reload_blocks(dcf_handle h, const float* const* M_i, const int64_t* ld_i,
+                             int where);
+
 /* Set the starting point U0 (m x r) and V0_i (n_i x r).  Without this call
  * dcf_step/dcf_solve start from U0 ~ N(0, 1/m) (counter-based Philox4x32-10,
  * keyed by params.seed) and V0 = M^T U0 (U0^T U0 + rho I)^{-1}, the V-step

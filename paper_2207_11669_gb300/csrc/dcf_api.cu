@@ -653,53 +653,103 @@ extern "C" dcf_status dcf_set_stream(dcf_handle h, void* stream) {
   return DCF_OK;
 }
 
-extern "C" dcf_status dcf_load_blocks(dcf_handle h, const float* const* M_i, const int64_t* ld_i,
-                                      int where, int borrow) {
-  if (!h) return DCF_EINVAL;
-  if (!M_i) return fail(h, DCF_EINVAL, "M_i is NULL");
-  if (where != 0 && where != 1) return fail(h, DCF_EINVAL, "where must be 0 or 1");
+namespace dcf {
+namespace api {
+
+// Copy the blocks into the handle's own M buffer and check them for NaN/Inf;
+// returns after both have completed (*nonfinite set when a value failed).
+static dcf_status copy_blocks_checked(dcf_handle h, const float* const* M_i, const int64_t* ld_i,
+                                      int where, bool* nonfinite) {
+  cudaMemcpyKind kind = where == 0 ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
   for (int i = 0; i < h->E; ++i) {
-    if (!M_i[i]) return fail(h, DCF_EINVAL, "a block pointer is NULL");
-    if (ld_i && ld_i[i] < h->m) return fail(h, DCF_EINVAL, "ld_i < m");
-  }
-  dcf_status st = begin_work(h);
-  if (st != DCF_OK) return st;
-  bool contiguous = where == 1;
-  for (int i = 0; i < h->E && contiguous; ++i) {
-    if (ld_i && ld_i[i] != h->m) contiguous = false;
-    if (i > 0 && M_i[i] != M_i[i - 1] + h->m * h->n_i[i - 1]) contiguous = false;
-  }
-  if (borrow && where == 1) {
-    if (!contiguous)
-      return fail(h, DCF_EINVAL, "borrowed blocks must form one contiguous column-major matrix");
-    h->M = const_cast<float*>(M_i[0]);
-    h->M_borrowed = true;
-  } else {
-    if (!h->M || h->M_borrowed) {
-      h->M = (float*)dev_alloc(h, (size_t)h->m * h->n * sizeof(float));
-      if (!h->M) return fail(h, DCF_ENOMEM, "cannot allocate M");
-      h->M_borrowed = false;
-    }
-    cudaMemcpyKind kind = where == 0 ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
-    for (int i = 0; i < h->E; ++i) {
-      int64_t ld = ld_i ? ld_i[i] : h->m;
-      CK(cudaMemcpy2DAsync(h->M + h->c_i[i] * h->m, h->m * sizeof(float), M_i[i],
-                           ld * sizeof(float), h->m * sizeof(float), h->n_i[i], kind, h->stream),
-         "copy block");
-    }
+    int64_t ld = ld_i ? ld_i[i] : h->m;
+    CK(cudaMemcpy2DAsync(h->M + h->c_i[i] * h->m, h->m * sizeof(float), M_i[i],
+                         ld * sizeof(float), h->m * sizeof(float), h->n_i[i], kind, h->stream),
+       "copy block");
   }
   CK(cudaMemsetAsync(h->flag, 0, sizeof(int), h->stream), "memset");
   CK(launch_check_finite(h->M, h->m * h->n, h->flag, h->stream), "check M");
   int flag = 0;
   CK(cudaMemcpyAsync(&flag, h->flag, sizeof(int), cudaMemcpyDeviceToHost, h->stream), "flag");
   CK(cudaStreamSynchronize(h->stream), "sync");
-  if (flag) return fail(h, DCF_ENONFINITE, "M contains NaN or Inf");
+  *nonfinite = flag != 0;
+  return DCF_OK;
+}
+
+static dcf_status check_block_args(dcf_handle h, const float* const* M_i, const int64_t* ld_i,
+                                   int where) {
+  if (!M_i) return fail(h, DCF_EINVAL, "M_i is NULL");
+  if (where != 0 && where != 1) return fail(h, DCF_EINVAL, "where must be 0 or 1");
+  for (int i = 0; i < h->E; ++i) {
+    if (!M_i[i]) return fail(h, DCF_EINVAL, "a block pointer is NULL");
+    if (ld_i && ld_i[i] < h->m) return fail(h, DCF_EINVAL, "ld_i < m");
+  }
+  return DCF_OK;
+}
+
+}  // namespace api
+}  // namespace dcf
+
+extern "C" dcf_status dcf_load_blocks(dcf_handle h, const float* const* M_i, const int64_t* ld_i,
+                                      int where, int borrow) {
+  if (!h) return DCF_EINVAL;
+  dcf_status st = check_block_args(h, M_i, ld_i, where);
+  if (st != DCF_OK) return st;
+  st = begin_work(h);
+  if (st != DCF_OK) return st;
+  bool contiguous = where == 1;
+  for (int i = 0; i < h->E && contiguous; ++i) {
+    if (ld_i && ld_i[i] != h->m) contiguous = false;
+    if (i > 0 && M_i[i] != M_i[i - 1] + h->m * h->n_i[i - 1]) contiguous = false;
+  }
+  bool nonfinite = false;
+  if (borrow && where == 1) {
+    if (!contiguous)
+      return fail(h, DCF_EINVAL, "borrowed blocks must form one contiguous column-major matrix");
+    h->M = const_cast<float*>(M_i[0]);
+    h->M_borrowed = true;
+    CK(cudaMemsetAsync(h->flag, 0, sizeof(int), h->stream), "memset");
+    CK(launch_check_finite(h->M, h->m * h->n, h->flag, h->stream), "check M");
+    int flag = 0;
+    CK(cudaMemcpyAsync(&flag, h->flag, sizeof(int), cudaMemcpyDeviceToHost, h->stream), "flag");
+    CK(cudaStreamSynchronize(h->stream), "sync");
+    nonfinite = flag != 0;
+  } else {
+    if (!h->M || h->M_borrowed) {
+      h->M = (float*)dev_alloc(h, (size_t)h->m * h->n * sizeof(float));
+      if (!h->M) return fail(h, DCF_ENOMEM, "cannot allocate M");
+      h->M_borrowed = false;
+    }
+    st = copy_blocks_checked(h, M_i, ld_i, where, &nonfinite);
+    if (st != DCF_OK) return st;
+  }
+  if (nonfinite) return fail(h, DCF_ENONFINITE, "M contains NaN or Inf");
   if ((h->path == 2 || h->path == 3) && fused_make_tmap(h->tmap, h->M, h->m, h->n) != 0)
     return fail(h, DCF_ECUDA, "cuTensorMapEncodeTiled failed for M");
   h->loaded = true;
   h->initialized = false;
   for (int p = 0; p < 2; ++p)
     if (h->graph[p]) { cudaGraphExecDestroy(h->graph[p]); h->graph[p] = nullptr; }
+  return end_work(h);
+}
+
+extern "C" dcf_status dcf_reload_blocks(dcf_handle h, const float* const* M_i,
+                                        const int64_t* ld_i, int where) {
+  if (!h) return DCF_EINVAL;
+  if (!h->loaded) return fail(h, DCF_ESTATE, "dcf_load_blocks has not been called");
+  if (h->M_borrowed)
+    return fail(h, DCF_ESTATE, "M is borrowed; write the new values into the borrowed matrix");
+  dcf_status st = check_block_args(h, M_i, ld_i, where);
+  if (st != DCF_OK) return st;
+  st = begin_work(h);
+  if (st != DCF_OK) return st;
+  bool nonfinite = false;
+  st = copy_blocks_checked(h, M_i, ld_i, where, &nonfinite);
+  if (st != DCF_OK) return st;
+  if (nonfinite) {
+    h->loaded = false;   // M now holds the rejected values: no step may run on them
+    return fail(h, DCF_ENONFINITE, "M contains NaN or Inf");
+  }
   return end_work(h);
 }
 

@@ -53,6 +53,8 @@ _SIGS = {
     "dcf_get_path": (C.c_int, [C.c_void_p]),
     "dcf_load_blocks": (C.c_int, [C.c_void_p, C.POINTER(C.c_void_p), C.POINTER(C.c_int64),
                                   C.c_int, C.c_int]),
+    "dcf_reload_blocks": (C.c_int, [C.c_void_p, C.POINTER(C.c_void_p), C.POINTER(C.c_int64),
+                                    C.c_int]),
     "dcf_load_init": (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(C.c_void_p), C.c_int]),
     "dcf_step": (C.c_int, [C.c_void_p, C.c_int]),
     "dcf_solve": (C.c_int, [C.c_void_p, C.POINTER(C.c_int), C.POINTER(C.c_double)]),
@@ -207,6 +209,13 @@ def dcf_load_blocks(h, blocks, ld=None, borrow=False):
     arr = (C.c_void_p * len(ptrs))(*[p.value for p in ptrs])
     ld_arr = None if ld is None else (C.c_int64 * len(ld))(*[int(x) for x in ld])
     _check(h, lib().dcf_load_blocks(h, arr, ld_arr, where, 1 if borrow else 0))
+
+
+def dcf_reload_blocks(h, blocks, ld=None):
+    ptrs, wheres = zip(*[_ptr_where(b) for b in blocks])
+    arr = (C.c_void_p * len(ptrs))(*[p.value for p in ptrs])
+    ld_arr = None if ld is None else (C.c_int64 * len(ld))(*[int(x) for x in ld])
+    _check(h, lib().dcf_reload_blocks(h, arr, ld_arr, wheres[0]))
 
 
 def dcf_load_init(h, U0, V0_blocks=None):
@@ -399,6 +408,12 @@ class Solver:
             borrow = _is_torch(M)
         self._keep = (M, blocks)
         dcf_load_blocks(self.h, blocks, borrow=borrow)
+
+    def reload(self, M):
+        """New values of M (same shape), copied into the loaded buffer; the
+        iterate carries over (dcf_reload_blocks).  The copy has completed on
+        return, so M need not outlive the call."""
+        dcf_reload_blocks(self.h, self.blocks_of(M))
 
     def load_init(self, U0, V0=None):
         U0 = self._as_factor(U0)

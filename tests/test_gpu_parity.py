@@ -305,3 +305,62 @@ def test_borrowed_device_matrix_matches_host_copy(path):
     assert np.array_equal(s1.factors()[0], s2.factors()[0])
     s1.close()
     s2.close()
+
+
+@pytest.mark.parametrize("path", PATHS)
+def test_reload_continues_from_the_current_factors(path):
+    """dcf_reload_blocks: two steps on M, new values M' copied in, one more
+    step equals one oracle round on M' from the factors the GPU held."""
+    import torch
+    m, n_i, r = 120, [40, 37, 50], 16
+    if not path_ok(path, m, r, sum(n_i)):
+        pytest.skip("shape outside this path")
+    case = make_case(m, n_i, r, seed=23)
+    case2 = make_case(m, n_i, r, seed=24)
+    s = gpu_solver(case, path=path)
+    s.step(2)
+    Ua, Va = s.factors()
+    s.reload(case2["M"])                           # host blocks
+    s.step(1)
+    U, V = s.factors()
+    U1, V1, S1, _, _ = O.dcf_run(case2["M"], n_i, Ua, Va, case2["rho"], case2["lam"], 1)
+    assert rel(U, U1) <= 1e-4
+    assert rel(V, V1) <= 1e-4
+    S_gpu = np.concatenate([s.LS(i)[1] for i in range(len(n_i))], axis=1)
+    assert rel(S_gpu, S1) <= 1e-4
+    # device blocks: back to M, then one more step, against the oracle again
+    Ub, Vb = U, V
+    s.reload(torch.from_numpy(np.ascontiguousarray(case["M"].T)).cuda())
+    s.step(1)
+    U, V = s.factors()
+    U2, V2, _, _, _ = O.dcf_run(case["M"], n_i, Ub, Vb, case["rho"], case["lam"], 1)
+    assert rel(U, U2) <= 1e-4
+    assert rel(V, V2) <= 1e-4
+    s.close()
+
+
+def test_reload_errors():
+    import torch
+    case = make_case(200, [50, 50, 50, 50], 5, seed=3)
+    s = dcf.Solver(200, case["n_i"], 5, case["rho"], case["lam"])
+    with pytest.raises(dcf.DcfError) as e:
+        s.reload(case["M"])                        # nothing loaded yet
+    assert e.value.status == dcf.DCF_ESTATE
+    Mt = torch.from_numpy(np.ascontiguousarray(case["M"].T)).cuda()
+    s.load(Mt)                                     # borrowed
+    with pytest.raises(dcf.DcfError) as e:
+        s.reload(case["M"])
+    assert e.value.status == dcf.DCF_ESTATE
+    s.load(case["M"])                              # own copy
+    s.step(1)
+    bad = case["M"].copy()
+    bad[7, 11] = np.nan
+    with pytest.raises(dcf.DcfError) as e:
+        s.reload(bad)
+    assert e.value.status == dcf.DCF_ENONFINITE
+    with pytest.raises(dcf.DcfError) as e:
+        s.step(1)                                  # the rejected values are never iterated on
+    assert e.value.status == dcf.DCF_ESTATE
+    s.load(case["M"])
+    s.step(1)
+    s.close()
