@@ -2,11 +2,12 @@
 // tails and by the learned network.
 //
 // Cost model.  GB300 issues an FP64 warp instruction every 64 cycles per SM
-// sub-partition (about 2 FP64 FMA/clk/SM), so the code below keeps FP64 to
-// the factorisation itself, packs its trailing updates across all threads of
-// the CTA, uses the root-free L D L^T form and replaces FP64 divisions by
-// Newton steps from the FP32 estimate.  The triangular inverse and the final
-// product are FP32 and run one warp per column.
+// sub-partition (about 2 FP64 FMA/clk/SM), and the factorisation is a chain
+// of R dependent steps, so it runs in double-float arithmetic on the FP32
+// pipes (about 48 bits), packs its trailing updates across all threads of
+// the CTA, uses the root-free L D L^T form and replaces divisions by Newton
+// steps from the FP32 estimate.  The triangular inverse and the final
+// product are FP32 from the rounded factors and run one warp per column.
 #pragma once
 #include <cuda_runtime.h>
 
@@ -15,60 +16,154 @@
 namespace dcf {
 
 // ---------------------------------------------------------------------------
-// FP64 root-free Cholesky G = L D L^T (L unit lower triangular), in place on a
-// row-major R x R matrix in shared memory (R <= 64): on return the strict
-// lower triangle holds L, the diagonal holds 1/D, the upper triangle is zero.
-// Block-wide: every thread of the CTA must call it.  A non-positive pivot
-// leaves NaN.
-//
-// Step k updates the trailing lower triangle with the unscaled column,
-//   A_ij -= A_ik (A_jk / D_k),
-// which needs one barrier per step: thread 0 updates A_{k+1,k+1} first and
-// forms the next reciprocal 1/D_{k+1} (FP32 estimate, one FP64 Newton step)
-// while warps 1.. finish the step.
+// Double-float arithmetic: a value is an unevaluated sum h + l of two floats
+// with |l| <= ulp(h)/2 (about 48 significant bits).  The building blocks are
+// Knuth's two-sum, Dekker's fast two-sum and the FMA form of the exact
+// product (p = a b rounded, e = fma(a, b, -p), so that p + e = a b exactly).
+// They run on the FP32 pipes, 64 times wider than the FP64 pipe of this GPU.
 // ---------------------------------------------------------------------------
+struct df2 {
+  float h, l;
+};
+
+static __device__ __forceinline__ df2 df_fast_two_sum(float a, float b) {   // |a| >= |b|
+  const float s = a + b;
+  return {s, b - (s - a)};
+}
+
+static __device__ __forceinline__ df2 df_two_sum(float a, float b) {
+  const float s = a + b;
+  const float bb = s - a;
+  return {s, (a - (s - bb)) + (b - bb)};
+}
+
+static __device__ __forceinline__ df2 df_mul(df2 x, df2 y) {
+  const float p = x.h * y.h;
+  float e = fmaf(x.h, y.h, -p);
+  e = fmaf(x.h, y.l, e);
+  e = fmaf(x.l, y.h, e);
+  return df_fast_two_sum(p, e);
+}
+
+static __device__ __forceinline__ df2 df_sub(df2 x, df2 y) {
+  const df2 s = df_two_sum(x.h, -y.h);
+  return df_fast_two_sum(s.h, s.l + (x.l - y.l));
+}
+
+// 1/d: the hardware reciprocal estimate x0 (relative error about 2^-22),
+// then one Newton step x0 + x0 (1 - d x0) with the residual formed exactly
+// enough in double-float: relative error about 2^-44.  d <= 0 or non-finite
+// gives NaN.
+static __device__ __forceinline__ df2 df_recip(df2 d) {
+  if (!(d.h > 0.f) || !isfinite(d.h)) return {__int_as_float(0x7fc00000), 0.f};
+  const float x0 = __fdividef(1.f, d.h);
+  const float p = d.h * x0;
+  const float pe = fmaf(d.h, x0, -p);            // d.h x0 = p + pe exactly
+  float e = (1.f - p) - pe;                      // 1 - p is exact (p is within 2^-21 of 1)
+  e = fmaf(-d.l, x0, e);
+  return df_fast_two_sum(x0, x0 * e);
+}
+
+// FP64 1/a: the FP32 estimate (relative error <= 2^-23) and one FP64 Newton
+// step (error about 2^-46).
 static __device__ __forceinline__ double recip_f64(double a) {
-  // FP32 estimate (relative error <= 2^-23), one Newton step: error ~ 2^-46
   const double r = a > 0.0 ? (double)__frcp_rn((float)a) : __longlong_as_double(0x7ff8000000000000LL);
   const double e = fma(-a, r, 1.0);
   return fma(r, e, r);
 }
 
-static __device__ __noinline__ void chol_inplace(double* A, int R) {
-  __shared__ double s_r[kMaxR];          // 1 / D_k
-  const int tid = threadIdx.x, nt = blockDim.x;
-  if (tid == 0) s_r[0] = recip_f64(A[0]);
+static __device__ __forceinline__ df2 df_from_double(double x) {
+  const float h = (float)x;
+  return {h, (float)(x - (double)h)};
+}
+
+// ---------------------------------------------------------------------------
+// Root-free Cholesky G = L D L^T (L unit lower triangular) in double-float.
+// Block-wide, 256 threads, R <= 64.  Thread t owns the lower-triangle entries
+// e = t, t + 256, ... (e = i (i + 1) / 2 + j, j <= i) and keeps them in
+// registers for the whole factorisation.  Step k updates every owned entry
+// with j > k,
+//   A_ij -= A_ik (A_jk / D_k),
+// from column k, which the owners of that column publish to shared memory
+// (double-buffered) together with 1/D_k; the owner of A_{k+1,k+1} forms
+// 1/D_{k+1} right after its update.  One barrier per step.
+//
+// Input: A (R*R doubles, row-major, lower triangle read).  Output: F = L^T in
+// FP32 with 1/D_k on the diagonal (row p of F is column p of L) and zeros
+// below its diagonal; s_r[k] = 1/D_k.  A non-positive pivot leaves NaN.
+// ---------------------------------------------------------------------------
+constexpr int kCholThreads = 256;
+
+// kCholSlots = ceil(R (R + 1) / 2 / 256) for the largest R of the instance
+template <int kCholSlots>
+static __device__ __noinline__ void chol_df_to_f(const double* A, int R, float* F, df2* col,
+                                                 df2* s_r) {
+  const int tid = threadIdx.x;
+  const int ne = R * (R + 1) / 2;
+  df2 a[kCholSlots];
+  int ei[kCholSlots], ej[kCholSlots];
+#pragma unroll
+  for (int q = 0; q < kCholSlots; ++q) {
+    const int e = tid + q * kCholThreads;
+    int i = -1, j = 0;
+    if (e < ne) {
+      i = (int)((sqrtf(8.0f * (float)e + 1.0f) - 1.0f) * 0.5f);
+      while ((i + 1) * (i + 2) / 2 <= e) ++i;
+      while (i * (i + 1) / 2 > e) --i;
+      j = e - i * (i + 1) / 2;
+      a[q] = df_from_double(A[i * R + j]);
+    } else {
+      a[q] = {0.f, 0.f};
+    }
+    ei[q] = i;
+    ej[q] = j;
+  }
+  for (int idx = tid; idx < R * R; idx += kCholThreads) F[idx] = 0.f;
+  // column 0 and 1/D_0
+#pragma unroll
+  for (int q = 0; q < kCholSlots; ++q) {
+    if (ei[q] >= 0 && ej[q] == 0) col[ei[q]] = a[q];
+    if (ei[q] == 0) s_r[0] = df_recip(a[q]);
+  }
   __syncthreads();
   for (int k = 0; k + 1 < R; ++k) {
-    const double rk = s_r[k];
-    const int m = R - k - 1;
-    const int count = m * (m + 1) / 2;     // entries (i, j), k < j <= i
-    if (tid == 0) {
-      // entry (k+1, k+1) first, then the next pivot's reciprocal
-      const int i = k + 1;
-      const double v = fma(-A[i * R + k], A[i * R + k] * rk, A[i * R + i]);
-      A[i * R + i] = v;
-      s_r[k + 1] = recip_f64(v);
+    const df2* ck = col + (k & 1) * kMaxR;          // column k
+    df2* cn = col + ((k + 1) & 1) * kMaxR;          // column k + 1, published below
+    const df2 rk = s_r[k];
+    // every load of the step before any store, so that the owned entries'
+    // updates overlap instead of queueing behind each other's stores
+    df2 ci[kCholSlots], cj[kCholSlots];
+#pragma unroll
+    for (int q = 0; q < kCholSlots; ++q) {
+      const bool act = ei[q] >= 0 && ej[q] > k;
+      ci[q] = ck[act ? ei[q] : 0];
+      cj[q] = ck[act ? ej[q] : 0];
     }
-    // the other entries, flattened over warps 1 .. (so that warp 0 runs only
-    // the pivot chain); entry t = 0 is (k+1, k+1)
-    for (int t = tid - 31; t < count; t += nt - 32) {
-      if (tid < 32) break;
-      int ii = (int)((sqrtf(8.0f * (float)t + 1.0f) - 1.0f) * 0.5f);
-      while ((ii + 1) * (ii + 2) / 2 <= t) ++ii;
-      while (ii * (ii + 1) / 2 > t) --ii;
-      const int jj = t - ii * (ii + 1) / 2;
-      const int i = k + 1 + ii, j = k + 1 + jj;
-      A[i * R + j] = fma(-A[i * R + k], A[j * R + k] * rk, A[i * R + j]);
+#pragma unroll
+    for (int q = 0; q < kCholSlots; ++q)
+      if (ei[q] >= 0 && ej[q] > k) a[q] = df_sub(a[q], df_mul(ci[q], df_mul(cj[q], rk)));
+#pragma unroll
+    for (int q = 0; q < kCholSlots; ++q) {
+      if (ei[q] >= 0 && ej[q] == k + 1) {
+        cn[ei[q]] = a[q];
+        if (ei[q] == k + 1) s_r[k + 1] = df_recip(a[q]);
+      }
     }
     __syncthreads();
   }
-  // L_ik = A_ik / D_k below the diagonal; 1/D_k on it; zeros above
-  for (int idx = tid; idx < R * R; idx += nt) {
-    const int i = idx / R, j = idx % R;
-    if (j < i) A[idx] *= s_r[j];
-    else if (j == i) A[idx] = s_r[i];
-    else A[idx] = 0.0;
+  // L_ij = A_ij / D_j below the diagonal, 1/D_i on it
+#pragma unroll
+  for (int q = 0; q < kCholSlots; ++q) {
+    const int i = ei[q], j = ej[q];
+    if (i < 0) continue;
+    float v;
+    if (j < i) {
+      const df2 l = df_mul(a[q], s_r[j]);
+      v = l.h + l.l;
+    } else {
+      v = s_r[i].h + s_r[i].l;
+    }
+    F[j * R + i] = v;
   }
   __syncthreads();
 }
@@ -85,21 +180,22 @@ static __device__ __noinline__ int all_finite(const double* A, int n) {
   return r;
 }
 
-// SPD inverse: FP64 factorisation G = L D L^T in place (the stability-critical
+// SPD inverse: double-float factorisation G = L D L^T (the stability-critical
 // step), then L^{-1} and G^{-1} = L^{-T} D^{-1} L^{-1} in FP32 from the
 // rounded factors.  A: R*R doubles (shared, destroyed); F: R*R floats (shared
-// scratch); out: R*R floats (any memory).  Block-wide, R <= 64, R even.
+// scratch); out: R*R floats (any memory).  Block-wide with 256 threads,
+// R <= 64, R even.
 static __device__ __noinline__ void spd_inverse_f32(double* A, float* F, int R, float* out) {
-  chol_inplace(A, R);
+  __shared__ df2 s_r[kMaxR];             // 1 / D_k
+  __shared__ df2 s_col[2 * kMaxR];       // the current column of the factorisation
   const int tid = threadIdx.x, nt = blockDim.x;
   const int lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
-  // F = L^T in FP32 (row p of F is column p of L), so that a warp reads a
-  // column of L with consecutive addresses
-  for (int idx = tid; idx < R * R; idx += nt) {
-    const int i = idx / R, p = idx % R;
-    F[p * R + i] = (float)A[idx];
-  }
-  __syncthreads();
+  // F = L^T in FP32 (row p of F is column p of L, so that a warp reads a
+  // column of L with consecutive addresses), 1/D_k on the diagonal
+  if (R <= 16) chol_df_to_f<1>(A, R, F, s_col, s_r);
+  else if (R <= 32) chol_df_to_f<3>(A, R, F, s_col, s_r);
+  else chol_df_to_f<(kMaxR * (kMaxR + 1) / 2 + kCholThreads - 1) / kCholThreads>(A, R, F, s_col,
+                                                                                s_r);
   float* Li = reinterpret_cast<float*>(A);   // R*R floats fit in the R*R doubles ...
   float* dinv = Li + R * R;                  // ... and so do R more
   for (int i = tid; i < R; i += nt) dinv[i] = F[i * R + i];
