@@ -91,7 +91,9 @@ typedef struct {
 
 /* Device allocator hook: alloc(bytes, ctx) returns device memory or NULL,
  * release(ptr, ctx) frees it.  Passing NULLs restores cudaMalloc/cudaFree.
- * Must be set before dcf_create to take effect for that handle. */
+ * Must be set before dcf_create to take effect for that handle.  Pointers
+ * must be 256-byte aligned, as cudaMalloc's are; a misaligned one is released
+ * again and the call that needed it fails with DCF_ENOMEM. */
 typedef void* (*dcf_alloc_fn)(size_t bytes, void* ctx);
 typedef void (*dcf_free_fn)(void* ptr, void* ctx);
 void dcf_set_allocator(dcf_alloc_fn alloc, dcf_free_fn release, void* ctx);

@@ -65,6 +65,10 @@ void* dev_alloc(dcf_handle h, size_t bytes) {
   void* p = nullptr;
   if (h->alloc) {
     p = h->alloc(bytes, h->alloc_ctx);
+    if (p && (reinterpret_cast<uintptr_t>(p) & 255u) != 0) {   // vector loads and TMA need it
+      if (h->release) h->release(p, h->alloc_ctx);
+      p = nullptr;
+    }
   } else if (cudaMalloc(&p, bytes) != cudaSuccess) {
     cudaGetLastError();
     p = nullptr;
@@ -478,8 +482,10 @@ extern "C" dcf_status dcf_create(const dcf_params* p, dcf_handle* out) {
   cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, h->device);
   if (h->num_sms <= 0) h->num_sms = 1;
   if (cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking) != cudaSuccess ||
       cudaEventCreateWithFlags(&h->ev_in, cudaEventDisableTiming) != cudaSuccess ||
-      cudaEventCreateWithFlags(&h->ev_out, cudaEventDisableTiming) != cudaSuccess) {
+      cudaEventCreateWithFlags(&h->ev_out, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&h->ev_side, cudaEventDisableTiming) != cudaSuccess) {
     dcf_destroy(h);
     return DCF_ECUDA;
   }
@@ -658,17 +664,23 @@ namespace api {
 
 // Copy the blocks into the handle's own M buffer and check them for NaN/Inf;
 // returns after both have completed (*nonfinite set when a value failed).
+// Block i is checked on the side stream while block i + 1 is being copied.
 static dcf_status copy_blocks_checked(dcf_handle h, const float* const* M_i, const int64_t* ld_i,
                                       int where, bool* nonfinite) {
   cudaMemcpyKind kind = where == 0 ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
+  CK(cudaMemsetAsync(h->flag, 0, sizeof(int), h->stream), "memset");
   for (int i = 0; i < h->E; ++i) {
     int64_t ld = ld_i ? ld_i[i] : h->m;
-    CK(cudaMemcpy2DAsync(h->M + h->c_i[i] * h->m, h->m * sizeof(float), M_i[i],
-                         ld * sizeof(float), h->m * sizeof(float), h->n_i[i], kind, h->stream),
+    float* dst = h->M + h->c_i[i] * h->m;
+    CK(cudaMemcpy2DAsync(dst, h->m * sizeof(float), M_i[i], ld * sizeof(float),
+                         h->m * sizeof(float), h->n_i[i], kind, h->stream),
        "copy block");
+    CK(cudaEventRecord(h->ev_side, h->stream), "record");
+    CK(cudaStreamWaitEvent(h->side, h->ev_side, 0), "wait");
+    CK(launch_check_finite(dst, h->m * h->n_i[i], h->flag, h->side), "check block");
   }
-  CK(cudaMemsetAsync(h->flag, 0, sizeof(int), h->stream), "memset");
-  CK(launch_check_finite(h->M, h->m * h->n, h->flag, h->stream), "check M");
+  CK(cudaEventRecord(h->ev_side, h->side), "record");
+  CK(cudaStreamWaitEvent(h->stream, h->ev_side, 0), "wait");
   int flag = 0;
   CK(cudaMemcpyAsync(&flag, h->flag, sizeof(int), cudaMemcpyDeviceToHost, h->stream), "flag");
   CK(cudaStreamSynchronize(h->stream), "sync");
@@ -1021,6 +1033,8 @@ extern "C" void dcf_destroy(dcf_handle h) {
   dev_free_all(h);
   if (h->ev_in) cudaEventDestroy(h->ev_in);
   if (h->ev_out) cudaEventDestroy(h->ev_out);
+  if (h->ev_side) cudaEventDestroy(h->ev_side);
   if (h->stream) cudaStreamDestroy(h->stream);
+  if (h->side) cudaStreamDestroy(h->side);
   delete h;
 }

@@ -29,7 +29,8 @@ struct dcf_handle_s {
   int device = 0, num_sms = 0;
   cudaStream_t user_stream = nullptr;
   cudaStream_t stream = nullptr;     // internal capture/launch stream
-  cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+  cudaStream_t side = nullptr;       // NaN/Inf checks of copied blocks, behind the copies
+  cudaEvent_t ev_in = nullptr, ev_out = nullptr, ev_side = nullptr;
   float* M = nullptr;
   bool M_borrowed = false;
   float* U[2] = {nullptr, nullptr};

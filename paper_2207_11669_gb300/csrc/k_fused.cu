@@ -757,29 +757,47 @@ __global__ void __launch_bounds__(256) k_bfused_prep(const BInst* __restrict__ i
 }
 
 // out = in Z for n rows of R (V_old Z, added to the cluster's column sums):
-// block blk of 256 (row, column group of 8) entries (block-wide).
+// block blk of 256 (row, column group of 8) entries (block-wide).  The row's
+// R inputs are fetched with vector loads before any arithmetic, so that they
+// are in flight together.
 template <int R>
 __device__ __forceinline__ void rowmat_block(const float* __restrict__ in,
                                              const float* __restrict__ zmat, int64_t n,
                                              float* __restrict__ out, int64_t blk) {
-  __shared__ float Z[R * R];
-  for (int i = threadIdx.x; i < R * R; i += 256) Z[i] = zmat[i];
+  __shared__ __align__(16) float Z[R * R];
+  for (int i = threadIdx.x; i < R * R / 4; i += 256)
+    reinterpret_cast<float4*>(Z)[i] = reinterpret_cast<const float4*>(zmat)[i];
   __syncthreads();
   const int64_t idx = blk * 256 + threadIdx.x;   // (row, column group of 8)
   const int64_t row = idx / (R / 8);
   const int cg = (int)(idx % (R / 8));
   if (row >= n) return;
-  const float* v = in + row * R;
+  float v[R];
+  const float4* src = reinterpret_cast<const float4*>(in + row * R);
+#pragma unroll
+  for (int k = 0; k < R / 4; ++k) {
+    const float4 t = src[k];
+    v[4 * k] = t.x; v[4 * k + 1] = t.y; v[4 * k + 2] = t.z; v[4 * k + 3] = t.w;
+  }
   float acc[8];
 #pragma unroll
   for (int l = 0; l < 8; ++l) acc[l] = 0.f;
+#pragma unroll
   for (int k = 0; k < R; ++k) {
-    const float x = v[k];
-#pragma unroll
-    for (int l = 0; l < 8; ++l) acc[l] = fmaf(x, Z[k * R + cg * 8 + l], acc[l]);
+    const float4 z0 = *reinterpret_cast<const float4*>(Z + k * R + cg * 8);
+    const float4 z1 = *reinterpret_cast<const float4*>(Z + k * R + cg * 8 + 4);
+    acc[0] = fmaf(v[k], z0.x, acc[0]);
+    acc[1] = fmaf(v[k], z0.y, acc[1]);
+    acc[2] = fmaf(v[k], z0.z, acc[2]);
+    acc[3] = fmaf(v[k], z0.w, acc[3]);
+    acc[4] = fmaf(v[k], z1.x, acc[4]);
+    acc[5] = fmaf(v[k], z1.y, acc[5]);
+    acc[6] = fmaf(v[k], z1.z, acc[6]);
+    acc[7] = fmaf(v[k], z1.w, acc[7]);
   }
-#pragma unroll
-  for (int l = 0; l < 8; ++l) out[row * R + cg * 8 + l] = acc[l];
+  float4* dst = reinterpret_cast<float4*>(out + row * R + cg * 8);
+  dst[0] = make_float4(acc[0], acc[1], acc[2], acc[3]);
+  dst[1] = make_float4(acc[4], acc[5], acc[6], acc[7]);
 }
 
 template <int R>
