@@ -582,7 +582,8 @@ extern "C" dcf_status dcf_create(const dcf_params* p, dcf_handle* out) {
   h->split_cols = ((h->n + splits - 1) / splits + 31) / 32 * 32;
   h->n_splits = (int)((h->n + h->split_cols - 1) / h->split_cols);
   h->n_rblocks = (int)((h->m + 31) / 32);
-  h->n_vgram = (int)std::min<int64_t>(2LL * h->num_sms, (h->n + 31) / 32);
+  // Gram partials of V: one CTA per SM at R >= 32 (4 x 4 register tiles), two below
+  h->n_vgram = (int)std::min<int64_t>((h->R >= 32 ? 1LL : 2LL) * h->num_sms, (h->n + 31) / 32);
 
   const size_t R = h->R, RR = R * R;
   bool ok = true;

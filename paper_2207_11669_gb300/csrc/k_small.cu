@@ -97,15 +97,21 @@ k_gram_part(const float* __restrict__ X, int ldx, int cx,
 }
 
 // Both Grams of the new V in one pass:  Q = V'^T V'  and  X_v = V_old^T V'.
-// Thread tile TB x TB of each output (R = 32: 2 x 2, R = 64: 4 x 4, R <= 16:
-// 1 x 1 with 256 / (R/TB)^2 row groups); 64-row chunks in shared memory.
+// Thread tile TB x TB of each output (R >= 32: 4 x 4, R <= 16: 1 x 1) with
+// 256 / (R/TB)^2 row groups; 64-row chunks staged in shared memory, the next
+// chunk's loads in flight (registers) while the current one is used.  With
+// 4 x 4 tiles a warp reads a row's operands in 3 shared-memory wavefronts.
 template <int R>
 struct GvvCfg {
-  static constexpr int TB = R >= 64 ? 4 : R >= 32 ? 2 : 1;
+  static constexpr int TB = R >= 32 ? 4 : 1;
   static constexpr int NT = R / TB;                 // tiles per dimension
   static constexpr int GROUPS = 256 / (NT * NT);    // row groups
   static constexpr int CH = 64;                     // rows per chunk
+  static constexpr int NV = (CH * R / 4 + 255) / 256;   // float4 per thread per chunk and array
   static constexpr size_t smem_bytes = 2 * (size_t)CH * R * 4;
+  // the row groups' partial tiles are combined one tile row at a time through
+  // the chunk buffers
+  static_assert(GROUPS * NT * NT * TB * 4 * 4 <= smem_bytes, "combine buffer");
 };
 
 // Rows [a0, a1) of one problem; writes the R*R partials at out_q, out_xv.
@@ -116,7 +122,7 @@ __device__ __forceinline__ void gram_vv_block(const float* __restrict__ Vo,
                                               int64_t a1, float2* __restrict__ out_q,
                                               float2* __restrict__ out_xv, float* gsh) {
   using C = GvvCfg<R>;
-  constexpr int TB = C::TB, NT = C::NT, G = C::GROUPS, CH = C::CH;
+  constexpr int TB = C::TB, NT = C::NT, G = C::GROUPS, CH = C::CH, NV = C::NV;
   float* So = gsh;              // [CH][R]  V_old rows
   float* Sn = gsh + CH * R;     // [CH][R]  V' rows
   const int tid = threadIdx.x;
@@ -127,17 +133,30 @@ __device__ __forceinline__ void gram_vv_block(const float* __restrict__ Vo,
   for (int i = 0; i < TB; ++i)
 #pragma unroll
     for (int j = 0; j < TB; ++j) { qh[i][j] = ql[i][j] = xh[i][j] = xl[i][j] = 0.f; }
-  for (int64_t c = a0; c < a1; c += CH) {
+  float4 po[NV], pn[NV];
+  auto fetch = [&](int64_t c) {
     const int rows = (int)dmin64((int64_t)CH, a1 - c);
-    __syncthreads();
-    for (int i = tid; i < CH * R / 4; i += 256) {
-      const int rr = (4 * i) / R;
-      const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
-      const bool ok = rr < rows;
-      reinterpret_cast<float4*>(So)[i] = ok ? reinterpret_cast<const float4*>(Vo + c * R)[i] : z;
-      reinterpret_cast<float4*>(Sn)[i] = ok ? reinterpret_cast<const float4*>(Vn + c * R)[i] : z;
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+      const int i = tid + v * 256;
+      const bool ok = i < CH * R / 4 && (4 * i) / R < rows;
+      po[v] = ok ? reinterpret_cast<const float4*>(Vo + c * R)[i] : make_float4(0.f, 0.f, 0.f, 0.f);
+      pn[v] = ok ? reinterpret_cast<const float4*>(Vn + c * R)[i] : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+  };
+  if (a0 < a1) fetch(a0);
+  for (int64_t c = a0; c < a1; c += CH) {
+    __syncthreads();   // every read of the previous chunk is done
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+      const int i = tid + v * 256;
+      if (i < CH * R / 4) {
+        reinterpret_cast<float4*>(So)[i] = po[v];
+        reinterpret_cast<float4*>(Sn)[i] = pn[v];
+      }
     }
     __syncthreads();
+    if (c + CH < a1) fetch(c + CH);
     float qa[TB][TB], xa[TB][TB];
 #pragma unroll
     for (int i = 0; i < TB; ++i)
@@ -145,11 +164,20 @@ __device__ __forceinline__ void gram_vv_block(const float* __restrict__ Vo,
       for (int j = 0; j < TB; ++j) { qa[i][j] = 0.f; xa[i][j] = 0.f; }
     for (int rr = grp; rr < CH; rr += G) {
       float nk[TB], nl[TB], ok[TB];
+      if constexpr (TB == 4) {
+        const float4 a = *reinterpret_cast<const float4*>(Sn + rr * R + k0);
+        const float4 b = *reinterpret_cast<const float4*>(So + rr * R + k0);
+        const float4 d = *reinterpret_cast<const float4*>(Sn + rr * R + l0);
+        nk[0] = a.x; nk[1] = a.y; nk[2] = a.z; nk[3] = a.w;
+        ok[0] = b.x; ok[1] = b.y; ok[2] = b.z; ok[3] = b.w;
+        nl[0] = d.x; nl[1] = d.y; nl[2] = d.z; nl[3] = d.w;
+      } else {
 #pragma unroll
-      for (int i = 0; i < TB; ++i) {
-        nk[i] = Sn[rr * R + k0 + i];
-        ok[i] = So[rr * R + k0 + i];
-        nl[i] = Sn[rr * R + l0 + i];
+        for (int i = 0; i < TB; ++i) {
+          nk[i] = Sn[rr * R + k0 + i];
+          ok[i] = So[rr * R + k0 + i];
+          nl[i] = Sn[rr * R + l0 + i];
+        }
       }
 #pragma unroll
       for (int i = 0; i < TB; ++i)
@@ -167,22 +195,32 @@ __device__ __forceinline__ void gram_vv_block(const float* __restrict__ Vo,
         two_sum_add(xh[i][j], xl[i][j], xa[i][j]);
       }
   }
-  // combine the row groups (G > 1 only for R <= 8) through shared memory
+  // combine the row groups through shared memory, one tile row at a time:
+  // cmb[g][tile][j][4] = (hi, lo of Q, hi, lo of X_v)
   if (G > 1) {
-    __syncthreads();
-    float* cmb = gsh;   // [G][NT*NT][4] (hi, lo of Q and X_v); fits in the chunk buffers
-    if (grp > 0) {
-      float* d = cmb + ((size_t)grp * NT * NT + tile) * 4;
-      d[0] = qh[0][0]; d[1] = ql[0][0]; d[2] = xh[0][0]; d[3] = xl[0][0];
-    }
-    __syncthreads();
-    if (grp == 0) {
-      for (int g2 = 1; g2 < G; ++g2) {
-        const float* d = cmb + ((size_t)g2 * NT * NT + tile) * 4;
-        two_sum_add(qh[0][0], ql[0][0], d[0]);
-        ql[0][0] += d[1];
-        two_sum_add(xh[0][0], xl[0][0], d[2]);
-        xl[0][0] += d[3];
+    float* cmb = gsh;
+#pragma unroll
+    for (int i = 0; i < TB; ++i) {
+      __syncthreads();
+      if (grp > 0) {
+#pragma unroll
+        for (int j = 0; j < TB; ++j) {
+          float* d = cmb + (((size_t)grp * NT * NT + tile) * TB + j) * 4;
+          d[0] = qh[i][j]; d[1] = ql[i][j]; d[2] = xh[i][j]; d[3] = xl[i][j];
+        }
+      }
+      __syncthreads();
+      if (grp == 0) {
+        for (int g2 = 1; g2 < G; ++g2) {
+#pragma unroll
+          for (int j = 0; j < TB; ++j) {
+            const float* d = cmb + (((size_t)g2 * NT * NT + tile) * TB + j) * 4;
+            two_sum_add(qh[i][j], ql[i][j], d[0]);
+            ql[i][j] += d[1];
+            two_sum_add(xh[i][j], xl[i][j], d[2]);
+            xl[i][j] += d[3];
+          }
+        }
       }
     }
   }
