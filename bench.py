@@ -40,6 +40,40 @@ def dist_env():
     return rank, world, local
 
 
+def init_ranks(world):
+    """One process per GPU: the process group of the replicas (NCCL on GPUs,
+    gloo when no GPU is visible, e.g. for host-side tests)."""
+    if world > 1:
+        import torch
+        import torch.distributed as tdist
+        tdist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as tdist
+        tdist.barrier()
+
+
+def max_over_ranks(x, world):
+    """The largest value of x over the ranks: a job's time is its slowest
+    replica's."""
+    if world == 1:
+        return float(x)
+    import torch
+    import torch.distributed as tdist
+    dev = "cuda" if tdist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([float(x)], dtype=torch.float64, device=dev)
+    tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def finish_ranks(world):
+    if world > 1:
+        import torch.distributed as tdist
+        tdist.destroy_process_group()
+
+
 def peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -225,9 +259,7 @@ def run_ours(args):
 
     rank, world, local = dist_env()
     torch.cuda.set_device(local)
-    if world > 1:
-        import torch.distributed as tdist
-        tdist.init_process_group("nccl")
+    init_ranks(world)
     wl = workload_by_name(args.workload)
     # replicas: every rank solves its own instance of the same workload
     inst = wl.instance(seed=wl.seed + rank, n=args.n_cols or None)
@@ -248,8 +280,7 @@ def run_ours(args):
     for _ in range(args.warmup):
         s.step(1)
     torch.cuda.synchronize()
-    if world > 1:
-        tdist.barrier()
+    barrier(world)
     clocks = ClockSampler(local)
     clocks.start()
     e0 = torch.cuda.Event(enable_timing=True)
@@ -261,11 +292,8 @@ def run_ours(args):
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1)
     clk = clocks.stop()
-    if world > 1:
-        t = torch.tensor([ms], device="cuda")
-        tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
-        ms = float(t.item())
-        tdist.barrier()
+    ms = max_over_ranks(ms, world)
+    barrier(world)
     ms_step = ms / args.steps
     value = world * 1e3 / ms_step
     launches_per_iter = {3: 9, 4: 1}.get(path_id, 8)   # kernels per iteration (graph nodes)
@@ -322,8 +350,7 @@ def run_ours(args):
                 "gpu_launches": 1 if path_id == 4 else launches_per_iter * args.steps,
                 "clocks": clk, "roofline": roofline, "e2e": e2e, "cpu_baseline": cpu}
         print(json.dumps(line), flush=True)
-    if world > 1:
-        tdist.destroy_process_group()
+    finish_ranks(world)
     return 0
 
 
@@ -347,7 +374,7 @@ def run_e2e(dcf, torch, inst, wl, U0, stream, args, world):
         s2.step(1)
         dcf.dcf_get_factors(s2.h, Uh)
     torch.cuda.synchronize()
-    e2e_s = (time.perf_counter() - t0) / e2e_steps
+    e2e_s = max_over_ranks((time.perf_counter() - t0) / e2e_steps, world)
     s2.close()
     return {"value": world / e2e_s, "unit": "iters/s", "h2d_bytes_per_step": 4 * m * n,
             "d2h_bytes_per_step": 4 * m * r}
@@ -394,9 +421,7 @@ def run_batched(args):
 
     rank, world, local = dist_env()
     torch.cuda.set_device(local)
-    if world > 1:
-        import torch.distributed as tdist
-        tdist.init_process_group("nccl")
+    init_ranks(world)
     shapes = synth.batched_instance_shapes(args.batch_count, seed=synth.SEED_BASE + 2 + rank)
     probs = [dict(m=sh["m"], n_i=sh["n_i"], r=sh["r"], rho=sh["rho"], lam=sh["lam"])
              for sh in shapes]
@@ -416,8 +441,7 @@ def run_batched(args):
     for _ in range(args.warmup):
         b.step(1)
     torch.cuda.synchronize()
-    if world > 1:
-        tdist.barrier()
+    barrier(world)
     clocks = ClockSampler(local)
     clocks.start()
     e0 = torch.cuda.Event(enable_timing=True)
@@ -429,10 +453,7 @@ def run_batched(args):
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1)
     clk = clocks.stop()
-    if world > 1:
-        t = torch.tensor([ms], device="cuda")
-        tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ms, world)
     ms_step = ms / args.steps
     hbm, peak_kind = peaks()
     achieved = alg / (ms_step * 1e-3) / 1e9
@@ -466,8 +487,7 @@ def run_batched(args):
                 "gpu_launches": launches * args.steps,
                 "e2e": None, "cpu_baseline": None}
         print(json.dumps(line), flush=True)
-    if world > 1:
-        tdist.destroy_process_group()
+    finish_ranks(world)
     return 0
 
 

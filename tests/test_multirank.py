@@ -1,0 +1,77 @@
+"""Host logic of bench.py at world size 2, on CPU with gloo: the replicas solve
+different instances, the reported time is the slowest rank's, and only rank 0
+runs the reference arm.  (The iteration itself does not shard: several GPUs run
+independent replicas, so no data-path collective exists to test.)"""
+import os
+import socket
+import subprocess
+import sys
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _worker(rank, world, port, q):
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank),
+                      WORLD_SIZE=str(world), LOCAL_RANK=str(rank))
+    sys.path.insert(0, ROOT)
+    import bench
+    bench.init_ranks(world)
+    got = bench.max_over_ranks(1.5 + rank, world)   # per-rank times 1.5 and 2.5
+    bench.barrier(world)
+    bench.finish_ranks(world)
+    q.put((rank, got))
+
+
+def test_time_is_max_over_two_gloo_ranks():
+    import torch.multiprocessing as mp
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_worker, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    try:
+        results = sorted(q.get(timeout=120) for _ in range(2))
+    finally:
+        for p in procs:
+            p.join(timeout=60)
+            if p.is_alive():
+                p.kill()
+    assert results == [(0, 2.5), (1, 2.5)]
+    assert all(p.exitcode == 0 for p in procs)
+
+
+def test_single_rank_needs_no_process_group():
+    sys.path.insert(0, ROOT)
+    import bench
+    bench.init_ranks(1)
+    assert bench.max_over_ranks(3.25, 1) == 3.25
+    bench.barrier(1)
+    bench.finish_ranks(1)
+
+
+def test_replicas_solve_distinct_instances():
+    sys.path.insert(0, ROOT)
+    from paper_2207_11669_gb300 import synth
+    wl = synth.workload_small()
+    a = wl.instance(seed=wl.seed + 0)
+    b = wl.instance(seed=wl.seed + 1)
+    assert a.M.shape == b.M.shape
+    assert not np.array_equal(a.M, b.M)
+
+
+def test_reference_arm_runs_on_rank_0_only():
+    env = dict(os.environ, RANK="1", WORLD_SIZE="2", LOCAL_RANK="1")
+    r = subprocess.run([sys.executable, "bench.py", "--impl", "reference", "--workload", "small",
+                        "--steps", "1", "--warmup", "1"], cwd=ROOT, env=env,
+                       capture_output=True, text=True, timeout=300)
+    assert r.returncode == 0, r.stderr
+    assert r.stdout.strip() == ""
