@@ -275,7 +275,9 @@ cudaError_t enqueue_batch_iteration(dcf_batch b, int cur, cudaStream_t s,
             e = launch_bpass(R, 2, b->dev, nullptr, 0, 0, c.p2, c.n_p2, c.grid_p2, cur, 0, s);
           break;
         case 3:   // Q = V'^T V', X_v partials
-          e = launch_bsmall(R, 2, b->dev, c.gv, c.n_gv, nullptr, grid_for(c.n_gv, 2 * S), cur, 0, s);
+          // one Gram CTA per SM at R >= 32 (its 4 x 4 register tiles), two below
+          e = launch_bsmall(R, 2, b->dev, c.gv, c.n_gv, nullptr,
+                            grid_for(c.n_gv, (R >= 32 ? 1 : 2) * S), cur, 0, s);
           break;
         case 4:   // (Q + rho I)^{-1}
           e = launch_bsmall(R, 3, b->dev, nullptr, ni, c.which, 0, cur, 1, s);

@@ -515,8 +515,18 @@ __device__ __forceinline__ void rows_block(const IterArgs& a, int64_t rb) {
     float hi = 0.f, lo = 0.f, uo = 0.f;
     if (rr < rows) {
       const int64_t off = row0 * R + i;
-      for (int s = 0; s < a.n_splits; ++s) two_sum_add(hi, lo, a.part_p[(int64_t)s * a.m * R + off]);
       uo = U[off];
+      // the partials in groups of 8 loads issued together, summed in order
+      if (a.n_splits == 1) hi = a.part_p[off];
+      else for (int s0 = 0; s0 < a.n_splits; s0 += 8) {
+        float v[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q)
+          v[q] = s0 + q < a.n_splits ? a.part_p[(int64_t)(s0 + q) * a.m * R + off] : 0.f;
+#pragma unroll
+        for (int q = 0; q < 8; ++q)
+          if (s0 + q < a.n_splits) two_sum_add(hi, lo, v[q]);
+      }
     }
     Ps[i] = hi + lo;
     Uo[i] = uo;
