@@ -296,10 +296,20 @@ __global__ void __launch_bounds__(256) k_reduce_parts(ReduceArgs a) {
     if (which < 2) {
       const float2* p = a.part[which];
       const int cnt = a.count[which];
-      for (int q = lane_p; q < a.nparts[which]; q += nsplit) {
-        const float2 v = p[(int64_t)q * cnt + idx];
-        two_sum_add(hi, lo, v.x);
-        lo += v.y;
+      const int np = a.nparts[which];
+      // groups of 8 loads issued together, summed in order
+      for (int q0 = lane_p; q0 < np; q0 += 8 * nsplit) {
+        float2 v[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          const int q = q0 + u * nsplit;
+          v[u] = q < np ? p[(int64_t)q * cnt + idx] : make_float2(0.f, 0.f);
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          two_sum_add(hi, lo, v[u].x);
+          lo += v[u].y;
+        }
       }
     } else {
       for (int q = lane_p; q < a.nparts[2]; q += nsplit) hs += a.hpart[q];
@@ -352,14 +362,26 @@ __device__ void tail_q(const ReduceArgs& a, double* A, float* F) {
     return;
   }
   const int nxt = a.copy ^ 1;
-  for (int i = threadIdx.x; i < R * R; i += blockDim.x) {
-    double q = __ldcg(a.out[0] + i);
-    sm->q[nxt][i] = q;
-    sm->xv[i] = __ldcg(a.out[1] + i);
-    int r = i / R, c = i % R;
-    double h = q + (r == c ? (double)a.rho : 0.0);
-    A[i] = h;
-    sm->qrho32[i] = (float)h;
+  // every load of the thread's entries first (they are independent), then the stores
+  for (int i0 = threadIdx.x; i0 < R * R; i0 += 4 * 256) {   // 4 entries per thread at a time
+    double qv[4], xv[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int i = i0 + u * 256;
+      qv[u] = i < R * R ? __ldcg(a.out[0] + i) : 0.0;
+      xv[u] = i < R * R ? __ldcg(a.out[1] + i) : 0.0;
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int i = i0 + u * 256;
+      if (i >= R * R) continue;
+      sm->q[nxt][i] = qv[u];
+      sm->xv[i] = xv[u];
+      const int r = i / R, c = i % R;
+      const double h = qv[u] + (r == c ? (double)a.rho : 0.0);
+      A[i] = h;
+      sm->qrho32[i] = (float)h;
+    }
   }
   if (threadIdx.x == 0) st->huber = __ldcg(a.out[2]);
   __syncthreads();
@@ -382,24 +404,42 @@ __device__ void tail_g(const ReduceArgs& a, double* A, float* F) {
   } else {
     const int cur = a.copy;
     tgt = cur ^ 1;
-    for (int i = threadIdx.x; i < R * R; i += blockDim.x) {
-      sm->gram[tgt][i] = __ldcg(a.out[0] + i);
-      sm->xu[i] = __ldcg(a.out[1] + i);
-    }
-    __syncthreads();
     // metrics: dL^2 = <G_t,Q_t> - 2 <X_u, X_v> + <G_{t-1}, Q_{t-1}>   (all r x r)
     // five FP64 sums in one reduction: per-thread partials, a shuffle tree
-    // per warp, then the per-warp values across lanes of warp 0
+    // per warp, then the per-warp values across lanes of warp 0.  Every load
+    // of the thread's entries is issued before any store or product; the new
+    // Gram also goes straight into A (G_t + rho I) for the inverse below.
     __shared__ double wsum[5][32];
     double v[5] = {0, 0, 0, 0, 0};
-    for (int i = threadIdx.x; i < R * R; i += blockDim.x) {
-      v[0] = fma(sm->gram[tgt][i], sm->q[tgt][i], v[0]);
-      v[1] = fma(sm->xu[i], sm->xv[i], v[1]);
-      v[2] = fma(sm->gram[cur][i], sm->q[cur][i], v[2]);
-    }
-    for (int i = threadIdx.x; i < R; i += blockDim.x) {
-      v[3] += sm->gram[cur][i * R + i];
-      v[4] += sm->q[cur][i * R + i];
+    for (int i0 = threadIdx.x; i0 < R * R; i0 += 4 * 256) {   // 4 entries per thread at a time
+      double gn[4], xu[4], qn[4], xv[4], go[4], qo[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int i = i0 + u * 256;
+        const bool in = i < R * R;
+        gn[u] = in ? __ldcg(a.out[0] + i) : 0.0;
+        xu[u] = in ? __ldcg(a.out[1] + i) : 0.0;
+        qn[u] = in ? sm->q[tgt][i] : 0.0;
+        xv[u] = in ? sm->xv[i] : 0.0;
+        go[u] = in ? sm->gram[cur][i] : 0.0;
+        qo[u] = in ? sm->q[cur][i] : 0.0;
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int i = i0 + u * 256;
+        if (i >= R * R) continue;
+        sm->gram[tgt][i] = gn[u];
+        sm->xu[i] = xu[u];
+        const int r = i / R, c = i % R;
+        A[i] = gn[u] + (r == c ? (double)a.rho : 0.0);
+        v[0] = fma(gn[u], qn[u], v[0]);
+        v[1] = fma(xu[u], xv[u], v[1]);
+        v[2] = fma(go[u], qo[u], v[2]);
+        if (r == c) {
+          v[3] += go[u];
+          v[4] += qo[u];
+        }
+      }
     }
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
 #pragma unroll
@@ -431,11 +471,12 @@ __device__ void tail_g(const ReduceArgs& a, double* A, float* F) {
     }
     __syncthreads();
   }
-  // (U^T U + rho I)^{-1} for the next V-step
-  for (int i = threadIdx.x; i < R * R; i += blockDim.x) {
-    int r = i / R, c = i % R;
-    A[i] = sm->gram[tgt][i] + (r == c ? (double)a.rho : 0.0);
-  }
+  // (U^T U + rho I)^{-1} for the next V-step (A already holds it after the metrics)
+  if (a.tail == TAIL_INIT_G)
+    for (int i = threadIdx.x; i < R * R; i += blockDim.x) {
+      const int r = i / R, c = i % R;
+      A[i] = sm->gram[tgt][i] + (r == c ? (double)a.rho : 0.0);
+    }
   __syncthreads();
   if (!all_finite(A, R * R)) {
     if (threadIdx.x == 0) st->status = 4;
