@@ -296,7 +296,7 @@ def run_ours(args):
     barrier(world)
     ms_step = ms / args.steps
     value = world * 1e3 / ms_step
-    launches_per_iter = {3: 9, 4: 1}.get(path_id, 7)   # kernels per iteration (graph nodes)
+    launches_per_iter = {1: 7, 2: 6, 3: 8, 4: 1}[path_id]   # kernels per iteration (graph nodes)
 
     # per-kernel phases, CUDA events on the launch stream, same workload
     phases = dcf.dcf_profile_step(s.h, max(3, min(args.steps, 10)))

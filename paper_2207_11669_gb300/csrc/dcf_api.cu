@@ -185,9 +185,8 @@ cudaError_t enqueue_fused_iteration(dcf_handle h, int cur, cudaStream_t s, cudaE
     return cudaSuccess;
   };
   if ((e = launch_fused_prep(h->R, h->U[cur], h->sm, h->st, h->m, h->nslabs, (float)h->rho,
-                             h->vmax + cur, h->vmax + nxt, h->img, h->scales, h->zmat, s)) !=
-          cudaSuccess ||
-      (e = launch_rowmat(h->R, h->V[cur], h->zmat, h->n, h->W_vz, h->st, s)) != cudaSuccess ||
+                             h->vmax + cur, h->vmax + nxt, h->img, h->scales, h->zmat,
+                             h->V[cur], h->n, h->W_vz, s)) != cudaSuccess ||
       (e = mark()) != cudaSuccess)
     return e;
   FusedArgs fa{};
@@ -238,9 +237,8 @@ cudaError_t enqueue_tc2_iteration(dcf_handle h, int cur, cudaStream_t s, cudaEve
     return cudaSuccess;
   };
   if ((e = launch_fused_prep(h->R, h->U[cur], h->sm, h->st, h->m, h->nslabs, (float)h->rho,
-                             h->vmax + cur, h->vmax + nxt, h->img, h->scales, h->zmat, s)) !=
-          cudaSuccess ||
-      (e = launch_rowmat(h->R, h->V[cur], h->zmat, h->n, h->W_vz, h->st, s)) != cudaSuccess ||
+                             h->vmax + cur, h->vmax + nxt, h->img, h->scales, h->zmat,
+                             h->V[cur], h->n, h->W_vz, s)) != cudaSuccess ||
       (e = mark()) != cudaSuccess)
     return e;
   Tc2Args ta{};

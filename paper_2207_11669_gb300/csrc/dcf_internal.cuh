@@ -237,7 +237,7 @@ int fused_make_tmap(void* tmap_out, const float* M, int64_t m, int64_t n);
 cudaError_t launch_fused_prep(int R, const float* U, const Smalls* sm, const DevState* st,
                               int64_t m, int nslabs, float rho, const unsigned int* vmax_in,
                               unsigned int* vmax_reset, uint8_t* img, float* scales, float* zmat,
-                              cudaStream_t s);
+                              const float* Vold, int64_t n, float* VZ, cudaStream_t s);
 cudaError_t launch_absmax(const float* x, int64_t count, unsigned int* out, cudaStream_t s);
 
 // Whole solve of a small problem in one CTA (k_solve_small.cu), R = 8 or 16,
@@ -283,7 +283,5 @@ cudaError_t launch_tc2_vreduce(int R, const float* ypart, int nslabs, const floa
 // The image preparation of the tensor-core paths also takes R = 64 (dynamic
 // shared memory above 48 KB): call once per process before the first launch.
 cudaError_t fused_prep_prepare();
-cudaError_t launch_rowmat(int R, const float* in, const float* zmat, int64_t n, float* out,
-                          const DevState* st, cudaStream_t s);
 
 }  // namespace dcf

@@ -13,9 +13,9 @@
 //                                   R feeds the soft-threshold support)
 //   GEMM2  Y  = C_s^T W_hi + C_s^T W_lo   (C/lambda in [-1,1] stored once in fp16)
 //   GEMM3  P_C += C_s V'_hi^T + C_s V'_lo^T
-// V Z is precomputed (k_rowmat) and added by the reducers; V^T V' (= V_{t-1}^T V_t,
-// also a metric) closes P in the r x r algebra and, with Q = V'^T V', comes
-// from the Gram kernels after the pass.
+// V Z is precomputed (by the preparation kernel) and added by the reducers;
+// V^T V' (= V_{t-1}^T V_t, also a metric) closes P in the r x r algebra and,
+// with Q = V'^T V', comes from the Gram kernels after the pass.
 //
 // The epilogue writes each C tile twice: into shared memory for GEMM2 (freed
 // as soon as GEMM2 completes) and into tensor memory as GEMM3's A operand
@@ -720,25 +720,13 @@ __device__ __forceinline__ void fused_prep_slab(const float* __restrict__ U, con
   }
   if (slab == 0) {
     for (int i = tid; i < R * R; i += 256)
-      zmat[i] = ((i / R) == (i % R) ? 1.f : 0.f) - rho * gi[i];
+      zmat[i] = fmaf(-rho, gi[i], (i / R) == (i % R) ? 1.f : 0.f);
     if (tid == 0) {
       const float vm = __uint_as_float(*vmax_in);
       scales[2 * nslabs] = pow2_scale_dev(vm, 1024.f);
       *vmax_reset = 0u;
     }
   }
-}
-
-template <int R>
-__global__ void __launch_bounds__(256) k_fused_prep(const float* __restrict__ U,
-                                                    const Smalls* sm, const DevState* st,
-                                                    int64_t m, int nslabs, float rho,
-                                                    const unsigned int* vmax_in,
-                                                    unsigned int* vmax_reset, uint8_t* img,
-                                                    float* scales, float* zmat) {
-  if (st->stop) return;
-  fused_prep_slab<R>(U, sm, m, nslabs, rho, vmax_in, vmax_reset, img, scales, zmat,
-                     (int)blockIdx.x);
 }
 
 // Batches: item (instance, slab), a persistent grid walks the list.
@@ -760,13 +748,20 @@ __global__ void __launch_bounds__(256) k_bfused_prep(const BInst* __restrict__ i
 // block blk of 256 (row, column group of 8) entries (block-wide).  The row's
 // R inputs are fetched with vector loads before any arithmetic, so that they
 // are in flight together.
-template <int R>
+// kFromGinv: zsrc is G^{-1} and Z = I - rho G^{-1} is formed here (as the
+// preparation forms zmat); otherwise zsrc is Z itself.
+template <int R, bool kFromGinv = false>
 __device__ __forceinline__ void rowmat_block(const float* __restrict__ in,
-                                             const float* __restrict__ zmat, int64_t n,
+                                             const float* __restrict__ zsrc, float rho, int64_t n,
                                              float* __restrict__ out, int64_t blk) {
   __shared__ __align__(16) float Z[R * R];
-  for (int i = threadIdx.x; i < R * R / 4; i += 256)
-    reinterpret_cast<float4*>(Z)[i] = reinterpret_cast<const float4*>(zmat)[i];
+  if constexpr (kFromGinv) {
+    for (int i = threadIdx.x; i < R * R; i += 256)
+      Z[i] = fmaf(-rho, zsrc[i], (i / R) == (i % R) ? 1.f : 0.f);
+  } else {
+    for (int i = threadIdx.x; i < R * R / 4; i += 256)
+      reinterpret_cast<float4*>(Z)[i] = reinterpret_cast<const float4*>(zsrc)[i];
+  }
   __syncthreads();
   const int64_t idx = blk * 256 + threadIdx.x;   // (row, column group of 8)
   const int64_t row = idx / (R / 8);
@@ -800,12 +795,24 @@ __device__ __forceinline__ void rowmat_block(const float* __restrict__ in,
   dst[1] = make_float4(acc[4], acc[5], acc[6], acc[7]);
 }
 
+// The per-iteration preparation in one launch: blocks [0, nslabs) prepare the
+// U/W slabs (fused_prep_slab), the other blocks form V_old Z for 256 (row,
+// column group of 8) entries each, with Z = I - rho G^{-1} built in place.
 template <int R>
-__global__ void __launch_bounds__(256) k_rowmat(const float* __restrict__ in,
-                                                const float* __restrict__ zmat, int64_t n,
-                                                float* __restrict__ out, const DevState* st) {
+__global__ void __launch_bounds__(256) k_fused_prep(const float* __restrict__ U,
+                                                    const Smalls* sm, const DevState* st,
+                                                    int64_t m, int nslabs, float rho,
+                                                    const unsigned int* vmax_in,
+                                                    unsigned int* vmax_reset, uint8_t* img,
+                                                    float* scales, float* zmat,
+                                                    const float* __restrict__ Vold, int64_t n,
+                                                    float* __restrict__ VZ) {
   if (st->stop) return;
-  rowmat_block<R>(in, zmat, n, out, blockIdx.x);
+  if ((int)blockIdx.x < nslabs)
+    fused_prep_slab<R>(U, sm, m, nslabs, rho, vmax_in, vmax_reset, img, scales, zmat,
+                       (int)blockIdx.x);
+  else
+    rowmat_block<R, true>(Vold, sm->ginv32, rho, n, VZ, (int64_t)blockIdx.x - nslabs);
 }
 
 // Batches: item (instance, block of 256 entries of V_old Z).
@@ -818,7 +825,7 @@ __global__ void __launch_bounds__(256) k_browmat(const BInst* __restrict__ insts
     const BInst& I = insts[w.inst];
     if (I.st->stop) continue;            // uniform over the block
     __syncthreads();                     // the previous item's shared Z is free
-    rowmat_block<R>(I.V[cur], I.zmat, I.n, I.VZ, w.a);
+    rowmat_block<R>(I.V[cur], I.zmat, 0.f, I.n, I.VZ, w.a);
   }
 }
 
@@ -835,15 +842,6 @@ cudaError_t launch_bfused_small(int R, int kind, const BInst* insts, const BItem
   return cudaGetLastError();
 }
 
-cudaError_t launch_rowmat(int R, const float* in, const float* zmat, int64_t n, float* out,
-                          const DevState* st, cudaStream_t s) {
-  const int64_t items = n * (R / 8);
-  const unsigned grid = (unsigned)((items + 255) / 256);
-  if (R == 16) k_rowmat<16><<<grid, 256, 0, s>>>(in, zmat, n, out, st);
-  else if (R == 32) k_rowmat<32><<<grid, 256, 0, s>>>(in, zmat, n, out, st);
-  else k_rowmat<64><<<grid, 256, 0, s>>>(in, zmat, n, out, st);
-  return cudaGetLastError();
-}
 
 __global__ void k_absmax(const float* x, int64_t count, unsigned int* out) {
   float mx = 0.f;
@@ -940,16 +938,21 @@ int fused_make_tmap(void* tmap_out, const float* M, int64_t m, int64_t n) {
 cudaError_t launch_fused_prep(int R, const float* U, const Smalls* sm, const DevState* st,
                               int64_t m, int nslabs, float rho, const unsigned int* vmax_in,
                               unsigned int* vmax_reset, uint8_t* img, float* scales, float* zmat,
-                              cudaStream_t s) {
+                              const float* Vold, int64_t n, float* VZ, cudaStream_t s) {
+  const int64_t zblocks = (n * (R / 8) + 255) / 256;    // V_old Z blocks after the slabs
+  const unsigned grid = (unsigned)(nslabs + zblocks);
   if (R == 16)
-    k_fused_prep<16><<<nslabs, 256, prep_smem<16>(), s>>>(U, sm, st, m, nslabs, rho, vmax_in,
-                                                          vmax_reset, img, scales, zmat);
+    k_fused_prep<16><<<grid, 256, prep_smem<16>(), s>>>(U, sm, st, m, nslabs, rho, vmax_in,
+                                                        vmax_reset, img, scales, zmat, Vold, n,
+                                                        VZ);
   else if (R == 32)
-    k_fused_prep<32><<<nslabs, 256, prep_smem<32>(), s>>>(U, sm, st, m, nslabs, rho, vmax_in,
-                                                          vmax_reset, img, scales, zmat);
+    k_fused_prep<32><<<grid, 256, prep_smem<32>(), s>>>(U, sm, st, m, nslabs, rho, vmax_in,
+                                                        vmax_reset, img, scales, zmat, Vold, n,
+                                                        VZ);
   else
-    k_fused_prep<64><<<nslabs, 256, prep_smem<64>(), s>>>(U, sm, st, m, nslabs, rho, vmax_in,
-                                                          vmax_reset, img, scales, zmat);
+    k_fused_prep<64><<<grid, 256, prep_smem<64>(), s>>>(U, sm, st, m, nslabs, rho, vmax_in,
+                                                        vmax_reset, img, scales, zmat, Vold, n,
+                                                        VZ);
   return cudaGetLastError();
 }
 
