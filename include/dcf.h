@@ -136,6 +136,24 @@ dcf_status dcf_load_blocks(dcf_handle h, const float* const* M_i, const int64_t*
 dcf_status dcf_reload_blocks(dcf_handle h, const float* const* M_i, const int64_t* ld_i,
                              int where);
 
+/* dcf_reload_blocks without waiting: the copy and its NaN/Inf check are
+ * enqueued on an internal stream into a second M buffer and the call returns
+ * at once.  The next call that iterates (dcf_step, dcf_solve, the learned
+ * network's forward pass, dcf_load_init) waits for them on the device and
+ * reads the new values, so the copy of the next step's M overlaps the
+ * iterations already enqueued; calls that only read factors or statistics do
+ * not wait for it, and dcf_get_LS keeps reading the M of the last iteration.
+ * The blocks must stay valid and unchanged until the next iteration's results
+ * have been read back (e.g. by dcf_get_factors).  A second call before the
+ * next step replaces the first; dcf_load_blocks and dcf_reload_blocks discard
+ * a pending one.  When the check finds a NaN or Inf, the next iteration stops
+ * the solve: the iterations do nothing and dcf_get_stats reports
+ * DCF_ENONFINITE until dcf_load_blocks.  DCF_ESTATE and DCF_EINVAL as for
+ * dcf_reload_blocks.  The second buffer (m n floats) is allocated on the first
+ * call. */
+dcf_status dcf_reload_blocks_async(dcf_handle h, const float* const* M_i, const int64_t* ld_i,
+                                   int where);
+
 /* Set the starting point U0 (m x r) and V0_i (n_i x r).  Without this call
  * dcf_step/dcf_solve start from U0 ~ N(0, 1/m) (counter-based Philox4x32-10,
  * keyed by params.seed) and V0 = M^T U0 (U0^T U0 + rho I)^{-1}, the V-step

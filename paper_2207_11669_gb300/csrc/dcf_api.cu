@@ -321,7 +321,7 @@ cudaError_t enqueue_iteration(dcf_handle h, int cur, cudaStream_t s, cudaEvent_t
 
 dcf_status build_graphs(dcf_handle h) {
   for (int p = 0; p < 2; ++p) {
-    if (h->graph[p]) continue;
+    if (h->graph[h->mcur][p]) continue;
     cudaGraph_t g = nullptr;
     CK(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal), "begin capture");
     cudaError_t e = enqueue_iteration(h, p, h->stream, nullptr);
@@ -331,10 +331,35 @@ dcf_status build_graphs(dcf_handle h) {
       return cuda_fail(h, e, "capture iteration");
     }
     CK(e2, "end capture");
-    cudaError_t e3 = cudaGraphInstantiate(&h->graph[p], g, 0);
+    cudaError_t e3 = cudaGraphInstantiate(&h->graph[h->mcur][p], g, 0);
     cudaGraphDestroy(g);
     CK(e3, "instantiate graph");
   }
+  return DCF_OK;
+}
+
+// A pending asynchronous reload becomes the M that work enqueued from now on
+// reads: the internal stream waits for its copy and check, a failed check
+// stops the solve (k_apply_mflag), and the buffers swap.  Called by the entry
+// points that read M (through ensure_init, and the loads); calls that only
+// read factors or statistics do not wait for a pending copy.
+dcf_status apply_pending(dcf_handle h) {
+  if (h->pend < 0) return DCF_OK;
+  CK(cudaStreamWaitEvent(h->stream, h->ev_copy, 0), "wait");
+  CK(launch_apply_mflag(h->mflag + h->pend, h->st, h->stream), "apply reload check");
+  h->mcur = h->pend;
+  h->M = h->Mbuf[h->mcur];
+  std::memcpy(h->tmap, h->tmaps[h->mcur], sizeof(h->tmap));
+  h->pend = -1;
+  return DCF_OK;
+}
+
+// A load or a synchronous reload supersedes a pending asynchronous reload:
+// its copy is waited for and its buffer stays out of use.
+static dcf_status drop_pending(dcf_handle h) {
+  if (h->pend < 0) return DCF_OK;
+  CK(cudaStreamSynchronize(h->side), "sync");
+  h->pend = -1;
   return DCF_OK;
 }
 
@@ -347,6 +372,7 @@ dcf_status begin_work(dcf_handle h) {
 }
 
 dcf_status end_work(dcf_handle h) {
+  CK(cudaEventRecord(h->ev_used[h->mcur], h->stream), "record");
   CK(cudaEventRecord(h->ev_out, h->stream), "record");
   CK(cudaStreamWaitEvent(h->user_stream, h->ev_out, 0), "wait");
   return DCF_OK;
@@ -411,6 +437,8 @@ dcf_status finish_init(dcf_handle h, bool have_v0) {
 
 dcf_status ensure_init(dcf_handle h) {
   if (!h->loaded) return fail(h, DCF_ESTATE, "dcf_load_blocks has not been called");
+  dcf_status pst = apply_pending(h);
+  if (pst != DCF_OK) return pst;
   if (h->initialized) return DCF_OK;
   CK(launch_philox_u0(h->U[0], h->m, h->r, h->R, h->seed, h->stream), "philox U0");
   return finish_init(h, false);
@@ -481,9 +509,14 @@ extern "C" dcf_status dcf_create(const dcf_params* p, dcf_handle* out) {
   if (h->num_sms <= 0) h->num_sms = 1;
   if (cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking) != cudaSuccess ||
       cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&h->side2, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&h->ev_side2, cudaEventDisableTiming) != cudaSuccess ||
       cudaEventCreateWithFlags(&h->ev_in, cudaEventDisableTiming) != cudaSuccess ||
       cudaEventCreateWithFlags(&h->ev_out, cudaEventDisableTiming) != cudaSuccess ||
-      cudaEventCreateWithFlags(&h->ev_side, cudaEventDisableTiming) != cudaSuccess) {
+      cudaEventCreateWithFlags(&h->ev_side, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&h->ev_copy, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&h->ev_used[0], cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&h->ev_used[1], cudaEventDisableTiming) != cudaSuccess) {
     dcf_destroy(h);
     return DCF_ECUDA;
   }
@@ -607,6 +640,7 @@ extern "C" dcf_status dcf_create(const dcf_params* p, dcf_handle* out) {
   h->st = (DevState*)A(sizeof(DevState));
   h->counters = (unsigned int*)A(4 * sizeof(unsigned int));
   h->flag = (int*)A(sizeof(int));
+  h->mflag = (int*)A(2 * sizeof(int));
   h->kerr = (int*)A(sizeof(int));
   if (h->path == 2) {
     const size_t grid = (size_t)h->cs * h->nclusters;
@@ -661,29 +695,50 @@ extern "C" dcf_status dcf_set_stream(dcf_handle h, void* stream) {
 namespace dcf {
 namespace api {
 
-// Copy the blocks into the handle's own M buffer and check them for NaN/Inf;
-// returns after both have completed (*nonfinite set when a value failed).
-// Block i is checked on the side stream while block i + 1 is being copied.
-static dcf_status copy_blocks_checked(dcf_handle h, const float* const* M_i, const int64_t* ld_i,
-                                      int where, bool* nonfinite) {
+// Enqueue the copy of the blocks into dst on stream cs and their NaN/Inf check
+// into *flag on stream ks: block i is checked while block i + 1 is copied,
+// and cs waits for the last check at the end.
+static dcf_status enqueue_copy_check(dcf_handle h, float* dst, const float* const* M_i,
+                                     const int64_t* ld_i, int where, int* flag, cudaStream_t cs,
+                                     cudaStream_t ks, cudaEvent_t ev) {
   cudaMemcpyKind kind = where == 0 ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
-  CK(cudaMemsetAsync(h->flag, 0, sizeof(int), h->stream), "memset");
+  CK(cudaMemsetAsync(flag, 0, sizeof(int), cs), "memset");
   for (int i = 0; i < h->E; ++i) {
     int64_t ld = ld_i ? ld_i[i] : h->m;
-    float* dst = h->M + h->c_i[i] * h->m;
-    CK(cudaMemcpy2DAsync(dst, h->m * sizeof(float), M_i[i], ld * sizeof(float),
-                         h->m * sizeof(float), h->n_i[i], kind, h->stream),
+    float* d = dst + h->c_i[i] * h->m;
+    CK(cudaMemcpy2DAsync(d, h->m * sizeof(float), M_i[i], ld * sizeof(float),
+                         h->m * sizeof(float), h->n_i[i], kind, cs),
        "copy block");
-    CK(cudaEventRecord(h->ev_side, h->stream), "record");
-    CK(cudaStreamWaitEvent(h->side, h->ev_side, 0), "wait");
-    CK(launch_check_finite(dst, h->m * h->n_i[i], h->flag, h->side), "check block");
+    CK(cudaEventRecord(ev, cs), "record");
+    CK(cudaStreamWaitEvent(ks, ev, 0), "wait");
+    CK(launch_check_finite(d, h->m * h->n_i[i], flag, ks), "check block");
   }
-  CK(cudaEventRecord(h->ev_side, h->side), "record");
-  CK(cudaStreamWaitEvent(h->stream, h->ev_side, 0), "wait");
+  CK(cudaEventRecord(ev, ks), "record");
+  CK(cudaStreamWaitEvent(cs, ev, 0), "wait");
+  return DCF_OK;
+}
+
+// Copy the blocks into the buffer in use (h->M) and check them; returns after
+// both have completed (*nonfinite set when a value failed).
+static dcf_status copy_blocks_checked(dcf_handle h, const float* const* M_i, const int64_t* ld_i,
+                                      int where, bool* nonfinite) {
+  dcf_status st = enqueue_copy_check(h, h->M, M_i, ld_i, where, h->flag, h->stream, h->side,
+                                     h->ev_side);
+  if (st != DCF_OK) return st;
   int flag = 0;
   CK(cudaMemcpyAsync(&flag, h->flag, sizeof(int), cudaMemcpyDeviceToHost, h->stream), "flag");
   CK(cudaStreamSynchronize(h->stream), "sync");
   *nonfinite = flag != 0;
+  return DCF_OK;
+}
+
+// Own buffer b of M (allocated on first use) and its tensor map.
+static dcf_status ensure_mbuf(dcf_handle h, int b) {
+  if (h->Mbuf[b]) return DCF_OK;
+  h->Mbuf[b] = (float*)dev_alloc(h, (size_t)h->m * h->n * sizeof(float));
+  if (!h->Mbuf[b]) return fail(h, DCF_ENOMEM, "cannot allocate M");
+  if ((h->path == 2 || h->path == 3) && fused_make_tmap(h->tmaps[b], h->Mbuf[b], h->m, h->n) != 0)
+    return fail(h, DCF_ECUDA, "cuTensorMapEncodeTiled failed for M");
   return DCF_OK;
 }
 
@@ -708,6 +763,7 @@ extern "C" dcf_status dcf_load_blocks(dcf_handle h, const float* const* M_i, con
   if (st != DCF_OK) return st;
   st = begin_work(h);
   if (st != DCF_OK) return st;
+  if ((st = drop_pending(h)) != DCF_OK) return st;
   bool contiguous = where == 1;
   for (int i = 0; i < h->E && contiguous; ++i) {
     if (ld_i && ld_i[i] != h->m) contiguous = false;
@@ -726,21 +782,26 @@ extern "C" dcf_status dcf_load_blocks(dcf_handle h, const float* const* M_i, con
     CK(cudaStreamSynchronize(h->stream), "sync");
     nonfinite = flag != 0;
   } else {
-    if (!h->M || h->M_borrowed) {
-      h->M = (float*)dev_alloc(h, (size_t)h->m * h->n * sizeof(float));
-      if (!h->M) return fail(h, DCF_ENOMEM, "cannot allocate M");
-      h->M_borrowed = false;
-    }
+    if ((st = ensure_mbuf(h, h->mcur)) != DCF_OK) return st;
+    h->M = h->Mbuf[h->mcur];
+    h->M_borrowed = false;
     st = copy_blocks_checked(h, M_i, ld_i, where, &nonfinite);
     if (st != DCF_OK) return st;
   }
   if (nonfinite) return fail(h, DCF_ENONFINITE, "M contains NaN or Inf");
-  if ((h->path == 2 || h->path == 3) && fused_make_tmap(h->tmap, h->M, h->m, h->n) != 0)
-    return fail(h, DCF_ECUDA, "cuTensorMapEncodeTiled failed for M");
+  if (h->path == 2 || h->path == 3) {
+    if (h->M_borrowed) {
+      if (fused_make_tmap(h->tmap, h->M, h->m, h->n) != 0)
+        return fail(h, DCF_ECUDA, "cuTensorMapEncodeTiled failed for M");
+    } else {
+      std::memcpy(h->tmap, h->tmaps[h->mcur], sizeof(h->tmap));
+    }
+  }
   h->loaded = true;
   h->initialized = false;
-  for (int p = 0; p < 2; ++p)
-    if (h->graph[p]) { cudaGraphExecDestroy(h->graph[p]); h->graph[p] = nullptr; }
+  for (int b = 0; b < 2; ++b)
+    for (int p = 0; p < 2; ++p)
+      if (h->graph[b][p]) { cudaGraphExecDestroy(h->graph[b][p]); h->graph[b][p] = nullptr; }
   return end_work(h);
 }
 
@@ -754,6 +815,7 @@ extern "C" dcf_status dcf_reload_blocks(dcf_handle h, const float* const* M_i,
   if (st != DCF_OK) return st;
   st = begin_work(h);
   if (st != DCF_OK) return st;
+  if ((st = drop_pending(h)) != DCF_OK) return st;
   bool nonfinite = false;
   st = copy_blocks_checked(h, M_i, ld_i, where, &nonfinite);
   if (st != DCF_OK) return st;
@@ -761,6 +823,32 @@ extern "C" dcf_status dcf_reload_blocks(dcf_handle h, const float* const* M_i,
     h->loaded = false;   // M now holds the rejected values: no step may run on them
     return fail(h, DCF_ENONFINITE, "M contains NaN or Inf");
   }
+  return end_work(h);
+}
+
+extern "C" dcf_status dcf_reload_blocks_async(dcf_handle h, const float* const* M_i,
+                                              const int64_t* ld_i, int where) {
+  if (!h) return DCF_EINVAL;
+  if (!h->loaded) return fail(h, DCF_ESTATE, "dcf_load_blocks has not been called");
+  if (h->M_borrowed)
+    return fail(h, DCF_ESTATE, "M is borrowed; write the new values into the borrowed matrix");
+  dcf_status st = check_block_args(h, M_i, ld_i, where);
+  if (st != DCF_OK) return st;
+  st = begin_work(h);
+  if (st != DCF_OK) return st;
+  // a pending reload's buffer is overwritten (after its copy: same stream)
+  const int tgt = h->pend >= 0 ? h->pend : 1 - h->mcur;
+  if ((st = ensure_mbuf(h, tgt)) != DCF_OK) return st;
+  // after every enqueued iteration that reads the target buffer, and for
+  // device sources after the caller's stream (which may produce them; it is
+  // itself behind the enqueued iterations, so host sources skip this wait)
+  if (where == 1) CK(cudaStreamWaitEvent(h->side, h->ev_in, 0), "wait");
+  CK(cudaStreamWaitEvent(h->side, h->ev_used[tgt], 0), "wait");
+  st = enqueue_copy_check(h, h->Mbuf[tgt], M_i, ld_i, where, h->mflag + tgt, h->side, h->side2,
+                          h->ev_side2);
+  if (st != DCF_OK) return st;
+  CK(cudaEventRecord(h->ev_copy, h->side), "record");
+  h->pend = tgt;
   return end_work(h);
 }
 
@@ -772,6 +860,7 @@ extern "C" dcf_status dcf_load_init(dcf_handle h, const float* U0, const float* 
   if (where != 0 && where != 1) return fail(h, DCF_EINVAL, "where must be 0 or 1");
   dcf_status st = begin_work(h);
   if (st != DCF_OK) return st;
+  if ((st = apply_pending(h)) != DCF_OK) return st;   // the start-point sweep reads M
   cudaMemcpyKind kind = where == 0 ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
   CK(cudaMemsetAsync(h->U[0], 0, h->m * h->R * 4, h->stream), "memset");
   CK(cudaMemcpy2DAsync(h->U[0], h->R * 4, U0, h->r * 4, h->r * 4, h->m, kind, h->stream), "copy U0");
@@ -804,7 +893,7 @@ extern "C" dcf_status dcf_step(dcf_handle h, int n_steps) {
   }
   if ((st = build_graphs(h)) != DCF_OK) return st;
   for (int i = 0; i < n_steps; ++i) {
-    CK(cudaGraphLaunch(h->graph[h->host_iter & 1], h->stream), "graph launch");
+    CK(cudaGraphLaunch(h->graph[h->mcur][h->host_iter & 1], h->stream), "graph launch");
     h->host_iter++;
   }
   return end_work(h);
@@ -830,7 +919,7 @@ extern "C" dcf_status dcf_solve(dcf_handle h, int* iters_out, double* final_dL_r
   while (done < h->max_iter) {
     int nb = std::min(batch, h->max_iter - done);
     for (int i = 0; i < nb; ++i) {
-      CK(cudaGraphLaunch(h->graph[h->host_iter & 1], h->stream), "graph launch");
+      CK(cudaGraphLaunch(h->graph[h->mcur][h->host_iter & 1], h->stream), "graph launch");
       h->host_iter++;
     }
     done += nb;
@@ -1027,13 +1116,20 @@ extern "C" void dcf_destroy(dcf_handle h) {
   if (!h) return;
   if (h->stream) cudaStreamSynchronize(h->stream);
   free_unrolled(h);
-  for (int p = 0; p < 2; ++p)
-    if (h->graph[p]) cudaGraphExecDestroy(h->graph[p]);
+  if (h->side) cudaStreamSynchronize(h->side);
+  for (int b = 0; b < 2; ++b)
+    for (int p = 0; p < 2; ++p)
+      if (h->graph[b][p]) cudaGraphExecDestroy(h->graph[b][p]);
   dev_free_all(h);
   if (h->ev_in) cudaEventDestroy(h->ev_in);
   if (h->ev_out) cudaEventDestroy(h->ev_out);
   if (h->ev_side) cudaEventDestroy(h->ev_side);
+  if (h->ev_copy) cudaEventDestroy(h->ev_copy);
+  if (h->ev_side2) cudaEventDestroy(h->ev_side2);
+  for (int b = 0; b < 2; ++b)
+    if (h->ev_used[b]) cudaEventDestroy(h->ev_used[b]);
   if (h->stream) cudaStreamDestroy(h->stream);
   if (h->side) cudaStreamDestroy(h->side);
+  if (h->side2) cudaStreamDestroy(h->side2);
   delete h;
 }

@@ -29,10 +29,21 @@ struct dcf_handle_s {
   int device = 0, num_sms = 0;
   cudaStream_t user_stream = nullptr;
   cudaStream_t stream = nullptr;     // internal capture/launch stream
-  cudaStream_t side = nullptr;       // NaN/Inf checks of copied blocks, behind the copies
-  cudaEvent_t ev_in = nullptr, ev_out = nullptr, ev_side = nullptr;
-  float* M = nullptr;
+  cudaStream_t side = nullptr;       // NaN/Inf checks of copied blocks, behind the copies;
+                                     // the copies of asynchronous reloads
+  cudaStream_t side2 = nullptr;      // the checks of asynchronous reloads
+  cudaEvent_t ev_in = nullptr, ev_out = nullptr, ev_side = nullptr, ev_side2 = nullptr;
+  float* M = nullptr;                 // the matrix the iterations read (Mbuf[mcur] unless borrowed)
   bool M_borrowed = false;
+  // own copies of M, two for asynchronous reloads (the next step's M is copied
+  // while the current one is iterated on)
+  float* Mbuf[2] = {nullptr, nullptr};
+  int mcur = 0;                       // buffer in use
+  int pend = -1;                      // buffer of a pending asynchronous reload, -1: none
+  int* mflag = nullptr;               // [2]: a NaN/Inf was found in Mbuf[b] by its last reload
+  cudaEvent_t ev_copy = nullptr;      // the pending reload's copy and check are done (side)
+  cudaEvent_t ev_used[2] = {nullptr, nullptr};   // last enqueued work that may read Mbuf[b]
+  alignas(64) unsigned char tmaps[2][128];        // tensor maps over Mbuf[0], Mbuf[1]
   float* U[2] = {nullptr, nullptr};
   float* V[2] = {nullptr, nullptr};
   float* W = nullptr;
@@ -71,7 +82,7 @@ struct dcf_handle_s {
   // state
   bool loaded = false, initialized = false;
   int host_iter = 0;                  // iterations enqueued (mirrors DevState::iter)
-  cudaGraphExec_t graph[2] = {nullptr, nullptr};
+  cudaGraphExec_t graph[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};   // [buffer][parity]
   float alpha = 1.0f;                 // relaxation of the U-step (learned network)
   float* ustar_out = nullptr;         // when set, the U-step also stores U* here
   UnrolledState* unrolled = nullptr;  // checkpoints and buffers of the learned network
@@ -92,6 +103,7 @@ dcf_status begin_work(dcf_handle h);
 dcf_status end_work(dcf_handle h);
 dcf_status read_state(dcf_handle h, DevState* out);
 dcf_status ensure_init(dcf_handle h);
+dcf_status apply_pending(dcf_handle h);
 dcf_status set_state_fields(dcf_handle h, int solve_mode, double tol);
 void free_unrolled(dcf_handle h);
 }  // namespace api

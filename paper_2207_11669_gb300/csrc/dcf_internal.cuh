@@ -201,6 +201,7 @@ cudaError_t launch_materialize(const float* M, int64_t m, int64_t c0, int64_t ni
 cudaError_t launch_philox_u0(float* U, int64_t m, int r, int R, uint64_t seed,
                              cudaStream_t s);
 cudaError_t launch_check_finite(const float* x, int64_t count, int* flag, cudaStream_t s);
+cudaError_t launch_apply_mflag(const int* flag, DevState* st, cudaStream_t s);
 
 int pick_R(int r);
 

@@ -804,6 +804,15 @@ __global__ void k_philox_u0(float* U, int64_t m, int r, int R, uint64_t seed) {
   U[idx] = z * rsqrtf((float)m);
 }
 
+// A reloaded M that failed its NaN/Inf check ends the solve before any step
+// reads it: status DCF_ENONFINITE, and the stop flag every kernel tests.
+__global__ void k_apply_mflag(const int* flag, DevState* st) {
+  if (*flag) {
+    st->status = 4;   // DCF_ENONFINITE
+    st->stop = 1;
+  }
+}
+
 __global__ void k_check_finite(const float* x, int64_t count, int* flag) {
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   int64_t stride = (int64_t)gridDim.x * blockDim.x;
@@ -970,6 +979,11 @@ cudaError_t launch_reduce_plain(const float2* part, int nparts, int count, doubl
 cudaError_t launch_philox_u0(float* U, int64_t m, int r, int R, uint64_t seed, cudaStream_t s) {
   int64_t tot = m * R;
   k_philox_u0<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(U, m, r, R, seed);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_apply_mflag(const int* flag, DevState* st, cudaStream_t s) {
+  k_apply_mflag<<<1, 1, 0, s>>>(flag, st);
   return cudaGetLastError();
 }
 

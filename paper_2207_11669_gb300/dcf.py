@@ -55,6 +55,8 @@ _SIGS = {
                                   C.c_int, C.c_int]),
     "dcf_reload_blocks": (C.c_int, [C.c_void_p, C.POINTER(C.c_void_p), C.POINTER(C.c_int64),
                                     C.c_int]),
+    "dcf_reload_blocks_async": (C.c_int, [C.c_void_p, C.POINTER(C.c_void_p),
+                                          C.POINTER(C.c_int64), C.c_int]),
     "dcf_load_init": (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(C.c_void_p), C.c_int]),
     "dcf_step": (C.c_int, [C.c_void_p, C.c_int]),
     "dcf_solve": (C.c_int, [C.c_void_p, C.POINTER(C.c_int), C.POINTER(C.c_double)]),
@@ -216,6 +218,13 @@ def dcf_reload_blocks(h, blocks, ld=None):
     arr = (C.c_void_p * len(ptrs))(*[p.value for p in ptrs])
     ld_arr = None if ld is None else (C.c_int64 * len(ld))(*[int(x) for x in ld])
     _check(h, lib().dcf_reload_blocks(h, arr, ld_arr, wheres[0]))
+
+
+def dcf_reload_blocks_async(h, blocks, ld=None):
+    ptrs, wheres = zip(*[_ptr_where(b) for b in blocks])
+    arr = (C.c_void_p * len(ptrs))(*[p.value for p in ptrs])
+    ld_arr = None if ld is None else (C.c_int64 * len(ld))(*[int(x) for x in ld])
+    _check(h, lib().dcf_reload_blocks_async(h, arr, ld_arr, wheres[0]))
 
 
 def dcf_load_init(h, U0, V0_blocks=None):
@@ -414,6 +423,14 @@ class Solver:
         iterate carries over (dcf_reload_blocks).  The copy has completed on
         return, so M need not outlive the call."""
         dcf_reload_blocks(self.h, self.blocks_of(M))
+
+    def reload_async(self, M):
+        """dcf_reload_blocks_async: M's copy overlaps the work already enqueued;
+        the next step reads it.  M must stay unchanged until a later call that
+        returns host data (factors, stats) has returned; the Solver keeps the
+        two most recent such matrices referenced."""
+        self._async_keep = (getattr(self, "_async_keep", (None, None))[1], M)
+        dcf_reload_blocks_async(self.h, self.blocks_of(M))
 
     def load_init(self, U0, V0=None):
         U0 = self._as_factor(U0)

@@ -364,3 +364,59 @@ def test_reload_errors():
     s.load(case["M"])
     s.step(1)
     s.close()
+
+
+@pytest.mark.parametrize("path", PATHS)
+def test_async_reload_continues_from_the_current_factors(path):
+    """dcf_reload_blocks_async: the new values are copied behind the enqueued
+    work into a second buffer; the next step reads them (oracle from the
+    factors the GPU held), a second call before a step replaces the first, and
+    the S of the step comes from the new values."""
+    m, n_i, r = 120, [40, 37, 50], 16
+    if not path_ok(path, m, r, sum(n_i)):
+        pytest.skip("shape outside this path")
+    case = make_case(m, n_i, r, seed=31)
+    case2 = make_case(m, n_i, r, seed=32)
+    case3 = make_case(m, n_i, r, seed=33)
+    s = gpu_solver(case, path=path)
+    s.step(2)
+    Ua, Va = s.factors()
+    s.reload_async(case3["M"])
+    s.reload_async(case2["M"])                     # replaces the first
+    s.step(1)
+    U, V = s.factors()
+    U1, V1, S1, _, _ = O.dcf_run(case2["M"], n_i, Ua, Va, case2["rho"], case2["lam"], 1)
+    assert rel(U, U1) <= 1e-4
+    assert rel(V, V1) <= 1e-4
+    S_gpu = np.concatenate([s.LS(i)[1] for i in range(len(n_i))], axis=1)
+    assert rel(S_gpu, S1) <= 1e-4
+    # alternate buffers for a few more steps: each reads the matrix copied before it
+    for q, c in enumerate([case, case3, case2]):
+        Ub, Vb = s.factors()
+        s.reload_async(c["M"])
+        s.step(1)
+        U, V = s.factors()
+        U2, V2, _, _, _ = O.dcf_run(c["M"], n_i, Ub, Vb, c["rho"], c["lam"], 1)
+        assert rel(U, U2) <= 1e-4, q
+        assert rel(V, V2) <= 1e-4, q
+    s.close()
+
+
+def test_async_reload_of_nonfinite_values_stops_the_solve():
+    case = make_case(200, [50, 50, 50, 50], 5, seed=4)
+    s = dcf.Solver(200, case["n_i"], 5, case["rho"], case["lam"])
+    s.load(case["M"])
+    s.step(1)
+    U0, _ = s.factors()
+    bad = case["M"].copy()
+    bad[3, 150] = np.inf
+    s.reload_async(bad)
+    s.step(2)                                      # no iteration runs on the rejected values
+    with pytest.raises(dcf.DcfError) as e:
+        s.stats()
+    assert e.value.status == dcf.DCF_ENONFINITE
+    assert np.array_equal(s.factors()[0], U0)
+    s.load(case["M"])                              # a full load starts over
+    s.step(1)
+    s.stats()
+    s.close()
