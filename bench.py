@@ -365,7 +365,7 @@ def run_e2e(dcf, torch, inst, wl, U0, stream, args, world):
     Mh = torch.empty((n, m), dtype=torch.float32, pin_memory=True)
     Mh.copy_(torch.from_numpy(np.ascontiguousarray(inst.M.T)))
     Uh = np.empty((m, r), np.float32)
-    e2e_steps = max(3, min(args.steps, 10))
+    e2e_steps = max(3, min(args.steps, 30))
     s2 = dcf.Solver(m, inst.n_i, r, wl.rho, wl.lam, stream=stream.cuda_stream)
     s2.load(Mh, borrow=False)
     s2.load_init(U0)
