@@ -16,7 +16,7 @@ arXiv 2207.11669) in float64 numpy, in the paper's order and notation:
   Huber form       §2.2 eq. ``cancelV`` and App. A.2
   error metric     §4.1 "Evaluation Metric" (squared, L and S together)
 
-Readings of the paper taken here (each one is listed in the design doc):
+Readings of the paper taken here:
   * one alternating S -> V sweep per iteration solves the (V,S) subproblem of
     Algorithm 1 eq. ``VS_arg`` (inner = 1); S uses (U_{t-1}, V_{t-1}), V uses
     (U_{t-1}, S_t), U uses (V_t, S_t);

@@ -84,7 +84,7 @@ def train(net, problems, steps, lr=0.05, log=None):
 
 # ---------------------------------------------------------------------------
 # Helpers of the learned workload: the plain method's fixed point is the
-# target the network is trained toward and the judge of its output.
+# target the network is trained toward and the reference its output is measured against.
 # ---------------------------------------------------------------------------
 def fixed_point(solver, U0, iters):
     """Plain iterations from (U0, V0 = S = 0 sweep); returns the factors
