@@ -107,6 +107,25 @@ __device__ __forceinline__ void split_h(float x, float s, __half& hi, __half& lo
   lo = __float2half_rn(xs - __half2float(hi));
 }
 
+// Packed FP32 pairs (one instruction for two lanes of arithmetic).
+__device__ __forceinline__ unsigned long long f2_bits(float2 v) {
+  return (unsigned long long)__float_as_uint(v.x) |
+         ((unsigned long long)__float_as_uint(v.y) << 32);
+}
+__device__ __forceinline__ float2 f2_from(unsigned long long b) {
+  return make_float2(__uint_as_float((unsigned)b), __uint_as_float((unsigned)(b >> 32)));
+}
+__device__ __forceinline__ float2 ffma2(float2 a, float2 b, float2 c) {
+  unsigned long long d;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(f2_bits(a)), "l"(f2_bits(b)), "l"(f2_bits(c)));
+  return f2_from(d);
+}
+__device__ __forceinline__ float2 fmul2(float2 a, float2 b) {
+  unsigned long long d;
+  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(f2_bits(a)), "l"(f2_bits(b)));
+  return f2_from(d);
+}
+
 __device__ __forceinline__ void tsum(float& hi, float& lo, float x) {
   float t = hi + x;
   float bp = t - hi;
@@ -416,6 +435,9 @@ __global__ void __launch_bounds__(kFThreads, 1)
     const int arow = rb * 128 + al;
     const float inv_uv = 1.f / (s_u * s_v);
     const float inv_lam = 1.f / a.lam;
+    const float2 neg_inv_uv = make_float2(-inv_uv, -inv_uv);
+    const float2 inv_lam2 = make_float2(inv_lam, inv_lam);
+    const float2 minus_half = make_float2(-0.5f, -0.5f);
     float hub_hi = 0.f, hub_lo = 0.f;
     for (int ls = 0; ls < S; ++ls) {
       if (!wait_(B(b_d1full), (uint32_t)(ls & 1))) err = 1;
@@ -429,7 +451,7 @@ __global__ void __launch_bounds__(kFThreads, 1)
       tc::fence_after_sync();
       uint8_t* cbuf = smem + L::CBUF + ps * L::CBYTES;
       const uint32_t tcrow = tcs(pc) + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(rb * 32);
-      float hub = 0.f;
+      float2 hub = make_float2(0.f, 0.f);   // even and odd columns
       // Software-pipelined over the 4 sub-tiles: the loads of sub-tile q+1 (D1
       // from tensor memory, M from the ring) are in flight while sub-tile q is
       // computed and stored.
@@ -461,16 +483,14 @@ __global__ void __launch_bounds__(kFThreads, 1)
         if (q < 3) load_sub(q + 1, dv[cb ^ 1], mv[cb ^ 1]);
         uint32_t packed[8];
 #pragma unroll
-        for (int jj = 0; jj < 16; jj += 2) {
-          float c2[2];
-#pragma unroll
-          for (int u = 0; u < 2; ++u) {
-            const float rn = (mv[cb][jj + u] - dv[cb][jj + u] * inv_uv) * inv_lam;   // R / lambda
-            const float c = fminf(fmaxf(rn, -1.f), 1.f);                             // C / lambda
-            hub = fmaf(c, rn - 0.5f * c, hub);                                       // H(R) / lambda^2
-            c2[u] = c;
-          }
-          __half2 h2 = __floats2half2_rn(c2[0], c2[1]);
+        for (int jj = 0; jj < 16; jj += 2) {   // two columns per packed instruction
+          const float2 m2 = make_float2(mv[cb][jj], mv[cb][jj + 1]);
+          const float2 d2 = make_float2(dv[cb][jj], dv[cb][jj + 1]);
+          const float2 rn = fmul2(ffma2(d2, neg_inv_uv, m2), inv_lam2);    // R / lambda
+          const float2 c = make_float2(fminf(fmaxf(rn.x, -1.f), 1.f),      // C / lambda
+                                       fminf(fmaxf(rn.y, -1.f), 1.f));
+          hub = ffma2(c, ffma2(c, minus_half, rn), hub);                   // H(R) / lambda^2
+          __half2 h2 = __floats2half2_rn(c.x, c.y);
           packed[jj / 2] = *reinterpret_cast<uint32_t*>(&h2);
         }
 #pragma unroll
@@ -488,7 +508,7 @@ __global__ void __launch_bounds__(kFThreads, 1)
         }
       }
       tc::tmem_st_wait();
-      tsum(hub_hi, hub_lo, hub);
+      tsum(hub_hi, hub_lo, hub.x + hub.y);
       tc::fence_before_sync();
       tc::fence_proxy_async_smem();
       __syncwarp();
