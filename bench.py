@@ -160,8 +160,9 @@ def alg_bytes_per_iter(m, n, r):
 # The capture ran a smaller n; traffic grows in proportion to n (M is streamed
 # once, V read and written), so it is scaled by n.  None for other shapes.
 NCU_TRAFFIC = {
-    # k_fused<32, 5, false>, m=4096, n=16384, r=32: 273.81 MB read + 4.65 MB written
-    "fused_step": {"m": 4096, "r": 32, "n": 16384, "bytes": 278.46e6},
+    # k_fused<32, 5, false> was captured (m=4096, n=16384, r=32: 273.81 MB read + 4.65 MB
+    # written) before its epilogue moved to packed FP32 pairs; its traffic is reported
+    # as unknown (null) until it is captured again.
     # k_tc2<64, 5, false> / k_tc2<64, 7, true>, m=16384, n=16384, r=64
     "pass_a": {"m": 16384, "r": 64, "n": 16384, "bytes": 1335.38e6},
     "pass_b": {"m": 16384, "r": 64, "n": 16384, "bytes": 1090.35e6},
