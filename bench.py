@@ -552,9 +552,14 @@ def run_learned(args):
                 dev = e0.elapsed_time(e1)
                 best = (dev, wall) if best is None or dev < best[0] else best
             times[arm] = best
+        # kernels in one timed learned run: per network step a re-factorisation plus
+        # one plain iteration's launches, one final re-factorisation, the refinement
+        L = {1: 7, 2: 6, 3: 8, 4: 1}[s.path]
+        K = len(theta[0])
         rows.append(dict(n_plain=n_plain, n_refine=n_ref, plain_ms=times["plain"][0],
                          learned_ms=times["learned"][0], plain_wall_ms=times["plain"][1],
-                         learned_wall_ms=times["learned"][1]))
+                         learned_wall_ms=times["learned"][1],
+                         learned_launches=(1 + L) * K + 1 + n_ref * L))
         s.close()
         del Mt
     plain = float(np.mean([r["plain_ms"] for r in rows]))
@@ -570,7 +575,7 @@ def run_learned(args):
                            "theta": {"a": th["a"], "b": th["b"], "c": th["c"]}},
                 "plain_ms": plain, "speedup_vs_plain": plain / learned,
                 "per_problem": rows, "e2e": None, "cpu_baseline": None,
-                "gpu_launches": None}
+                "gpu_launches": int(sum(r["learned_launches"] for r in rows))}
         print(json.dumps(line), flush=True)
     return 0
 
