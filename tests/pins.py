@@ -171,3 +171,113 @@ def check_fedavg_is_global_gd(dcf_iteration, objective, s_step, v_step, seed=7):
     G = fd_grad(lambda X: objective(M, X, V_ref, S_ref, rho, lam), U)
     U_ref = U - eta / len(n_i) * G
     return float(np.max(np.abs(U1 - U_ref)))
+
+
+# --- FedAvg U-step of Algorithm 1, and its K > 1 local steps --------------------------
+def _split(M, V, S, n_i):
+    off = np.concatenate([[0], np.cumsum(n_i)])
+    E = len(n_i)
+    return ([M[:, off[i]:off[i + 1]] for i in range(E)],
+            [V[off[i]:off[i + 1]] for i in range(E)],
+            [S[:, off[i]:off[i + 1]] for i in range(E)])
+
+
+def check_u_step_fedavg(u_step_fedavg, local_objective, seed=8):
+    """Algorithm 1 eqs. U_local and U_agg with the (V_i, S_i) fixed: every client
+    takes U - eta grad_U L_i, the gradient by central finite differences of the
+    brute-force L_i of §2.2 (which carries the rho n_i/(2n) ||U||^2 share), and the
+    server takes the unweighted mean of the E results."""
+    p = small_problem(seed, m=8, n=13, r=3, E=3)
+    M, U, V, rho, lam, n_i = p["M"], p["U"], p["V"], p["rho"], p["lam"], p["n_i"]
+    n_i = np.array([2, 4, 7])          # uneven shares n_i / n
+    g = rng(seed + 1)
+    S = np.where(g.random(M.shape) < 0.2, g.standard_normal(M.shape), 0.0)
+    n = M.shape[1]
+    Ms, Vs, Ss = _split(M, V, S, n_i)
+    eta = 0.03
+    got = u_step_fedavg(Ms, Ss, Vs, U, rho, eta, n_i, n)
+    ref = np.zeros_like(U)
+    for Mi, Vi, Si, ni in zip(Ms, Vs, Ss, n_i):
+        G = fd_grad(lambda X: local_objective(Mi, X, Vi, Si, rho, lam, int(ni), n), U)
+        ref += U - eta * G
+    ref /= len(n_i)
+    return float(np.max(np.abs(got - ref)))
+
+
+def check_u_step_fedavg_is_global_gd(u_step_fedavg, objective, seed=9):
+    """With the clients' (V_i, S_i) fixed and K = 1, the unweighted FedAvg of the
+    client steps is one global gradient step U - (eta/E) grad_U F of the §1
+    objective (the K = 1 remark of §2.2), F's gradient by finite differences."""
+    p = small_problem(seed, m=7, n=12, r=2, E=4)
+    M, U, V, rho, lam, n_i = p["M"], p["U"], p["V"], p["rho"], p["lam"], p["n_i"]
+    n_i = np.array([1, 2, 4, 5])
+    g = rng(seed + 1)
+    S = np.where(g.random(M.shape) < 0.2, g.standard_normal(M.shape), 0.0)
+    Ms, Vs, Ss = _split(M, V, S, n_i)
+    eta = 0.02
+    got = u_step_fedavg(Ms, Ss, Vs, U, rho, eta, n_i, M.shape[1])
+    G = fd_grad(lambda X: objective(M, X, V, S, rho, lam), U)
+    return float(np.max(np.abs(got - (U - eta / len(n_i) * G))))
+
+
+def check_local_steps(dcf_iteration, local_objective, s_step, v_step, K=3, seed=10):
+    """Algorithm 1 with K local steps: each client i starts from the round's U and
+    its own V_i; at every local step S_i and V_i are recomputed from the client's
+    CURRENT U_i (eq. VS_arg with one S -> V sweep), then U_i moves by -eta times the
+    finite-difference gradient of the brute-force L_i at (U_i, V_i, S_i)
+    (eq. U_local).  Only after the K steps does the server average the U_i
+    (eq. U_agg).  V and S returned are each client's last local V_i and S_i."""
+    p = small_problem(seed, m=8, n=14, r=3, E=3)
+    M, U, V, rho, lam = p["M"], p["U"], p["V"], p["rho"], p["lam"]
+    n_i = np.array([3, 5, 6])
+    n = M.shape[1]
+    eta = 0.05
+    U1, V1, S1 = dcf_iteration(M, n_i, U, V, rho, lam, u_mode=1, eta=eta, local_steps=K)
+    off = np.concatenate([[0], np.cumsum(n_i)])
+    U_acc = np.zeros_like(U)
+    res = 0.0
+    for i in range(len(n_i)):
+        Mi = M[:, off[i]:off[i + 1]]
+        Ui = U.copy()
+        Vi = V[off[i]:off[i + 1]].copy()
+        for _ in range(K):
+            Si = s_step(Mi, Ui, Vi, lam)
+            Vi = v_step(Mi, Si, Ui, rho)
+            G = fd_grad(lambda X: local_objective(Mi, X, Vi, Si, rho, lam, int(n_i[i]), n),
+                        Ui)
+            Ui = Ui - eta * G
+        U_acc += Ui
+        res = max(res, float(np.max(np.abs(V1[off[i]:off[i + 1]] - Vi))))
+        res = max(res, float(np.max(np.abs(S1[:, off[i]:off[i + 1]] - Si))))
+    res = max(res, float(np.max(np.abs(U1 - U_acc / len(n_i)))))
+    return res
+
+
+def check_clients_independent(dcf_iteration, K=4, seed=11):
+    """The clients of Algorithm 1 run their K local steps on their own data only
+    and meet once, in the unweighted mean of eq. U_agg.  With two blocks of equal
+    width (share n_i/n = 1/2 each), a round over [M_1, X] must therefore return
+    U = (U_1 + U_2)/2 where U_1 is the round over the identical pair [M_1, M_1]
+    (both clients take M_1's trajectory, so their mean is that trajectory) and U_2
+    the round over [X, X]; the V and S blocks of [M_1, X] are those of the
+    matching pairs.  Averaging inside the local loop breaks this for K > 1."""
+    p = small_problem(seed, m=7, n=10, r=2, E=2)
+    M, U, V, rho, lam = p["M"], p["U"], p["V"], p["rho"], p["lam"]
+    w = 5
+    M1, X = M[:, :w], M[:, w:]
+    V1, VX = V[:w], V[w:]
+    eta = 0.04
+    kw = dict(u_mode=1, eta=eta, local_steps=K)
+    Ua, Va, Sa = dcf_iteration(M, [w, w], U, V, rho, lam, **kw)
+    U1, V11, S11 = dcf_iteration(np.hstack([M1, M1]), [w, w], U, np.vstack([V1, V1]),
+                                 rho, lam, **kw)
+    U2, VXX, SXX = dcf_iteration(np.hstack([X, X]), [w, w], U, np.vstack([VX, VX]),
+                                 rho, lam, **kw)
+    res = float(np.max(np.abs(2.0 * Ua - (U1 + U2))))
+    res = max(res, float(np.max(np.abs(Va[:w] - V11[:w]))),
+              float(np.max(np.abs(Va[w:] - VXX[w:]))))
+    res = max(res, float(np.max(np.abs(Sa[:, :w] - S11[:, :w]))),
+              float(np.max(np.abs(Sa[:, w:] - SXX[:, w:]))))
+    # the identical pair: both clients end in the same state
+    res = max(res, float(np.max(np.abs(V11[:w] - V11[w:]))))
+    return res

@@ -71,6 +71,78 @@ def _weighted_fedavg_iteration(M, n_i, U, V, rho, lam, *, u_mode=0, eta=0.0, loc
     return acc, None, None
 
 
+def _fedavg_no_share(Ms, Ss, Vs, U, rho, eta, n_i, n):
+    # drops the n_i/n share of the rho term in every client's gradient
+    acc = np.zeros_like(U)
+    for M, S, V in zip(Ms, Ss, Vs):
+        acc += U - eta * (rho * U + (U @ V.T + S - M) @ V)
+    return acc / len(Ms)
+
+
+def _fedavg_weighted(Ms, Ss, Vs, U, rho, eta, n_i, n):
+    # weights the client results by n_i/n instead of the unweighted mean
+    acc = np.zeros_like(U)
+    for M, S, V, ni in zip(Ms, Ss, Vs, n_i):
+        acc += (ni / n) * (U - eta * O.grad_U_local(M, U, V, S, rho, ni, n))
+    return acc
+
+
+def _local_steps_round_U(M, n_i, U, V, rho, lam, *, u_mode=0, eta=0.0, local_steps=1):
+    # S and V of every local step use the round's U, not the client's own U_i
+    off = O.block_offsets(n_i)
+    n = int(off[-1])
+    Us, Vs, Ss = [], [], []
+    for i in range(len(n_i)):
+        Mi = M[:, off[i]:off[i + 1]]
+        Ui, Vi = U.copy(), V[off[i]:off[i + 1]].copy()
+        for _ in range(local_steps):
+            Si = O.s_step(Mi, U, Vi, lam)
+            Vi = O.v_step(Mi, Si, U, rho)
+            Ui = Ui - eta * O.grad_U_local(Mi, Ui, Vi, Si, rho, int(n_i[i]), n)
+        Us.append(Ui)
+        Vs.append(Vi)
+        Ss.append(Si)
+    return sum(Us) / len(Us), np.vstack(Vs), np.hstack(Ss)
+
+
+def _local_steps_average_each_step(M, n_i, U, V, rho, lam, *, u_mode=0, eta=0.0,
+                                   local_steps=1):
+    # the server averages after every local step instead of once after K
+    off = O.block_offsets(n_i)
+    n = int(off[-1])
+    E = len(n_i)
+    Vs = [V[off[i]:off[i + 1]].copy() for i in range(E)]
+    Ss = [None] * E
+    for _ in range(local_steps):
+        acc = np.zeros_like(U)
+        for i in range(E):
+            Mi = M[:, off[i]:off[i + 1]]
+            Ss[i] = O.s_step(Mi, U, Vs[i], lam)
+            Vs[i] = O.v_step(Mi, Ss[i], U, rho)
+            acc += U - eta * O.grad_U_local(Mi, U, Vs[i], Ss[i], rho, int(n_i[i]), n)
+        U = acc / E
+    return U, np.vstack(Vs), np.hstack(Ss)
+
+
+def _local_steps_stale_V(M, n_i, U, V, rho, lam, *, u_mode=0, eta=0.0, local_steps=1):
+    # every local step restarts its S-step from the round's V_i
+    off = O.block_offsets(n_i)
+    n = int(off[-1])
+    Us, Vs, Ss = [], [], []
+    for i in range(len(n_i)):
+        Mi = M[:, off[i]:off[i + 1]]
+        Ui = U.copy()
+        V0 = V[off[i]:off[i + 1]]
+        for _ in range(local_steps):
+            Si = O.s_step(Mi, Ui, V0, lam)
+            Vi = O.v_step(Mi, Si, Ui, rho)
+            Ui = Ui - eta * O.grad_U_local(Mi, Ui, Vi, Si, rho, int(n_i[i]), n)
+        Us.append(Ui)
+        Vs.append(Vi)
+        Ss.append(Si)
+    return sum(Us) / len(Us), np.vstack(Vs), np.hstack(Ss)
+
+
 CASES = [
     ("s_hard", lambda: pins.check_s_step(_hard_threshold_s_step)),
     ("s_sign", lambda: pins.check_s_step(_flipped_s_step)),
@@ -85,6 +157,20 @@ CASES = [
     ("local_share", lambda: pins.check_local_split(_local_no_share, O.objective)),
     ("fedavg_weights", lambda: pins.check_fedavg_is_global_gd(
         _weighted_fedavg_iteration, O.objective, O.s_step, O.v_step)),
+    ("fedavg_fn_no_share", lambda: pins.check_u_step_fedavg(_fedavg_no_share,
+                                                            O.local_objective)),
+    ("fedavg_fn_weighted", lambda: pins.check_u_step_fedavg(_fedavg_weighted,
+                                                            O.local_objective)),
+    ("fedavg_fn_no_share_gd", lambda: pins.check_u_step_fedavg_is_global_gd(
+        _fedavg_no_share, O.objective)),
+    ("local_round_U", lambda: pins.check_local_steps(
+        _local_steps_round_U, O.local_objective, O.s_step, O.v_step, K=3)),
+    ("local_avg_each_step", lambda: pins.check_local_steps(
+        _local_steps_average_each_step, O.local_objective, O.s_step, O.v_step, K=3)),
+    ("local_avg_each_step_indep", lambda: pins.check_clients_independent(
+        _local_steps_average_each_step, K=3)),
+    ("local_stale_V", lambda: pins.check_local_steps(
+        _local_steps_stale_V, O.local_objective, O.s_step, O.v_step, K=3)),
 ]
 
 

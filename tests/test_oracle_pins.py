@@ -57,6 +57,40 @@ def test_fedavg_k1_is_one_global_gradient_step():
                                           O.v_step) < 1e-7
 
 
+def test_u_step_fedavg_matches_finite_difference_client_steps():
+    assert pins.check_u_step_fedavg(O.u_step_fedavg, O.local_objective) < 1e-7
+
+
+def test_u_step_fedavg_k1_is_one_global_gradient_step():
+    assert pins.check_u_step_fedavg_is_global_gd(O.u_step_fedavg, O.objective) < 1e-7
+
+
+@pytest.mark.parametrize("K", [1, 2, 3])
+def test_local_steps_follow_algorithm_1(K):
+    assert pins.check_local_steps(O.dcf_iteration, O.local_objective, O.s_step,
+                                  O.v_step, K=K) < 1e-7
+
+
+@pytest.mark.parametrize("K", [2, 5])
+def test_local_steps_clients_meet_only_in_the_average(K):
+    assert pins.check_clients_independent(O.dcf_iteration, K=K) < 1e-12
+
+
+def test_local_steps_k1_equals_fedavg_function():
+    """The K = 1 branch of the round and u_step_fedavg on the round's own
+    (V_t, S_t) give the same U."""
+    p = pins.small_problem(12)
+    M, U, V, rho, lam, n_i = p["M"], p["U"], p["V"], p["rho"], p["lam"], p["n_i"]
+    U1, V1, S1 = O.dcf_iteration(M, n_i, U, V, rho, lam, u_mode=1, eta=0.02)
+    off = O.block_offsets(n_i)
+    E = len(n_i)
+    U2 = O.u_step_fedavg([M[:, off[i]:off[i + 1]] for i in range(E)],
+                         [S1[:, off[i]:off[i + 1]] for i in range(E)],
+                         [V1[off[i]:off[i + 1]] for i in range(E)],
+                         U, rho, 0.02, n_i, M.shape[1])
+    assert np.max(np.abs(U1 - U2)) < 1e-13
+
+
 def test_ridge_solve_matches_dense_solve():
     g = np.random.default_rng(3)
     A = g.standard_normal((6, 6))
