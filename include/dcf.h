@@ -89,7 +89,8 @@ typedef struct {
                            m % 4 == 0 with m > 4096 or r > 32, else 1         */
 } dcf_params;
 
-/* Device allocator hook: alloc(bytes, ctx) returns device memory or NULL,
+/* Device allocator hook (no counterpart in the paper: a deployment hook for
+ * callers that manage device memory themselves).  alloc(bytes, ctx) returns device memory or NULL,
  * release(ptr, ctx) frees it.  Passing NULLs restores cudaMalloc/cudaFree.
  * Must be set before dcf_create to take effect for that handle.  Pointers
  * must be 256-byte aligned, as cudaMalloc's are; a misaligned one is released
@@ -98,22 +99,28 @@ typedef void* (*dcf_alloc_fn)(size_t bytes, void* ctx);
 typedef void (*dcf_free_fn)(void* ptr, void* ctx);
 void dcf_set_allocator(dcf_alloc_fn alloc, dcf_free_fn release, void* ctx);
 
-/* Validate `p` and create a handle.  Fails with DCF_EINVAL for m < 1, E < 1,
+/* The problem statement of §2.1 (M in R^{m x n} split by columns into E
+ * client blocks M_i of n_i columns, rank r) with the weights rho, lambda of
+ * §1 and Algorithm 1's round count and step size.
+ * Validate `p` and create a handle.  Fails with DCF_EINVAL for m < 1, E < 1,
  * any n_i < 1, r outside [1, 64] or r > m, rho <= 0, lambda <= 0,
  * local_steps != 1, or u_mode not in {0, 1}.  When rho^2 > lambda^2 m n
  * (the necessary condition of §3.2 fails) the handle is still created and
  * dcf_last_error() carries a warning. */
 dcf_status dcf_create(const dcf_params* p, dcf_handle* out);
 
-/* Which kernels run an iteration: 1 general two-pass path, 2 fused
+/* (No counterpart in the paper.)  Which kernels run an iteration: 1 general two-pass path, 2 fused
  * single-pass tensor-core path, 3 two-pass tensor-core path, 4 whole solve in
  * one CTA. */
 int dcf_get_path(dcf_handle h);
 
-/* Enqueue all further work of the handle on `stream` (a cudaStream_t). */
+/* (No counterpart in the paper.)  Enqueue all further work of the handle on
+ * `stream` (a cudaStream_t). */
 dcf_status dcf_set_stream(dcf_handle h, void* stream);
 
-/* Provide the blocks M_i (m x n_i column-major, leading dimension ld_i >= m).
+/* The clients' local data of §2.1: M = [M_1 ... M_E], block M_i in
+ * R^{m x n_i} held by client i (Algorithm 1, input).
+ * Provide the blocks M_i (m x n_i column-major, leading dimension ld_i >= m).
  * where = 0: host pointers, copied to the device.  where = 1: device
  * pointers; with borrow = 1 the blocks must be one contiguous column-major
  * matrix (M_{i+1} == M_i + m*n_i, ld_i == m) that is used in place, otherwise
@@ -154,23 +161,33 @@ dcf_status dcf_reload_blocks(dcf_handle h, const float* const* M_i, const int64_
 dcf_status dcf_reload_blocks_async(dcf_handle h, const float* const* M_i, const int64_t* ld_i,
                                    int where);
 
-/* Set the starting point U0 (m x r) and V0_i (n_i x r).  Without this call
+/* Algorithm 1's initialisation of U^(0) and the clients' V_i (the paper leaves
+ * the law open; the default below is this library's reading).
+ * Set the starting point U0 (m x r) and V0_i (n_i x r).  Without this call
  * dcf_step/dcf_solve start from U0 ~ N(0, 1/m) (counter-based Philox4x32-10,
  * keyed by params.seed) and V0 = M^T U0 (U0^T U0 + rho I)^{-1}, the V-step
  * with S = 0.  Passing V0_i = NULL keeps U0 and computes V0 that way.
  * Resets the iteration counter to 0. */
 dcf_status dcf_load_init(dcf_handle h, const float* U0, const float* const* V0_i, int where);
 
-/* Run exactly n_steps iterations (no stopping test). */
+/* Run exactly n_steps iterations, each one communication round t of
+ * Algorithm 1: every client's S-step (§2.2 eq. optS) and V-step (App. B eq.
+ * condition1), then the server's consensus U (exact, or eqs. U_local and
+ * U_agg in FedAvg mode).  No stopping test, as in Algorithm 1's fixed T. */
 dcf_status dcf_step(dcf_handle h, int n_steps);
 
-/* Iterate until ||U_t V_t^T - U_{t-1} V_{t-1}^T||_F / ||U_t V_t^T||_F <= tol
+/* Rounds of Algorithm 1 as in dcf_step, with a stopping rule.  The paper runs
+ * a fixed number of rounds T and states no rule; the rule below is this
+ * library's reading.
+ * Iterate until ||U_t V_t^T - U_{t-1} V_{t-1}^T||_F / ||U_t V_t^T||_F <= tol
  * (evaluated exactly from r x r Gram matrices) or max_iter iterations in this
  * call.  Returns DCF_ENOTCONV when the cap is reached above tol.  The
  * iterations run and the last relative change are written when non-NULL. */
 dcf_status dcf_solve(dcf_handle h, int* iters_out, double* final_dL_rel);
 
-/* Copy out U (m x r) and, when V_i is non-NULL, every V_i (n_i x r). */
+/* The factors of §2.1's L = U V^T (U shared, V_i per client; Algorithm 1's
+ * outputs are L_i = U V_i^T, see dcf_get_LS).
+ * Copy out U (m x r) and, when V_i is non-NULL, every V_i (n_i x r). */
 dcf_status dcf_get_factors(dcf_handle h, float* U, float* const* V_i, int where);
 
 /* Block i's outputs of Algorithm 1: L_i = U V_i^T and S_i, the S-step of the
@@ -183,23 +200,29 @@ dcf_status dcf_get_LS(dcf_handle h, int i, float* L_i, float* S_i, int where);
  * by dcf_get_LS (§2.2 "Privacy Preserving", Algorithm 1 output). */
 dcf_status dcf_set_private(dcf_handle h, int i, int is_private);
 
-/* Statistics of the last iteration t: the objective of §1 at
+/* (§1 eq. noncovex_problem in its Huber form of §2.2 eq. cancelV; the
+ * relative change is the stopping quantity of dcf_solve.)
+ * Statistics of the last iteration t: the objective of §1 at
  * (U_{t-1}, V_{t-1}, S_t), evaluated in its Huber form, the relative change
  * of L, and t.  Any pointer may be NULL. */
 dcf_status dcf_get_stats(dcf_handle h, double* objective, double* dL_rel, int* iter);
 
-/* Register a ground truth L* = A B^T (A: m x k, B: n x k, row-major) so that
+/* The ground truth of the synthetic experiments of §4.1 (L0 = A B^T) and
+ * the relative error of L against it (§4.1 "Evaluation Metric", here the
+ * non-squared error of L alone).
+ * Register a ground truth L* = A B^T (A: m x k, B: n x k, row-major) so that
  * dcf_rel_err can report ||U V^T - L*||_F / ||L*||_F (from Gram matrices). */
 dcf_status dcf_set_truth(dcf_handle h, const float* A, const float* B, int k, int where);
 dcf_status dcf_rel_err(dcf_handle h, double* rel_err_L);
 
-/* Message of the last failure (or warning) on this handle; never NULL. */
+/* (No counterpart in the paper.)  Message of the last failure (or warning) on
+ * this handle; never NULL. */
 const char* dcf_last_error(dcf_handle h);
 
-/* Release everything the handle owns.  Safe on NULL. */
+/* (No counterpart in the paper.)  Release everything the handle owns.  Safe on NULL. */
 void dcf_destroy(dcf_handle h);
 
-/* Profiling: number of kernel phases of one iteration (the names, comma
+/* (No counterpart in the paper.)  Profiling: number of kernel phases of one iteration (the names, comma
  * separated, are copied into names_csv when it is non-NULL), and
  * dcf_profile_step(), which runs n_steps iterations launching each phase
  * separately (no CUDA graph) and adds each phase's CUDA-event time in
@@ -218,11 +241,12 @@ int dcf_tc_selftest(const int* cfg, float* out_host);
 
 /* ---- Allocation-free iteration ----------------------------------------------
  * One exact-consensus DCF-PCA iteration on buffers the caller owns, for
- * callers that cannot let a library allocate device memory: work being
- * recorded into a CUDA graph by stream capture, latency-critical loops where
- * cudaMalloc/cudaFree would synchronise the device, and frameworks that hand
- * out all device memory from their own pools.  The paper has no counterpart;
- * it is a deployment variant of the general two-pass path of dcf_step.
+ * callers that cannot let a library allocate device memory: frameworks that
+ * hand out all device memory from their own pools and forbid libraries to
+ * call cudaMalloc, and latency-critical loops where cudaMalloc/cudaFree would
+ * synchronise the device.  The paper has no counterpart; it is a deployment
+ * variant of the general two-pass path of dcf_step (same kernels, same
+ * partition of the partial sums).
  *
  * Inputs (device memory of the current device): M, m x n column-major
  * (one block; exact consensus does not depend on the client split); U_in,
@@ -235,7 +259,8 @@ int dcf_tc_selftest(const int* cfg, float* out_host);
  * library, held by every GPU that loads the library until the process
  * exits.  Returns DCF_EINVAL, touching nothing, when the problem needs more
  * scratch than that (about 4(3m + 2n)R + 4mR*splits bytes plus r x r
- * workspace, R = r rounded up to 8, 16, 32 or 64), and for invalid sizes,
+ * workspace, R = r rounded up to 8, 16, 32 or 64; m = 300, n = 317, r = 16
+ * fits easily, m = 4096, n = 65536, r = 32 does not), and for invalid sizes,
  * rho <= 0, lambda <= 0 or NULL pointers.  Never calls cudaMalloc, cudaFree
  * or any allocating routine.
  *

@@ -2,13 +2,12 @@
 // caller owns, with every piece of scratch memory taken from one fixed,
 // file-scope device array instead of being allocated.
 //
-// Who needs this: code that must not call cudaMalloc -- work recorded while a
-// CUDA stream is being captured into a graph (an allocation there breaks or
-// invalidates the capture), latency-critical loops (cudaMalloc and cudaFree
-// can synchronise the device), and host frameworks that own all device
-// memory through their own pools and do not let libraries allocate behind
-// their back.  Such callers hand in M, U and V and receive the new U and V;
-// the library itself allocates nothing on this path.
+// Who needs this: callers that may not allocate device memory behind their
+// own back -- host frameworks that hand out all device memory from their own
+// pools and forbid libraries to call cudaMalloc, and latency-critical loops
+// where cudaMalloc and cudaFree can synchronise the device.  Such callers hand
+// in M, U and V and receive the new U and V; the library allocates nothing on
+// this path.
 //
 // The scratch array lives in the library's device image, so every GPU that
 // loads libdcf.so holds kNoAllocScratchBytes of it until the process exits.
@@ -101,7 +100,9 @@ extern "C" dcf_status dcf_iterate_noalloc(const float* M, int64_t m, int64_t n, 
   const int64_t split_cols = ((n + splits - 1) / splits + 31) / 32 * 32;
   const int n_splits = (int)((n + split_cols - 1) / split_cols);
   const int n_rblocks = (int)((m + 31) / 32);
-  const int n_vgram = (int)std::min<int64_t>(2LL * sms, (n + 31) / 32);
+  // the same V-Gram partition as the general path of dcf_step (one CTA per SM
+  // at R >= 32, two below), so both sum the partials in the same order
+  const int n_vgram = (int)std::min<int64_t>((R >= 32 ? 1LL : 2LL) * sms, (n + 31) / 32);
   const size_t ngp = (size_t)std::max(n_vgram, n_rblocks);
 
   // carve the scratch (a dry run first: reject sizes beyond the array)
@@ -167,10 +168,15 @@ extern "C" dcf_status dcf_iterate_noalloc(const float* M, int64_t m, int64_t n, 
       return DCF_ECUDA;                               \
     }                                                 \
   } while (0)
-  // the array keeps the previous call's contents: clear what must start at
-  // zero (rank padding of the factors, last-block counters, state, r x r workspace)
+  // the array keeps the previous call's contents (possibly of another size or
+  // rank): clear what must start at zero -- both copies of the factors and W,
+  // whose columns r..R-1 are the exact zero padding of the rank, the
+  // last-block counters, the state and the r x r workspace
   NA_CK(cudaMemsetAsync(a.U[0], 0, (size_t)m * R * 4, s));
+  NA_CK(cudaMemsetAsync(a.U[1], 0, (size_t)m * R * 4, s));
   NA_CK(cudaMemsetAsync(a.V[0], 0, (size_t)n * R * 4, s));
+  NA_CK(cudaMemsetAsync(a.V[1], 0, (size_t)n * R * 4, s));
+  NA_CK(cudaMemsetAsync(a.W, 0, (size_t)m * R * 4, s));
   NA_CK(cudaMemsetAsync(counters, 0, 4 * sizeof(unsigned int), s));
   NA_CK(cudaMemsetAsync(a.st, 0, sizeof(DevState), s));
   NA_CK(cudaMemsetAsync(a.sm, 0, sizeof(Smalls), s));
