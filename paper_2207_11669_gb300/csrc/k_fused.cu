@@ -30,9 +30,15 @@
 // V' image), which is the only cross-CTA exchange.  Each cluster walks the
 // strips s = cluster_id, cluster_id + #clusters, ...
 //
-// Every wait on an mbarrier is bounded; on expiry the kernel records
-// DCF_ETIMEOUT and runs to completion (all cluster barriers are still
-// executed, tensor memory is always released).
+// Every wait on an mbarrier is bounded.  The first wait that expires raises a
+// CTA-wide abort flag; from then on no role issues another MMA, tcgen05.st,
+// TMA load or st.async that the expired wait was guarding, the single-thread
+// roles and the epilogue leave their loops, and the exchange warps run their
+// remaining strips without waiting or sending (their named barriers stay
+// matched).  Before tensor memory is released the MMA issuers' final commits
+// and the TMA loads still in flight are drained with bounded waits; if even
+// that fails the tensor memory is left allocated.  The kernel records
+// DCF_ETIMEOUT and every CTA still reaches the final cluster barrier.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <cuda_fp16.h>
@@ -79,11 +85,12 @@ struct FL {  // shared-memory layout (bytes)
   static constexpr int BAR = STG + 2 * (2 * R * kChunk * 2);     // mbarriers (2 staging chunks)
   // full/empty NST each; vfull, vempty, d1full, d1empty 2 each (only [0] of
   // each is used); cfull, cempty kNC each; c2free kNCS; d2full, d2empty,
-  // g3done, yfull, yfree, pfull, pfree 2 each; img, last
-  static constexpr int NBAR = 2 * NST + 8 + 2 * kNC + kNCS + 14 + 2;
+  // g3done, yfull, yfree, pfull, pfree 2 each; img, last, fin1
+  static constexpr int NBAR = 2 * NST + 8 + 2 * kNC + kNCS + 14 + 3;
   static constexpr int TSLOT = BAR + NBAR * 8;
   static constexpr int RED = TSLOT + 16;                         // 16 doubles
-  static constexpr int TOTAL = RED + 16 * 8;
+  static constexpr int ABRT = RED + 16 * 8;                      // abort flag (int)
+  static constexpr int TOTAL = ABRT + 16;
   // tensor-memory columns (512 allocated)
   static constexpr int T_D1 = 0;                                 // 2 blocks x 64 (U V_s^T)
   static constexpr int T_D2 = 128;                               // 2 x (M=64 result, R columns)
@@ -192,13 +199,25 @@ __global__ void __launch_bounds__(kFThreads, 1)
             b_d2empty = b_d2full + 2,
             b_g3done = b_d2empty + 2, b_yfull = b_g3done + 2, b_yfree = b_yfull + 2,
             b_pfull = b_yfree + 2, b_pfree = b_pfull + 2, b_img = b_pfree + 2,
-            b_last = b_img + 1;
+            b_last = b_img + 1, b_fin1 = b_last + 1;
   double* red = reinterpret_cast<double*>(smem + L::RED);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(smem + L::ABRT);
   int err = 0;
   const uint64_t deadline = tc::globaltimer_ns() + kDeadlineNs;
+  // One thread's bounded wait; on expiry (or once another role has given up)
+  // it raises the abort flag and returns false.
   auto wait_ = [&](uint32_t bar, uint32_t parity) {
-    return tc::mbar_wait_deadline(bar, parity, deadline);
+    if (tc::mbar_wait_or_abort(bar, parity, deadline, abort_flag)) return true;
+    *abort_flag = 1;
+    err = 1;
+    return false;
   };
+  // The same wait by a whole warp, with one answer for all of its lanes.
+  auto wait_w = [&](uint32_t bar, uint32_t parity) {
+    const bool ok = wait_(bar, parity);
+    return __all_sync(0xffffffffu, ok) != 0;
+  };
+  auto aborted = [&]() { return *abort_flag != 0; };
 
   // ---- set-up -------------------------------------------------------------
   if (warp == 1) {
@@ -234,7 +253,9 @@ __global__ void __launch_bounds__(kFThreads, 1)
       tc::mbar_init(B(b_pfree + p), cs);    // every CTA's GEMM3, remote arrivals
     }
     tc::mbar_init(B(b_img), 1);
-    tc::mbar_init(B(b_last), 1);            // every MMA of the kernel has completed
+    tc::mbar_init(B(b_last), 1);            // every MMA of the GEMM3 issuer has completed
+    tc::mbar_init(B(b_fin1), 1);            // every MMA of the GEMM1/GEMM2 issuer has completed
+    *abort_flag = 0;
     tc::fence_mbar_init();
     tc::prefetch_tmap(tmp);
   }
@@ -284,35 +305,37 @@ __global__ void __launch_bounds__(kFThreads, 1)
   tc::fence_after_sync();
 
   constexpr uint32_t SB_R = (R / 8) * 128;    // N-direction core stride of the K=R V image
+  int issued = 0;                             // TMA sub-tile loads issued (thread 0)
   if (warp == 0) {
     // ================= TMA producer ==========================================
     if (lane == 0) {
       const int total = S * 4;
       for (int g = 0; g < total; ++g) {
         const int slot = g % NST;
-        if (g >= NST && !wait_(B(b_empty + slot), (uint32_t)((g / NST - 1) & 1)))
-          err = 1;
+        if (g >= NST && !wait_(B(b_empty + slot), (uint32_t)((g / NST - 1) & 1))) break;
+        if (aborted()) break;
         const int ls = g >> 2, q = g & 3;
         tc::mbar_arrive_expect_tx(B(b_full + slot), kSubBytes);
         tc::tma_load_2d(sbase + L::RING + slot * kSubBytes, tmp, (int)row0,
                         (int)(strip_col0(ls) + kSubCols * q), B(b_full + slot));
+        issued = g + 1;
       }
     }
   } else if (warp == 1) {
     // ================= MMA issuer: GEMM1 and GEMM2 ============================
     if (lane == 0) {
-      if (!wait_(B(b_img), 0)) err = 1;
+      const bool img_ok = wait_(B(b_img), 0);
       const uint32_t idesc1 = tc::idesc_f16(128, kFW, 0, 0);
       const uint32_t idesc2 = tc::idesc_f16(64, R, 1, 0);
       // descriptors are built once; moving along K adds (bytes >> 4) to the address field
       const uint64_t vdesc0 = tc::smem_desc(sbase + L::VIMG, 128, SB_R);
       const uint64_t cdesc0 = tc::smem_desc(sbase + L::CBUF, 128, kFH * 16);
       const uint64_t wdesc0 = tc::smem_desc(sbase + L::WIMG, 128, kFH * 16);
-      for (int i = 0; i < S + 1; ++i) {
+      for (int i = 0; img_ok && i < S + 1; ++i) {
         if (i < S) {   // GEMM1(i): D1 = U_b V_s^T, terms (hi,hi), (hi,lo), (lo,hi)
-          if (!wait_(B(b_vfull), (uint32_t)(i & 1))) err = 1;
+          if (!wait_(B(b_vfull), (uint32_t)(i & 1))) break;
           // one D1: the epilogue of strip i-1 has read it
-          if (i >= 1 && !wait_(B(b_d1empty), (uint32_t)((i - 1) & 1))) err = 1;
+          if (i >= 1 && !wait_(B(b_d1empty), (uint32_t)((i - 1) & 1))) break;
           tc::fence_after_sync();
           const uint64_t vd = vdesc0;
 #pragma unroll
@@ -333,11 +356,9 @@ __global__ void __launch_bounds__(kFThreads, 1)
         if (i >= 1) {   // GEMM2(i-1): Y = C^T W_hi + C^T W_lo (same columns)
           const int s2 = i - 1, q2 = s2 & 1;
           const int pc = s2 % kNC;
-          if (!wait_(B(b_cfull + pc), (uint32_t)((s2 / kNC) & 1))) err = 1;
+          if (!wait_(B(b_cfull + pc), (uint32_t)((s2 / kNC) & 1))) break;
           // two D2 buffers: the exchange has read the result of strip s2-2
-          if (s2 >= 2 &&
-              !wait_(B(b_d2empty + q2), (uint32_t)(((s2 >> 1) - 1) & 1)))
-            err = 1;
+          if (s2 >= 2 && !wait_(B(b_d2empty + q2), (uint32_t)(((s2 >> 1) - 1) & 1))) break;
           tc::fence_after_sync();
           const int ps = s2 % kNCS;                       // shared-memory C slot
           const uint64_t cd = cdesc0 + (uint64_t)((ps * L::CBYTES) >> 4);
@@ -353,6 +374,9 @@ __global__ void __launch_bounds__(kFThreads, 1)
           tc::mma_commit(B(b_c2free + ps));
         }
       }
+      // completes once every MMA this thread issued has completed (drained
+      // before tensor memory is released when the kernel gave up)
+      tc::mma_commit(B(b_fin1));
     }
   } else if (warp == 2) {
     // ================= MMA issuer: GEMM3 =======================================
@@ -362,11 +386,11 @@ __global__ void __launch_bounds__(kFThreads, 1)
       for (int s3 = 0; s3 < S; ++s3) {   // P_C += C V'_hi^T + C V'_lo^T
         const int p = s3 & 1;
         tc::mbar_arrive_expect_tx(B(b_pfull + p), (uint32_t)L::PBYTES);
-        if (!wait_(B(b_pfull + p), (uint32_t)((s3 >> 1) & 1))) err = 1;
+        if (!wait_(B(b_pfull + p), (uint32_t)((s3 >> 1) & 1))) break;
         const int pc = s3 % kNC;
         // the tensor-memory C tile of the strip was written before its cfull
         // phase (already complete: GEMM2 waited for it before the exchange)
-        if (!wait_(B(b_cfull + pc), (uint32_t)((s3 / kNC) & 1))) err = 1;
+        if (!wait_(B(b_cfull + pc), (uint32_t)((s3 / kNC) & 1))) break;
         tc::fence_proxy_async_smem();
         tc::fence_after_sync();
         const uint64_t pd = pdesc0 + (uint64_t)((p * L::PBYTES) >> 4);
@@ -405,8 +429,7 @@ __global__ void __launch_bounds__(kFThreads, 1)
     };
     if (S > 0) load_v(0);
     for (int ls = 0; ls < S; ++ls) {
-      if (ls >= 1 && !wait_(B(b_vempty), (uint32_t)((ls - 1) & 1)))
-        err = 1;
+      if (ls >= 1 && !wait_w(B(b_vempty), (uint32_t)((ls - 1) & 1))) break;
       uint8_t* img = smem + L::VIMG;
 #pragma unroll
       for (int t = 0; t < V4; ++t) {
@@ -439,15 +462,21 @@ __global__ void __launch_bounds__(kFThreads, 1)
     const float2 inv_lam2 = make_float2(inv_lam, inv_lam);
     const float2 minus_half = make_float2(-0.5f, -0.5f);
     float hub_hi = 0.f, hub_lo = 0.f;
+    bool ok = true;   // warp-uniform; false once a wait of this warp has failed
     for (int ls = 0; ls < S; ++ls) {
-      if (!wait_(B(b_d1full), (uint32_t)(ls & 1))) err = 1;
+      if (!wait_w(B(b_d1full), (uint32_t)(ls & 1))) { ok = false; break; }
       const int pc = ls % kNC, ps = ls % kNCS;
-      // tensor-memory C slot: GEMM3 of strip ls-kNC has completed
-      if (ls >= kNC && !wait_(B(b_cempty + pc), (uint32_t)(((ls / kNC) - 1) & 1)))
-        err = 1;
+      // tensor-memory C slot: GEMM3 of strip ls-kNC has completed (without
+      // this, the tcgen05.st below would race GEMM3's reads of the slot)
+      if (ls >= kNC && !wait_w(B(b_cempty + pc), (uint32_t)(((ls / kNC) - 1) & 1))) {
+        ok = false;
+        break;
+      }
       // shared-memory C slot: GEMM2 of strip ls-kNCS has completed
-      if (ls >= kNCS && !wait_(B(b_c2free + ps), (uint32_t)(((ls / kNCS) - 1) & 1)))
-        err = 1;
+      if (ls >= kNCS && !wait_w(B(b_c2free + ps), (uint32_t)(((ls / kNCS) - 1) & 1))) {
+        ok = false;
+        break;
+      }
       tc::fence_after_sync();
       uint8_t* cbuf = smem + L::CBUF + ps * L::CBYTES;
       const uint32_t tcrow = tcs(pc) + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(rb * 32);
@@ -456,16 +485,20 @@ __global__ void __launch_bounds__(kFThreads, 1)
       // from tensor memory, M from the ring) are in flight while sub-tile q is
       // computed and stored.
       float dv[2][16], mv[2][16];
+      // A failed wait for an M sub-tile leaves garbage in this strip (it is
+      // never handed on) but nothing is issued that could race an MMA: D1 and
+      // both C slots were waited for above.
       auto load_sub = [&](int q, float* d, float* mm) {
         const int g = ls * 4 + q;
         const int rs = g % NST;
-        if (!wait_(B(b_full + rs), (uint32_t)((g / NST) & 1))) err = 1;
+        if (!wait_w(B(b_full + rs), (uint32_t)((g / NST) & 1))) ok = false;
         const float* msub = reinterpret_cast<const float*>(smem + L::RING + rs * kSubBytes);
         tc::tmem_ld16(d1 + ((uint32_t)(quarter * 32) << 16) + rb * kFW + q * kSubCols, d);
 #pragma unroll
         for (int jj = 0; jj < 16; ++jj) mm[jj] = msub[jj * kSubRows + arow];
       };
       auto release_sub = [&](int q) {   // after tcgen05.wait::ld: D1 and M of sub-tile q read
+        if (!ok) return;                // gave up: hand nothing on
         if (q == 3) {   // this warp's last read of D1: GEMM1 of the next strip may start
           tc::fence_before_sync();
           __syncwarp();
@@ -509,15 +542,16 @@ __global__ void __launch_bounds__(kFThreads, 1)
       }
       tc::tmem_st_wait();
       tsum(hub_hi, hub_lo, hub.x + hub.y);
+      if (!ok) break;   // this strip's C tiles are never handed to GEMM2/GEMM3
       tc::fence_before_sync();
       tc::fence_proxy_async_smem();
       __syncwarp();
       if (lane == 0) tc::mbar_arrive(B(b_cfull + pc));
     }
-    // P partial of this cluster's columns (after the last GEMM3)
-    if (!wait_(B(b_last), 0)) err = 1;
-    tc::fence_after_sync();
-    {
+    // P partial of this cluster's columns (after the last GEMM3; its issuer
+    // commits b_last after its final MMA whether or not it gave up)
+    if (ok && wait_w(B(b_last), 0)) {
+      tc::fence_after_sync();
       const int64_t grow = row0 + arow;
       float pv[R];
 #pragma unroll
@@ -558,21 +592,30 @@ __global__ void __launch_bounds__(kFThreads, 1)
       const uint32_t par = (uint32_t)((ls >> 1) & 1);
       const float vz_first = vz_next;
       if (ls + 2 < S) vz_next = vz_of(ls + 2, 0);   // in flight for a whole strip pair
+      // Once the CTA has given up, the loop still runs to its end so that the
+      // group's named barriers stay matched, but every wait returns at once
+      // and nothing guarded by a failed wait is issued (tcgen05.ld, st.async,
+      // remote arrivals).  Each guard is warp-uniform.
       // ---- column sums of this CTA's rows out of tensor memory ----
       const int q2 = ls & 1;                      // D2 buffer of the strip (== grp)
-      if (!wait_(B(b_d2full + q2), (uint32_t)((ls >> 1) & 1))) err = 1;
-      tc::fence_after_sync();
+      const bool d2ok = wait_w(B(b_d2full + q2), (uint32_t)((ls >> 1) & 1));
       float yv[R];
+      if (d2ok) {
+        tc::fence_after_sync();
 #pragma unroll
-      for (int c = 0; c < R; c += 16)
-        tc::tmem_ld16(d2(q2) + ((uint32_t)(xw * 32) << 16) + c, yv + c);
-      tc::tmem_ld_wait();
-      tc::fence_before_sync();
-      __syncwarp();
-      if (lane == 0) tc::mbar_arrive(B(b_d2empty + q2));
+        for (int c = 0; c < R; c += 16)
+          tc::tmem_ld16(d2(q2) + ((uint32_t)(xw * 32) << 16) + c, yv + c);
+        tc::tmem_ld_wait();
+        tc::fence_before_sync();
+        __syncwarp();
+        if (lane == 0) tc::mbar_arrive(B(b_d2empty + q2));
+      } else {
+#pragma unroll
+        for (int c = 0; c < R; ++c) yv[c] = 0.f;
+      }
       // ---- send them to their reducers (every reducer has consumed strip ls-2) ----
-      if (ls >= 2 && !wait_(B(b_yfree + p), par ^ 1u)) err = 1;
-      if (lane < 16) {
+      const bool yfree_ok = (ls < 2 || wait_w(B(b_yfree + p), par ^ 1u)) && d2ok;
+      if (yfree_ok && lane < 16) {
         const int j = xw * 16 + lane;               // strip column of this thread
         const int cc = j / kChunk, owner = cc % cs, ci = cc / cs, jj = j % kChunk;
         const uint32_t off = (uint32_t)(((ci * cs + (int)crank) * kChunk + jj) * R) * 4;
@@ -590,13 +633,14 @@ __global__ void __launch_bounds__(kFThreads, 1)
       }
       // ---- GEMM3 of strip ls-2 done here: its V' image buffer may be refilled ----
       if (ls >= 2 && xw == 0) {
-        if (!wait_(B(b_g3done + p), par ^ 1u)) err = 1;
-        if (lane < cs) tc::mbar_arrive_cluster_relaxed(B(b_pfree + p), (uint32_t)lane);
+        if (wait_w(B(b_g3done + p), par ^ 1u) && lane < cs)
+          tc::mbar_arrive_cluster_relaxed(B(b_pfree + p), (uint32_t)lane);
       }
       // ---- reduce this CTA's chunks of strip ls ----
       if (xt == 0) tc::mbar_arrive_expect_tx(B(b_yfull + p), (uint32_t)L::YBYTES);
       const int64_t col0 = strip_col0(ls);
-      if (!wait_(B(b_yfull + p), par)) err = 1;
+      const bool yfull_ok = wait_w(B(b_yfull + p), par);
+      bool pfree_ok = true;
       for (int ci = 0; ci < nch; ++ci) {
         const int cc = (int)crank + ci * cs;
         float y = ci == 0 ? vz_first : vz_of(ls, ci);
@@ -607,7 +651,7 @@ __global__ void __launch_bounds__(kFThreads, 1)
         if (ci == nch - 1) {
           // every read of this strip's sums is done (the values are in registers)
           tc::named_bar(nb, 128);
-          if (xt < cs) tc::mbar_arrive_cluster_relaxed(B(b_yfree + p), (uint32_t)xt);
+          if (yfull_ok && xt < cs) tc::mbar_arrive_cluster_relaxed(B(b_yfree + p), (uint32_t)xt);
         }
         if (act) {
           const int64_t col = col0 + cc * kChunk + jl;
@@ -622,10 +666,10 @@ __global__ void __launch_bounds__(kFThreads, 1)
           *reinterpret_cast<__half*>(stg + (R + kx) * 8 + jl * 2) = lo;
         }
         // all-gather of the chunk's V' image into every CTA (after their GEMM3 of ls-2)
-        if (ci == 0 && ls >= 2 && !wait_(B(b_pfree + p), par ^ 1u)) err = 1;
+        if (ci == 0 && ls >= 2) pfree_ok = wait_w(B(b_pfree + p), par ^ 1u);
         tc::named_bar(nb, 128);
         const uint8_t* stg = smem + L::STG + grp * (2 * R * kChunk * 2);
-        for (int idx = xt; idx < cs * 2 * R; idx += 128) {
+        for (int idx = xt; pfree_ok && !aborted() && idx < cs * 2 * R; idx += 128) {
           const int p2 = idx / (2 * R), nn = idx % (2 * R);
           const uint2 v = *reinterpret_cast<const uint2*>(stg + nn * 8);
           const uint32_t dst = pbase + (nn >> 3) * (kFW / 8) * 128 + (cc >> 1) * 128 +
@@ -643,12 +687,37 @@ __global__ void __launch_bounds__(kFThreads, 1)
   if (err) atomicExch(a.err, DCF_ETIMEOUT);
   tc::fence_before_sync();
   __syncthreads();
+  // Every role has left its loop, so the flag is final and the same for all
+  // threads.  After an expiry, drain what may still be in flight before the
+  // tensor memory is released and the CTA leaves: the W image copy and the
+  // last TMA load of every ring slot (thread 0 issued them), and the final
+  // commits of both MMA issuers (all of their MMAs have completed).
+  bool tmem_free_ok = true;
+  if (*abort_flag != 0) {
+    const uint64_t dl = tc::globaltimer_ns() + 100000000ull;
+    if (tid == 0) {
+      tc::mbar_wait_deadline(B(b_img), 0, dl);
+      for (int slot = 0; slot < NST && slot < issued; ++slot) {
+        const int g_last = slot + ((issued - 1 - slot) / NST) * NST;
+        tc::mbar_wait_deadline(B(b_full + slot), (uint32_t)((g_last / NST) & 1), dl);
+      }
+    }
+    if (warp == 1) {
+      int drained = 1;
+      if (lane == 0)
+        drained = tc::mbar_wait_deadline(B(b_fin1), 0, dl) &&
+                  tc::mbar_wait_deadline(B(b_last), 0, dl);
+      tmem_free_ok = __shfl_sync(0xffffffffu, drained, 0) != 0;
+    }
+    __syncthreads();
+  }
   if (tid == 0) {
     double t = 0.0;
     for (int w = 0; w < 8; ++w) t += red[w];
     a.part_h[cid * cs + (int)crank] = t;
   }
-  if (warp == 1) tc::tmem_dealloc(tbase, 512);
+  // (if an MMA is still running after all that, the tensor memory stays allocated)
+  if (warp == 1 && tmem_free_ok) tc::tmem_dealloc(tbase, 512);
   tc::cluster_sync();  // no CTA leaves while a peer may still address its shared memory
 }
 

@@ -20,8 +20,13 @@
 // strips g, g + G, g + 2G, ... of its strip group g; P partials are per strip
 // group, column sums per slab.
 //
-// Every wait on an mbarrier is bounded; on expiry the kernel records
-// DCF_ETIMEOUT and runs to completion (tensor memory is always released).
+// Every wait on an mbarrier is bounded.  The first wait that expires raises a
+// CTA-wide abort flag; from then on no role issues another MMA, tcgen05.ld,
+// TMA load or shared-memory write that the expired wait was guarding, and
+// every role leaves its loop.  Before tensor memory is released the MMA
+// issuer's final commit and the TMA loads still in flight are drained with
+// bounded waits; if even that fails the tensor memory is left allocated.  The
+// kernel records DCF_ETIMEOUT.
 #include <cuda.h>
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
@@ -82,7 +87,8 @@ struct TL {
   static constexpr int NBAR = 2 * NST + 2 + 4 + 2 * kTNC + 4 + 2;
   static constexpr int TSLOT = BAR + NBAR * 8;
   static constexpr int RED = TSLOT + 16;                           // 8 doubles
-  static constexpr int TOTAL = RED + 8 * 8;
+  static constexpr int ABRT = RED + 8 * 8;                         // abort flag (int)
+  static constexpr int TOTAL = ABRT + 16;
   // tensor memory (512 columns): D1 2 x 128, U 2R, then D2 2 x R (A) or D3 2R (B)
   static constexpr int T_D1 = 0;
   static constexpr int T_U = 256;
@@ -119,10 +125,21 @@ __global__ void __launch_bounds__(kTThreads, 1)
             b_cempty = b_cfull + kTNC, b_xfull = b_cempty + kTNC, b_xempty = b_xfull + 2,
             b_img = b_xempty + 2, b_last = b_img + 1;
   double* red = reinterpret_cast<double*>(smem + L::RED);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(smem + L::ABRT);
   int err = 0;
   const uint64_t deadline = tc::globaltimer_ns() + kTDeadlineNs;
+  // One thread's bounded wait; on expiry (or once another role has given up)
+  // it raises the abort flag and returns false.
   auto wait_ = [&](uint32_t bar, uint32_t parity) {
-    return tc::mbar_wait_deadline(bar, parity, deadline);
+    if (tc::mbar_wait_or_abort(bar, parity, deadline, abort_flag)) return true;
+    *abort_flag = 1;
+    err = 1;
+    return false;
+  };
+  // The same wait by a whole warp, with one answer for all of its lanes.
+  auto wait_w = [&](uint32_t bar, uint32_t parity) {
+    const bool ok = wait_(bar, parity);
+    return __all_sync(0xffffffffu, ok) != 0;
   };
 
   // ---- set-up ---------------------------------------------------------------
@@ -153,6 +170,7 @@ __global__ void __launch_bounds__(kTThreads, 1)
     }
     tc::mbar_init(B(b_img), 1);
     tc::mbar_init(B(b_last), 1);
+    *abort_flag = 0;
     tc::fence_mbar_init();
     tc::prefetch_tmap(&tmap);
   }
@@ -198,17 +216,21 @@ __global__ void __launch_bounds__(kTThreads, 1)
   tc::fence_after_sync();
 
   constexpr uint32_t SB_R = (R / 8) * 128;    // N-direction core stride of the K=R V image
+  int issued = 0;                             // TMA sub-tile loads issued (thread 0)
+  int mma_drained = 1;                        // the MMA issuer's final commit landed
   if (warp == 0) {
     // ================= TMA producer ==========================================
     if (lane == 0) {
       const int total = S * 4;
       for (int g = 0; g < total; ++g) {
         const int slot = g % NST;
-        if (g >= NST && !wait_(B(b_empty + slot), (uint32_t)((g / NST - 1) & 1))) err = 1;
+        if (g >= NST && !wait_(B(b_empty + slot), (uint32_t)((g / NST - 1) & 1))) break;
+        if (*abort_flag != 0) break;
         const int ls = g >> 2, q = g & 3;
         tc::mbar_arrive_expect_tx(B(b_full + slot), kTSubBytes);
         tc::tma_load_2d(sbase + L::RING + slot * kTSubBytes, &tmap, (int)row0,
                         (int)(strip_col0(ls) + kTSubCols * q), B(b_full + slot));
+        issued = g + 1;
       }
     }
   } else if (warp == 1) {
@@ -216,12 +238,12 @@ __global__ void __launch_bounds__(kTThreads, 1)
     if (lane == 0) {
       const uint32_t idesc1 = tc::idesc_f16(128, kTW, 0, 0);
       const uint64_t vdesc0 = tc::smem_desc(sbase + L::VIMG, 128, SB_R);
-      if (!kB && !wait_(B(b_img), 0)) err = 1;
-      for (int i = 0; i < S + 1; ++i) {
+      const bool img_ok = kB || wait_(B(b_img), 0);
+      for (int i = 0; img_ok && i < S + 1; ++i) {
         if (i < S) {   // GEMM1(i): D1 = U_b V_s^T, terms (hi,hi), (hi,lo), (lo,hi)
           const int p = i & 1;
-          if (!wait_(B(b_vfull), (uint32_t)(i & 1))) err = 1;
-          if (i >= 2 && !wait_(B(b_d1empty + p), (uint32_t)(((i >> 1) - 1) & 1))) err = 1;
+          if (!wait_(B(b_vfull), (uint32_t)(i & 1))) break;
+          if (i >= 2 && !wait_(B(b_d1empty + p), (uint32_t)(((i >> 1) - 1) & 1))) break;
           tc::fence_after_sync();
 #pragma unroll
           for (int b = 0; b < 2; ++b) {
@@ -240,11 +262,11 @@ __global__ void __launch_bounds__(kTThreads, 1)
         }
         if (i >= 1) {
           const int s2 = i - 1, q2 = s2 & 1, pc = s2 % kTNC;
-          if (!wait_(B(b_cfull + pc), (uint32_t)((s2 / kTNC) & 1))) err = 1;
+          if (!wait_(B(b_cfull + pc), (uint32_t)((s2 / kTNC) & 1))) break;
           if (!kB) {
             // GEMM2(s2): Y = C^T W_hi + C^T W_lo; two D2 buffers, the writers
             // have read the result of strip s2 - 2
-            if (s2 >= 2 && !wait_(B(b_xempty + q2), (uint32_t)(((s2 >> 1) - 1) & 1))) err = 1;
+            if (s2 >= 2 && !wait_(B(b_xempty + q2), (uint32_t)(((s2 >> 1) - 1) & 1))) break;
             tc::fence_after_sync();
             const uint32_t idesc2 = tc::idesc_f16(64, R, 1, 0);
             const uint64_t cd = tc::smem_desc(sbase + L::CBUF + pc * L::CBYTES, 128, kTH * 16);
@@ -261,7 +283,7 @@ __global__ void __launch_bounds__(kTThreads, 1)
             tc::mma_commit(B(b_cempty + pc));
           } else {
             // GEMM3(s2): P_C += C V'_hi^T + C V'_lo^T (accumulated over the strips)
-            if (!wait_(B(b_xfull + q2), (uint32_t)((s2 >> 1) & 1))) err = 1;
+            if (!wait_(B(b_xfull + q2), (uint32_t)((s2 >> 1) & 1))) break;
             tc::fence_after_sync();
             const uint32_t idesc3 = tc::idesc_f16(128, R, 0, 0);
             const uint64_t cd = tc::smem_desc(sbase + L::CBUF + pc * L::CBYTES, kTH * 16, 128);
@@ -286,10 +308,16 @@ __global__ void __launch_bounds__(kTThreads, 1)
       }
       // every MMA of this thread has completed (and its commits have landed)
       // before the CTA releases tensor memory and shared memory; pass B's
-      // epilogue also reads the P partial after this
+      // epilogue also reads the P partial after this.  This wait must not give
+      // up because another role did: it drains the MMAs already issued.
       tc::mma_commit(B(b_last));
-      if (!wait_(B(b_last), 0)) err = 1;
+      if (!tc::mbar_wait_deadline(B(b_last), 0, deadline + 100000000ull)) {
+        mma_drained = 0;
+        *abort_flag = 1;
+        err = 1;
+      }
     }
+    mma_drained = __shfl_sync(0xffffffffu, mma_drained, 0);
   } else if (warp == 2 || warp == 3) {
     // ================= V_old image (GEMM1 operand), one strip ahead ============
     // two warps, each a half of the strip's 64 x R floats (kTW * R / 256 float4
@@ -308,7 +336,7 @@ __global__ void __launch_bounds__(kTThreads, 1)
     };
     if (S > 0) load_v(0);
     for (int ls = 0; ls < S; ++ls) {
-      if (ls >= 1 && !wait_(B(b_vempty), (uint32_t)((ls - 1) & 1))) err = 1;
+      if (ls >= 1 && !wait_w(B(b_vempty), (uint32_t)((ls - 1) & 1))) break;
       uint8_t* img = smem + L::VIMG;
 #pragma unroll
       for (int t = 0; t < V4; ++t) {
@@ -337,20 +365,27 @@ __global__ void __launch_bounds__(kTThreads, 1)
     const float inv_uv = 1.f / (s_u * s_v);
     const float inv_lam = 1.f / a.lam;
     float hub_hi = 0.f, hub_lo = 0.f;
+    bool ok = true;   // warp-uniform; false once a wait of this warp has failed
     for (int ls = 0; ls < S; ++ls) {
       const int p = ls & 1, pc = ls % kTNC;
-      if (!wait_(B(b_d1full + p), (uint32_t)((ls >> 1) & 1))) err = 1;
-      if (ls >= kTNC && !wait_(B(b_cempty + pc), (uint32_t)(((ls / kTNC) - 1) & 1))) err = 1;
+      if (!wait_w(B(b_d1full + p), (uint32_t)((ls >> 1) & 1))) { ok = false; break; }
+      // C slot: the GEMM that read it (strip ls - kTNC) has completed
+      if (ls >= kTNC && !wait_w(B(b_cempty + pc), (uint32_t)(((ls / kTNC) - 1) & 1))) {
+        ok = false;
+        break;
+      }
       tc::fence_after_sync();
       uint8_t* cbuf = smem + L::CBUF + pc * L::CBYTES;
       float hub = 0.f;
       // four sub-tiles of 16 columns; the loads of the next are in flight while
       // the current one is computed
       float dv[2][16], mv[2][16];
+      // a failed wait for an M sub-tile leaves garbage in this strip, which is
+      // never handed on
       auto load_sub = [&](int q, float* d, float* mm) {
         const int g = ls * 4 + q;
         const int rs = g % NST;
-        if (!wait_(B(b_full + rs), (uint32_t)((g / NST) & 1))) err = 1;
+        if (!wait_w(B(b_full + rs), (uint32_t)((g / NST) & 1))) ok = false;
         const float* msub = reinterpret_cast<const float*>(smem + L::RING + rs * kTSubBytes);
         tc::tmem_ld16(d1(p) + ((uint32_t)(quarter * 32) << 16) + rb * kTW + q * kTSubCols, d);
 #pragma unroll
@@ -359,7 +394,7 @@ __global__ void __launch_bounds__(kTThreads, 1)
       load_sub(0, dv[0], mv[0]);
       tc::tmem_ld_wait();
       __syncwarp();
-      if (lane == 0) tc::mbar_arrive(B(b_empty + (ls * 4) % NST));
+      if (ok && lane == 0) tc::mbar_arrive(B(b_empty + (ls * 4) % NST));
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
         const int cb = q & 1;
@@ -388,10 +423,11 @@ __global__ void __launch_bounds__(kTThreads, 1)
         if (q < 3) {
           tc::tmem_ld_wait();
           __syncwarp();
-          if (lane == 0) tc::mbar_arrive(B(b_empty + (ls * 4 + q + 1) % NST));
+          if (ok && lane == 0) tc::mbar_arrive(B(b_empty + (ls * 4 + q + 1) % NST));
         }
       }
       if (!kB) ttwo_sum(hub_hi, hub_lo, hub);
+      if (!ok) break;   // this strip's C tile is never handed to a GEMM
       tc::fence_before_sync();
       tc::fence_proxy_async_smem();
       __syncwarp();
@@ -400,9 +436,8 @@ __global__ void __launch_bounds__(kTThreads, 1)
         tc::mbar_arrive(B(b_cfull + pc));
       }
     }
-    if (kB) {
+    if (kB && ok && wait_w(B(b_last), 0)) {
       // P partial of this strip group's columns for the CTA's rows
-      if (!wait_(B(b_last), 0)) err = 1;
       tc::fence_after_sync();
       const int64_t grow = row0 + arow;
       const float ps = a.lam / s_p;
@@ -420,7 +455,7 @@ __global__ void __launch_bounds__(kTThreads, 1)
                       : make_float4(0.f, 0.f, 0.f, 0.f);
         }
       }
-    } else {
+    } else if (!kB) {
       double hsum = ((double)hub_hi + (double)hub_lo) * (double)a.lam * (double)a.lam;
       for (int o = 16; o > 0; o >>= 1) hsum += __shfl_xor_sync(0xffffffffu, hsum, o);
       if (lane == 0) red[warp - 4] = hsum;
@@ -433,7 +468,7 @@ __global__ void __launch_bounds__(kTThreads, 1)
     float* ybase = a.ypart + (int64_t)slab * a.n * R;
     for (int ls = 0; ls < S; ++ls) {
       const int q2 = ls & 1;
-      if (!wait_(B(b_xfull + q2), (uint32_t)((ls >> 1) & 1))) err = 1;
+      if (!wait_w(B(b_xfull + q2), (uint32_t)((ls >> 1) & 1))) break;
       tc::fence_after_sync();
       float yv[R];
 #pragma unroll
@@ -482,7 +517,7 @@ __global__ void __launch_bounds__(kTThreads, 1)
     if (S > 0) load_p(0);
     for (int ls = 0; ls < S; ++ls) {
       const int p = ls & 1;
-      if (ls >= 2 && !wait_(B(b_xempty + p), (uint32_t)(((ls >> 1) - 1) & 1))) err = 1;
+      if (ls >= 2 && !wait_w(B(b_xempty + p), (uint32_t)(((ls >> 1) - 1) & 1))) break;
       uint8_t* img = smem + L::PIMG + p * L::PBYTES;
 #pragma unroll
       for (int u = 0; u < TPT; ++u) {
@@ -522,12 +557,27 @@ __global__ void __launch_bounds__(kTThreads, 1)
   if (err) atomicExch(a.err, DCF_ETIMEOUT);
   tc::fence_before_sync();
   __syncthreads();
+  // Every role has left its loop, so the flag is final and the same for all
+  // threads.  After an expiry, drain the TMA loads thread 0 issued (the W
+  // image and the last load of every ring slot) before the CTA leaves.
+  if (*abort_flag != 0) {
+    if (tid == 0) {
+      const uint64_t dl = tc::globaltimer_ns() + 100000000ull;
+      if (!kB) tc::mbar_wait_deadline(B(b_img), 0, dl);
+      for (int slot = 0; slot < NST && slot < issued; ++slot) {
+        const int g_last = slot + ((issued - 1 - slot) / NST) * NST;
+        tc::mbar_wait_deadline(B(b_full + slot), (uint32_t)((g_last / NST) & 1), dl);
+      }
+    }
+    __syncthreads();
+  }
   if (!kB && tid == 0) {
     double t = 0.0;
     for (int w = 0; w < 8; ++w) t += red[w];
     a.part_h[blockIdx.x] = t;
   }
-  if (warp == 1) tc::tmem_dealloc(tbase, 512);
+  // (if an MMA is still running after all that, the tensor memory stays allocated)
+  if (warp == 1 && mma_drained) tc::tmem_dealloc(tbase, 512);
 }
 
 // V' = V_old Z + sum over the slabs of their column sums (FP32, slabs in
