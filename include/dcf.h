@@ -215,6 +215,22 @@ dcf_status dcf_get_stats(dcf_handle h, double* objective, double* dL_rel, int* i
 dcf_status dcf_set_truth(dcf_handle h, const float* A, const float* B, int k, int where);
 dcf_status dcf_rel_err(dcf_handle h, double* rel_err_L);
 
+/* The relative singular-value error of the upper-bound-rank experiments
+ * (§4.2 "Upper-bound rank recovery", Table 1): with a factor rank r above the
+ * rank k of the truth (r = p = 2k there), max_i |sigma_i(L) - sigma_i(L0)| /
+ * sigma_k(L0), L = U V^T the current iterate and L0 = A B^T the registered
+ * truth (dcf_set_truth), sigma_i = 0 beyond a matrix's rank.
+ * sigma (required): r host doubles, the singular values of L in descending
+ * order.  sigma0 (k host doubles, those of L0) and err may be NULL; asking for
+ * either without a registered truth is DCF_ESTATE.  Computed on the device in
+ * FP64: Gram matrices G_u = U^T U, G_v = V^T V (exact FP32 products, FP64
+ * sums), sigma_i^2 = the eigenvalues of G_u^{1/2} G_v G_u^{1/2} by cyclic
+ * Jacobi rotations; likewise for A, B.  Synchronous.  The factors of the
+ * current iterate are read in place; the handle allocates its work buffers
+ * (partial sums of 64 x 64 doubles for two row ranges per SM, about 10 MB on
+ * a 152-SM GPU) on the first call. */
+dcf_status dcf_singular_values(dcf_handle h, double* sigma, double* sigma0, double* err);
+
 /* (No counterpart in the paper.)  Message of the last failure (or warning) on
  * this handle; never NULL. */
 const char* dcf_last_error(dcf_handle h);

@@ -15,6 +15,8 @@ arXiv 2207.11669) in float64 numpy, in the paper's order and notation:
                    FedAvg gradient mode: Algorithm 1, eqs. ``U_local`` and ``U_agg``
   Huber form       §2.2 eq. ``cancelV`` and App. A.2
   error metric     §4.1 "Evaluation Metric" (squared, L and S together)
+  singular values  §4.2 "Upper-bound rank recovery", Table 1: the relative
+                   singular-value error max_i |sigma_i(L) - sigma_i(L0)| / sigma_r(L0)
 
 Readings of the paper taken here:
   * one alternating S -> V sweep per iteration solves the (V,S) subproblem of
@@ -34,6 +36,7 @@ __all__ = [
     "grad_U_local", "s_step", "v_step", "u_step_exact", "u_step_fedavg",
     "ridge_solve", "init_v0", "dcf_iteration", "dcf_run", "dcf_solve",
     "block_offsets", "factor_delta_rel", "rel_err_L", "paper_err",
+    "singular_values_factored", "singular_value_error",
 ]
 
 
@@ -286,3 +289,27 @@ def paper_err(L, S, L0, S0):
     L, S, L0, S0 = map(_f64, (L, S, L0, S0))
     return float((np.sum((L - L0) ** 2) + np.sum((S - S0) ** 2))
                  / (np.sum(L0 ** 2) + np.sum(S0 ** 2)))
+
+
+def singular_values_factored(X, Y):
+    """Singular values of L = X Y^T (X: N1 x p, Y: N2 x p), descending, from the
+    factors alone: X = Q_x R_x and Y = Q_y R_y (Householder QR), so that
+    L = Q_x (R_x R_y^T) Q_y^T with orthonormal Q's and the singular values of L
+    are those of the p x p matrix R_x R_y^T (an SVD)."""
+    X, Y = _f64(X), _f64(Y)
+    Rx = np.linalg.qr(X, mode="r")
+    Ry = np.linalg.qr(Y, mode="r")
+    return np.linalg.svd(Rx @ Ry.T, compute_uv=False)
+
+
+def singular_value_error(sigma, sigma0, k):
+    """Table 1 of §4.2: max_i |sigma_i(L) - sigma_i(L0)| / sigma_k(L0), with k the
+    rank of L0, over every index either list has (a missing value is 0)."""
+    sigma = np.sort(_f64(sigma))[::-1]
+    sigma0 = np.sort(_f64(sigma0))[::-1]
+    n = max(len(sigma), len(sigma0))
+    a = np.zeros(n)
+    b = np.zeros(n)
+    a[:len(sigma)] = sigma
+    b[:len(sigma0)] = sigma0
+    return float(np.max(np.abs(a - b)) / sigma0[k - 1])

@@ -1032,6 +1032,56 @@ extern "C" dcf_status dcf_set_truth(dcf_handle h, const float* A, const float* B
   return end_work(h);
 }
 
+extern "C" dcf_status dcf_singular_values(dcf_handle h, double* sigma, double* sigma0,
+                                          double* err) {
+  if (!h) return DCF_EINVAL;
+  if (!sigma) return fail(h, DCF_EINVAL, "sigma is NULL");
+  const bool want0 = sigma0 || err;
+  if (want0 && !h->A_truth) return fail(h, DCF_ESTATE, "no truth registered");
+  dcf_status st = begin_work(h);
+  if (st != DCF_OK) return st;
+  if ((st = ensure_init(h)) != DCF_OK) return st;
+  const int nparts = std::max(1, 2 * h->num_sms);
+  if (!h->sv_part) {
+    CK(sv_prepare(), "singular-value kernel attributes");
+    h->sv_part = (double*)dev_alloc(h, sv_part_doubles(nparts) * 8);
+    h->sv_gram = (double*)dev_alloc(h, (size_t)4 * 64 * 64 * 8);
+    h->sv_pdim = (int*)dev_alloc(h, 2 * sizeof(int));
+    h->sv_out = (double*)dev_alloc(h, (size_t)(2 * 64 + 1) * 8);
+    if (!h->sv_part || !h->sv_gram || !h->sv_pdim || !h->sv_out)
+      return fail(h, DCF_ENOMEM, "singular-value buffers");
+  }
+  const int cur = h->host_iter & 1;
+  const int r = h->r, R = h->R, k = h->k_truth;
+  const int nprob = want0 ? 2 : 1;
+  const int pd[2] = {r, want0 ? k : 0};
+  const size_t G = (size_t)64 * 64;
+  // problem 0: L = U V^T (first r columns of the padded factors);
+  // problem 1: L0 = A B^T (the registered truth, rank <= k)
+  CK(launch_gram64(h->U[cur], R, h->U[cur], R, r, h->m, h->sv_part, nparts, h->sv_gram,
+                   h->stream), "gram U");
+  CK(launch_gram64(h->V[cur], R, h->V[cur], R, r, h->n, h->sv_part, nparts, h->sv_gram + G,
+                   h->stream), "gram V");
+  if (want0) {
+    CK(launch_gram64(h->A_truth, k, h->A_truth, k, k, h->m, h->sv_part, nparts,
+                     h->sv_gram + 2 * G, h->stream), "gram A");
+    CK(launch_gram64(h->B_truth, k, h->B_truth, k, k, h->n, h->sv_part, nparts,
+                     h->sv_gram + 3 * G, h->stream), "gram B");
+  }
+  CK(cudaMemcpyAsync(h->sv_pdim, pd, sizeof(pd), cudaMemcpyHostToDevice, h->stream), "pdim");
+  CK(launch_sv_factored(h->sv_gram, h->sv_pdim, nprob, h->sv_out, h->stream), "sv");
+  if (want0) CK(launch_sv_error(h->sv_out, h->sv_out + 64, k, h->sv_out + 128, h->stream),
+                "sv error");
+  double host[2 * 64 + 1];
+  CK(cudaMemcpyAsync(host, h->sv_out, sizeof(host), cudaMemcpyDeviceToHost, h->stream), "copy");
+  CK(cudaStreamSynchronize(h->stream), "sync");
+  for (int i = 0; i < r; ++i) sigma[i] = host[i];
+  if (sigma0)
+    for (int i = 0; i < k; ++i) sigma0[i] = host[64 + i];
+  if (err) *err = host[128];
+  return end_work(h);
+}
+
 extern "C" dcf_status dcf_rel_err(dcf_handle h, double* rel_err_L) {
   if (!h) return DCF_EINVAL;
   if (!h->A_truth) return fail(h, DCF_ESTATE, "no truth registered");

@@ -56,6 +56,10 @@ struct dcf_handle_s {
   double* red = nullptr;             // reduction outputs: q, xv, h, g, xu (R*R each)
   float2* truth_part = nullptr;
   double* truth_red = nullptr;
+  double* sv_part = nullptr;         // singular values: FP64 Gram partials,
+  double* sv_gram = nullptr;         //   [2 problems][G_x, G_y][64 x 64],
+  int* sv_pdim = nullptr;            //   the two problems' ranks,
+  double* sv_out = nullptr;          //   sigma [64], sigma0 [64], error
   dcf::Smalls* sm = nullptr;
   dcf::DevState* st = nullptr;
   unsigned int* counters = nullptr;  // 4 last-block counters

@@ -285,4 +285,15 @@ cudaError_t launch_tc2_vreduce(int R, const float* ypart, int nslabs, const floa
 // shared memory above 48 KB): call once per process before the first launch.
 cudaError_t fused_prep_prepare();
 
+// Singular values of factored matrices X Y^T (k_sv.cu): FP64 Gram matrices,
+// then one warp per problem (cyclic Jacobi).  sv_prepare once per process.
+size_t sv_part_doubles(int nparts);
+cudaError_t sv_prepare();
+cudaError_t launch_gram64(const float* X, int ldx, const float* Y, int ldy, int p, int64_t N,
+                          double* part, int nparts, double* gram_out, cudaStream_t s);
+cudaError_t launch_sv_factored(const double* gram, const int* pdim, int nprob, double* sig,
+                               cudaStream_t s);
+cudaError_t launch_sv_error(const double* sig, const double* sig0, int k, double* err,
+                            cudaStream_t s);
+
 }  // namespace dcf

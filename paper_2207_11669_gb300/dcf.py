@@ -67,6 +67,8 @@ _SIGS = {
                                 C.POINTER(C.c_int)]),
     "dcf_set_truth": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_int]),
     "dcf_rel_err": (C.c_int, [C.c_void_p, C.POINTER(C.c_double)]),
+    "dcf_singular_values": (C.c_int, [C.c_void_p, C.POINTER(C.c_double),
+                                      C.POINTER(C.c_double), C.POINTER(C.c_double)]),
     "dcf_last_error": (C.c_char_p, [C.c_void_p]),
     "dcf_destroy": (None, [C.c_void_p]),
     "dcf_version": (C.c_char_p, []),
@@ -287,6 +289,20 @@ def dcf_rel_err(h):
     return e.value
 
 
+def dcf_singular_values(h, r, k=0):
+    """(sigma (r,), sigma0 (k,) or None, err or None): singular values of the
+    current L = U V^T, and with k > 0 those of the registered truth and the
+    relative singular-value error of Table 1."""
+    sig = (C.c_double * r)()
+    if k > 0:
+        sig0 = (C.c_double * k)()
+        err = C.c_double()
+        _check(h, lib().dcf_singular_values(h, sig, sig0, C.byref(err)))
+        return np.array(sig[:]), np.array(sig0[:]), float(err.value)
+    _check(h, lib().dcf_singular_values(h, sig, None, None))
+    return np.array(sig[:]), None, None
+
+
 def dcf_last_error(h):
     return lib().dcf_last_error(h).decode()
 
@@ -479,6 +495,12 @@ class Solver:
 
     def rel_err(self):
         return dcf_rel_err(self.h)
+
+    def singular_values(self, with_truth=False):
+        """dcf_singular_values: sigma of U V^T, and (with_truth) sigma of the
+        registered truth plus the relative singular-value error of Table 1."""
+        k = self._truth[0].shape[1] if with_truth else 0
+        return dcf_singular_values(self.h, self.r, k)
 
     def unrolled_forward(self, a, b, c, weights=None, want_loss=True):
         return dcf_unrolled_forward(self.h, a, b, c, weights, want_loss)

@@ -143,6 +143,29 @@ def _local_steps_stale_V(M, n_i, U, V, rho, lam, *, u_mode=0, eta=0.0, local_ste
     return sum(Us) / len(Us), np.vstack(Vs), np.hstack(Ss)
 
 
+def _sv_one_factor(X, Y):
+    # forgets the right factor's triangular part
+    return np.linalg.svd(np.linalg.qr(np.asarray(X, float), mode="r"), compute_uv=False)
+
+
+def _sv_error_first(sigma, sigma0, k):
+    # divides by the largest value of L0 instead of the k-th
+    d = np.abs(np.asarray(sigma)[:len(sigma0)] - np.asarray(sigma0)[:len(sigma)])
+    return float(np.max(d) / np.max(sigma0))
+
+
+def _check_sv(fn):
+    g = np.random.default_rng(93)
+    X, Y = g.standard_normal((30, 5)), g.standard_normal((40, 5))
+    d = np.linalg.svd(X @ Y.T, compute_uv=False)[:5]
+    return float(np.max(np.abs(fn(X, Y) - d)) / d[0])
+
+
+def _check_sv_err(fn):
+    return abs(fn([3.0, 2.0, 0.5], [3.0, 2.0], 2) - 0.25) + \
+        abs(fn([3.1, 1.8], [3.0, 2.0, 1.0], 3) - 1.0)
+
+
 CASES = [
     ("s_hard", lambda: pins.check_s_step(_hard_threshold_s_step)),
     ("s_sign", lambda: pins.check_s_step(_flipped_s_step)),
@@ -171,6 +194,8 @@ CASES = [
         _local_steps_average_each_step, K=3)),
     ("local_stale_V", lambda: pins.check_local_steps(
         _local_steps_stale_V, O.local_objective, O.s_step, O.v_step, K=3)),
+    ("sv_one_factor", lambda: _check_sv(_sv_one_factor)),
+    ("sv_error_first", lambda: _check_sv_err(_sv_error_first)),
 ]
 
 

@@ -243,3 +243,33 @@ def test_init_v0_is_v_step_with_zero_S():
     V0 = O.init_v0(M, U, rho)
     G = U.T @ U + rho * np.eye(U.shape[1])
     assert np.max(np.abs(G @ V0.T - U.T @ M)) < 1e-10
+
+
+def test_singular_values_factored_match_dense_svd():
+    """sigma(X Y^T) from the factors equals numpy's SVD of the dense product,
+    also for a rank-deficient product (a zero column pair) and p > rank."""
+    g = np.random.default_rng(91)
+    X, Y = g.standard_normal((30, 6)), g.standard_normal((45, 6))
+    X[:, 5] = 0.0                               # rank 5
+    s = O.singular_values_factored(X, Y)
+    d = np.linalg.svd(X @ Y.T, compute_uv=False)[:6]
+    assert np.max(np.abs(s - d)) < 1e-12 * d[0]
+    assert s[5] < 1e-12 * d[0]
+
+
+def test_singular_values_factored_gauge_invariant():
+    """L = X Y^T = (X T)(Y T^{-T})^T for any invertible T: the same values."""
+    g = np.random.default_rng(92)
+    X, Y = g.standard_normal((20, 4)), g.standard_normal((25, 4))
+    T = g.standard_normal((4, 4)) + 3 * np.eye(4)
+    a = O.singular_values_factored(X, Y)
+    b = O.singular_values_factored(X @ T, Y @ np.linalg.inv(T).T)
+    assert np.max(np.abs(a - b)) < 1e-11 * a[0]
+
+
+def test_singular_value_error_definition():
+    """Table 1's quantity on hand-made lists: the largest gap over all indices
+    (missing values are 0), divided by the k-th value of L0."""
+    assert O.singular_value_error([3.0, 2.0, 0.5], [3.0, 2.0], 2) == 0.25
+    assert O.singular_value_error([3.1, 1.8], [3.0, 2.0, 1.0], 3) == 1.0
+    assert O.singular_value_error([2.0, 1.0], [2.0, 1.0], 2) == 0.0
