@@ -95,6 +95,7 @@ IterArgs iter_args(dcf_handle h, int cur) {
   a.R = h->R;
   a.lam = (float)h->lam;
   a.rho = (float)h->rho;
+  a.rho_q = (float)h->rho_u;
   a.u_mode = h->u_mode;
   a.E = h->E;
   a.U[0] = h->U[0]; a.U[1] = h->U[1];
@@ -472,7 +473,8 @@ extern "C" dcf_status dcf_create(const dcf_params* p, dcf_handle* out) {
   if (p->r < 1 || p->r > kMaxR || p->r > p->m) return bad("r");
   if (!(p->rho > 0) || !(p->lambda > 0)) return bad("rho, lambda");
   if (p->u_mode != 0 && p->u_mode != 1) return bad("u_mode");
-  if (p->local_steps != 1) return bad("local_steps");
+  if (p->local_steps < 1 || (p->local_steps > 1 && p->u_mode != 1)) return bad("local_steps");
+  if (p->local_steps > 1 && p->path == 4) return bad("path");
   if (p->max_iter < 1) return bad("max_iter");
   if (p->path < 0 || p->path > 4) return bad("path");
   h->m = p->m;
@@ -521,10 +523,14 @@ extern "C" dcf_status dcf_create(const dcf_params* p, dcf_handle* out) {
     return DCF_ECUDA;
   }
 
+  // K > 1 local steps: this handle holds the round's U, V and metrics and runs
+  // the server's kernels on the general path's buffers; the clients (created
+  // below, one per block) run the local iterations on the requested path
+  const bool local = p->local_steps > 1;
   // whole solve in one CTA: exact U-step, r <= 16, M and the factors in one
   // SM's shared memory; on request only (the learned network and the FedAvg
   // step run on the multi-kernel paths)
-  {
+  if (!local) {
     const int Rs = pick_R(p->r);
     const bool small_ok = p->u_mode == 0 && p->r <= 16 &&
                           solve_small_smem(Rs, h->m, h->n) + 2048 <= 232448;
@@ -544,7 +550,7 @@ extern "C" dcf_status dcf_create(const dcf_params* p, dcf_handle* out) {
   }
   // fused single-pass path: r <= 32, m a multiple of 4 (TMA row stride), at most
   // 16 slabs of 256 rows per cluster, and the cluster shape must fit on the GPU
-  {
+  if (!local) {
     const bool shape_ok = p->r <= 32 && h->m % 4 == 0 && (h->m + 255) / 256 <= 16;
     if (p->path == 2 && !shape_ok) {
       dcf_destroy(h);
@@ -576,7 +582,7 @@ extern "C" dcf_status dcf_create(const dcf_params* p, dcf_handle* out) {
   // two-pass tensor-core path: any m that is a multiple of 4 (TMA row stride),
   // r <= 64; chosen automatically where the fused path does not apply because
   // of the size (m > 4096 or r > 32)
-  {
+  if (!local) {
     const bool tc2_ok = h->m % 4 == 0;
     if (p->path == 3 && !tc2_ok) {
       dcf_destroy(h);
@@ -677,6 +683,41 @@ extern "C" dcf_status dcf_create(const dcf_params* p, dcf_handle* out) {
     dcf_destroy(h);
     return DCF_ECUDA;
   }
+  if (local) {
+    // one client per block: its own U_i, the block's V_i, the block of M
+    // borrowed from this handle at load, its share rho n_i / n of the ridge
+    // term in the U-step, work ordered on this handle's internal stream
+    dcf_params cp = *p;
+    cp.E = 1;
+    cp.local_steps = 1;
+    cp.u_mode = 1;
+    h->clients.assign(p->E, nullptr);
+    for (int i = 0; i < p->E; ++i) {
+      cp.n_i = &h->n_i[i];
+      dcf_status cst = dcf_create(&cp, &h->clients[i]);
+      if (cst != DCF_OK) {
+        dcf_destroy(h);
+        return cst;
+      }
+      h->clients[i]->rho_u = h->rho * (double)h->n_i[i] / (double)h->n;
+      h->clients[i]->user_stream = h->stream;
+    }
+    h->client_path = h->clients[0]->path;
+    h->loc_uptr = (const float**)dev_alloc(h, (size_t)p->E * sizeof(float*));
+    h->loc_h = (double*)dev_alloc(h, (size_t)p->E * sizeof(double));
+    if (!h->loc_uptr || !h->loc_h) {
+      dcf_destroy(h);
+      return DCF_ENOMEM;
+    }
+    // after its K local steps (started from copy 0) a client's U is in copy K & 1
+    std::vector<const float*> up(p->E);
+    for (int i = 0; i < p->E; ++i) up[i] = h->clients[i]->U[p->local_steps & 1];
+    if (cudaMemcpy(h->loc_uptr, up.data(), up.size() * sizeof(float*),
+                   cudaMemcpyHostToDevice) != cudaSuccess) {
+      dcf_destroy(h);
+      return DCF_ECUDA;
+    }
+  }
   const double mn = (double)h->m * (double)h->n;
   if (h->rho * h->rho > h->lam * h->lam * mn)
     h->err = "warning: rho^2 > lambda^2 m n; the necessary condition for exact recovery fails";
@@ -684,7 +725,10 @@ extern "C" dcf_status dcf_create(const dcf_params* p, dcf_handle* out) {
   return DCF_OK;
 }
 
-extern "C" int dcf_get_path(dcf_handle h) { return h ? h->path : 0; }
+extern "C" int dcf_get_path(dcf_handle h) {
+  if (!h) return 0;
+  return h->clients.empty() ? h->path : h->client_path;
+}
 
 extern "C" dcf_status dcf_set_stream(dcf_handle h, void* stream) {
   if (!h) return DCF_EINVAL;
@@ -802,6 +846,12 @@ extern "C" dcf_status dcf_load_blocks(dcf_handle h, const float* const* M_i, con
   for (int b = 0; b < 2; ++b)
     for (int p = 0; p < 2; ++p)
       if (h->graph[b][p]) { cudaGraphExecDestroy(h->graph[b][p]); h->graph[b][p] = nullptr; }
+  // clients of the local-step mode read their block of this handle's M in place
+  for (int i = 0; i < (int)h->clients.size(); ++i) {
+    const float* blk = h->M + h->c_i[i] * h->m;
+    if ((st = dcf_load_blocks(h->clients[i], &blk, nullptr, 1, 1)) != DCF_OK)
+      return fail(h, st, std::string("client block: ") + dcf_last_error(h->clients[i]));
+  }
   return end_work(h);
 }
 
@@ -829,6 +879,8 @@ extern "C" dcf_status dcf_reload_blocks(dcf_handle h, const float* const* M_i,
 extern "C" dcf_status dcf_reload_blocks_async(dcf_handle h, const float* const* M_i,
                                               const int64_t* ld_i, int where) {
   if (!h) return DCF_EINVAL;
+  if (!h->clients.empty())
+    return fail(h, DCF_EINVAL, "asynchronous reloads are not available with local_steps > 1");
   if (!h->loaded) return fail(h, DCF_ESTATE, "dcf_load_blocks has not been called");
   if (h->M_borrowed)
     return fail(h, DCF_ESTATE, "M is borrowed; write the new values into the borrowed matrix");
@@ -878,12 +930,95 @@ extern "C" dcf_status dcf_load_init(dcf_handle h, const float* U0, const float* 
   return end_work(h);
 }
 
+namespace dcf {
+namespace api {
+
+// One communication round t of Algorithm 1 with K = local_steps > 1 (FedAvg
+// mode), enqueued on h->stream:
+//   every client i starts from the round's U and its block V_i, then runs K
+//   plain iterations of its own block in FedAvg mode with E = 1: S_i, V_i from
+//   its current U_i (§2.2 eq. optS, App. B eq. condition1), then
+//   U_i <- U_i - eta_t (U_i Q_i - P_i + rho (n_i / n) U_i)   (eq. U_local),
+//   eta_t = eta0 / sqrt(t + 1) for all K steps of the round;
+//   the server takes U_t = (1/E) sum_i U_i (eq. U_agg) and V_t = [V_1; ...; V_E].
+// The clients' streams all wait on h->stream and h->stream waits on every
+// client, so the clients of a round run concurrently.  The round's objective
+// is that of the K = 1 case, at (U_{t-1}, V_{t-1}, S from the first local
+// step): every client's first local step computes its Huber sum at
+// (U_{t-1}, V_{i,t-1}).
+dcf_status local_round(dcf_handle h) {
+  const int cur = h->host_iter & 1, nxt = cur ^ 1;
+  const int K = h->local_steps;
+  const double eta = h->eta0 / std::sqrt((double)h->host_iter + 1.0);
+  dcf_status st;
+  for (int i = 0; i < h->E; ++i) {
+    dcf_handle c = h->clients[i];
+    if ((st = begin_work(c)) != DCF_OK) return fail(h, st, dcf_last_error(c));
+    if ((st = apply_pending(c)) != DCF_OK) return fail(h, st, dcf_last_error(c));
+    const int64_t ni = h->n_i[i];
+    CK(cudaMemsetAsync(c->U[0], 0, (size_t)h->m * c->R * 4, c->stream), "client U");
+    CK(cudaMemcpy2DAsync(c->U[0], c->R * 4, h->U[cur], h->R * 4, h->r * 4, h->m,
+                         cudaMemcpyDeviceToDevice, c->stream), "client U");
+    CK(cudaMemsetAsync(c->V[0], 0, (size_t)ni * c->R * 4, c->stream), "client V");
+    CK(cudaMemcpy2DAsync(c->V[0], c->R * 4, h->V[cur] + h->c_i[i] * h->R, h->R * 4, h->r * 4, ni,
+                         cudaMemcpyDeviceToDevice, c->stream), "client V");
+    if ((st = finish_init(c, true)) != DCF_OK) return fail(h, st, dcf_last_error(c));
+    CK(cudaMemcpyAsync(&c->st->eta_fixed, &eta, sizeof(double), cudaMemcpyHostToDevice,
+                       c->stream), "client step size");
+    if ((st = build_graphs(c)) != DCF_OK) return fail(h, st, dcf_last_error(c));
+    for (int k = 0; k < K; ++k) {
+      CK(cudaGraphLaunch(c->graph[c->mcur][c->host_iter & 1], c->stream), "client step");
+      c->host_iter++;
+      if (k == 0)
+        CK(cudaMemcpyAsync(h->loc_h + i, &c->st->huber, sizeof(double),
+                           cudaMemcpyDeviceToDevice, c->stream), "client Huber sum");
+    }
+    if ((st = end_work(c)) != DCF_OK) return fail(h, st, dcf_last_error(c));
+  }
+  for (int i = 0; i < h->E; ++i) {
+    dcf_handle c = h->clients[i];
+    CK(cudaMemcpy2DAsync(h->V[nxt] + h->c_i[i] * h->R, h->R * 4, c->V[K & 1], c->R * 4, h->r * 4,
+                         h->n_i[i], cudaMemcpyDeviceToDevice, h->stream), "V_t");
+  }
+  IterArgs a = iter_args(h, cur);
+  a.part_h = h->loc_h;
+  a.n_vblocks = h->E;
+  CK(launch_avg_rows(a, h->loc_uptr, h->E, h->stream), "average");
+  CK(launch_gram_vv(h->R, h->V[cur], h->V[nxt], h->n, h->part_q, h->part_xv, h->n_vgram, h->st,
+                    h->stream), "gram V");
+  CK(launch_reduce_q(a, red_q(h), red_xv(h), red_h(h), h->n_vgram, h->counters + 0, h->stream),
+     "reduce Q");
+  CK(launch_reduce_g(a, red_g(h), red_xu(h), h->counters + 1, h->stream), "reduce G");
+  h->host_iter++;
+  return DCF_OK;
+}
+
+// A bounded wait that expired inside a client's kernels (DCF_ETIMEOUT).
+dcf_status check_clients(dcf_handle h) {
+  for (dcf_handle c : h->clients) {
+    int kerr = 0;
+    CK(cudaMemcpyAsync(&kerr, c->kerr, sizeof(int), cudaMemcpyDeviceToHost, c->stream), "err");
+    CK(cudaStreamSynchronize(c->stream), "sync");
+    if (kerr == DCF_ETIMEOUT)
+      return fail(h, DCF_ETIMEOUT, "a bounded device-side wait expired in a client's kernels");
+  }
+  return DCF_OK;
+}
+
+}  // namespace api
+}  // namespace dcf
+
 extern "C" dcf_status dcf_step(dcf_handle h, int n_steps) {
   if (!h) return DCF_EINVAL;
   if (n_steps < 0) return fail(h, DCF_EINVAL, "n_steps < 0");
   dcf_status st = begin_work(h);
   if (st != DCF_OK) return st;
   if ((st = ensure_init(h)) != DCF_OK) return st;
+  if (!h->clients.empty()) {   // K > 1 local steps per round
+    for (int i = 0; i < n_steps; ++i)
+      if ((st = local_round(h)) != DCF_OK) return st;
+    return end_work(h);
+  }
   if (h->path == 4) {   // every iteration in one launch of the whole-solve kernel
     if (n_steps > 0) {
       CK(enqueue_small(h, h->host_iter & 1, n_steps, h->stream), "whole solve");
@@ -904,19 +1039,30 @@ extern "C" dcf_status dcf_solve(dcf_handle h, int* iters_out, double* final_dL_r
   dcf_status st = begin_work(h);
   if (st != DCF_OK) return st;
   if ((st = ensure_init(h)) != DCF_OK) return st;
-  if (h->path != 4 && (st = build_graphs(h)) != DCF_OK) return st;
+  const bool local = !h->clients.empty();
+  if (h->path != 4 && !local && (st = build_graphs(h)) != DCF_OK) return st;
   if ((st = set_state_fields(h, 1, h->tol)) != DCF_OK) return st;
   DevState ds{};
   if ((st = read_state(h, &ds)) != DCF_OK) return st;
   const int start = ds.iter;
   int done = 0;
   const int batch = 8;
+  // K > 1 local steps: one round at a time, the stop test read after each
+  for (; local && done < h->max_iter; ++done) {
+    if ((st = local_round(h)) != DCF_OK) return st;
+    if ((st = read_state(h, &ds)) != DCF_OK) return st;
+    if ((st = check_clients(h)) != DCF_OK) return st;
+    if (ds.stop) {
+      ++done;
+      break;
+    }
+  }
   if (h->path == 4) {   // one launch runs until the stop test or max_iter
     CK(enqueue_small(h, h->host_iter & 1, h->max_iter, h->stream), "whole solve");
     if ((st = read_state(h, &ds)) != DCF_OK) return st;
     done = h->max_iter;
   }
-  while (done < h->max_iter) {
+  while (!local && done < h->max_iter) {
     int nb = std::min(batch, h->max_iter - done);
     for (int i = 0; i < nb; ++i) {
       CK(cudaGraphLaunch(h->graph[h->mcur][h->host_iter & 1], h->stream), "graph launch");
@@ -987,8 +1133,17 @@ extern "C" dcf_status dcf_get_LS(dcf_handle h, int i, float* L_i, float* S_i, in
     float* target = where == 0 ? tmp : dst;
     const float* Uu = which == 0 ? h->U[cur] : h->U[prev];
     const float* Vv = which == 0 ? h->V[cur] : h->V[prev];
-    CK(launch_materialize(h->M, h->m, c0, ni, Uu, Vv, h->R, (float)h->lam, which, target,
-                          h->stream), "materialize");
+    if (which == 1 && !h->clients.empty()) {
+      // K > 1 local steps: the S of block i's last local step, from that
+      // step's inputs (the client's copy before its last iteration)
+      dcf_handle c = h->clients[i];
+      const int cp = (c->host_iter & 1) ^ 1;
+      CK(launch_materialize(c->M, h->m, 0, ni, c->U[cp], c->V[cp], c->R, (float)h->lam, 1,
+                            target, h->stream), "materialize");
+    } else {
+      CK(launch_materialize(h->M, h->m, c0, ni, Uu, Vv, h->R, (float)h->lam, which, target,
+                            h->stream), "materialize");
+    }
     if (where == 0)
       CK(cudaMemcpyAsync(dst, tmp, bytes, cudaMemcpyDeviceToHost, h->stream), "copy out");
   }
@@ -1137,6 +1292,8 @@ extern "C" int dcf_profile_phases(dcf_handle h, char* names_csv, int len) {
 
 extern "C" dcf_status dcf_profile_step(dcf_handle h, int n_steps, double* phase_ms) {
   if (!h) return DCF_EINVAL;
+  if (!h->clients.empty())
+    return fail(h, DCF_EINVAL, "per-phase profiling is not available with local_steps > 1");
   if (n_steps < 1 || !phase_ms) return fail(h, DCF_EINVAL, "n_steps < 1 or phase_ms NULL");
   dcf_status st = begin_work(h);
   if (st != DCF_OK) return st;
@@ -1165,6 +1322,8 @@ extern "C" dcf_status dcf_profile_step(dcf_handle h, int n_steps, double* phase_
 extern "C" void dcf_destroy(dcf_handle h) {
   if (!h) return;
   if (h->stream) cudaStreamSynchronize(h->stream);
+  for (dcf_handle c : h->clients) dcf_destroy(c);
+  h->clients.clear();
   free_unrolled(h);
   if (h->side) cudaStreamSynchronize(h->side);
   for (int b = 0; b < 2; ++b)

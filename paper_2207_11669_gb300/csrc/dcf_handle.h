@@ -17,6 +17,8 @@ struct dcf_handle_s {
   int E = 0, r = 0, R = 0;
   double rho = 0, lam = 0, tol = 0, eta0 = 0;
   int max_iter = 0, u_mode = 0, local_steps = 1;
+  double rho_u = 0;                   // rho of the U-step's ridge term when > 0 (a client
+                                      // handle: rho n_i / n); 0: rho
   uint64_t seed = 0;
   std::vector<int64_t> n_i, c_i;
   std::vector<char> priv;
@@ -90,6 +92,12 @@ struct dcf_handle_s {
   float alpha = 1.0f;                 // relaxation of the U-step (learned network)
   float* ustar_out = nullptr;         // when set, the U-step also stores U* here
   UnrolledState* unrolled = nullptr;  // checkpoints and buffers of the learned network
+  // K > 1 local steps of Algorithm 1 (FedAvg mode): one client handle per block,
+  // each iterating on its own block (M borrowed from this handle) with its own U_i
+  std::vector<dcf_handle_s*> clients;
+  int client_path = 0;                // the path the clients' iterations run on
+  const float** loc_uptr = nullptr;   // device array: every client's U after its K steps
+  double* loc_h = nullptr;            // E Huber sums of the clients' first local steps
   std::string err;
 };
 

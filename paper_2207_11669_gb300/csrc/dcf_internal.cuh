@@ -30,6 +30,8 @@ struct DevState {
   double objective;  // objective at (U_{t-1}, V_{t-1}, S_t)
   double dL_rel;     // ||L_t - L_{t-1}||_F / ||L_t||_F
   double huber;      // sum H_lambda(R) of the last pass
+  double eta_fixed;  // FedAvg step size when > 0 (a client's local steps all use the
+                     // step size of their communication round); 0: eta0 / sqrt(t + 1)
 };
 
 // r x r FP64 workspace of one problem.
@@ -50,6 +52,8 @@ struct IterArgs {
   int r, R;
   float lam;
   float rho;
+  float rho_q;       // rho of the U-step's Q + rho I when > 0 (a client's local step:
+                     // its share rho n_i / n of the ridge term); 0: rho
   int u_mode;        // 0 exact, 1 FedAvg
   int E;
   float* U[2];
@@ -166,6 +170,9 @@ cudaError_t launch_gram_vv(int R, const float* Vo, const float* Vn, int64_t N, f
                            float2* part_xv, int nparts, const DevState* st, cudaStream_t s);
 cudaError_t launch_make_w(const IterArgs& a, int copy, int respect_stop, cudaStream_t s);
 cudaError_t launch_rows(const IterArgs& a, cudaStream_t s);
+// U_t = (1/E) sum_i Ui[i] (the server's average of the clients' U after their
+// local steps) with the Gram partials of U_t and U_{t-1}^T U_t, as k_rows.
+cudaError_t launch_avg_rows(const IterArgs& a, const float* const* Ui, int E, cudaStream_t s);
 cudaError_t launch_reduce_q(const IterArgs& a, double* out_q, double* out_xv, double* out_h,
                             int nparts_gram, unsigned int* counter, cudaStream_t s);
 cudaError_t launch_reduce_g(const IterArgs& a, double* out_g, double* out_xu,

@@ -204,10 +204,12 @@ __global__ void __launch_bounds__(kFThreads, 1)
   volatile int* abort_flag = reinterpret_cast<volatile int*>(smem + L::ABRT);
   int err = 0;
   const uint64_t deadline = tc::globaltimer_ns() + kDeadlineNs;
-  // One thread's bounded wait; on expiry (or once another role has given up)
-  // it raises the abort flag and returns false.
+  // One thread's bounded wait; on expiry it raises the abort flag and returns
+  // false.  The deadline is one instant for every role of the launch, so once
+  // one wait has expired every later wait that is not already satisfied fails
+  // at once; the flag stops the roles whose own waits still succeed.
   auto wait_ = [&](uint32_t bar, uint32_t parity) {
-    if (tc::mbar_wait_or_abort(bar, parity, deadline, abort_flag)) return true;
+    if (tc::mbar_wait_deadline(bar, parity, deadline)) return true;
     *abort_flag = 1;
     err = 1;
     return false;
@@ -464,16 +466,15 @@ __global__ void __launch_bounds__(kFThreads, 1)
     float hub_hi = 0.f, hub_lo = 0.f;
     bool ok = true;   // warp-uniform; false once a wait of this warp has failed
     for (int ls = 0; ls < S; ++ls) {
-      if (!wait_w(B(b_d1full), (uint32_t)(ls & 1))) { ok = false; break; }
       const int pc = ls % kNC, ps = ls % kNCS;
-      // tensor-memory C slot: GEMM3 of strip ls-kNC has completed (without
-      // this, the tcgen05.st below would race GEMM3's reads of the slot)
-      if (ls >= kNC && !wait_w(B(b_cempty + pc), (uint32_t)(((ls / kNC) - 1) & 1))) {
-        ok = false;
-        break;
-      }
-      // shared-memory C slot: GEMM2 of strip ls-kNCS has completed
-      if (ls >= kNCS && !wait_w(B(b_c2free + ps), (uint32_t)(((ls / kNCS) - 1) & 1))) {
+      // D1 of the strip, the tensor-memory C slot (GEMM3 of strip ls-kNC has
+      // completed: without this the tcgen05.st below would race GEMM3's reads
+      // of the slot) and the shared-memory C slot (GEMM2 of strip ls-kNCS);
+      // one answer for the warp, which issues warp-wide tcgen05 loads and stores
+      bool w_ok = wait_(B(b_d1full), (uint32_t)(ls & 1));
+      if (w_ok && ls >= kNC) w_ok = wait_(B(b_cempty + pc), (uint32_t)(((ls / kNC) - 1) & 1));
+      if (w_ok && ls >= kNCS) w_ok = wait_(B(b_c2free + ps), (uint32_t)(((ls / kNCS) - 1) & 1));
+      if (!__all_sync(0xffffffffu, w_ok)) {
         ok = false;
         break;
       }
@@ -487,25 +488,26 @@ __global__ void __launch_bounds__(kFThreads, 1)
       float dv[2][16], mv[2][16];
       // A failed wait for an M sub-tile leaves garbage in this strip (it is
       // never handed on) but nothing is issued that could race an MMA: D1 and
-      // both C slots were waited for above.
+      // both C slots were waited for above.  m_ok is this lane's view; lane 0's
+      // decides the arrivals, the warp's vote at the end of the strip the rest.
+      bool m_ok = true;
       auto load_sub = [&](int q, float* d, float* mm) {
         const int g = ls * 4 + q;
         const int rs = g % NST;
-        if (!wait_w(B(b_full + rs), (uint32_t)((g / NST) & 1))) ok = false;
+        if (!wait_(B(b_full + rs), (uint32_t)((g / NST) & 1))) m_ok = false;
         const float* msub = reinterpret_cast<const float*>(smem + L::RING + rs * kSubBytes);
         tc::tmem_ld16(d1 + ((uint32_t)(quarter * 32) << 16) + rb * kFW + q * kSubCols, d);
 #pragma unroll
         for (int jj = 0; jj < 16; ++jj) mm[jj] = msub[jj * kSubRows + arow];
       };
       auto release_sub = [&](int q) {   // after tcgen05.wait::ld: D1 and M of sub-tile q read
-        if (!ok) return;                // gave up: hand nothing on
         if (q == 3) {   // this warp's last read of D1: GEMM1 of the next strip may start
           tc::fence_before_sync();
           __syncwarp();
-          if (lane == 0) tc::mbar_arrive(B(b_d1empty));
+          if (lane == 0 && m_ok) tc::mbar_arrive(B(b_d1empty));
         }
         __syncwarp();
-        if (lane == 0) tc::mbar_arrive(B(b_empty + (ls * 4 + q) % NST));
+        if (lane == 0 && m_ok) tc::mbar_arrive(B(b_empty + (ls * 4 + q) % NST));
       };
       load_sub(0, dv[0], mv[0]);
       tc::tmem_ld_wait();
@@ -542,7 +544,10 @@ __global__ void __launch_bounds__(kFThreads, 1)
       }
       tc::tmem_st_wait();
       tsum(hub_hi, hub_lo, hub.x + hub.y);
-      if (!ok) break;   // this strip's C tiles are never handed to GEMM2/GEMM3
+      if (!__all_sync(0xffffffffu, m_ok)) {   // this strip's C tiles are never handed on
+        ok = false;
+        break;
+      }
       tc::fence_before_sync();
       tc::fence_proxy_async_smem();
       __syncwarp();
@@ -595,7 +600,8 @@ __global__ void __launch_bounds__(kFThreads, 1)
       // Once the CTA has given up, the loop still runs to its end so that the
       // group's named barriers stay matched, but every wait returns at once
       // and nothing guarded by a failed wait is issued (tcgen05.ld, st.async,
-      // remote arrivals).  Each guard is warp-uniform.
+      // remote arrivals).  The guard of the warp-wide tcgen05.ld is the warp's
+      // vote; the others guard per-thread operations.
       // ---- column sums of this CTA's rows out of tensor memory ----
       const int q2 = ls & 1;                      // D2 buffer of the strip (== grp)
       const bool d2ok = wait_w(B(b_d2full + q2), (uint32_t)((ls >> 1) & 1));
@@ -614,7 +620,7 @@ __global__ void __launch_bounds__(kFThreads, 1)
         for (int c = 0; c < R; ++c) yv[c] = 0.f;
       }
       // ---- send them to their reducers (every reducer has consumed strip ls-2) ----
-      const bool yfree_ok = (ls < 2 || wait_w(B(b_yfree + p), par ^ 1u)) && d2ok;
+      const bool yfree_ok = (ls < 2 || wait_(B(b_yfree + p), par ^ 1u)) && d2ok;
       if (yfree_ok && lane < 16) {
         const int j = xw * 16 + lane;               // strip column of this thread
         const int cc = j / kChunk, owner = cc % cs, ci = cc / cs, jj = j % kChunk;
@@ -633,13 +639,13 @@ __global__ void __launch_bounds__(kFThreads, 1)
       }
       // ---- GEMM3 of strip ls-2 done here: its V' image buffer may be refilled ----
       if (ls >= 2 && xw == 0) {
-        if (wait_w(B(b_g3done + p), par ^ 1u) && lane < cs)
+        if (wait_(B(b_g3done + p), par ^ 1u) && lane < cs)
           tc::mbar_arrive_cluster_relaxed(B(b_pfree + p), (uint32_t)lane);
       }
       // ---- reduce this CTA's chunks of strip ls ----
       if (xt == 0) tc::mbar_arrive_expect_tx(B(b_yfull + p), (uint32_t)L::YBYTES);
       const int64_t col0 = strip_col0(ls);
-      const bool yfull_ok = wait_w(B(b_yfull + p), par);
+      const bool yfull_ok = wait_(B(b_yfull + p), par);
       bool pfree_ok = true;
       for (int ci = 0; ci < nch; ++ci) {
         const int cc = (int)crank + ci * cs;
@@ -666,10 +672,11 @@ __global__ void __launch_bounds__(kFThreads, 1)
           *reinterpret_cast<__half*>(stg + (R + kx) * 8 + jl * 2) = lo;
         }
         // all-gather of the chunk's V' image into every CTA (after their GEMM3 of ls-2)
-        if (ci == 0 && ls >= 2) pfree_ok = wait_w(B(b_pfree + p), par ^ 1u);
+        if (ci == 0 && ls >= 2) pfree_ok = wait_(B(b_pfree + p), par ^ 1u);
         tc::named_bar(nb, 128);
         const uint8_t* stg = smem + L::STG + grp * (2 * R * kChunk * 2);
-        for (int idx = xt; pfree_ok && !aborted() && idx < cs * 2 * R; idx += 128) {
+        const bool send = pfree_ok && !aborted();
+        for (int idx = xt; send && idx < cs * 2 * R; idx += 128) {
           const int p2 = idx / (2 * R), nn = idx % (2 * R);
           const uint2 v = *reinterpret_cast<const uint2*>(stg + nn * 8);
           const uint32_t dst = pbase + (nn >> 3) * (kFW / 8) * 128 + (cc >> 1) * 128 +

@@ -264,6 +264,7 @@ struct ReduceArgs {
   int tail;
   int R;
   float rho;
+  float rho_q;             // rho of Q + rho I in the Q tail when > 0, else rho
   int u_mode;
   int copy;                // TAIL_INIT_*: copy written; TAIL_Q/G: copy holding U_{t-1}
   unsigned int* counter;   // last-block counter (starts at 0, reset by the tail)
@@ -378,7 +379,7 @@ __device__ void tail_q(const ReduceArgs& a, double* A, float* F) {
       sm->q[nxt][i] = qv[u];
       sm->xv[i] = xv[u];
       const int r = i / R, c = i % R;
-      const double h = qv[u] + (r == c ? (double)a.rho : 0.0);
+      const double h = qv[u] + (r == c ? (double)(a.rho_q > 0.f ? a.rho_q : a.rho) : 0.0);
       A[i] = h;
       sm->qrho32[i] = (float)h;
     }
@@ -600,7 +601,8 @@ __device__ __forceinline__ void rows_block(const IterArgs& a, int64_t rb) {
     for (int l = 0; l < CG; ++l) acc[l] = fmaf(v, Mat[k * R + g * CG + l], acc[l]);
   }
   if (a.u_mode != 0) {
-    const double eta = st->eta0 / sqrt((double)st->iter + 1.0);
+    const double eta =
+        st->eta_fixed > 0.0 ? st->eta_fixed : st->eta0 / sqrt((double)st->iter + 1.0);
     const float step = (float)(eta / (double)a.E);
 #pragma unroll
     for (int l = 0; l < CG; ++l) {
@@ -648,6 +650,53 @@ template <int R>
 __global__ void __launch_bounds__(256) k_rows(IterArgs a) {
   if (a.st->stop) return;
   rows_block<R>(a, blockIdx.x);
+}
+
+// The server's step of Algorithm 1 (eq. U_agg) after the clients' local steps:
+// U_t[a,:] = (1/E) sum_i Ui[i][a,:], the clients summed in order, plus the
+// Gram partials G = U_t^T U_t and X_u = U_{t-1}^T U_t of the 32-row block, as
+// the consensus rows kernel leaves them for the metrics.
+template <int R>
+__global__ void __launch_bounds__(256) k_avg_rows(IterArgs a, const float* const* __restrict__ Ui,
+                                                  int E) {
+  if (a.st->stop) return;
+  __shared__ __align__(16) float Uo[kRowsPerCta * R];
+  __shared__ __align__(16) float Un[kRowsPerCta * R];
+  const int tid = threadIdx.x;
+  const int64_t rb = blockIdx.x;
+  const float* U = a.U[a.cur];
+  float* Unew = a.U[a.cur ^ 1];
+  const int64_t row0 = rb * kRowsPerCta;
+  const int rows = (int)dmin64((int64_t)kRowsPerCta, a.m - row0);
+  const float invE = 1.f / (float)E;
+  bool finite = true;
+  for (int i = tid; i < kRowsPerCta * R; i += 256) {
+    const int rr = i / R;
+    float uo = 0.f, un = 0.f;
+    if (rr < rows) {
+      const int64_t off = row0 * R + i;
+      uo = U[off];
+      float hi = 0.f, lo = 0.f;
+      for (int c = 0; c < E; ++c) two_sum_add(hi, lo, Ui[c][off]);
+      un = (hi + lo) * invE;
+      finite = finite && isfinite(un);
+      Unew[off] = un;
+    }
+    Uo[i] = uo;
+    Un[i] = un;
+  }
+  if (!finite) a.st->status = 4;
+  __syncthreads();
+  for (int e = tid; e < R * R; e += 256) {
+    const int k = e / R, l = e % R;
+    float gg = 0.f, xu = 0.f;
+    for (int rr = 0; rr < rows; ++rr) {
+      gg = fmaf(Un[rr * R + k], Un[rr * R + l], gg);
+      xu = fmaf(Uo[rr * R + k], Un[rr * R + l], xu);
+    }
+    a.part_g[rb * R * R + e] = make_float2(gg, 0.f);
+    a.part_xu[rb * R * R + e] = make_float2(xu, 0.f);
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -923,6 +972,16 @@ cudaError_t launch_rows(const IterArgs& a, cudaStream_t s) {
   }
 }
 
+cudaError_t launch_avg_rows(const IterArgs& a, const float* const* Ui, int E, cudaStream_t s) {
+  switch (a.R) {
+    case 8: k_avg_rows<8><<<a.n_rblocks, 256, 0, s>>>(a, Ui, E); break;
+    case 16: k_avg_rows<16><<<a.n_rblocks, 256, 0, s>>>(a, Ui, E); break;
+    case 32: k_avg_rows<32><<<a.n_rblocks, 256, 0, s>>>(a, Ui, E); break;
+    default: k_avg_rows<64><<<a.n_rblocks, 256, 0, s>>>(a, Ui, E); break;
+  }
+  return cudaGetLastError();
+}
+
 // reduction of V-side partials (Q_t, V_{t-1}^T V_t, Huber) + Cholesky(Q_t + rho I)
 cudaError_t launch_reduce_q(const IterArgs& a, double* out_q, double* out_xv, double* out_h,
                             int nparts_gram, unsigned int* counter, cudaStream_t s) {
@@ -934,7 +993,7 @@ cudaError_t launch_reduce_q(const IterArgs& a, double* out_q, double* out_xv, do
   ra.total = 2 * RR + 1;
   ra.tail = TAIL_Q;
   ra.copy = a.cur;
-  ra.R = a.R; ra.rho = a.rho; ra.u_mode = a.u_mode;
+  ra.R = a.R; ra.rho = a.rho; ra.rho_q = a.rho_q; ra.u_mode = a.u_mode;
   ra.counter = counter; ra.sm = a.sm; ra.st = a.st;
   return launch_reduce(ra, s);
 }

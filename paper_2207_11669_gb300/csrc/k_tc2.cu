@@ -128,10 +128,12 @@ __global__ void __launch_bounds__(kTThreads, 1)
   volatile int* abort_flag = reinterpret_cast<volatile int*>(smem + L::ABRT);
   int err = 0;
   const uint64_t deadline = tc::globaltimer_ns() + kTDeadlineNs;
-  // One thread's bounded wait; on expiry (or once another role has given up)
-  // it raises the abort flag and returns false.
+  // One thread's bounded wait; on expiry it raises the abort flag and returns
+  // false.  The deadline is one instant for every role of the launch, so once
+  // one wait has expired every later wait that is not already satisfied fails
+  // at once; the flag stops the roles whose own waits still succeed.
   auto wait_ = [&](uint32_t bar, uint32_t parity) {
-    if (tc::mbar_wait_or_abort(bar, parity, deadline, abort_flag)) return true;
+    if (tc::mbar_wait_deadline(bar, parity, deadline)) return true;
     *abort_flag = 1;
     err = 1;
     return false;

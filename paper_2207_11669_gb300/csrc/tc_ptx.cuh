@@ -202,20 +202,6 @@ __device__ __forceinline__ bool mbar_wait_deadline(uint32_t mbar, uint32_t parit
     if (globaltimer_ns() > deadline) return false;
   }
 }
-// The same wait, which also gives up as soon as another thread of the CTA has
-// raised the CTA's abort flag (a word in shared memory): once one wait of a
-// warp-specialised kernel has expired, the others stop waiting for work that
-// will not come.
-__device__ __forceinline__ bool mbar_wait_or_abort(uint32_t mbar, uint32_t parity,
-                                                   uint64_t deadline,
-                                                   const volatile int* abort_flag) {
-  for (;;) {
-    if (mbar_try_wait(mbar, parity)) return true;
-    if (*abort_flag != 0) return false;
-    if (globaltimer_ns() > deadline) return false;
-  }
-}
-
 // --- TMA ------------------------------------------------------------------------
 __device__ __forceinline__ void tma_load_2d(uint32_t dst, const void* tmap, int x, int y,
                                             uint32_t mbar) {

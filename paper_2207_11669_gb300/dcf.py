@@ -401,10 +401,11 @@ class Solver:
     """
 
     def __init__(self, m, n_i, r, rho, lam, max_iter=100, tol=1e-6, u_mode=0, eta0=0.0,
-                 seed=0, stream=None, path=PATH_AUTO):
+                 seed=0, stream=None, path=PATH_AUTO, local_steps=1):
         self.m, self.n_i, self.r = int(m), [int(x) for x in n_i], int(r)
         self.n = int(sum(self.n_i))
-        self.h = dcf_create(m, n_i, r, rho, lam, max_iter, tol, u_mode, 1, eta0, seed, path)
+        self.h = dcf_create(m, n_i, r, rho, lam, max_iter, tol, u_mode, local_steps, eta0, seed,
+                            path)
         if stream is not None:
             dcf_set_stream(self.h, stream)
         self._keep = None
