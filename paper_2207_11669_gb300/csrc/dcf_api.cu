@@ -983,7 +983,7 @@ dcf_status local_round(dcf_handle h) {
   IterArgs a = iter_args(h, cur);
   a.part_h = h->loc_h;
   a.n_vblocks = h->E;
-  CK(launch_avg_rows(a, h->loc_uptr, h->E, h->stream), "average");
+  CK(launch_avg_rows(a, h->loc_uptr, h->E, h->clients[0]->R, h->stream), "average");
   CK(launch_gram_vv(h->R, h->V[cur], h->V[nxt], h->n, h->part_q, h->part_xv, h->n_vgram, h->st,
                     h->stream), "gram V");
   CK(launch_reduce_q(a, red_q(h), red_xv(h), red_h(h), h->n_vgram, h->counters + 0, h->stream),

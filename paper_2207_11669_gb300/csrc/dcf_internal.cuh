@@ -171,8 +171,10 @@ cudaError_t launch_gram_vv(int R, const float* Vo, const float* Vn, int64_t N, f
 cudaError_t launch_make_w(const IterArgs& a, int copy, int respect_stop, cudaStream_t s);
 cudaError_t launch_rows(const IterArgs& a, cudaStream_t s);
 // U_t = (1/E) sum_i Ui[i] (the server's average of the clients' U after their
-// local steps) with the Gram partials of U_t and U_{t-1}^T U_t, as k_rows.
-cudaError_t launch_avg_rows(const IterArgs& a, const float* const* Ui, int E, cudaStream_t s);
+// local steps; client rows of ldc >= R floats) with the Gram partials of U_t
+// and U_{t-1}^T U_t, as k_rows.
+cudaError_t launch_avg_rows(const IterArgs& a, const float* const* Ui, int E, int ldc,
+                            cudaStream_t s);
 cudaError_t launch_reduce_q(const IterArgs& a, double* out_q, double* out_xv, double* out_h,
                             int nparts_gram, unsigned int* counter, cudaStream_t s);
 cudaError_t launch_reduce_g(const IterArgs& a, double* out_g, double* out_xu,

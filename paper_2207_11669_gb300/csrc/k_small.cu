@@ -655,10 +655,11 @@ __global__ void __launch_bounds__(256) k_rows(IterArgs a) {
 // The server's step of Algorithm 1 (eq. U_agg) after the clients' local steps:
 // U_t[a,:] = (1/E) sum_i Ui[i][a,:], the clients summed in order, plus the
 // Gram partials G = U_t^T U_t and X_u = U_{t-1}^T U_t of the 32-row block, as
-// the consensus rows kernel leaves them for the metrics.
+// the consensus rows kernel leaves them for the metrics.  The clients' rows
+// have ldc >= R entries (their own padded rank); columns past R are zero.
 template <int R>
 __global__ void __launch_bounds__(256) k_avg_rows(IterArgs a, const float* const* __restrict__ Ui,
-                                                  int E) {
+                                                  int E, int ldc) {
   if (a.st->stop) return;
   __shared__ __align__(16) float Uo[kRowsPerCta * R];
   __shared__ __align__(16) float Un[kRowsPerCta * R];
@@ -675,9 +676,10 @@ __global__ void __launch_bounds__(256) k_avg_rows(IterArgs a, const float* const
     float uo = 0.f, un = 0.f;
     if (rr < rows) {
       const int64_t off = row0 * R + i;
+      const int64_t offc = (row0 + rr) * ldc + (i % R);
       uo = U[off];
       float hi = 0.f, lo = 0.f;
-      for (int c = 0; c < E; ++c) two_sum_add(hi, lo, Ui[c][off]);
+      for (int c = 0; c < E; ++c) two_sum_add(hi, lo, Ui[c][offc]);
       un = (hi + lo) * invE;
       finite = finite && isfinite(un);
       Unew[off] = un;
@@ -972,12 +974,14 @@ cudaError_t launch_rows(const IterArgs& a, cudaStream_t s) {
   }
 }
 
-cudaError_t launch_avg_rows(const IterArgs& a, const float* const* Ui, int E, cudaStream_t s) {
+cudaError_t launch_avg_rows(const IterArgs& a, const float* const* Ui, int E, int ldc,
+                            cudaStream_t s) {
+  if (ldc < a.R) return cudaErrorInvalidValue;
   switch (a.R) {
-    case 8: k_avg_rows<8><<<a.n_rblocks, 256, 0, s>>>(a, Ui, E); break;
-    case 16: k_avg_rows<16><<<a.n_rblocks, 256, 0, s>>>(a, Ui, E); break;
-    case 32: k_avg_rows<32><<<a.n_rblocks, 256, 0, s>>>(a, Ui, E); break;
-    default: k_avg_rows<64><<<a.n_rblocks, 256, 0, s>>>(a, Ui, E); break;
+    case 8: k_avg_rows<8><<<a.n_rblocks, 256, 0, s>>>(a, Ui, E, ldc); break;
+    case 16: k_avg_rows<16><<<a.n_rblocks, 256, 0, s>>>(a, Ui, E, ldc); break;
+    case 32: k_avg_rows<32><<<a.n_rblocks, 256, 0, s>>>(a, Ui, E, ldc); break;
+    default: k_avg_rows<64><<<a.n_rblocks, 256, 0, s>>>(a, Ui, E, ldc); break;
   }
   return cudaGetLastError();
 }
