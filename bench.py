@@ -659,6 +659,61 @@ def run_batched(args):
     return 0
 
 
+def run_phase(args):
+    """The sparsity x rank sweep of §4.2 (phase-transition figure): every cell
+    (truth rank 0.05n .. 0.2n, density 0.05 .. 0.3, m = n = 160) is one problem
+    of a single dcf_batch, solved together to a relative change of 1e-6 (at
+    most 500 iterations).  value = cells solved per second; the line carries
+    the relative error of L against the planted L* per cell."""
+    import torch
+    from paper_2207_11669_gb300 import dcf
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    cells = synth.phase_grid(trials=args.phase_trials)
+    probs = [dict(m=c["m"], n_i=c["n_i"], r=c["r"], rho=c["rho"], lam=c["lam"]) for c in cells]
+    stream = torch.cuda.current_stream()
+    b = dcf.Batch(probs, max_iter=500, tol=1e-6, seed=3, stream=stream.cuda_stream)
+    insts = []
+    for q, c in enumerate(cells):
+        inst = synth.make_instance(c["m"], c["n"], c["k"], seed=c["seed"], density=c["density"],
+                                   amp=c["amp"], factor_std=c["factor_std"], n_i=c["n_i"])
+        b.load(q, inst.M)
+        b.load_init(q, synth.gaussian_u0(c["m"], c["r"], c["seed"]))   # V0: the S = 0 sweep
+        insts.append(inst)
+    torch.cuda.synchronize()
+    w0 = time.perf_counter()
+    its, nconv = b.solve()
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - w0
+    grid = {}
+    for q, (c, inst) in enumerate(zip(cells, insts)):
+        U, V = b.factors(q)
+        a = U.astype(np.float64).T @ U.astype(np.float64)
+        bb = V.astype(np.float64).T @ V.astype(np.float64)
+        x = U.astype(np.float64).T @ inst.A.astype(np.float64)
+        y = V.astype(np.float64).T @ inst.B.astype(np.float64)
+        g0 = (inst.A.astype(np.float64).T @ inst.A) * (inst.B.astype(np.float64).T @ inst.B)
+        e2 = max(0.0, float(np.sum(a * bb) - 2 * np.sum(x * y) + np.sum(g0)))
+        key = f"r={c['cell'][0]:.3f}n,s={c['cell'][1]:.2f}"
+        grid.setdefault(key, []).append(round(float(np.sqrt(e2 / np.sum(g0))), 5))
+    b.close()
+    if rank == 0:
+        line = {"metric": METRIC, "value": len(cells) / wall, "unit": "phase cells/s",
+                "n_gpus": world, "steps": 1, "warmup": 0, "ms_per_step": wall * 1e3,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": "f32", "data": "synthetic",
+                "config": {"workload": f"phase_m{synth.PHASE_N}_n{synth.PHASE_N}",
+                           "cells": len(cells), "trials": args.phase_trials,
+                           "ranks": list(synth.PHASE_RANKS),
+                           "densities": list(synth.PHASE_DENSITIES),
+                           "stop": "relative change <= 1e-6 or 500 iterations",
+                           "l2": "every problem (100 KiB) stays in L2"},
+                "iterations": its, "converged": nconv, "rel_err_L": grid,
+                "e2e": None, "cpu_baseline": None}
+        print(json.dumps(line), flush=True)
+    return 0
+
+
 def learned_rows(dcf, torch, args, rank, stream, count):
     """Per held-out problem of the learned workload: plain iterations and the
     network plus plain refinement to 1e-4 of the plain fixed point, and the
@@ -768,11 +823,13 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="medium",
-                    choices=["medium", "small", "large", "batched", "learned"])
+                    choices=["medium", "small", "large", "batched", "learned", "phase"])
     ap.add_argument("--learned-count", type=int, default=8,
                     help="held-out problems of the learned workload")
     ap.add_argument("--batch-count", type=int, default=512,
                     help="instances of the batched workload")
+    ap.add_argument("--phase-trials", type=int, default=1,
+                    help="seeded instances per cell of the phase sweep")
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle baseline leg")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end leg")
     ap.add_argument("--no-extras", action="store_true",
@@ -788,6 +845,8 @@ def main():
         return run_batched(args)
     if args.workload == "learned":
         return run_learned(args)
+    if args.workload == "phase":
+        return run_phase(args)
     return run_ours(args)
 
 

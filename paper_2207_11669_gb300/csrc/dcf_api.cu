@@ -103,6 +103,7 @@ IterArgs iter_args(dcf_handle h, int cur) {
   a.W = h->W;
   a.part_q = h->part_q;
   a.part_xv = h->part_xv;
+  a.part_dv = h->part_dv;
   a.part_h = h->part_h;
   a.part_p = h->part_p;
   a.n_vblocks = h->n_vblocks;
@@ -110,6 +111,7 @@ IterArgs iter_args(dcf_handle h, int cur) {
   a.split_cols = h->split_cols;
   a.part_g = h->part_g;
   a.part_xu = h->part_xu;
+  a.part_du = h->part_du;
   a.n_rblocks = h->n_rblocks;
   a.sm = h->sm;
   a.st = h->st;
@@ -128,11 +130,14 @@ IterArgs iter_args(dcf_handle h, int cur) {
   return a;
 }
 
+// reduction outputs: Q, V-side cross, dV Gram, Huber (8), G, U-side cross, dU Gram
 double* red_q(dcf_handle h) { return h->red; }
 double* red_xv(dcf_handle h) { return h->red + (size_t)h->R * h->R; }
-double* red_h(dcf_handle h) { return h->red + 2 * (size_t)h->R * h->R; }
-double* red_g(dcf_handle h) { return h->red + 2 * (size_t)h->R * h->R + 8; }
-double* red_xu(dcf_handle h) { return h->red + 3 * (size_t)h->R * h->R + 8; }
+double* red_dv(dcf_handle h) { return h->red + 2 * (size_t)h->R * h->R; }
+double* red_h(dcf_handle h) { return h->red + 3 * (size_t)h->R * h->R; }
+double* red_g(dcf_handle h) { return h->red + 3 * (size_t)h->R * h->R + 8; }
+double* red_xu(dcf_handle h) { return h->red + 4 * (size_t)h->R * h->R + 8; }
+double* red_du(dcf_handle h) { return h->red + 5 * (size_t)h->R * h->R + 8; }
 
 // Phases of one iteration, in launch order (names used by dcf_profile_*).
 const char* const kPhaseNames[] = {"make_w", "pass1_vstep", "pass2_pstep", "gram_v",
@@ -212,16 +217,16 @@ cudaError_t enqueue_fused_iteration(dcf_handle h, int cur, cudaStream_t s, cudaE
   if ((e = launch_fused(h->R, h->tmap, fa, s)) != cudaSuccess || (e = mark()) != cudaSuccess)
     return e;
   // Q_t = V_t^T V_t and V_{t-1}^T V_t from the new V (Gram partials)
-  if ((e = launch_gram_vv(h->R, h->V[cur], h->V[nxt], h->n, h->part_q, h->part_xv, h->n_vgram,
+  if ((e = launch_gram_vv(h->R, h->V[cur], h->V[nxt], h->n, h->part_q, h->part_xv, h->part_dv, h->n_vgram,
                           h->st, s)) != cudaSuccess ||
       (e = mark()) != cudaSuccess)
     return e;
-  if ((e = launch_reduce_q(a, red_q(h), red_xv(h), red_h(h), h->n_vgram, h->counters + 0, s)) !=
+  if ((e = launch_reduce_q(a, red_q(h), red_xv(h), red_dv(h), red_h(h), h->n_vgram, h->counters + 0, s)) !=
           cudaSuccess ||
       (e = mark()) != cudaSuccess)
     return e;
   if ((e = launch_rows(a, s)) != cudaSuccess || (e = mark()) != cudaSuccess) return e;
-  if ((e = launch_reduce_g(a, red_g(h), red_xu(h), h->counters + 1, s)) != cudaSuccess) return e;
+  if ((e = launch_reduce_g(a, red_g(h), red_xu(h), red_du(h), h->counters + 1, s)) != cudaSuccess) return e;
   return mark();
 }
 
@@ -265,18 +270,18 @@ cudaError_t enqueue_tc2_iteration(dcf_handle h, int cur, cudaStream_t s, cudaEve
                               h->vmax + nxt, h->st, h->num_sms, s)) != cudaSuccess ||
       (e = mark()) != cudaSuccess)
     return e;
-  if ((e = launch_gram_vv(h->R, h->V[cur], h->V[nxt], h->n, h->part_q, h->part_xv, h->n_vgram,
+  if ((e = launch_gram_vv(h->R, h->V[cur], h->V[nxt], h->n, h->part_q, h->part_xv, h->part_dv, h->n_vgram,
                           h->st, s)) != cudaSuccess ||
       (e = mark()) != cudaSuccess)
     return e;
-  if ((e = launch_reduce_q(a, red_q(h), red_xv(h), red_h(h), h->n_vgram, h->counters + 0, s)) !=
+  if ((e = launch_reduce_q(a, red_q(h), red_xv(h), red_dv(h), red_h(h), h->n_vgram, h->counters + 0, s)) !=
           cudaSuccess ||
       (e = mark()) != cudaSuccess)
     return e;
   if ((e = launch_tc2(h->R, 1, h->tmap, ta, s)) != cudaSuccess || (e = mark()) != cudaSuccess)
     return e;
   if ((e = launch_rows(a, s)) != cudaSuccess || (e = mark()) != cudaSuccess) return e;
-  if ((e = launch_reduce_g(a, red_g(h), red_xu(h), h->counters + 1, s)) != cudaSuccess) return e;
+  if ((e = launch_reduce_g(a, red_g(h), red_xu(h), red_du(h), h->counters + 1, s)) != cudaSuccess) return e;
   return mark();
 }
 
@@ -305,18 +310,18 @@ cudaError_t enqueue_iteration(dcf_handle h, int cur, cudaStream_t s, cudaEvent_t
   // U-step numerator P = X V' (second pass over M)
   if ((e = launch_pass2(a, s)) != cudaSuccess || (e = mark()) != cudaSuccess) return e;
   // Q_t = V_t^T V_t and V_{t-1}^T V_t
-  if ((e = launch_gram_vv(h->R, h->V[cur], h->V[nxt], h->n, h->part_q, h->part_xv, h->n_vgram,
+  if ((e = launch_gram_vv(h->R, h->V[cur], h->V[nxt], h->n, h->part_q, h->part_xv, h->part_dv, h->n_vgram,
                           h->st, s)) != cudaSuccess ||
       (e = mark()) != cudaSuccess)
     return e;
-  if ((e = launch_reduce_q(a, red_q(h), red_xv(h), red_h(h), h->n_vgram, h->counters + 0, s)) !=
+  if ((e = launch_reduce_q(a, red_q(h), red_xv(h), red_dv(h), red_h(h), h->n_vgram, h->counters + 0, s)) !=
           cudaSuccess ||
       (e = mark()) != cudaSuccess)
     return e;
   // consensus U-update + Gram partials of U_t
   if ((e = launch_rows(a, s)) != cudaSuccess || (e = mark()) != cudaSuccess) return e;
   // U_t^T U_t, metrics, stop test, (U_t^T U_t + rho I)^{-1} for the next V-step
-  if ((e = launch_reduce_g(a, red_g(h), red_xu(h), h->counters + 1, s)) != cudaSuccess) return e;
+  if ((e = launch_reduce_g(a, red_g(h), red_xu(h), red_du(h), h->counters + 1, s)) != cudaSuccess) return e;
   return mark();
 }
 
@@ -639,9 +644,11 @@ extern "C" dcf_status dcf_create(const dcf_params* p, dcf_handle* out) {
   size_t ngp = std::max<size_t>(h->n_vgram, h->n_rblocks);
   h->part_q = (float2*)A(ngp * RR * 8);
   h->part_xv = (float2*)A((size_t)h->n_vgram * RR * 8);
+  h->part_dv = (float2*)A((size_t)h->n_vgram * RR * 8);
   h->part_g = (float2*)A(ngp * RR * 8);
   h->part_xu = (float2*)A((size_t)h->n_rblocks * RR * 8);
-  h->red = (double*)A((4 * RR + 8) * 8);
+  h->part_du = (float2*)A((size_t)h->n_rblocks * RR * 8);
+  h->red = (double*)A((6 * RR + 8) * 8);
   h->sm = (Smalls*)A(sizeof(Smalls));
   h->st = (DevState*)A(sizeof(DevState));
   h->counters = (unsigned int*)A(4 * sizeof(unsigned int));
@@ -984,11 +991,11 @@ dcf_status local_round(dcf_handle h) {
   a.part_h = h->loc_h;
   a.n_vblocks = h->E;
   CK(launch_avg_rows(a, h->loc_uptr, h->E, h->clients[0]->R, h->stream), "average");
-  CK(launch_gram_vv(h->R, h->V[cur], h->V[nxt], h->n, h->part_q, h->part_xv, h->n_vgram, h->st,
+  CK(launch_gram_vv(h->R, h->V[cur], h->V[nxt], h->n, h->part_q, h->part_xv, h->part_dv, h->n_vgram, h->st,
                     h->stream), "gram V");
-  CK(launch_reduce_q(a, red_q(h), red_xv(h), red_h(h), h->n_vgram, h->counters + 0, h->stream),
+  CK(launch_reduce_q(a, red_q(h), red_xv(h), red_dv(h), red_h(h), h->n_vgram, h->counters + 0, h->stream),
      "reduce Q");
-  CK(launch_reduce_g(a, red_g(h), red_xu(h), h->counters + 1, h->stream), "reduce G");
+  CK(launch_reduce_g(a, red_g(h), red_xu(h), red_du(h), h->counters + 1, h->stream), "reduce G");
   h->host_iter++;
   return DCF_OK;
 }

@@ -181,9 +181,11 @@ void layout_instance(Arena& ar, BInst& I) {
   I.part_h = ar.take<double>((size_t)std::max(I.n_strips, I.nslabs));
   I.part_q = ar.take<float2>((size_t)ng * R * R);
   I.part_xv = ar.take<float2>((size_t)ng * R * R);
+  I.part_dv = ar.take<float2>((size_t)ng * R * R);
   I.part_g = ar.take<float2>((size_t)I.n_rblocks * R * R);
   I.part_xu = ar.take<float2>((size_t)I.n_rblocks * R * R);
-  I.red = ar.take<double>((size_t)4 * R * R + 8);
+  I.part_du = ar.take<float2>((size_t)I.n_rblocks * R * R);
+  I.red = ar.take<double>((size_t)6 * R * R + 8);
   I.sm = ar.take<Smalls>(1);
   I.st = ar.take<DevState>(1);
   if (I.fused) {

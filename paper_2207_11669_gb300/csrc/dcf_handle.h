@@ -53,9 +53,11 @@ struct dcf_handle_s {
   double* part_h = nullptr;
   float2* part_q = nullptr;
   float2* part_xv = nullptr;
+  float2* part_dv = nullptr;
   float2* part_g = nullptr;
   float2* part_xu = nullptr;
-  double* red = nullptr;             // reduction outputs: q, xv, h, g, xu (R*R each)
+  float2* part_du = nullptr;
+  double* red = nullptr;             // reduction outputs: q, xv, dv, h (8), g, xu, du
   float2* truth_part = nullptr;
   double* truth_red = nullptr;
   double* sv_part = nullptr;         // singular values: FP64 Gram partials,

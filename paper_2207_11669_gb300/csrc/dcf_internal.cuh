@@ -38,8 +38,10 @@ struct DevState {
 struct Smalls {
   double gram[2][kMaxR * kMaxR];   // U^T U for copy 0/1 of U
   double q[2][kMaxR * kMaxR];      // V^T V for copy 0/1 of V
-  double xu[kMaxR * kMaxR];        // U_{t-1}^T U_t
+  double xu[kMaxR * kMaxR];        // U_{t-1}^T (U_t - U_{t-1})
   double xv[kMaxR * kMaxR];        // V_{t-1}^T V_t
+  double dvy[kMaxR * kMaxR];       // V_{t-1}^T (V_t - V_{t-1})
+  double dvv[kMaxR * kMaxR];       // (V_t - V_{t-1})^T (V_t - V_{t-1})
   float ginv32[kMaxR * kMaxR];     // (U^T U + rho I)^{-1} of the current U
   float hinv32[kMaxR * kMaxR];     // (V^T V + rho I)^{-1} of the new V (exact mode)
   float qrho32[kMaxR * kMaxR];     // (V^T V + rho I) in float (FedAvg mode)
@@ -61,14 +63,16 @@ struct IterArgs {
   float* W;          // m x R
   // partial results of the streaming passes
   float2* part_q;    // [n_vblocks][R*R]   V'^T V'      (compensated pairs hi, lo)
-  float2* part_xv;   // [n_vblocks][R*R]   V_old^T V'
+  float2* part_xv;   // [n_vblocks][R*R]   V_old^T (V' - V_old)
+  float2* part_dv;   // [n_vblocks][R*R]   (V' - V_old)^T (V' - V_old)
   double* part_h;    // [n_vblocks]        Huber partial
   float* part_p;     // [n_splits][m*R]    P partials (X V')
   int n_vblocks;
   int n_splits;
   int64_t split_cols;
   float2* part_g;    // [n_rblocks][R*R]   U_new^T U_new partials (hi, lo)
-  float2* part_xu;   // [n_rblocks][R*R]   U_old^T U_new partials (hi, lo)
+  float2* part_xu;   // [n_rblocks][R*R]   U_old^T (U_new - U_old) partials (hi, lo)
+  float2* part_du;   // [n_rblocks][R*R]   (U_new - U_old)^T (U_new - U_old) partials
   int n_rblocks;
   Smalls* sm;
   DevState* st;
@@ -94,14 +98,17 @@ struct BInst {
   int64_t split_cols;
   double* part_h;    // [n_strips]       Huber partial per 64-column strip
   float2* part_q;    // [n_gitems][R*R]  Gram partials (V'^T V', or U^T U at the start)
-  float2* part_xv;   // [n_gitems][R*R]
+  float2* part_xv;   // [n_gitems][R*R]  V_old^T (V' - V_old)
+  float2* part_dv;   // [n_gitems][R*R]  (V' - V_old)^T (V' - V_old)
   int n_gitems;      // Gram items over the n rows of V
   int n_uitems;      // Gram items over the m rows of U (start point)
   float2* part_g;    // [n_rblocks][R*R]
-  float2* part_xu;   // [n_rblocks][R*R]
+  float2* part_xu;   // [n_rblocks][R*R]  U_old^T (U_new - U_old)
+  float2* part_du;   // [n_rblocks][R*R]  (U_new - U_old)^T (U_new - U_old)
   int n_rblocks;     // 32-row blocks of U
   int n_strips;      // 64-column strips of M
-  double* red;       // 4 R*R + 8 doubles: reduced Q, X_v, Huber, G, X_u
+  double* red;       // 6 R*R + 8 doubles: reduced Q, V-side cross, dV Gram, Huber (8),
+                     // G, U-side cross, dU Gram
   Smalls* sm;
   DevState* st;
   // the tensor-core single-pass path (k_fused in table mode); 0 = general passes
@@ -142,6 +149,7 @@ __device__ __forceinline__ IterArgs batch_iter_args(const BInst& I, int cur) {
   a.W = I.W;
   a.part_q = I.part_q;
   a.part_xv = I.part_xv;
+  a.part_dv = I.part_dv;
   a.part_h = I.part_h;
   a.part_p = I.part_p;
   a.n_vblocks = I.n_strips;
@@ -149,6 +157,7 @@ __device__ __forceinline__ IterArgs batch_iter_args(const BInst& I, int cur) {
   a.split_cols = I.split_cols;
   a.part_g = I.part_g;
   a.part_xu = I.part_xu;
+  a.part_du = I.part_du;
   a.n_rblocks = I.n_rblocks;
   a.sm = I.sm;
   a.st = I.st;
@@ -165,19 +174,22 @@ __device__ __forceinline__ IterArgs batch_iter_args(const BInst& I, int cur) {
 cudaError_t launch_gram(const float* X, int ldx, int cx, const float* Y, int ldy, int cy,
                         int64_t N, float2* part, int nparts, const DevState* st,
                         int respect_stop, cudaStream_t s);
-// Q = V'^T V' and X_v = V_old^T V' partials in one pass (square R x R, stop-aware).
+// Per-CTA Gram partials of the new V (Vn) against the old (Vo): Q = Vn^T Vn,
+// Vo^T (Vn - Vo) into part_xv and (Vn - Vo)^T (Vn - Vo) into part_dv.
 cudaError_t launch_gram_vv(int R, const float* Vo, const float* Vn, int64_t N, float2* part_q,
-                           float2* part_xv, int nparts, const DevState* st, cudaStream_t s);
+                           float2* part_xv, float2* part_dv, int nparts, const DevState* st,
+                           cudaStream_t s);
 cudaError_t launch_make_w(const IterArgs& a, int copy, int respect_stop, cudaStream_t s);
 cudaError_t launch_rows(const IterArgs& a, cudaStream_t s);
 // U_t = (1/E) sum_i Ui[i] (the server's average of the clients' U after their
 // local steps; client rows of ldc >= R floats) with the Gram partials of U_t
-// and U_{t-1}^T U_t, as k_rows.
+// and of its change, as k_rows.
 cudaError_t launch_avg_rows(const IterArgs& a, const float* const* Ui, int E, int ldc,
                             cudaStream_t s);
-cudaError_t launch_reduce_q(const IterArgs& a, double* out_q, double* out_xv, double* out_h,
-                            int nparts_gram, unsigned int* counter, cudaStream_t s);
-cudaError_t launch_reduce_g(const IterArgs& a, double* out_g, double* out_xu,
+cudaError_t launch_reduce_q(const IterArgs& a, double* out_q, double* out_xv, double* out_dv,
+                            double* out_h, int nparts_gram, unsigned int* counter,
+                            cudaStream_t s);
+cudaError_t launch_reduce_g(const IterArgs& a, double* out_g, double* out_xu, double* out_du,
                             unsigned int* counter, cudaStream_t s);
 cudaError_t launch_reduce_init(const IterArgs& a, int which, int copy, const float2* part,
                                int nparts, double* out, unsigned int* counter, cudaStream_t s);

@@ -116,9 +116,11 @@ extern "C" dcf_status dcf_iterate_noalloc(const float* M, int64_t m, int64_t n, 
     a.part_h = (double*)c.take((size_t)n_vblocks * 8);
     a.part_q = (float2*)c.take(ngp * RR * 8);
     a.part_xv = (float2*)c.take((size_t)n_vgram * RR * 8);
+    a.part_dv = (float2*)c.take((size_t)n_vgram * RR * 8);
     a.part_g = (float2*)c.take(ngp * RR * 8);
     a.part_xu = (float2*)c.take((size_t)n_rblocks * RR * 8);
-    *red = (double*)c.take((4 * RR + 8) * 8);
+    a.part_du = (float2*)c.take((size_t)n_rblocks * RR * 8);
+    *red = (double*)c.take((6 * RR + 8) * 8);
     a.sm = (Smalls*)c.take(sizeof(Smalls));
     a.st = (DevState*)c.take(sizeof(DevState));
     *counters = (unsigned int*)c.take(4 * sizeof(unsigned int));
@@ -156,9 +158,11 @@ extern "C" dcf_status dcf_iterate_noalloc(const float* M, int64_t m, int64_t n, 
   a.ustar_out = nullptr;
   double* red_q = red;
   double* red_xv = red + RR;
-  double* red_h = red + 2 * RR;
-  double* red_g = red + 2 * RR + 8;
-  double* red_xu = red + 3 * RR + 8;
+  double* red_dv = red + 2 * RR;
+  double* red_h = red + 3 * RR;
+  double* red_g = red + 3 * RR + 8;
+  double* red_xu = red + 4 * RR + 8;
+  double* red_du = red + 5 * RR + 8;
   cudaStream_t s = (cudaStream_t)stream;
 
 #define NA_CK(call)                                   \
@@ -191,10 +195,10 @@ extern "C" dcf_status dcf_iterate_noalloc(const float* M, int64_t m, int64_t n, 
   NA_CK(launch_make_w(a, 0, 1, s));
   NA_CK(launch_pass1(a, n_vblocks, 0, 0, s));
   NA_CK(launch_pass2(a, s));
-  NA_CK(launch_gram_vv(R, a.V[0], a.V[1], n, a.part_q, a.part_xv, n_vgram, a.st, s));
-  NA_CK(launch_reduce_q(a, red_q, red_xv, red_h, n_vgram, counters + 0, s));
+  NA_CK(launch_gram_vv(R, a.V[0], a.V[1], n, a.part_q, a.part_xv, a.part_dv, n_vgram, a.st, s));
+  NA_CK(launch_reduce_q(a, red_q, red_xv, red_dv, red_h, n_vgram, counters + 0, s));
   NA_CK(launch_rows(a, s));
-  NA_CK(launch_reduce_g(a, red_g, red_xu, counters + 1, s));
+  NA_CK(launch_reduce_g(a, red_g, red_xu, red_du, counters + 1, s));
   NA_CK(cudaMemcpy2DAsync(U_out, r * 4, a.U[1], R * 4, r * 4, m, cudaMemcpyDeviceToDevice, s));
   NA_CK(cudaMemcpy2DAsync(V_out, r * 4, a.V[1], R * 4, r * 4, n, cudaMemcpyDeviceToDevice, s));
 #undef NA_CK

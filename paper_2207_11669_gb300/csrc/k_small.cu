@@ -96,11 +96,15 @@ k_gram_part(const float* __restrict__ X, int ldx, int cx,
   }
 }
 
-// Both Grams of the new V in one pass:  Q = V'^T V'  and  X_v = V_old^T V'.
+// The Grams of the new V in one pass:  Q = V'^T V',  Y = V_old^T dV  and
+// D = dV^T dV with dV = V' - V_old.  (The change metric of the stop test is
+// formed from Y and D, which are of the size of the change itself, so that it
+// does not cancel against |L|^2; V_old^T V' = Q_old + Y for the fused path.)
 // Thread tile TB x TB of each output (R >= 32: 4 x 4, R <= 16: 1 x 1) with
 // 256 / (R/TB)^2 row groups; 64-row chunks staged in shared memory, the next
 // chunk's loads in flight (registers) while the current one is used.  With
-// 4 x 4 tiles a warp reads a row's operands in 3 shared-memory wavefronts.
+// 4 x 4 tiles a warp reads a row's operands in 4 shared-memory wavefronts.
+// kDelta = false: Q alone (Vo unused), for start-point Grams.
 template <int R>
 struct GvvCfg {
   static constexpr int TB = R >= 32 ? 4 : 1;
@@ -108,19 +112,21 @@ struct GvvCfg {
   static constexpr int GROUPS = 256 / (NT * NT);    // row groups
   static constexpr int CH = 64;                     // rows per chunk
   static constexpr int NV = (CH * R / 4 + 255) / 256;   // float4 per thread per chunk and array
-  static constexpr size_t smem_bytes = 2 * (size_t)CH * R * 4;
-  // the row groups' partial tiles are combined one tile row at a time through
-  // the chunk buffers
-  static_assert(GROUPS * NT * NT * TB * 4 * 4 <= smem_bytes, "combine buffer");
+  static constexpr size_t data_bytes = 2 * (size_t)CH * R * 4;
+  // the row groups' partial tiles (3 outputs x hi, lo) are combined one tile
+  // row at a time
+  static constexpr size_t cmb_bytes = GROUPS > 1 ? (size_t)GROUPS * NT * NT * TB * 6 * 4 : 0;
+  static constexpr size_t smem_bytes = data_bytes > cmb_bytes ? data_bytes : cmb_bytes;
 };
 
-// Rows [a0, a1) of one problem; writes the R*R partials at out_q, out_xv.
+// Rows [a0, a1) of one problem; writes the R*R partials at out_q, out_y, out_d.
 // Block-wide (256 threads); gsh: GvvCfg smem.
-template <int R>
+template <int R, bool kDelta>
 __device__ __forceinline__ void gram_vv_block(const float* __restrict__ Vo,
                                               const float* __restrict__ Vn, int64_t a0,
                                               int64_t a1, float2* __restrict__ out_q,
-                                              float2* __restrict__ out_xv, float* gsh) {
+                                              float2* __restrict__ out_y,
+                                              float2* __restrict__ out_d, float* gsh) {
   using C = GvvCfg<R>;
   constexpr int TB = C::TB, NT = C::NT, G = C::GROUPS, CH = C::CH, NV = C::NV;
   float* So = gsh;              // [CH][R]  V_old rows
@@ -128,11 +134,13 @@ __device__ __forceinline__ void gram_vv_block(const float* __restrict__ Vo,
   const int tid = threadIdx.x;
   const int tile = tid % (NT * NT), grp = tid / (NT * NT);
   const int k0 = (tile / NT) * TB, l0 = (tile % NT) * TB;
-  float qh[TB][TB], ql[TB][TB], xh[TB][TB], xl[TB][TB];
+  float qh[TB][TB], ql[TB][TB], yh[TB][TB], yl[TB][TB], dh[TB][TB], dl[TB][TB];
 #pragma unroll
   for (int i = 0; i < TB; ++i)
 #pragma unroll
-    for (int j = 0; j < TB; ++j) { qh[i][j] = ql[i][j] = xh[i][j] = xl[i][j] = 0.f; }
+    for (int j = 0; j < TB; ++j) {
+      qh[i][j] = ql[i][j] = yh[i][j] = yl[i][j] = dh[i][j] = dl[i][j] = 0.f;
+    }
   float4 po[NV], pn[NV];
   auto fetch = [&](int64_t c) {
     const int rows = (int)dmin64((int64_t)CH, a1 - c);
@@ -140,7 +148,9 @@ __device__ __forceinline__ void gram_vv_block(const float* __restrict__ Vo,
     for (int v = 0; v < NV; ++v) {
       const int i = tid + v * 256;
       const bool ok = i < CH * R / 4 && (4 * i) / R < rows;
-      po[v] = ok ? reinterpret_cast<const float4*>(Vo + c * R)[i] : make_float4(0.f, 0.f, 0.f, 0.f);
+      if (kDelta)
+        po[v] = ok ? reinterpret_cast<const float4*>(Vo + c * R)[i]
+                   : make_float4(0.f, 0.f, 0.f, 0.f);
       pn[v] = ok ? reinterpret_cast<const float4*>(Vn + c * R)[i] : make_float4(0.f, 0.f, 0.f, 0.f);
     }
   };
@@ -151,32 +161,39 @@ __device__ __forceinline__ void gram_vv_block(const float* __restrict__ Vo,
     for (int v = 0; v < NV; ++v) {
       const int i = tid + v * 256;
       if (i < CH * R / 4) {
-        reinterpret_cast<float4*>(So)[i] = po[v];
+        if (kDelta) reinterpret_cast<float4*>(So)[i] = po[v];
         reinterpret_cast<float4*>(Sn)[i] = pn[v];
       }
     }
     __syncthreads();
     if (c + CH < a1) fetch(c + CH);
-    float qa[TB][TB], xa[TB][TB];
+    float qa[TB][TB], ya[TB][TB], da[TB][TB];
 #pragma unroll
     for (int i = 0; i < TB; ++i)
 #pragma unroll
-      for (int j = 0; j < TB; ++j) { qa[i][j] = 0.f; xa[i][j] = 0.f; }
+      for (int j = 0; j < TB; ++j) { qa[i][j] = 0.f; ya[i][j] = 0.f; da[i][j] = 0.f; }
     for (int rr = grp; rr < CH; rr += G) {
-      float nk[TB], nl[TB], ok[TB];
+      float nk[TB], nl[TB], ok[TB], ol[TB];
       if constexpr (TB == 4) {
         const float4 a = *reinterpret_cast<const float4*>(Sn + rr * R + k0);
-        const float4 b = *reinterpret_cast<const float4*>(So + rr * R + k0);
         const float4 d = *reinterpret_cast<const float4*>(Sn + rr * R + l0);
         nk[0] = a.x; nk[1] = a.y; nk[2] = a.z; nk[3] = a.w;
-        ok[0] = b.x; ok[1] = b.y; ok[2] = b.z; ok[3] = b.w;
         nl[0] = d.x; nl[1] = d.y; nl[2] = d.z; nl[3] = d.w;
+        if (kDelta) {
+          const float4 b = *reinterpret_cast<const float4*>(So + rr * R + k0);
+          const float4 e = *reinterpret_cast<const float4*>(So + rr * R + l0);
+          ok[0] = b.x; ok[1] = b.y; ok[2] = b.z; ok[3] = b.w;
+          ol[0] = e.x; ol[1] = e.y; ol[2] = e.z; ol[3] = e.w;
+        }
       } else {
 #pragma unroll
         for (int i = 0; i < TB; ++i) {
           nk[i] = Sn[rr * R + k0 + i];
-          ok[i] = So[rr * R + k0 + i];
           nl[i] = Sn[rr * R + l0 + i];
+          if (kDelta) {
+            ok[i] = So[rr * R + k0 + i];
+            ol[i] = So[rr * R + l0 + i];
+          }
         }
       }
 #pragma unroll
@@ -184,7 +201,11 @@ __device__ __forceinline__ void gram_vv_block(const float* __restrict__ Vo,
 #pragma unroll
         for (int j = 0; j < TB; ++j) {
           qa[i][j] = fmaf(nk[i], nl[j], qa[i][j]);
-          xa[i][j] = fmaf(ok[i], nl[j], xa[i][j]);
+          if (kDelta) {
+            const float dlj = nl[j] - ol[j];
+            ya[i][j] = fmaf(ok[i], dlj, ya[i][j]);
+            da[i][j] = fmaf(nk[i] - ok[i], dlj, da[i][j]);
+          }
         }
     }
 #pragma unroll
@@ -192,11 +213,14 @@ __device__ __forceinline__ void gram_vv_block(const float* __restrict__ Vo,
 #pragma unroll
       for (int j = 0; j < TB; ++j) {
         two_sum_add(qh[i][j], ql[i][j], qa[i][j]);
-        two_sum_add(xh[i][j], xl[i][j], xa[i][j]);
+        if (kDelta) {
+          two_sum_add(yh[i][j], yl[i][j], ya[i][j]);
+          two_sum_add(dh[i][j], dl[i][j], da[i][j]);
+        }
       }
   }
   // combine the row groups through shared memory, one tile row at a time:
-  // cmb[g][tile][j][4] = (hi, lo of Q, hi, lo of X_v)
+  // cmb[g][tile][j][6] = (hi, lo of Q, Y, D)
   if (G > 1) {
     float* cmb = gsh;
 #pragma unroll
@@ -205,8 +229,9 @@ __device__ __forceinline__ void gram_vv_block(const float* __restrict__ Vo,
       if (grp > 0) {
 #pragma unroll
         for (int j = 0; j < TB; ++j) {
-          float* d = cmb + (((size_t)grp * NT * NT + tile) * TB + j) * 4;
-          d[0] = qh[i][j]; d[1] = ql[i][j]; d[2] = xh[i][j]; d[3] = xl[i][j];
+          float* d = cmb + (((size_t)grp * NT * NT + tile) * TB + j) * 6;
+          d[0] = qh[i][j]; d[1] = ql[i][j]; d[2] = yh[i][j]; d[3] = yl[i][j];
+          d[4] = dh[i][j]; d[5] = dl[i][j];
         }
       }
       __syncthreads();
@@ -214,11 +239,13 @@ __device__ __forceinline__ void gram_vv_block(const float* __restrict__ Vo,
         for (int g2 = 1; g2 < G; ++g2) {
 #pragma unroll
           for (int j = 0; j < TB; ++j) {
-            const float* d = cmb + (((size_t)g2 * NT * NT + tile) * TB + j) * 4;
+            const float* d = cmb + (((size_t)g2 * NT * NT + tile) * TB + j) * 6;
             two_sum_add(qh[i][j], ql[i][j], d[0]);
             ql[i][j] += d[1];
-            two_sum_add(xh[i][j], xl[i][j], d[2]);
-            xl[i][j] += d[3];
+            two_sum_add(yh[i][j], yl[i][j], d[2]);
+            yl[i][j] += d[3];
+            two_sum_add(dh[i][j], dl[i][j], d[4]);
+            dl[i][j] += d[5];
           }
         }
       }
@@ -231,7 +258,10 @@ __device__ __forceinline__ void gram_vv_block(const float* __restrict__ Vo,
       for (int j = 0; j < TB; ++j) {
         const int e = (k0 + i) * R + l0 + j;
         out_q[e] = make_float2(qh[i][j], ql[i][j]);
-        out_xv[e] = make_float2(xh[i][j], xl[i][j]);
+        if (kDelta) {
+          out_y[e] = make_float2(yh[i][j], yl[i][j]);
+          out_d[e] = make_float2(dh[i][j], dl[i][j]);
+        }
       }
   }
 }
@@ -240,13 +270,13 @@ template <int R>
 __global__ void __launch_bounds__(256)
 k_gram_vv(const float* __restrict__ Vo, const float* __restrict__ Vn, int64_t N,
           int64_t rows_per_cta, float2* __restrict__ part_q, float2* __restrict__ part_xv,
-          const DevState* st) {
+          float2* __restrict__ part_dv, const DevState* st) {
   if (st->stop) return;
   extern __shared__ __align__(16) float gsh[];
   const int64_t a0 = (int64_t)blockIdx.x * rows_per_cta;
   const int64_t a1 = min(N, a0 + rows_per_cta);
   const int64_t base = (int64_t)blockIdx.x * R * R;
-  gram_vv_block<R>(Vo, Vn, a0, a1, part_q + base, part_xv + base, gsh);
+  gram_vv_block<R, true>(Vo, Vn, a0, a1, part_q + base, part_xv + base, part_dv + base, gsh);
 }
 
 // ---------------------------------------------------------------------------
@@ -255,12 +285,12 @@ k_gram_vv(const float* __restrict__ Vo, const float* __restrict__ Vn, int64_t N,
 enum TailKind { TAIL_NONE = 0, TAIL_Q = 1, TAIL_G = 2, TAIL_INIT_G = 3, TAIL_INIT_Q = 4 };
 
 struct ReduceArgs {
-  const float2* part[2];   // compensated partial arrays ([nparts][count_s]) of inputs 0, 1
-  const double* hpart;     // input 2: FP64 partials (the Huber sum), count[2] <= 1
-  int count[3];            // entries per input (0 = unused)
-  double* out[3];          // destinations (FP64)
-  int nparts[3];
-  int total;               // count[0] + count[1] + count[2]
+  const float2* part[3];   // compensated partial arrays ([nparts][count_s]) of inputs 0..2
+  const double* hpart;     // input 3: FP64 partials (the Huber sum), count[3] <= 1
+  int count[4];            // entries per input (0 = unused)
+  double* out[4];          // destinations (FP64)
+  int nparts[4];
+  int total;               // count[0] + ... + count[3]
   int tail;
   int R;
   float rho;
@@ -294,7 +324,7 @@ __global__ void __launch_bounds__(256) k_reduce_parts(ReduceArgs a) {
     idx = e;
     which = 0;
     while (idx >= a.count[which]) { idx -= a.count[which]; ++which; }
-    if (which < 2) {
+    if (which < 3) {
       const float2* p = a.part[which];
       const int cnt = a.count[which];
       const int np = a.nparts[which];
@@ -313,14 +343,14 @@ __global__ void __launch_bounds__(256) k_reduce_parts(ReduceArgs a) {
         }
       }
     } else {
-      for (int q = lane_p; q < a.nparts[2]; q += nsplit) hs += a.hpart[q];
+      for (int q = lane_p; q < a.nparts[3]; q += nsplit) hs += a.hpart[q];
     }
   }
   red2[tid] = make_float2(hi, lo);
   red[tid] = hs;
   __syncthreads();
   if (lane_p == 0 && which >= 0) {
-    if (which < 2) {
+    if (which < 3) {
       float th = 0.f, tl = 0.f;
       for (int q = 0; q < nsplit; ++q) {
         const float2 v = red2[q * kRedEntriesPerCta + e_local];
@@ -352,7 +382,8 @@ __global__ void __launch_bounds__(256) k_reduce_parts(ReduceArgs a) {
   else tail_g(a, dsh, F);
 }
 
-// Q_t is in out[0] (R*R), X_v = V_{t-1}^T V_t in out[1], Huber in out[2].
+// Q_t is in out[0] (R*R), Y = V_{t-1}^T (V_t - V_{t-1}) in out[1], the Gram of
+// V_t - V_{t-1} in out[2], Huber in out[3].  V_{t-1}^T V_t = Q_{t-1} + Y.
 __device__ void tail_q(const ReduceArgs& a, double* A, float* F) {
   const int R = a.R;
   Smalls* sm = a.sm;
@@ -362,29 +393,34 @@ __device__ void tail_q(const ReduceArgs& a, double* A, float* F) {
     for (int i = threadIdx.x; i < R * R; i += blockDim.x) sm->q[a.copy][i] = __ldcg(a.out[0] + i);
     return;
   }
-  const int nxt = a.copy ^ 1;
+  const int cur = a.copy, nxt = cur ^ 1;
   // every load of the thread's entries first (they are independent), then the stores
   for (int i0 = threadIdx.x; i0 < R * R; i0 += 4 * 256) {   // 4 entries per thread at a time
-    double qv[4], xv[4];
+    double qv[4], yv[4], dv[4], qo[4];
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
       const int i = i0 + u * 256;
-      qv[u] = i < R * R ? __ldcg(a.out[0] + i) : 0.0;
-      xv[u] = i < R * R ? __ldcg(a.out[1] + i) : 0.0;
+      const bool in = i < R * R;
+      qv[u] = in ? __ldcg(a.out[0] + i) : 0.0;
+      yv[u] = in ? __ldcg(a.out[1] + i) : 0.0;
+      dv[u] = in ? __ldcg(a.out[2] + i) : 0.0;
+      qo[u] = in ? sm->q[cur][i] : 0.0;
     }
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
       const int i = i0 + u * 256;
       if (i >= R * R) continue;
       sm->q[nxt][i] = qv[u];
-      sm->xv[i] = xv[u];
+      sm->dvy[i] = yv[u];
+      sm->dvv[i] = dv[u];
+      sm->xv[i] = qo[u] + yv[u];
       const int r = i / R, c = i % R;
       const double h = qv[u] + (r == c ? (double)(a.rho_q > 0.f ? a.rho_q : a.rho) : 0.0);
       A[i] = h;
       sm->qrho32[i] = (float)h;
     }
   }
-  if (threadIdx.x == 0) st->huber = __ldcg(a.out[2]);
+  if (threadIdx.x == 0) st->huber = __ldcg(a.out[3]);
   __syncthreads();
   if (!all_finite(A, R * R)) {
     if (threadIdx.x == 0) st->status = 4;  // DCF_ENONFINITE
@@ -393,7 +429,8 @@ __device__ void tail_q(const ReduceArgs& a, double* A, float* F) {
   if (a.u_mode == 0) spd_inverse_f32(A, F, R, sm->hinv32);
 }
 
-// Gram of U_t in out[0], X_u = U_{t-1}^T U_t in out[1].
+// Gram of U_t in out[0], U_{t-1}^T (U_t - U_{t-1}) in out[1], the Gram of
+// U_t - U_{t-1} in out[2].
 __device__ void tail_g(const ReduceArgs& a, double* A, float* F) {
   const int R = a.R;
   Smalls* sm = a.sm;
@@ -405,23 +442,31 @@ __device__ void tail_g(const ReduceArgs& a, double* A, float* F) {
   } else {
     const int cur = a.copy;
     tgt = cur ^ 1;
-    // metrics: dL^2 = <G_t,Q_t> - 2 <X_u, X_v> + <G_{t-1}, Q_{t-1}>   (all r x r)
-    // five FP64 sums in one reduction: per-thread partials, a shuffle tree
-    // per warp, then the per-warp values across lanes of warp 0.  Every load
-    // of the thread's entries is issued before any store or product; the new
-    // Gram also goes straight into A (G_t + rho I) for the inverse below.
-    __shared__ double wsum[5][32];
-    double v[5] = {0, 0, 0, 0, 0};
+    // metrics.  With dU = U_t - U_{t-1}, dV = V_t - V_{t-1}:
+    //   L_t - L_{t-1} = dU V_t^T + U_{t-1} dV^T, so
+    //   |L_t - L_{t-1}|^2 = <dU^T dU, Q_t> + 2 <(U_{t-1}^T dU)^T, V_t^T dV>
+    //                       + <G_{t-1}, dV^T dV>,   V_t^T dV = Y + dV^T dV,
+    // every term of the size of the change (no cancellation against |L|^2);
+    // |L_t|^2 = <G_t, Q_t>.  Six FP64 sums in one reduction: per-thread partials,
+    // a shuffle tree per warp, then the per-warp values across lanes of warp 0.
+    // Every load of the thread's entries is issued before any store or product;
+    // the new Gram also goes straight into A (G_t + rho I) for the inverse below.
+    __shared__ double wsum[6][32];
+    double v[6] = {0, 0, 0, 0, 0, 0};
     for (int i0 = threadIdx.x; i0 < R * R; i0 += 4 * 256) {   // 4 entries per thread at a time
-      double gn[4], xu[4], qn[4], xv[4], go[4], qo[4];
+      double gn[4], a2t[4], a1[4], qn[4], b2[4], b3[4], go[4], qo[4], a2[4];
 #pragma unroll
       for (int u = 0; u < 4; ++u) {
         const int i = i0 + u * 256;
         const bool in = i < R * R;
+        const int r = in ? i / R : 0, c = in ? i % R : 0;
         gn[u] = in ? __ldcg(a.out[0] + i) : 0.0;
-        xu[u] = in ? __ldcg(a.out[1] + i) : 0.0;
+        a2[u] = in ? __ldcg(a.out[1] + i) : 0.0;
+        a2t[u] = in ? __ldcg(a.out[1] + c * R + r) : 0.0;
+        a1[u] = in ? __ldcg(a.out[2] + i) : 0.0;
         qn[u] = in ? sm->q[tgt][i] : 0.0;
-        xv[u] = in ? sm->xv[i] : 0.0;
+        b3[u] = in ? sm->dvv[i] : 0.0;
+        b2[u] = in ? sm->dvy[i] + b3[u] : 0.0;
         go[u] = in ? sm->gram[cur][i] : 0.0;
         qo[u] = in ? sm->q[cur][i] : 0.0;
       }
@@ -430,15 +475,16 @@ __device__ void tail_g(const ReduceArgs& a, double* A, float* F) {
         const int i = i0 + u * 256;
         if (i >= R * R) continue;
         sm->gram[tgt][i] = gn[u];
-        sm->xu[i] = xu[u];
+        sm->xu[i] = a2[u];
         const int r = i / R, c = i % R;
         A[i] = gn[u] + (r == c ? (double)a.rho : 0.0);
         v[0] = fma(gn[u], qn[u], v[0]);
-        v[1] = fma(xu[u], xv[u], v[1]);
-        v[2] = fma(go[u], qo[u], v[2]);
+        v[1] = fma(a1[u], qn[u], v[1]);
+        v[2] = fma(a2t[u], b2[u], v[2]);
+        v[3] = fma(go[u], b3[u], v[3]);
         if (r == c) {
-          v[3] += go[u];
-          v[4] += qo[u];
+          v[4] += go[u];
+          v[5] += qo[u];
         }
       }
     }
@@ -446,25 +492,25 @@ __device__ void tail_g(const ReduceArgs& a, double* A, float* F) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1)
 #pragma unroll
-      for (int q = 0; q < 5; ++q) v[q] += __shfl_xor_sync(0xffffffffu, v[q], o);
+      for (int q = 0; q < 6; ++q) v[q] += __shfl_xor_sync(0xffffffffu, v[q], o);
     if (lane == 0)
 #pragma unroll
-      for (int q = 0; q < 5; ++q) wsum[q][wid] = v[q];
+      for (int q = 0; q < 6; ++q) wsum[q][wid] = v[q];
     __syncthreads();
     if (wid == 0) {
 #pragma unroll
-      for (int q = 0; q < 5; ++q) v[q] = lane < nw ? wsum[q][lane] : 0.0;
+      for (int q = 0; q < 6; ++q) v[q] = lane < nw ? wsum[q][lane] : 0.0;
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1)
 #pragma unroll
-        for (int q = 0; q < 5; ++q) v[q] += __shfl_xor_sync(0xffffffffu, v[q], o);
+        for (int q = 0; q < 6; ++q) v[q] += __shfl_xor_sync(0xffffffffu, v[q], o);
     }
-    const double a0 = v[0], a1 = v[1], a2 = v[2], t0 = v[3], t1 = v[4];   // valid in warp 0
     if (threadIdx.x == 0) {
-      double d2 = a0 - 2.0 * a1 + a2;
+      const double a0 = v[0];
+      double d2 = v[1] + 2.0 * v[2] + v[3];
       if (d2 < 0) d2 = 0;
       st->dL_rel = a0 > 0 ? sqrt(d2 / a0) : INFINITY;
-      st->objective = st->huber + 0.5 * (double)a.rho * (t0 + t1);
+      st->objective = st->huber + 0.5 * (double)a.rho * (v[4] + v[5]);
       st->iter = st->iter + 1;
       st->has_S = 1;
       if (!isfinite(a0) || !isfinite(st->objective)) st->status = 4;
@@ -530,6 +576,28 @@ __global__ void __launch_bounds__(256) k_make_w(const float* __restrict__ U,
                                                 int respect_stop) {
   if (respect_stop && st->stop) return;
   make_w_block<R>(U, sm, W, m, blockIdx.x);
+}
+
+// Gram partials over a CTA's rows of U: G = Un^T Un, Uo^T dU and dU^T dU with
+// dU = Un - Uo (the change metric is formed from the last two, which are of
+// the size of the change).  Block-wide; Uo, Un: rows x R in shared memory.
+template <int R>
+__device__ __forceinline__ void rows_gram_partials(const IterArgs& a, const float* Uo,
+                                                   const float* Un, int rows, int64_t rb) {
+  for (int e = threadIdx.x; e < R * R; e += blockDim.x) {
+    const int k = e / R, l = e % R;
+    float gg = 0.f, xu = 0.f, du = 0.f;
+    for (int rr = 0; rr < rows; ++rr) {
+      const float dk = Un[rr * R + k] - Uo[rr * R + k];
+      const float dl = Un[rr * R + l] - Uo[rr * R + l];
+      gg = fmaf(Un[rr * R + k], Un[rr * R + l], gg);
+      xu = fmaf(Uo[rr * R + k], dl, xu);
+      du = fmaf(dk, dl, du);
+    }
+    a.part_g[rb * R * R + e] = make_float2(gg, 0.f);
+    a.part_xu[rb * R * R + e] = make_float2(xu, 0.f);
+    a.part_du[rb * R * R + e] = make_float2(du, 0.f);
+  }
 }
 
 // Consensus U-update plus Gram partials of the new U:
@@ -633,17 +701,7 @@ __device__ __forceinline__ void rows_block(const IterArgs& a, int64_t rb) {
   }
   if (!finite) st->status = 4;
   __syncthreads();
-  // Gram partials over this CTA's rows: G = Un^T Un, Xu = Uo^T Un
-  for (int e = tid; e < R * R; e += 256) {
-    int k = e / R, l = e % R;
-    float gg = 0.f, xu = 0.f;
-    for (int rr = 0; rr < rows; ++rr) {
-      gg = fmaf(Un[rr * R + k], Un[rr * R + l], gg);
-      xu = fmaf(Uo[rr * R + k], Un[rr * R + l], xu);
-    }
-    a.part_g[rb * R * R + e] = make_float2(gg, 0.f);
-    a.part_xu[rb * R * R + e] = make_float2(xu, 0.f);
-  }
+  rows_gram_partials<R>(a, Uo, Un, rows, rb);
 }
 
 template <int R>
@@ -654,8 +712,8 @@ __global__ void __launch_bounds__(256) k_rows(IterArgs a) {
 
 // The server's step of Algorithm 1 (eq. U_agg) after the clients' local steps:
 // U_t[a,:] = (1/E) sum_i Ui[i][a,:], the clients summed in order, plus the
-// Gram partials G = U_t^T U_t and X_u = U_{t-1}^T U_t of the 32-row block, as
-// the consensus rows kernel leaves them for the metrics.  The clients' rows
+// Gram partials of the 32-row block (rows_gram_partials), as the consensus
+// rows kernel leaves them for the metrics.  The clients' rows
 // have ldc >= R entries (their own padded rank); columns past R are zero.
 template <int R>
 __global__ void __launch_bounds__(256) k_avg_rows(IterArgs a, const float* const* __restrict__ Ui,
@@ -689,16 +747,7 @@ __global__ void __launch_bounds__(256) k_avg_rows(IterArgs a, const float* const
   }
   if (!finite) a.st->status = 4;
   __syncthreads();
-  for (int e = tid; e < R * R; e += 256) {
-    const int k = e / R, l = e % R;
-    float gg = 0.f, xu = 0.f;
-    for (int rr = 0; rr < rows; ++rr) {
-      gg = fmaf(Un[rr * R + k], Un[rr * R + l], gg);
-      xu = fmaf(Uo[rr * R + k], Un[rr * R + l], xu);
-    }
-    a.part_g[rb * R * R + e] = make_float2(gg, 0.f);
-    a.part_xu[rb * R * R + e] = make_float2(xu, 0.f);
-  }
+  rows_gram_partials<R>(a, Uo, Un, rows, rb);
 }
 
 // ---------------------------------------------------------------------------
@@ -752,16 +801,21 @@ __global__ void __launch_bounds__(256) k_bgram(const BInst* __restrict__ insts,
     const int64_t a0 = (int64_t)w.a * kBGramRows;
     const int64_t a1 = min(N, a0 + (int64_t)kBGramRows);
     __syncthreads();
-    gram_vv_block<R>(X, Y, a0, a1, I.part_q + (int64_t)w.a * R * R,
-                     I.part_xv + (int64_t)w.a * R * R, gsh);
+    const int64_t base = (int64_t)w.a * R * R;
+    if (mode == BG_ITER)
+      gram_vv_block<R, true>(X, Y, a0, a1, I.part_q + base, I.part_xv + base, I.part_dv + base,
+                             gsh);
+    else
+      gram_vv_block<R, false>(X, Y, a0, a1, I.part_q + base, nullptr, nullptr, gsh);
   }
 }
 
 // One CTA per instance (list `which`): reduce the instance's partials in
 // compensated FP32 pairs, store them in FP64, then run the r x r tail.
-//   tail TAIL_Q      Q, X_v (Gram items), Huber (strips)  -> (Q + rho I)^{-1}
-//   tail TAIL_G      G, X_u (32-row blocks)               -> metrics, stop, (G + rho I)^{-1}
+//   tail TAIL_Q      Q, V-side cross, dV Gram (Gram items), Huber (strips) -> (Q + rho I)^{-1}
+//   tail TAIL_G      G, U-side cross, dU Gram (32-row blocks) -> metrics, stop, (G + rho I)^{-1}
 //   tail TAIL_INIT_G U0^T U0 (Gram items over m rows);  TAIL_INIT_Q  V0^T V0
+// red layout: Q, V-side cross, dV Gram (R*R each), Huber (8), G, U-side cross, dU Gram.
 template <int R>
 __global__ void __launch_bounds__(256) k_breduce(const BInst* __restrict__ insts,
                                                  const int* __restrict__ which, int cur,
@@ -770,39 +824,49 @@ __global__ void __launch_bounds__(256) k_breduce(const BInst* __restrict__ insts
   if ((tail == TAIL_Q || tail == TAIL_G) && I.st->stop) return;
   constexpr int RR = R * R;
   double* red = I.red;
-  double* out0 = tail == TAIL_G ? red + 2 * RR + 8 : red;
-  double* out1 = tail == TAIL_G ? red + 3 * RR + 8 : red + RR;
-  const float2* p0 = tail == TAIL_G ? I.part_g : I.part_q;
+  const bool gside = tail == TAIL_G || tail == TAIL_INIT_G;
+  double* out0 = gside ? red + 3 * RR + 8 : red;
+  double* out1 = out0 + RR;
+  double* out2 = out1 + RR;
+  const float2* p0 = gside && tail == TAIL_G ? I.part_g : I.part_q;
   const float2* p1 = tail == TAIL_G ? I.part_xu : I.part_xv;
+  const float2* p2 = tail == TAIL_G ? I.part_du : I.part_dv;
   const int np = tail == TAIL_G ? I.n_rblocks : tail == TAIL_INIT_G ? I.n_uitems : I.n_gitems;
-  const bool two = tail == TAIL_Q || tail == TAIL_G;
+  const bool three = tail == TAIL_Q || tail == TAIL_G;
   for (int e = threadIdx.x; e < RR; e += blockDim.x) {
-    float h0 = 0.f, l0 = 0.f, h1 = 0.f, l1 = 0.f;
+    float h0 = 0.f, l0 = 0.f, h1 = 0.f, l1 = 0.f, h2 = 0.f, l2 = 0.f;
     for (int q = 0; q < np; ++q) {
       const float2 v0 = p0[(int64_t)q * RR + e];
       two_sum_add(h0, l0, v0.x);
       l0 += v0.y;
-      if (two) {
+      if (three) {
         const float2 v1 = p1[(int64_t)q * RR + e];
         two_sum_add(h1, l1, v1.x);
         l1 += v1.y;
+        const float2 v2 = p2[(int64_t)q * RR + e];
+        two_sum_add(h2, l2, v2.x);
+        l2 += v2.y;
       }
     }
     out0[e] = (double)h0 + (double)l0;
-    if (two) out1[e] = (double)h1 + (double)l1;
+    if (three) {
+      out1[e] = (double)h1 + (double)l1;
+      out2[e] = (double)h2 + (double)l2;
+    }
   }
   if (tail == TAIL_Q && threadIdx.x < 32) {
     double hs = 0.0;
     for (int q = threadIdx.x; q < I.n_hparts; q += 32) hs += I.part_h[q];
     for (int o = 16; o > 0; o >>= 1) hs += __shfl_xor_sync(0xffffffffu, hs, o);
-    if (threadIdx.x == 0) red[2 * RR] = hs;
+    if (threadIdx.x == 0) red[3 * RR] = hs;
   }
   __threadfence();
   __syncthreads();
   ReduceArgs ra{};
   ra.out[0] = out0;
   ra.out[1] = out1;
-  ra.out[2] = red + 2 * RR;
+  ra.out[2] = out2;
+  ra.out[3] = red + 3 * RR;
   ra.tail = tail;
   ra.R = R;
   ra.rho = I.rho;
@@ -889,19 +953,21 @@ cudaError_t launch_gram(const float* X, int ldx, int cx, const float* Y, int ldy
 
 template <int R>
 static cudaError_t gram_vv_T(const float* Vo, const float* Vn, int64_t N, float2* pq,
-                             float2* pxv, int nparts, const DevState* st, cudaStream_t s) {
+                             float2* pxv, float2* pdv, int nparts, const DevState* st,
+                             cudaStream_t s) {
   const int64_t rows_per = (N + nparts - 1) / nparts;
-  k_gram_vv<R><<<nparts, 256, GvvCfg<R>::smem_bytes, s>>>(Vo, Vn, N, rows_per, pq, pxv, st);
+  k_gram_vv<R><<<nparts, 256, GvvCfg<R>::smem_bytes, s>>>(Vo, Vn, N, rows_per, pq, pxv, pdv, st);
   return cudaGetLastError();
 }
 
 cudaError_t launch_gram_vv(int R, const float* Vo, const float* Vn, int64_t N, float2* part_q,
-                           float2* part_xv, int nparts, const DevState* st, cudaStream_t s) {
+                           float2* part_xv, float2* part_dv, int nparts, const DevState* st,
+                           cudaStream_t s) {
   switch (R) {
-    case 8: return gram_vv_T<8>(Vo, Vn, N, part_q, part_xv, nparts, st, s);
-    case 16: return gram_vv_T<16>(Vo, Vn, N, part_q, part_xv, nparts, st, s);
-    case 32: return gram_vv_T<32>(Vo, Vn, N, part_q, part_xv, nparts, st, s);
-    default: return gram_vv_T<64>(Vo, Vn, N, part_q, part_xv, nparts, st, s);
+    case 8: return gram_vv_T<8>(Vo, Vn, N, part_q, part_xv, part_dv, nparts, st, s);
+    case 16: return gram_vv_T<16>(Vo, Vn, N, part_q, part_xv, part_dv, nparts, st, s);
+    case 32: return gram_vv_T<32>(Vo, Vn, N, part_q, part_xv, part_dv, nparts, st, s);
+    default: return gram_vv_T<64>(Vo, Vn, N, part_q, part_xv, part_dv, nparts, st, s);
   }
 }
 
@@ -987,14 +1053,16 @@ cudaError_t launch_avg_rows(const IterArgs& a, const float* const* Ui, int E, in
 }
 
 // reduction of V-side partials (Q_t, V_{t-1}^T V_t, Huber) + Cholesky(Q_t + rho I)
-cudaError_t launch_reduce_q(const IterArgs& a, double* out_q, double* out_xv, double* out_h,
-                            int nparts_gram, unsigned int* counter, cudaStream_t s) {
+cudaError_t launch_reduce_q(const IterArgs& a, double* out_q, double* out_xv, double* out_dv,
+                            double* out_h, int nparts_gram, unsigned int* counter,
+                            cudaStream_t s) {
   ReduceArgs ra{};
   const int RR = a.R * a.R;
   ra.part[0] = a.part_q; ra.count[0] = RR; ra.out[0] = out_q; ra.nparts[0] = nparts_gram;
   ra.part[1] = a.part_xv; ra.count[1] = RR; ra.out[1] = out_xv; ra.nparts[1] = nparts_gram;
-  ra.hpart = a.part_h; ra.count[2] = 1; ra.out[2] = out_h; ra.nparts[2] = a.n_vblocks;
-  ra.total = 2 * RR + 1;
+  ra.part[2] = a.part_dv; ra.count[2] = RR; ra.out[2] = out_dv; ra.nparts[2] = nparts_gram;
+  ra.hpart = a.part_h; ra.count[3] = 1; ra.out[3] = out_h; ra.nparts[3] = a.n_vblocks;
+  ra.total = 3 * RR + 1;
   ra.tail = TAIL_Q;
   ra.copy = a.cur;
   ra.R = a.R; ra.rho = a.rho; ra.rho_q = a.rho_q; ra.u_mode = a.u_mode;
@@ -1002,13 +1070,14 @@ cudaError_t launch_reduce_q(const IterArgs& a, double* out_q, double* out_xv, do
   return launch_reduce(ra, s);
 }
 
-cudaError_t launch_reduce_g(const IterArgs& a, double* out_g, double* out_xu,
+cudaError_t launch_reduce_g(const IterArgs& a, double* out_g, double* out_xu, double* out_du,
                             unsigned int* counter, cudaStream_t s) {
   ReduceArgs ra{};
   const int RR = a.R * a.R;
   ra.part[0] = a.part_g; ra.count[0] = RR; ra.out[0] = out_g; ra.nparts[0] = a.n_rblocks;
   ra.part[1] = a.part_xu; ra.count[1] = RR; ra.out[1] = out_xu; ra.nparts[1] = a.n_rblocks;
-  ra.total = 2 * RR;
+  ra.part[2] = a.part_du; ra.count[2] = RR; ra.out[2] = out_du; ra.nparts[2] = a.n_rblocks;
+  ra.total = 3 * RR;
   ra.tail = TAIL_G;
   ra.copy = a.cur;
   ra.R = a.R; ra.rho = a.rho; ra.u_mode = a.u_mode;

@@ -14,8 +14,11 @@
 //              (= M_ij - S_ij),  v'_j = sum_i x_ij w_i,  Huber sum of r_ij
 //   Q' = V'^T V', X_v = V^T V',  H = (Q' + rho I)^{-1}
 //   row i:     p_i = sum_j x_ij v'_j  (x recomputed),  u'_i = p_i H
-//   G' = U'^T U', X_u = U^T U'
-//   dL^2 = <G', Q'> - 2 <X_u, X_v> + <G, Q>,  objective = Huber + rho/2 (tr G + tr Q)
+//   G' = U'^T U', and with dU = U' - U, dV = V' - V the change Grams
+//   A = U^T dU, D_u = dU^T dU, Y = V^T dV, D_v = dV^T dV:
+//   dL^2 = <D_u, Q'> + 2 <A^T, Y + D_v> + <G, D_v>   (L' - L = dU V'^T + U dV^T;
+//   every term of the size of the change), |L'|^2 = <G', Q'>,
+//   objective = Huber + rho/2 (tr G + tr Q)
 // The r x r inverses are FP64 (Gauss-Jordan in one warp), the long sums FP32.
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -35,7 +38,7 @@ struct SSLayout {
   int RR;
   int64_t ldm;        // M is stored with leading dimension m + 1 (odd: no bank
                       // conflicts when threads walk different columns)
-  size_t A, G, Q, Gn, Qn, XU, XV, WS;   // doubles
+  size_t A, G, Q, Gn, Qn, XU, XV, DU, DV, WS;   // doubles
   size_t GI, HI, GP;                    // floats (GP: float2 Gram partials)
   size_t Ms, U0, U1, V0, V1, W;         // floats
   size_t total;
@@ -50,6 +53,8 @@ struct SSLayout {
     Qn = o; o += (size_t)RR * 8;
     XU = o; o += (size_t)RR * 8;
     XV = o; o += (size_t)RR * 8;
+    DU = o; o += (size_t)RR * 8;
+    DV = o; o += (size_t)RR * 8;
     WS = o; o += 8 * 32 * 8;
     GI = o; o += (size_t)RR * 4;
     HI = o; o += (size_t)RR * 4;
@@ -71,9 +76,10 @@ __device__ __forceinline__ void ss_two_sum(float& hi, float& lo, float x) {
   hi = t;
 }
 
-// out[k*R + l] = sum_i X[i*R + k] Y[i*R + l] over N rows (compensated FP32
+// out[k*R + l] = sum_i x_k y_l over N rows, with (x, y) = (X_i, Y_i) in mode
+// 0, (X_i, Y_i - X_i) in mode 1 and (Y_i - X_i, Y_i - X_i) in mode 2 (compensated FP32
 // partials over row groups, FP64 result).  Block-wide.
-template <int R>
+template <int R, int kMode = 0>
 __device__ void ss_gram(const float* X, const float* Y, int64_t N, double* out, float2* gp) {
   constexpr int RR = R * R;
   constexpr int NG = kSSThreads / RR >= 1 ? kSSThreads / RR : 1;   // row groups
@@ -83,7 +89,12 @@ __device__ void ss_gram(const float* X, const float* Y, int64_t N, double* out, 
     float hi = 0.f, lo = 0.f;
     if (e < RR && g < NG) {
       const int k = e / R, l = e % R;
-      for (int64_t i = g; i < N; i += NG) ss_two_sum(hi, lo, X[i * R + k] * Y[i * R + l]);
+      for (int64_t i = g; i < N; i += NG) {
+        const float xk = X[i * R + k], xl = X[i * R + l], yk = Y[i * R + k], yl = Y[i * R + l];
+        const float a = kMode == 2 ? yk - xk : xk;
+        const float b = kMode == 0 ? yl : yl - xl;
+        ss_two_sum(hi, lo, a * b);
+      }
     }
     __syncthreads();
     gp[tid] = make_float2(hi, lo);
@@ -164,6 +175,8 @@ __global__ void __launch_bounds__(kSSThreads, 1) k_solve_small(SmallSolveArgs a)
   double* Qn = reinterpret_cast<double*>(smem + L.Qn);
   double* XU = reinterpret_cast<double*>(smem + L.XU);
   double* XV = reinterpret_cast<double*>(smem + L.XV);
+  double* DU = reinterpret_cast<double*>(smem + L.DU);
+  double* DV = reinterpret_cast<double*>(smem + L.DV);
   double* ws = reinterpret_cast<double*>(smem + L.WS);
   float* GI = reinterpret_cast<float*>(smem + L.GI);
   float* HI = reinterpret_cast<float*>(smem + L.HI);
@@ -285,7 +298,8 @@ __global__ void __launch_bounds__(kSSThreads, 1) k_solve_small(SmallSolveArgs a)
     }
     __syncthreads();
     ss_gram<R>(Vn, Vn, n, Qn, gp);
-    ss_gram<R>(V, Vn, n, XV, gp);
+    ss_gram<R, 1>(V, Vn, n, XV, gp);      // V^T dV
+    ss_gram<R, 2>(V, Vn, n, DV, gp);      // dV^T dV
     // ---- U-step: P = X V', U' = P (Q' + rho I)^{-1}, one thread per row ---------
     if (!ss_ridge_inverse<R>(Qn, rho, A, HI, &s_flags[2])) {
       if (tid == 0) s_flags[1] = DCF_ENONFINITE;
@@ -339,23 +353,26 @@ __global__ void __launch_bounds__(kSSThreads, 1) k_solve_small(SmallSolveArgs a)
     }
     __syncthreads();
     ss_gram<R>(Un, Un, m, Gn, gp);
-    ss_gram<R>(U, Un, m, XU, gp);
+    ss_gram<R, 1>(U, Un, m, XU, gp);      // U^T dU
+    ss_gram<R, 2>(U, Un, m, DU, gp);      // dU^T dU
     // ---- metrics and the stop test (warp 0) -----------------------------------------
     if (tid < 32) {
-      double v[6] = {0, 0, 0, 0, 0, 0};
+      double v[7] = {0, 0, 0, 0, 0, 0, 0};
       for (int e = tid; e < R * R; e += 32) {
+        const int k = e / R, l = e % R;
         v[0] = fma(Gn[e], Qn[e], v[0]);
-        v[1] = fma(XU[e], XV[e], v[1]);
-        v[2] = fma(G[e], Q[e], v[2]);
-        if (e / R == e % R) { v[3] += G[e]; v[4] += Q[e]; }
+        v[1] = fma(DU[e], Qn[e], v[1]);
+        v[2] = fma(XU[l * R + k], XV[e] + DV[e], v[2]);
+        v[6] = fma(G[e], DV[e], v[6]);
+        if (k == l) { v[3] += G[e]; v[4] += Q[e]; }
       }
       if (tid < kSSThreads / 32) v[5] = ws[tid];      // per-warp Huber partials
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1)
 #pragma unroll
-        for (int q = 0; q < 6; ++q) v[q] += __shfl_xor_sync(0xffffffffu, v[q], o);
+        for (int q = 0; q < 7; ++q) v[q] += __shfl_xor_sync(0xffffffffu, v[q], o);
       if (tid == 0) {
-        double d2 = v[0] - 2.0 * v[1] + v[2];
+        double d2 = v[1] + 2.0 * v[2] + v[6];
         if (d2 < 0) d2 = 0;
         const double dl = v[0] > 0 ? sqrt(d2 / v[0]) : INFINITY;
         const double obj = v[5] + 0.5 * (double)rho * (v[3] + v[4]);

@@ -215,3 +215,28 @@ def learned_instance(q: int, split: str = "train") -> Instance:
 LEARNED_RHO = 1e-2
 LEARNED_LAMBDA = 1.0 / 32.0     # 1 / sqrt(m)
 LEARNED_K = 10
+
+
+PHASE_N = 160
+PHASE_RANKS = (0.05, 0.075, 0.1, 0.125, 0.15, 0.175, 0.2)
+PHASE_DENSITIES = (0.05, 0.1, 0.15, 0.2, 0.25, 0.3)
+
+
+def phase_grid(n: int = PHASE_N, ranks=PHASE_RANKS, densities=PHASE_DENSITIES,
+               trials: int = 1, E: int = 4, seed: int = SEED_BASE + 5):
+    """Cells of the sparsity x rank sweep of §4.2 (the phase-transition figure):
+    m = n, truth rank r = ratio * n for each ratio in ``ranks`` (the solver runs
+    with that rank), S* density s for each s in ``densities``, values U[-10, 10],
+    N(0, 1/r) truth factors, E equal blocks, ``trials`` seeded instances per
+    cell.  rho = 1e-2 and lambda = 1/sqrt(n).  Returns a list of dicts (shape,
+    law and seed of every instance, cell coordinates under "cell")."""
+    out = []
+    for a, ratio in enumerate(ranks):
+        k = max(1, int(round(ratio * n)))
+        for b, dens in enumerate(densities):
+            for t in range(trials):
+                out.append(dict(m=n, n=n, k=k, r=k, density=float(dens), amp=10.0,
+                                factor_std=1.0 / np.sqrt(k), rho=1e-2, lam=1.0 / np.sqrt(n),
+                                n_i=equal_blocks(n, E), seed=seed * 1000 + 97 * a + 7 * b + t,
+                                cell=(float(ratio), float(dens), t)))
+    return out

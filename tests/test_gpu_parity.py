@@ -45,7 +45,7 @@ def small_ok(m, n, r):
     # the whole-solve kernel's shared memory (M with leading dimension m + 1,
     # two copies of U and V, W, the r x r workspace) within one SM
     R = 8 if r <= 8 else 16
-    smem = (8 * R * R * 8 + 2048 + 2 * R * R * 4 + 512 * 8 + ((m + 1) * n * 4 + 15) // 16 * 16
+    smem = (10 * R * R * 8 + 2048 + 2 * R * R * 4 + 512 * 8 + ((m + 1) * n * 4 + 15) // 16 * 16
             + 4 * (3 * m * R + 2 * n * R))
     return r <= 16 and smem + 2048 <= 232448
 
