@@ -48,6 +48,17 @@ dcf_status cuda_fail(dcf_handle h, cudaError_t e, const char* what) {
   return fail(h, DCF_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
 }
 
+// The fused path's concurrent tail (see dcf_create): the two-pass kernels'
+// bytes of M per CTA and second (counting both of their reads of M) relative
+// to a fused CTA's, at most this many strip groups, and only for problems of at
+// least this many 64-column strips.
+#ifndef DCF_TAIL_RATE
+#define DCF_TAIL_RATE 0.7
+#endif
+constexpr double kTailRate = DCF_TAIL_RATE;
+constexpr int kTailMaxGroups = 2;
+constexpr int kTailMinStrips = 128;
+
 #define CK(call, what)                                   \
   do {                                                   \
     cudaError_t e_ = (call);                             \
@@ -119,8 +130,10 @@ IterArgs iter_args(dcf_handle h, int cur) {
   a.alpha = h->alpha;
   a.ustar_out = h->ustar_out;
   if (h->path == 2) {
-    a.n_vblocks = h->cs * h->nclusters;   // per-CTA partials of the fused kernel
-    a.n_splits = h->nclusters;            // P partials: one per cluster
+    // per-CTA Huber partials of the fused kernel, then of the tail's pass A;
+    // P partials: one per cluster, then one per strip group of the tail
+    a.n_vblocks = h->cs * h->nclusters + (h->n_tail > 0 ? h->nslabs * h->G_tail : 0);
+    a.n_splits = h->nclusters + (h->n_tail > 0 ? h->G_tail : 0);
   }
   if (h->path == 3) {
     a.add_uxv = 1;
@@ -214,8 +227,47 @@ cudaError_t enqueue_fused_iteration(dcf_handle h, int cur, cudaStream_t s, cudaE
   fa.part_p = h->part_p;
   fa.st = h->st;
   fa.err = h->kerr;
-  if ((e = launch_fused(h->R, h->tmap, fa, s)) != cudaSuccess || (e = mark()) != cudaSuccess)
-    return e;
+  if (h->n_tail == 0) {
+    if ((e = launch_fused(h->R, h->tmap, fa, s)) != cudaSuccess || (e = mark()) != cudaSuccess)
+      return e;
+  } else {
+    // the fused kernel on the first n_head columns (its clusters first), and on
+    // the SMs they leave idle the two-pass kernels on the last n_tail columns:
+    // column sums (pass A), V' = V_old Z + their sum, P partials (pass B)
+    const int64_t n_head = h->n - h->n_tail;
+    fa.n = n_head;
+    if ((e = cudaEventRecord(h->ev_fork, s)) != cudaSuccess ||
+        (e = cudaStreamWaitEvent(h->tail_stream, h->ev_fork, 0)) != cudaSuccess ||
+        (e = launch_fused(h->R, h->tmap, fa, s, &h->prio_high)) != cudaSuccess)
+      return e;
+    cudaStream_t t = h->tail_stream;
+    Tc2Args ta{};
+    ta.cur = cur;
+    ta.nslabs = h->nslabs;
+    ta.G = h->G_tail;
+    ta.m = h->m;
+    ta.n = h->n_tail;
+    ta.lam = (float)h->lam;
+    ta.Vold = h->V[cur] + n_head * h->R;
+    ta.Vp = h->V[nxt] + n_head * h->R;
+    ta.img = h->img;
+    ta.scales = h->scales;
+    ta.vp_max = h->vmax_tail + nxt;
+    ta.ypart = h->ypart_tail;
+    ta.part_h = h->part_h + (size_t)h->cs * h->nclusters;
+    ta.part_p = h->part_p + (size_t)h->nclusters * h->m * h->R;
+    ta.st = h->st;
+    ta.err = h->kerr;
+    if ((e = cudaMemsetAsync(h->vmax_tail + nxt, 0, sizeof(unsigned int), t)) != cudaSuccess ||
+        (e = launch_tc2(h->R, 0, h->tmap_tail, ta, t)) != cudaSuccess ||
+        (e = launch_tc2_vreduce(h->R, h->ypart_tail, h->nslabs, h->W_vz + n_head * h->R,
+                                h->n_tail, h->V[nxt] + n_head * h->R, h->vmax_tail + nxt, h->st,
+                                h->num_sms, t, h->vmax + nxt)) != cudaSuccess ||
+        (e = launch_tc2(h->R, 1, h->tmap_tail, ta, t)) != cudaSuccess ||
+        (e = cudaEventRecord(h->ev_join, t)) != cudaSuccess ||
+        (e = cudaStreamWaitEvent(s, h->ev_join, 0)) != cudaSuccess || (e = mark()) != cudaSuccess)
+      return e;
+  }
   // Q_t = V_t^T V_t and V_{t-1}^T V_t from the new V (Gram partials)
   if ((e = launch_gram_vv(h->R, h->V[cur], h->V[nxt], h->n, h->part_q, h->part_xv, h->part_dv, h->n_vgram,
                           h->st, s)) != cudaSuccess ||
@@ -356,6 +408,7 @@ dcf_status apply_pending(dcf_handle h) {
   h->mcur = h->pend;
   h->M = h->Mbuf[h->mcur];
   std::memcpy(h->tmap, h->tmaps[h->mcur], sizeof(h->tmap));
+  std::memcpy(h->tmap_tail, h->tmaps_tail[h->mcur], sizeof(h->tmap_tail));
   h->pend = -1;
   return DCF_OK;
 }
@@ -578,6 +631,24 @@ extern "C" dcf_status dcf_create(const dcf_params* p, dcf_handle* out) {
         h->nslabs = cs;
         const int64_t nstrips64 = (h->n + 63) / 64;
         h->nclusters = (int)std::min<int64_t>(ncl, nstrips64);
+        // the SMs the clusters leave idle (a cluster must fit in one GPC) take
+        // a share of the columns on the two-pass kernels, one CTA per SM and
+        // slab; the share balances the two rates (kTailRate: the two-pass
+        // kernels' bytes of M per CTA and second, two reads, relative to a
+        // fused CTA's), in whole 64-column strips, every tail CTA with a strip
+        const int idle = h->num_sms - h->cs * h->nclusters;
+        const int gt = std::min(idle / h->nslabs, kTailMaxGroups);
+        if (h->nclusters == ncl && gt >= 1 && nstrips64 >= kTailMinStrips) {
+          const double tr = kTailRate * gt * h->nslabs;
+          int64_t st = (int64_t)((double)nstrips64 * tr / (tr + h->cs * h->nclusters));
+          st = std::min<int64_t>(st, nstrips64 - h->nclusters);   // every cluster keeps a strip
+          if (st >= 2 * gt && tc2_prepare(Rf) == cudaSuccess) {
+            // whole strips for the head: a ragged last strip goes to the tail
+            h->G_tail = gt;
+            h->n_tail = st * 64 - (h->n % 64 ? 64 - h->n % 64 : 0);
+          }
+          cudaGetLastError();
+        }
       } else if (p->path == 2) {
         dcf_destroy(h);
         return DCF_EINVAL;
@@ -657,13 +728,19 @@ extern "C" dcf_status dcf_create(const dcf_params* p, dcf_handle* out) {
   h->kerr = (int*)A(sizeof(int));
   if (h->path == 2) {
     const size_t grid = (size_t)h->cs * h->nclusters;
+    const size_t tail_ctas = h->n_tail > 0 ? (size_t)h->nslabs * h->G_tail : 0;
+    const size_t tail_groups = h->n_tail > 0 ? (size_t)h->G_tail : 0;
     h->img = (uint8_t*)A((size_t)h->nslabs * 2048 * R);
     h->scales = (float*)A((2 * (size_t)h->nslabs + 1) * sizeof(float));
     h->zmat = (float*)A(RR * sizeof(float));
     h->W_vz = (float*)A((size_t)h->n * R * sizeof(float));
     h->vmax = (unsigned int*)A(2 * sizeof(unsigned int));
-    h->part_p = (float*)A((size_t)h->nclusters * h->m * R * 4);
-    h->part_h = (double*)A(grid * 8);
+    h->part_p = (float*)A(((size_t)h->nclusters + tail_groups) * h->m * R * 4);
+    h->part_h = (double*)A((grid + tail_ctas) * 8);
+    if (h->n_tail > 0) {
+      h->ypart_tail = (float*)A((size_t)h->nslabs * h->n_tail * R * sizeof(float));
+      h->vmax_tail = (unsigned int*)A(2 * sizeof(unsigned int));
+    }
   }
   if (h->path == 3) {
     h->img = (uint8_t*)A((size_t)h->nslabs * 2048 * R);
@@ -678,6 +755,20 @@ extern "C" dcf_status dcf_create(const dcf_params* p, dcf_handle* out) {
   if (!ok) {
     dcf_destroy(h);
     return DCF_ENOMEM;
+  }
+  if (h->n_tail > 0) {
+    // the tail's stream at the lowest priority, the fused kernel at the highest,
+    // so that its clusters are placed before the tail's CTAs fill the rest
+    int least = 0, greatest = 0;
+    if (cudaDeviceGetStreamPriorityRange(&least, &greatest) != cudaSuccess ||
+        cudaStreamCreateWithPriority(&h->tail_stream, cudaStreamNonBlocking, least) !=
+            cudaSuccess ||
+        cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming) != cudaSuccess) {
+      dcf_destroy(h);
+      return DCF_ECUDA;
+    }
+    h->prio_high = greatest;
   }
   if (cudaMemsetAsync(h->U[0], 0, h->m * R * 4, h->stream) != cudaSuccess ||
       cudaMemsetAsync(h->U[1], 0, h->m * R * 4, h->stream) != cudaSuccess ||
@@ -790,6 +881,9 @@ static dcf_status ensure_mbuf(dcf_handle h, int b) {
   if (!h->Mbuf[b]) return fail(h, DCF_ENOMEM, "cannot allocate M");
   if ((h->path == 2 || h->path == 3) && fused_make_tmap(h->tmaps[b], h->Mbuf[b], h->m, h->n) != 0)
     return fail(h, DCF_ECUDA, "cuTensorMapEncodeTiled failed for M");
+  if (h->n_tail > 0 && fused_make_tmap(h->tmaps_tail[b], h->Mbuf[b] + (h->n - h->n_tail) * h->m,
+                                       h->m, h->n_tail) != 0)
+    return fail(h, DCF_ECUDA, "cuTensorMapEncodeTiled failed for the tail of M");
   return DCF_OK;
 }
 
@@ -844,8 +938,12 @@ extern "C" dcf_status dcf_load_blocks(dcf_handle h, const float* const* M_i, con
     if (h->M_borrowed) {
       if (fused_make_tmap(h->tmap, h->M, h->m, h->n) != 0)
         return fail(h, DCF_ECUDA, "cuTensorMapEncodeTiled failed for M");
+      if (h->n_tail > 0 &&
+          fused_make_tmap(h->tmap_tail, h->M + (h->n - h->n_tail) * h->m, h->m, h->n_tail) != 0)
+        return fail(h, DCF_ECUDA, "cuTensorMapEncodeTiled failed for the tail of M");
     } else {
       std::memcpy(h->tmap, h->tmaps[h->mcur], sizeof(h->tmap));
+      std::memcpy(h->tmap_tail, h->tmaps_tail[h->mcur], sizeof(h->tmap_tail));
     }
   }
   h->loaded = true;
@@ -1345,6 +1443,9 @@ extern "C" void dcf_destroy(dcf_handle h) {
   for (int b = 0; b < 2; ++b)
     if (h->ev_used[b]) cudaEventDestroy(h->ev_used[b]);
   if (h->stream) cudaStreamDestroy(h->stream);
+  if (h->tail_stream) cudaStreamDestroy(h->tail_stream);
+  if (h->ev_fork) cudaEventDestroy(h->ev_fork);
+  if (h->ev_join) cudaEventDestroy(h->ev_join);
   if (h->side) cudaStreamDestroy(h->side);
   if (h->side2) cudaStreamDestroy(h->side2);
   delete h;

@@ -85,6 +85,18 @@ struct dcf_handle_s {
   unsigned int* vmax = nullptr;       // [2]: max |V| of copy 0 / 1 (float bits)
   float* ypart = nullptr;             // two-pass tensor core: [nslabs][n][R] column sums
   int G = 0;                          // two-pass tensor core: strip groups (CTAs per slab)
+  // fused path: the SMs that its clusters leave idle run the two-pass
+  // tensor-core kernels on the last n_tail columns, concurrently with the fused
+  // kernel on the first n - n_tail (0: not used)
+  int64_t n_tail = 0;
+  int G_tail = 0;                     // strip groups of the tail (CTAs per slab)
+  float* ypart_tail = nullptr;        // [nslabs][n_tail][R] column sums of the tail
+  unsigned int* vmax_tail = nullptr;  // [2]: max |V'| of the tail columns (float bits)
+  alignas(64) unsigned char tmap_tail[128];         // tensor map over the tail columns of M
+  alignas(64) unsigned char tmaps_tail[2][128];     // the same over Mbuf[0], Mbuf[1]
+  cudaStream_t tail_stream = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  int prio_high = 0;                  // scheduling priority of the fused kernel
   int* kerr = nullptr;                // kernel-side error (DCF_ETIMEOUT)
   alignas(64) unsigned char tmap[128];
   // state

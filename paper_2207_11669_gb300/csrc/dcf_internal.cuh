@@ -247,7 +247,9 @@ struct FusedArgs {
   int* err;
   const void* tmap_g;       // tensor map of M in global memory (table launches)
 };
-cudaError_t launch_fused(int R, const void* tmap, const FusedArgs& fa, cudaStream_t s);
+// priority: NULL, or the scheduling priority of the launch (lower = sooner)
+cudaError_t launch_fused(int R, const void* tmap, const FusedArgs& fa, cudaStream_t s,
+                         const int* priority = nullptr);
 // Many problems in one launch: cluster c runs every strip of problem table[c]
 // (cs CTAs each; table in device memory, nclusters entries, each with its own
 // tensor map in tmap_g, nclusters = 1 and cs equal to the launch's).
@@ -299,9 +301,10 @@ struct Tc2Args {
 };
 cudaError_t tc2_prepare(int R);
 cudaError_t launch_tc2(int R, int pass_b, const void* tmap, const Tc2Args& a, cudaStream_t s);
+// V' = V_old Z + sum over slabs; max |V'| into vmax and, when non-NULL, vmax_all.
 cudaError_t launch_tc2_vreduce(int R, const float* ypart, int nslabs, const float* VZ, int64_t n,
                                float* Vnew, unsigned int* vmax, const DevState* st,
-                               int num_sms, cudaStream_t s);
+                               int num_sms, cudaStream_t s, unsigned int* vmax_all = nullptr);
 // The image preparation of the tensor-core paths also takes R = 64 (dynamic
 // shared memory above 48 KB): call once per process before the first launch.
 cudaError_t fused_prep_prepare();

@@ -1058,26 +1058,34 @@ cudaError_t fused_prep_prepare() {
 }
 
 template <int R, int NST>
-static cudaError_t launch_fused_T(const void* tmap, const FusedArgs& fa, cudaStream_t s) {
+static cudaError_t launch_fused_T(const void* tmap, const FusedArgs& fa, cudaStream_t s,
+                                  const int* priority) {
   cudaLaunchConfig_t cfg{};
   cfg.gridDim = dim3(fa.cs * fa.nclusters, 1, 1);
   cfg.blockDim = dim3(kFThreads, 1, 1);
   cfg.dynamicSmemBytes = fused_smem<R, NST>();
   cfg.stream = s;
-  cudaLaunchAttribute attr[1];
+  cudaLaunchAttribute attr[2];
   attr[0].id = cudaLaunchAttributeClusterDimension;
   attr[0].val.clusterDim.x = fa.cs;
   attr[0].val.clusterDim.y = 1;
   attr[0].val.clusterDim.z = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
+  if (priority) {
+    attr[1].id = cudaLaunchAttributePriority;
+    attr[1].val.priority = *priority;
+    cfg.numAttrs = 2;
+  }
   const CUtensorMap* tm = reinterpret_cast<const CUtensorMap*>(tmap);
   return cudaLaunchKernelEx(&cfg, k_fused<R, NST, false>, *tm, fa,
                             static_cast<const FusedArgs*>(nullptr));
 }
 
-cudaError_t launch_fused(int R, const void* tmap, const FusedArgs& fa, cudaStream_t s) {
-  return R == 16 ? launch_fused_T<16, kNST16>(tmap, fa, s) : launch_fused_T<32, kNST32>(tmap, fa, s);
+cudaError_t launch_fused(int R, const void* tmap, const FusedArgs& fa, cudaStream_t s,
+                         const int* priority) {
+  return R == 16 ? launch_fused_T<16, kNST16>(tmap, fa, s, priority)
+                 : launch_fused_T<32, kNST32>(tmap, fa, s, priority);
 }
 
 template <int R, int NST>

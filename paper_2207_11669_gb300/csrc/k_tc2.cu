@@ -589,7 +589,8 @@ __global__ void __launch_bounds__(256) k_tc2_vreduce(const float* __restrict__ y
                                                      int nslabs, const float* __restrict__ VZ,
                                                      int64_t count4, int64_t slab_stride4,
                                                      float* __restrict__ Vnew,
-                                                     unsigned int* vmax, const DevState* st) {
+                                                     unsigned int* vmax, const DevState* st,
+                                                     unsigned int* vmax_all) {
   if (st->stop) return;
   float mx = 0.f;
   const float4* y4 = reinterpret_cast<const float4*>(ypart);
@@ -607,7 +608,10 @@ __global__ void __launch_bounds__(256) k_tc2_vreduce(const float* __restrict__ y
     mx = fmaxf(mx, fmaxf(fmaxf(fabsf(acc.x), fabsf(acc.y)), fmaxf(fabsf(acc.z), fabsf(acc.w))));
   }
   for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-  if ((threadIdx.x & 31) == 0 && mx > 0.f) atomicMax(vmax, __float_as_uint(mx));
+  if ((threadIdx.x & 31) == 0 && mx > 0.f) {
+    atomicMax(vmax, __float_as_uint(mx));
+    if (vmax_all) atomicMax(vmax_all, __float_as_uint(mx));
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -664,13 +668,13 @@ cudaError_t launch_tc2(int R, int pass_b, const void* tmap, const Tc2Args& a, cu
 
 cudaError_t launch_tc2_vreduce(int R, const float* ypart, int nslabs, const float* VZ, int64_t n,
                                float* Vnew, unsigned int* vmax, const DevState* st,
-                               int num_sms, cudaStream_t s) {
+                               int num_sms, cudaStream_t s, unsigned int* vmax_all) {
   const int64_t count4 = n * R / 4;
   int64_t blocks = (count4 + 255) / 256;
   if (blocks > 8LL * num_sms) blocks = 8LL * num_sms;
   if (blocks < 1) blocks = 1;
   k_tc2_vreduce<<<(unsigned)blocks, 256, 0, s>>>(ypart, nslabs, VZ, count4, count4, Vnew, vmax,
-                                                 st);
+                                                 st, vmax_all);
   return cudaGetLastError();
 }
 
