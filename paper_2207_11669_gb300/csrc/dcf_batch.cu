@@ -75,10 +75,11 @@ struct FusedWave {
 };
 struct FusedGroup {
   int R = 0, cs = 0;
+  int ncl = 0;                            // clusters of this shape that fit on the GPU
   std::vector<int> insts;                 // largest first
   std::vector<FusedWave> waves;
 };
-constexpr int kFusedLanes = 8;            // side streams of the fused phase
+constexpr int kFusedLanes = 16;           // side streams of the fused phase (at most)
 
 constexpr int64_t kFusedMaxM = 4096;      // 16 slabs of 256 rows
 
@@ -105,6 +106,8 @@ struct dcf_batch_s {
   cudaEvent_t forked = nullptr;
   std::vector<cudaStream_t> lanes;
   std::vector<cudaEvent_t> joined;
+  int nlanes = 0;                         // side streams in use (tuned)
+  int wave_div = 1;                       // waves of ncl / wave_div clusters (tuned)
   // allocation
   dcf_alloc_fn alloc = nullptr;
   dcf_free_fn release = nullptr;
@@ -245,6 +248,23 @@ const char* const kBatchPhases[] = {"make_w", "pass1_vstep", "pass2_pstep", "gra
                                     "reduce_q", "rows_ustep", "reduce_g"};
 constexpr int kNumBatchPhases = 7;
 
+// The single pass over M of every fused instance: the waves on the side
+// streams in use, forked from and joined back to s.
+cudaError_t enqueue_fused_phase(dcf_batch b, int cur, cudaStream_t s) {
+  cudaError_t e = cudaEventRecord(b->forked, s);
+  for (int l = 0; l < b->nlanes; ++l)
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(b->lanes[l], b->forked, 0);
+  for (const FusedGroup& g : b->fgroups)
+    for (const FusedWave& wv : g.waves)
+      if (e == cudaSuccess)
+        e = launch_fused_table(g.R, g.cs, wv.nclusters, wv.table[cur], b->lanes[wv.lane]);
+  for (int l = 0; l < b->nlanes; ++l) {
+    if (e == cudaSuccess) e = cudaEventRecord(b->joined[l], b->lanes[l]);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(s, b->joined[l], 0);
+  }
+  return e;
+}
+
 // One iteration of every running instance, reading copy `cur`: each phase for
 // every rank class, then the next phase.  With ev, ev[p] is recorded after
 // phase p (profiling; not captured).
@@ -295,17 +315,7 @@ cudaError_t enqueue_batch_iteration(dcf_batch b, int cur, cudaStream_t s,
     if (ph == 1 && !b->fgroups.empty()) {
       // the single pass over M of every fused instance: waves on the side
       // streams (forked here, joined before the next phase)
-      if (e == cudaSuccess) e = cudaEventRecord(b->forked, s);
-      for (cudaStream_t ln : b->lanes)
-        if (e == cudaSuccess) e = cudaStreamWaitEvent(ln, b->forked, 0);
-      for (const FusedGroup& g : b->fgroups)
-        for (const FusedWave& wv : g.waves)
-          if (e == cudaSuccess)
-            e = launch_fused_table(g.R, g.cs, wv.nclusters, wv.table[cur], b->lanes[wv.lane]);
-      for (size_t l = 0; l < b->lanes.size(); ++l) {
-        if (e == cudaSuccess) e = cudaEventRecord(b->joined[l], b->lanes[l]);
-        if (e == cudaSuccess) e = cudaStreamWaitEvent(s, b->joined[l], 0);
-      }
+      if (e == cudaSuccess) e = enqueue_fused_phase(b, cur, s);
     }
     if (e != cudaSuccess) return e;
     if (ev && (e = cudaEventRecord(ev[ph], s)) != cudaSuccess) return e;
@@ -393,6 +403,92 @@ dcf_status batch_init(dcf_batch b) {
   return DCF_OK;
 }
 
+// Waves of every fused group: its instances (largest first) in launches of at
+// most ncl / div clusters, with an argument table per copy parity.
+dcf_status build_waves(dcf_batch b, int div) {
+  b->wave_div = div;
+  for (FusedGroup& g : b->fgroups) {
+    g.waves.clear();
+    const int cap = std::max(1, g.ncl / div);
+    for (size_t w0 = 0; w0 < g.insts.size(); w0 += (size_t)cap) {
+      FusedWave wv;
+      wv.nclusters = (int)std::min<size_t>((size_t)cap, g.insts.size() - w0);
+      wv.cost = (int64_t)b->host[g.insts[w0]].n_strips * g.cs;
+      for (int cur = 0; cur < 2; ++cur) {
+        std::vector<FusedArgs> tab(wv.nclusters);
+        for (int c = 0; c < wv.nclusters; ++c) {
+          const int q = g.insts[w0 + c];
+          const BInst& I = b->host[q];
+          FusedArgs& f = tab[c];
+          f = FusedArgs{};
+          f.cur = cur;
+          f.cs = g.cs;
+          f.nclusters = 1;
+          f.nslabs = I.nslabs;
+          f.m = I.m;
+          f.n = I.n;
+          f.lam = I.lam;
+          f.Vold = I.V[cur];
+          f.Vnew = I.V[cur ^ 1];
+          f.img = I.img;
+          f.scales = I.scales;
+          f.zmat = I.zmat;
+          f.VZ = I.VZ;
+          f.vmax_out = I.vmax + (cur ^ 1);
+          f.part_h = I.part_h;
+          f.part_p = I.part_p;
+          f.st = I.st;
+          f.err = b->kerr;
+          f.tmap_g = b->tmaps[q];
+        }
+        wv.table[cur] = upload(b, tab);
+        if (!wv.table[cur]) return bfail(b, DCF_ENOMEM, "wave tables");
+      }
+      g.waves.push_back(wv);
+    }
+  }
+  return DCF_OK;
+}
+
+// The waves dealt, longest first, to the least loaded of `nl` side streams.
+void deal_lanes(dcf_batch b, int nl) {
+  std::vector<FusedWave*> all;
+  for (FusedGroup& g : b->fgroups)
+    for (FusedWave& wv : g.waves) all.push_back(&wv);
+  std::stable_sort(all.begin(), all.end(),
+                   [](const FusedWave* x, const FusedWave* y) { return x->cost > y->cost; });
+  nl = std::max(1, std::min(nl, (int)b->lanes.size()));
+  b->nlanes = std::min<int>(nl, (int)std::max<size_t>(1, all.size()));
+  std::vector<int64_t> load(b->nlanes, 0);
+  for (FusedWave* wv : all) {
+    const int l = (int)(std::min_element(load.begin(), load.end()) - load.begin());
+    wv->lane = l;
+    load[l] += wv->cost;
+  }
+}
+
+// Median device time (ms) of `reps` fused phases on the batch stream, with the
+// current waves and lanes, reading copy 0 (the images of copy 0 are prepared).
+float time_fused_phase(dcf_batch b, int reps) {
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  std::vector<float> t;
+  for (int i = 0; i < reps; ++i) {
+    cudaEventRecord(e0, b->stream);
+    enqueue_fused_phase(b, 0, b->stream);
+    cudaEventRecord(e1, b->stream);
+    cudaEventSynchronize(e1);
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    t.push_back(ms);
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  std::sort(t.begin(), t.end());
+  return t[t.size() / 2];
+}
+
 // Time `reps` launches of one pass of one class (median, ms).
 float time_pass(dcf_batch b, int k, int which, int reps) {
   BatchClass& c = b->cls[k];
@@ -472,13 +568,50 @@ dcf_status batch_tune(dcf_batch b, int reps) {
              kClassR[k], c.grid_p1, sbest, g2best);
     b->tune_report += line;
   }
-  for (const FusedGroup& g : b->fgroups) {
-    snprintf(line, sizeof(line),
-             "R=%d cs=%d chosen: tensor-core kernel, %d instances in %d waves of up to %d "
-             "clusters\n",
-             g.R, g.cs, (int)g.insts.size(), (int)g.waves.size(),
-             g.waves.empty() ? 0 : g.waves[0].nclusters);
-    b->tune_report += line;
+  if (!b->fgroups.empty()) {
+    // the tensor-core pass of the fused instances: wave size (ncl / div
+    // clusters per launch) and side streams, timed as a whole phase on the
+    // batch itself (the images and V_old Z of copy 0 prepared first)
+    for (int k = 0; k < kClasses; ++k) {
+      BatchClass& c = b->cls[k];
+      if (c.insts.empty()) continue;
+      BCK(launch_bfused_small(kClassR[k], 0, b->dev, c.fp, c.n_fp, grid_for(c.n_fp, 4 * S), 0,
+                              b->stream), "tune images");
+      BCK(launch_bfused_small(kClassR[k], 1, b->dev, c.fr, c.n_fr, grid_for(c.n_fr, 8 * S), 0,
+                              b->stream), "tune V_old Z");
+    }
+    float best = 1e30f;
+    int bdiv = 1, blanes = (int)b->lanes.size();
+    for (int div : {1, 2}) {
+      dcf_status st = build_waves(b, div);
+      if (st != DCF_OK) return st;
+      for (int nl : {1, 2, 4, 8, 16}) {
+        if (nl > (int)b->lanes.size()) continue;
+        deal_lanes(b, nl);
+        time_fused_phase(b, 1);
+        const float t = time_fused_phase(b, reps);
+        BCK(cudaGetLastError(), "tune fused phase");
+        int nw = 0;
+        for (const FusedGroup& g : b->fgroups) nw += (int)g.waves.size();
+        snprintf(line, sizeof(line),
+                 "tensor-core pass: waves of ncl/%d clusters (%d waves), %d side streams: "
+                 "%.4f ms\n", div, nw, b->nlanes, t);
+        b->tune_report += line;
+        if (t < best) { best = t; bdiv = div; blanes = nl; }
+      }
+    }
+    dcf_status st = build_waves(b, bdiv);
+    if (st != DCF_OK) return st;
+    deal_lanes(b, blanes);
+    for (const FusedGroup& g : b->fgroups) {
+      snprintf(line, sizeof(line),
+               "R=%d cs=%d chosen: tensor-core kernel, %d instances in %d waves of up to %d "
+               "clusters on %d side streams (%.4f ms for the whole pass)\n",
+               g.R, g.cs, (int)g.insts.size(), (int)g.waves.size(),
+               g.waves.empty() ? 0 : g.waves[0].nclusters, b->nlanes, best);
+      b->tune_report += line;
+    }
+    // the timed phases wrote copy 1 and its max |V|: the first step rewrites them
   }
   BCK(cudaMemcpyAsync(b->dev, b->host.data(), b->host.size() * sizeof(BInst),
                       cudaMemcpyHostToDevice, b->stream), "descriptors");
@@ -719,64 +852,19 @@ extern "C" dcf_status dcf_batch_create(const dcf_problem* problems, int count, i
     std::stable_sort(g.insts.begin(), g.insts.end(), [&](int x, int y) {
       return b->host[x].n_strips > b->host[y].n_strips;
     });
-    const int ncl = fused_max_clusters(g.R, g.cs);
-    for (size_t w0 = 0; w0 < g.insts.size(); w0 += (size_t)ncl) {
-      FusedWave wv;
-      wv.nclusters = (int)std::min<size_t>((size_t)ncl, g.insts.size() - w0);
-      wv.cost = (int64_t)b->host[g.insts[w0]].n_strips * g.cs;
-      for (int cur = 0; cur < 2; ++cur) {
-        std::vector<FusedArgs> tab(wv.nclusters);
-        for (int c = 0; c < wv.nclusters; ++c) {
-          const int q = g.insts[w0 + c];
-          const BInst& I = b->host[q];
-          FusedArgs& f = tab[c];
-          f = FusedArgs{};
-          f.cur = cur;
-          f.cs = g.cs;
-          f.nclusters = 1;
-          f.nslabs = I.nslabs;
-          f.m = I.m;
-          f.n = I.n;
-          f.lam = I.lam;
-          f.Vold = I.V[cur];
-          f.Vnew = I.V[cur ^ 1];
-          f.img = I.img;
-          f.scales = I.scales;
-          f.zmat = I.zmat;
-          f.VZ = I.VZ;
-          f.vmax_out = I.vmax + (cur ^ 1);
-          f.part_h = I.part_h;
-          f.part_p = I.part_p;
-          f.st = I.st;
-          f.err = b->kerr;
-          f.tmap_g = b->tmaps[q];
-        }
-        wv.table[cur] = upload(b, tab);
-        if (!wv.table[cur]) {
-          dcf_batch_destroy(b);
-          return DCF_ENOMEM;
-        }
-      }
-      g.waves.push_back(wv);
-    }
+    g.ncl = fused_max_clusters(g.R, g.cs);
   }
-  // side streams: waves dealt longest first to the least loaded stream
+  if (build_waves(b, 1) != DCF_OK) {
+    dcf_batch_destroy(b);
+    return DCF_ENOMEM;
+  }
+  // side streams (the tuner picks how many are used; 8 until then)
   {
-    std::vector<FusedWave*> all;
-    for (FusedGroup& g : b->fgroups)
-      for (FusedWave& wv : g.waves) all.push_back(&wv);
-    std::stable_sort(all.begin(), all.end(),
-                     [](const FusedWave* x, const FusedWave* y) { return x->cost > y->cost; });
-    const int nl = (int)std::min<size_t>(all.size(), (size_t)kFusedLanes);
-    std::vector<int64_t> load(nl, 0);
-    for (FusedWave* wv : all) {
-      const int l = (int)(std::min_element(load.begin(), load.end()) - load.begin());
-      wv->lane = l;
-      load[l] += wv->cost;
-    }
-    bool ok = !all.empty() ? cudaEventCreateWithFlags(&b->forked, cudaEventDisableTiming) ==
-                                 cudaSuccess
-                           : true;
+    int nw = 0;
+    for (const FusedGroup& g : b->fgroups) nw += (int)g.waves.size();
+    bool ok = nw > 0 ? cudaEventCreateWithFlags(&b->forked, cudaEventDisableTiming) == cudaSuccess
+                     : true;
+    const int nl = nw > 0 ? kFusedLanes : 0;
     b->lanes.assign(nl, nullptr);
     b->joined.assign(nl, nullptr);
     for (int l = 0; l < nl && ok; ++l)
@@ -787,6 +875,7 @@ extern "C" dcf_status dcf_batch_create(const dcf_problem* problems, int count, i
       dcf_batch_destroy(b);
       return DCF_ECUDA;
     }
+    if (nl > 0) deal_lanes(b, 8);
   }
   b->dev = upload(b, b->host);
   if (!b->dev || cudaStreamSynchronize(b->stream) != cudaSuccess) {

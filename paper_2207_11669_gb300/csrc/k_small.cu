@@ -34,6 +34,20 @@ __device__ __forceinline__ void two_sum_add(float& hi, float& lo, float x) {
   lo += err;
 }
 
+// hi + lo += x * y with the product's rounding error kept (the FMA gives the
+// exact error of the FP32 product): the compensated dot product "Dot2" of
+// Ogita, Rump and Oishi, "Accurate sum and dot product" (SIAM J. Sci. Comput.,
+// 2005), about twice FP32 precision.  Used for the Gram matrices whose
+// inverse the next step applies (U^T U, and the start point's Grams), so that
+// a nearly singular U^T U + rho I is not perturbed by the FP32 rounding of
+// its products.
+__device__ __forceinline__ void dot2_add(float& hi, float& lo, float x, float y) {
+  const float p = x * y;
+  const float e = fmaf(x, y, -p);
+  two_sum_add(hi, lo, p);
+  lo += e;
+}
+
 // ---------------------------------------------------------------------------
 // Gram partials:  part[b][k*cy + l] = sum_{rows a of CTA b} X[a,k] * Y[a,l]
 // as compensated pairs (hi, lo): FP32 sums per 32-row chunk, TwoSum across
@@ -78,16 +92,11 @@ k_gram_part(const float* __restrict__ X, int ldx, int cx,
       Ys[i] = rr < rows ? Y[(c + rr) * ldy + k] : 0.f;
     }
     __syncthreads();
-    float acc[kGramMaxEntriesPerThread];
-#pragma unroll
-    for (int s = 0; s < kGramMaxEntriesPerThread; ++s) acc[s] = 0.f;
     for (int rr = 0; rr < kGramChunk; ++rr) {   // rows past the end are zero
 #pragma unroll
       for (int s = 0; s < kGramMaxEntriesPerThread; ++s)
-        if (tid + s * 256 < ne) acc[s] = fmaf(Xs[rr * cx + xo[s]], Ys[rr * cy + yo[s]], acc[s]);
+        if (tid + s * 256 < ne) dot2_add(hi[s], lo[s], Xs[rr * cx + xo[s]], Ys[rr * cy + yo[s]]);
     }
-#pragma unroll
-    for (int s = 0; s < kGramMaxEntriesPerThread; ++s) two_sum_add(hi[s], lo[s], acc[s]);
   }
 #pragma unroll
   for (int s = 0; s < kGramMaxEntriesPerThread; ++s) {
@@ -578,7 +587,8 @@ __global__ void __launch_bounds__(256) k_make_w(const float* __restrict__ U,
   make_w_block<R>(U, sm, W, m, blockIdx.x);
 }
 
-// Gram partials over a CTA's rows of U: G = Un^T Un, Uo^T dU and dU^T dU with
+// Gram partials over a CTA's rows of U: G = Un^T Un (compensated products:
+// its inverse is applied in the next V-step), Uo^T dU and dU^T dU with
 // dU = Un - Uo (the change metric is formed from the last two, which are of
 // the size of the change).  Block-wide; Uo, Un: rows x R in shared memory.
 template <int R>
@@ -586,15 +596,15 @@ __device__ __forceinline__ void rows_gram_partials(const IterArgs& a, const floa
                                                    const float* Un, int rows, int64_t rb) {
   for (int e = threadIdx.x; e < R * R; e += blockDim.x) {
     const int k = e / R, l = e % R;
-    float gg = 0.f, xu = 0.f, du = 0.f;
+    float gh = 0.f, gl = 0.f, xu = 0.f, du = 0.f;
     for (int rr = 0; rr < rows; ++rr) {
       const float dk = Un[rr * R + k] - Uo[rr * R + k];
       const float dl = Un[rr * R + l] - Uo[rr * R + l];
-      gg = fmaf(Un[rr * R + k], Un[rr * R + l], gg);
+      dot2_add(gh, gl, Un[rr * R + k], Un[rr * R + l]);
       xu = fmaf(Uo[rr * R + k], dl, xu);
       du = fmaf(dk, dl, du);
     }
-    a.part_g[rb * R * R + e] = make_float2(gg, 0.f);
+    a.part_g[rb * R * R + e] = make_float2(gh, gl);
     a.part_xu[rb * R * R + e] = make_float2(xu, 0.f);
     a.part_du[rb * R * R + e] = make_float2(du, 0.f);
   }
