@@ -109,6 +109,12 @@ void dcf_set_allocator(dcf_alloc_fn alloc, dcf_free_fn release, void* ctx);
  * dcf_last_error() carries a warning. */
 dcf_status dcf_create(const dcf_params* p, dcf_handle* out);
 
+/* (No counterpart in the paper.)  Kernels one iteration launches on the handle's
+ * path (graph nodes that are kernels): 7 general, 6 fused (9 when the fused
+ * kernel's idle SMs run a share of the columns on the two-pass kernels), 8
+ * two-pass tensor core, 1 whole solve (per call); -1 with local_steps > 1. */
+int dcf_kernels_per_iteration(dcf_handle h);
+
 /* (No counterpart in the paper.)  Which kernels run an iteration: 1 general two-pass path, 2 fused
  * single-pass tensor-core path, 3 two-pass tensor-core path, 4 whole solve in
  * one CTA. */

@@ -823,6 +823,17 @@ extern "C" dcf_status dcf_create(const dcf_params* p, dcf_handle* out) {
   return DCF_OK;
 }
 
+extern "C" int dcf_kernels_per_iteration(dcf_handle h) {
+  if (!h) return 0;
+  if (!h->clients.empty()) return -1;   // rounds of local steps: not one fixed graph
+  switch (h->path) {
+    case 2: return h->n_tail > 0 ? 9 : 6;   // + the tail's pass A, V' reduction, pass B
+    case 3: return 8;
+    case 4: return 1;                      // every iteration of a call in one launch
+    default: return 7;
+  }
+}
+
 extern "C" int dcf_get_path(dcf_handle h) {
   if (!h) return 0;
   return h->clients.empty() ? h->path : h->client_path;

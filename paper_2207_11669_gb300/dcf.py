@@ -51,6 +51,7 @@ _SIGS = {
     "dcf_create": (C.c_int, [C.POINTER(dcf_params), C.POINTER(C.c_void_p)]),
     "dcf_set_stream": (C.c_int, [C.c_void_p, C.c_void_p]),
     "dcf_get_path": (C.c_int, [C.c_void_p]),
+    "dcf_kernels_per_iteration": (C.c_int, [C.c_void_p]),
     "dcf_load_blocks": (C.c_int, [C.c_void_p, C.POINTER(C.c_void_p), C.POINTER(C.c_int64),
                                   C.c_int, C.c_int]),
     "dcf_reload_blocks": (C.c_int, [C.c_void_p, C.POINTER(C.c_void_p), C.POINTER(C.c_int64),
@@ -197,6 +198,10 @@ def dcf_create(m, n_i, r, rho, lam, max_iter=100, tol=1e-6, u_mode=0, local_step
     if st != DCF_OK:
         raise DcfError(st, "dcf_create rejected the parameters")
     return h
+
+
+def dcf_kernels_per_iteration(h):
+    return lib().dcf_kernels_per_iteration(h)
 
 
 def dcf_get_path(h):
