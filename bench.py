@@ -174,8 +174,8 @@ NCU_TRAFFIC = {
     # k_tc2_vreduce (5.86 MB) and pass B (45.31 MB) on the last 2688
     "fused_step": {"m": 4096, "r": 32, "n": 16384, "bytes": 330.06e6},
     # k_tc2<64, 5, false> / k_tc2<64, 7, true>, m=16384, n=16384, r=64
-    "pass_a": {"m": 16384, "r": 64, "n": 16384, "bytes": 1334.88e6},
-    "pass_b": {"m": 16384, "r": 64, "n": 16384, "bytes": 1086.84e6},
+    "pass_a": {"m": 16384, "r": 64, "n": 16384, "bytes": 1334.76e6},
+    "pass_b": {"m": 16384, "r": 64, "n": 16384, "bytes": 1086.43e6},
 }
 
 
@@ -646,6 +646,7 @@ def run_batched(args):
                                           "general two-pass item lists otherwise; one CUDA "
                                           "graph per iteration",
                            "tuned": chosen,
+                           "tune_report": [ln for ln in report.splitlines() if ln.strip()],
                            "l2": "inputs larger than L2 (%.1f GB of M)" % (bytes_m / 1e9)},
                 "clocks": clk,
                 "roofline": {"bound": "hbm", "kernel": "whole batched iteration",
@@ -765,10 +766,33 @@ def learned_rows(dcf, torch, args, rank, stream, count):
         # one plain iteration's launches, one final re-factorisation, the refinement
         L = dcf.dcf_kernels_per_iteration(s.h)
         K = len(theta[0])
-        rows.append(dict(n_plain=n_plain, n_refine=n_ref, plain_ms=times["plain"][0],
-                         learned_ms=times["learned"][0], plain_wall_ms=times["plain"][1],
-                         learned_wall_ms=times["learned"][1],
-                         learned_launches=(1 + L) * K + 1 + n_ref * L))
+        row = dict(n_plain=n_plain, n_refine=n_ref, plain_ms=times["plain"][0],
+                   learned_ms=times["learned"][0], plain_wall_ms=times["plain"][1],
+                   learned_wall_ms=times["learned"][1],
+                   learned_launches=(1 + L) * K + 1 + n_ref * L)
+        if q == 0:
+            # one training step of this problem: the network's forward with its loss
+            # (checkpoints) and the hand-written reverse pass, which recomputes each
+            # step from its checkpoint and reads M three times per step
+            fwd, bwd = [], []
+            for _ in range(3):
+                s.load_init(U0)
+                torch.cuda.synchronize()
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e2 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                s.unrolled_forward(*theta)
+                e1.record(stream)
+                s.unrolled_backward(K)
+                e2.record(stream)
+                torch.cuda.synchronize()
+                fwd.append(e0.elapsed_time(e1))
+                bwd.append(e1.elapsed_time(e2))
+            b_ms = min(bwd)
+            row.update(train_forward_ms=min(fwd), train_backward_ms=b_ms,
+                       backward_gbs=K * 3 * 4.0 * m * n / (b_ms * 1e-3) / 1e9)
+        rows.append(row)
         s.close()
         del Mt
     return rows, th
@@ -784,7 +808,14 @@ def learned_summary(rows_th):
             "plain_ms": plain, "learned_plus_refine_ms": learned,
             "speedup_vs_plain": plain / learned,
             "plain_iterations": [r["n_plain"] for r in rows],
-            "refine_iterations": [r["n_refine"] for r in rows]}
+            "refine_iterations": [r["n_refine"] for r in rows],
+            "training_step_per_problem": {
+                "forward_with_loss_ms": rows[0].get("train_forward_ms"),
+                "backward_ms": rows[0].get("train_backward_ms"),
+                "backward_alg_gbs": rows[0].get("backward_gbs"),
+                "backward_bytes": "K steps x 3 reads of M (4mn bytes each)",
+                "adam_step_of_64_problems_ms_estimate":
+                    64 * (rows[0].get("train_forward_ms", 0) + rows[0].get("train_backward_ms", 0))}}
 
 
 def run_learned(args):

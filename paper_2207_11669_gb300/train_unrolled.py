@@ -42,7 +42,8 @@ def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--out", required=True)
     ap.add_argument("--problems", type=int, default=64)
-    ap.add_argument("--per-step", type=int, default=16, help="problems per Adam step")
+    ap.add_argument("--per-step", type=int, default=64,
+                    help="problems per Adam step (the batch of 64 of the learned workload)")
     ap.add_argument("--steps", type=int, default=40)
     ap.add_argument("--lr", type=float, default=0.05)
     ap.add_argument("--fp-iters", type=int, default=1500)
@@ -57,7 +58,9 @@ def main():
     hist = []
     t0 = time.time()
     rng = np.random.default_rng(0)
+    step_s = []
     for it in range(args.steps):
+        ts = time.time()
         pick = rng.choice(len(probs), size=min(args.per_step, len(probs)), replace=False)
         opt.zero_grad()
         total = 0.0
@@ -67,14 +70,17 @@ def main():
             loss.backward()
             total += float(loss.detach())
         opt.step()
+        torch.cuda.synchronize()
+        step_s.append(time.time() - ts)
         hist.append(total)
-        print(f"step {it}: loss {total:.4e}", flush=True)
+        print(f"step {it}: loss {total:.4e} ({step_s[-1]:.3f} s)", flush=True)
     t_train = time.time() - t0
     a, b, c = net.theta()
     out = {"K": synth.LEARNED_K, "a": a.tolist(), "b": b.tolist(), "c": c.tolist(),
            "loss_history": hist, "problems": args.problems, "per_step": args.per_step,
            "adam_steps": args.steps, "lr": args.lr, "fixed_point_iters": args.fp_iters,
            "setup_s": t_setup, "train_s": t_train,
+           "adam_step_s_median": float(np.median(step_s)),
            "workload": "m=1024, n=16384 (E=8), rank 16, density 0.10, values U[-10,10], "
                        "rho=1e-2, lambda=1/32"}
     with open(args.out, "w") as f:
