@@ -72,7 +72,7 @@ typedef struct {
   int max_iter;         /* dcf_solve: iteration cap (>= 1)                    */
   double tol;           /* dcf_solve: stop when ||L_t-L_{t-1}||_F/||L_t||_F <= tol */
   int u_mode;           /* 0: exact consensus (default); 1: FedAvg gradient   */
-  int local_steps;      /* K of Algorithm 1; only 1 is supported               */
+  int local_steps;      /* K of Algorithm 1 (>= 1; > 1 needs u_mode = 1)      */
   double eta0;          /* FedAvg mode: eta_t = eta0 / sqrt(t + 1)             */
   uint64_t seed;        /* seed of the default initialisation                  */
   int path;             /* 0: automatic; 1: general two-pass kernels; 2: fused
@@ -104,7 +104,12 @@ void dcf_set_allocator(dcf_alloc_fn alloc, dcf_free_fn release, void* ctx);
  * §1 and Algorithm 1's round count and step size.
  * Validate `p` and create a handle.  Fails with DCF_EINVAL for m < 1, E < 1,
  * any n_i < 1, r outside [1, 64] or r > m, rho <= 0, lambda <= 0,
- * local_steps != 1, or u_mode not in {0, 1}.  When rho^2 > lambda^2 m n
+ * local_steps < 1, local_steps > 1 with u_mode != 1 (Algorithm 1's local
+ * steps are FedAvg gradient steps) or with the whole-solve path 4, or u_mode
+ * not in {0, 1}.  With local_steps = K > 1 every client iterates K times on
+ * its own block and its own copy U_i before the server averages the U_i
+ * (Algorithm 1 eqs. U_local, U_agg); dcf_reload_blocks_async and
+ * dcf_profile_step are not available then.  When rho^2 > lambda^2 m n
  * (the necessary condition of §3.2 fails) the handle is still created and
  * dcf_last_error() carries a warning. */
 dcf_status dcf_create(const dcf_params* p, dcf_handle* out);
@@ -212,6 +217,17 @@ dcf_status dcf_set_private(dcf_handle h, int i, int is_private);
  * (U_{t-1}, V_{t-1}, S_t), evaluated in its Huber form, the relative change
  * of L, and t.  Any pointer may be NULL. */
 dcf_status dcf_get_stats(dcf_handle h, double* objective, double* dL_rel, int* iter);
+
+/* (App. B eq. condition1: the ridge systems U^T U + rho I of the V-step and
+ * V^T V + rho I of the exact U-step.)
+ * 1-norm condition estimates |A|_1 |A^{-1}|_1 of the two r x r systems as the
+ * last iteration formed them (0 before the first; kappa_h stays 0 in FedAvg
+ * mode, which inverts no V-side system).  Above 100 the inverses are formed in
+ * double-float and applied with compensated products, and the Grams that feed
+ * them are summed with compensated products (about 1e-5 relative accuracy of
+ * the factors up to kappa ~ 1e8 instead of FP32 rounding times kappa).  Either
+ * pointer may be NULL. */
+dcf_status dcf_get_conditioning(dcf_handle h, double* kappa_g, double* kappa_h);
 
 /* The ground truth of the synthetic experiments of §4.1 (L0 = A B^T) and
  * the relative error of L against it (§4.1 "Evaluation Metric", here the

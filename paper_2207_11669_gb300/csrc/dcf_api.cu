@@ -1280,6 +1280,17 @@ extern "C" dcf_status dcf_get_stats(dcf_handle h, double* objective, double* dL_
   return end_work(h);
 }
 
+extern "C" dcf_status dcf_get_conditioning(dcf_handle h, double* kappa_g, double* kappa_h) {
+  if (!h) return DCF_EINVAL;
+  dcf_status st = begin_work(h);
+  if (st != DCF_OK) return st;
+  DevState ds{};
+  if ((st = read_state(h, &ds)) != DCF_OK) return st;
+  if (kappa_g) *kappa_g = ds.kappa_g;
+  if (kappa_h) *kappa_h = ds.kappa_h;
+  return end_work(h);
+}
+
 extern "C" dcf_status dcf_set_truth(dcf_handle h, const float* A, const float* B, int k,
                                     int where) {
   if (!h) return DCF_EINVAL;

@@ -32,7 +32,20 @@ struct DevState {
   double huber;      // sum H_lambda(R) of the last pass
   double eta_fixed;  // FedAvg step size when > 0 (a client's local steps all use the
                      // step size of their communication round); 0: eta0 / sqrt(t + 1)
+  double kappa_g;    // 1-norm condition estimate of the latest U^T U + rho I
+  double kappa_h;    //   and of the latest V^T V + rho I (exact U-step)
 };
+
+// Condition estimate above which the r x r inverses are formed in double-float
+// and the steps that apply them, or that feed them with cancelling sums (W,
+// V_{t-1}^T V_t applied to U_{t-1}, the Grams of V), use compensated products.
+// Below it the FP32 rounding errors, amplified by at most kappa, stay under
+// about 1e-5 relative.
+constexpr double kDfKappa = 100.0;
+
+__device__ __forceinline__ bool df_route(const DevState* st) {
+  return st->kappa_g > kDfKappa || st->kappa_h > kDfKappa;
+}
 
 // r x r FP64 workspace of one problem.
 struct Smalls {
@@ -40,9 +53,11 @@ struct Smalls {
   double q[2][kMaxR * kMaxR];      // V^T V for copy 0/1 of V
   double xu[kMaxR * kMaxR];        // U_{t-1}^T (U_t - U_{t-1})
   double xv[kMaxR * kMaxR];        // V_{t-1}^T V_t
+  float xv32[2][kMaxR * kMaxR];    // V_{t-1}^T V_t as the float pair hi, lo
   double dvy[kMaxR * kMaxR];       // V_{t-1}^T (V_t - V_{t-1})
   double dvv[kMaxR * kMaxR];       // (V_t - V_{t-1})^T (V_t - V_{t-1})
-  float ginv32[kMaxR * kMaxR];     // (U^T U + rho I)^{-1} of the current U
+  float ginv32[kMaxR * kMaxR];     // (U^T U + rho I)^{-1} of the current U (hi part)
+  float ginv32_lo[kMaxR * kMaxR];  //   and its lo part (the inverse is hi + lo)
   float hinv32[kMaxR * kMaxR];     // (V^T V + rho I)^{-1} of the new V (exact mode)
   float qrho32[kMaxR * kMaxR];     // (V^T V + rho I) in float (FedAvg mode)
 };

@@ -6,8 +6,11 @@
 // of R dependent steps, so it runs in double-float arithmetic on the FP32
 // pipes (about 48 bits), packs its trailing updates across all threads of
 // the CTA, uses the root-free L D L^T form and replaces divisions by Newton
-// steps from the FP32 estimate.  The triangular inverse and the final
-// product are FP32 from the rounded factors and run one warp per column.
+// steps from the FP32 estimate.  The triangular inverse (one warp per column)
+// and the final product run in FP32 from the rounded factors when the system
+// is well-conditioned and in double-float otherwise; the double-float inverse
+// is handed on as a pair of floats (hi, lo), so that its consumers can apply
+// it to about twice FP32 precision.
 #pragma once
 #include <cuda_runtime.h>
 
@@ -50,6 +53,11 @@ static __device__ __forceinline__ df2 df_sub(df2 x, df2 y) {
   return df_fast_two_sum(s.h, s.l + (x.l - y.l));
 }
 
+static __device__ __forceinline__ df2 df_add(df2 x, df2 y) {
+  const df2 s = df_two_sum(x.h, y.h);
+  return df_fast_two_sum(s.h, s.l + (x.l + y.l));
+}
+
 // 1/d: the hardware reciprocal estimate x0 (relative error about 2^-22),
 // then one Newton step x0 + x0 (1 - d x0) with the residual formed exactly
 // enough in double-float: relative error about 2^-44.  d <= 0 or non-finite
@@ -89,15 +97,17 @@ static __device__ __forceinline__ df2 df_from_double(double x) {
 // 1/D_{k+1} right after its update.  One barrier per step.
 //
 // Input: A (R*R doubles, row-major, lower triangle read).  Output: F = L^T in
-// FP32 with 1/D_k on the diagonal (row p of F is column p of L) and zeros
-// below its diagonal; s_r[k] = 1/D_k.  A non-positive pivot leaves NaN.
+// double-float with 1/D_k on the diagonal (row p of F is column p of L) and
+// zeros below its diagonal; s_r[k] = 1/D_k; Ff (optional, may alias the space
+// of A, which is read only before the first barrier): the entries of F on and
+// above its diagonal rounded to FP32.  A non-positive pivot leaves NaN.
 // ---------------------------------------------------------------------------
 constexpr int kCholThreads = 256;
 
 // kCholSlots = ceil(R (R + 1) / 2 / 256) for the largest R of the instance
 template <int kCholSlots>
-static __device__ __noinline__ void chol_df_to_f(const double* A, int R, float* F, df2* col,
-                                                 df2* s_r) {
+static __device__ __noinline__ void chol_df(const double* A, int R, df2* F, float* Ff, df2* col,
+                                            df2* s_r) {
   const int tid = threadIdx.x;
   const int ne = R * (R + 1) / 2;
   df2 a[kCholSlots];
@@ -118,7 +128,7 @@ static __device__ __noinline__ void chol_df_to_f(const double* A, int R, float* 
     ei[q] = i;
     ej[q] = j;
   }
-  for (int idx = tid; idx < R * R; idx += kCholThreads) F[idx] = 0.f;
+  for (int idx = tid; idx < R * R; idx += kCholThreads) F[idx] = {0.f, 0.f};
   // column 0 and 1/D_0
 #pragma unroll
   for (int q = 0; q < kCholSlots; ++q) {
@@ -156,14 +166,9 @@ static __device__ __noinline__ void chol_df_to_f(const double* A, int R, float* 
   for (int q = 0; q < kCholSlots; ++q) {
     const int i = ei[q], j = ej[q];
     if (i < 0) continue;
-    float v;
-    if (j < i) {
-      const df2 l = df_mul(a[q], s_r[j]);
-      v = l.h + l.l;
-    } else {
-      v = s_r[i].h + s_r[i].l;
-    }
+    const df2 v = j < i ? df_mul(a[q], s_r[j]) : s_r[i];
     F[j * R + i] = v;
+    if (Ff) Ff[j * R + i] = v.h + v.l;
   }
   __syncthreads();
 }
@@ -180,78 +185,188 @@ static __device__ __noinline__ int all_finite(const double* A, int n) {
   return r;
 }
 
-// SPD inverse: double-float factorisation G = L D L^T (the stability-critical
-// step), then L^{-1} and G^{-1} = L^{-T} D^{-1} L^{-1} in FP32 from the
-// rounded factors.  A: R*R doubles (shared, destroyed); F: R*R floats (shared
-// scratch); out: R*R floats (any memory).  Block-wide with 256 threads,
-// R <= 64, R even.
-static __device__ __noinline__ void spd_inverse_f32(double* A, float* F, int R, float* out) {
+// SPD inverse.  The factorisation G = L D L^T always runs in double-float
+// (the stability-critical step).  L^{-1} and G^{-1} = L^{-T} D^{-1} L^{-1}
+// are first formed in FP32 from the rounded factors (relative error about
+// kappa * 2^-24); the 1-norm condition estimate kappa = |G|_1 |G^{-1}|_1 of
+// that inverse (over the leading rn x rn block: the padded rank columns form
+// the decoupled block rho I) then decides: above `df_above` both steps are redone in
+// double-float (relative error about kappa * 2^-44) and the inverse is handed
+// on as the float pair out_hi + out_lo, otherwise out_lo is zero.  (The FP32
+// route is the common, well-conditioned case; the double-float route costs
+// about 8 us more at R = 32.)
+// A: R*R doubles (shared, both triangles, destroyed); F: R*R df2 (shared
+// scratch); out_hi, out_lo: R*R floats each (any memory; out_lo may be NULL,
+// then out_hi gets the rounded sum).  Returns kappa (the same value on every
+// thread).  Block-wide with 256 threads, R <= 64, R even.
+static __device__ __noinline__ double spd_inverse(double* A, df2* F, int R, int rn,
+                                                  float* out_hi, float* out_lo, double df_above) {
   __shared__ df2 s_r[kMaxR];             // 1 / D_k
   __shared__ df2 s_col[2 * kMaxR];       // the current column of the factorisation
+  // partial column sums of |G| and |G^{-1}|: entry p R + c holds rows
+  // p, p + nt/R, ... of column c (no atomics: they serialise on the columns)
+  __shared__ float s_gpart[kCholThreads], s_xpart[kCholThreads];
+  __shared__ double s_kappa;
   const int tid = threadIdx.x, nt = blockDim.x;
   const int lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
-  // F = L^T in FP32 (row p of F is column p of L, so that a warp reads a
-  // column of L with consecutive addresses), 1/D_k on the diagonal
-  if (R <= 16) chol_df_to_f<1>(A, R, F, s_col, s_r);
-  else if (R <= 32) chol_df_to_f<3>(A, R, F, s_col, s_r);
-  else chol_df_to_f<(kMaxR * (kMaxR + 1) / 2 + kCholThreads - 1) / kCholThreads>(A, R, F, s_col,
-                                                                                s_r);
-  float* Li = reinterpret_cast<float*>(A);   // R*R floats fit in the R*R doubles ...
-  float* dinv = Li + R * R;                  // ... and so do R more
-  for (int i = tid; i < R; i += nt) dinv[i] = F[i * R + i];
-  __syncthreads();
-  // L^{-1} (unit lower): one warp per column c (columns dealt in snake order
-  // so that every warp gets the same number of steps), lanes hold rows
-  // (lane, lane + 32)
+  const int col = tid % R, phase = tid / R, nphase = nt / R;
+  // |G|_1 in FP32 (an estimate needs no more)
+  {
+    float cs = 0.f;
+    if (col < rn && phase < nphase)
+      for (int i = phase; i < rn; i += nphase) cs += fabsf((float)A[i * R + col]);
+    s_gpart[tid] = cs;
+  }
+  // F = L^T (row p of F is column p of L, so that a warp reads a column of L
+  // with consecutive addresses), 1/D_k on the diagonal
+  // F32: F rounded to FP32, in the second half of the space of A
+  float* F32 = reinterpret_cast<float*>(A) + R * R;
+  if (R <= 16) chol_df<1>(A, R, F, F32, s_col, s_r);
+  else if (R <= 32) chol_df<3>(A, R, F, F32, s_col, s_r);
+  else
+    chol_df<(kMaxR * (kMaxR + 1) / 2 + kCholThreads - 1) / kCholThreads>(A, R, F, F32, s_col,
+                                                                        s_r);
+  const int nb = R / 2;
+  // ---- FP32 route.  Li: R*R floats in the first half of the space of A.
+  {
+    __shared__ float dinv[kMaxR];
+    float* Li = reinterpret_cast<float*>(A);
+    float* Xa = F32;   // |G^{-1}| once L^{-1} is formed
+    for (int i = tid; i < R; i += nt) dinv[i] = s_r[i].h + s_r[i].l;
+    for (int round = 0; round * nw < R; ++round) {
+      const int c = (round & 1) ? (round + 1) * nw - 1 - warp : round * nw + warp;
+      if (c >= R) continue;
+      float acc0 = 0.f, acc1 = 0.f, y0 = 0.f, y1 = 0.f;
+      for (int i = c; i < R; ++i) {
+        const float acc_i = __shfl_sync(0xffffffffu, i < 32 ? acc0 : acc1, i & 31);
+        const float yi = (i == c ? 1.f : 0.f) - acc_i;
+        if (lane == (i & 31)) { if (i < 32) y0 = yi; else y1 = yi; }
+        const int j0 = lane, j1 = lane + 32;
+        if (j0 > i && j0 < R) acc0 = fmaf(F32[i * R + j0], yi, acc0);
+        if (j1 > i && j1 < R) acc1 = fmaf(F32[i * R + j1], yi, acc1);
+      }
+      __syncwarp();
+      if (lane < R) Li[lane * R + c] = lane >= c ? y0 : 0.f;
+      if (lane + 32 < R) Li[(lane + 32) * R + c] = lane + 32 >= c ? y1 : 0.f;
+    }
+    __syncthreads();
+    for (int b = tid; b < nb * nb; b += nt) {
+      const int bi = b / nb, bj = b % nb;
+      if (bi > bj) continue;
+      const int i = 2 * bi, j = 2 * bj;
+      float s00 = 0.f, s01 = 0.f, s10 = 0.f, s11 = 0.f;
+      for (int k = j; k < R; ++k) {      // j >= i
+        const float d = dinv[k];
+        const float2 li = *reinterpret_cast<const float2*>(Li + k * R + i);
+        float2 lj = *reinterpret_cast<const float2*>(Li + k * R + j);
+        lj.x *= d;
+        lj.y *= d;
+        s00 = fmaf(li.x, lj.x, s00);
+        s01 = fmaf(li.x, lj.y, s01);
+        s10 = fmaf(li.y, lj.x, s10);
+        s11 = fmaf(li.y, lj.y, s11);
+      }
+      const float v[4] = {s00, s01, s10, s11};
+      const int rr[4] = {i, i, i + 1, i + 1}, cc[4] = {j, j + 1, j, j + 1};
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        out_hi[rr[q] * R + cc[q]] = v[q];
+        out_hi[cc[q] * R + rr[q]] = v[q];
+        Xa[rr[q] * R + cc[q]] = fabsf(v[q]);   // F32 is no longer read
+        Xa[cc[q] * R + rr[q]] = fabsf(v[q]);
+        if (out_lo) {
+          out_lo[rr[q] * R + cc[q]] = 0.f;
+          out_lo[cc[q] * R + rr[q]] = 0.f;
+        }
+      }
+    }
+    __syncthreads();
+    {
+      float cs = 0.f;
+      if (col < rn && phase < nphase)
+        for (int i = phase; i < rn; i += nphase) cs += Xa[i * R + col];
+      s_xpart[tid] = cs;
+    }
+    __syncthreads();
+    if (warp == 0) {
+      float mx = 0.f, mg = 0.f;
+      for (int c = lane; c < rn; c += 32) {
+        float sx = 0.f, sg = 0.f;
+        for (int p = 0; p < nphase; ++p) {
+          sx += s_xpart[p * R + c];
+          sg += s_gpart[p * R + c];
+        }
+        mx = fmaxf(mx, sx);
+        mg = fmaxf(mg, sg);
+      }
+      for (int o = 16; o > 0; o >>= 1) {
+        mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+        mg = fmaxf(mg, __shfl_xor_sync(0xffffffffu, mg, o));
+      }
+      if (lane == 0) s_kappa = (double)mg * (double)mx;
+    }
+    __syncthreads();
+  }
+  const double kappa = s_kappa;
+  if (!(kappa > df_above)) return kappa;
+  // ---- double-float route: Li as R*R df2 in the space of A
+  df2* Li = reinterpret_cast<df2*>(A);
   for (int round = 0; round * nw < R; ++round) {
     const int c = (round & 1) ? (round + 1) * nw - 1 - warp : round * nw + warp;
     if (c >= R) continue;
-    float acc0 = 0.f, acc1 = 0.f, y0 = 0.f, y1 = 0.f;
+    df2 acc0 = {0.f, 0.f}, acc1 = {0.f, 0.f}, y0 = {0.f, 0.f}, y1 = {0.f, 0.f};
     for (int i = c; i < R; ++i) {
       // row i finalises y_i = delta_ic - acc_i
-      const float acc_i = __shfl_sync(0xffffffffu, i < 32 ? acc0 : acc1, i & 31);
-      const float yi = (i == c ? 1.f : 0.f) - acc_i;
+      const df2 mine = i < 32 ? acc0 : acc1;
+      const df2 acc_i = {__shfl_sync(0xffffffffu, mine.h, i & 31),
+                         __shfl_sync(0xffffffffu, mine.l, i & 31)};
+      const df2 yi = df_sub({i == c ? 1.f : 0.f, 0.f}, acc_i);
       if (lane == (i & 31)) { if (i < 32) y0 = yi; else y1 = yi; }
       // rows below i: acc_j += L_ji y_i  (L_ji = F[i][j])
       const int j0 = lane, j1 = lane + 32;
-      if (j0 > i && j0 < R) acc0 = fmaf(F[i * R + j0], yi, acc0);
-      if (j1 > i && j1 < R) acc1 = fmaf(F[i * R + j1], yi, acc1);
+      if (j0 > i && j0 < R) acc0 = df_add(acc0, df_mul(F[i * R + j0], yi));
+      if (j1 > i && j1 < R) acc1 = df_add(acc1, df_mul(F[i * R + j1], yi));
     }
-    if (lane < R) Li[lane * R + c] = lane >= c ? y0 : 0.f;
-    if (lane + 32 < R) Li[(lane + 32) * R + c] = lane + 32 >= c ? y1 : 0.f;
+    __syncwarp();
+    if (lane < R) Li[lane * R + c] = lane >= c ? y0 : df2{0.f, 0.f};
+    if (lane + 32 < R) Li[(lane + 32) * R + c] = lane + 32 >= c ? y1 : df2{0.f, 0.f};
   }
   __syncthreads();
   // G^{-1}[i][j] = sum_{k >= max(i,j)} Li[k][i] D_k^{-1} Li[k][j]: 2 x 2 blocks
   // of the upper triangle, mirrored
-  const int nb = R / 2;
   for (int b = tid; b < nb * nb; b += nt) {
     const int bi = b / nb, bj = b % nb;
     if (bi > bj) continue;
     const int i = 2 * bi, j = 2 * bj;
-    float s00 = 0.f, s01 = 0.f, s10 = 0.f, s11 = 0.f;
+    df2 s00 = {0.f, 0.f}, s01 = {0.f, 0.f}, s10 = {0.f, 0.f}, s11 = {0.f, 0.f};
     for (int k = j; k < R; ++k) {      // j >= i
-      const float d = dinv[k];
-      const float2 li = *reinterpret_cast<const float2*>(Li + k * R + i);
-      float2 lj = *reinterpret_cast<const float2*>(Li + k * R + j);
-      lj.x *= d;
-      lj.y *= d;
-      s00 = fmaf(li.x, lj.x, s00);
-      s01 = fmaf(li.x, lj.y, s01);
-      s10 = fmaf(li.y, lj.x, s10);
-      s11 = fmaf(li.y, lj.y, s11);
+      const df2 d = s_r[k];
+      const df2 li0 = Li[k * R + i], li1 = Li[k * R + i + 1];
+      const df2 lj0 = df_mul(Li[k * R + j], d), lj1 = df_mul(Li[k * R + j + 1], d);
+      s00 = df_add(s00, df_mul(li0, lj0));
+      s01 = df_add(s01, df_mul(li0, lj1));
+      s10 = df_add(s10, df_mul(li1, lj0));
+      s11 = df_add(s11, df_mul(li1, lj1));
     }
     // terms with k < max(row, column) vanish (Li is lower triangular), so
     // starting at k = j covers all four entries of the block
-    out[i * R + j] = s00;
-    out[i * R + j + 1] = s01;
-    out[(i + 1) * R + j] = s10;
-    out[(i + 1) * R + j + 1] = s11;
-    out[j * R + i] = s00;
-    out[(j + 1) * R + i] = s01;
-    out[j * R + i + 1] = s10;
-    out[(j + 1) * R + i + 1] = s11;
+    const df2 v[4] = {s00, s01, s10, s11};
+    const int rr[4] = {i, i, i + 1, i + 1}, cc[4] = {j, j + 1, j, j + 1};
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      if (out_lo) {
+        out_hi[rr[q] * R + cc[q]] = v[q].h;
+        out_lo[rr[q] * R + cc[q]] = v[q].l;
+        out_hi[cc[q] * R + rr[q]] = v[q].h;
+        out_lo[cc[q] * R + rr[q]] = v[q].l;
+      } else {
+        out_hi[rr[q] * R + cc[q]] = v[q].h + v[q].l;
+        out_hi[cc[q] * R + rr[q]] = v[q].h + v[q].l;
+      }
+    }
   }
   __syncthreads();
+  return kappa;
 }
 
 // Sum of v over the CTA (FP64, shuffle tree then one value per warp).

@@ -60,9 +60,9 @@ __device__ __forceinline__ void tsum(float& hi, float& lo, float x) {
 // one the previous U-step used.
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(256) k_refactor_ginv(Smalls* sm, DevState* st, int cur, int R,
-                                                       float rho) {
+                                                       int r, float rho) {
   extern __shared__ double dsh[];
-  float* F = reinterpret_cast<float*>(dsh + R * R);
+  df2* F = reinterpret_cast<df2*>(dsh + R * R);
   for (int i = threadIdx.x; i < R * R; i += blockDim.x) {
     int r = i / R, c = i % R;
     dsh[i] = sm->gram[cur][i] + (r == c ? (double)rho : 0.0);
@@ -72,7 +72,8 @@ __global__ void __launch_bounds__(256) k_refactor_ginv(Smalls* sm, DevState* st,
     if (threadIdx.x == 0) st->status = DCF_ENONFINITE;
     return;
   }
-  spd_inverse_f32(dsh, F, R, sm->ginv32);
+  const double kappa = spd_inverse(dsh, F, R, r, sm->ginv32, sm->ginv32_lo, kDfKappa);
+  if (threadIdx.x == 0) st->kappa_g = kappa;
 }
 
 // ---------------------------------------------------------------------------
@@ -108,6 +109,7 @@ enum Scalar { SC_C = 0, SC_ABAR, SC_RBAR, kNumSc };
 struct SmallArgs {
   int mode;
   int R, k;            // padded rank, truth rank
+  int r;               // the solver's rank (leading block of the r x r systems)
   int K, step;
   double lam_k, rho_k, alpha_k, w_k;
   const double* red;   // [kNumRed][kSlot]
@@ -178,7 +180,7 @@ __global__ void __launch_bounds__(256) k_unrolled_small(SmallArgs a) {
     }
     case SM_RECOMP: {
       double* A = dsh;
-      float* F = reinterpret_cast<float*>(dsh + 3 * RR);
+      df2* F = reinterpret_cast<df2*>(dsh + 3 * RR);
       for (int pass = 0; pass < 2; ++pass) {
         const double* g = pass == 0 ? S(RD_G) : S(RD_VV);
         for (int i = tid; i < RR; i += blockDim.x)
@@ -188,7 +190,7 @@ __global__ void __launch_bounds__(256) k_unrolled_small(SmallArgs a) {
           if (tid == 0) a.st->status = DCF_ENONFINITE;
           return;
         }
-        spd_inverse_f32(A, F, R, pass == 0 ? Mt(MT_GINV) : Mt(MT_HINV));
+        spd_inverse(A, F, R, a.r, pass == 0 ? Mt(MT_GINV) : Mt(MT_HINV), nullptr, kDfKappa);
       }
       for (int i = tid; i < RR; i += blockDim.x)
         Mt(MT_AHINV)[i] = (float)(a.alpha_k * (double)Mt(MT_HINV)[i]);
@@ -608,7 +610,7 @@ cudaError_t launch_adjoint_passes(int R, const AdjArgs& a, int grid_cols, int n_
 }
 
 cudaError_t launch_small(const SmallArgs& sa, cudaStream_t s) {
-  const size_t smem = (size_t)sa.R * sa.R * (3 * sizeof(double) + sizeof(float));
+  const size_t smem = (size_t)sa.R * sa.R * (3 * sizeof(double) + sizeof(df2));
   k_unrolled_small<<<1, 256, smem, s>>>(sa);
   return cudaGetLastError();
 }
@@ -755,6 +757,7 @@ SmallArgs small_args(dcf_handle h, int mode, int K, int step) {
   SmallArgs sa{};
   sa.mode = mode;
   sa.R = h->R;
+  sa.r = h->r;
   sa.k = h->k_truth;
   sa.K = K;
   sa.step = step;
@@ -859,12 +862,12 @@ extern "C" dcf_status dcf_unrolled_forward(dcf_handle h, int K, const double* a,
     UCK(launch_small(small_args(h, SM_LOSS_C, K, -1), s), "loss scale");
   }
   const double lam0 = h->lam, rho0 = h->rho;
-  const size_t ginv_smem = (size_t)R * R * 12;
+  const size_t ginv_smem = (size_t)R * R * 16;
   cudaError_t e = cudaSuccess;
   for (int k = 0; k < K && e == cudaSuccess; ++k) {
     e = [&]() -> cudaError_t {
       cudaError_t e2;
-      k_refactor_ginv<<<1, 256, ginv_smem, s>>>(h->sm, h->st, cur, R, (float)rho_k[k]);
+      k_refactor_ginv<<<1, 256, ginv_smem, s>>>(h->sm, h->st, cur, R, h->r, (float)rho_k[k]);
       if ((e2 = cudaGetLastError()) != cudaSuccess) return e2;
       h->lam = lam_k[k];
       h->rho = rho_k[k];
@@ -896,7 +899,7 @@ extern "C" dcf_status dcf_unrolled_forward(dcf_handle h, int K, const double* a,
   h->alpha = 1.0f;
   h->ustar_out = nullptr;
   if (e != cudaSuccess) return cuda_fail(h, e, "unrolled forward");
-  k_refactor_ginv<<<1, 256, ginv_smem, s>>>(h->sm, h->st, cur, R, (float)rho0);
+  k_refactor_ginv<<<1, 256, ginv_smem, s>>>(h->sm, h->st, cur, R, h->r, (float)rho0);
   UCK(cudaGetLastError(), "refactor");
   std::vector<double> lk(K, 0.0);
   if (with_loss)

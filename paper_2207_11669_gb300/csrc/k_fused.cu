@@ -736,36 +736,70 @@ __global__ void __launch_bounds__(kFThreads, 1)
 // the W image staging (2R x 256 fp16), 16 floats of reductions.
 template <int R>
 constexpr int prep_smem() {
-  return R * R * 4 + 2 * R * kFH * 2 + 16 * 4;
+  return 2 * R * R * 4 + 2 * R * kFH * 2 + 16 * 4;
 }
 
-// One 256-row slab (block-wide, 256 threads).
+// Row l of W for the thread's row u: sum_k u_k (gi + gl)[k][l] with
+// compensated products (Dot2; the lo part of G^{-1} into the error term).
+template <int R>
+__device__ __forceinline__ float w_entry_df(const float (&u)[R], const float* gi, const float* gl,
+                                            int l) {
+  float s = 0.f, e = 0.f;
+#pragma unroll
+  for (int k = 0; k < R; ++k) {
+    const float g = gi[k * R + l];
+    const float p = u[k] * g;
+    const float pe = fmaf(u[k], g, -p);
+    const float t = s + p;
+    const float bp = t - s;
+    e += ((s - (t - bp)) + (p - bp)) + pe;
+    e = fmaf(u[k], gl[k * R + l], e);
+    s = t;
+  }
+  return s + e;
+}
+
+// One 256-row slab (block-wide, 256 threads).  df (ill-conditioned U^T U +
+// rho I): W = U G^{-1} with compensated products against the double-float
+// G^{-1}, formed twice (for the scale, then for the image) so that no row of
+// W is held in registers; otherwise FP32 products with the hi part.
 template <int R>
 __device__ __forceinline__ void fused_prep_slab(const float* __restrict__ U, const Smalls* sm,
                                                 int64_t m, int nslabs, float rho,
                                                 const unsigned int* vmax_in,
                                                 unsigned int* vmax_reset, uint8_t* img,
-                                                float* scales, float* zmat, int slab) {
+                                                float* scales, float* zmat, int slab, bool df) {
   extern __shared__ __align__(16) uint8_t psm[];
-  float* gi = reinterpret_cast<float*>(psm);
-  uint8_t* wst = psm + R * R * 4;
+  float* gi = reinterpret_cast<float*>(psm);       // G^{-1} = gi + gl (double-float)
+  float* gl = gi + R * R;
+  uint8_t* wst = psm + 2 * R * R * 4;
   float(*red)[8] = reinterpret_cast<float(*)[8]>(wst + 2 * R * kFH * 2);
   const int tid = threadIdx.x;
-  for (int i = tid; i < R * R; i += 256) gi[i] = sm->ginv32[i];
+  for (int i = tid; i < R * R; i += 256) {
+    gi[i] = sm->ginv32[i];
+    gl[i] = sm->ginv32_lo[i];
+  }
   __syncthreads();
   const int64_t arow = (int64_t)slab * kFH + tid;
   float u[R], w[R];
   float umax = 0.f, wmax = 0.f;
 #pragma unroll
-  for (int k = 0; k < R; ++k) u[k] = arow < m ? U[arow * R + k] : 0.f;
+  for (int k = 0; k < R; ++k) {
+    u[k] = arow < m ? U[arow * R + k] : 0.f;
+    umax = fmaxf(umax, fabsf(u[k]));
+  }
+  if (df) {
+#pragma unroll 1
+    for (int l = 0; l < R; ++l) wmax = fmaxf(wmax, fabsf(w_entry_df<R>(u, gi, gl, l)));
+  } else {
 #pragma unroll
-  for (int l = 0; l < R; ++l) {
-    float s = 0.f;
+    for (int l = 0; l < R; ++l) {
+      float s = 0.f;
 #pragma unroll
-    for (int k = 0; k < R; ++k) s = fmaf(u[k], gi[k * R + l], s);
-    w[l] = s;
-    wmax = fmaxf(wmax, fabsf(s));
-    umax = fmaxf(umax, fabsf(u[l]));
+      for (int k = 0; k < R; ++k) s = fmaf(u[k], gi[k * R + l], s);
+      w[l] = s;
+      wmax = fmaxf(wmax, fabsf(s));
+    }
   }
   for (int o = 16; o > 0; o >>= 1) {
     umax = fmaxf(umax, __shfl_xor_sync(0xffffffffu, umax, o));
@@ -799,13 +833,19 @@ __device__ __forceinline__ void fused_prep_slab(const float* __restrict__ U, con
   }
   // W image: entry (n, a), n < R -> W_hi[a, n], n >= R -> W_lo[a, n-R]:
   //   (n/8)*(256*16) + (a/8)*128 + (n%8)*16 + (a%8)*2
-#pragma unroll
-  for (int k = 0; k < R; ++k) {
+  const int wbase = (tid >> 3) * 128 + (tid & 7) * 2;
+  auto put_w = [&](int k, float v) {
     __half hi, lo;
-    split_h(w[k], s_w, hi, lo);
-    const int base = (tid >> 3) * 128 + (tid & 7) * 2;
-    *reinterpret_cast<__half*>(wst + (k >> 3) * (kFH * 16) + (k & 7) * 16 + base) = hi;
-    *reinterpret_cast<__half*>(wst + ((R + k) >> 3) * (kFH * 16) + (k & 7) * 16 + base) = lo;
+    split_h(v, s_w, hi, lo);
+    *reinterpret_cast<__half*>(wst + (k >> 3) * (kFH * 16) + (k & 7) * 16 + wbase) = hi;
+    *reinterpret_cast<__half*>(wst + ((R + k) >> 3) * (kFH * 16) + (k & 7) * 16 + wbase) = lo;
+  };
+  if (df) {
+#pragma unroll 1
+    for (int k = 0; k < R; ++k) put_w(k, w_entry_df<R>(u, gi, gl, k));
+  } else {
+#pragma unroll
+    for (int k = 0; k < R; ++k) put_w(k, w[k]);
   }
   __syncthreads();
   for (int i = tid; i < (2 * R * kFH * 2) / 16; i += 256)
@@ -816,7 +856,7 @@ __device__ __forceinline__ void fused_prep_slab(const float* __restrict__ U, con
   }
   if (slab == 0) {
     for (int i = tid; i < R * R; i += 256)
-      zmat[i] = fmaf(-rho, gi[i], (i / R) == (i % R) ? 1.f : 0.f);
+      zmat[i] = fmaf(-rho, gl[i], fmaf(-rho, gi[i], (i / R) == (i % R) ? 1.f : 0.f));
     if (tid == 0) {
       const float vm = __uint_as_float(*vmax_in);
       scales[2 * nslabs] = pow2_scale_dev(vm, 1024.f);
@@ -836,7 +876,7 @@ __global__ void __launch_bounds__(256) k_bfused_prep(const BInst* __restrict__ i
     if (I.st->stop) continue;            // uniform over the block
     __syncthreads();                     // the previous item's shared memory is free
     fused_prep_slab<R>(I.U[cur], I.sm, I.m, I.nslabs, I.rho, I.vmax + cur, I.vmax + (cur ^ 1),
-                       I.img, I.scales, I.zmat, w.a);
+                       I.img, I.scales, I.zmat, w.a, df_route(I.st));
   }
 }
 
@@ -844,16 +884,18 @@ __global__ void __launch_bounds__(256) k_bfused_prep(const BInst* __restrict__ i
 // block blk of 256 (row, column group of 8) entries (block-wide).  The row's
 // R inputs are fetched with vector loads before any arithmetic, so that they
 // are in flight together.
-// kFromGinv: zsrc is G^{-1} and Z = I - rho G^{-1} is formed here (as the
-// preparation forms zmat); otherwise zsrc is Z itself.
+// kFromGinv: zsrc, zlo are G^{-1} = zsrc + zlo (double-float) and
+// Z = I - rho G^{-1} is formed here (as the preparation forms zmat);
+// otherwise zsrc is Z itself.
 template <int R, bool kFromGinv = false>
 __device__ __forceinline__ void rowmat_block(const float* __restrict__ in,
-                                             const float* __restrict__ zsrc, float rho, int64_t n,
+                                             const float* __restrict__ zsrc,
+                                             const float* __restrict__ zlo, float rho, int64_t n,
                                              float* __restrict__ out, int64_t blk) {
   __shared__ __align__(16) float Z[R * R];
   if constexpr (kFromGinv) {
     for (int i = threadIdx.x; i < R * R; i += 256)
-      Z[i] = fmaf(-rho, zsrc[i], (i / R) == (i % R) ? 1.f : 0.f);
+      Z[i] = fmaf(-rho, zlo[i], fmaf(-rho, zsrc[i], (i / R) == (i % R) ? 1.f : 0.f));
   } else {
     for (int i = threadIdx.x; i < R * R / 4; i += 256)
       reinterpret_cast<float4*>(Z)[i] = reinterpret_cast<const float4*>(zsrc)[i];
@@ -906,9 +948,10 @@ __global__ void __launch_bounds__(256) k_fused_prep(const float* __restrict__ U,
   if (st->stop) return;
   if ((int)blockIdx.x < nslabs)
     fused_prep_slab<R>(U, sm, m, nslabs, rho, vmax_in, vmax_reset, img, scales, zmat,
-                       (int)blockIdx.x);
+                       (int)blockIdx.x, df_route(st));
   else
-    rowmat_block<R, true>(Vold, sm->ginv32, rho, n, VZ, (int64_t)blockIdx.x - nslabs);
+    rowmat_block<R, true>(Vold, sm->ginv32, sm->ginv32_lo, rho, n, VZ,
+                          (int64_t)blockIdx.x - nslabs);
 }
 
 // Batches: item (instance, block of 256 entries of V_old Z).
@@ -921,7 +964,7 @@ __global__ void __launch_bounds__(256) k_browmat(const BInst* __restrict__ insts
     const BInst& I = insts[w.inst];
     if (I.st->stop) continue;            // uniform over the block
     __syncthreads();                     // the previous item's shared Z is free
-    rowmat_block<R>(I.V[cur], I.zmat, 0.f, I.n, I.VZ, w.a);
+    rowmat_block<R>(I.V[cur], I.zmat, nullptr, 0.f, I.n, I.VZ, w.a);
   }
 }
 

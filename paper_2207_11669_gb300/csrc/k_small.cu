@@ -109,6 +109,11 @@ k_gram_part(const float* __restrict__ X, int ldx, int cx,
 // D = dV^T dV with dV = V' - V_old.  (The change metric of the stop test is
 // formed from Y and D, which are of the size of the change itself, so that it
 // does not cancel against |L|^2; V_old^T V' = Q_old + Y for the fused path.)
+// df (ill-conditioned systems): Q and Y are sums of compensated products
+// (Dot2), and dV enters Y exactly (TwoSum pair): Q + rho I is inverted for the
+// U-step and Q_old + Y is applied to U_{t-1}, where nearly collinear columns
+// cancel and FP32 sums of the products would be amplified by the condition
+// number.  Otherwise, and always for D (metric only), FP32 sums per chunk.
 // Thread tile TB x TB of each output (R >= 32: 4 x 4, R <= 16: 1 x 1) with
 // 256 / (R/TB)^2 row groups; 64-row chunks staged in shared memory, the next
 // chunk's loads in flight (registers) while the current one is used.  With
@@ -135,7 +140,7 @@ __device__ __forceinline__ void gram_vv_block(const float* __restrict__ Vo,
                                               const float* __restrict__ Vn, int64_t a0,
                                               int64_t a1, float2* __restrict__ out_q,
                                               float2* __restrict__ out_y,
-                                              float2* __restrict__ out_d, float* gsh) {
+                                              float2* __restrict__ out_d, float* gsh, bool df) {
   using C = GvvCfg<R>;
   constexpr int TB = C::TB, NT = C::NT, G = C::GROUPS, CH = C::CH, NV = C::NV;
   float* So = gsh;              // [CH][R]  V_old rows
@@ -176,13 +181,12 @@ __device__ __forceinline__ void gram_vv_block(const float* __restrict__ Vo,
     }
     __syncthreads();
     if (c + CH < a1) fetch(c + CH);
-    float qa[TB][TB], ya[TB][TB], da[TB][TB];
+    float da[TB][TB];
 #pragma unroll
     for (int i = 0; i < TB; ++i)
 #pragma unroll
-      for (int j = 0; j < TB; ++j) { qa[i][j] = 0.f; ya[i][j] = 0.f; da[i][j] = 0.f; }
-    for (int rr = grp; rr < CH; rr += G) {
-      float nk[TB], nl[TB], ok[TB], ol[TB];
+      for (int j = 0; j < TB; ++j) da[i][j] = 0.f;
+    auto load_row = [&](int rr, float* nk, float* nl, float* ok, float* ol) {
       if constexpr (TB == 4) {
         const float4 a = *reinterpret_cast<const float4*>(Sn + rr * R + k0);
         const float4 d = *reinterpret_cast<const float4*>(Sn + rr * R + l0);
@@ -205,28 +209,69 @@ __device__ __forceinline__ void gram_vv_block(const float* __restrict__ Vo,
           }
         }
       }
+    };
+    if (df) {
+      for (int rr = grp; rr < CH; rr += G) {
+        float nk[TB], nl[TB], ok[TB], ol[TB];
+        load_row(rr, nk, nl, ok, ol);
+        // dV = V' - V_old exactly, as the pair dvh + dvl (TwoSum)
+        float dvh[TB], dvl[TB];
+        if (kDelta) {
+#pragma unroll
+          for (int j = 0; j < TB; ++j) {
+            dvh[j] = nl[j] - ol[j];
+            const float bp = dvh[j] - nl[j];
+            dvl[j] = (nl[j] - (dvh[j] - bp)) + (-ol[j] - bp);
+          }
+        }
+#pragma unroll
+        for (int i = 0; i < TB; ++i)
+#pragma unroll
+          for (int j = 0; j < TB; ++j) {
+            dot2_add(qh[i][j], ql[i][j], nk[i], nl[j]);
+            if (kDelta) {
+              dot2_add(yh[i][j], yl[i][j], ok[i], dvh[j]);
+              yl[i][j] = fmaf(ok[i], dvl[j], yl[i][j]);
+              da[i][j] = fmaf(nk[i] - ok[i], dvh[j], da[i][j]);
+            }
+          }
+      }
+    } else {
+      // FP32 sums per chunk, compensated across chunks
+      float qa[TB][TB], ya[TB][TB];
+#pragma unroll
+      for (int i = 0; i < TB; ++i)
+#pragma unroll
+        for (int j = 0; j < TB; ++j) qa[i][j] = ya[i][j] = 0.f;
+      for (int rr = grp; rr < CH; rr += G) {
+        float nk[TB], nl[TB], ok[TB], ol[TB];
+        load_row(rr, nk, nl, ok, ol);
+#pragma unroll
+        for (int i = 0; i < TB; ++i)
+#pragma unroll
+          for (int j = 0; j < TB; ++j) {
+            qa[i][j] = fmaf(nk[i], nl[j], qa[i][j]);
+            if (kDelta) {
+              const float dlj = nl[j] - ol[j];
+              ya[i][j] = fmaf(ok[i], dlj, ya[i][j]);
+              da[i][j] = fmaf(nk[i] - ok[i], dlj, da[i][j]);
+            }
+          }
+      }
 #pragma unroll
       for (int i = 0; i < TB; ++i)
 #pragma unroll
         for (int j = 0; j < TB; ++j) {
-          qa[i][j] = fmaf(nk[i], nl[j], qa[i][j]);
-          if (kDelta) {
-            const float dlj = nl[j] - ol[j];
-            ya[i][j] = fmaf(ok[i], dlj, ya[i][j]);
-            da[i][j] = fmaf(nk[i] - ok[i], dlj, da[i][j]);
-          }
+          two_sum_add(qh[i][j], ql[i][j], qa[i][j]);
+          if (kDelta) two_sum_add(yh[i][j], yl[i][j], ya[i][j]);
         }
     }
+    if (kDelta) {
 #pragma unroll
-    for (int i = 0; i < TB; ++i)
+      for (int i = 0; i < TB; ++i)
 #pragma unroll
-      for (int j = 0; j < TB; ++j) {
-        two_sum_add(qh[i][j], ql[i][j], qa[i][j]);
-        if (kDelta) {
-          two_sum_add(yh[i][j], yl[i][j], ya[i][j]);
-          two_sum_add(dh[i][j], dl[i][j], da[i][j]);
-        }
-      }
+        for (int j = 0; j < TB; ++j) two_sum_add(dh[i][j], dl[i][j], da[i][j]);
+    }
   }
   // combine the row groups through shared memory, one tile row at a time:
   // cmb[g][tile][j][6] = (hi, lo of Q, Y, D)
@@ -285,7 +330,8 @@ k_gram_vv(const float* __restrict__ Vo, const float* __restrict__ Vn, int64_t N,
   const int64_t a0 = (int64_t)blockIdx.x * rows_per_cta;
   const int64_t a1 = min(N, a0 + rows_per_cta);
   const int64_t base = (int64_t)blockIdx.x * R * R;
-  gram_vv_block<R, true>(Vo, Vn, a0, a1, part_q + base, part_xv + base, part_dv + base, gsh);
+  gram_vv_block<R, true>(Vo, Vn, a0, a1, part_q + base, part_xv + base, part_dv + base, gsh,
+                         df_route(st));
 }
 
 // ---------------------------------------------------------------------------
@@ -302,6 +348,8 @@ struct ReduceArgs {
   int total;               // count[0] + ... + count[3]
   int tail;
   int R;
+  int r;                   // rank: the leading r x r block of the r x r systems (the
+                           // rest is the padding's decoupled rho I); 0: R
   float rho;
   float rho_q;             // rho of Q + rho I in the Q tail when > 0, else rho
   int u_mode;
@@ -313,8 +361,8 @@ struct ReduceArgs {
 
 constexpr int kRedEntriesPerCta = 16;
 
-__device__ void tail_q(const ReduceArgs& a, double* A, float* F);
-__device__ void tail_g(const ReduceArgs& a, double* A, float* F);
+__device__ void tail_q(const ReduceArgs& a, double* A, df2* F);
+__device__ void tail_g(const ReduceArgs& a, double* A, df2* F);
 
 __global__ void __launch_bounds__(256) k_reduce_parts(ReduceArgs a) {
   if ((a.tail == TAIL_Q || a.tail == TAIL_G) && a.st->stop) return;
@@ -384,8 +432,8 @@ __global__ void __launch_bounds__(256) k_reduce_parts(ReduceArgs a) {
   __syncthreads();
   if (!is_last) return;
   __threadfence();
-  extern __shared__ double dsh[];   // R*R doubles, then R*R floats
-  float* F = reinterpret_cast<float*>(dsh + a.R * a.R);
+  extern __shared__ double dsh[];   // R*R doubles, then R*R double-floats
+  df2* F = reinterpret_cast<df2*>(dsh + a.R * a.R);
   if (tid == 0) *a.counter = 0u;
   if (a.tail == TAIL_Q || a.tail == TAIL_INIT_Q) tail_q(a, dsh, F);
   else tail_g(a, dsh, F);
@@ -393,7 +441,7 @@ __global__ void __launch_bounds__(256) k_reduce_parts(ReduceArgs a) {
 
 // Q_t is in out[0] (R*R), Y = V_{t-1}^T (V_t - V_{t-1}) in out[1], the Gram of
 // V_t - V_{t-1} in out[2], Huber in out[3].  V_{t-1}^T V_t = Q_{t-1} + Y.
-__device__ void tail_q(const ReduceArgs& a, double* A, float* F) {
+__device__ void tail_q(const ReduceArgs& a, double* A, df2* F) {
   const int R = a.R;
   Smalls* sm = a.sm;
   DevState* st = a.st;
@@ -422,7 +470,11 @@ __device__ void tail_q(const ReduceArgs& a, double* A, float* F) {
       sm->q[nxt][i] = qv[u];
       sm->dvy[i] = yv[u];
       sm->dvv[i] = dv[u];
-      sm->xv[i] = qo[u] + yv[u];
+      const double xv = qo[u] + yv[u];
+      sm->xv[i] = xv;
+      const float xh = (float)xv;
+      sm->xv32[0][i] = xh;
+      sm->xv32[1][i] = (float)(xv - (double)xh);
       const int r = i / R, c = i % R;
       const double h = qv[u] + (r == c ? (double)(a.rho_q > 0.f ? a.rho_q : a.rho) : 0.0);
       A[i] = h;
@@ -435,12 +487,15 @@ __device__ void tail_q(const ReduceArgs& a, double* A, float* F) {
     if (threadIdx.x == 0) st->status = 4;  // DCF_ENONFINITE
     return;
   }
-  if (a.u_mode == 0) spd_inverse_f32(A, F, R, sm->hinv32);
+  if (a.u_mode == 0) {
+    const double kappa = spd_inverse(A, F, R, a.r > 0 ? a.r : R, sm->hinv32, nullptr, kDfKappa);
+    if (threadIdx.x == 0) st->kappa_h = kappa;
+  }
 }
 
 // Gram of U_t in out[0], U_{t-1}^T (U_t - U_{t-1}) in out[1], the Gram of
 // U_t - U_{t-1} in out[2].
-__device__ void tail_g(const ReduceArgs& a, double* A, float* F) {
+__device__ void tail_g(const ReduceArgs& a, double* A, df2* F) {
   const int R = a.R;
   Smalls* sm = a.sm;
   DevState* st = a.st;
@@ -538,7 +593,9 @@ __device__ void tail_g(const ReduceArgs& a, double* A, float* F) {
     if (threadIdx.x == 0) st->status = 4;
     return;
   }
-  spd_inverse_f32(A, F, R, sm->ginv32);
+  const double kappa =
+      spd_inverse(A, F, R, a.r > 0 ? a.r : R, sm->ginv32, sm->ginv32_lo, kDfKappa);
+  if (threadIdx.x == 0) st->kappa_g = kappa;
 }
 
 // ---------------------------------------------------------------------------
@@ -548,16 +605,24 @@ __device__ void tail_g(const ReduceArgs& a, double* A, float* F) {
 constexpr int kRowsPerCta = 32;
 
 // W = U (U^T U + rho I)^{-1}
-// Rows [32 rb, 32 rb + 32) of W = U G^{-1}; block-wide (256 threads).
+// Rows [32 rb, 32 rb + 32) of W = U G^{-1}; block-wide (256 threads).  df: G
+// is ill-conditioned, G^{-1} is the double-float pair hi + lo and the products
+// with hi are compensated (Dot2), so that W carries the inverse's ~44 bits up
+// to its own FP32 rounding (the rows of U G^{-1} cancel then).
 template <int R>
 __device__ __forceinline__ void make_w_block(const float* __restrict__ U, const Smalls* sm,
-                                             float* __restrict__ W, int64_t m, int64_t rb) {
+                                             float* __restrict__ W, int64_t m, int64_t rb,
+                                             bool df) {
   constexpr int CG = R / 8;
   __shared__ __align__(16) float Gi[R * R];
+  __shared__ __align__(16) float Gl[R * R];
   __shared__ __align__(16) float Us[kRowsPerCta * R];
   const int tid = threadIdx.x;
   const int64_t row0 = rb * kRowsPerCta;
-  for (int i = tid; i < R * R; i += 256) Gi[i] = sm->ginv32[i];
+  for (int i = tid; i < R * R; i += 256) {
+    Gi[i] = sm->ginv32[i];
+    Gl[i] = sm->ginv32_lo[i];
+  }
   for (int i = tid; i < kRowsPerCta * R; i += 256) {
     int64_t a = row0 + i / R;
     Us[i] = a < m ? U[row0 * R + i] : 0.f;
@@ -566,16 +631,27 @@ __device__ __forceinline__ void make_w_block(const float* __restrict__ U, const 
   const int ar = tid >> 3, g = tid & 7;
   const int64_t a = row0 + ar;
   if (a >= m) return;
-  float acc[CG];
+  float acc[CG], lo[CG];
 #pragma unroll
-  for (int l = 0; l < CG; ++l) acc[l] = 0.f;
-  for (int k = 0; k < R; ++k) {
-    float u = Us[ar * R + k];
+  for (int l = 0; l < CG; ++l) acc[l] = lo[l] = 0.f;
+  if (df) {
+    for (int k = 0; k < R; ++k) {
+      const float u = Us[ar * R + k];
 #pragma unroll
-    for (int l = 0; l < CG; ++l) acc[l] = fmaf(u, Gi[k * R + g * CG + l], acc[l]);
+      for (int l = 0; l < CG; ++l) {
+        dot2_add(acc[l], lo[l], u, Gi[k * R + g * CG + l]);
+        lo[l] = fmaf(u, Gl[k * R + g * CG + l], lo[l]);
+      }
+    }
+  } else {
+    for (int k = 0; k < R; ++k) {
+      const float u = Us[ar * R + k];
+#pragma unroll
+      for (int l = 0; l < CG; ++l) acc[l] = fmaf(u, Gi[k * R + g * CG + l], acc[l]);
+    }
   }
 #pragma unroll
-  for (int l = 0; l < CG; ++l) W[a * R + g * CG + l] = acc[l];
+  for (int l = 0; l < CG; ++l) W[a * R + g * CG + l] = acc[l] + lo[l];
 }
 
 template <int R>
@@ -584,7 +660,7 @@ __global__ void __launch_bounds__(256) k_make_w(const float* __restrict__ U,
                                                 float* __restrict__ W, int64_t m,
                                                 int respect_stop) {
   if (respect_stop && st->stop) return;
-  make_w_block<R>(U, sm, W, m, blockIdx.x);
+  make_w_block<R>(U, sm, W, m, blockIdx.x, df_route(st));
 }
 
 // Gram partials over a CTA's rows of U: G = Un^T Un (compensated products:
@@ -629,7 +705,7 @@ __device__ __forceinline__ void rows_block(const IterArgs& a, int64_t rb) {
   const int64_t row0 = rb * kRowsPerCta;
   const int rows = (int)dmin64((int64_t)kRowsPerCta, a.m - row0);
   if (a.add_uxv)
-    for (int i = tid; i < R * R; i += 256) Mat[i] = (float)a.sm->xv[i];
+    for (int i = tid; i < R * R; i += 256) Mat[i] = a.sm->xv32[0][i];
   for (int i = tid; i < kRowsPerCta * R; i += 256) {
     const int rr = i / R;
     float hi = 0.f, lo = 0.f, uo = 0.f;
@@ -654,18 +730,37 @@ __device__ __forceinline__ void rows_block(const IterArgs& a, int64_t rb) {
   __syncthreads();
   const int ar = tid >> 3, g = tid & 7;
   if (a.add_uxv) {
-    // P = U_{t-1} (V_{t-1}^T V_t) + C V'   (the fused pass returns only C V')
-    float add[CG];
+    // P = U_{t-1} (V_{t-1}^T V_t) + C V'   (the fused pass returns only C V').
+    // V_{t-1}^T V_t = hi + lo, compensated products: with nearly collinear
+    // columns the terms of U_{t-1} (V_{t-1}^T V_t) cancel.
+    // (Ill-conditioned systems only; otherwise FP32 products with hi.)
+    const float* __restrict__ Xl = a.sm->xv32[1];
+    float add[CG], addl[CG];
 #pragma unroll
-    for (int l = 0; l < CG; ++l) add[l] = 0.f;
-    for (int k = 0; k < R; ++k) {
-      const float u = Uo[ar * R + k];
+    for (int l = 0; l < CG; ++l) add[l] = addl[l] = 0.f;
+    if (df_route(st)) {
+      for (int k = 0; k < R; ++k) {
+        const float u = Uo[ar * R + k];
 #pragma unroll
-      for (int l = 0; l < CG; ++l) add[l] = fmaf(u, Mat[k * R + g * CG + l], add[l]);
+        for (int l = 0; l < CG; ++l) {
+          dot2_add(add[l], addl[l], u, Mat[k * R + g * CG + l]);
+          addl[l] = fmaf(u, __ldg(Xl + k * R + g * CG + l), addl[l]);
+        }
+      }
+    } else {
+      for (int k = 0; k < R; ++k) {
+        const float u = Uo[ar * R + k];
+#pragma unroll
+        for (int l = 0; l < CG; ++l) add[l] = fmaf(u, Mat[k * R + g * CG + l], add[l]);
+      }
     }
     __syncthreads();
 #pragma unroll
-    for (int l = 0; l < CG; ++l) Ps[ar * R + g * CG + l] += add[l];
+    for (int l = 0; l < CG; ++l) {
+      float h = add[l], lo = addl[l];
+      two_sum_add(h, lo, Ps[ar * R + g * CG + l]);
+      Ps[ar * R + g * CG + l] = h + lo;
+    }
   }
   for (int i = tid; i < R * R; i += 256) Mat[i] = a.u_mode == 0 ? a.sm->hinv32[i] : a.sm->qrho32[i];
   __syncthreads();
@@ -674,7 +769,7 @@ __device__ __forceinline__ void rows_block(const IterArgs& a, int64_t rb) {
   for (int l = 0; l < CG; ++l) acc[l] = 0.f;
   const float* src = a.u_mode == 0 ? Ps : Uo;
   for (int k = 0; k < R; ++k) {
-    float v = src[ar * R + k];
+    const float v = src[ar * R + k];
 #pragma unroll
     for (int l = 0; l < CG; ++l) acc[l] = fmaf(v, Mat[k * R + g * CG + l], acc[l]);
   }
@@ -775,7 +870,7 @@ __global__ void __launch_bounds__(256) k_bmake_w(const BInst* __restrict__ insts
     const BInst& I = insts[w.inst];
     if (respect_stop && I.st->stop) continue;
     __syncthreads();
-    make_w_block<R>(I.U[cur], I.sm, I.W, I.m, w.a);
+    make_w_block<R>(I.U[cur], I.sm, I.W, I.m, w.a, df_route(I.st));
   }
 }
 
@@ -814,9 +909,9 @@ __global__ void __launch_bounds__(256) k_bgram(const BInst* __restrict__ insts,
     const int64_t base = (int64_t)w.a * R * R;
     if (mode == BG_ITER)
       gram_vv_block<R, true>(X, Y, a0, a1, I.part_q + base, I.part_xv + base, I.part_dv + base,
-                             gsh);
-    else
-      gram_vv_block<R, false>(X, Y, a0, a1, I.part_q + base, nullptr, nullptr, gsh);
+                             gsh, df_route(I.st));
+    else   // start point (once): compensated
+      gram_vv_block<R, false>(X, Y, a0, a1, I.part_q + base, nullptr, nullptr, gsh, true);
   }
 }
 
@@ -879,13 +974,14 @@ __global__ void __launch_bounds__(256) k_breduce(const BInst* __restrict__ insts
   ra.out[3] = red + 3 * RR;
   ra.tail = tail;
   ra.R = R;
+  ra.r = I.r;
   ra.rho = I.rho;
   ra.u_mode = I.u_mode;
   ra.copy = (tail == TAIL_INIT_G || tail == TAIL_INIT_Q) ? 0 : cur;
   ra.sm = I.sm;
   ra.st = I.st;
-  extern __shared__ double dsh[];   // R*R doubles, then R*R floats
-  float* F = reinterpret_cast<float*>(dsh + RR);
+  extern __shared__ double dsh[];   // R*R doubles, then R*R double-floats
+  df2* F = reinterpret_cast<df2*>(dsh + RR);
   if (tail == TAIL_Q || tail == TAIL_INIT_Q) tail_q(ra, dsh, F);
   else tail_g(ra, dsh, F);
 }
@@ -991,7 +1087,7 @@ static cudaError_t bsmall_T(int kind, const BInst* insts, const BItem* items, in
     case 1: k_brows<R><<<grid, 256, 0, s>>>(insts, items, nitems, cur); break;
     case 2: k_bgram<R><<<grid, 256, GvvCfg<R>::smem_bytes, s>>>(insts, items, nitems, cur, arg); break;
     default:
-      k_breduce<R><<<nitems, 256, (size_t)R * R * 12, s>>>(insts, which, cur, arg);
+      k_breduce<R><<<nitems, 256, (size_t)R * R * 16, s>>>(insts, which, cur, arg);
       break;
   }
   return cudaGetLastError();
@@ -1008,7 +1104,7 @@ cudaError_t launch_bsmall(int R, int kind, const BInst* insts, const BItem* item
 
 static cudaError_t launch_reduce(const ReduceArgs& ra, cudaStream_t s) {
   int grid = (ra.total + kRedEntriesPerCta - 1) / kRedEntriesPerCta;
-  size_t smem = (size_t)ra.R * ra.R * (sizeof(double) + sizeof(float));
+  size_t smem = (size_t)ra.R * ra.R * (sizeof(double) + sizeof(df2));
   k_reduce_parts<<<grid, 256, smem, s>>>(ra);
   return cudaGetLastError();
 }
@@ -1029,10 +1125,10 @@ cudaError_t launch_make_w(const IterArgs& a, int copy, int respect_stop, cudaStr
   }
 }
 
-// The reduction tail needs R*R*12 bytes of dynamic shared memory (48 KB at R = 64).
+// The reduction tail needs R*R*16 bytes of dynamic shared memory (64 KB at R = 64).
 cudaError_t prepare_small_kernels() {
   return cudaFuncSetAttribute(k_reduce_parts, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              kMaxR * kMaxR * 12);
+                              kMaxR * kMaxR * 16);
 }
 
 template <int R>
@@ -1075,7 +1171,7 @@ cudaError_t launch_reduce_q(const IterArgs& a, double* out_q, double* out_xv, do
   ra.total = 3 * RR + 1;
   ra.tail = TAIL_Q;
   ra.copy = a.cur;
-  ra.R = a.R; ra.rho = a.rho; ra.rho_q = a.rho_q; ra.u_mode = a.u_mode;
+  ra.R = a.R; ra.r = a.r; ra.rho = a.rho; ra.rho_q = a.rho_q; ra.u_mode = a.u_mode;
   ra.counter = counter; ra.sm = a.sm; ra.st = a.st;
   return launch_reduce(ra, s);
 }
@@ -1090,7 +1186,7 @@ cudaError_t launch_reduce_g(const IterArgs& a, double* out_g, double* out_xu, do
   ra.total = 3 * RR;
   ra.tail = TAIL_G;
   ra.copy = a.cur;
-  ra.R = a.R; ra.rho = a.rho; ra.u_mode = a.u_mode;
+  ra.R = a.R; ra.r = a.r; ra.rho = a.rho; ra.u_mode = a.u_mode;
   ra.counter = counter; ra.sm = a.sm; ra.st = a.st;
   return launch_reduce(ra, s);
 }
@@ -1103,7 +1199,7 @@ cudaError_t launch_reduce_init(const IterArgs& a, int which /*0: G, 1: Q*/, int 
   ra.part[0] = part; ra.count[0] = RR; ra.out[0] = out; ra.nparts[0] = nparts;
   ra.total = RR;
   ra.tail = which == 0 ? TAIL_INIT_G : TAIL_INIT_Q;
-  ra.R = a.R; ra.rho = a.rho; ra.u_mode = a.u_mode; ra.copy = copy;
+  ra.R = a.R; ra.r = a.r; ra.rho = a.rho; ra.u_mode = a.u_mode; ra.copy = copy;
   ra.counter = counter; ra.sm = a.sm; ra.st = a.st;
   return launch_reduce(ra, s);
 }

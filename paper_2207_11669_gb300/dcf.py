@@ -66,6 +66,8 @@ _SIGS = {
     "dcf_set_private": (C.c_int, [C.c_void_p, C.c_int, C.c_int]),
     "dcf_get_stats": (C.c_int, [C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_double),
                                 C.POINTER(C.c_int)]),
+    "dcf_get_conditioning": (C.c_int, [C.c_void_p, C.POINTER(C.c_double),
+                                       C.POINTER(C.c_double)]),
     "dcf_set_truth": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_int]),
     "dcf_rel_err": (C.c_int, [C.c_void_p, C.POINTER(C.c_double)]),
     "dcf_singular_values": (C.c_int, [C.c_void_p, C.POINTER(C.c_double),
@@ -282,6 +284,12 @@ def dcf_get_stats(h):
     return o.value, d.value, it.value
 
 
+def dcf_get_conditioning(h):
+    g, q = C.c_double(), C.c_double()
+    _check(h, lib().dcf_get_conditioning(h, C.byref(g), C.byref(q)))
+    return g.value, q.value
+
+
 def dcf_set_truth(h, A, B):
     pa, where = _ptr_where(A)
     pb, _ = _ptr_where(B)
@@ -494,6 +502,10 @@ class Solver:
 
     def stats(self):
         return dcf_get_stats(self.h)
+
+    def conditioning(self):
+        """(kappa of U^T U + rho I, kappa of V^T V + rho I) of the last iteration."""
+        return dcf_get_conditioning(self.h)
 
     def set_truth(self, A, B):
         self._truth = (np.ascontiguousarray(A, np.float32), np.ascontiguousarray(B, np.float32))
