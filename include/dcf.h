@@ -222,12 +222,14 @@ dcf_status dcf_get_stats(dcf_handle h, double* objective, double* dL_rel, int* i
  * V^T V + rho I of the exact U-step.)
  * 1-norm condition estimates |A|_1 |A^{-1}|_1 of the two r x r systems as the
  * last iteration formed them (0 before the first; kappa_h stays 0 in FedAvg
- * mode, which inverts no V-side system).  Above 100 the inverses are formed in
- * double-float and applied with compensated products, and the Grams that feed
- * them are summed with compensated products (about 1e-5 relative accuracy of
- * the factors up to kappa ~ 1e8 instead of FP32 rounding times kappa).  Either
- * pointer may be NULL. */
-dcf_status dcf_get_conditioning(dcf_handle h, double* kappa_g, double* kappa_h);
+ * mode, which inverts no V-side system).  Above 100 the inverses are applied
+ * in double-float with compensated products, and the Grams that feed them are
+ * summed with compensated products (about 1e-5 relative accuracy of the
+ * factors up to kappa ~ 1e8 instead of FP32 rounding times kappa).
+ * route_g, route_h: how the last inverses were formed: 0 FP32 from the
+ * double-float L D L^T factors, 1 double-float.  Any pointer may be NULL. */
+dcf_status dcf_get_conditioning(dcf_handle h, double* kappa_g, double* kappa_h, int* route_g,
+                                int* route_h);
 
 /* The ground truth of the synthetic experiments of §4.1 (L0 = A B^T) and
  * the relative error of L against it (§4.1 "Evaluation Metric", here the

@@ -1280,7 +1280,8 @@ extern "C" dcf_status dcf_get_stats(dcf_handle h, double* objective, double* dL_
   return end_work(h);
 }
 
-extern "C" dcf_status dcf_get_conditioning(dcf_handle h, double* kappa_g, double* kappa_h) {
+extern "C" dcf_status dcf_get_conditioning(dcf_handle h, double* kappa_g, double* kappa_h,
+                                           int* route_g, int* route_h) {
   if (!h) return DCF_EINVAL;
   dcf_status st = begin_work(h);
   if (st != DCF_OK) return st;
@@ -1288,6 +1289,8 @@ extern "C" dcf_status dcf_get_conditioning(dcf_handle h, double* kappa_g, double
   if ((st = read_state(h, &ds)) != DCF_OK) return st;
   if (kappa_g) *kappa_g = ds.kappa_g;
   if (kappa_h) *kappa_h = ds.kappa_h;
+  if (route_g) *route_g = ds.route_g;
+  if (route_h) *route_h = ds.route_h;
   return end_work(h);
 }
 

@@ -34,6 +34,8 @@ struct DevState {
                      // step size of their communication round); 0: eta0 / sqrt(t + 1)
   double kappa_g;    // 1-norm condition estimate of the latest U^T U + rho I
   double kappa_h;    //   and of the latest V^T V + rho I (exact U-step)
+  int route_g;       // how their inverses were formed: 0 FP32 from the double-float
+  int route_h;       //   factors, 1 double-float
 };
 
 // Condition estimate above which the r x r inverses are formed in double-float

@@ -185,28 +185,67 @@ static __device__ __noinline__ int all_finite(const double* A, int n) {
   return r;
 }
 
-// SPD inverse.  The factorisation G = L D L^T always runs in double-float
-// (the stability-critical step).  L^{-1} and G^{-1} = L^{-T} D^{-1} L^{-1}
-// are first formed in FP32 from the rounded factors (relative error about
-// kappa * 2^-24); the 1-norm condition estimate kappa = |G|_1 |G^{-1}|_1 of
-// that inverse (over the leading rn x rn block: the padded rank columns form
-// the decoupled block rho I) then decides: above `df_above` both steps are redone in
-// double-float (relative error about kappa * 2^-44) and the inverse is handed
-// on as the float pair out_hi + out_lo, otherwise out_lo is zero.  (The FP32
-// route is the common, well-conditioned case; the double-float route costs
-// about 8 us more at R = 32.)
+// Column sums for a 1-norm: thread (column c, row phase p) sums rows
+// p, p + nt/R, ... of column c of X (R x R floats, shared) into part[tid].
+static __device__ __forceinline__ void colsum_part(const float* X, int R, int rn, float* part) {
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const int col = tid % R, phase = tid / R, nphase = nt / R;
+  float cs = 0.f;
+  if (col < rn && phase < nphase)
+    for (int i = phase; i < rn; i += nphase) cs += fabsf(X[i * R + col]);
+  part[tid] = cs;
+}
+
+// max over columns c < rn of the phase sums in part (filled by colsum_part
+// or the same layout).  Block-wide; the same value on every thread.
+static __device__ float part_colmax(const float* part, int R, int rn) {
+  __shared__ float s_max;
+  const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, nphase = nt / R;
+  __syncthreads();
+  if (tid < 32) {
+    float mx = 0.f;
+    for (int c = lane; c < rn; c += 32) {
+      float sc = 0.f;
+      for (int p = 0; p < nphase; ++p) sc += part[p * R + c];
+      mx = fmaxf(mx, sc);
+    }
+    for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    if (lane == 0) s_max = mx;
+  }
+  __syncthreads();
+  const float r = s_max;
+  __syncthreads();
+  return r;
+}
+
+// |X|_1 restricted to the leading rn x rn block.  Block-wide.
+static __device__ float colsum_max(const float* X, int R, int rn, float* part) {
+  colsum_part(X, R, rn, part);
+  return part_colmax(part, R, rn);
+}
+
+// SPD inverse G^{-1} of G = A (R x R, FP64 input):
+//  - the factorisation G = L D L^T in double-float (the stability-critical
+//    step), then L^{-1} and G^{-1} = L^{-T} D^{-1} L^{-1} in FP32 from the
+//    rounded factors (relative error about kappa 2^-24);
+//  - when the 1-norm condition estimate kappa = |G|_1 |G^{-1}|_1 (over the
+//    leading rn x rn block: the padded rank columns form the decoupled block
+//    rho I) exceeds `df_above`, L^{-1} and the product again in double-float
+//    (relative error about kappa 2^-44), handed on as the float pair
+//    out_hi + out_lo (out_lo is zero after the FP32 route).
 // A: R*R doubles (shared, both triangles, destroyed); F: R*R df2 (shared
-// scratch); out_hi, out_lo: R*R floats each (any memory; out_lo may be NULL,
-// then out_hi gets the rounded sum).  Returns kappa (the same value on every
-// thread).  Block-wide with 256 threads, R <= 64, R even.
+// scratch); out_hi, out_lo: R*R floats each (any memory;
+// out_lo may be NULL, then out_hi gets the rounded sum).  Returns kappa (the
+// same value on every thread); *route (when given) records the route: 0 FP32,
+// 1 double-float.  Block-wide with 256 threads, R <= 64, R even.
 static __device__ __noinline__ double spd_inverse(double* A, df2* F, int R, int rn,
-                                                  float* out_hi, float* out_lo, double df_above) {
+                                                  float* out_hi, float* out_lo, double df_above,
+                                                  int* route = nullptr) {
   __shared__ df2 s_r[kMaxR];             // 1 / D_k
   __shared__ df2 s_col[2 * kMaxR];       // the current column of the factorisation
   // partial column sums of |G| and |G^{-1}|: entry p R + c holds rows
   // p, p + nt/R, ... of column c (no atomics: they serialise on the columns)
   __shared__ float s_gpart[kCholThreads], s_xpart[kCholThreads];
-  __shared__ double s_kappa;
   const int tid = threadIdx.x, nt = blockDim.x;
   const int lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
   const int col = tid % R, phase = tid / R, nphase = nt / R;
@@ -217,98 +256,83 @@ static __device__ __noinline__ double spd_inverse(double* A, df2* F, int R, int 
       for (int i = phase; i < rn; i += nphase) cs += fabsf((float)A[i * R + col]);
     s_gpart[tid] = cs;
   }
-  // F = L^T (row p of F is column p of L, so that a warp reads a column of L
-  // with consecutive addresses), 1/D_k on the diagonal
-  // F32: F rounded to FP32, in the second half of the space of A
+  // |G^{-1}| for the estimate: in the space of F32 once L^{-1} is formed
   float* F32 = reinterpret_cast<float*>(A) + R * R;
-  if (R <= 16) chol_df<1>(A, R, F, F32, s_col, s_r);
-  else if (R <= 32) chol_df<3>(A, R, F, F32, s_col, s_r);
-  else
-    chol_df<(kMaxR * (kMaxR + 1) / 2 + kCholThreads - 1) / kCholThreads>(A, R, F, F32, s_col,
-                                                                        s_r);
-  const int nb = R / 2;
-  // ---- FP32 route.  Li: R*R floats in the first half of the space of A.
+  const float* absx = F32;
   {
-    __shared__ float dinv[kMaxR];
-    float* Li = reinterpret_cast<float*>(A);
-    float* Xa = F32;   // |G^{-1}| once L^{-1} is formed
-    for (int i = tid; i < R; i += nt) dinv[i] = s_r[i].h + s_r[i].l;
-    for (int round = 0; round * nw < R; ++round) {
-      const int c = (round & 1) ? (round + 1) * nw - 1 - warp : round * nw + warp;
-      if (c >= R) continue;
-      float acc0 = 0.f, acc1 = 0.f, y0 = 0.f, y1 = 0.f;
-      for (int i = c; i < R; ++i) {
-        const float acc_i = __shfl_sync(0xffffffffu, i < 32 ? acc0 : acc1, i & 31);
-        const float yi = (i == c ? 1.f : 0.f) - acc_i;
-        if (lane == (i & 31)) { if (i < 32) y0 = yi; else y1 = yi; }
-        const int j0 = lane, j1 = lane + 32;
-        if (j0 > i && j0 < R) acc0 = fmaf(F32[i * R + j0], yi, acc0);
-        if (j1 > i && j1 < R) acc1 = fmaf(F32[i * R + j1], yi, acc1);
-      }
-      __syncwarp();
-      if (lane < R) Li[lane * R + c] = lane >= c ? y0 : 0.f;
-      if (lane + 32 < R) Li[(lane + 32) * R + c] = lane + 32 >= c ? y1 : 0.f;
-    }
-    __syncthreads();
-    for (int b = tid; b < nb * nb; b += nt) {
-      const int bi = b / nb, bj = b % nb;
-      if (bi > bj) continue;
-      const int i = 2 * bi, j = 2 * bj;
-      float s00 = 0.f, s01 = 0.f, s10 = 0.f, s11 = 0.f;
-      for (int k = j; k < R; ++k) {      // j >= i
-        const float d = dinv[k];
-        const float2 li = *reinterpret_cast<const float2*>(Li + k * R + i);
-        float2 lj = *reinterpret_cast<const float2*>(Li + k * R + j);
-        lj.x *= d;
-        lj.y *= d;
-        s00 = fmaf(li.x, lj.x, s00);
-        s01 = fmaf(li.x, lj.y, s01);
-        s10 = fmaf(li.y, lj.x, s10);
-        s11 = fmaf(li.y, lj.y, s11);
-      }
-      const float v[4] = {s00, s01, s10, s11};
-      const int rr[4] = {i, i, i + 1, i + 1}, cc[4] = {j, j + 1, j, j + 1};
-#pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        out_hi[rr[q] * R + cc[q]] = v[q];
-        out_hi[cc[q] * R + rr[q]] = v[q];
-        Xa[rr[q] * R + cc[q]] = fabsf(v[q]);   // F32 is no longer read
-        Xa[cc[q] * R + rr[q]] = fabsf(v[q]);
-        if (out_lo) {
-          out_lo[rr[q] * R + cc[q]] = 0.f;
-          out_lo[cc[q] * R + rr[q]] = 0.f;
-        }
-      }
-    }
-    __syncthreads();
+    // F = L^T (row p of F is column p of L, so that a warp reads a column of
+    // L with consecutive addresses), 1/D_k on the diagonal; F32: F rounded to
+    // FP32, in the second half of the space of A
+    if (R <= 16) chol_df<1>(A, R, F, F32, s_col, s_r);
+    else if (R <= 32) chol_df<3>(A, R, F, F32, s_col, s_r);
+    else
+      chol_df<(kMaxR * (kMaxR + 1) / 2 + kCholThreads - 1) / kCholThreads>(A, R, F, F32, s_col,
+                                                                          s_r);
+    const int nb = R / 2;
+    // ---- FP32 route.  Li: R*R floats in the first half of the space of A.
     {
-      float cs = 0.f;
-      if (col < rn && phase < nphase)
-        for (int i = phase; i < rn; i += nphase) cs += Xa[i * R + col];
-      s_xpart[tid] = cs;
-    }
-    __syncthreads();
-    if (warp == 0) {
-      float mx = 0.f, mg = 0.f;
-      for (int c = lane; c < rn; c += 32) {
-        float sx = 0.f, sg = 0.f;
-        for (int p = 0; p < nphase; ++p) {
-          sx += s_xpart[p * R + c];
-          sg += s_gpart[p * R + c];
+      __shared__ float dinv[kMaxR];
+      float* Li = reinterpret_cast<float*>(A);
+      float* Xa = F32;
+      for (int i = tid; i < R; i += nt) dinv[i] = s_r[i].h + s_r[i].l;
+      for (int round = 0; round * nw < R; ++round) {
+        const int c = (round & 1) ? (round + 1) * nw - 1 - warp : round * nw + warp;
+        if (c >= R) continue;
+        float acc0 = 0.f, acc1 = 0.f, y0 = 0.f, y1 = 0.f;
+        for (int i = c; i < R; ++i) {
+          const float acc_i = __shfl_sync(0xffffffffu, i < 32 ? acc0 : acc1, i & 31);
+          const float yi = (i == c ? 1.f : 0.f) - acc_i;
+          if (lane == (i & 31)) { if (i < 32) y0 = yi; else y1 = yi; }
+          const int j0 = lane, j1 = lane + 32;
+          if (j0 > i && j0 < R) acc0 = fmaf(F32[i * R + j0], yi, acc0);
+          if (j1 > i && j1 < R) acc1 = fmaf(F32[i * R + j1], yi, acc1);
         }
-        mx = fmaxf(mx, sx);
-        mg = fmaxf(mg, sg);
+        __syncwarp();
+        if (lane < R) Li[lane * R + c] = lane >= c ? y0 : 0.f;
+        if (lane + 32 < R) Li[(lane + 32) * R + c] = lane + 32 >= c ? y1 : 0.f;
       }
-      for (int o = 16; o > 0; o >>= 1) {
-        mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-        mg = fmaxf(mg, __shfl_xor_sync(0xffffffffu, mg, o));
+      __syncthreads();
+      for (int b = tid; b < nb * nb; b += nt) {
+        const int bi = b / nb, bj = b % nb;
+        if (bi > bj) continue;
+        const int i = 2 * bi, j = 2 * bj;
+        float s00 = 0.f, s01 = 0.f, s10 = 0.f, s11 = 0.f;
+#pragma unroll 4
+        for (int k = j; k < R; ++k) {      // j >= i
+          const float d = dinv[k];
+          const float2 li = *reinterpret_cast<const float2*>(Li + k * R + i);
+          float2 lj = *reinterpret_cast<const float2*>(Li + k * R + j);
+          lj.x *= d;
+          lj.y *= d;
+          s00 = fmaf(li.x, lj.x, s00);
+          s01 = fmaf(li.x, lj.y, s01);
+          s10 = fmaf(li.y, lj.x, s10);
+          s11 = fmaf(li.y, lj.y, s11);
+        }
+        const float v[4] = {s00, s01, s10, s11};
+        const int rr[4] = {i, i, i + 1, i + 1}, cc[4] = {j, j + 1, j, j + 1};
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          out_hi[rr[q] * R + cc[q]] = v[q];
+          out_hi[cc[q] * R + rr[q]] = v[q];
+          Xa[rr[q] * R + cc[q]] = fabsf(v[q]);
+          Xa[cc[q] * R + rr[q]] = fabsf(v[q]);
+          if (out_lo) {
+            out_lo[rr[q] * R + cc[q]] = 0.f;
+            out_lo[cc[q] * R + rr[q]] = 0.f;
+          }
+        }
       }
-      if (lane == 0) s_kappa = (double)mg * (double)mx;
     }
-    __syncthreads();
   }
-  const double kappa = s_kappa;
-  if (!(kappa > df_above)) return kappa;
+  const float gnorm = part_colmax(s_gpart, R, rn);
+  const double kappa = (double)gnorm * (double)colsum_max(absx, R, rn, s_xpart);
+  if (!(kappa > df_above)) {
+    if (route && tid == 0) *route = 0;
+    return kappa;
+  }
+  if (route && tid == 0) *route = 1;
+  const int nb = R / 2;
   // ---- double-float route: Li as R*R df2 in the space of A
   df2* Li = reinterpret_cast<df2*>(A);
   for (int round = 0; round * nw < R; ++round) {

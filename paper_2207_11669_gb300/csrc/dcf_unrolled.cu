@@ -61,7 +61,7 @@ __device__ __forceinline__ void tsum(float& hi, float& lo, float x) {
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(256) k_refactor_ginv(Smalls* sm, DevState* st, int cur, int R,
                                                        int r, float rho) {
-  extern __shared__ double dsh[];
+  extern __shared__ double dsh[];   // R*R doubles, R*R double-floats
   df2* F = reinterpret_cast<df2*>(dsh + R * R);
   for (int i = threadIdx.x; i < R * R; i += blockDim.x) {
     int r = i / R, c = i % R;
@@ -72,7 +72,8 @@ __global__ void __launch_bounds__(256) k_refactor_ginv(Smalls* sm, DevState* st,
     if (threadIdx.x == 0) st->status = DCF_ENONFINITE;
     return;
   }
-  const double kappa = spd_inverse(dsh, F, R, r, sm->ginv32, sm->ginv32_lo, kDfKappa);
+  const double kappa = spd_inverse(dsh, F, R, r, sm->ginv32, sm->ginv32_lo, kDfKappa,
+                                   &st->route_g);
   if (threadIdx.x == 0) st->kappa_g = kappa;
 }
 
@@ -135,7 +136,7 @@ __device__ double block_sum(double v, double* red) {
 }
 
 __global__ void __launch_bounds__(256) k_unrolled_small(SmallArgs a) {
-  extern __shared__ double dsh[];          // 3 R*R doubles + R*R floats
+  extern __shared__ double dsh[];   // 3 R*R doubles, R*R double-floats
   __shared__ double red[256];
   const int R = a.R, k = a.k, RR = R * R;
   const int tid = threadIdx.x;
@@ -863,12 +864,20 @@ extern "C" dcf_status dcf_unrolled_forward(dcf_handle h, int K, const double* a,
   }
   const double lam0 = h->lam, rho0 = h->rho;
   const size_t ginv_smem = (size_t)R * R * 16;
+  // rho of the (U^T U + rho I)^{-1} held now: the last U-step's tail formed
+  // it with the plain rho; a step with another rho refactors first (with the
+  // same rho nothing is recomputed, so that the untrained network repeats the
+  // plain iteration bit for bit)
+  float rho_inv = (float)rho0;
   cudaError_t e = cudaSuccess;
   for (int k = 0; k < K && e == cudaSuccess; ++k) {
     e = [&]() -> cudaError_t {
       cudaError_t e2;
-      k_refactor_ginv<<<1, 256, ginv_smem, s>>>(h->sm, h->st, cur, R, h->r, (float)rho_k[k]);
-      if ((e2 = cudaGetLastError()) != cudaSuccess) return e2;
+      if ((float)rho_k[k] != rho_inv) {
+        k_refactor_ginv<<<1, 256, ginv_smem, s>>>(h->sm, h->st, cur, R, h->r, (float)rho_k[k]);
+        if ((e2 = cudaGetLastError()) != cudaSuccess) return e2;
+      }
+      rho_inv = (float)rho_k[k];   // also what the step's own tail uses
       h->lam = lam_k[k];
       h->rho = rho_k[k];
       h->alpha = (float)alpha_k[k];
@@ -899,8 +908,10 @@ extern "C" dcf_status dcf_unrolled_forward(dcf_handle h, int K, const double* a,
   h->alpha = 1.0f;
   h->ustar_out = nullptr;
   if (e != cudaSuccess) return cuda_fail(h, e, "unrolled forward");
-  k_refactor_ginv<<<1, 256, ginv_smem, s>>>(h->sm, h->st, cur, R, h->r, (float)rho0);
-  UCK(cudaGetLastError(), "refactor");
+  if (rho_inv != (float)rho0) {
+    k_refactor_ginv<<<1, 256, ginv_smem, s>>>(h->sm, h->st, cur, R, h->r, (float)rho0);
+    UCK(cudaGetLastError(), "refactor");
+  }
   std::vector<double> lk(K, 0.0);
   if (with_loss)
     UCK(cudaMemcpyAsync(lk.data(), u->loss, (size_t)K * 8, cudaMemcpyDeviceToHost, s), "loss");

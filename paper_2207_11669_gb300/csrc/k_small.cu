@@ -361,8 +361,15 @@ struct ReduceArgs {
 
 constexpr int kRedEntriesPerCta = 16;
 
-__device__ void tail_q(const ReduceArgs& a, double* A, df2* F);
-__device__ void tail_g(const ReduceArgs& a, double* A, df2* F);
+// The tails leave the r x r system to invert in A and return whether there
+// is one; invert_tail then inverts it (one call site for both systems).
+__device__ bool tail_q(const ReduceArgs& a, double* A);
+__device__ bool tail_g(const ReduceArgs& a, double* A);
+__device__ void invert_tail(const ReduceArgs& a, double* A, df2* F);
+
+// Dynamic shared memory of a reduction tail: R*R doubles (A), R*R
+// double-floats (F).
+constexpr size_t tail_smem(int R) { return (size_t)R * R * (sizeof(double) + sizeof(df2)); }
 
 __global__ void __launch_bounds__(256) k_reduce_parts(ReduceArgs a) {
   if ((a.tail == TAIL_Q || a.tail == TAIL_G) && a.st->stop) return;
@@ -432,23 +439,23 @@ __global__ void __launch_bounds__(256) k_reduce_parts(ReduceArgs a) {
   __syncthreads();
   if (!is_last) return;
   __threadfence();
-  extern __shared__ double dsh[];   // R*R doubles, then R*R double-floats
+  extern __shared__ double dsh[];   // tail_smem(R): A, F
   df2* F = reinterpret_cast<df2*>(dsh + a.R * a.R);
   if (tid == 0) *a.counter = 0u;
-  if (a.tail == TAIL_Q || a.tail == TAIL_INIT_Q) tail_q(a, dsh, F);
-  else tail_g(a, dsh, F);
+  const bool inv = (a.tail == TAIL_Q || a.tail == TAIL_INIT_Q) ? tail_q(a, dsh) : tail_g(a, dsh);
+  if (inv) invert_tail(a, dsh, F);
 }
 
 // Q_t is in out[0] (R*R), Y = V_{t-1}^T (V_t - V_{t-1}) in out[1], the Gram of
 // V_t - V_{t-1} in out[2], Huber in out[3].  V_{t-1}^T V_t = Q_{t-1} + Y.
-__device__ void tail_q(const ReduceArgs& a, double* A, df2* F) {
+__device__ bool tail_q(const ReduceArgs& a, double* A) {
   const int R = a.R;
   Smalls* sm = a.sm;
   DevState* st = a.st;
   if (a.tail == TAIL_INIT_Q) {
     // start point: only V0^T V0 is needed (for the first metrics)
     for (int i = threadIdx.x; i < R * R; i += blockDim.x) sm->q[a.copy][i] = __ldcg(a.out[0] + i);
-    return;
+    return false;
   }
   const int cur = a.copy, nxt = cur ^ 1;
   // every load of the thread's entries first (they are independent), then the stores
@@ -485,17 +492,29 @@ __device__ void tail_q(const ReduceArgs& a, double* A, df2* F) {
   __syncthreads();
   if (!all_finite(A, R * R)) {
     if (threadIdx.x == 0) st->status = 4;  // DCF_ENONFINITE
-    return;
+    return false;
   }
-  if (a.u_mode == 0) {
-    const double kappa = spd_inverse(A, F, R, a.r > 0 ? a.r : R, sm->hinv32, nullptr, kDfKappa);
-    if (threadIdx.x == 0) st->kappa_h = kappa;
+  return a.u_mode == 0;   // FedAvg steps with Q_t + rho I itself
+}
+
+// (Q_t + rho I)^{-1} (hi + lo rounded) or (U_t^T U_t + rho I)^{-1} (hi, lo).
+__device__ void invert_tail(const ReduceArgs& a, double* A, df2* F) {
+  const bool q = a.tail == TAIL_Q || a.tail == TAIL_INIT_Q;
+  Smalls* sm = a.sm;
+  DevState* st = a.st;
+  float* hi = q ? sm->hinv32 : sm->ginv32;
+  float* lo = q ? nullptr : sm->ginv32_lo;
+  const double kappa = spd_inverse(A, F, a.R, a.r > 0 ? a.r : a.R, hi, lo, kDfKappa,
+                                   q ? &st->route_h : &st->route_g);
+  if (threadIdx.x == 0) {
+    if (q) st->kappa_h = kappa;
+    else st->kappa_g = kappa;
   }
 }
 
 // Gram of U_t in out[0], U_{t-1}^T (U_t - U_{t-1}) in out[1], the Gram of
 // U_t - U_{t-1} in out[2].
-__device__ void tail_g(const ReduceArgs& a, double* A, df2* F) {
+__device__ bool tail_g(const ReduceArgs& a, double* A) {
   const int R = a.R;
   Smalls* sm = a.sm;
   DevState* st = a.st;
@@ -591,11 +610,9 @@ __device__ void tail_g(const ReduceArgs& a, double* A, df2* F) {
   __syncthreads();
   if (!all_finite(A, R * R)) {
     if (threadIdx.x == 0) st->status = 4;
-    return;
+    return false;
   }
-  const double kappa =
-      spd_inverse(A, F, R, a.r > 0 ? a.r : R, sm->ginv32, sm->ginv32_lo, kDfKappa);
-  if (threadIdx.x == 0) st->kappa_g = kappa;
+  return true;
 }
 
 // ---------------------------------------------------------------------------
@@ -980,10 +997,10 @@ __global__ void __launch_bounds__(256) k_breduce(const BInst* __restrict__ insts
   ra.copy = (tail == TAIL_INIT_G || tail == TAIL_INIT_Q) ? 0 : cur;
   ra.sm = I.sm;
   ra.st = I.st;
-  extern __shared__ double dsh[];   // R*R doubles, then R*R double-floats
+  extern __shared__ double dsh[];   // tail_smem(R): A, F
   df2* F = reinterpret_cast<df2*>(dsh + RR);
-  if (tail == TAIL_Q || tail == TAIL_INIT_Q) tail_q(ra, dsh, F);
-  else tail_g(ra, dsh, F);
+  const bool inv = (tail == TAIL_Q || tail == TAIL_INIT_Q) ? tail_q(ra, dsh) : tail_g(ra, dsh);
+  if (inv) invert_tail(ra, dsh, F);
 }
 
 // ---------------------------------------------------------------------------
@@ -1087,7 +1104,7 @@ static cudaError_t bsmall_T(int kind, const BInst* insts, const BItem* items, in
     case 1: k_brows<R><<<grid, 256, 0, s>>>(insts, items, nitems, cur); break;
     case 2: k_bgram<R><<<grid, 256, GvvCfg<R>::smem_bytes, s>>>(insts, items, nitems, cur, arg); break;
     default:
-      k_breduce<R><<<nitems, 256, (size_t)R * R * 16, s>>>(insts, which, cur, arg);
+      k_breduce<R><<<nitems, 256, tail_smem(R), s>>>(insts, which, cur, arg);
       break;
   }
   return cudaGetLastError();
@@ -1104,7 +1121,7 @@ cudaError_t launch_bsmall(int R, int kind, const BInst* insts, const BItem* item
 
 static cudaError_t launch_reduce(const ReduceArgs& ra, cudaStream_t s) {
   int grid = (ra.total + kRedEntriesPerCta - 1) / kRedEntriesPerCta;
-  size_t smem = (size_t)ra.R * ra.R * (sizeof(double) + sizeof(df2));
+  size_t smem = tail_smem(ra.R);
   k_reduce_parts<<<grid, 256, smem, s>>>(ra);
   return cudaGetLastError();
 }
@@ -1125,10 +1142,10 @@ cudaError_t launch_make_w(const IterArgs& a, int copy, int respect_stop, cudaStr
   }
 }
 
-// The reduction tail needs R*R*16 bytes of dynamic shared memory (64 KB at R = 64).
+// The reduction tail needs tail_smem(R) bytes of dynamic shared memory (64 KB at R = 64).
 cudaError_t prepare_small_kernels() {
   return cudaFuncSetAttribute(k_reduce_parts, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              kMaxR * kMaxR * 16);
+                              (int)tail_smem(kMaxR));
 }
 
 template <int R>

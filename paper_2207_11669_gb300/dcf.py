@@ -67,7 +67,8 @@ _SIGS = {
     "dcf_get_stats": (C.c_int, [C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_double),
                                 C.POINTER(C.c_int)]),
     "dcf_get_conditioning": (C.c_int, [C.c_void_p, C.POINTER(C.c_double),
-                                       C.POINTER(C.c_double)]),
+                                       C.POINTER(C.c_double), C.POINTER(C.c_int),
+                                       C.POINTER(C.c_int)]),
     "dcf_set_truth": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_int]),
     "dcf_rel_err": (C.c_int, [C.c_void_p, C.POINTER(C.c_double)]),
     "dcf_singular_values": (C.c_int, [C.c_void_p, C.POINTER(C.c_double),
@@ -284,10 +285,10 @@ def dcf_get_stats(h):
     return o.value, d.value, it.value
 
 
-def dcf_get_conditioning(h):
-    g, q = C.c_double(), C.c_double()
-    _check(h, lib().dcf_get_conditioning(h, C.byref(g), C.byref(q)))
-    return g.value, q.value
+def dcf_get_conditioning(h, routes=False):
+    g, q, rg, rq = C.c_double(), C.c_double(), C.c_int(), C.c_int()
+    _check(h, lib().dcf_get_conditioning(h, C.byref(g), C.byref(q), C.byref(rg), C.byref(rq)))
+    return (g.value, q.value, rg.value, rq.value) if routes else (g.value, q.value)
 
 
 def dcf_set_truth(h, A, B):
@@ -503,9 +504,11 @@ class Solver:
     def stats(self):
         return dcf_get_stats(self.h)
 
-    def conditioning(self):
-        """(kappa of U^T U + rho I, kappa of V^T V + rho I) of the last iteration."""
-        return dcf_get_conditioning(self.h)
+    def conditioning(self, routes=False):
+        """(kappa of U^T U + rho I, kappa of V^T V + rho I) of the last iteration,
+        and with routes=True how their inverses were formed (0 FP32 route,
+        1 double-float)."""
+        return dcf_get_conditioning(self.h, routes)
 
     def set_truth(self, A, B):
         self._truth = (np.ascontiguousarray(A, np.float32), np.ascontiguousarray(B, np.float32))
