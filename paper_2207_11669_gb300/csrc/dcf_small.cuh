@@ -173,6 +173,98 @@ static __device__ __noinline__ void chol_df(const double* A, int R, df2* F, floa
   __syncthreads();
 }
 
+// Row and column (i >= j) of entry e of a packed lower triangle.
+static __device__ __forceinline__ void tri_decode(int e, int& i, int& j) {
+  i = (int)((sqrtf(8.0f * (float)e + 1.0f) - 1.0f) * 0.5f);
+  while ((i + 1) * (i + 2) / 2 <= e) ++i;
+  while (i * (i + 1) / 2 > e) --i;
+  j = e - i * (i + 1) / 2;
+}
+
+// The same L D L^T by blocks of 8 columns (R a multiple of 8), with the
+// output contract of chol_df.  The unblocked form pays one block barrier per
+// column on a chain of R dependent steps; here a block of 8 columns costs
+// three: (a) warp 0 factors the 8 x 8 diagonal block (warp-synchronous
+// steps), (b) the rows below it are brought through the block's 8 steps,
+// 8 threads per row exchanging values by shuffles, (c) the trailing matrix
+// takes the block's rank-8 update, every entry independently.  Working
+// storage is F itself: row j of F holds column j of the lower triangle,
+// unscaled (W = L D) until the end, where L = W D^{-1} and 1/D_k on the
+// diagonal are written.
+static __device__ __noinline__ void chol_df_blocked(const double* A, int R, df2* F, float* Ff,
+                                                    df2* s_r) {
+  __shared__ df2 Lt[8 * 8];        // Lt[m * 8 + c] = L_{k0+c, k0+m} of the diagonal block
+  __shared__ df2 Lp[8 * kMaxR];    // Lp[m * R + i] = L_{i, k0+m} of the panel
+  const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5;
+  for (int idx = tid; idx < R * R; idx += nt) {
+    const int r = idx / R, c = idx % R;
+    F[idx] = c >= r ? df_from_double(A[idx]) : df2{0.f, 0.f};
+  }
+  __syncthreads();
+  for (int k0 = 0; k0 < R; k0 += 8) {
+    // (a) diagonal block
+    if (warp == 0) {
+      for (int mm = 0; mm < 8; ++mm) {
+        const int m = k0 + mm;
+        const df2 rm = df_recip(F[m * R + m]);
+        if (lane == 0) s_r[m] = rm;
+        const int nrem = 7 - mm;
+        if (lane < nrem * (nrem + 1) / 2) {
+          int ii, jj;
+          tri_decode(lane, ii, jj);
+          const int i = m + 1 + ii, j = m + 1 + jj;
+          F[j * R + i] = df_sub(F[j * R + i], df_mul(F[m * R + i], df_mul(F[m * R + j], rm)));
+        }
+        __syncwarp();
+      }
+      for (int e = lane; e < 64; e += 32) {
+        const int mm = e / 8, c = e % 8;
+        Lt[e] = c > mm ? df_mul(F[(k0 + mm) * R + k0 + c], s_r[k0 + mm]) : df2{0.f, 0.f};
+      }
+    }
+    __syncthreads();
+    // (b) panel: rows i >= k0 + 8, thread (row, c) holds A_{i, k0+c}
+    const int nrows = R - k0 - 8;
+    const int tot = (nrows * 8 + 31) / 32 * 32;   // whole warps, for the shuffles
+    for (int t = tid; t < tot; t += nt) {
+      const int row = t / 8, c = t % 8, i = k0 + 8 + row;
+      const bool act = row < nrows;
+      df2 a = act ? F[(k0 + c) * R + i] : df2{0.f, 0.f};
+      for (int mm = 0; mm < 7; ++mm) {
+        const float ah = __shfl_sync(0xffffffffu, a.h, (lane & ~7) + mm);
+        const float al = __shfl_sync(0xffffffffu, a.l, (lane & ~7) + mm);
+        if (c > mm) a = df_sub(a, df_mul(df2{ah, al}, Lt[mm * 8 + c]));
+      }
+      if (act) {
+        F[(k0 + c) * R + i] = a;
+        Lp[c * R + i] = df_mul(a, s_r[k0 + c]);
+      }
+    }
+    __syncthreads();
+    // (c) trailing matrix: A_ij -= sum_m W_{i,m} L_{j,m} over the block's columns
+    const int nt2 = nrows * (nrows + 1) / 2;
+    for (int e = tid; e < nt2; e += nt) {
+      int ii, jj;
+      tri_decode(e, ii, jj);
+      const int i = k0 + 8 + ii, j = k0 + 8 + jj;
+      df2 acc = df_mul(F[k0 * R + i], Lp[j]);
+#pragma unroll
+      for (int mm = 1; mm < 8; ++mm) acc = df_add(acc, df_mul(F[(k0 + mm) * R + i], Lp[mm * R + j]));
+      F[j * R + i] = df_sub(F[j * R + i], acc);
+    }
+    __syncthreads();
+  }
+  // L = W D^{-1} above the diagonal of F, 1/D_k on it
+  for (int idx = tid; idx < R * R; idx += nt) {
+    const int r = idx / R, c = idx % R;
+    if (c < r) continue;
+    const df2 v = c > r ? df_mul(F[idx], s_r[r]) : s_r[r];
+    F[idx] = v;
+    if (Ff) Ff[idx] = v.h + v.l;
+  }
+  __syncthreads();
+}
+
 static __device__ __noinline__ int all_finite(const double* A, int n) {
   __shared__ int ok;
   if (threadIdx.x == 0) ok = 1;
@@ -224,20 +316,78 @@ static __device__ float colsum_max(const float* X, int R, int rn, float* part) {
   return part_colmax(part, R, rn);
 }
 
+// In-place Gauss-Jordan inverse in FP32 on one warp, without pivoting (SPD
+// systems need none): lane j holds column j of the matrix in registers.  Step
+// k: lane k publishes its column to shared memory (pc), every lane reads the
+// pivot and column k from there; row k, which the update also needs, is
+// column k up to sign (the in-place sweep keeps a symmetric matrix
+// symmetric in its unswept part and antisymmetric across the swept rows and
+// columns: a[k][j] = -a[j][k] for j < k, a[j][k] for j > k), so lane j reads
+// its own entry pc[j].  R dependent steps without barriers and without
+// dynamically indexed registers.  Af: R*R floats (shared, row-major, SPD);
+// pc: 2R floats (shared scratch).  Writes X = Af^{-1} to out_hi (out_lo
+// zeroed when given) and returns max_{j < rn} sum_{i < rn} |X_ij| on every
+// lane.  Warp-wide (one warp).
+template <int R>
+static __device__ __noinline__ float gj_inverse_f32(const float* Af, int rn, float* out_hi,
+                                                    float* out_lo, float* pc) {
+  static_assert(R <= 32, "one column per lane");
+  const int lane = threadIdx.x & 31;
+  float c[R];
+#pragma unroll
+  for (int i = 0; i < R; ++i) c[i] = lane < R ? Af[i * R + lane] : 0.f;
+#pragma unroll 1
+  for (int k = 0; k < R; ++k) {
+    float* col = pc + (k & 1) * R;   // double-buffered: no write-after-read wait
+    if (lane == k) {
+#pragma unroll
+      for (int i = 0; i < R; ++i) col[i] = c[i];
+    }
+    __syncwarp();
+    // reciprocal: the fast estimate and one Newton step (an IEEE division is
+    // a quarter of the step's time here)
+    float pinv = __fdividef(1.f, col[k]);
+    pinv = pinv * (2.f - col[k] * pinv);
+    const float own = lane < R ? col[lane] : 0.f;
+    const float rowk = lane == k ? pinv : (lane < k ? -own : own) * pinv;   // new a[k][j]
+#pragma unroll
+    for (int i = 0; i < R; ++i) {
+      const float f = col[i];                              // a[i][k]
+      const float v = fmaf(-f, rowk, lane == k ? 0.f : c[i]);
+      c[i] = i == k ? rowk : v;
+    }
+  }
+  float cs = 0.f;
+#pragma unroll
+  for (int i = 0; i < R; ++i) {
+    if (lane < R) {
+      out_hi[i * R + lane] = c[i];
+      if (out_lo) out_lo[i * R + lane] = 0.f;
+    }
+    if (i < rn) cs += fabsf(c[i]);
+  }
+  cs = lane < rn ? cs : 0.f;
+  for (int o = 16; o > 0; o >>= 1) cs = fmaxf(cs, __shfl_xor_sync(0xffffffffu, cs, o));
+  return cs;
+}
+
 // SPD inverse G^{-1} of G = A (R x R, FP64 input):
-//  - the factorisation G = L D L^T in double-float (the stability-critical
-//    step), then L^{-1} and G^{-1} = L^{-T} D^{-1} L^{-1} in FP32 from the
-//    rounded factors (relative error about kappa 2^-24);
+//  - first in FP32: for R <= 32 by Gauss-Jordan on one warp
+//    (gj_inverse_f32), for R = 64 from the double-float factorisation
+//    G = L D L^T (blocked) with L^{-1} and G^{-1} = L^{-T} D^{-1} L^{-1} in
+//    FP32 from the rounded factors; relative error about kappa 2^-24 times a
+//    small multiple of R;
 //  - when the 1-norm condition estimate kappa = |G|_1 |G^{-1}|_1 (over the
 //    leading rn x rn block: the padded rank columns form the decoupled block
-//    rho I) exceeds `df_above`, L^{-1} and the product again in double-float
-//    (relative error about kappa 2^-44), handed on as the float pair
-//    out_hi + out_lo (out_lo is zero after the FP32 route).
+//    rho I) exceeds `df_above`, again from the double-float factorisation with
+//    L^{-1} and the product in double-float (relative error about kappa
+//    2^-44), handed on as the float pair out_hi + out_lo (out_lo is zero after
+//    the FP32 route).
 // A: R*R doubles (shared, both triangles, destroyed); F: R*R df2 (shared
-// scratch); out_hi, out_lo: R*R floats each (any memory;
-// out_lo may be NULL, then out_hi gets the rounded sum).  Returns kappa (the
-// same value on every thread); *route (when given) records the route: 0 FP32,
-// 1 double-float.  Block-wide with 256 threads, R <= 64, R even.
+// scratch); out_hi, out_lo: R*R floats each (any memory; out_lo may be NULL,
+// then out_hi gets the rounded sum).  Returns kappa (the same value on every
+// thread); *route (when given) records the route: 0 FP32, 1 double-float.
+// Block-wide with 256 threads, R <= 64, R a multiple of 8.
 static __device__ __noinline__ double spd_inverse(double* A, df2* F, int R, int rn,
                                                   float* out_hi, float* out_lo, double df_above,
                                                   int* route = nullptr) {
@@ -246,6 +396,7 @@ static __device__ __noinline__ double spd_inverse(double* A, df2* F, int R, int 
   // partial column sums of |G| and |G^{-1}|: entry p R + c holds rows
   // p, p + nt/R, ... of column c (no atomics: they serialise on the columns)
   __shared__ float s_gpart[kCholThreads], s_xpart[kCholThreads];
+  __shared__ float s_xnorm;
   const int tid = threadIdx.x, nt = blockDim.x;
   const int lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
   const int col = tid % R, phase = tid / R, nphase = nt / R;
@@ -256,20 +407,35 @@ static __device__ __noinline__ double spd_inverse(double* A, df2* F, int R, int 
       for (int i = phase; i < rn; i += nphase) cs += fabsf((float)A[i * R + col]);
     s_gpart[tid] = cs;
   }
-  // |G^{-1}| for the estimate: in the space of F32 once L^{-1} is formed
+  // the factorisation into F (and its FP32 rounding into the second half of
+  // the space of A, for the FP32 route at R = 64)
   float* F32 = reinterpret_cast<float*>(A) + R * R;
-  const float* absx = F32;
-  {
-    // F = L^T (row p of F is column p of L, so that a warp reads a column of
-    // L with consecutive addresses), 1/D_k on the diagonal; F32: F rounded to
-    // FP32, in the second half of the space of A
-    if (R <= 16) chol_df<1>(A, R, F, F32, s_col, s_r);
-    else if (R <= 32) chol_df<3>(A, R, F, F32, s_col, s_r);
-    else
-      chol_df<(kMaxR * (kMaxR + 1) / 2 + kCholThreads - 1) / kCholThreads>(A, R, F, F32, s_col,
-                                                                          s_r);
+  auto factor = [&](float* f32) {
+    if (R == 64) chol_df_blocked(A, R, F, f32, s_r);
+    else if (R <= 16) chol_df<1>(A, R, F, f32, s_col, s_r);
+    else chol_df<3>(A, R, F, f32, s_col, s_r);
+  };
+  float xnorm;
+  if (R <= 32) {
+    // G in FP32 in the space of F (free until the factorisation)
+    float* Af = reinterpret_cast<float*>(F);
+    for (int i = tid; i < R * R; i += nt) Af[i] = (float)A[i];
+    __syncthreads();
+    if (warp == 0) {
+      float xn;
+      float* pc = reinterpret_cast<float*>(s_col);   // 2R floats, unused until the factorisation
+      if (R == 8) xn = gj_inverse_f32<8>(Af, rn, out_hi, out_lo, pc);
+      else if (R == 16) xn = gj_inverse_f32<16>(Af, rn, out_hi, out_lo, pc);
+      else xn = gj_inverse_f32<32>(Af, rn, out_hi, out_lo, pc);
+      if (lane == 0) s_xnorm = xn;
+    }
+    __syncthreads();
+    xnorm = s_xnorm;
+  } else {
+    factor(F32);
+    // FP32 route.  Li: R*R floats in the first half of the space of A;
+    // |G^{-1}| for the estimate in the space of F32 once L^{-1} is formed
     const int nb = R / 2;
-    // ---- FP32 route.  Li: R*R floats in the first half of the space of A.
     {
       __shared__ float dinv[kMaxR];
       float* Li = reinterpret_cast<float*>(A);
@@ -324,14 +490,16 @@ static __device__ __noinline__ double spd_inverse(double* A, df2* F, int R, int 
         }
       }
     }
+    xnorm = colsum_max(F32, R, rn, s_xpart);
   }
   const float gnorm = part_colmax(s_gpart, R, rn);
-  const double kappa = (double)gnorm * (double)colsum_max(absx, R, rn, s_xpart);
+  const double kappa = (double)gnorm * (double)xnorm;
   if (!(kappa > df_above)) {
     if (route && tid == 0) *route = 0;
     return kappa;
   }
   if (route && tid == 0) *route = 1;
+  if (R <= 32) factor(nullptr);   // A is still intact there
   const int nb = R / 2;
   // ---- double-float route: Li as R*R df2 in the space of A
   df2* Li = reinterpret_cast<df2*>(A);
