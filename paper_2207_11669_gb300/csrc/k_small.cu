@@ -458,35 +458,24 @@ __device__ bool tail_q(const ReduceArgs& a, double* A) {
     return false;
   }
   const int cur = a.copy, nxt = cur ^ 1;
-  // every load of the thread's entries first (they are independent), then the stores
-  for (int i0 = threadIdx.x; i0 < R * R; i0 += 4 * 256) {   // 4 entries per thread at a time
-    double qv[4], yv[4], dv[4], qo[4];
-#pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      const int i = i0 + u * 256;
-      const bool in = i < R * R;
-      qv[u] = in ? __ldcg(a.out[0] + i) : 0.0;
-      yv[u] = in ? __ldcg(a.out[1] + i) : 0.0;
-      dv[u] = in ? __ldcg(a.out[2] + i) : 0.0;
-      qo[u] = in ? sm->q[cur][i] : 0.0;
-    }
-#pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      const int i = i0 + u * 256;
-      if (i >= R * R) continue;
-      sm->q[nxt][i] = qv[u];
-      sm->dvy[i] = yv[u];
-      sm->dvv[i] = dv[u];
-      const double xv = qo[u] + yv[u];
-      sm->xv[i] = xv;
-      const float xh = (float)xv;
-      sm->xv32[0][i] = xh;
-      sm->xv32[1][i] = (float)(xv - (double)xh);
-      const int r = i / R, c = i % R;
-      const double h = qv[u] + (r == c ? (double)(a.rho_q > 0.f ? a.rho_q : a.rho) : 0.0);
-      A[i] = h;
-      sm->qrho32[i] = (float)h;
-    }
+  // a rolled loop: this tail runs once on one CTA with the instruction cache
+  // cold, so code size costs more than load latency
+  const double rq = (double)(a.rho_q > 0.f ? a.rho_q : a.rho);
+#pragma unroll 1
+  for (int i = threadIdx.x; i < R * R; i += blockDim.x) {
+    const double qv = __ldcg(a.out[0] + i), yv = __ldcg(a.out[1] + i);
+    const double dv = __ldcg(a.out[2] + i), qo = sm->q[cur][i];
+    sm->q[nxt][i] = qv;
+    sm->dvy[i] = yv;
+    sm->dvv[i] = dv;
+    const double xv = qo + yv;
+    sm->xv[i] = xv;
+    const float xh = (float)xv;
+    sm->xv32[0][i] = xh;
+    sm->xv32[1][i] = (float)(xv - (double)xh);
+    const double h = qv + ((i / R) == (i % R) ? rq : 0.0);
+    A[i] = h;
+    sm->qrho32[i] = (float)h;
   }
   if (threadIdx.x == 0) st->huber = __ldcg(a.out[3]);
   __syncthreads();
@@ -534,60 +523,47 @@ __device__ bool tail_g(const ReduceArgs& a, double* A) {
     // a shuffle tree per warp, then the per-warp values across lanes of warp 0.
     // Every load of the thread's entries is issued before any store or product;
     // the new Gram also goes straight into A (G_t + rho I) for the inverse below.
-    __shared__ double wsum[6][32];
-    double v[6] = {0, 0, 0, 0, 0, 0};
-    for (int i0 = threadIdx.x; i0 < R * R; i0 += 4 * 256) {   // 4 entries per thread at a time
-      double gn[4], a2t[4], a1[4], qn[4], b2[4], b3[4], go[4], qo[4], a2[4];
-#pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        const int i = i0 + u * 256;
-        const bool in = i < R * R;
-        const int r = in ? i / R : 0, c = in ? i % R : 0;
-        gn[u] = in ? __ldcg(a.out[0] + i) : 0.0;
-        a2[u] = in ? __ldcg(a.out[1] + i) : 0.0;
-        a2t[u] = in ? __ldcg(a.out[1] + c * R + r) : 0.0;
-        a1[u] = in ? __ldcg(a.out[2] + i) : 0.0;
-        qn[u] = in ? sm->q[tgt][i] : 0.0;
-        b3[u] = in ? sm->dvv[i] : 0.0;
-        b2[u] = in ? sm->dvy[i] + b3[u] : 0.0;
-        go[u] = in ? sm->gram[cur][i] : 0.0;
-        qo[u] = in ? sm->q[cur][i] : 0.0;
-      }
-#pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        const int i = i0 + u * 256;
-        if (i >= R * R) continue;
-        sm->gram[tgt][i] = gn[u];
-        sm->xu[i] = a2[u];
-        const int r = i / R, c = i % R;
-        A[i] = gn[u] + (r == c ? (double)a.rho : 0.0);
-        v[0] = fma(gn[u], qn[u], v[0]);
-        v[1] = fma(a1[u], qn[u], v[1]);
-        v[2] = fma(a2t[u], b2[u], v[2]);
-        v[3] = fma(go[u], b3[u], v[3]);
-        if (r == c) {
-          v[4] += go[u];
-          v[5] += qo[u];
-        }
+    // The loops are rolled: this tail runs once on one CTA with the
+    // instruction cache cold, so code size costs more than load latency.
+    __shared__ double s6[6][256];   // per-thread partial sums, then the six totals in [q][0]
+    double v0 = 0, v1 = 0, v2 = 0, v3 = 0, v4 = 0, v5 = 0;
+#pragma unroll 1
+    for (int i = threadIdx.x; i < R * R; i += blockDim.x) {
+      const int r = i / R, c = i % R;
+      const double gn = __ldcg(a.out[0] + i), a2 = __ldcg(a.out[1] + i);
+      const double a2t = __ldcg(a.out[1] + c * R + r), a1 = __ldcg(a.out[2] + i);
+      const double qn = sm->q[tgt][i], b3 = sm->dvv[i], b2 = sm->dvy[i] + b3;
+      const double go = sm->gram[cur][i], qo = sm->q[cur][i];
+      sm->gram[tgt][i] = gn;
+      sm->xu[i] = a2;
+      A[i] = gn + (r == c ? (double)a.rho : 0.0);
+      v0 = fma(gn, qn, v0);
+      v1 = fma(a1, qn, v1);
+      v2 = fma(a2t, b2, v2);
+      v3 = fma(go, b3, v3);
+      if (r == c) {
+        v4 += go;
+        v5 += qo;
       }
     }
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1)
-#pragma unroll
-      for (int q = 0; q < 6; ++q) v[q] += __shfl_xor_sync(0xffffffffu, v[q], o);
-    if (lane == 0)
-#pragma unroll
-      for (int q = 0; q < 6; ++q) wsum[q][wid] = v[q];
+    s6[0][threadIdx.x] = v0; s6[1][threadIdx.x] = v1; s6[2][threadIdx.x] = v2;
+    s6[3][threadIdx.x] = v3; s6[4][threadIdx.x] = v4; s6[5][threadIdx.x] = v5;
     __syncthreads();
-    if (wid == 0) {
-#pragma unroll
-      for (int q = 0; q < 6; ++q) v[q] = lane < nw ? wsum[q][lane] : 0.0;
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1)
-#pragma unroll
-        for (int q = 0; q < 6; ++q) v[q] += __shfl_xor_sync(0xffffffffu, v[q], o);
+    // warp q < 6 adds row q of s6
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (wid < 6) {
+      double t = 0.0;
+#pragma unroll 1
+      for (int k = lane; k < 256; k += 32) t += s6[wid][k];
+#pragma unroll 1
+      for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+      __syncwarp();
+      if (lane == 0) s6[wid][0] = t;
     }
+    __syncthreads();
+    double v[6];
+    if (threadIdx.x == 0)
+      for (int q = 0; q < 6; ++q) v[q] = s6[q][0];
     if (threadIdx.x == 0) {
       const double a0 = v[0];
       double d2 = v[1] + 2.0 * v[2] + v[3];
