@@ -699,26 +699,41 @@ __device__ __forceinline__ void rows_block(const IterArgs& a, int64_t rb) {
   const int rows = (int)dmin64((int64_t)kRowsPerCta, a.m - row0);
   if (a.add_uxv)
     for (int i = tid; i < R * R; i += 256) Mat[i] = a.sm->xv32[0][i];
-  for (int i = tid; i < kRowsPerCta * R; i += 256) {
-    const int rr = i / R;
-    float hi = 0.f, lo = 0.f, uo = 0.f;
-    if (rr < rows) {
-      const int64_t off = row0 * R + i;
-      uo = U[off];
-      // the partials in groups of 8 loads issued together, summed in order
-      if (a.n_splits == 1) hi = a.part_p[off];
-      else for (int s0 = 0; s0 < a.n_splits; s0 += 8) {
-        float v[8];
+  // The thread's PER entries: U and the partials of P, every load of a group
+  // of 8 splits in flight together (one latency round per group instead of
+  // one per entry and group).
+  constexpr int PER = kRowsPerCta * R / 256;
+  {
+    float hi[PER], lo[PER], uo[PER];
+    int64_t off[PER];
+    bool in[PER];
 #pragma unroll
-        for (int q = 0; q < 8; ++q)
-          v[q] = s0 + q < a.n_splits ? a.part_p[(int64_t)(s0 + q) * a.m * R + off] : 0.f;
-#pragma unroll
-        for (int q = 0; q < 8; ++q)
-          if (s0 + q < a.n_splits) two_sum_add(hi, lo, v[q]);
-      }
+    for (int u = 0; u < PER; ++u) {
+      const int i = tid + u * 256;
+      in[u] = i / R < rows;
+      off[u] = row0 * R + i;
+      uo[u] = in[u] ? U[off[u]] : 0.f;
+      hi[u] = lo[u] = 0.f;
     }
-    Ps[i] = hi + lo;
-    Uo[i] = uo;
+    for (int s0 = 0; s0 < a.n_splits; s0 += 8) {
+      float v[8][PER];
+#pragma unroll
+      for (int q = 0; q < 8; ++q)
+#pragma unroll
+        for (int u = 0; u < PER; ++u)
+          v[q][u] = s0 + q < a.n_splits && in[u]
+                        ? a.part_p[(int64_t)(s0 + q) * a.m * R + off[u]] : 0.f;
+#pragma unroll
+      for (int q = 0; q < 8; ++q)
+#pragma unroll
+        for (int u = 0; u < PER; ++u)
+          if (s0 + q < a.n_splits) two_sum_add(hi[u], lo[u], v[q][u]);
+    }
+#pragma unroll
+    for (int u = 0; u < PER; ++u) {
+      Ps[tid + u * 256] = hi[u] + lo[u];
+      Uo[tid + u * 256] = uo[u];
+    }
   }
   __syncthreads();
   const int ar = tid >> 3, g = tid & 7;
