@@ -490,6 +490,7 @@ static __device__ __noinline__ double spd_inverse(double* A, df2* F, int R, int 
         }
       }
     }
+    __syncthreads();   // every |G^{-1}| entry of the product is written
     xnorm = colsum_max(F32, R, rn, s_xpart);
   }
   const float gnorm = part_colmax(s_gpart, R, rn);
