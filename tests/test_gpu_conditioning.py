@@ -99,17 +99,24 @@ def test_one_step_parity_ill_conditioned(eps, rho, path):
     assert eu <= (1e-4 if kappa < 1e7 else 1e-3)
 
 
-def test_well_conditioned_problem_takes_the_fp32_route():
-    case = make_case(300, [100, 76, 140], 8, seed=5)
-    s = dcf.Solver(300, case["n_i"], 8, case["rho"], case["lam"], path=dcf.PATH_GENERAL)
+@pytest.mark.parametrize("r", [8, 16, 32, 64])
+def test_well_conditioned_problem_takes_the_fp32_route(r):
+    """Each padded rank has its own FP32 route (one-warp Gauss-Jordan up to 32,
+    the factorisation-based one at 64); the estimate must be right on all."""
+    case = make_case(300, [100, 76, 140], r, seed=5)
+    s = dcf.Solver(300, case["n_i"], r, case["rho"], case["lam"], path=dcf.PATH_GENERAL)
     s.load(case["M"])
     s.load_init(case["U0"], case["V0"])
     s.step(1)
-    U, _ = s.factors()
-    kg, kh = s.conditioning()
+    U, V = s.factors()
+    kg, kh, route_g, route_h = s.conditioning(routes=True)
     s.close()
-    U64 = U.astype(np.float64)
-    kap = float(np.linalg.cond(U64.T @ U64 + case["rho"] * np.eye(8), 1))
-    print(f"\nkappa_1 {kap:.3g}, estimate {kg:.3g}, V side {kh:.3g}")
+    U64, V64 = U.astype(np.float64), V.astype(np.float64)
+    kap = float(np.linalg.cond(U64.T @ U64 + case["rho"] * np.eye(r), 1))
+    kap_h = float(np.linalg.cond(V64.T @ V64 + case["rho"] * np.eye(r), 1))
+    print(f"\nr {r}: kappa_1 {kap:.3g}, estimate {kg:.3g} (route {route_g}); V side "
+          f"{kap_h:.3g}, estimate {kh:.3g} (route {route_h})")
     assert kap / 4 <= kg <= 4 * kap
-    assert 1.0 <= kg < 100.0 and 1.0 <= kh < 100.0
+    assert kap_h / 4 <= kh <= 4 * kap_h
+    assert kg < 100.0 and route_g == 0
+    assert route_h == (0 if kh < 100.0 else 1)
