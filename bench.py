@@ -173,9 +173,9 @@ NCU_TRAFFIC = {
     # (229.04 MB read + 4.36 MB written) and on the idle SMs k_tc2 pass A (45.49 MB),
     # k_tc2_vreduce (5.86 MB) and pass B (45.31 MB) on the last 2688
     "fused_step": {"m": 4096, "r": 32, "n": 16384, "bytes": 330.06e6},
-    # k_tc2<64, 5, false> / k_tc2<64, 7, true>, m=16384, n=16384, r=64
-    "pass_a": {"m": 16384, "r": 64, "n": 16384, "bytes": 1334.76e6},
-    "pass_b": {"m": 16384, "r": 64, "n": 16384, "bytes": 1086.43e6},
+    # k_tc2<64, 4, false, pair> / k_tc2<64, 7, true>, m=16384, n=16384, r=64
+    "pass_a": {"m": 16384, "r": 64, "n": 16384, "bytes": 1211.20e6},
+    "pass_b": {"m": 16384, "r": 64, "n": 16384, "bytes": 1087.02e6},
 }
 
 
@@ -321,7 +321,10 @@ def kernel_bytes(m, n, r, path_id, sms):
         Rp = 16 if r <= 16 else 32 if r <= 32 else 64
         nslabs = (m + 255) // 256
         G = max(1, min(sms // nslabs, (n + 63) // 64))
-        kb["pass_a"] = 4.0 * m * n + 4.0 * n * Rp + 4.0 * nslabs * n * Rp + 8.0 * m * Rp
+        # pass A at R = 64 with an even slab count runs in two-CTA clusters that
+        # add their column sums before writing them: one partial per slab pair
+        parts = nslabs // 2 if Rp == 64 and nslabs % 2 == 0 else nslabs
+        kb["pass_a"] = 4.0 * m * n + 4.0 * n * Rp + 4.0 * parts * n * Rp + 8.0 * m * Rp
         kb["pass_b"] = 4.0 * m * n + 8.0 * n * Rp + 4.0 * G * m * Rp + 4.0 * m * Rp
     return kb
 

@@ -260,7 +260,8 @@ cudaError_t enqueue_fused_iteration(dcf_handle h, int cur, cudaStream_t s, cudaE
     ta.err = h->kerr;
     if ((e = cudaMemsetAsync(h->vmax_tail + nxt, 0, sizeof(unsigned int), t)) != cudaSuccess ||
         (e = launch_tc2(h->R, 0, h->tmap_tail, ta, t)) != cudaSuccess ||
-        (e = launch_tc2_vreduce(h->R, h->ypart_tail, h->nslabs, h->W_vz + n_head * h->R,
+        (e = launch_tc2_vreduce(h->R, h->ypart_tail, tc2_parts(h->R, h->nslabs),
+                                h->W_vz + n_head * h->R,
                                 h->n_tail, h->V[nxt] + n_head * h->R, h->vmax_tail + nxt, h->st,
                                 h->num_sms, t, h->vmax + nxt)) != cudaSuccess ||
         (e = launch_tc2(h->R, 1, h->tmap_tail, ta, t)) != cudaSuccess ||
@@ -318,7 +319,7 @@ cudaError_t enqueue_tc2_iteration(dcf_handle h, int cur, cudaStream_t s, cudaEve
   ta.err = h->kerr;
   if ((e = launch_tc2(h->R, 0, h->tmap, ta, s)) != cudaSuccess || (e = mark()) != cudaSuccess)
     return e;
-  if ((e = launch_tc2_vreduce(h->R, h->ypart, h->nslabs, h->W_vz, h->n, h->V[nxt],
+  if ((e = launch_tc2_vreduce(h->R, h->ypart, tc2_parts(h->R, h->nslabs), h->W_vz, h->n, h->V[nxt],
                               h->vmax + nxt, h->st, h->num_sms, s)) != cudaSuccess ||
       (e = mark()) != cudaSuccess)
     return e;

@@ -318,6 +318,9 @@ struct Tc2Args {
 };
 cudaError_t tc2_prepare(int R);
 cudaError_t launch_tc2(int R, int pass_b, const void* tmap, const Tc2Args& a, cudaStream_t s);
+// Pass A's column-sum partials per column: one per slab, or one per slab pair
+// where pass A runs in two-CTA clusters (R = 64, even slab count).
+int tc2_parts(int R, int nslabs);
 // V' = V_old Z + sum over slabs; max |V'| into vmax and, when non-NULL, vmax_all.
 cudaError_t launch_tc2_vreduce(int R, const float* ypart, int nslabs, const float* VZ, int64_t n,
                                float* Vnew, unsigned int* vmax, const DevState* st,

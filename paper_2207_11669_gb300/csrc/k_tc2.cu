@@ -69,7 +69,10 @@ __device__ __forceinline__ void ttwo_sum(float& hi, float& lo, float x) {
 }
 
 // Shared-memory layout (bytes) of pass A (kB = false) or pass B (kB = true).
-template <int R, int NST, bool kB>
+// kPair (pass A): the CTAs of a two-CTA cluster (two slabs) add their column
+// sums before writing them: RECV holds the partner's half of a strip, two
+// slots.
+template <int R, int NST, bool kB, bool kPair = false>
 struct TL {
   static constexpr int RING = 0;                                   // NST M sub-tiles
   static constexpr int WIMG = RING + NST * kTSubBytes;             // pass A: 2R x 256 fp16
@@ -80,11 +83,13 @@ struct TL {
   static constexpr int VIMG = CBUF + kTNC * CBYTES;
   static constexpr int PBYTES = 2 * R * kTW * 2;                   // one V' image (2 terms)
   static constexpr int PIMG = VIMG + VBYTES;                       // pass B: 2 V' images
-  static constexpr int BAR = PIMG + (kB ? 2 * PBYTES : 0);
+  static constexpr int RSLOT = kTW / 2 * R * 4;                    // half a strip's sums
+  static constexpr int RECV = PIMG + (kB ? 2 * PBYTES : 0);        // kPair: 2 slots
+  static constexpr int BAR = RECV + (kPair ? 2 * RSLOT : 0);
   // full/empty NST each; vfull, vempty; d1full, d1empty 2 each; cfull, cempty
   // kTNC each; d2full, d2empty (pass A) or pvfull, pvempty (pass B) 2 each;
-  // img, last
-  static constexpr int NBAR = 2 * NST + 2 + 4 + 2 * kTNC + 4 + 2;
+  // img, last; kPair: yfull, yfree 2 each
+  static constexpr int NBAR = 2 * NST + 2 + 4 + 2 * kTNC + 4 + 2 + (kPair ? 4 : 0);
   static constexpr int TSLOT = BAR + NBAR * 8;
   static constexpr int RED = TSLOT + 16;                           // 8 doubles
   static constexpr int ABRT = RED + 8 * 8;                         // abort flag (int)
@@ -107,10 +112,11 @@ struct TL {
 //   warps 4-11   S-step epilogue: C/lambda into a C tile (and the Huber sum in A)
 //   warps 12-15  pass A: column sums out of tensor memory into the slab's partials;
 //                pass B: fp16 image of V' (B operand of GEMM3), double-buffered
-template <int R, int NST, bool kB>
+template <int R, int NST, bool kB, bool kPair = false>
 __global__ void __launch_bounds__(kTThreads, 1)
     k_tc2(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ Tc2Args a) {
-  using L = TL<R, NST, kB>;
+  static_assert(!(kPair && kB), "pairs reduce pass A's column sums");
+  using L = TL<R, NST, kB, kPair>;
   if (a.st->stop) return;   // uniform over the grid
   extern __shared__ __align__(1024) uint8_t smem[];
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -123,7 +129,8 @@ __global__ void __launch_bounds__(kTThreads, 1)
   const int b_full = 0, b_empty = NST, b_vfull = 2 * NST, b_vempty = b_vfull + 1,
             b_d1full = b_vempty + 1, b_d1empty = b_d1full + 2, b_cfull = b_d1empty + 2,
             b_cempty = b_cfull + kTNC, b_xfull = b_cempty + kTNC, b_xempty = b_xfull + 2,
-            b_img = b_xempty + 2, b_last = b_img + 1;
+            b_img = b_xempty + 2, b_last = b_img + 1, b_yfull = b_last + 1,
+            b_yfree = b_yfull + 2;
   double* red = reinterpret_cast<double*>(smem + L::RED);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(smem + L::ABRT);
   int err = 0;
@@ -172,6 +179,12 @@ __global__ void __launch_bounds__(kTThreads, 1)
     }
     tc::mbar_init(B(b_img), 1);
     tc::mbar_init(B(b_last), 1);
+    if (kPair) {
+      for (int p = 0; p < 2; ++p) {
+        tc::mbar_init(B(b_yfull + p), 1);   // armed with the slot's bytes by one owner warp
+        tc::mbar_init(B(b_yfree + p), 2);   // the partner's two owner warps, remotely
+      }
+    }
     *abort_flag = 0;
     tc::fence_mbar_init();
     tc::prefetch_tmap(&tmap);
@@ -179,6 +192,7 @@ __global__ void __launch_bounds__(kTThreads, 1)
   tc::fence_before_sync();
   __syncthreads();
   tc::fence_after_sync();
+  if (kPair) tc::cluster_sync();   // the partner's barriers are initialised
   const uint32_t tbase = *reinterpret_cast<volatile uint32_t*>(smem + L::TSLOT);
   auto d1 = [&](int p) { return tbase + (uint32_t)(L::T_D1 + 128 * p); };
   const uint32_t tu = tbase + L::T_U, tx = tbase + L::T_X;
@@ -467,7 +481,15 @@ __global__ void __launch_bounds__(kTThreads, 1)
     // D2 (M = 64: strip column j in lane 16 (j / 16) + j % 16 of quarter j / 16)
     const int xw = warp & 3;
     const float y_scale = a.lam / s_w;
-    float* ybase = a.ypart + (int64_t)slab * a.n * R;
+    // kPair: the cluster's two CTAs (slabs 2k, 2k + 1) share one partial per
+    // column: cluster rank 0 owns strip columns 0..31 (writer warps 0, 1), rank
+    // 1 columns 32..63 (warps 2, 3); a warp whose columns the partner owns
+    // sends its sums into the partner's receive slot (st.async, counted on the
+    // partner's yfull), an owner warp adds what it receives and writes.
+    const uint32_t crank = kPair ? tc::cluster_rank() : 0u, partner = crank ^ 1u;
+    const bool owner = !kPair || (xw >> 1) == (int)crank;
+    const int jl = (xw & 1) * 16 + lane;          // column within the owner's half
+    float* ybase = a.ypart + (int64_t)(kPair ? slab >> 1 : slab) * a.n * R;
     for (int ls = 0; ls < S; ++ls) {
       const int q2 = ls & 1;
       if (!wait_w(B(b_xfull + q2), (uint32_t)((ls >> 1) & 1))) break;
@@ -482,13 +504,47 @@ __global__ void __launch_bounds__(kTThreads, 1)
       __syncwarp();
       if (lane == 0) tc::mbar_arrive(B(b_xempty + q2));
       const int64_t col = strip_col0(ls) + xw * 16 + lane;
+      if (kPair && !owner) {
+        // the partner has consumed strip ls - 2 from this slot
+        if (ls >= 2 && !wait_w(B(b_yfree + q2), (uint32_t)(((ls >> 1) - 1) & 1))) break;
+        if (__any_sync(0xffffffffu, *abort_flag != 0)) break;   // one answer per warp
+        if (lane < 16) {   // every column, zeros past n: the slot's byte count is fixed
+          const uint32_t dst = tc::map_cluster(
+              sbase + (uint32_t)(L::RECV + q2 * L::RSLOT + jl * R * 4), partner);
+          const uint32_t bar = tc::map_cluster(B(b_yfull + q2), partner);
+#pragma unroll
+          for (int k = 0; k < R; k += 4) {
+            uint4 v;
+            v.x = __float_as_uint(yv[k] * y_scale);
+            v.y = __float_as_uint(yv[k + 1] * y_scale);
+            v.z = __float_as_uint(yv[k + 2] * y_scale);
+            v.w = __float_as_uint(yv[k + 3] * y_scale);
+            tc::st_async_u32x4(dst + (uint32_t)k * 4, v, bar);
+          }
+        }
+        continue;
+      }
+      if (kPair) {
+        if (lane == 0 && (xw & 1) == 0) tc::mbar_arrive_expect_tx(B(b_yfull + q2), L::RSLOT);
+        if (!wait_w(B(b_yfull + q2), (uint32_t)((ls >> 1) & 1))) break;
+      }
       if (lane < 16 && col < a.n) {
         float* dst = ybase + col * R;
+        const float* rcv = reinterpret_cast<const float*>(smem + L::RECV + q2 * L::RSLOT) + jl * R;
 #pragma unroll
-        for (int k = 0; k < R; k += 4)
-          *reinterpret_cast<float4*>(dst + k) =
-              make_float4(yv[k] * y_scale, yv[k + 1] * y_scale, yv[k + 2] * y_scale,
-                          yv[k + 3] * y_scale);
+        for (int k = 0; k < R; k += 4) {
+          float4 y = make_float4(yv[k] * y_scale, yv[k + 1] * y_scale, yv[k + 2] * y_scale,
+                                 yv[k + 3] * y_scale);
+          if (kPair) {
+            const float4 o = *reinterpret_cast<const float4*>(rcv + k);
+            y.x += o.x; y.y += o.y; y.z += o.z; y.w += o.w;
+          }
+          *reinterpret_cast<float4*>(dst + k) = y;
+        }
+      }
+      if (kPair) {
+        __syncwarp();
+        if (lane == 0) tc::mbar_arrive_cluster_relaxed(B(b_yfree + q2), partner);
       }
     }
   } else {
@@ -578,6 +634,8 @@ __global__ void __launch_bounds__(kTThreads, 1)
     for (int w = 0; w < 8; ++w) t += red[w];
     a.part_h[blockIdx.x] = t;
   }
+  // no CTA of a pair leaves while its partner may still address its shared memory
+  if (kPair) tc::cluster_sync();
   // (if an MMA is still running after all that, the tensor memory stays allocated)
   if (warp == 1 && mma_drained) tc::tmem_dealloc(tbase, 512);
 }
@@ -619,17 +677,19 @@ __global__ void __launch_bounds__(256) k_tc2_vreduce(const float* __restrict__ y
 // ---------------------------------------------------------------------------
 namespace {
 
-// ring depth per (R, pass): as deep as shared memory allows
-template <int R, bool kB>
+// ring depth per (R, pass): as deep as shared memory allows (one slot fewer
+// for the receive slots of the paired pass A)
+template <int R, bool kB, bool kPair = false>
 constexpr int tc2_nst() {
-  return R == 64 ? (kB ? 7 : 5) : R == 32 ? (kB ? 8 : 7) : (kB ? 9 : 8);
+  return R == 64 ? (kB ? 7 : (kPair ? 4 : 5)) : R == 32 ? (kB ? 8 : 7) : (kB ? 9 : 8);
 }
 
-template <int R, bool kB>
+template <int R, bool kB, bool kPair = false>
 cudaError_t tc2_attr() {
-  constexpr int NST = tc2_nst<R, kB>();
-  return cudaFuncSetAttribute(k_tc2<R, NST, kB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)TL<R, NST, kB>::TOTAL);
+  constexpr int NST = tc2_nst<R, kB, kPair>();
+  return cudaFuncSetAttribute(k_tc2<R, NST, kB, kPair>,
+                              cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)TL<R, NST, kB, kPair>::TOTAL);
 }
 
 template <int R, bool kB>
@@ -640,7 +700,32 @@ cudaError_t tc2_launch(const void* tmap, const Tc2Args& a, cudaStream_t s) {
   return cudaGetLastError();
 }
 
+// Pass A in two-CTA clusters (slabs 2k, 2k + 1 of a strip group).
+template <int R>
+cudaError_t tc2_launch_pair(const void* tmap, const Tc2Args& a, cudaStream_t s) {
+  constexpr int NST = tc2_nst<R, false, true>();
+  cudaLaunchConfig_t cfg{};
+  cfg.gridDim = dim3((unsigned)(a.nslabs * a.G), 1, 1);
+  cfg.blockDim = dim3(kTThreads, 1, 1);
+  cfg.dynamicSmemBytes = TL<R, NST, false, true>::TOTAL;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = 2;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  const CUtensorMap* tm = reinterpret_cast<const CUtensorMap*>(tmap);
+  return cudaLaunchKernelEx(&cfg, k_tc2<R, NST, false, true>, *tm, a);
+}
+
 }  // namespace
+
+// Whether pass A reduces its column sums in slab pairs (R = 64, an even
+// number of slabs), and so how many partials per column it leaves.
+bool tc2_paired(int R, int nslabs) { return R == 64 && nslabs % 2 == 0; }
+int tc2_parts(int R, int nslabs) { return tc2_paired(R, nslabs) ? nslabs / 2 : nslabs; }
 
 cudaError_t tc2_prepare(int R) {
   cudaError_t e;
@@ -653,6 +738,7 @@ cudaError_t tc2_prepare(int R) {
       return tc2_attr<32, true>();
     default:
       if ((e = tc2_attr<64, false>()) != cudaSuccess) return e;
+      if ((e = tc2_attr<64, false, true>()) != cudaSuccess) return e;
       return tc2_attr<64, true>();
   }
 }
@@ -662,7 +748,10 @@ cudaError_t launch_tc2(int R, int pass_b, const void* tmap, const Tc2Args& a, cu
   switch (R) {
     case 16: return pass_b ? tc2_launch<16, true>(tmap, a, s) : tc2_launch<16, false>(tmap, a, s);
     case 32: return pass_b ? tc2_launch<32, true>(tmap, a, s) : tc2_launch<32, false>(tmap, a, s);
-    default: return pass_b ? tc2_launch<64, true>(tmap, a, s) : tc2_launch<64, false>(tmap, a, s);
+    default:
+      if (pass_b) return tc2_launch<64, true>(tmap, a, s);
+      return tc2_paired(64, a.nslabs) ? tc2_launch_pair<64>(tmap, a, s)
+                                      : tc2_launch<64, false>(tmap, a, s);
   }
 }
 
