@@ -117,7 +117,8 @@ dcf_status dcf_create(const dcf_params* p, dcf_handle* out);
 /* (No counterpart in the paper.)  Kernels one iteration launches on the handle's
  * path (graph nodes that are kernels): 7 general, 6 fused (9 when the fused
  * kernel's idle SMs run a share of the columns on the two-pass kernels), 8
- * two-pass tensor core, 1 whole solve (per call); -1 with local_steps > 1. */
+ * two-pass tensor core (9 at r > 32), 1 whole solve (per call); -1 with
+ * local_steps > 1. */
 int dcf_kernels_per_iteration(dcf_handle h);
 
 /* (No counterpart in the paper.)  Which kernels run an iteration: 1 general two-pass path, 2 fused

@@ -829,7 +829,7 @@ extern "C" int dcf_kernels_per_iteration(dcf_handle h) {
   if (!h->clients.empty()) return -1;   // rounds of local steps: not one fixed graph
   switch (h->path) {
     case 2: return h->n_tail > 0 ? 9 : 6;   // + the tail's pass A, V' reduction, pass B
-    case 3: return 8;
+    case 3: return h->R == 64 ? 9 : 8;     // V_old Z in its own launch at R = 64
     case 4: return 1;                      // every iteration of a call in one launch
     default: return 7;
   }

@@ -39,6 +39,8 @@
 // and the TMA loads still in flight are drained with bounded waits; if even
 // that fails the tensor memory is left allocated.  The kernel records
 // DCF_ETIMEOUT and every CTA still reaches the final cluster barrier.
+#include <algorithm>
+
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <cuda_fp16.h>
@@ -880,19 +882,16 @@ __global__ void __launch_bounds__(256) k_bfused_prep(const BInst* __restrict__ i
   }
 }
 
-// out = in Z for n rows of R (V_old Z, added to the cluster's column sums):
-// block blk of 256 (row, column group of 8) entries (block-wide).  The row's
-// R inputs are fetched with vector loads before any arithmetic, so that they
-// are in flight together.
-// kFromGinv: zsrc, zlo are G^{-1} = zsrc + zlo (double-float) and
-// Z = I - rho G^{-1} is formed here (as the preparation forms zmat);
-// otherwise zsrc is Z itself.
-template <int R, bool kFromGinv = false>
-__device__ __forceinline__ void rowmat_block(const float* __restrict__ in,
-                                             const float* __restrict__ zsrc,
-                                             const float* __restrict__ zlo, float rho, int64_t n,
-                                             float* __restrict__ out, int64_t blk) {
-  __shared__ __align__(16) float Z[R * R];
+// out = in Z for n rows of R (V_old Z, added to the cluster's column sums),
+// in entries (row, column group of 8), 256 per chunk.  The row's R inputs are
+// fetched with vector loads before any arithmetic, so that they are in
+// flight together.
+// rowmat_fill_z: Z into shared memory; kFromGinv: zsrc, zlo are G^{-1} =
+// zsrc + zlo (double-float) and Z = I - rho G^{-1} is formed here (as the
+// preparation forms zmat); otherwise zsrc is Z itself.  Block-wide.
+template <int R, bool kFromGinv>
+__device__ __forceinline__ void rowmat_fill_z(float* Z, const float* __restrict__ zsrc,
+                                              const float* __restrict__ zlo, float rho) {
   if constexpr (kFromGinv) {
     for (int i = threadIdx.x; i < R * R; i += 256)
       Z[i] = fmaf(-rho, zlo[i], fmaf(-rho, zsrc[i], (i / R) == (i % R) ? 1.f : 0.f));
@@ -900,8 +899,12 @@ __device__ __forceinline__ void rowmat_block(const float* __restrict__ in,
     for (int i = threadIdx.x; i < R * R / 4; i += 256)
       reinterpret_cast<float4*>(Z)[i] = reinterpret_cast<const float4*>(zsrc)[i];
   }
-  __syncthreads();
-  const int64_t idx = blk * 256 + threadIdx.x;   // (row, column group of 8)
+}
+
+// Entry idx of out = in Z (nothing past row n).
+template <int R>
+__device__ __forceinline__ void rowmat_entry(const float* __restrict__ in, const float* Z,
+                                             int64_t n, float* __restrict__ out, int64_t idx) {
   const int64_t row = idx / (R / 8);
   const int cg = (int)(idx % (R / 8));
   if (row >= n) return;
@@ -931,6 +934,34 @@ __device__ __forceinline__ void rowmat_block(const float* __restrict__ in,
   float4* dst = reinterpret_cast<float4*>(out + row * R + cg * 8);
   dst[0] = make_float4(acc[0], acc[1], acc[2], acc[3]);
   dst[1] = make_float4(acc[4], acc[5], acc[6], acc[7]);
+}
+
+// One chunk blk of 256 entries (block-wide).
+template <int R, bool kFromGinv = false>
+__device__ __forceinline__ void rowmat_block(const float* __restrict__ in,
+                                             const float* __restrict__ zsrc,
+                                             const float* __restrict__ zlo, float rho, int64_t n,
+                                             float* __restrict__ out, int64_t blk) {
+  __shared__ __align__(16) float Z[R * R];
+  rowmat_fill_z<R, kFromGinv>(Z, zsrc, zlo, rho);
+  __syncthreads();
+  rowmat_entry<R>(in, Z, n, out, blk * 256 + threadIdx.x);
+}
+
+// V_old Z in its own launch with Z formed once per CTA and the chunks walked
+// with a stride: at R = 64, where the preparation's slab part takes every
+// register, the combined launch would run its 8192 row blocks one CTA per SM.
+template <int R>
+__global__ void __launch_bounds__(256) k_rowmat(const DevState* st, const Smalls* sm, float rho,
+                                                const float* __restrict__ Vold, int64_t n,
+                                                float* __restrict__ VZ) {
+  if (st->stop) return;
+  __shared__ __align__(16) float Z[R * R];
+  rowmat_fill_z<R, true>(Z, sm->ginv32, sm->ginv32_lo, rho);
+  __syncthreads();
+  const int64_t nchunks = (n * (R / 8) + 255) / 256;
+  for (int64_t blk = blockIdx.x; blk < nchunks; blk += gridDim.x)
+    rowmat_entry<R>(Vold, Z, n, VZ, blk * 256 + threadIdx.x);
 }
 
 // The per-iteration preparation in one launch: blocks [0, nslabs) prepare the
@@ -1079,6 +1110,19 @@ cudaError_t launch_fused_prep(int R, const float* U, const Smalls* sm, const Dev
                               unsigned int* vmax_reset, uint8_t* img, float* scales, float* zmat,
                               const float* Vold, int64_t n, float* VZ, cudaStream_t s) {
   const int64_t zblocks = (n * (R / 8) + 255) / 256;    // V_old Z blocks after the slabs
+  if (R == 64) {
+    // the slabs alone, then V_old Z in its own persistent launch
+    k_fused_prep<64><<<(unsigned)nslabs, 256, prep_smem<64>(), s>>>(
+        U, sm, st, m, nslabs, rho, vmax_in, vmax_reset, img, scales, zmat, Vold, n, VZ);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int64_t g = std::max<int64_t>(1, std::min<int64_t>(zblocks, 4LL * sms));
+    k_rowmat<64><<<(unsigned)g, 256, 0, s>>>(st, sm, rho, Vold, n, VZ);
+    return cudaGetLastError();
+  }
   const unsigned grid = (unsigned)(nslabs + zblocks);
   if (R == 16)
     k_fused_prep<16><<<grid, 256, prep_smem<16>(), s>>>(U, sm, st, m, nslabs, rho, vmax_in,
@@ -1086,10 +1130,6 @@ cudaError_t launch_fused_prep(int R, const float* U, const Smalls* sm, const Dev
                                                         VZ);
   else if (R == 32)
     k_fused_prep<32><<<grid, 256, prep_smem<32>(), s>>>(U, sm, st, m, nslabs, rho, vmax_in,
-                                                        vmax_reset, img, scales, zmat, Vold, n,
-                                                        VZ);
-  else
-    k_fused_prep<64><<<grid, 256, prep_smem<64>(), s>>>(U, sm, st, m, nslabs, rho, vmax_in,
                                                         vmax_reset, img, scales, zmat, Vold, n,
                                                         VZ);
   return cudaGetLastError();
