@@ -26,6 +26,22 @@ __host__ __device__ __forceinline__ int64_t dmin64(int64_t a, int64_t b) { retur
 // ---------------------------------------------------------------------------
 // compensated accumulation (Knuth's TwoSum; exact error term of s + x)
 // ---------------------------------------------------------------------------
+// 16-byte asynchronous global -> shared copy; src_bytes < 16 zero-fills the
+// rest (0: nothing is read).
+__device__ __forceinline__ void cp_async16(float* sdst, const float* gsrc, int src_bytes) {
+  const uint32_t d = (uint32_t)__cvta_generic_to_shared(sdst);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(d), "l"(gsrc),
+               "r"(src_bytes)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() {
+  asm volatile("cp.async.commit_group;" ::: "memory");
+}
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
 __device__ __forceinline__ void two_sum_add(float& hi, float& lo, float x) {
   float t = hi + x;
   float bp = t - hi;
@@ -124,9 +140,10 @@ struct GvvCfg {
   static constexpr int TB = R >= 32 ? 4 : 1;
   static constexpr int NT = R / TB;                 // tiles per dimension
   static constexpr int GROUPS = 256 / (NT * NT);    // row groups
-  static constexpr int CH = 64;                     // rows per chunk
+  static constexpr int CH = R >= 64 ? 32 : 64;      // rows per chunk
   static constexpr int NV = (CH * R / 4 + 255) / 256;   // float4 per thread per chunk and array
-  static constexpr size_t data_bytes = 2 * (size_t)CH * R * 4;
+  static constexpr int STAGES = 3;                  // chunks in flight (cp.async ring)
+  static constexpr size_t data_bytes = (size_t)STAGES * 2 * CH * R * 4;
   // the row groups' partial tiles (3 outputs x hi, lo) are combined one tile
   // row at a time
   static constexpr size_t cmb_bytes = GROUPS > 1 ? (size_t)GROUPS * NT * NT * TB * 6 * 4 : 0;
@@ -142,8 +159,8 @@ __device__ __forceinline__ void gram_vv_block(const float* __restrict__ Vo,
                                               float2* __restrict__ out_y,
                                               float2* __restrict__ out_d, float* gsh, bool df) {
   using C = GvvCfg<R>;
-  constexpr int TB = C::TB, NT = C::NT, G = C::GROUPS, CH = C::CH, NV = C::NV;
-  float* So = gsh;              // [CH][R]  V_old rows
+  constexpr int TB = C::TB, NT = C::NT, G = C::GROUPS, CH = C::CH, NV = C::NV, ST = C::STAGES;
+  float* So = gsh;              // [CH][R]  V_old rows of the current chunk's stage
   float* Sn = gsh + CH * R;     // [CH][R]  V' rows
   const int tid = threadIdx.x;
   const int tile = tid % (NT * NT), grp = tid / (NT * NT);
@@ -155,32 +172,36 @@ __device__ __forceinline__ void gram_vv_block(const float* __restrict__ Vo,
     for (int j = 0; j < TB; ++j) {
       qh[i][j] = ql[i][j] = yh[i][j] = yl[i][j] = dh[i][j] = dl[i][j] = 0.f;
     }
-  float4 po[NV], pn[NV];
-  auto fetch = [&](int64_t c) {
-    const int rows = (int)dmin64((int64_t)CH, a1 - c);
+  // chunk c into ring stage st: asynchronous copies (no registers held), rows
+  // past a1 zero-filled; every thread commits one group per chunk (empty past
+  // the end) so that the group counts stay uniform
+  auto issue = [&](int64_t c, int st) {
+    if (c < a1) {
+      const int rows = (int)dmin64((int64_t)CH, a1 - c);
+      float* so = gsh + (size_t)st * 2 * CH * R;
+      float* sn = so + CH * R;
 #pragma unroll
-    for (int v = 0; v < NV; ++v) {
-      const int i = tid + v * 256;
-      const bool ok = i < CH * R / 4 && (4 * i) / R < rows;
-      if (kDelta)
-        po[v] = ok ? reinterpret_cast<const float4*>(Vo + c * R)[i]
-                   : make_float4(0.f, 0.f, 0.f, 0.f);
-      pn[v] = ok ? reinterpret_cast<const float4*>(Vn + c * R)[i] : make_float4(0.f, 0.f, 0.f, 0.f);
-    }
-  };
-  if (a0 < a1) fetch(a0);
-  for (int64_t c = a0; c < a1; c += CH) {
-    __syncthreads();   // every read of the previous chunk is done
-#pragma unroll
-    for (int v = 0; v < NV; ++v) {
-      const int i = tid + v * 256;
-      if (i < CH * R / 4) {
-        if (kDelta) reinterpret_cast<float4*>(So)[i] = po[v];
-        reinterpret_cast<float4*>(Sn)[i] = pn[v];
+      for (int v = 0; v < NV; ++v) {
+        const int i = tid + v * 256;
+        if (i < CH * R / 4) {
+          const bool in = (4 * i) / R < rows;
+          const int64_t off = in ? c * R + 4 * i : c * R;   // a valid address either way
+          if (kDelta) cp_async16(so + 4 * i, Vo + off, in ? 16 : 0);
+          cp_async16(sn + 4 * i, Vn + off, in ? 16 : 0);
+        }
       }
     }
-    __syncthreads();
-    if (c + CH < a1) fetch(c + CH);
+    cp_async_commit();
+  };
+  const int64_t nch = a0 < a1 ? (a1 - a0 + CH - 1) / CH : 0;
+  for (int t = 0; t < ST - 1; ++t) issue(a0 + (int64_t)t * CH, t);
+  for (int64_t t = 0; t < nch; ++t) {
+    const int64_t c = a0 + t * CH;
+    issue(c + (int64_t)(ST - 1) * CH, (int)((t + ST - 1) % ST));
+    cp_async_wait<ST - 1>();   // this thread's copies of chunk t have landed
+    __syncthreads();           // and every thread's
+    So = gsh + (size_t)(t % ST) * 2 * CH * R;
+    Sn = So + CH * R;
     float da[TB][TB];
 #pragma unroll
     for (int i = 0; i < TB; ++i)
@@ -243,18 +264,24 @@ __device__ __forceinline__ void gram_vv_block(const float* __restrict__ Vo,
       for (int i = 0; i < TB; ++i)
 #pragma unroll
         for (int j = 0; j < TB; ++j) qa[i][j] = ya[i][j] = 0.f;
+      // two rows per trip: the next row's shared loads overlap this row's FMAs
+#pragma unroll 2
       for (int rr = grp; rr < CH; rr += G) {
-        float nk[TB], nl[TB], ok[TB], ol[TB];
+        float nk[TB], nl[TB], ok[TB], ol[TB], dk[TB], dl[TB];
         load_row(rr, nk, nl, ok, ol);
+#pragma unroll
+        for (int i = 0; i < TB; ++i) {
+          dk[i] = nk[i] - ok[i];
+          dl[i] = nl[i] - ol[i];
+        }
 #pragma unroll
         for (int i = 0; i < TB; ++i)
 #pragma unroll
           for (int j = 0; j < TB; ++j) {
             qa[i][j] = fmaf(nk[i], nl[j], qa[i][j]);
             if (kDelta) {
-              const float dlj = nl[j] - ol[j];
-              ya[i][j] = fmaf(ok[i], dlj, ya[i][j]);
-              da[i][j] = fmaf(nk[i] - ok[i], dlj, da[i][j]);
+              ya[i][j] = fmaf(ok[i], dl[j], ya[i][j]);
+              da[i][j] = fmaf(dk[i], dl[j], da[i][j]);
             }
           }
       }
@@ -272,7 +299,9 @@ __device__ __forceinline__ void gram_vv_block(const float* __restrict__ Vo,
 #pragma unroll
         for (int j = 0; j < TB; ++j) two_sum_add(dh[i][j], dl[i][j], da[i][j]);
     }
+    __syncthreads();   // this stage is refilled by the next iteration's issue
   }
+  cp_async_wait<0>();   // only empty groups remain; the ring memory is reused below
   // combine the row groups through shared memory, one tile row at a time:
   // cmb[g][tile][j][6] = (hi, lo of Q, Y, D)
   if (G > 1) {
