@@ -2,15 +2,17 @@
 // tails and by the learned network.
 //
 // Cost model.  GB300 issues an FP64 warp instruction every 64 cycles per SM
-// sub-partition (about 2 FP64 FMA/clk/SM), and the factorisation is a chain
-// of R dependent steps, so it runs in double-float arithmetic on the FP32
-// pipes (about 48 bits), packs its trailing updates across all threads of
-// the CTA, uses the root-free L D L^T form and replaces divisions by Newton
-// steps from the FP32 estimate.  The triangular inverse (one warp per column)
-// and the final product run in FP32 from the rounded factors when the system
-// is well-conditioned and in double-float otherwise; the double-float inverse
-// is handed on as a pair of floats (hi, lo), so that its consumers can apply
-// it to about twice FP32 precision.
+// sub-partition (about 2 FP64 FMA/clk/SM), and a factorisation is a chain of
+// R dependent steps, so it runs in double-float arithmetic on the FP32 pipes
+// (about 48 bits), packs its trailing updates across all threads of the CTA,
+// uses the root-free L D L^T form and replaces divisions by Newton steps from
+// the FP32 estimate.  A well-conditioned system (by a 1-norm estimate) is
+// inverted in FP32: by Gauss-Jordan on one warp up to R = 32, from the
+// rounded double-float factors at R = 64; otherwise the triangular inverse
+// and the product run in double-float and the inverse is handed on as a pair
+// of floats (hi, lo), so that its consumers can apply it to about twice FP32
+// precision.  The tails run once per launch on one CTA, after larger kernels
+// have evicted the instruction cache, so their loops are kept rolled.
 #pragma once
 #include <cuda_runtime.h>
 
