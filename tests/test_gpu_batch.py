@@ -161,3 +161,44 @@ def test_more_problems_than_clusters():
         L = U.astype(np.float64) @ V.T.astype(np.float64)
         assert rel(L, U2 @ V2.T) <= 1e-4, (q, rel(L, U2 @ V2.T))
     b.close()
+
+
+def collinear_instance(m, n_i, r, eps, rho, seed):
+    """An instance whose U0 has two nearly collinear columns (the second within
+    eps of the first, relative), so that U0^T U0 + rho I is ill-conditioned."""
+    c = make_case(m, n_i, r, seed=seed, rho=rho, density=0.05, amp=5.0)
+    U0 = c["U0"].astype(np.float64)
+    g = np.random.default_rng(seed + 2)
+    U0[:, 1] = U0[:, 0] + eps * g.standard_normal(m) / np.sqrt(m)
+    c["U0"] = U0.astype(np.float32)
+    c["V0"] = O.init_v0(c["M"], c["U0"].astype(np.float64), rho).astype(np.float32)
+    G = c["U0"].astype(np.float64).T @ c["U0"].astype(np.float64) + rho * np.eye(r)
+    return c, float(np.linalg.cond(G, 1))
+
+
+def test_ill_conditioned_instances_take_the_double_float_route():
+    """Ill-conditioned instances next to a well-conditioned one in one batch:
+    the batched tails, Grams, rows and images switch to the compensated route
+    per instance (from the instance's own condition estimate) and every
+    instance still meets 1e-4 after one step."""
+    specs = [((300, [100, 76, 140], 8), 1e-3, 1e-6),     # tensor-core table mode, R = 8
+             ((257, [200, 99], 12), 1e-3, 1e-6),         # R = 16
+             ((520, [180, 190], 24), 1e-2, 1e-6),        # R = 32
+             ((4100, [150, 170], 6), 1e-3, 1e-6)]        # general passes
+    cs, kaps = [], []
+    for q, (shape, eps, rho) in enumerate(specs):
+        c, k = collinear_instance(*shape, eps, rho, seed=40 + q)
+        cs.append(c)
+        kaps.append(k)
+    cs.append(make_case(200, [50, 50, 50, 50], 5, seed=7, density=0.05, amp=5.0))
+    kaps.append(None)
+    b = batch_of(cs)
+    b.step(1)
+    for q, c in enumerate(cs):
+        U, V = b.factors(q)
+        U1, V1, _, _, _ = O.dcf_run(c["M"], c["n_i"], c["U0"], c["V0"], c["rho"], c["lam"], 1)
+        print(f"\ninstance {q}: kappa_1(U0^T U0 + rho I) {kaps[q] if kaps[q] else 0:.2e}: "
+              f"rel err U {rel(U, U1):.2e}, V {rel(V, V1):.2e}")
+        assert rel(U, U1) <= 1e-4, (q, rel(U, U1))
+        assert rel(V, V1) <= 1e-4, (q, rel(V, V1))
+    b.close()
