@@ -309,6 +309,20 @@ def device_instance(wl, seed, device):
     return Mt, A.cpu().numpy(), B.cpu().numpy(), n_i
 
 
+def tc2_strip_groups(nslabs, nstrips, sms):
+    """The library's strip groups per slab on the two-pass path: the smallest G
+    whose wave cost ceil(nslabs G / sms) / G is within 6 % of the best."""
+    gmax = max(1, min(nstrips, max(32, sms // nslabs)))
+
+    def cost(g):
+        return -(-nslabs * g // sms) / g
+    best = min(cost(g) for g in range(1, gmax + 1))
+    g = 1
+    while cost(g) > 1.06 * best:
+        g += 1
+    return g
+
+
 def kernel_bytes(m, n, r, path_id, sms):
     """Algorithmic bytes of one launch of each streaming kernel: M once, V read
     and written, per-row factors once (fused: U/W images; general: U, W or U,
@@ -320,7 +334,7 @@ def kernel_bytes(m, n, r, path_id, sms):
     if path_id == 3:
         Rp = 16 if r <= 16 else 32 if r <= 32 else 64
         nslabs = (m + 255) // 256
-        G = max(1, min(sms // nslabs, (n + 63) // 64))
+        G = tc2_strip_groups(nslabs, (n + 63) // 64, sms)
         # pass A at R = 64 with an even slab count runs in two-CTA clusters that
         # add their column sums before writing them: one partial per slab pair
         parts = nslabs // 2 if Rp == 64 and nslabs % 2 == 0 else nslabs

@@ -678,9 +678,24 @@ extern "C" dcf_status dcf_create(const dcf_params* p, dcf_handle* out) {
       h->R = Rt;
       h->nslabs = (int)((h->m + 255) / 256);
       const int64_t nstrips64 = (h->n + 63) / 64;
-      // one CTA per SM (the kernels hold 200+ KB of shared memory): slabs x strip
-      // groups at most one wave, every CTA with at least one strip
-      h->G = (int)std::max<int64_t>(1, std::min<int64_t>(h->num_sms / h->nslabs, nstrips64));
+      // one CTA per SM (the kernels hold 200+ KB of shared memory).  G strip
+      // groups per slab make nslabs x G equal CTAs in ceil(nslabs G / SMs) waves,
+      // so a pass takes time in proportion to ceil(nslabs G / SMs) / G: the
+      // smallest G within 6 % of the best (64 slabs on 152 SMs: G = 7, three
+      // waves on every SM, against one wave of G = 2 on 128 SMs), every CTA
+      // with at least one strip
+      {
+        const int64_t gmax = std::max<int64_t>(
+            1, std::min<int64_t>(nstrips64, std::max<int64_t>(32, h->num_sms / h->nslabs)));
+        auto cost = [&](int64_t g) {
+          return (double)((h->nslabs * g + h->num_sms - 1) / h->num_sms) / (double)g;
+        };
+        double best = cost(1);
+        for (int64_t g = 2; g <= gmax; ++g) best = std::min(best, cost(g));
+        int64_t g = 1;
+        while (cost(g) > 1.06 * best) ++g;
+        h->G = (int)g;
+      }
     }
   }
   // launch geometry

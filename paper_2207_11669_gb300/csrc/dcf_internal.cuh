@@ -212,6 +212,24 @@ cudaError_t launch_reduce_init(const IterArgs& a, int which, int copy, const flo
                                int nparts, double* out, unsigned int* counter, cudaStream_t s);
 cudaError_t launch_reduce_plain(const float2* part, int nparts, int count, double* out,
                                 cudaStream_t s);
+// Up to kMaxGramJobs Grams X^T Y in two launches: the compensated partials of
+// every job (blockIdx.y = job), then their FP64 sums (the same partials and
+// order of summation as launch_gram followed by launch_reduce_plain).
+struct GramJob {
+  const float* X;
+  const float* Y;
+  int ldx, cx, ldy, cy;
+  int64_t N;       // rows
+  int nparts;      // CTAs, one partial each
+  float2* part;    // [nparts][cx * cy] scratch
+  double* out;     // cx * cy sums, row-major (k, l)
+};
+constexpr int kMaxGramJobs = 4;
+struct GramJobs {
+  GramJob j[kMaxGramJobs];
+  int n;
+};
+cudaError_t launch_gram_jobs(const GramJobs& g, cudaStream_t s);
 cudaError_t launch_pass1(const IterArgs& a, int grid, int mode_init, int out_copy,
                          cudaStream_t s);
 cudaError_t launch_pass2(const IterArgs& a, cudaStream_t s);

@@ -90,7 +90,7 @@ enum SmallMode {
 };
 
 // FP64 reduction slots (kSlot doubles each)
-enum RedSlot { RD_UU = 0, RD_VV, RD_UA, RD_VB, RD_AA, RD_BB, RD_G, RD_A1, RD_A2, RD_WWB, kNumRed };
+enum RedSlot { RD_UU = 0, RD_VV, RD_UA, RD_VB, RD_AA, RD_BB, RD_A1, RD_A2, RD_WWB, kNumRed };
 // FP32 matrix slots (kSlot floats each)
 enum MatSlot {
   MT_SVV = 0,  // s V^T V          (R x R)
@@ -114,6 +114,7 @@ struct SmallArgs {
   int K, step;
   double lam_k, rho_k, alpha_k, w_k;
   const double* red;   // [kNumRed][kSlot]
+  const double* red_prev;   // SM_RECOMP: the slots whose RD_UU holds U_k^T U_k
   float* mats;         // [kNumMat][kSlot]
   double* sc;          // [kNumSc]
   double* loss;        // [K]
@@ -183,7 +184,7 @@ __global__ void __launch_bounds__(256) k_unrolled_small(SmallArgs a) {
       double* A = dsh;
       df2* F = reinterpret_cast<df2*>(dsh + 3 * RR);
       for (int pass = 0; pass < 2; ++pass) {
-        const double* g = pass == 0 ? S(RD_G) : S(RD_VV);
+        const double* g = pass == 0 ? a.red_prev + (size_t)RD_UU * kSlot : S(RD_VV);
         for (int i = tid; i < RR; i += blockDim.x)
           A[i] = g[i] + ((i / R) == (i % R) ? a.rho_k : 0.0);
         __syncthreads();
@@ -628,6 +629,11 @@ struct UnrolledState {
   float* ckU = nullptr;    // (K+1) x m x R
   float* ckV = nullptr;    // (K+1) x n x R
   float* ckUs = nullptr;   // K x m x R   (U* of each step)
+  double* ckred = nullptr; // (K+1) x [kNumRed][kSlot]: block j holds the Grams of
+                           // (U_j, V_j) the loss needs (RD_UU, RD_VV, RD_UA, RD_VB),
+                           // formed by the forward and read again by the reverse
+                           // pass; the reverse pass's own Grams of step j-1 go to
+                           // the other slots of block j
   // adjoint buffers
   float* Ub[2] = {nullptr, nullptr};
   float* Vb[2] = {nullptr, nullptr};
@@ -717,7 +723,7 @@ dcf_status ensure_unrolled(dcf_handle h, int K) {
     u->part_wb = (float*)dev_alloc(h, mR * u->n_splits);
     u->mats = (float*)dev_alloc(h, (size_t)kNumMat * kSlot * 4);
     u->red = (double*)dev_alloc(h, (size_t)kNumRed * kSlot * 8);
-    u->part = (float2*)dev_alloc(h, (size_t)u->n_gram * kSlot * 8);
+    u->part = (float2*)dev_alloc(h, (size_t)kMaxGramJobs * u->n_gram * kSlot * 8);
     u->sc = (double*)dev_alloc(h, (size_t)kNumSc * 8);
     u->lam_part = (double*)dev_alloc(h, (size_t)grid * 8);
     u->hub_part = (double*)dev_alloc(h, (size_t)std::max(grid, h->n_vblocks) * 8);
@@ -735,22 +741,47 @@ dcf_status ensure_unrolled(dcf_handle h, int K) {
   u->ckU = (float*)dev_alloc(h, mR * (K + 1));
   u->ckV = (float*)dev_alloc(h, nR * (K + 1));
   u->ckUs = (float*)dev_alloc(h, mR * K);
+  u->ckred = (double*)dev_alloc(h, (size_t)(K + 1) * kNumRed * kSlot * 8);
   u->loss = (double*)dev_alloc(h, (size_t)K * 8);
   u->grads = (double*)dev_alloc(h, (size_t)3 * K * 8);
-  if (!u->ckU || !u->ckV || !u->ckUs || !u->loss || !u->grads)
+  if (!u->ckU || !u->ckV || !u->ckUs || !u->ckred || !u->loss || !u->grads)
     return fail(h, DCF_ENOMEM, "unrolled checkpoints");
   u->K = K;
   return DCF_OK;
 }
 
-// Gram X^T Y (N rows) reduced into red slot `slot`.
-cudaError_t gram_into(dcf_handle h, const float* X, int cx, const float* Y, int cy, int64_t N,
-                      int slot) {
+// Grams X^T Y (N rows each) summed in FP64 into `out`: up to kMaxGramJobs in
+// one launch of partials and one of sums.
+struct GSpec {
+  const float* X;
+  int cx;
+  const float* Y;
+  int cy;
+  int64_t N;
+  double* out;
+};
+
+cudaError_t grams(dcf_handle h, std::initializer_list<GSpec> list) {
   UnrolledState* u = h->unrolled;
-  const int np = (int)std::min<int64_t>(u->n_gram, std::max<int64_t>(1, N / 32));
-  cudaError_t e = launch_gram(X, cx, cx, Y, cy, cy, N, u->part, np, u->st, 0, h->stream);
-  if (e != cudaSuccess) return e;
-  return launch_reduce_plain(u->part, np, cx * cy, u->red + (size_t)slot * kSlot, h->stream);
+  GramJobs g{};
+  for (const GSpec& q : list) {
+    GramJob& j = g.j[g.n];
+    j.X = q.X;
+    j.Y = q.Y;
+    j.ldx = j.cx = q.cx;
+    j.ldy = j.cy = q.cy;
+    j.N = q.N;
+    j.nparts = (int)std::min<int64_t>(u->n_gram, std::max<int64_t>(1, q.N / 32));
+    j.part = u->part + (size_t)g.n * u->n_gram * kSlot;
+    j.out = q.out;
+    ++g.n;
+  }
+  return launch_gram_jobs(g, h->stream);
+}
+
+// slot s of block j of the stored Grams
+double* ckslot(UnrolledState* u, int j, int s) {
+  return u->ckred + ((size_t)j * kNumRed + s) * kSlot;
 }
 
 SmallArgs small_args(dcf_handle h, int mode, int K, int step) {
@@ -769,6 +800,7 @@ SmallArgs small_args(dcf_handle h, int mode, int K, int step) {
     sa.w_k = u->w_k[step];
   }
   sa.red = u->red;
+  sa.red_prev = u->red;
   sa.mats = u->mats;
   sa.sc = u->sc;
   sa.loss = u->loss;
@@ -858,8 +890,11 @@ extern "C" dcf_status dcf_unrolled_forward(dcf_handle h, int K, const double* a,
   UCK(cudaMemcpyAsync(u->ckU, h->U[cur], mR * 4, cudaMemcpyDeviceToDevice, s), "checkpoint");
   UCK(cudaMemcpyAsync(u->ckV, h->V[cur], nR * 4, cudaMemcpyDeviceToDevice, s), "checkpoint");
   if (with_loss) {
-    UCK(gram_into(h, h->A_truth, kt, h->A_truth, kt, m, RD_AA), "gram A");
-    UCK(gram_into(h, h->B_truth, kt, h->B_truth, kt, n, RD_BB), "gram B");
+    // ||A B^T||^2 from A^T A and B^T B; U_0^T U_0 for the reverse pass of step 0
+    UCK(grams(h, {{h->A_truth, kt, h->A_truth, kt, m, u->red + (size_t)RD_AA * kSlot},
+                  {h->B_truth, kt, h->B_truth, kt, n, u->red + (size_t)RD_BB * kSlot},
+                  {h->U[cur], R, h->U[cur], R, m, ckslot(u, 0, RD_UU)}}),
+        "grams");
     UCK(launch_small(small_args(h, SM_LOSS_C, K, -1), s), "loss scale");
   }
   const double lam0 = h->lam, rho0 = h->rho;
@@ -892,11 +927,14 @@ extern "C" dcf_status dcf_unrolled_forward(dcf_handle h, int K, const double* a,
                                 cudaMemcpyDeviceToDevice, s)) != cudaSuccess)
         return e2;
       if (with_loss) {
-        if ((e2 = gram_into(h, h->U[cur], R, h->U[cur], R, m, RD_UU)) != cudaSuccess ||
-            (e2 = gram_into(h, h->V[cur], R, h->V[cur], R, n, RD_VV)) != cudaSuccess ||
-            (e2 = gram_into(h, h->U[cur], R, h->A_truth, kt, m, RD_UA)) != cudaSuccess ||
-            (e2 = gram_into(h, h->V[cur], R, h->B_truth, kt, n, RD_VB)) != cudaSuccess ||
-            (e2 = launch_small(small_args(h, SM_LOSS_TERM, K, k), s)) != cudaSuccess)
+        SmallArgs sa = small_args(h, SM_LOSS_TERM, K, k);
+        sa.red = ckslot(u, k + 1, 0);
+        if ((e2 = grams(h, {{h->U[cur], R, h->U[cur], R, m, ckslot(u, k + 1, RD_UU)},
+                            {h->V[cur], R, h->V[cur], R, n, ckslot(u, k + 1, RD_VV)},
+                            {h->U[cur], R, h->A_truth, kt, m, ckslot(u, k + 1, RD_UA)},
+                            {h->V[cur], R, h->B_truth, kt, n, ckslot(u, k + 1, RD_VB)}})) !=
+                cudaSuccess ||
+            (e2 = launch_small(sa, s)) != cudaSuccess)
           return e2;
       }
       return cudaSuccess;
@@ -959,12 +997,15 @@ extern "C" dcf_status dcf_unrolled_backward(dcf_handle h, double* grad_a, double
     float* Ub2 = u->Ub[ib ^ 1];
     float* Vb2 = u->Vb[ib ^ 1];
     const float alpha = (float)u->alpha_k[k];
-    // loss gradient at (U_{k+1}, V_{k+1})
-    UCK(gram_into(h, Uk1, R, Uk1, R, m, RD_UU), "gram");
-    UCK(gram_into(h, Vn, R, Vn, R, n, RD_VV), "gram");
-    UCK(gram_into(h, Uk1, R, h->A_truth, kt, m, RD_UA), "gram");
-    UCK(gram_into(h, Vn, R, h->B_truth, kt, n, RD_VB), "gram");
-    UCK(launch_small(small_args(h, SM_LOSSGRAD, K, k), s), "loss grad");
+    // loss gradient at (U_{k+1}, V_{k+1}), from the Grams the forward formed
+    double* blk = ckslot(u, k + 1, 0);
+    auto small = [&](int mode) {
+      SmallArgs sa = small_args(h, mode, K, k);
+      sa.red = blk;
+      sa.red_prev = ckslot(u, k, 0);
+      return launch_small(sa, s);
+    };
+    UCK(small(SM_LOSSGRAD), "loss grad");
     {
       RowLin L = rowlin(m, Ub);
       add_mat(L, Uk1, R, mat(h, MT_SVV));
@@ -978,17 +1019,17 @@ extern "C" dcf_status dcf_unrolled_backward(dcf_handle h, double* grad_a, double
       UCK(launch_rowlin(R, L2, s), "rowlin");
     }
     // G^{-1}, H^{-1} of step k and W = U_k G^{-1}
-    UCK(gram_into(h, Uk, R, Uk, R, m, RD_G), "gram");
-    UCK(launch_small(small_args(h, SM_RECOMP, K, k), s), "recompute");
+    UCK(small(SM_RECOMP), "recompute");
     {
       RowLin L = rowlin(m, u->Wk);
       add_mat(L, Uk, R, mat(h, MT_GINV));
       UCK(launch_rowlin(R, L, s), "rowlin");
     }
     // relaxation and U* = P H^{-1}
-    UCK(gram_into(h, Us, R, Ub, R, m, RD_A1), "gram");
-    UCK(gram_into(h, Uk, R, Ub, R, m, RD_A2), "gram");
-    UCK(launch_small(small_args(h, SM_HBAR, K, k), s), "Hbar");
+    UCK(grams(h, {{Us, R, Ub, R, m, blk + (size_t)RD_A1 * kSlot},
+                  {Uk, R, Ub, R, m, blk + (size_t)RD_A2 * kSlot}}),
+        "grams");
+    UCK(small(SM_HBAR), "Hbar");
     {
       RowLin L = rowlin(m, u->Pb);
       add_mat(L, Ub, R, mat(h, MT_AHINV));
@@ -1047,8 +1088,8 @@ extern "C" dcf_status dcf_unrolled_backward(dcf_handle h, double* grad_a, double
       add_term(L, u->part_wb, 1.f, u->n_splits, (int64_t)mR);
       UCK(launch_rowlin(R, L, s), "rowlin");
     }
-    UCK(gram_into(h, u->Wk, R, u->Wbar, R, m, RD_WWB), "gram");
-    UCK(launch_small(small_args(h, SM_GBAR, K, k), s), "Gbar");
+    UCK(grams(h, {{u->Wk, R, u->Wbar, R, m, blk + (size_t)RD_WWB * kSlot}}), "gram");
+    UCK(small(SM_GBAR), "Gbar");
     {
       RowLin L = rowlin(m, Ub2);
       add_mat(L, u->Wbar, R, mat(h, MT_GINV));

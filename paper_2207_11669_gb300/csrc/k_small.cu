@@ -1,7 +1,7 @@
 // Small-matrix and per-row kernels of the DCF-PCA iteration.
 //
-//   k_gram_part      per-CTA partial Gram X^T Y over a row range (FP32 products,
-//                    chunked FP32 sums folded into a compensated (TwoSum) pair)
+//   k_gram_part      per-CTA partial Gram X^T Y over a row range (compensated
+//                    Dot2 products: a float pair per entry)
 //   k_reduce_parts   deterministic FP64 sum of those partials over many CTAs;
 //                    the last CTA to finish runs the serial r x r tail:
 //                      TAIL_Q : Q_t = V_t^T V_t, Cholesky of Q_t + rho I (U-step)
@@ -66,13 +66,66 @@ __device__ __forceinline__ void dot2_add(float& hi, float& lo, float x, float y)
 
 // ---------------------------------------------------------------------------
 // Gram partials:  part[b][k*cy + l] = sum_{rows a of CTA b} X[a,k] * Y[a,l]
-// as compensated pairs (hi, lo): FP32 sums per 32-row chunk, TwoSum across
-// chunks.  Generic shapes (cx, cy <= 64); the per-iteration V Grams use the
-// register-blocked k_gram_vv below.
+// as compensated pairs (hi, lo) (Dot2 per row).  Generic shapes (cx, cy <= 64);
+// the per-iteration V Grams use the register-blocked k_gram_vv below.  NS is
+// the number of entries per thread (ceil(cx cy / 256)); the loops stay short
+// because a launch runs only a few chunks per CTA with a cold instruction
+// cache, so unrolled code costs more than it saves.
 // ---------------------------------------------------------------------------
 constexpr int kGramChunk = 32;
-constexpr int kGramMaxEntriesPerThread = 16;   // (64*64)/256
 
+// Partial of CTA b over rows [b rows_per, (b + 1) rows_per) into part[b][*].
+template <int NS>
+__device__ __forceinline__ void gram_part_body(const float* __restrict__ X, int ldx, int cx,
+                                               const float* __restrict__ Y, int ldy, int cy,
+                                               int64_t N, int64_t rows_per_cta, int64_t b,
+                                               float2* __restrict__ part, float* sh) {
+  float* Xs = sh;                           // [chunk][cx]
+  float* Ys = sh + kGramChunk * cx;         // [chunk][cy]
+  const int tid = threadIdx.x;
+  const int ne = cx * cy;
+  float hi[NS], lo[NS];
+  int xo[NS], yo[NS];
+  bool on[NS];
+#pragma unroll
+  for (int s = 0; s < NS; ++s) {
+    hi[s] = 0.f;
+    lo[s] = 0.f;
+    const int e = tid + s * 256;
+    on[s] = e < ne;
+    xo[s] = on[s] ? e / cy : 0;
+    yo[s] = on[s] ? e % cy : 0;
+  }
+  const int64_t a0 = b * rows_per_cta;
+  const int64_t a1 = min(N, a0 + rows_per_cta);
+#pragma unroll 1
+  for (int64_t c = a0; c < a1; c += kGramChunk) {
+    const int rows = (int)dmin64((int64_t)(kGramChunk), a1 - c);
+    __syncthreads();
+#pragma unroll 1
+    for (int i = tid; i < kGramChunk * cx; i += blockDim.x) {
+      const int rr = i / cx, k = i - rr * cx;
+      Xs[i] = rr < rows ? X[(c + rr) * ldx + k] : 0.f;
+    }
+#pragma unroll 1
+    for (int i = tid; i < kGramChunk * cy; i += blockDim.x) {
+      const int rr = i / cy, k = i - rr * cy;
+      Ys[i] = rr < rows ? Y[(c + rr) * ldy + k] : 0.f;
+    }
+    __syncthreads();
+#pragma unroll 4
+    for (int rr = 0; rr < rows; ++rr) {
+#pragma unroll
+      for (int s = 0; s < NS; ++s)
+        if (on[s]) dot2_add(hi[s], lo[s], Xs[rr * cx + xo[s]], Ys[rr * cy + yo[s]]);
+    }
+  }
+#pragma unroll
+  for (int s = 0; s < NS; ++s)
+    if (on[s]) part[b * ne + tid + s * 256] = make_float2(hi[s], lo[s]);
+}
+
+template <int NS>
 __global__ void __launch_bounds__(256)
 k_gram_part(const float* __restrict__ X, int ldx, int cx,
             const float* __restrict__ Y, int ldy, int cy,
@@ -80,45 +133,16 @@ k_gram_part(const float* __restrict__ X, int ldx, int cx,
             const DevState* st, int respect_stop) {
   if (respect_stop && st->stop) return;
   extern __shared__ float sh[];
-  float* Xs = sh;                           // [chunk][cx]
-  float* Ys = sh + kGramChunk * cx;         // [chunk][cy]
-  const int tid = threadIdx.x;
-  const int ne = cx * cy;
-  float hi[kGramMaxEntriesPerThread], lo[kGramMaxEntriesPerThread];
-  int xo[kGramMaxEntriesPerThread], yo[kGramMaxEntriesPerThread];
-#pragma unroll
-  for (int s = 0; s < kGramMaxEntriesPerThread; ++s) {
-    hi[s] = 0.f;
-    lo[s] = 0.f;
-    const int e = tid + s * 256;
-    xo[s] = e < ne ? e / cy : 0;
-    yo[s] = e < ne ? e % cy : 0;
-  }
-  const int64_t a0 = (int64_t)blockIdx.x * rows_per_cta;
-  const int64_t a1 = min(N, a0 + rows_per_cta);
-  for (int64_t c = a0; c < a1; c += kGramChunk) {
-    const int rows = (int)dmin64((int64_t)(kGramChunk), a1 - c);
-    __syncthreads();
-    for (int i = tid; i < kGramChunk * cx; i += blockDim.x) {
-      int rr = i / cx, k = i % cx;
-      Xs[i] = rr < rows ? X[(c + rr) * ldx + k] : 0.f;
-    }
-    for (int i = tid; i < kGramChunk * cy; i += blockDim.x) {
-      int rr = i / cy, k = i % cy;
-      Ys[i] = rr < rows ? Y[(c + rr) * ldy + k] : 0.f;
-    }
-    __syncthreads();
-    for (int rr = 0; rr < kGramChunk; ++rr) {   // rows past the end are zero
-#pragma unroll
-      for (int s = 0; s < kGramMaxEntriesPerThread; ++s)
-        if (tid + s * 256 < ne) dot2_add(hi[s], lo[s], Xs[rr * cx + xo[s]], Ys[rr * cy + yo[s]]);
-    }
-  }
-#pragma unroll
-  for (int s = 0; s < kGramMaxEntriesPerThread; ++s) {
-    int e = tid + s * 256;
-    if (e < ne) part[(int64_t)blockIdx.x * ne + e] = make_float2(hi[s], lo[s]);
-  }
+  gram_part_body<NS>(X, ldx, cx, Y, ldy, cy, N, rows_per_cta, blockIdx.x, part, sh);
+}
+
+template <int NS>
+__global__ void __launch_bounds__(256) k_gram_jobs(GramJobs g) {
+  const GramJob& j = g.j[blockIdx.y];
+  if ((int)blockIdx.x >= j.nparts) return;
+  extern __shared__ float sh[];
+  const int64_t rows_per = (j.N + j.nparts - 1) / j.nparts;
+  gram_part_body<NS>(j.X, j.ldx, j.cx, j.Y, j.ldy, j.cy, j.N, rows_per, blockIdx.x, j.part, sh);
 }
 
 // The Grams of the new V in one pass:  Q = V'^T V',  Y = V_old^T dV  and
@@ -1088,9 +1112,18 @@ static size_t gram_smem(int cx, int cy) { return (size_t)kGramChunk * (cx + cy) 
 cudaError_t launch_gram(const float* X, int ldx, int cx, const float* Y, int ldy, int cy,
                         int64_t N, float2* part, int nparts, const DevState* st,
                         int respect_stop, cudaStream_t s) {
-  int64_t rows_per = (N + nparts - 1) / nparts;
-  k_gram_part<<<nparts, 256, gram_smem(cx, cy), s>>>(X, ldx, cx, Y, ldy, cy, N, rows_per, part,
-                                                     st, respect_stop);
+  const int64_t rows_per = (N + nparts - 1) / nparts;
+  const size_t smem = gram_smem(cx, cy);
+  const int ns = (cx * cy + 255) / 256;
+  if (ns <= 1)
+    k_gram_part<1><<<nparts, 256, smem, s>>>(X, ldx, cx, Y, ldy, cy, N, rows_per, part, st,
+                                             respect_stop);
+  else if (ns <= 4)
+    k_gram_part<4><<<nparts, 256, smem, s>>>(X, ldx, cx, Y, ldy, cy, N, rows_per, part, st,
+                                             respect_stop);
+  else
+    k_gram_part<16><<<nparts, 256, smem, s>>>(X, ldx, cx, Y, ldy, cy, N, rows_per, part, st,
+                                              respect_stop);
   return cudaGetLastError();
 }
 
@@ -1239,6 +1272,81 @@ cudaError_t launch_reduce_init(const IterArgs& a, int which /*0: G, 1: Q*/, int 
   ra.R = a.R; ra.r = a.r; ra.rho = a.rho; ra.u_mode = a.u_mode; ra.copy = copy;
   ra.counter = counter; ra.sm = a.sm; ra.st = a.st;
   return launch_reduce(ra, s);
+}
+
+// FP64 sums of the partials of several Gram jobs: the summation of
+// k_reduce_parts (16 entries per CTA, 16 lanes per entry, each lane's
+// partials in order, then the lanes in order), without a tail.
+__global__ void __launch_bounds__(256) k_reduce_jobs(GramJobs g) {
+  __shared__ float2 red2[256];
+  const int tid = threadIdx.x;
+  const int e_local = tid % kRedEntriesPerCta;
+  const int lane_p = tid / kRedEntriesPerCta;
+  constexpr int nsplit = 256 / kRedEntriesPerCta;
+  int idx = blockIdx.x * kRedEntriesPerCta + e_local;
+  int which = -1;
+  for (int q = 0; q < g.n; ++q) {
+    const int c = g.j[q].cx * g.j[q].cy;
+    if (idx < c) {
+      which = q;
+      break;
+    }
+    idx -= c;
+  }
+  float hi = 0.f, lo = 0.f;
+  if (which >= 0) {
+    const float2* p = g.j[which].part;
+    const int cnt = g.j[which].cx * g.j[which].cy;
+    const int np = g.j[which].nparts;
+    for (int q0 = lane_p; q0 < np; q0 += 8 * nsplit) {
+      float2 v[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int q = q0 + u * nsplit;
+        v[u] = q < np ? p[(int64_t)q * cnt + idx] : make_float2(0.f, 0.f);
+      }
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        two_sum_add(hi, lo, v[u].x);
+        lo += v[u].y;
+      }
+    }
+  }
+  red2[tid] = make_float2(hi, lo);
+  __syncthreads();
+  if (lane_p == 0 && which >= 0) {
+    float th = 0.f, tl = 0.f;
+    for (int q = 0; q < nsplit; ++q) {
+      const float2 v = red2[q * kRedEntriesPerCta + e_local];
+      two_sum_add(th, tl, v.x);
+      tl += v.y;
+    }
+    g.j[which].out[idx] = (double)th + (double)tl;
+  }
+}
+
+cudaError_t launch_gram_jobs(const GramJobs& g, cudaStream_t s) {
+  if (g.n <= 0 || g.n > kMaxGramJobs) return g.n == 0 ? cudaSuccess : cudaErrorInvalidValue;
+  int maxp = 0, maxe = 0, total = 0;
+  size_t smem = 0;
+  for (int q = 0; q < g.n; ++q) {
+    const GramJob& j = g.j[q];
+    if (j.cx < 1 || j.cy < 1 || j.cx > kMaxR || j.cy > kMaxR || j.nparts < 1)
+      return cudaErrorInvalidValue;
+    maxp = j.nparts > maxp ? j.nparts : maxp;
+    maxe = j.cx * j.cy > maxe ? j.cx * j.cy : maxe;
+    total += j.cx * j.cy;
+    smem = gram_smem(j.cx, j.cy) > smem ? gram_smem(j.cx, j.cy) : smem;
+  }
+  const dim3 grid((unsigned)maxp, (unsigned)g.n);
+  const int ns = (maxe + 255) / 256;
+  if (ns <= 1) k_gram_jobs<1><<<grid, 256, smem, s>>>(g);
+  else if (ns <= 4) k_gram_jobs<4><<<grid, 256, smem, s>>>(g);
+  else k_gram_jobs<16><<<grid, 256, smem, s>>>(g);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  k_reduce_jobs<<<(total + kRedEntriesPerCta - 1) / kRedEntriesPerCta, 256, 0, s>>>(g);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_reduce_plain(const float2* part, int nparts, int count, double* out,
