@@ -56,7 +56,7 @@ dcf_status cuda_fail(dcf_handle h, cudaError_t e, const char* what) {
 #define DCF_TAIL_RATE 0.7
 #endif
 constexpr double kTailRate = DCF_TAIL_RATE;
-constexpr int kTailMaxGroups = 2;
+constexpr int kTailMaxGroups = 8;
 constexpr int kTailMinStrips = 128;
 
 #define CK(call, what)                                   \
@@ -634,13 +634,26 @@ extern "C" dcf_status dcf_create(const dcf_params* p, dcf_handle* out) {
         h->nclusters = (int)std::min<int64_t>(ncl, nstrips64);
         // the SMs the clusters leave idle (a cluster must fit in one GPC) take
         // a share of the columns on the two-pass kernels, one CTA per SM and
-        // slab; the share balances the two rates (kTailRate: the two-pass
-        // kernels' bytes of M per CTA and second, two reads, relative to a
-        // fused CTA's), in whole 64-column strips, every tail CTA with a strip
+        // (slab, strip group); the share balances the two rates (kTailRate:
+        // the two-pass kernels' bytes of M per CTA and second, two reads,
+        // relative to a fused CTA's), in whole 64-column strips, every tail
+        // CTA with a strip.  The strip groups follow the wave-cost rule of the
+        // two-pass path over the idle SMs (16 slabs on 40 SMs: 5 groups, two
+        // waves of 40 CTAs, against one wave of 32)
         const int idle = h->num_sms - h->cs * h->nclusters;
-        const int gt = std::min(idle / h->nslabs, kTailMaxGroups);
+        int gt = 0;
+        double tail_ctas = 0.0;   // tail CTAs running at a time
+        if (idle >= h->nslabs) {
+          auto waves = [&](int g) { return (h->nslabs * g + idle - 1) / idle; };
+          auto cost = [&](int g) { return (double)waves(g) / (double)g; };
+          double best = cost(1);
+          for (int g = 2; g <= kTailMaxGroups; ++g) best = std::min(best, cost(g));
+          gt = 1;
+          while (cost(gt) > 1.06 * best) ++gt;
+          tail_ctas = (double)h->nslabs * gt / waves(gt);
+        }
         if (h->nclusters == ncl && gt >= 1 && nstrips64 >= kTailMinStrips) {
-          const double tr = kTailRate * gt * h->nslabs;
+          const double tr = kTailRate * tail_ctas;
           int64_t st = (int64_t)((double)nstrips64 * tr / (tr + h->cs * h->nclusters));
           st = std::min<int64_t>(st, nstrips64 - h->nclusters);   // every cluster keeps a strip
           if (st >= 2 * gt && tc2_prepare(Rf) == cudaSuccess) {
