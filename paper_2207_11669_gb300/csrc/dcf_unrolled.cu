@@ -23,6 +23,8 @@
 //   Xbar = Pbar V'^T + W Vbar_tot^T,  D = Xbar . 1[|R| > lambda_k]
 //   Vbar = D^T U,  lambda_bar = sum D . sign(R)      (pass B: column strips)
 //   Ubar_D = D V,  Wbar = X Vbar_tot                 (pass C: row blocks)
+//   (for R <= 16 passes B and C are one kernel over row blocks x column
+//   splits, k_adj_fused, with Vbar summed from per-row-block partials)
 //   Gbar = sym(-(W^T Wbar) G^{-1}),  rho_bar += tr Gbar
 //   Ubar = (1 - alpha) Ubar' + Ubar_D + Wbar G^{-1} + 2 U Gbar
 //   grad a_k = lambda_bar lambda_k,  grad b_k = rho_bar rho_k,  grad c_k = alpha_bar
@@ -342,6 +344,7 @@ struct AdjArgs {
   double* lam_part;    // out: per-CTA sum of D . sign(R)
   float* part_ud;      // out: [split][m][R]  D V partials
   float* part_wb;      // out: [split][m][R]  X Vbar_tot partials
+  float* part_vb;      // out (fused kernel): [row block][n][R]  D^T U partials
   int64_t split_cols;
 };
 
@@ -556,6 +559,331 @@ __global__ void __launch_bounds__(256) k_adj_rows(AdjArgs a) {
   }
 }
 
+// Adjoint passes over M for R <= 16 (k_adj_a, k_adj_fused): a CTA takes a
+// 128-row block and a column split and walks the split in chunks of 32
+// columns, brought into shared memory by cp.async in two stages.
+constexpr int kAfRows = 128;
+constexpr int kAfCols = 32;
+constexpr int kAfLdd = kAfCols + 1;   // D tile row stride: conflict-free by row and by column
+
+// Shared-memory layout of the fused adjoint kernels: NV column-vector arrays
+// per chunk (pass A: V; passes B and C: V, V', Vbar_tot).
+template <int R, int NV>
+struct AfCfg {
+  static constexpr int MT = kAfCols * kAfRows;   // M tile, column-major [32][128]
+  static constexpr int VT = NV * kAfCols * R;    // the column vectors of the chunk
+  static constexpr int STAGE = MT + VT;
+  static constexpr int DT = kAfRows * kAfLdd;    // D (or X) tile [128][33]
+  static constexpr int US = kAfRows * R;         // rows of U (or Pbar) of the block
+  static constexpr size_t smem_floats = 2 * (size_t)STAGE + DT + US;
+};
+
+// 4- and 16-byte asynchronous copies global -> shared; ok == false zero-fills
+// the destination and reads nothing.
+__device__ __forceinline__ void af_cp4(float* sdst, const float* gsrc, bool ok) {
+  const uint32_t d = (uint32_t)__cvta_generic_to_shared(sdst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(d), "l"(gsrc),
+               "r"(ok ? 4 : 0)
+               : "memory");
+}
+__device__ __forceinline__ void af_cp16(float* sdst, const float* gsrc, bool ok) {
+  const uint32_t d = (uint32_t)__cvta_generic_to_shared(sdst);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(d), "l"(gsrc),
+               "r"(ok ? 16 : 0)
+               : "memory");
+}
+__device__ __forceinline__ void af_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void af_wait() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
+// One chunk (columns [c0, c0 + 32) of the split, rows [a0, a0 + 128)) into a
+// stage: the M tile and the rows of the NV column-vector arrays; columns at or
+// past c_end and rows at or past m read as zero.  Block-wide; one commit group.
+template <int R, int NV>
+__device__ __forceinline__ void af_load_chunk(float* stage, const float* M, int64_t m,
+                                              int64_t a0, int64_t c0, int64_t c_end,
+                                              const float* v0, const float* v1,
+                                              const float* v2) {
+  using C = AfCfg<R, NV>;
+  const int tid = threadIdx.x;
+  float* Mt = stage;
+  float* Vt = stage + C::MT;
+  if ((m & 3) == 0) {   // columns of M start on 16-byte boundaries: groups of 4 rows
+    for (int idx = tid; idx < C::MT / 4; idx += 256) {
+      const int jj = idx / (kAfRows / 4), aq = idx % (kAfRows / 4);
+      const int64_t col = c0 + jj, row = a0 + 4 * aq;
+      const bool ok = col < c_end && row < m;
+      af_cp16(Mt + jj * kAfRows + 4 * aq, ok ? M + col * m + row : M, ok);
+    }
+  } else {
+    for (int idx = tid; idx < C::MT; idx += 256) {
+      const int jj = idx / kAfRows, aa = idx % kAfRows;
+      const int64_t col = c0 + jj, row = a0 + aa;
+      const bool ok = col < c_end && row < m;
+      af_cp4(Mt + idx, ok ? M + col * m + row : M, ok);
+    }
+  }
+  for (int idx = tid; idx < NV * kAfCols * (R / 4); idx += 256) {
+    const int q = idx / (kAfCols * (R / 4));
+    const int rem = idx % (kAfCols * (R / 4));
+    const int jj = rem / (R / 4), k4 = rem % (R / 4);
+    const int64_t col = c0 + jj;
+    const bool ok = col < c_end;
+    const float* src = q == 0 ? v0 : q == 1 ? v1 : v2;
+    af_cp16(Vt + (q * kAfCols + jj) * R + 4 * k4, ok ? src + col * R + 4 * k4 : src, ok);
+  }
+  af_commit();
+}
+
+// out[rb][col][k] = sum over the block's 128 rows of T[row][col] Y[row][k] for
+// the chunk's columns (T: the [128][33] tile, Y: [128][R] rows in shared
+// memory).  Warp w takes columns 4w .. 4w + 3; its lanes split the rows and
+// the k values and a shuffle tree adds the row groups.  Block-wide (8 warps).
+template <int R>
+__device__ __forceinline__ void af_colsum(const float* T, const float* Y, float* out, int64_t n,
+                                          int64_t rb, int64_t c0, int64_t c_end) {
+  constexpr int NKG = R / 4;            // k groups of four
+  constexpr int NRQ = 32 / NKG;         // row groups of a warp
+  constexpr int RPL = kAfRows / NRQ;    // rows per lane
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int kg = lane % NKG, rq = lane / NKG;
+  float acc[4][4];
+#pragma unroll
+  for (int cc = 0; cc < 4; ++cc)
+#pragma unroll
+    for (int q = 0; q < 4; ++q) acc[cc][q] = 0.f;
+#pragma unroll 4
+  for (int i = 0; i < RPL; ++i) {
+    const int aa = i * NRQ + rq;
+    const float4 yy = *reinterpret_cast<const float4*>(Y + aa * R + 4 * kg);
+#pragma unroll
+    for (int cc = 0; cc < 4; ++cc) {
+      const float tv = T[aa * kAfLdd + 4 * warp + cc];
+      acc[cc][0] = fmaf(tv, yy.x, acc[cc][0]);
+      acc[cc][1] = fmaf(tv, yy.y, acc[cc][1]);
+      acc[cc][2] = fmaf(tv, yy.z, acc[cc][2]);
+      acc[cc][3] = fmaf(tv, yy.w, acc[cc][3]);
+    }
+  }
+#pragma unroll
+  for (int o = NKG; o < 32; o <<= 1)
+#pragma unroll
+    for (int cc = 0; cc < 4; ++cc)
+#pragma unroll
+      for (int q = 0; q < 4; ++q) acc[cc][q] += __shfl_xor_sync(0xffffffffu, acc[cc][q], o);
+  if (rq == 0) {
+#pragma unroll
+    for (int cc = 0; cc < 4; ++cc) {
+      const int64_t col = c0 + 4 * warp + cc;
+      if (col < c_end)
+        *reinterpret_cast<float4*>(out + (rb * n + col) * R + 4 * kg) =
+            make_float4(acc[cc][0], acc[cc][1], acc[cc][2], acc[cc][3]);
+    }
+  }
+}
+
+// Pass A for R <= 16: y1 = X^T Pbar with X = U V^T + clamp(M - U V^T, +-lambda),
+// per (128-row block) x (column split) as k_adj_fused; the row block's partial
+// of y1 goes to part_vb.  2R flop per element.
+template <int R>
+__global__ void __launch_bounds__(256, 2) k_adj_a(AdjArgs a) {
+  using C = AfCfg<R, 1>;
+  static_assert(R % 4 == 0 && R <= 16, "register budget");
+  constexpr int HC = kAfCols / 2;
+  extern __shared__ __align__(16) float sh[];
+  float* Xt = sh + 2 * C::STAGE;
+  float* Ps = Xt + C::DT;
+  const int tid = threadIdx.x;
+  const int ar = tid & (kAfRows - 1), h = tid >> 7;
+  const float lam = a.lam;
+  const int64_t m = a.m, n = a.n;
+  const int64_t a0 = (int64_t)blockIdx.x * kAfRows;
+  const int64_t arow = a0 + ar;
+  const bool rvalid = arow < m;
+  const int64_t c_begin = (int64_t)blockIdx.y * a.split_cols;
+  const int64_t c_end = imin64(n, c_begin + a.split_cols);
+  const int nchunks = c_end > c_begin ? (int)((c_end - c_begin + kAfCols - 1) / kAfCols) : 0;
+  if (nchunks > 0) af_load_chunk<R, 1>(sh, a.M, m, a0, c_begin, c_end, a.V, a.V, a.V);
+  float u[R];
+#pragma unroll
+  for (int k = 0; k < R; ++k) u[k] = rvalid ? a.U[arow * R + k] : 0.f;
+  for (int idx = tid; idx < kAfRows * R; idx += 256) {
+    const int64_t row = a0 + idx / R;
+    Ps[idx] = row < m ? a.Pb[row * R + idx % R] : 0.f;
+  }
+  for (int c = 0; c < nchunks; ++c) {
+    const int64_t c0 = c_begin + (int64_t)c * kAfCols;
+    if (c + 1 < nchunks) {
+      af_load_chunk<R, 1>(sh + ((c + 1) & 1) * C::STAGE, a.M, m, a0, c0 + kAfCols, c_end, a.V,
+                          a.V, a.V);
+      af_wait<1>();
+    } else {
+      af_wait<0>();
+    }
+    __syncthreads();
+    const float* Mt = sh + (c & 1) * C::STAGE;
+    const float* Vs = Mt + C::MT;
+#pragma unroll 2
+    for (int i = 0; i < HC; ++i) {
+      const int jj = h * HC + i;
+      const float4* v4 = reinterpret_cast<const float4*>(Vs + jj * R);
+      float d0 = 0.f, d1 = 0.f;
+#pragma unroll
+      for (int k4 = 0; k4 < R / 4; ++k4) {
+        const float4 v = v4[k4];
+        d0 = fmaf(u[4 * k4], v.x, d0);
+        d1 = fmaf(u[4 * k4 + 1], v.y, d1);
+        d0 = fmaf(u[4 * k4 + 2], v.z, d0);
+        d1 = fmaf(u[4 * k4 + 3], v.w, d1);
+      }
+      const float d = d0 + d1;
+      const float r = Mt[jj * kAfRows + ar] - d;
+      Xt[ar * kAfLdd + jj] = d + fminf(fmaxf(r, -lam), lam);
+    }
+    __syncthreads();
+    af_colsum<R>(Xt, Ps, a.part_vb, n, blockIdx.x, c0, c_end);
+  }
+}
+
+// Passes B and C in one kernel (R <= 16): (128-row block) x (column split),
+// chunks of 32 columns brought into shared memory by cp.async, two stages, so
+// that the next chunk's loads overlap this chunk's arithmetic.  Thread (row
+// ar, column half h) forms R, X, Xbar and D of its row for 16 columns of a
+// chunk (U, Pbar and W of its row in registers) and accumulates D V and
+// X Vbar_tot of its row over the split in registers (FP32).  Then Vbar = D^T U
+// of the chunk's columns is summed over the block's rows (af_colsum) into the
+// row block's partial in part_vb.  M is read once for both passes, and every
+// value of an element is formed once (6R flop per element against 9R).
+template <int R>
+__global__ void __launch_bounds__(256, 2) k_adj_fused(AdjArgs a) {
+  using C = AfCfg<R, 3>;
+  static_assert(R % 4 == 0 && R <= 16, "register budget");
+  static_assert(kAfRows * (2 * R + 1) <= C::STAGE, "final combine reuses the stages");
+  constexpr int HC = kAfCols / 2;       // columns per thread and chunk
+  extern __shared__ __align__(16) float sh[];
+  float* Dt = sh + 2 * C::STAGE;
+  float* Us = Dt + C::DT;
+  const int tid = threadIdx.x;
+  const int ar = tid & (kAfRows - 1), h = tid >> 7;
+  const float lam = a.lam;
+  const int64_t m = a.m, n = a.n;
+  const int64_t a0 = (int64_t)blockIdx.x * kAfRows;
+  const int64_t arow = a0 + ar;
+  const bool rvalid = arow < m;
+  const int64_t c_begin = (int64_t)blockIdx.y * a.split_cols;
+  const int64_t c_end = imin64(n, c_begin + a.split_cols);
+  const int nchunks = c_end > c_begin ? (int)((c_end - c_begin + kAfCols - 1) / kAfCols) : 0;
+  if (nchunks > 0) af_load_chunk<R, 3>(sh, a.M, m, a0, c_begin, c_end, a.V, a.Vn, a.Vtot);
+  float u[R], p[R], w[R];
+#pragma unroll
+  for (int k = 0; k < R; ++k) {
+    u[k] = rvalid ? a.U[arow * R + k] : 0.f;
+    p[k] = rvalid ? a.Pb[arow * R + k] : 0.f;
+    w[k] = rvalid ? a.W[arow * R + k] : 0.f;
+  }
+  for (int idx = tid; idx < kAfRows * R; idx += 256) {
+    const int64_t row = a0 + idx / R;
+    Us[idx] = row < m ? a.U[row * R + idx % R] : 0.f;
+  }
+  float ud[R], wb[R];
+#pragma unroll
+  for (int k = 0; k < R; ++k) ud[k] = wb[k] = 0.f;
+  float lb_hi = 0.f, lb_lo = 0.f;
+
+  for (int c = 0; c < nchunks; ++c) {
+    const int64_t c0 = c_begin + (int64_t)c * kAfCols;
+    if (c + 1 < nchunks) {
+      af_load_chunk<R, 3>(sh + ((c + 1) & 1) * C::STAGE, a.M, m, a0, c0 + kAfCols, c_end, a.V,
+                          a.Vn, a.Vtot);
+      af_wait<1>();
+    } else {
+      af_wait<0>();
+    }
+    __syncthreads();
+    const float* Mt = sh + (c & 1) * C::STAGE;
+    const float* Vs = Mt + C::MT;
+    const float* Vns = Vs + kAfCols * R;
+    const float* Vbs = Vns + kAfCols * R;
+    float lb = 0.f;
+#pragma unroll 1
+    for (int i = 0; i < HC; ++i) {
+      const int jj = h * HC + i;
+      const float4* v4 = reinterpret_cast<const float4*>(Vs + jj * R);
+      const float4* vn4 = reinterpret_cast<const float4*>(Vns + jj * R);
+      const float4* vb4 = reinterpret_cast<const float4*>(Vbs + jj * R);
+      // two chains each for U V^T and for Pbar V'^T + W Vbar_tot^T
+      float d0 = 0.f, d1 = 0.f, x0 = 0.f, x1 = 0.f;
+#pragma unroll
+      for (int k4 = 0; k4 < R / 4; ++k4) {
+        const float4 v = v4[k4], vn = vn4[k4], vb = vb4[k4];
+        d0 = fmaf(u[4 * k4], v.x, d0);
+        d1 = fmaf(u[4 * k4 + 1], v.y, d1);
+        d0 = fmaf(u[4 * k4 + 2], v.z, d0);
+        d1 = fmaf(u[4 * k4 + 3], v.w, d1);
+        x0 = fmaf(p[4 * k4], vn.x, x0);
+        x1 = fmaf(p[4 * k4 + 1], vn.y, x1);
+        x0 = fmaf(p[4 * k4 + 2], vn.z, x0);
+        x1 = fmaf(p[4 * k4 + 3], vn.w, x1);
+        x0 = fmaf(w[4 * k4], vb.x, x0);
+        x1 = fmaf(w[4 * k4 + 1], vb.y, x1);
+        x0 = fmaf(w[4 * k4 + 2], vb.z, x0);
+        x1 = fmaf(w[4 * k4 + 3], vb.w, x1);
+      }
+      const float d = d0 + d1, xb = x0 + x1;
+      const float r = Mt[jj * kAfRows + ar] - d;
+      const bool outside = fabsf(r) > lam;
+      const float dv = outside ? xb : 0.f;
+      const float x = d + fminf(fmaxf(r, -lam), lam);
+      lb += outside ? (r > 0.f ? xb : -xb) : 0.f;
+      Dt[ar * kAfLdd + jj] = dv;
+#pragma unroll
+      for (int k4 = 0; k4 < R / 4; ++k4) {
+        const float4 v = v4[k4], vb = vb4[k4];
+        ud[4 * k4] = fmaf(dv, v.x, ud[4 * k4]);
+        ud[4 * k4 + 1] = fmaf(dv, v.y, ud[4 * k4 + 1]);
+        ud[4 * k4 + 2] = fmaf(dv, v.z, ud[4 * k4 + 2]);
+        ud[4 * k4 + 3] = fmaf(dv, v.w, ud[4 * k4 + 3]);
+        wb[4 * k4] = fmaf(x, vb.x, wb[4 * k4]);
+        wb[4 * k4 + 1] = fmaf(x, vb.y, wb[4 * k4 + 1]);
+        wb[4 * k4 + 2] = fmaf(x, vb.z, wb[4 * k4 + 2]);
+        wb[4 * k4 + 3] = fmaf(x, vb.w, wb[4 * k4 + 3]);
+      }
+    }
+    tsum(lb_hi, lb_lo, lb);
+    __syncthreads();
+    af_colsum<R>(Dt, Us, a.part_vb, n, blockIdx.x, c0, c_end);
+  }
+  // the two column halves of each row: h = 1 hands its sums to h = 0
+  __syncthreads();
+  float* comb = sh;   // [128][2R + 1]
+  if (h == 1) {
+#pragma unroll
+    for (int k = 0; k < R; ++k) {
+      comb[ar * (2 * R + 1) + k] = ud[k];
+      comb[ar * (2 * R + 1) + R + k] = wb[k];
+    }
+  }
+  __syncthreads();
+  if (h == 0 && rvalid) {
+    const int64_t o = ((int64_t)blockIdx.y * m + arow) * R;
+#pragma unroll
+    for (int k = 0; k < R; ++k) {
+      a.part_ud[o + k] = ud[k] + comb[ar * (2 * R + 1) + k];
+      a.part_wb[o + k] = wb[k] + comb[ar * (2 * R + 1) + R + k];
+    }
+  }
+  __shared__ double red[256];
+  red[tid] = (double)lb_hi + (double)lb_lo;
+  __syncthreads();
+  for (int s = 128; s > 0; s >>= 1) {
+    if (tid < s) red[tid] += red[tid + s];
+    __syncthreads();
+  }
+  if (tid == 0) a.lam_part[(int64_t)blockIdx.y * gridDim.x + blockIdx.x] = red[0];
+}
+
 // ---------------------------------------------------------------------------
 // launchers
 // ---------------------------------------------------------------------------
@@ -570,6 +898,15 @@ cudaError_t prep_T() {
 
 cudaError_t prepare_unrolled_kernels() {
   cudaError_t e;
+  if ((e = cudaFuncSetAttribute(k_adj_fused<8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)(AfCfg<8, 3>::smem_floats * 4))) != cudaSuccess ||
+      (e = cudaFuncSetAttribute(k_adj_fused<16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)(AfCfg<16, 3>::smem_floats * 4))) != cudaSuccess ||
+      (e = cudaFuncSetAttribute(k_adj_a<8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)(AfCfg<8, 1>::smem_floats * 4))) != cudaSuccess ||
+      (e = cudaFuncSetAttribute(k_adj_a<16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)(AfCfg<16, 1>::smem_floats * 4))) != cudaSuccess)
+    return e;
   if ((e = prep_T<8>()) != cudaSuccess) return e;
   if ((e = prep_T<16>()) != cudaSuccess) return e;
   return prep_T<32>();
@@ -599,6 +936,26 @@ cudaError_t adj_T(const AdjArgs& a, int grid_cols, int n_splits, cudaStream_t s)
   if (e != cudaSuccess) return e;
   dim3 g((unsigned)((a.m + kAcRows - 1) / kAcRows), (unsigned)n_splits);
   k_adj_rows<R><<<g, 256, AcCfg<R>::smem_floats * 4, s>>>(a);
+  return cudaGetLastError();
+}
+
+// Passes B and C in one launch for R <= 16 (grid: row blocks x column splits).
+cudaError_t launch_adjoint_fused(int R, const AdjArgs& a, int n_splits, cudaStream_t s) {
+  const dim3 g((unsigned)((a.m + kAfRows - 1) / kAfRows), (unsigned)n_splits);
+  if (R == 8)
+    k_adj_fused<8><<<g, 256, AfCfg<8, 3>::smem_floats * 4, s>>>(a);
+  else
+    k_adj_fused<16><<<g, 256, AfCfg<16, 3>::smem_floats * 4, s>>>(a);
+  return cudaGetLastError();
+}
+
+// Pass A (row-block partials of X^T Pbar into part_vb) for R <= 16.
+cudaError_t launch_adjoint_a(int R, const AdjArgs& a, int n_splits, cudaStream_t s) {
+  const dim3 g((unsigned)((a.m + kAfRows - 1) / kAfRows), (unsigned)n_splits);
+  if (R == 8)
+    k_adj_a<8><<<g, 256, AfCfg<8, 1>::smem_floats * 4, s>>>(a);
+  else
+    k_adj_a<16><<<g, 256, AfCfg<16, 1>::smem_floats * 4, s>>>(a);
   return cudaGetLastError();
 }
 
@@ -644,6 +1001,7 @@ struct UnrolledState {
   float* Wbar = nullptr;
   float* part_ud = nullptr;
   float* part_wb = nullptr;
+  float* part_vb = nullptr;  // fused passes B, C: [row block][n][R]
   float* mats = nullptr;
   double* red = nullptr;
   float2* part = nullptr;
@@ -657,6 +1015,9 @@ struct UnrolledState {
   bool have_forward = false;
   bool with_loss = false;
   int n_cols_grid = 0, n_splits = 0;
+  bool fused_bc = false;     // passes B and C in one kernel (R <= 16)
+  int n_rb = 0;              // its row blocks
+  int n_lam = 0;             // lambda_bar partials
   int64_t split_cols = 0;
   int n_gram = 0;
 };
@@ -707,6 +1068,9 @@ dcf_status ensure_unrolled(dcf_handle h, int K) {
   u->n_cols_grid = grid;
   u->split_cols = split_cols;
   u->n_splits = (int)((n + split_cols - 1) / split_cols);
+  u->fused_bc = R <= 16;
+  u->n_rb = (int)((m + kAfRows - 1) / kAfRows);
+  u->n_lam = u->fused_bc ? u->n_rb * u->n_splits : grid;
   u->n_gram = (int)std::min<int64_t>(2LL * h->num_sms, std::max<int64_t>(1, std::max(m, n) / 32));
   // first-time buffers
   if (!u->Ub[0]) {
@@ -725,7 +1089,11 @@ dcf_status ensure_unrolled(dcf_handle h, int K) {
     u->red = (double*)dev_alloc(h, (size_t)kNumRed * kSlot * 8);
     u->part = (float2*)dev_alloc(h, (size_t)kMaxGramJobs * u->n_gram * kSlot * 8);
     u->sc = (double*)dev_alloc(h, (size_t)kNumSc * 8);
-    u->lam_part = (double*)dev_alloc(h, (size_t)grid * 8);
+    u->lam_part = (double*)dev_alloc(h, (size_t)u->n_lam * 8);
+    if (u->fused_bc) {
+      u->part_vb = (float*)dev_alloc(h, (size_t)u->n_rb * nR);
+      if (!u->part_vb) return fail(h, DCF_ENOMEM, "unrolled network buffers");
+    }
     u->hub_part = (double*)dev_alloc(h, (size_t)std::max(grid, h->n_vblocks) * 8);
     u->st = (DevState*)dev_alloc(h, sizeof(DevState));
     if (!u->Ub[0] || !u->Ub[1] || !u->Vb[0] || !u->Vb[1] || !u->Pb || !u->Wk || !u->Wbar ||
@@ -806,7 +1174,7 @@ SmallArgs small_args(dcf_handle h, int mode, int K, int step) {
   sa.loss = u->loss;
   sa.grads = u->grads;
   sa.lam_part = u->lam_part;
-  sa.n_lam_part = u->n_cols_grid;
+  sa.n_lam_part = u->n_lam;
   sa.st = u->st;
   return sa;
 }
@@ -1035,8 +1403,28 @@ extern "C" dcf_status dcf_unrolled_backward(dcf_handle h, double* grad_a, double
       add_mat(L, Ub, R, mat(h, MT_AHINV));
       UCK(launch_rowlin(R, L, s), "rowlin");
     }
-    // pass A: y1 = X^T Pbar (the V-step kernel with Pbar in place of W)
-    {
+    // pass A: y1 = X^T Pbar (R <= 16: k_adj_a's row-block partials; otherwise
+    // the V-step kernel with Pbar in place of W)
+    AdjArgs aa{};
+    aa.M = h->M;
+    aa.m = m;
+    aa.n = n;
+    aa.lam = (float)u->lam_k[k];
+    aa.U = Uk;
+    aa.V = Vk;
+    aa.Pb = u->Pb;
+    aa.W = u->Wk;
+    aa.Vn = Vn;
+    aa.Vtot = u->Vtot;
+    aa.Vbar = Vb2;
+    aa.lam_part = u->lam_part;
+    aa.part_ud = u->part_ud;
+    aa.part_wb = u->part_wb;
+    aa.part_vb = u->part_vb;
+    aa.split_cols = u->split_cols;
+    if (u->fused_bc) {
+      UCK(launch_adjoint_a(R, aa, u->n_splits, s), "adjoint pass A");
+    } else {
       IterArgs ia{};
       ia.cur = 0;
       ia.M = h->M;
@@ -1060,28 +1448,22 @@ extern "C" dcf_status dcf_unrolled_backward(dcf_handle h, double* grad_a, double
       RowLin L = rowlin(n, u->Vtot);
       add_mat(L, Vn, R, mat(h, MT_HBAR2));
       add_term(L, Vb, 1.f);
-      add_term(L, u->y1, 1.f);
+      if (u->fused_bc)
+        add_term(L, u->part_vb, 1.f, u->n_rb, (int64_t)nR);
+      else
+        add_term(L, u->y1, 1.f);
       UCK(launch_rowlin(R, L, s), "rowlin");
     }
     // passes B and C
     {
-      AdjArgs aa{};
-      aa.M = h->M;
-      aa.m = m;
-      aa.n = n;
-      aa.lam = (float)u->lam_k[k];
-      aa.U = Uk;
-      aa.V = Vk;
-      aa.Pb = u->Pb;
-      aa.W = u->Wk;
-      aa.Vn = Vn;
-      aa.Vtot = u->Vtot;
-      aa.Vbar = Vb2;
-      aa.lam_part = u->lam_part;
-      aa.part_ud = u->part_ud;
-      aa.part_wb = u->part_wb;
-      aa.split_cols = u->split_cols;
-      UCK(launch_adjoint_passes(R, aa, u->n_cols_grid, u->n_splits, s), "adjoint passes B, C");
+      if (u->fused_bc) {
+        UCK(launch_adjoint_fused(R, aa, u->n_splits, s), "adjoint passes B, C");
+        RowLin L = rowlin(n, Vb2);
+        add_term(L, u->part_vb, 1.f, u->n_rb, (int64_t)nR);
+        UCK(launch_rowlin(R, L, s), "rowlin");
+      } else {
+        UCK(launch_adjoint_passes(R, aa, u->n_cols_grid, u->n_splits, s), "adjoint passes B, C");
+      }
     }
     {
       RowLin L = rowlin(m, u->Wbar);
