@@ -169,13 +169,14 @@ def alg_bytes_per_iter(m, n, r):
 # The capture ran a smaller n; traffic grows in proportion to n (M is streamed
 # once, V read and written), so it is scaled by n.  None for other shapes.
 NCU_TRAFFIC = {
-    # the fused phase, m=4096, n=16384, r=32: k_fused on the first 13696 columns
-    # (229.04 MB read + 4.36 MB written) and on the idle SMs k_tc2 pass A (45.49 MB),
-    # k_tc2_vreduce (5.86 MB) and pass B (45.31 MB) on the last 2688
-    "fused_step": {"m": 4096, "r": 32, "n": 16384, "bytes": 330.06e6},
-    # k_tc2<64, 4, false, pair> / k_tc2<64, 7, true>, m=16384, n=16384, r=64
-    "pass_a": {"m": 16384, "r": 64, "n": 16384, "bytes": 1211.20e6},
-    "pass_b": {"m": 16384, "r": 64, "n": 16384, "bytes": 1087.02e6},
+    # the fused phase, m=4096, n=16384, r=32: k_fused on the first 13120 columns
+    # (219.44 MB read + 3.81 MB written) and on the idle SMs k_tc2 pass A (55.00 MB),
+    # k_tc2_vreduce (7.11 MB) and pass B (54.89 MB) on the last 3264
+    "fused_step": {"m": 4096, "r": 32, "n": 16384, "bytes": 340.25e6},
+    # k_tc2<64, 4, false, pair> / k_tc2<64, 7, true> (64 slabs x 7 strip groups),
+    # m=16384, n=16384, r=64
+    "pass_a": {"m": 16384, "r": 64, "n": 16384, "bytes": 1229.31e6},
+    "pass_b": {"m": 16384, "r": 64, "n": 16384, "bytes": 1117.22e6},
 }
 
 
@@ -790,8 +791,10 @@ def learned_rows(dcf, torch, args, rank, stream, count):
         if q == 0:
             # one training step of this problem: the network's forward with its loss
             # (checkpoints) and the hand-written reverse pass, which recomputes each
-            # step from its checkpoint and reads M three times per step
+            # step from its checkpoint and reads M twice per step (r <= 16); the
+            # profiler range marks these launches for `ncu --profile-from-start off`
             fwd, bwd = [], []
+            torch.cuda.profiler.start()
             for _ in range(3):
                 s.load_init(U0)
                 torch.cuda.synchronize()
@@ -806,9 +809,10 @@ def learned_rows(dcf, torch, args, rank, stream, count):
                 torch.cuda.synchronize()
                 fwd.append(e0.elapsed_time(e1))
                 bwd.append(e1.elapsed_time(e2))
+            torch.cuda.profiler.stop()
             b_ms = min(bwd)
             row.update(train_forward_ms=min(fwd), train_backward_ms=b_ms,
-                       backward_gbs=K * 3 * 4.0 * m * n / (b_ms * 1e-3) / 1e9)
+                       backward_gbs=K * 2 * 4.0 * m * n / (b_ms * 1e-3) / 1e9)
         rows.append(row)
         s.close()
         del Mt
@@ -830,7 +834,7 @@ def learned_summary(rows_th):
                 "forward_with_loss_ms": rows[0].get("train_forward_ms"),
                 "backward_ms": rows[0].get("train_backward_ms"),
                 "backward_alg_gbs": rows[0].get("backward_gbs"),
-                "backward_bytes": "K steps x 3 reads of M (4mn bytes each)",
+                "backward_bytes": "K steps x 2 reads of M (4mn bytes each)",
                 "adam_step_of_64_problems_ms_estimate":
                     64 * (rows[0].get("train_forward_ms", 0) + rows[0].get("train_backward_ms", 0))}}
 
