@@ -34,6 +34,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <initializer_list>
 #include <vector>
 
 #include "dcf.h"
@@ -111,6 +112,7 @@ enum Scalar { SC_C = 0, SC_ABAR, SC_RBAR, kNumSc };
 
 struct SmallArgs {
   int mode;
+  int mode2;           // a second, independent mode run after the first (-1: none)
   int R, k;            // padded rank, truth rank
   int r;               // the solver's rank (leading block of the r x r systems)
   int K, step;
@@ -138,16 +140,26 @@ __device__ double block_sum(double v, double* red) {
   return r;
 }
 
+__device__ void small_mode(const SmallArgs& a, int mode, double* dsh, double* red);
+
 __global__ void __launch_bounds__(256) k_unrolled_small(SmallArgs a) {
   extern __shared__ double dsh[];   // 3 R*R doubles, R*R double-floats
   __shared__ double red[256];
+  small_mode(a, a.mode, dsh, red);
+  if (a.mode2 >= 0) {
+    __syncthreads();
+    small_mode(a, a.mode2, dsh, red);
+  }
+}
+
+__device__ void small_mode(const SmallArgs& a, int mode, double* dsh, double* red) {
   const int R = a.R, k = a.k, RR = R * R;
   const int tid = threadIdx.x;
   const double* slot = a.red;
   auto S = [&](int s) { return slot + (size_t)s * kSlot; };
   float* mats = a.mats;
   auto Mt = [&](int s) { return mats + (size_t)s * kSlot; };
-  switch (a.mode) {
+  switch (mode) {
     case SM_LOSS_C: {
       double v = 0;
       for (int i = tid; i < k * k; i += blockDim.x) v += S(RD_AA)[i] * S(RD_BB)[i];
@@ -285,10 +297,18 @@ struct RowLin {
   int64_t pstride[3];     // floats between the partial copies of Y_s
 };
 
+// Up to three independent row jobs in one launch (blockIdx.y = job).
+struct RowLinSet {
+  RowLin L[3];
+  int n;
+};
+
 template <int R>
-__global__ void __launch_bounds__(256) k_rowlin(RowLin L) {
+__global__ void __launch_bounds__(256) k_rowlin(RowLinSet S) {
   extern __shared__ float msh[];   // the Mat_t, concatenated
   constexpr int CG = R / 8;
+  const RowLin& L = S.L[blockIdx.y];
+  if ((int64_t)blockIdx.x * 32 >= L.rows) return;
   const int tid = threadIdx.x;
   int off[3] = {0, 0, 0};
   {
@@ -913,20 +933,36 @@ cudaError_t prepare_unrolled_kernels() {
 }
 
 template <int R>
-cudaError_t rowlin_T(const RowLin& L, cudaStream_t s) {
+cudaError_t rowlin_T(const RowLinSet& S, cudaStream_t s) {
   size_t smem = 0;
-  for (int t = 0; t < L.nmat; ++t) smem += (size_t)L.cx[t] * R * 4;
-  const unsigned grid = (unsigned)((L.rows + 31) / 32);
-  k_rowlin<R><<<grid, 256, smem, s>>>(L);
+  int64_t rows = 0;
+  for (int j = 0; j < S.n; ++j) {
+    size_t sj = 0;
+    for (int t = 0; t < S.L[j].nmat; ++t) sj += (size_t)S.L[j].cx[t] * R * 4;
+    smem = sj > smem ? sj : smem;
+    rows = S.L[j].rows > rows ? S.L[j].rows : rows;
+  }
+  const dim3 grid((unsigned)((rows + 31) / 32), (unsigned)S.n);
+  k_rowlin<R><<<grid, 256, smem, s>>>(S);
   return cudaGetLastError();
 }
 
-cudaError_t launch_rowlin(int R, const RowLin& L, cudaStream_t s) {
-  switch (R) {
-    case 8: return rowlin_T<8>(L, s);
-    case 16: return rowlin_T<16>(L, s);
-    default: return rowlin_T<32>(L, s);
+// Independent row jobs (no job reads what another writes) in one launch.
+cudaError_t launch_rowlins(int R, std::initializer_list<RowLin> jobs, cudaStream_t s) {
+  RowLinSet S{};
+  for (const RowLin& L : jobs) {
+    if (S.n == 3) return cudaErrorInvalidValue;
+    S.L[S.n++] = L;
   }
+  switch (R) {
+    case 8: return rowlin_T<8>(S, s);
+    case 16: return rowlin_T<16>(S, s);
+    default: return rowlin_T<32>(S, s);
+  }
+}
+
+cudaError_t launch_rowlin(int R, const RowLin& L, cudaStream_t s) {
+  return launch_rowlins(R, {L}, s);
 }
 
 template <int R>
@@ -1156,6 +1192,7 @@ SmallArgs small_args(dcf_handle h, int mode, int K, int step) {
   UnrolledState* u = h->unrolled;
   SmallArgs sa{};
   sa.mode = mode;
+  sa.mode2 = -1;
   sa.R = h->R;
   sa.r = h->r;
   sa.k = h->k_truth;
@@ -1367,31 +1404,28 @@ extern "C" dcf_status dcf_unrolled_backward(dcf_handle h, double* grad_a, double
     const float alpha = (float)u->alpha_k[k];
     // loss gradient at (U_{k+1}, V_{k+1}), from the Grams the forward formed
     double* blk = ckslot(u, k + 1, 0);
-    auto small = [&](int mode) {
+    auto small = [&](int mode, int mode2 = -1) {
       SmallArgs sa = small_args(h, mode, K, k);
+      sa.mode2 = mode2;
       sa.red = blk;
       sa.red_prev = ckslot(u, k, 0);
       return launch_small(sa, s);
     };
-    UCK(small(SM_LOSSGRAD), "loss grad");
+    // with G^{-1}, H^{-1} of step k (independent of the loss gradient: one launch)
+    UCK(small(SM_LOSSGRAD, SM_RECOMP), "loss grad, recompute");
     {
       RowLin L = rowlin(m, Ub);
       add_mat(L, Uk1, R, mat(h, MT_SVV));
       add_mat(L, h->A_truth, kt, mat(h, MT_SBV));
       add_term(L, Ub, 1.f);
-      UCK(launch_rowlin(R, L, s), "rowlin");
       RowLin L2 = rowlin(n, Vb);
       add_mat(L2, Vn, R, mat(h, MT_SUU));
       add_mat(L2, h->B_truth, kt, mat(h, MT_SAU));
       add_term(L2, Vb, 1.f);
-      UCK(launch_rowlin(R, L2, s), "rowlin");
-    }
-    // G^{-1}, H^{-1} of step k and W = U_k G^{-1}
-    UCK(small(SM_RECOMP), "recompute");
-    {
-      RowLin L = rowlin(m, u->Wk);
-      add_mat(L, Uk, R, mat(h, MT_GINV));
-      UCK(launch_rowlin(R, L, s), "rowlin");
+      // W = U_k G^{-1}
+      RowLin L3 = rowlin(m, u->Wk);
+      add_mat(L3, Uk, R, mat(h, MT_GINV));
+      UCK(launch_rowlins(R, {L, L2, L3}, s), "rowlin");
     }
     // relaxation and U* = P H^{-1}
     UCK(grams(h, {{Us, R, Ub, R, m, blk + (size_t)RD_A1 * kSlot},
@@ -1456,19 +1490,17 @@ extern "C" dcf_status dcf_unrolled_backward(dcf_handle h, double* grad_a, double
     }
     // passes B and C
     {
-      if (u->fused_bc) {
-        UCK(launch_adjoint_fused(R, aa, u->n_splits, s), "adjoint passes B, C");
-        RowLin L = rowlin(n, Vb2);
-        add_term(L, u->part_vb, 1.f, u->n_rb, (int64_t)nR);
-        UCK(launch_rowlin(R, L, s), "rowlin");
-      } else {
-        UCK(launch_adjoint_passes(R, aa, u->n_cols_grid, u->n_splits, s), "adjoint passes B, C");
-      }
-    }
-    {
       RowLin L = rowlin(m, u->Wbar);
       add_term(L, u->part_wb, 1.f, u->n_splits, (int64_t)mR);
-      UCK(launch_rowlin(R, L, s), "rowlin");
+      if (u->fused_bc) {
+        UCK(launch_adjoint_fused(R, aa, u->n_splits, s), "adjoint passes B, C");
+        RowLin L2 = rowlin(n, Vb2);
+        add_term(L2, u->part_vb, 1.f, u->n_rb, (int64_t)nR);
+        UCK(launch_rowlins(R, {L, L2}, s), "rowlin");
+      } else {
+        UCK(launch_adjoint_passes(R, aa, u->n_cols_grid, u->n_splits, s), "adjoint passes B, C");
+        UCK(launch_rowlin(R, L, s), "rowlin");
+      }
     }
     UCK(grams(h, {{u->Wk, R, u->Wbar, R, m, blk + (size_t)RD_WWB * kSlot}}), "gram");
     UCK(small(SM_GBAR), "Gbar");
