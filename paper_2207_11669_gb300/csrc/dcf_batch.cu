@@ -56,7 +56,7 @@ struct BatchClass {
   BItem* mw = nullptr;  int n_mw = 0;     // (inst, 32-row block): rows (every instance)
   BItem* mwg = nullptr; int n_mwg = 0;    // (inst, 32-row block): make_w (general path)
   BItem* fp = nullptr;  int n_fp = 0;     // (inst, slab): U / W images (fused path)
-  BItem* fr = nullptr;  int n_fr = 0;     // (inst, block of 256): V_old Z (fused path)
+  BItem* fr = nullptr;  int n_fr = 0;     // (inst, block of 256 rows): V_old Z (fused path)
   BItem* p1 = nullptr;  int n_p1 = 0;     // (inst, strip)
   BItem* p2 = nullptr;  int n_p2 = 0;     // (inst, 128-row block, split)
   BItem* gv = nullptr;  int n_gv = 0;     // (inst, Gram chunk of V)
@@ -794,7 +794,7 @@ extern "C" dcf_status dcf_batch_create(const dcf_problem* problems, int count, i
       for (int g = 0; g < I.n_uitems; ++g) gu.push_back(BItem{q, g, 0, 0});
       if (I.fused) {
         for (int sl = 0; sl < I.nslabs; ++sl) fp.push_back(BItem{q, sl, 0, 0});
-        const int64_t blocks = (I.n * (I.R / 8) + 255) / 256;
+        const int64_t blocks = (I.n + 255) / 256;   // V_old Z: 256 rows per item
         for (int64_t bk = 0; bk < blocks; ++bk) fr.push_back(BItem{q, (int)bk, 0, 0});
       } else {
         for (int rb = 0; rb < I.n_rblocks; ++rb) mwg.push_back(BItem{q, rb, 0, 0});

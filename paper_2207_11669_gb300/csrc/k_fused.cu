@@ -936,6 +936,41 @@ __device__ __forceinline__ void rowmat_entry(const float* __restrict__ in, const
   dst[1] = make_float4(acc[4], acc[5], acc[6], acc[7]);
 }
 
+// Row `row` of out = in Z with all R outputs in one thread (R <= 32: the row
+// and its sums fit in registers; Z by broadcast from shared memory).  The sums
+// run over k in the order of rowmat_entry, so both give the same bits.
+template <int R>
+__device__ __forceinline__ void rowmat_row(const float* __restrict__ in, const float* Z, int64_t n,
+                                           float* __restrict__ out, int64_t row) {
+  static_assert(R <= 32, "registers");
+  if (row >= n) return;
+  float v[R];
+  const float4* src = reinterpret_cast<const float4*>(in + row * R);
+#pragma unroll
+  for (int k = 0; k < R / 4; ++k) {
+    const float4 t = src[k];
+    v[4 * k] = t.x; v[4 * k + 1] = t.y; v[4 * k + 2] = t.z; v[4 * k + 3] = t.w;
+  }
+  float acc[R];
+#pragma unroll
+  for (int l = 0; l < R; ++l) acc[l] = 0.f;
+#pragma unroll
+  for (int k = 0; k < R; ++k) {
+#pragma unroll
+    for (int l4 = 0; l4 < R / 4; ++l4) {
+      const float4 z = *reinterpret_cast<const float4*>(Z + k * R + 4 * l4);
+      acc[4 * l4] = fmaf(v[k], z.x, acc[4 * l4]);
+      acc[4 * l4 + 1] = fmaf(v[k], z.y, acc[4 * l4 + 1]);
+      acc[4 * l4 + 2] = fmaf(v[k], z.z, acc[4 * l4 + 2]);
+      acc[4 * l4 + 3] = fmaf(v[k], z.w, acc[4 * l4 + 3]);
+    }
+  }
+  float4* dst = reinterpret_cast<float4*>(out + row * R);
+#pragma unroll
+  for (int l4 = 0; l4 < R / 4; ++l4)
+    dst[l4] = make_float4(acc[4 * l4], acc[4 * l4 + 1], acc[4 * l4 + 2], acc[4 * l4 + 3]);
+}
+
 // One chunk blk of 256 entries (block-wide).
 template <int R, bool kFromGinv = false>
 __device__ __forceinline__ void rowmat_block(const float* __restrict__ in,
@@ -985,17 +1020,20 @@ __global__ void __launch_bounds__(256) k_fused_prep(const float* __restrict__ U,
                           (int64_t)blockIdx.x - nslabs);
 }
 
-// Batches: item (instance, block of 256 entries of V_old Z).
+// Batches: item (instance, block of 256 rows of V_old Z), one row per thread.
 template <int R>
 __global__ void __launch_bounds__(256) k_browmat(const BInst* __restrict__ insts,
                                                  const BItem* __restrict__ items, int nitems,
                                                  int cur) {
+  __shared__ __align__(16) float Z[R * R];
   for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
     const BItem w = items[it];
     const BInst& I = insts[w.inst];
     if (I.st->stop) continue;            // uniform over the block
     __syncthreads();                     // the previous item's shared Z is free
-    rowmat_block<R>(I.V[cur], I.zmat, nullptr, 0.f, I.n, I.VZ, w.a);
+    rowmat_fill_z<R, false>(Z, I.zmat, nullptr, 0.f);
+    __syncthreads();
+    rowmat_row<R>(I.V[cur], Z, I.n, I.VZ, (int64_t)w.a * 256 + threadIdx.x);
   }
 }
 
