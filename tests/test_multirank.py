@@ -96,3 +96,25 @@ def test_reference_arm_prints_the_contract_line():
     assert d["impl"] == "reference" and d["value"] > 0 and d["steps"] == 2
     assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["value"] == d["value"]
     assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["value"] == d["value"]
+
+
+def test_strip_groups_follow_the_wave_cost_rule():
+    """The algorithmic bytes of the two-pass passes count one P partial per
+    (slab, strip group); bench.py's strip-group count is the library's rule:
+    the smallest G whose wave cost ceil(nslabs G / SMs) / G is within 6 % of
+    the best, never more groups than strips."""
+    sys.path.insert(0, ROOT)
+    import bench
+    assert bench.tc2_strip_groups(64, 4096, 152) == 7      # large workload: 3 waves
+    assert bench.tc2_strip_groups(16, 1024, 152) == 9      # one wave of 144 CTAs
+    for nslabs, nstrips, sms in [(64, 4096, 152), (16, 1024, 152), (2, 1024, 152),
+                                 (17, 1024, 152), (64, 3, 152), (1, 1, 152), (40, 64, 132)]:
+        g = bench.tc2_strip_groups(nslabs, nstrips, sms)
+        assert 1 <= g <= max(1, nstrips)
+
+        def cost(x):
+            return -(-nslabs * x // sms) / x
+        gmax = max(1, min(nstrips, max(32, sms // nslabs)))
+        best = min(cost(x) for x in range(1, gmax + 1))
+        assert cost(g) <= 1.06 * best
+        assert all(cost(x) > 1.06 * best for x in range(1, g))
