@@ -983,20 +983,86 @@ __device__ __forceinline__ void rowmat_block(const float* __restrict__ in,
   rowmat_entry<R>(in, Z, n, out, blk * 256 + threadIdx.x);
 }
 
-// V_old Z in its own launch with Z formed once per CTA and the chunks walked
-// with a stride: at R = 64, where the preparation's slab part takes every
-// register, the combined launch would run its 8192 row blocks one CTA per SM.
-template <int R>
-__global__ void __launch_bounds__(256) k_rowmat(const DevState* st, const Smalls* sm, float rho,
-                                                const float* __restrict__ Vold, int64_t n,
-                                                float* __restrict__ VZ) {
+// V_old Z at R = 64 in its own launch (the preparation's slab part takes every
+// register there) as a register-tiled product: a CTA walks tiles of 64 rows,
+// staged in shared memory by cp.async (two stages, the next tile in flight),
+// and thread (row group rg, output group og) forms a 4 x 4 block of outputs
+// with 16 FMAs per two 16-byte shared loads.  Z = I - rho G^{-1} is formed once
+// per CTA.  Every output sums over k in order, as rowmat_entry does.
+constexpr int kRm64Rows = 64;
+constexpr int kRm64Ld = 68;                       // row stride (floats): 16-byte rows
+constexpr size_t kRm64Smem = (64 * 64 + 2 * kRm64Rows * kRm64Ld) * sizeof(float);
+
+__global__ void __launch_bounds__(256) k_rowmat64(const DevState* st, const Smalls* sm, float rho,
+                                                  const float* __restrict__ Vold, int64_t n,
+                                                  float* __restrict__ VZ) {
   if (st->stop) return;
-  __shared__ __align__(16) float Z[R * R];
-  rowmat_fill_z<R, true>(Z, sm->ginv32, sm->ginv32_lo, rho);
-  __syncthreads();
-  const int64_t nchunks = (n * (R / 8) + 255) / 256;
-  for (int64_t blk = blockIdx.x; blk < nchunks; blk += gridDim.x)
-    rowmat_entry<R>(Vold, Z, n, VZ, blk * 256 + threadIdx.x);
+  extern __shared__ __align__(16) float rsh[];
+  float* Z = rsh;                                 // [64][64]
+  float* Vs = rsh + 64 * 64;                      // [2][64 rows][68]
+  const int tid = threadIdx.x;
+  const int rg = tid >> 4, og = tid & 15;
+  const int64_t ntiles = (n + kRm64Rows - 1) / kRm64Rows;
+  auto stage = [&](int64_t tile, int b) {
+    float* dst = Vs + b * kRm64Rows * kRm64Ld;
+    const int64_t r0 = tile * kRm64Rows;
+    for (int i = tid; i < kRm64Rows * 16; i += 256) {   // 16 float4 per row
+      const int r = i >> 4, c4 = i & 15;
+      const bool ok = r0 + r < n;
+      const float* src = ok ? Vold + (r0 + r) * 64 + 4 * c4 : Vold;
+      const uint32_t d = (uint32_t)__cvta_generic_to_shared(dst + r * kRm64Ld + 4 * c4);
+      asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(d), "l"(src),
+                   "r"(ok ? 16 : 0)
+                   : "memory");
+    }
+    asm volatile("cp.async.commit_group;" ::: "memory");
+  };
+  int64_t tile = blockIdx.x;
+  if (tile < ntiles) stage(tile, 0);
+  rowmat_fill_z<64, true>(Z, sm->ginv32, sm->ginv32_lo, rho);
+  for (int b = 0; tile < ntiles; tile += gridDim.x, b ^= 1) {
+    const int64_t next = tile + gridDim.x;
+    if (next < ntiles) {
+      stage(next, b ^ 1);
+      asm volatile("cp.async.wait_group 1;" ::: "memory");
+    } else {
+      asm volatile("cp.async.wait_group 0;" ::: "memory");
+    }
+    __syncthreads();
+    const float* V = Vs + b * kRm64Rows * kRm64Ld + (4 * rg) * kRm64Ld;
+    float acc[4][4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+#pragma unroll
+      for (int o = 0; o < 4; ++o) acc[j][o] = 0.f;
+#pragma unroll 4
+    for (int k4 = 0; k4 < 16; ++k4) {
+      float4 v[4], z[4];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) v[j] = *reinterpret_cast<const float4*>(V + j * kRm64Ld + 4 * k4);
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+        z[i] = *reinterpret_cast<const float4*>(Z + (4 * k4 + i) * 64 + 4 * og);
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const float vk[4] = {v[j].x, v[j].y, v[j].z, v[j].w};
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          acc[j][0] = fmaf(vk[i], z[i].x, acc[j][0]);
+          acc[j][1] = fmaf(vk[i], z[i].y, acc[j][1]);
+          acc[j][2] = fmaf(vk[i], z[i].z, acc[j][2]);
+          acc[j][3] = fmaf(vk[i], z[i].w, acc[j][3]);
+        }
+      }
+    }
+    const int64_t r0 = tile * kRm64Rows + 4 * rg;
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+      if (r0 + j < n)
+        *reinterpret_cast<float4*>(VZ + (r0 + j) * 64 + 4 * og) =
+            make_float4(acc[j][0], acc[j][1], acc[j][2], acc[j][3]);
+    __syncthreads();   // stage b is refilled two tiles on
+  }
 }
 
 // The per-iteration preparation in one launch: blocks [0, nslabs) prepare the
@@ -1157,8 +1223,9 @@ cudaError_t launch_fused_prep(int R, const float* U, const Smalls* sm, const Dev
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    const int64_t g = std::max<int64_t>(1, std::min<int64_t>(zblocks, 4LL * sms));
-    k_rowmat<64><<<(unsigned)g, 256, 0, s>>>(st, sm, rho, Vold, n, VZ);
+    const int64_t tiles = (n + kRm64Rows - 1) / kRm64Rows;
+    const int64_t g = std::max<int64_t>(1, std::min<int64_t>(tiles, 4LL * sms));
+    k_rowmat64<<<(unsigned)g, 256, kRm64Smem, s>>>(st, sm, rho, Vold, n, VZ);
     return cudaGetLastError();
   }
   const unsigned grid = (unsigned)(nslabs + zblocks);
@@ -1174,8 +1241,11 @@ cudaError_t launch_fused_prep(int R, const float* U, const Smalls* sm, const Dev
 }
 
 cudaError_t fused_prep_prepare() {
-  return cudaFuncSetAttribute(k_fused_prep<64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              prep_smem<64>());
+  cudaError_t e = cudaFuncSetAttribute(k_fused_prep<64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       prep_smem<64>());
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(k_rowmat64, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)kRm64Smem);
 }
 
 template <int R, int NST>
