@@ -25,6 +25,9 @@ CASES = [
     (300, [100, 77, 140], 16, 12),
     (128, [33, 64, 31], 32, 20),
     (64, [10, 9, 11], 8, 3),
+    # m not a multiple of 4 (4-byte copies of M in the adjoint kernels; general
+    # path only) and column splits of several 32-column chunks
+    (130, [2600, 2403], 12, 6),
 ]
 PATHS = [dcf.PATH_GENERAL, dcf.PATH_FUSED]
 
