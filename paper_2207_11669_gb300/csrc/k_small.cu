@@ -161,7 +161,7 @@ __global__ void __launch_bounds__(256) k_gram_jobs(GramJobs g) {
 // kDelta = false: Q alone (Vo unused), for start-point Grams.
 template <int R>
 struct GvvCfg {
-  static constexpr int TB = R >= 32 ? 4 : 1;
+  static constexpr int TB = R >= 32 ? 4 : R >= 16 ? 2 : 1;
   static constexpr int NT = R / TB;                 // tiles per dimension
   static constexpr int GROUPS = 256 / (NT * NT);    // row groups
   static constexpr int CH = R >= 64 ? 32 : 64;      // rows per chunk
