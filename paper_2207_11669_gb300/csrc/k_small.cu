@@ -154,10 +154,10 @@ __global__ void __launch_bounds__(256) k_gram_jobs(GramJobs g) {
 // U-step and Q_old + Y is applied to U_{t-1}, where nearly collinear columns
 // cancel and FP32 sums of the products would be amplified by the condition
 // number.  Otherwise, and always for D (metric only), FP32 sums per chunk.
-// Thread tile TB x TB of each output (R >= 32: 4 x 4, R <= 16: 1 x 1) with
-// 256 / (R/TB)^2 row groups; 64-row chunks staged in shared memory, the next
-// chunk's loads in flight (registers) while the current one is used.  With
-// 4 x 4 tiles a warp reads a row's operands in 4 shared-memory wavefronts.
+// Thread tile TB x TB of each output (R >= 32: 4 x 4, R = 16: 2 x 2, R = 8:
+// 1 x 1) with 256 / (R/TB)^2 row groups; chunks of rows staged in shared
+// memory by a three-stage cp.async ring.  With 4 x 4 tiles a warp reads a
+// row's operands in 4 shared-memory wavefronts.
 // kDelta = false: Q alone (Vo unused), for start-point Grams.
 template <int R>
 struct GvvCfg {
