@@ -118,3 +118,24 @@ def test_strip_groups_follow_the_wave_cost_rule():
         best = min(cost(x) for x in range(1, gmax + 1))
         assert cost(g) <= 1.06 * best
         assert all(cost(x) > 1.06 * best for x in range(1, g))
+
+
+def test_kernel_bytes_and_scaled_traffic():
+    """The roofline's algorithmic bytes per launch (M once, V read and written,
+    the per-row factors; the two-pass kernels also move their column sums and
+    P partials) and the ncu traffic scaled from the captured n to the run's n."""
+    sys.path.insert(0, ROOT)
+    import bench
+    m, n, r = 4096, 65536, 32
+    kb = bench.kernel_bytes(m, n, r, 2, 152)
+    assert kb["fused_step"] == 4.0 * m * n + 8.0 * n * r + 8.0 * m * r
+    m, n, r = 16384, 262144, 64
+    kb = bench.kernel_bytes(m, n, r, 3, 152)
+    G = bench.tc2_strip_groups(m // 256, n // 64, 152)
+    assert kb["pass_a"] == 4.0 * m * n + 4.0 * n * r + 4.0 * (m // 512) * n * r + 8.0 * m * r
+    assert kb["pass_b"] == 4.0 * m * n + 8.0 * n * r + 4.0 * G * m * r + 4.0 * m * r
+    t = bench.ncu_traffic("pass_a", m, n, r)
+    assert t == bench.NCU_TRAFFIC["pass_a"]["bytes"] * n / bench.NCU_TRAFFIC["pass_a"]["n"]
+    assert bench.ncu_traffic("pass_a", m, n, 32) is None      # another rank: no capture
+    # traffic within a few percent of the algorithmic bytes: M is read once per pass
+    assert 0.98 < t / kb["pass_a"] < 1.05
